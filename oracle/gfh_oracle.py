@@ -1,0 +1,374 @@
+"""CPU oracle of the generalized FrequencyHough hot path (Miller et al., arXiv:1810.09784).
+
+TEST INFRASTRUCTURE ONLY.  Only the test-suite, the smoke check of the build entry module and the
+benchmark's CPU-baseline / reference leg may import or call this module.  The library in
+`paper_1810_09784_gb300/` never imports it, and it imports nothing from that library: the two paths
+share no code, tables or constants.  Everything here is plain, slow fp64 numpy (pure-Python loops
+only for the brute-force checks on tiny inputs), written from the paper's equations:
+
+  Sec. II   Eq. diff_powlaws  fdot = -k f^n;  Eq. powlaws  f(t) = f0 / (1 + k (n-1) f0^(n-1) (t-t0))^(1/(n-1))
+  Sec. II   k = |fdot0| / f0^n
+  Sec. III  peakmap: equalised spectra, peaks above a threshold that are local maxima
+  Sec. IV   Eq. transform  x = 1/f^(n-1), x0 = 1/f0^(n-1);  line x = x0 + (n-1) k (t - t0)
+  Sec. IV   each peak is a line in the (x0, k) plane; the Hough map is the histogram of lines
+  Sec. IV   candidates per region of the map, critical ratio CR = (y - mu)/sigma, distance d
+  Sec. VI.B Eq. dkeqn  dk = k((1 + df/f0max)^(-n) - 1)
+  Sec. VI.C dx0 = (n-1) df / f^n taken at the highest frequency f_max
+
+Where the paper is silent the readings are fixed here and listed in the design notes:
+  * time stamp of FFT i = its centre; t0 = start of the data (Sec. IV, Fig. hm caption)
+  * equaliser = clipped auto-regressive mean along frequency with an unbiasing gain (Sec. III
+    names only "an auto-regressive mean ... not sensitive to peaks"); boxcar window
+  * peak test: R > theta strictly and R strictly above both frequency neighbours, theta = 2.5 (Sec. VII)
+  * a peak of bin j covers x in [x(f_j + df/2), x(f_j - df/2)); it counts in every x0 column its
+    shifted interval overlaps (positions on a lattice of 2^-32 columns, rounded down)
+  * uniform k grid k_r = k_min + r dk; the shift of FFT i on row r is B_i + r S_i on that lattice
+  * one candidate per band of `band_hz` in f0: the maximum count, ties to the lowest (row, column);
+    columns whose centre f0 lies outside the analysis band are not candidates (Sec. IV, extended band)
+  * CR uses the population mean / std over all analysis-band cells of the map
+
+Parity status: every function below is pinned by the CPU tests (closed forms, brute force on tiny
+maps, invariants, the noise-only peak density p0) except the equaliser's constants, whose values the
+paper does not give ("parity unpinned" beyond the p0 statistic).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+FRAC_BITS = 32                  # fixed-point fraction bits of x0-column positions
+THETA = 2.5                     # peak threshold on the equalised spectrum (Sec. VII, Fig. h0mincompar)
+
+# Equaliser reading (Sec. III).  S is an AR(1) mean along frequency with weight 2^-7.  Each bin
+# enters as GAIN * P, clipped at CLIP * GAIN * S; GAIN = 1/(1 - exp(-CLIP)) makes the clipped update
+# unbiased for exponentially distributed noise power (E[min(P, CLIP mu)] = mu (1 - e^-CLIP)).  The
+# estimate starts as the plain mean of WARMUP bins below the first bin that is equalised.  The paper
+# fixes no precision; the peak decision is taken in float32 (IEEE-rounded per operation), the
+# precision of the GPU kernel, so the constants are float32 values.
+AR_WEIGHT = np.float32(0.0078125)       # 2^-7
+CLIP = 2.5
+GAIN = np.float32(1.08942544)           # float32(1 / (1 - exp(-2.5)))
+CLIP_GAIN = np.float32(2.72356367)      # float32(2.5 / (1 - exp(-2.5)))
+WARMUP = 128
+
+
+# ----------------------------------------------------------------------------------------------
+# Sec. II / IV closed forms
+# ----------------------------------------------------------------------------------------------
+def powerlaw_f(t, f0: float, k: float, n: float):
+    """Sec. II Eq. powlaws: f(t) = f0 / (1 + k (n-1) f0^(n-1) t)^(1/(n-1)), t measured from t0."""
+    return f0 / (1.0 + k * (n - 1.0) * f0 ** (n - 1.0) * np.asarray(t, dtype=np.float64)) ** (1.0 / (n - 1.0))
+
+
+def k_from_spindown(f0: float, fdot0: float, n: float) -> float:
+    """Sec. II: k = |fdot0| / f0^n."""
+    return abs(fdot0) / f0 ** n
+
+
+def x_of_f(f, n: float):
+    """Sec. IV Eq. transform: x = 1 / f^(n-1)."""
+    return np.asarray(f, dtype=np.float64) ** (1.0 - n)
+
+
+def f_of_x(x, n: float):
+    """Inverse of Sec. IV Eq. transform: f = x^(-1/(n-1))."""
+    return np.asarray(x, dtype=np.float64) ** (-1.0 / (n - 1.0))
+
+
+def dk_step(k: float, df: float, f0max: float, n: float) -> float:
+    """Sec. VI.B Eq. dkeqn: dk = k((1 + df/f0max)^(-n) - 1) (negative; its magnitude is the step)."""
+    return k * ((1.0 + df / f0max) ** (-n) - 1.0)
+
+
+def coincidence_distance(x0_a, k_a, x0_b, k_b, dx0: float, dk: float):
+    """Sec. IV distance between two points of the (x0, k) plane in units of bins."""
+    return np.sqrt(((np.asarray(x0_b) - x0_a) / dx0) ** 2 + ((np.asarray(k_b) - k_a) / dk) ** 2)
+
+
+def p0_local_max(theta: float) -> float:
+    """Probability that a bin of an iid exp(1) spectrum exceeds theta and both neighbours:
+    integral_theta^inf e^-x (1 - e^-x)^2 dx = e^-theta - e^-2theta + e^-3theta / 3."""
+    return math.exp(-theta) - math.exp(-2 * theta) + math.exp(-3 * theta) / 3.0
+
+
+# ----------------------------------------------------------------------------------------------
+# Sec. VI grids
+# ----------------------------------------------------------------------------------------------
+@dataclasses.dataclass
+class Grid:
+    """One Hough map: braking index, peakmap band, time stamps, k grid, analysis band."""
+
+    n: float
+    df: float               # frequency bin width 1/T_FFT
+    bin_lo: int             # peakmap band: bins bin_lo..bin_hi (f_j = j df)
+    bin_hi: int
+    n_fft: int
+    t_first: float          # time of FFT 0 from t0 (its centre)
+    t_hop: float            # time between FFTs
+    t_obs: float            # observation time
+    n_k: int                # k rows
+    k_min: float = 0.0
+    dk: float = 0.0         # 0: dx0 / ((n-1) T_obs), one x0 column of drift over T_obs per row
+    f_max: float = 0.0      # 0: bin_hi * df, the highest frequency of the band (Sec. VI.C)
+    ana_lo: float = 0.0     # analysis band [ana_lo, ana_hi) for candidates
+    ana_hi: float = 0.0
+    band_hz: float = 1.0    # candidate band width in f0
+    # derived by make_grid
+    dx0: float = 0.0
+    x0_min: float = 0.0
+    n_x0: int = 0
+
+
+def make_grid(g: Grid) -> Grid:
+    """Fill the derived fields: dx0 (Sec. VI.C, finest step at f_max), dk, x0_min, n_x0.
+
+    x0_min is one column left of the lowest x0 any peak can reach, x(f_top edge) - (n-1) k_max t_max;
+    n_x0 reaches one column past x(f_bottom edge).
+    """
+    g = dataclasses.replace(g)
+    n = g.n
+    if not (n > 1.0) or g.bin_lo < 1 or g.bin_hi < g.bin_lo or g.n_fft < 1 or g.n_k < 1:
+        raise ValueError("invalid grid request")
+    if g.f_max <= 0.0:
+        g.f_max = g.bin_hi * g.df
+    g.dx0 = (n - 1.0) * g.df / math.pow(g.f_max, n)
+    if g.dk <= 0.0:
+        g.dk = g.dx0 / ((n - 1.0) * g.t_obs)
+    k_max = g.k_min + (g.n_k - 1) * g.dk
+    t_max = g.t_first + (g.n_fft - 1) * g.t_hop
+    x_top = math.pow((g.bin_hi + 0.5) * g.df, 1.0 - n)
+    x_bot = math.pow((g.bin_lo - 0.5) * g.df, 1.0 - n)
+    g.x0_min = x_top - (n - 1.0) * k_max * t_max - g.dx0
+    g.n_x0 = int(math.ceil((x_bot - g.x0_min) / g.dx0)) + 1
+    return g
+
+
+def fixed_floor(v: float) -> int:
+    """floor(v * 2^32) as an exact integer."""
+    return math.floor(math.ldexp(v, FRAC_BITS))
+
+
+def edge_positions(g: Grid) -> list:
+    """U_e, e = 0..J: x of the bin edge f = (bin_lo + e - 1/2) df (Sec. IV Eq. transform), as an
+    x0-column position (x - x0_min)/dx0 on the 2^-32 lattice.  Bin j spans edges j-bin_lo
+    (lower f, larger x) and j-bin_lo+1 (upper f, smaller x)."""
+    J = g.bin_hi - g.bin_lo + 1
+    out = []
+    for e in range(J + 1):
+        x = math.pow((g.bin_lo + e - 0.5) * g.df, 1.0 - g.n)
+        out.append(fixed_floor((x - g.x0_min) / g.dx0))
+    return out
+
+
+def fft_shifts(g: Grid):
+    """(B_i, S_i): the shift (n-1) k t_i / dx0 of Sec. IV's line, for k = k_min (B) and per k row (S),
+    on the 2^-32 column lattice.  t_i = t_first + i t_hop."""
+    B, S = [], []
+    for i in range(g.n_fft):
+        t = g.t_first + i * g.t_hop
+        B.append(fixed_floor((g.n - 1.0) * g.k_min * t / g.dx0))
+        S.append(fixed_floor((g.n - 1.0) * g.dk * t / g.dx0))
+    return B, S
+
+
+def _peak_intervals(g: Grid, fft_idx, bins):
+    """Per in-band peak: (A_lo, A_hi, S) so that on row r its x0 interval is [A_lo - rS, A_hi - rS)."""
+    fft_idx = np.asarray(fft_idx, dtype=np.int64)
+    bins = np.asarray(bins, dtype=np.int64)
+    if fft_idx.size and (fft_idx.min() < 0 or fft_idx.max() >= g.n_fft):
+        raise ValueError("fft index out of range")
+    keep = (bins >= g.bin_lo) & (bins <= g.bin_hi)
+    fi, bj = fft_idx[keep], bins[keep] - g.bin_lo
+    U = np.array(edge_positions(g), dtype=np.int64)
+    B, S = (np.array(v, dtype=np.int64) for v in fft_shifts(g))
+    a_lo = U[bj + 1] - B[fi]        # upper-f edge: smallest x
+    a_hi = U[bj] - B[fi]            # lower-f edge: largest x
+    return a_lo, a_hi, S[fi]
+
+
+# ----------------------------------------------------------------------------------------------
+# Sec. IV Hough map
+# ----------------------------------------------------------------------------------------------
+def hough_map(g: Grid, fft_idx, bins) -> np.ndarray:
+    """Integer Hough map [n_k][n_x0] by differential counting: per row, +1 at the first column a
+    peak's interval touches, -1 after the last, then a running sum along x0 (Sec. IV, Sec. VI.C)."""
+    W, K = g.n_x0, g.n_k
+    a_lo, a_hi, S = _peak_intervals(g, fft_idx, bins)
+    out = np.zeros((K, W), dtype=np.int32)
+    for r in range(K):
+        lo = (a_lo - r * S) >> FRAC_BITS
+        hi = ((a_hi - r * S) - 1) >> FRAC_BITS
+        lo = np.maximum(lo, 0)
+        hi = np.minimum(hi, W - 1)
+        ok = lo <= hi
+        d = np.bincount(lo[ok], minlength=W + 1) - np.bincount(hi[ok] + 1, minlength=W + 1)
+        out[r] = np.cumsum(d[:W])
+    return out
+
+
+def hough_map_bruteforce(g: Grid, fft_idx, bins) -> np.ndarray:
+    """Same map by direct definition, cell by cell: count(r, m) = number of peaks whose interval on
+    row r overlaps column m, i.e. A_lo - rS < (m+1) 2^32 and A_hi - rS > m 2^32.  Tiny maps only."""
+    a_lo, a_hi, S = _peak_intervals(g, fft_idx, bins)
+    one = 1 << FRAC_BITS
+    out = np.zeros((g.n_k, g.n_x0), dtype=np.int32)
+    for r in range(g.n_k):
+        for m in range(g.n_x0):
+            c = 0
+            for p in range(len(a_lo)):
+                a = int(a_lo[p]) - r * int(S[p])
+                b = int(a_hi[p]) - r * int(S[p])
+                if a < (m + 1) * one and b > m * one:
+                    c += 1
+            out[r, m] = c
+    return out
+
+
+def hough_cells(g: Grid, fft_idx, bins, rows, cols) -> np.ndarray:
+    """Counts of the listed cells (rows[q], cols[q]) by the direct definition, vectorised over peaks."""
+    a_lo, a_hi, S = _peak_intervals(g, fft_idx, bins)
+    one = np.int64(1 << FRAC_BITS)
+    out = np.empty(len(rows), dtype=np.int64)
+    for q, (r, m) in enumerate(zip(rows, cols)):
+        a = a_lo - np.int64(r) * S
+        b = a_hi - np.int64(r) * S
+        out[q] = np.count_nonzero((a < (np.int64(m) + 1) * one) & (b > np.int64(m) * one))
+    return out
+
+
+def hough_row(g: Grid, fft_idx, bins, r: int) -> np.ndarray:
+    """One row of the map (differential counting), for large maps where the full map is too slow."""
+    W = g.n_x0
+    a_lo, a_hi, S = _peak_intervals(g, fft_idx, bins)
+    lo = np.maximum((a_lo - r * S) >> FRAC_BITS, 0)
+    hi = np.minimum(((a_hi - r * S) - 1) >> FRAC_BITS, W - 1)
+    ok = lo <= hi
+    d = np.bincount(lo[ok], minlength=W + 1) - np.bincount(hi[ok] + 1, minlength=W + 1)
+    return np.cumsum(d[:W]).astype(np.int32)
+
+
+# ----------------------------------------------------------------------------------------------
+# Sec. IV candidates
+# ----------------------------------------------------------------------------------------------
+def column_bands(g: Grid):
+    """Per x0 column m: the f0 of its centre (inverse of Eq. transform), f0^n, and its candidate
+    band index (floor((f0 - ana_lo)/band_hz), or -1 outside the analysis band)."""
+    W = g.n_x0
+    nb = n_bands(g)
+    f0c = np.zeros(W)
+    f0n = np.zeros(W)
+    band = np.full(W, -1, dtype=np.int64)
+    e = -1.0 / (g.n - 1.0)
+    for m in range(W):
+        x0c = g.x0_min + (m + 0.5) * g.dx0
+        if x0c <= 0.0:
+            continue
+        f = math.pow(x0c, e)
+        f0c[m] = f
+        f0n[m] = math.pow(f, g.n)
+        if g.ana_lo <= f < g.ana_hi:
+            band[m] = min(math.floor((f - g.ana_lo) / g.band_hz), nb - 1)
+    return f0c, f0n, band
+
+
+def n_bands(g: Grid) -> int:
+    return int(math.ceil((g.ana_hi - g.ana_lo) / g.band_hz))
+
+
+def select_candidates(g: Grid, hmap: np.ndarray):
+    """One candidate per f0 band: the cell of highest count over all rows and the band's columns,
+    ties to the lowest row then column; CR = (y - mu)/sigma over all analysis-band cells (Sec. IV).
+
+    Returns a list of dicts (bands without any column give no record) and (sum_y, sum_y2, n_cells).
+    """
+    f0c, f0n, band = column_bands(g)
+    K = g.n_k
+    ana = band >= 0
+    n_cells = K * int(np.count_nonzero(ana))
+    sub = hmap[:, ana].astype(np.int64)
+    s1 = int(sub.sum())
+    s2 = int((sub * sub).sum())
+    if n_cells > 0:
+        mu = float(s1) / float(n_cells)
+        var = float(s2) / float(n_cells) - mu * mu
+        sigma = math.sqrt(var) if var > 0.0 else 0.0
+    else:
+        mu, sigma = 0.0, 0.0
+    out = []
+    for b in range(n_bands(g)):
+        cols = np.nonzero(band == b)[0]
+        if cols.size == 0:
+            continue
+        block = hmap[:, cols]
+        flat = int(np.argmax(block))               # first maximum in (row, column) order
+        r, c = divmod(flat, cols.size)
+        m = int(cols[c])
+        y = int(hmap[r, m])
+        cr = (y - mu) / sigma if sigma > 0.0 else 0.0
+        k = g.k_min + r * g.dk
+        out.append(dict(band=b, row=r, col=m, count=y, cr=cr,
+                        x0=g.x0_min + (m + 0.5) * g.dx0, k=k,
+                        f0=float(f0c[m]), fdot0=-(k * float(f0n[m]))))
+    return out, (s1, s2, n_cells)
+
+
+# ----------------------------------------------------------------------------------------------
+# Sec. III peakmap
+# ----------------------------------------------------------------------------------------------
+def short_power_spectra(series, fs: float, t_fft: float):
+    """Interlaced (50% overlap) boxcar FFTs of length N = fs T_FFT (fp64); returns |X|^2 rounded to
+    float32, [n_fft][N/2+1]."""
+    x = np.asarray(series, dtype=np.float64)
+    N = int(round(fs * t_fft))
+    hop = N // 2
+    n_fft = (x.size - N) // hop + 1
+    frames = np.lib.stride_tricks.as_strided(x, shape=(n_fft, N), strides=(hop * 8, 8))
+    X = np.fft.rfft(frames, axis=1)
+    return (X.real * X.real + X.imag * X.imag).astype(np.float32)
+
+
+def equalise(P: np.ndarray, bin_lo: int, bin_hi: int, return_mean: bool = False):
+    """Equalised spectra R_j = P_j / S_(j-1) for bins bin_lo-1 .. bin_hi+1 (column c of the result
+    is bin bin_lo-1+c), in float32.  S is the clipped AR mean along frequency described at the top
+    of this module, updated after each bin, so a bin never whitens itself:
+        S <- sum of the WARMUP bins below bin_lo-1, times 2^-7;
+        per bin: R = P/S;  u = min(GAIN P, CLIP_GAIN S);  S <- S + 2^-7 (u - S).
+    With `return_mean` the estimate each bin was divided by is returned too."""
+    P = np.asarray(P, dtype=np.float32)
+    j0 = bin_lo - 1 - WARMUP
+    if j0 < 1:
+        raise ValueError("band too close to DC for the equaliser warm-up")
+    S = np.zeros(P.shape[0], dtype=np.float32)
+    for j in range(j0, j0 + WARMUP):
+        S = S + P[:, j]
+    S = S * np.float32(1.0 / WARMUP)
+    R = np.empty((P.shape[0], bin_hi - bin_lo + 3), dtype=np.float32)
+    used = np.empty_like(R)
+    for c, j in enumerate(range(bin_lo - 1, bin_hi + 2)):
+        p = P[:, j]
+        R[:, c] = p / S
+        used[:, c] = S
+        u = np.minimum(p * GAIN, S * CLIP_GAIN)
+        S = S + AR_WEIGHT * (u - S)
+    return (R, used) if return_mean else R
+
+
+def peaks_from_equalised(R: np.ndarray, bin_lo: int, theta: float = THETA):
+    """Sec. III peak selection: bin j is a peak iff R_j > theta and R_j > R_(j-1) and R_j > R_(j+1).
+    R's column c is bin bin_lo-1+c.  Returns (fft_idx, bin) sorted by bin, then FFT."""
+    mid = R[:, 1:-1]
+    sel = (mid > np.float32(theta)) & (mid > R[:, :-2]) & (mid > R[:, 2:])
+    b_idx, f_idx = np.nonzero(sel.T)
+    return f_idx.astype(np.uint32), (b_idx + bin_lo).astype(np.uint32)
+
+
+def peaks_from_power(P: np.ndarray, bin_lo: int, bin_hi: int, theta: float = THETA):
+    """Equalise power spectra P [n_fft][bins] and select peaks in bins bin_lo..bin_hi."""
+    return peaks_from_equalised(equalise(P, bin_lo, bin_hi), bin_lo, theta)
+
+
+def peakmap(series, fs: float, t_fft: float, bin_lo: int, bin_hi: int, theta: float = THETA):
+    """Sec. III: time series -> interlaced FFTs -> equalised spectra -> thresholded local maxima."""
+    return peaks_from_power(short_power_spectra(series, fs, t_fft), bin_lo, bin_hi, theta)

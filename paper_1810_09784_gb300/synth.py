@@ -1,0 +1,91 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module only draws inputs: white Gaussian strain noise and power-law spin-down injections
+(Sec. II, Eq. powlaws for f(t); the phase is the integral of Sec. V, Eq. phcor).  It holds no step of
+the FrequencyHough method itself (no peakmap, no x = f^(1-n) transform, no Hough accumulation, no
+candidate selection), so both the CUDA path and the CPU oracle can be fed from it.
+
+Every array is a deterministic function of its seed (numpy PCG64).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+
+@dataclasses.dataclass(frozen=True)
+class Injection:
+    """One power-law signal h(t) = amp * sin(phi(t) + phase0), f(t) from Sec. II Eq. powlaws."""
+
+    f0: float       # frequency at t0 = start of the data [Hz]
+    k: float        # spin-down constant of fdot = -k f^n (Sec. II Eq. diff_powlaws), k > 0
+    n: float        # braking index
+    amp: float      # strain amplitude in units of the noise sigma
+    phase0: float = 0.0
+
+    @property
+    def fdot0(self) -> float:
+        """Initial spin-down fdot0 = -k f0^n (Sec. II)."""
+        return -self.k * self.f0 ** self.n
+
+
+def amplitude_for_snr(snr: float, sigma: float, n_fft_samples: int) -> float:
+    """Amplitude giving a mean spectral SNR `snr` at a bin centre with a boxcar window.
+
+    A sinusoid of amplitude A gives |X|^2 = (A N / 2)^2 at its bin; white noise of variance
+    sigma^2 gives E|X|^2 = N sigma^2.  Their ratio A^2 N / (4 sigma^2) = snr.
+    """
+    return 2.0 * sigma * math.sqrt(snr / n_fft_samples)
+
+
+def powerlaw_phase(t: np.ndarray, f0: float, k: float, n: float) -> np.ndarray:
+    """phi(t) = 2 pi * integral_0^t f(t') dt' for f(t) = f0 (1 + a t)^(-1/(n-1)), a = (n-1) k f0^(n-1).
+
+    Closed form of the integral in Sec. V Eq. phcor: for n != 2 it is
+    f0 (n-1) / (a (n-2)) [(1 + a t)^((n-2)/(n-1)) - 1]; for n = 2 it is (f0 / a) ln(1 + a t).
+    """
+    a = (n - 1.0) * k * f0 ** (n - 1.0)
+    if a == 0.0:
+        return 2.0 * np.pi * f0 * t
+    if abs(n - 2.0) < 1e-12:
+        return 2.0 * np.pi * (f0 / a) * np.log1p(a * t)
+    e = (n - 2.0) / (n - 1.0)
+    return 2.0 * np.pi * f0 * (n - 1.0) / (a * (n - 2.0)) * np.expm1(e * np.log1p(a * t))
+
+
+def strain_series(n_samples: int, fs: float, seed: int, injections=(), sigma: float = 1.0,
+                  chunk: int = 1 << 22) -> np.ndarray:
+    """White Gaussian noise N(0, sigma^2) at `fs` plus injections, returned as float32.
+
+    Noise comes from numpy PCG64(seed); injections are added in float64 before rounding.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = np.empty(n_samples, dtype=np.float32)
+    for s0 in range(0, n_samples, chunk):
+        s1 = min(n_samples, s0 + chunk)
+        x = rng.standard_normal(s1 - s0) * sigma
+        if injections:
+            t = np.arange(s0, s1, dtype=np.float64) / fs
+            for inj in injections:
+                x += inj.amp * np.sin(powerlaw_phase(t, inj.f0, inj.k, inj.n) + inj.phase0)
+        out[s0:s1] = x
+    return out
+
+
+def random_peaklist(n_fft: int, bin_lo: int, bin_hi: int, density: float, seed: int):
+    """Random (fft_idx, bin) pairs sorted by (bin, fft_idx), at most one per cell.
+
+    A structural stand-in for a peakmap: each (FFT, bin) cell is occupied with probability
+    `density`, and two occupied cells of one FFT are never adjacent in frequency (a peakmap's
+    peaks are local maxima along frequency).  Used for Hough tests independent of the peakmap.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    nb = bin_hi - bin_lo + 1
+    occ = rng.random((n_fft, nb)) < density
+    # drop the right neighbour of every occupied cell, scanning left to right
+    for j in range(1, nb):
+        occ[:, j] &= ~occ[:, j - 1]
+    b_idx, f_idx = np.nonzero(occ.T)    # row-major over [bin][fft]: sorted by bin, then fft
+    return f_idx.astype(np.uint32), (b_idx + bin_lo).astype(np.uint32)
