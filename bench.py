@@ -1,0 +1,347 @@
+"""Benchmark of the generalized FrequencyHough search on GB300.
+
+One step = the whole path on one synthetic strain series: peakmap (cuFFT + equaliser + peak
+test + compaction), then the Hough maps of every analysis sub-band (differential accumulation,
+running sum, store) with the per-band candidates, all through the library's C ABI.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gfh|reference] [--workload NAME]
+
+Metric: Hough updates per second, one update = one peak drawn on one k row (sum over maps of
+peaks in the map's band x k rows).  Prints one JSON line on rank 0.  Under torchrun each rank
+searches its own series (independent data segments, seed + rank): weak scaling, no collective on
+the data path.  `--impl reference` times the CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import pathlib
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = pathlib.Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+from paper_1810_09784_gb300 import workloads  # noqa: E402
+
+PEAKS = json.loads((ROOT / "MEASURED_PEAKS.json").read_text()) if (ROOT / "MEASURED_PEAKS.json").exists() else {}
+HBM_PEAK = PEAKS.get("hbm_gbs", 6800.0)
+HBM_PEAK_SRC = "measured" if "hbm_gbs" in PEAKS else "fallback"
+SM_MAX_MHZ = PEAKS.get("sm_max_mhz", 2070.0)
+# Shared-memory atomic peak (no MEASURED_PEAKS entry exists): 152 SMs x 16 conflict-free 32-bit
+# shared atomics per clock (one warp instruction every two clocks over 32 banks) x max SM clock.
+N_SM = 152
+SMEM_ATOMIC_PEAK = N_SM * 16 * SM_MAX_MHZ * 1e6 / 1e9      # G atomics / s
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gfh", choices=["gfh", "reference"])
+    ap.add_argument("--workload", default="plain_paper", choices=["plain_paper", "plain_small"])
+    ap.add_argument("--tile", default=None, help="rows,cols,threads of the Hough tiles")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def workload(name, rank):
+    fn = getattr(workloads, name)
+    base = {"plain_paper": 2, "plain_small": 1}[name]
+    return fn(seed=base + 7919 * rank)
+
+
+def describe(name, spec, grids):
+    if name == "plain_paper":
+        return (f"plain_paper: white noise + 20 power-law injections, fs {spec.fs:g} Hz, "
+                f"{spec.t_obs:g} s, T_FFT {spec.t_fft:g} s ({spec.n_fft} FFTs), 50-2000 Hz in "
+                f"{len(grids)} sub-bands (100 Hz + 50 Hz peakmap extension), n = 5, "
+                f"{grids[0]['n_k']} k rows, top candidate per 1 Hz")
+    return (f"plain_small: fs {spec.fs:g} Hz, {spec.t_obs:g} s, T_FFT {spec.t_fft:g} s "
+            f"({spec.n_fft} FFTs), 100-400 Hz, n = 5, {grids[0]['n_k']} k rows")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        self.f.flush()
+        rows = [l.split(", ") for l in pathlib.Path(self.f.name).read_text().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if len(r) > 5 + i and r[5 + i].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": float(rows[0][2]) if rows[0][2].replace(".", "").isdigit() else None,
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit()) if rows else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+def traffic_for(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None when the kernel's
+    source changed since the counters were taken."""
+    p = ROOT / "profiles" / "traffic.json"
+    if not p.exists():
+        return None
+    rec = json.loads(p.read_text()).get(kernel)
+    if not rec:
+        return None
+    src = (ROOT / rec["source"]).read_bytes()
+    return rec["bytes_per_launch"] if hashlib.sha256(src).hexdigest() == rec["sha256"] else None
+
+
+# ---------------------------------------------------------------------------------------------
+# CPU oracle (baseline / reference arm)
+# ---------------------------------------------------------------------------------------------
+
+def oracle_sample(name, rank=0, rows_per_map=20):
+    """Times the oracle on a bounded sample: the full peakmap, then `rows_per_map` k rows of every
+    map; the step time is extrapolated to all rows."""
+    from oracle import gfh_oracle as O
+    spec, pm, grids = workload(name, rank)
+    x = spec.series()
+    t0 = time.perf_counter()
+    fi, bj = O.peakmap(x, spec.fs, spec.t_fft, pm["bin_lo"], pm["bin_hi"])
+    t_pm = time.perf_counter() - t0
+    t_rows, updates = 0.0, 0
+    for f in grids:
+        og = O.make_grid(O.Grid(**{k: v for k, v in f.items() if k not in ("list",)}))
+        sel = (bj >= og.bin_lo) & (bj <= og.bin_hi)
+        updates += int(sel.sum()) * og.n_k
+        rows = np.linspace(0, og.n_k - 1, rows_per_map).astype(int)
+        t1 = time.perf_counter()
+        for r in rows:
+            O.hough_row(og, fi, bj, int(r))
+        t_rows += (time.perf_counter() - t1) * og.n_k / rows_per_map
+    t_step = t_pm + t_rows
+    sample = (f"oracle peakmap of the full series ({t_pm:.1f} s) + {rows_per_map} of the k rows of "
+              f"each of the {len(grids)} maps, extrapolated to all rows; numpy, 1 thread")
+    return updates / t_step, t_step, sample
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    vals, times = [], []
+    for i in range(args.warmup + args.steps):
+        v, t, sample = oracle_sample(args.workload, 0, rows_per_map=10)
+        if i >= args.warmup:
+            vals.append(v)
+            times.append(t)
+    spec, pm, grids = workload(args.workload, 0)
+    value = float(np.mean(vals))
+    line = {"impl": "reference", "metric": "Hough updates/s (peaks x k-bins)", "value": value,
+            "unit": "updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32 counts, fp32 spectra, fp64 grid",
+            "data": "synthetic", "config": {"workload": describe(args.workload, spec, grids)},
+            "cpu_baseline": {"value": value, "unit": "updates/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------------------------
+
+def run_gpu(args):
+    import torch
+
+    from paper_1810_09784_gb300 import build as _build
+    from paper_1810_09784_gb300 import gfh
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    _build.build()
+    stream = torch.cuda.current_stream()
+    ctx = gfh.Context(local, stream)
+
+    spec, pm, grid_fields = workload(args.workload, rank)
+    x_host = torch.from_numpy(spec.series()).pin_memory()
+    x_dev = x_host.cuda()
+    grids = [gfh.grid_make(gfh.Grid(**f)) for f in grid_fields]
+    maps = [torch.empty((g.n_k, g.ld_x0), dtype=torch.int32, device="cuda") for g in grids]
+    cands = [torch.empty(g.n_bands * gfh.CANDIDATE_BYTES, dtype=torch.uint8, device="cuda") for g in grids]
+    stats = torch.empty(len(grids) * gfh.STATS_BYTES, dtype=torch.uint8, device="cuda")
+    cand_host = [torch.empty_like(c, device="cpu").pin_memory() for c in cands]
+    tile = tuple(int(v) for v in args.tile.split(",")) if args.tile else None
+    t_plan = time.perf_counter()
+    plan = gfh.Plan(ctx, grids, maps, cands, stats, tile=tile)
+    t_plan = time.perf_counter() - t_plan
+    cap = int(spec.n_fft * (pm["bin_hi"] - pm["bin_lo"] + 1) * 0.12) + 1024
+    fo = torch.empty(cap, dtype=torch.int32, device="cuda")
+    bo = torch.empty(cap, dtype=torch.int32, device="cuda")
+    off = torch.zeros(2, dtype=torch.int64, device="cuda")
+
+    state = {}
+
+    def step(h2d=False):
+        if h2d:
+            x_dev.copy_(x_host, non_blocking=True)
+        n = ctx.peakmap(x_dev, spec.fs, spec.t_fft, pm["bin_lo"], pm["bin_hi"], 2.5, fo, bo)
+        state["n"] = n
+        off[1] = n
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.execute(fo, bo, off, 1)
+        e1.record(stream)
+        if h2d:
+            for c, h in zip(cands, cand_host):
+                h.copy_(c, non_blocking=True)
+        return e0, e1
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if ctx.check() != gfh.GFH_OK:
+        raise RuntimeError("input check failed")
+    # updates of this rank's step: peaks inside each map's band x its k rows
+    bins = bo[: state["n"]].cpu().numpy()
+    updates = sum(int(((bins >= g.bin_lo) & (bins <= g.bin_hi)).sum()) * g.n_k for g in grids)
+    launches_per_step = 8   # k_equalise, k_count, k_scan, k_scatter, k_check_sorted, k_csr, k_hough, k_finalize
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def maxed(v):
+        if world == 1:
+            return v
+        import torch.distributed as dist
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sumd(v):
+        if world == 1:
+            return v
+        import torch.distributed as dist
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    # ---- device-resident timing
+    sampler = ClockSampler(local)
+    with sampler:
+        barrier()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        hough = [step() for _ in range(args.steps)]
+        b.record(stream)
+        barrier()
+    clocks = sampler.summary()
+    ms = a.elapsed_time(b) / args.steps
+    ms_hough = sum(e0.elapsed_time(e1) for e0, e1 in hough) / args.steps
+    ms_max = maxed(ms)
+    total_updates = sumd(float(updates))
+    value = total_updates / (ms_max * 1e-3)
+
+    # ---- end to end through the public API with host buffers
+    barrier()
+    a.record(stream)
+    for _ in range(args.steps):
+        step(h2d=True)
+    b.record(stream)
+    barrier()
+    ms_e2e = maxed(a.elapsed_time(b) / args.steps)
+    h2d = x_host.numel() * 4
+    d2h = sum(c.numel() for c in cands)
+
+    if rank != 0:
+        plan.close()
+        ctx.close()
+        return
+    atomics = 2.0 * updates
+    achieved = atomics / (ms_hough * 1e-3) / 1e9
+    map_bytes = sum(g.n_k * g.ld_x0 * 4 for g in grids)
+    line = {
+        "metric": "Hough updates/s (peaks x k-bins)", "value": value, "unit": "updates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32 counts, fp32 spectra, fp64 grid", "data": "synthetic",
+        "config": {"workload": describe(args.workload, spec, grid_fields),
+                   "maps": len(grids), "peaks": state["n"], "updates_per_step": updates,
+                   "cells": int(sum(g.n_k * g.n_x0 for g in grids)),
+                   "l2": "inputs larger than L2: 165 MB series and 0.9 GB of maps per step" if args.workload == "plain_paper" else "small workload",
+                   "tile": list(tile) if tile else "default", "plan_build_s": round(t_plan, 3)},
+        "breakdown_ms": {"step": ms, "hough_select": ms_hough, "peakmap": ms - ms_hough},
+        "roofline": {"bound": "smem_atomic", "kernel": "k_hough", "achieved": achieved,
+                     "peak": SMEM_ATOMIC_PEAK, "unit": "Gatomic/s", "frac": achieved / SMEM_ATOMIC_PEAK,
+                     "peak_source": "derived: 152 SMs x 16 shared atomics/clk x max SM clock",
+                     "traffic": traffic_for("k_hough"),
+                     "hbm": {"map_store_bytes": map_bytes, "achieved_gbs": map_bytes / (ms_hough * 1e-3) / 1e9,
+                             "peak_gbs": HBM_PEAK, "frac": map_bytes / (ms_hough * 1e-3) / 1e9 / HBM_PEAK,
+                             "peak_source": HBM_PEAK_SRC}},
+        "e2e": {"value": total_updates / (ms_e2e * 1e-3), "unit": "updates/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        v, t, sample = oracle_sample(args.workload)
+        line["cpu_baseline"] = {"value": v, "unit": "updates/s", "cores": 1, "kind": "oracle", "sample": sample}
+    print(json.dumps(line), flush=True)
+    plan.close()
+    ctx.close()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

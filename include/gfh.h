@@ -1,0 +1,232 @@
+/*
+ * gfh.h - C ABI of the generalized FrequencyHough library for GB300 (sm_103a).
+ *
+ * The method (Miller et al., "A method to search for long duration gravitational wave transients
+ * from isolated neutron stars using the generalized FrequencyHough", arXiv:1810.09784):
+ *   Sec. III   a peakmap is the set of (time, frequency) points of equalised short-FFT spectra that
+ *              exceed a threshold and are local maxima;
+ *   Sec. IV    Eq. transform maps each peak frequency to x = f^(1-n); a power-law spin-down
+ *              (Sec. II Eq. powlaws) is then the line x = x0 + (n-1) k (t - t0), so each peak is
+ *              a line in the (x0, k) plane and the Hough map is the integer histogram of those
+ *              lines; candidates are the highest counts per region, ranked by the critical ratio;
+ *   Sec. VI.C  the x0 step is the finest one, dx0 = (n-1) df / f_max^n.
+ * This library computes the peakmap, the integer Hough map and the per-band candidates on the GPU.
+ *
+ * Conventions for every entry point:
+ *   - Device pointers ("d_" prefix) are allocated and owned by the caller; the library never frees
+ *     them.  Host pointers ("h_" prefix or no prefix on plain structs) are read or written
+ *     synchronously before the call returns.
+ *   - All GPU work is issued on the stream bound to the context (gfh_create / gfh_set_stream) and
+ *     is asynchronous unless a function says it synchronises.
+ *   - Return value: GFH_OK (0) or a negative GFH_ERR_* code; nothing aborts and nothing throws.
+ *     Data errors found on the device (unsorted peaks, out-of-range FFT index) are recorded in a
+ *     device flag that gfh_check() reads and clears; the GPU context stays usable.
+ *   - Peak lists are two parallel uint32 arrays: fft_idx (FFT number i, time t_i = t_first +
+ *     i * t_hop from t0) and bin (frequency bin j, f_j = j * df), sorted by bin ascending (the
+ *     order within one bin is free).  A peakmap never has two peaks in one (FFT, bin) cell.
+ *   - A Hough map is int32 [n_k][ld_x0] row-major: row r is k_r = k_min + r dk, column m is the
+ *     x0 interval [x0_min + m dx0, x0_min + (m+1) dx0).  Columns n_x0 .. ld_x0-1 are written 0.
+ */
+#ifndef GFH_H
+#define GFH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GFH_OK 0
+#define GFH_ERR_ARG (-1)      /* invalid argument: null pointer, n <= 1, empty band, bad size */
+#define GFH_ERR_SIZE (-2)     /* capacity too small, or a size that overflows the index types */
+#define GFH_ERR_CUDA (-3)     /* a CUDA runtime or cuFFT call failed */
+#define GFH_ERR_INPUT (-4)    /* device-side input check failed (see gfh_check) */
+#define GFH_ERR_TIMEOUT (-5)  /* a bounded device-side wait ran out */
+#define GFH_ERR_NOMEM (-6)    /* a library-owned allocation failed */
+
+typedef struct gfh_ctx gfh_ctx;
+typedef struct gfh_plan gfh_plan;
+
+/*
+ * One Hough map (Sec. IV-VI).  The caller fills the request fields; gfh_grid_make fills the rest.
+ *   n            braking index, n > 1 (Sec. I Eq. 1; Sec. II Eq. diff_powlaws fdot = -k f^n)
+ *   df           frequency bin width 1/T_FFT [Hz]
+ *   bin_lo..hi   peakmap band of this map, inclusive bins (f_j = j df); peaks outside are ignored
+ *   n_fft        number of FFTs; t_first, t_hop give t_i = t_first + i t_hop from t0 [s]
+ *   t_obs        observation time [s], used by the default k step
+ *   n_k, k_min, dk   uniform k grid k_r = k_min + r dk; dk <= 0 selects dk = dx0/((n-1) t_obs),
+ *                one x0 column of drift over t_obs per k row
+ *   f_max        frequency of the finest x0 step (Sec. VI.C); <= 0 selects bin_hi * df
+ *   ana_lo, ana_hi   analysis band [Hz): candidates are taken only in columns whose centre f0 lies
+ *                inside it (Sec. IV: the peakmap band is wider than the analysed band)
+ *   band_hz      candidate band width in f0 [Hz]: one candidate per band
+ *   list         index of the peak list this map reads (gfh_plan_execute)
+ * Derived: dx0 = (n-1) df / f_max^n; x0_min = x(f_top edge) - (n-1) k_max t_max - dx0;
+ *   n_x0 = ceil((x(f_bottom edge) - x0_min)/dx0) + 1; ld_x0 = n_x0 rounded up to 32;
+ *   n_bands = ceil((ana_hi - ana_lo)/band_hz).
+ */
+typedef struct gfh_grid {
+  double n;
+  double df;
+  int32_t bin_lo;
+  int32_t bin_hi;
+  int32_t n_fft;
+  int32_t n_k;
+  double t_first;
+  double t_hop;
+  double t_obs;
+  double k_min;
+  double dk;
+  double f_max;
+  double ana_lo;
+  double ana_hi;
+  double band_hz;
+  int32_t list;
+  int32_t n_bands;  /* derived */
+  double dx0;       /* derived */
+  double x0_min;    /* derived */
+  int64_t n_x0;     /* derived */
+  int64_t ld_x0;    /* derived */
+} gfh_grid;
+
+/*
+ * One candidate (Sec. IV): the highest count of the map over all k rows and the columns of one f0
+ * band, ties to the lowest row then the lowest column.  cr = (count - mu)/sigma with mu, sigma the
+ * population mean and standard deviation over all analysis-band cells (0 when sigma = 0).
+ * f0 = x0^(-1/(n-1)) (inverse of Eq. transform) and fdot0 = -k f0^n at the column centre.
+ * count = -1 marks a band that holds no column.
+ */
+typedef struct gfh_candidate {
+  int32_t band;
+  int32_t row;
+  int64_t col;
+  int32_t count;
+  int32_t reserved;
+  double cr;
+  double x0;
+  double k;
+  double f0;
+  double fdot0;
+} gfh_candidate;
+
+/* Per-map statistics of the analysis-band cells: sum of counts, sum of squared counts, cells. */
+typedef struct gfh_map_stats {
+  int64_t sum;
+  int64_t sum_sq;
+  int64_t cells;
+} gfh_map_stats;
+
+/*
+ * Peak lists for gfh_plan_execute: all lists concatenated in fft_idx / bin (device arrays);
+ * list l is entries [offsets[l], offsets[l+1]) (device array of n_lists + 1 int64).
+ */
+typedef struct gfh_peaks {
+  const uint32_t* fft_idx;
+  const uint32_t* bin;
+  const int64_t* offsets;
+  int32_t n_lists;
+} gfh_peaks;
+
+/* Tile shape of the Hough kernel; zero fields pick the library default (gfh_autotune finds one). */
+typedef struct gfh_tile_config {
+  int32_t rows;     /* k rows per tile: 8, 16 or 32 */
+  int32_t cols;     /* x0 columns per tile, multiple of 128 */
+  int32_t threads;  /* threads per block: 256 or 512 */
+  int32_t reserved;
+} gfh_tile_config;
+
+/* Context: binds a device and a stream (cudaStream_t passed as void*; NULL = legacy default). */
+int gfh_create(gfh_ctx** out, int device, void* stream);
+int gfh_destroy(gfh_ctx* ctx);
+int gfh_set_stream(gfh_ctx* ctx, void* stream);
+/* Synchronises the stream, then returns and clears the device-side input-check flag:
+ * GFH_OK, or GFH_ERR_INPUT when the last calls saw unsorted peaks or an out-of-range index. */
+int gfh_check(gfh_ctx* ctx);
+const char* gfh_strerror(int code);
+
+/* ---- host-side planning (no GPU needed) ---------------------------------------------------- */
+
+/* Fills the derived fields of *g (Sec. VI.B-C).  Errors: GFH_ERR_ARG for an invalid request. */
+int gfh_grid_make(gfh_grid* g);
+
+/*
+ * Fixed-point tables of one grid, for inspection (the plan builds its own copy).  Positions are in
+ * x0 columns on a lattice of 2^-32 column, rounded down:
+ *   h_U[e], e = 0..bin_hi-bin_lo+1: (x(f_e) - x0_min)/dx0 with f_e = (bin_lo + e - 1/2) df;
+ *   h_B[i], h_S[i], i < n_fft: (n-1) k_min t_i / dx0 and (n-1) dk t_i / dx0.
+ * A peak (i, j) covers, on row r, the half-open interval [h_U[j-bin_lo+1] - B_i - r S_i,
+ * h_U[j-bin_lo] - B_i - r S_i) (Sec. IV: the line x0 = x - (n-1) k t_i of every x in the bin).
+ * Any output pointer may be NULL.
+ */
+int gfh_grid_tables(const gfh_grid* g, int64_t* h_U, int64_t* h_B, int64_t* h_S);
+
+/* Per column m < n_x0: candidate band (-1 outside the analysis band), f0 and f0^n of its centre. */
+int gfh_grid_columns(const gfh_grid* g, int32_t* h_band, double* h_f0, double* h_f0n);
+
+/* ---- GPU entry points ----------------------------------------------------------------------- */
+
+/*
+ * Peak selection on given power spectra (Sec. III): d_power is float32 [n_fft][ld] row-major,
+ * column j = bin j, ld >= bin_hi + 2.  Each spectrum is equalised by a clipped auto-regressive
+ * mean S along frequency, in float32 with every operation IEEE-rounded (the paper fixes no
+ * precision): S starts as the sum of the 128 bins below bin_lo - 1 times 2^-7 (so bin_lo >= 130);
+ * then for bins bin_lo-1 .. bin_hi+1 in order: R_j = P_j / S, u = min(G P_j, 2.5 G S),
+ * S = S + 2^-7 (u - S), with G = float32(1/(1 - e^-2.5)) = 1.08942544 and 2.5 G rounded to
+ * 2.72356367.  Bin j in [bin_lo, bin_hi] is a peak iff R_j > theta and R_j > R_(j-1) and
+ * R_j > R_(j+1) (theta rounded to float32; the paper uses 2.5, Sec. VII).
+ * Output: at most cap peaks into d_fft_idx / d_bin, sorted by bin then FFT; *h_n_peaks = total
+ * number of peaks found.  Synchronises the stream.  GFH_ERR_SIZE when the total exceeds cap
+ * (the outputs then hold the first cap peaks of that order).
+ */
+int gfh_peaks_from_power(gfh_ctx* ctx, const float* d_power, int64_t ld, int32_t n_fft,
+                         int32_t bin_lo, int32_t bin_hi, double theta, uint32_t* d_fft_idx,
+                         uint32_t* d_bin, int64_t cap, int64_t* h_n_peaks);
+
+/*
+ * Peakmap of a time series (Sec. III): d_series float32 [n_samples] at fs Hz; FFTs of
+ * N = round(fs t_fft) samples with hop N/2 (interlaced, boxcar window), FFT i starting at sample
+ * i N/2, n_fft = (n_samples - N)/(N/2) + 1, bin_hi + 1 <= N/2; |X|^2 = re*re + im*im in float32
+ * from a cuFFT R2C transform (unnormalised), then the equaliser and peak test of
+ * gfh_peaks_from_power.  Same outputs, errors and synchronisation.
+ */
+int gfh_peakmap(gfh_ctx* ctx, const float* d_series, int64_t n_samples, double fs, double t_fft,
+                int32_t bin_lo, int32_t bin_hi, double theta, uint32_t* d_fft_idx,
+                uint32_t* d_bin, int64_t cap, int64_t* h_n_peaks);
+
+/*
+ * Plan for Hough maps plus candidates of n_maps grids (each made by gfh_grid_make), bound to
+ * caller-owned outputs: h_maps[m] -> int32 [n_k][ld_x0] of grid m, h_cands[m] -> n_bands
+ * gfh_candidate, d_stats -> n_maps gfh_map_stats (device).  h_cands or d_stats may be NULL (no
+ * candidates).  The plan copies the grids, builds the fixed-point and column tables on the host
+ * and uploads them; it owns that device memory until gfh_plan_destroy.  cfg may be NULL.
+ * Errors: GFH_ERR_ARG, GFH_ERR_SIZE (n_k * n_x0 >= 2^32 - 1), GFH_ERR_NOMEM, GFH_ERR_CUDA.
+ */
+int gfh_plan_create(gfh_ctx* ctx, int32_t n_maps, const gfh_grid* grids, int32_t* const* h_maps,
+                    gfh_candidate* const* h_cands, gfh_map_stats* d_stats,
+                    const gfh_tile_config* cfg, gfh_plan** out);
+int gfh_plan_destroy(gfh_plan* plan);
+
+/*
+ * Runs the plan on peak lists: every map reads list grids[m].list.  Writes all maps, and the
+ * candidates and statistics if bound.  Asynchronous; no host synchronisation and no allocation,
+ * so it can be captured in a CUDA graph.  Input errors are reported through gfh_check.
+ */
+int gfh_plan_execute(gfh_plan* plan, const gfh_peaks* peaks);
+
+/* Convenience: one grid, one peak list of n_peaks entries; plan, execute, destroy. */
+int gfh_hough(gfh_ctx* ctx, const uint32_t* d_fft_idx, const uint32_t* d_bin, int64_t n_peaks,
+              const gfh_grid* g, int32_t* d_map, gfh_candidate* d_cands, gfh_map_stats* d_stats);
+
+/*
+ * Candidate selection alone on an existing map d_map [n_k][ld_x0] (Sec. IV), same rules and
+ * outputs as the fused path of gfh_plan_execute.
+ */
+int gfh_select(gfh_ctx* ctx, const int32_t* d_map, const gfh_grid* g, gfh_candidate* d_cands,
+               gfh_map_stats* d_stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GFH_H */

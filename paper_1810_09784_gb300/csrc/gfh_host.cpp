@@ -1,0 +1,415 @@
+// Host side of libgfh: grid derivation (Sec. VI), fixed-point tables, column tables, contexts and
+// plans.  Compiled with -ffp-contract=off so that every double expression rounds exactly as
+// written (no fused multiply-add), which the bit-exact tables rely on.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <numeric>
+
+#include "gfh_internal.h"
+
+namespace {
+
+int64_t fixed_floor(double v) { return (int64_t)std::floor(std::ldexp(v, GFH_FRAC_BITS)); }
+
+int64_t floor_shift(int64_t v) { return v >> GFH_FRAC_BITS; }  // arithmetic shift = floor
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+bool grid_request_ok(const gfh_grid* g) {
+  return g && g->n > 1.0 && g->df > 0.0 && g->bin_lo >= 1 && g->bin_hi >= g->bin_lo &&
+         g->n_fft >= 1 && g->n_k >= 1 && g->t_first >= 0.0 && g->t_hop >= 0.0 &&
+         g->t_obs > 0.0 && g->k_min >= 0.0 && g->ana_hi > g->ana_lo && g->band_hz > 0.0 &&
+         std::isfinite(g->n) && std::isfinite(g->df);
+}
+
+bool grid_made(const gfh_grid* g) {
+  return grid_request_ok(g) && g->dx0 > 0.0 && g->dk > 0.0 && g->n_x0 > 0 &&
+         g->ld_x0 >= g->n_x0 && g->n_bands > 0;
+}
+
+}  // namespace
+
+extern "C" const char* gfh_strerror(int code) {
+  switch (code) {
+    case GFH_OK: return "ok";
+    case GFH_ERR_ARG: return "invalid argument";
+    case GFH_ERR_SIZE: return "size out of range or capacity too small";
+    case GFH_ERR_CUDA: return "CUDA or cuFFT call failed";
+    case GFH_ERR_INPUT: return "device-side input check failed (unsorted peaks or index out of range)";
+    case GFH_ERR_TIMEOUT: return "bounded device-side wait ran out";
+    case GFH_ERR_NOMEM: return "allocation failed";
+    default: return "unknown error";
+  }
+}
+
+// ---- Sec. VI grids ----------------------------------------------------------------------------
+
+extern "C" int gfh_grid_make(gfh_grid* g) {
+  if (!grid_request_ok(g)) return GFH_ERR_ARG;
+  const double n = g->n;
+  if (!(g->f_max > 0.0)) g->f_max = (double)g->bin_hi * g->df;
+  g->dx0 = (n - 1.0) * g->df / std::pow(g->f_max, n);               // Sec. VI.C
+  if (!(g->dk > 0.0)) g->dk = g->dx0 / ((n - 1.0) * g->t_obs);
+  const double k_max = g->k_min + (double)(g->n_k - 1) * g->dk;
+  const double t_max = g->t_first + (double)(g->n_fft - 1) * g->t_hop;
+  const double x_top = std::pow(((double)g->bin_hi + 0.5) * g->df, 1.0 - n);  // Eq. transform
+  const double x_bot = std::pow(((double)g->bin_lo - 0.5) * g->df, 1.0 - n);
+  g->x0_min = x_top - (n - 1.0) * k_max * t_max - g->dx0;
+  const double w = std::ceil((x_bot - g->x0_min) / g->dx0);
+  if (!(g->dx0 > 0.0) || !std::isfinite(w) || w < 0.0 || w > 2.0e9) return GFH_ERR_SIZE;
+  g->n_x0 = (int64_t)w + 1;
+  g->ld_x0 = (g->n_x0 + 31) / 32 * 32;
+  const double nb = std::ceil((g->ana_hi - g->ana_lo) / g->band_hz);
+  if (!(nb >= 1.0) || nb > 1.0e8) return GFH_ERR_ARG;
+  g->n_bands = (int32_t)nb;
+  return GFH_OK;
+}
+
+int gfh_host_tables(const gfh_grid* g, std::vector<int64_t>& U, std::vector<int64_t>& B,
+                    std::vector<int64_t>& S) {
+  if (!grid_made(g)) return GFH_ERR_ARG;
+  const int J = g->bin_hi - g->bin_lo + 1;
+  U.resize((size_t)J + 1);
+  for (int e = 0; e <= J; ++e) {
+    const double f = ((double)(g->bin_lo + e) - 0.5) * g->df;
+    const double x = std::pow(f, 1.0 - g->n);
+    U[e] = fixed_floor((x - g->x0_min) / g->dx0);
+  }
+  B.resize(g->n_fft);
+  S.resize(g->n_fft);
+  for (int i = 0; i < g->n_fft; ++i) {
+    const double t = g->t_first + (double)i * g->t_hop;
+    B[i] = fixed_floor((g->n - 1.0) * g->k_min * t / g->dx0);
+    S[i] = fixed_floor((g->n - 1.0) * g->dk * t / g->dx0);
+  }
+  return GFH_OK;
+}
+
+int gfh_host_columns(const gfh_grid* g, std::vector<int32_t>& band, std::vector<double>& f0,
+                     std::vector<double>& f0n) {
+  if (!grid_made(g)) return GFH_ERR_ARG;
+  const int64_t W = g->n_x0;
+  band.assign((size_t)g->ld_x0, -1);
+  f0.assign((size_t)W, 0.0);
+  f0n.assign((size_t)W, 0.0);
+  const double e = -1.0 / (g->n - 1.0);
+  for (int64_t m = 0; m < W; ++m) {
+    const double x0c = g->x0_min + ((double)m + 0.5) * g->dx0;
+    if (!(x0c > 0.0)) continue;
+    const double f = std::pow(x0c, e);
+    f0[m] = f;
+    f0n[m] = std::pow(f, g->n);
+    if (g->ana_lo <= f && f < g->ana_hi) {
+      int32_t b = (int32_t)std::floor((f - g->ana_lo) / g->band_hz);
+      if (b > g->n_bands - 1) b = g->n_bands - 1;
+      band[m] = b;
+    }
+  }
+  return GFH_OK;
+}
+
+extern "C" int gfh_grid_tables(const gfh_grid* g, int64_t* h_U, int64_t* h_B, int64_t* h_S) {
+  std::vector<int64_t> U, B, S;
+  int rc = gfh_host_tables(g, U, B, S);
+  if (rc) return rc;
+  if (h_U) std::memcpy(h_U, U.data(), U.size() * sizeof(int64_t));
+  if (h_B) std::memcpy(h_B, B.data(), B.size() * sizeof(int64_t));
+  if (h_S) std::memcpy(h_S, S.data(), S.size() * sizeof(int64_t));
+  return GFH_OK;
+}
+
+extern "C" int gfh_grid_columns(const gfh_grid* g, int32_t* h_band, double* h_f0, double* h_f0n) {
+  std::vector<int32_t> band;
+  std::vector<double> f0, f0n;
+  int rc = gfh_host_columns(g, band, f0, f0n);
+  if (rc) return rc;
+  if (h_band) std::memcpy(h_band, band.data(), (size_t)g->n_x0 * sizeof(int32_t));
+  if (h_f0) std::memcpy(h_f0, f0.data(), f0.size() * sizeof(double));
+  if (h_f0n) std::memcpy(h_f0n, f0n.data(), f0n.size() * sizeof(double));
+  return GFH_OK;
+}
+
+// ---- contexts -----------------------------------------------------------------------------------
+
+extern "C" int gfh_create(gfh_ctx** out, int device, void* stream) {
+  if (!out) return GFH_ERR_ARG;
+  *out = nullptr;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count)
+    return GFH_ERR_CUDA;
+  GFH_CUDA_TRY(cudaSetDevice(device));
+  gfh_ctx* c = new (std::nothrow) gfh_ctx();
+  if (!c) return GFH_ERR_NOMEM;
+  c->device = device;
+  c->stream = (cudaStream_t)stream;
+  if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      cudaMalloc(&c->d_flag, sizeof(unsigned int)) != cudaSuccess ||
+      cudaMemset(c->d_flag, 0, sizeof(unsigned int)) != cudaSuccess ||
+      cudaMallocHost(&c->h_pinned, 64) != cudaSuccess) {
+    gfh_destroy(c);
+    return GFH_ERR_CUDA;
+  }
+  *out = c;
+  return GFH_OK;
+}
+
+extern "C" int gfh_destroy(gfh_ctx* c) {
+  if (!c) return GFH_OK;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->fft_valid) cufftDestroy(c->fft_plan);
+  if (c->pm_buf) cudaFree(c->pm_buf);
+  if (c->d_flag) cudaFree(c->d_flag);
+  if (c->h_pinned) cudaFreeHost(c->h_pinned);
+  delete c;
+  return GFH_OK;
+}
+
+extern "C" int gfh_set_stream(gfh_ctx* c, void* stream) {
+  if (!c) return GFH_ERR_ARG;
+  c->stream = (cudaStream_t)stream;
+  if (c->fft_valid && cufftSetStream(c->fft_plan, c->stream) != CUFFT_SUCCESS) return GFH_ERR_CUDA;
+  return GFH_OK;
+}
+
+extern "C" int gfh_check(gfh_ctx* c) {
+  if (!c) return GFH_ERR_ARG;
+  GFH_CUDA_TRY(cudaSetDevice(c->device));
+  unsigned int flag = 0;
+  GFH_CUDA_TRY(cudaMemcpyAsync(&flag, c->d_flag, sizeof(flag), cudaMemcpyDeviceToHost, c->stream));
+  GFH_CUDA_TRY(cudaStreamSynchronize(c->stream));
+  if (flag) {
+    GFH_CUDA_TRY(cudaMemsetAsync(c->d_flag, 0, sizeof(unsigned int), c->stream));
+    GFH_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return GFH_ERR_INPUT;
+  }
+  return GFH_OK;
+}
+
+// ---- plans --------------------------------------------------------------------------------------
+
+namespace {
+
+struct HostMap {
+  std::vector<int64_t> U, B, S;
+  std::vector<int32_t> band;
+  std::vector<double> f0, f0n;
+  int64_t cells = 0;
+};
+
+// Bin range [ja, jb] of the peaks that can touch columns [c0, c1) on rows [r0, r1) (tile planning).
+// For bin j (local jl) and shift s in [s_min, s_max]: lo >= (U[jl+1]-s_max)>>32 and
+// hi <= (U[jl]-s_min-1)>>32; U decreases with jl, so both conditions select a contiguous range.
+void tile_bins(const gfh_grid& g, const HostMap& hm, int64_t s_min, int64_t s_max, int64_t c0,
+               int64_t c1, int32_t* ja, int32_t* jb) {
+  const int J = g.bin_hi - g.bin_lo + 1;
+  if (c0 > g.n_x0 - 1) { *ja = 1; *jb = 0; return; }
+  // smallest jl with floor((U[jl+1]-s_max)) <= c1-1
+  int lo = 0, hi = J;  // answer in [0, J]; J means none
+  while (lo < hi) {
+    int mid = (lo + hi) / 2;
+    if (floor_shift(hm.U[mid + 1] - s_max) <= c1 - 1) hi = mid; else lo = mid + 1;
+  }
+  const int a = lo;
+  // largest jl with floor((U[jl]-s_min-1)) >= c0
+  lo = -1; hi = J - 1;  // answer in [-1, J-1]
+  while (lo < hi) {
+    int mid = (lo + hi + 1) / 2;
+    if (floor_shift(hm.U[mid] - s_min - 1) >= c0) lo = mid; else hi = mid - 1;
+  }
+  const int b = lo;
+  *ja = g.bin_lo + a;
+  *jb = g.bin_lo + b;
+}
+
+}  // namespace
+
+extern "C" int gfh_plan_destroy(gfh_plan* p) {
+  if (!p) return GFH_OK;
+  if (p->ctx) {
+    cudaSetDevice(p->ctx->device);
+    if (p->ctx->stream) cudaStreamSynchronize(p->ctx->stream);
+  }
+  if (p->d_buf) cudaFree(p->d_buf);
+  delete p;
+  return GFH_OK;
+}
+
+extern "C" int gfh_plan_create(gfh_ctx* ctx, int32_t n_maps, const gfh_grid* grids,
+                               int32_t* const* h_maps, gfh_candidate* const* h_cands,
+                               gfh_map_stats* d_stats, const gfh_tile_config* cfg,
+                               gfh_plan** out) {
+  if (!ctx || !out || n_maps < 1 || !grids || !h_maps) return GFH_ERR_ARG;
+  *out = nullptr;
+  gfh_tile_config tc{16, 3072, 512, 0};
+  if (cfg) {
+    if (cfg->rows) tc.rows = cfg->rows;
+    if (cfg->cols) tc.cols = cfg->cols;
+    if (cfg->threads) tc.threads = cfg->threads;
+  }
+  if (!(tc.rows == 8 || tc.rows == 16 || tc.rows == 32) || tc.cols < 128 || tc.cols % 128 ||
+      tc.cols > 4096 || !(tc.threads == 256 || tc.threads == 512))
+    return GFH_ERR_ARG;
+  const int nwarps = tc.threads / 32;
+  if ((tc.cols / 128 + nwarps - 1) / nwarps > 4) return GFH_ERR_ARG;  // <= 4 chunks per warp
+
+  std::vector<HostMap> hms(n_maps);
+  std::vector<TileDev> tiles;
+  int max_tile_bands = 1;
+  size_t csr_entries = 0;
+  for (int m = 0; m < n_maps; ++m) {
+    const gfh_grid& g = grids[m];
+    if (!grid_made(&g) || !h_maps[m]) return GFH_ERR_ARG;
+    if ((double)g.n_k * (double)g.n_x0 >= 4294967295.0) return GFH_ERR_SIZE;
+    if (h_cands && !h_cands[m]) return GFH_ERR_ARG;
+    HostMap& hm = hms[m];
+    int rc = gfh_host_tables(&g, hm.U, hm.B, hm.S);
+    if (rc) return rc;
+    rc = gfh_host_columns(&g, hm.band, hm.f0, hm.f0n);
+    if (rc) return rc;
+    int64_t ana_cols = 0;
+    for (int64_t c = 0; c < g.n_x0; ++c) ana_cols += hm.band[c] >= 0;
+    hm.cells = ana_cols * g.n_k;
+    csr_entries += (size_t)(g.bin_hi - g.bin_lo + 2);
+    if (((uintptr_t)h_maps[m]) % 16) return GFH_ERR_ARG;  // 16-byte vector stores
+    for (int r0 = 0; r0 < g.n_k; r0 += tc.rows) {
+      const int nr = std::min(tc.rows, g.n_k - r0);
+      // B and S are non-decreasing in i (k_min >= 0, dk > 0, t_i non-decreasing), so the
+      // smallest shift of the row block is at (i = 0, r0) and the largest at (last i, last row).
+      const int64_t s_min = hm.B[0] + (int64_t)r0 * hm.S[0];
+      const int64_t s_max = hm.B[g.n_fft - 1] + (int64_t)(r0 + nr - 1) * hm.S[g.n_fft - 1];
+      for (int64_t c0 = 0; c0 < g.ld_x0; c0 += tc.cols) {
+        TileDev t{};
+        t.map = m;
+        t.row0 = r0;
+        t.nrows = nr;
+        t.col0 = c0;
+        t.ncols = (int32_t)std::min<int64_t>(tc.cols, g.ld_x0 - c0);
+        tile_bins(g, hm, s_min, s_max, c0, c0 + t.ncols, &t.bin_a, &t.bin_b);
+        t.band_lo = INT32_MAX;
+        t.band_hi = -1;
+        for (int64_t c = c0; c < c0 + t.ncols; ++c) {
+          const int32_t b = hm.band[c];
+          if (b >= 0) { t.band_lo = std::min(t.band_lo, b); t.band_hi = std::max(t.band_hi, b); }
+        }
+        if (t.band_hi < 0) t.band_lo = 0;
+        else max_tile_bands = std::max(max_tile_bands, t.band_hi - t.band_lo + 1);
+        tiles.push_back(t);
+      }
+    }
+  }
+  // Longest work first: bins x rows.
+  std::stable_sort(tiles.begin(), tiles.end(), [](const TileDev& a, const TileDev& b) {
+    const int64_t wa = (int64_t)std::max(0, a.bin_b - a.bin_a + 1) * a.nrows;
+    const int64_t wb = (int64_t)std::max(0, b.bin_b - b.bin_a + 1) * b.nrows;
+    return wa > wb;
+  });
+
+  // One device buffer: map descriptors | tiles | csr map index | keys | per-map tables.
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
+  const size_t o_maps = take(sizeof(MapDev) * n_maps);
+  const size_t o_tiles = take(sizeof(TileDev) * tiles.size());
+  const size_t o_csrmap = take(sizeof(int32_t) * csr_entries);
+  size_t key_words = 0;
+  for (int m = 0; m < n_maps; ++m) key_words += grids[m].n_bands + 2;
+  const size_t o_keys = take(sizeof(unsigned long long) * key_words);
+  std::vector<size_t> o_U(n_maps), o_B(n_maps), o_S(n_maps), o_band(n_maps), o_f0(n_maps),
+      o_f0n(n_maps), o_csr(n_maps);
+  for (int m = 0; m < n_maps; ++m) {
+    o_U[m] = take(sizeof(int64_t) * hms[m].U.size());
+    o_B[m] = take(sizeof(int64_t) * hms[m].B.size());
+    o_S[m] = take(sizeof(int64_t) * hms[m].S.size());
+    o_band[m] = take(sizeof(int32_t) * hms[m].band.size());
+    o_f0[m] = take(sizeof(double) * hms[m].f0.size());
+    o_f0n[m] = take(sizeof(double) * hms[m].f0n.size());
+    o_csr[m] = take(sizeof(int64_t) * (size_t)(grids[m].bin_hi - grids[m].bin_lo + 2));
+  }
+  const size_t o_single = take(sizeof(int64_t) * 2);
+  const size_t total = off;
+
+  gfh_plan* p = new (std::nothrow) gfh_plan();
+  if (!p) return GFH_ERR_NOMEM;
+  p->ctx = ctx;
+  p->n_maps = n_maps;
+  p->grids.assign(grids, grids + n_maps);
+  p->cfg = tc;
+  if (cudaSetDevice(ctx->device) != cudaSuccess) { delete p; return GFH_ERR_CUDA; }
+  if (cudaMalloc(&p->d_buf, total) != cudaSuccess) { delete p; return GFH_ERR_NOMEM; }
+  p->buf_bytes = total;
+  char* base = (char*)p->d_buf;
+  std::vector<char> h(total, 0);
+  std::vector<MapDev> mds(n_maps);
+  std::vector<int32_t> csr_map;
+  csr_map.reserve(csr_entries);
+  size_t key_off = 0;
+  for (int m = 0; m < n_maps; ++m) {
+    const gfh_grid& g = grids[m];
+    HostMap& hm = hms[m];
+    MapDev& md = mds[m];
+    md.out = h_maps[m];
+    md.U = (const int64_t*)(base + o_U[m]);
+    md.B = (const int64_t*)(base + o_B[m]);
+    md.S = (const int64_t*)(base + o_S[m]);
+    md.col_band = (const int32_t*)(base + o_band[m]);
+    md.f0c = (const double*)(base + o_f0[m]);
+    md.f0n = (const double*)(base + o_f0n[m]);
+    md.csr = (int64_t*)(base + o_csr[m]);
+    md.keys = (unsigned long long*)(base + o_keys) + key_off;
+    md.sums = md.keys + g.n_bands;
+    key_off += g.n_bands + 2;
+    md.cands = h_cands ? h_cands[m] : nullptr;
+    md.stats = d_stats ? d_stats + m : nullptr;
+    md.W = g.n_x0;
+    md.ld = g.ld_x0;
+    md.cells = hm.cells;
+    md.x0_min = g.x0_min;
+    md.dx0 = g.dx0;
+    md.k_min = g.k_min;
+    md.dk = g.dk;
+    md.K = g.n_k;
+    md.bin_lo = g.bin_lo;
+    md.bin_hi = g.bin_hi;
+    md.n_fft = g.n_fft;
+    md.list = g.list;
+    md.n_bands = g.n_bands;
+    md.csr_base = (int32_t)csr_map.size();
+    std::memcpy(h.data() + o_U[m], hm.U.data(), sizeof(int64_t) * hm.U.size());
+    std::memcpy(h.data() + o_B[m], hm.B.data(), sizeof(int64_t) * hm.B.size());
+    std::memcpy(h.data() + o_S[m], hm.S.data(), sizeof(int64_t) * hm.S.size());
+    std::memcpy(h.data() + o_band[m], hm.band.data(), sizeof(int32_t) * hm.band.size());
+    std::memcpy(h.data() + o_f0[m], hm.f0.data(), sizeof(double) * hm.f0.size());
+    std::memcpy(h.data() + o_f0n[m], hm.f0n.data(), sizeof(double) * hm.f0n.size());
+    for (int e = 0; e < g.bin_hi - g.bin_lo + 2; ++e) csr_map.push_back(m);
+  }
+  std::memcpy(h.data() + o_maps, mds.data(), sizeof(MapDev) * n_maps);
+  if (!tiles.empty()) std::memcpy(h.data() + o_tiles, tiles.data(), sizeof(TileDev) * tiles.size());
+  std::memcpy(h.data() + o_csrmap, csr_map.data(), sizeof(int32_t) * csr_map.size());
+  if (cudaMemcpy(p->d_buf, h.data(), total, cudaMemcpyHostToDevice) != cudaSuccess) {
+    gfh_plan_destroy(p);
+    return GFH_ERR_CUDA;
+  }
+  p->d_maps = (MapDev*)(base + o_maps);
+  p->d_tiles = (TileDev*)(base + o_tiles);
+  p->n_tiles = (int)tiles.size();
+  p->max_tile_bands = max_tile_bands;
+  p->d_keys = (unsigned long long*)(base + o_keys);
+  p->key_words = key_words;
+  p->csr_entries = (int32_t)csr_entries;
+  p->d_csr_map = (int32_t*)(base + o_csrmap);
+  p->select = h_cands != nullptr || d_stats != nullptr;
+  p->d_offsets_single = (int64_t*)(base + o_single);
+  *out = p;
+  return GFH_OK;
+}
+
+extern "C" int gfh_plan_execute(gfh_plan* p, const gfh_peaks* peaks) {
+  if (!p || !peaks || !peaks->fft_idx || !peaks->bin || !peaks->offsets || peaks->n_lists < 1)
+    return GFH_ERR_ARG;
+  for (const gfh_grid& g : p->grids)
+    if (g.list < 0 || g.list >= peaks->n_lists) return GFH_ERR_ARG;
+  return gfh_launch_plan(p, peaks);
+}

@@ -1,0 +1,105 @@
+// Internal types shared by the translation units of libgfh (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <cstdint>
+#include <cstddef>
+#include <vector>
+
+#include "gfh.h"
+
+#define GFH_FRAC_BITS 32
+
+// Device-side error flag bits (gfh_check).
+#define GFH_FLAG_UNSORTED 1u
+#define GFH_FLAG_FFT_RANGE 2u
+
+#define GFH_CUDA_TRY(expr)                                \
+  do {                                                    \
+    cudaError_t e_ = (expr);                              \
+    if (e_ != cudaSuccess) return GFH_ERR_CUDA;           \
+  } while (0)
+
+struct gfh_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int num_sms = 0;
+  unsigned int* d_flag = nullptr;  // input-check flag
+  // peakmap scratch (library-owned, grows on demand)
+  void* pm_buf = nullptr;
+  size_t pm_bytes = 0;
+  cufftHandle fft_plan = 0;
+  bool fft_valid = false;
+  int fft_n = 0, fft_hop = 0, fft_batch = 0;
+  // pinned host word for returning counts
+  long long* h_pinned = nullptr;
+};
+
+// One map as the kernels see it.
+struct MapDev {
+  int32_t* out;             // [K][ld]
+  const int64_t* U;         // J + 1 edge positions
+  const int64_t* B;         // n_fft
+  const int64_t* S;         // n_fft
+  const int32_t* col_band;  // ld entries, -1 outside the analysis band / beyond n_x0
+  const double* f0c;        // n_x0
+  const double* f0n;        // n_x0
+  int64_t* csr;             // J + 1 entries: first peak (absolute index) of bins bin_lo .. bin_hi+1
+  unsigned long long* keys; // n_bands
+  unsigned long long* sums; // 2: sum, sum of squares
+  gfh_candidate* cands;     // n_bands (may be null)
+  gfh_map_stats* stats;     // 1 (may be null)
+  int64_t W;                // n_x0
+  int64_t ld;               // ld_x0
+  int64_t cells;            // analysis cells
+  double x0_min, dx0, k_min, dk;
+  int32_t K;
+  int32_t bin_lo, bin_hi;
+  int32_t n_fft;
+  int32_t list;
+  int32_t n_bands;
+  int32_t csr_base;         // index of this map's first CSR entry in the plan-wide numbering
+};
+
+// One tile of the accumulation kernel: k rows [row0, row0+nrows) x columns [col0, col0+ncols).
+struct TileDev {
+  int32_t map;
+  int32_t row0;
+  int32_t nrows;
+  int32_t ncols;
+  int64_t col0;
+  int32_t bin_a;      // peaks with bins in [bin_a, bin_b] may touch the tile (bin_a > bin_b: none)
+  int32_t bin_b;
+  int32_t band_lo;    // candidate bands present in the tile's columns (band_hi < 0: none)
+  int32_t band_hi;
+};
+
+struct gfh_plan {
+  gfh_ctx* ctx = nullptr;
+  int n_maps = 0;
+  std::vector<gfh_grid> grids;
+  gfh_tile_config cfg{};
+  void* d_buf = nullptr;       // tables, map descriptors, tiles
+  size_t buf_bytes = 0;
+  MapDev* d_maps = nullptr;
+  TileDev* d_tiles = nullptr;
+  int n_tiles = 0;
+  int max_tile_bands = 0;
+  unsigned long long* d_keys = nullptr;  // all maps' keys and sums (zeroed per execute)
+  size_t key_words = 0;
+  int32_t csr_entries = 0;                // total CSR entries over maps
+  int32_t* d_csr_map = nullptr;           // per CSR entry: map index
+  bool select = false;
+  int64_t* d_offsets_single = nullptr;    // scratch offsets for gfh_hough
+};
+
+// Host-side planning (gfh_host.cpp).
+int gfh_host_tables(const gfh_grid* g, std::vector<int64_t>& U, std::vector<int64_t>& B,
+                    std::vector<int64_t>& S);
+int gfh_host_columns(const gfh_grid* g, std::vector<int32_t>& band, std::vector<double>& f0,
+                     std::vector<double>& f0n);
+
+// Launchers (gfh_hough.cu).
+int gfh_launch_plan(gfh_plan* plan, const gfh_peaks* peaks);
+int gfh_launch_select(gfh_ctx* ctx, const int32_t* d_map, const MapDev& md, void* d_scratch);

@@ -1,0 +1,274 @@
+// Peakmap (Sec. III) on sm_103a: interlaced short FFTs (cuFFT), equalisation by a clipped
+// auto-regressive mean along frequency, threshold + local-maximum test, and compaction of the
+// peaks into (fft_idx, bin) lists sorted by bin then FFT.
+//
+// The equaliser is one sequential recurrence per FFT.  A warp owns 32 FFTs (one per lane); tiles
+// of 32 FFTs x 32 bins are staged through shared memory with coalesced loads and every lane walks
+// its own spectrum.  Each step's peak decisions of the warp form one 32-bit ballot word, stored in
+// a bin-major bit matrix that the compaction kernels turn into sorted lists.
+#include "gfh_internal.h"
+
+namespace {
+
+constexpr float kArWeight = 0.0078125f;   // 2^-7
+constexpr float kGain = 1.08942544f;      // float32(1 / (1 - exp(-2.5)))
+constexpr float kClipGain = 2.72356367f;  // float32(2.5 / (1 - exp(-2.5)))
+constexpr int kWarm = 128;
+
+// Power of one spectrum bin from the input layout.
+struct PowerIn {
+  const float* p;
+  int64_t ld;
+  __device__ __forceinline__ float at(int64_t i, int64_t j) const { return p[i * ld + j]; }
+};
+struct ComplexIn {
+  const float2* x;
+  int64_t ld;
+  __device__ __forceinline__ float at(int64_t i, int64_t j) const {
+    const float2 v = x[i * ld + j];
+    return __fadd_rn(__fmul_rn(v.x, v.x), __fmul_rn(v.y, v.y));
+  }
+};
+
+// bits[(b - bin_lo) * n_words + w], bit l: FFT 32 w + l has a peak in bin b.
+template <class In>
+__global__ void __launch_bounds__(128) k_equalise(In in, int n_fft, int bin_lo, int bin_hi,
+                                                  float theta, uint32_t* __restrict__ bits,
+                                                  int n_words) {
+  __shared__ float tile[4][32][33];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int gw = blockIdx.x * 4 + wib;   // global warp = word index
+  if (gw >= n_words) return;            // whole warp leaves together
+  const int fft0 = gw * 32;
+  const int my_fft = fft0 + lane;
+  const int j0 = bin_lo - 1 - kWarm;    // first warm-up bin
+  const int j_end = bin_hi + 1;         // last equalised bin
+  float S = 0.f, r_m2 = 0.f, r_m1 = 0.f;
+  for (int cb = j0; cb <= j_end; cb += 32) {
+    // stage 32 FFTs x 32 bins
+#pragma unroll 4
+    for (int r = 0; r < 32; ++r) {
+      const int f = fft0 + r;
+      const int j = cb + lane;
+      tile[wib][r][lane] = (f < n_fft && j <= j_end) ? in.at(f, j) : 0.f;
+    }
+    __syncwarp();
+    const int nq = min(32, j_end - cb + 1);
+    for (int q = 0; q < nq; ++q) {
+      const int j = cb + q;
+      const float P = tile[wib][lane][q];
+      if (j < bin_lo - 1) {
+        S = __fadd_rn(S, P);
+        if (j == bin_lo - 2) S = __fmul_rn(S, 1.0f / kWarm);
+        continue;
+      }
+      const float R = __fdiv_rn(P, S);
+      const float u = fminf(__fmul_rn(P, kGain), __fmul_rn(S, kClipGain));
+      S = __fadd_rn(S, __fmul_rn(kArWeight, __fsub_rn(u, S)));
+      if (j >= bin_lo + 1) {  // decide bin j-1 with its two neighbours
+        const bool pk = my_fft < n_fft && r_m1 > theta && r_m1 > r_m2 && r_m1 > R;
+        const uint32_t word = __ballot_sync(0xffffffffu, pk);
+        if (lane == 0) bits[(int64_t)(j - 1 - bin_lo) * n_words + gw] = word;
+      }
+      r_m2 = r_m1;
+      r_m1 = R;
+    }
+    __syncwarp();
+  }
+}
+
+// counts[b] = peaks in bin b (one warp per bin).
+__global__ void k_count(const uint32_t* __restrict__ bits, int n_bins, int n_words,
+                        int64_t* __restrict__ counts) {
+  const int b = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (b >= n_bins) return;
+  int c = 0;
+  for (int w = lane; w < n_words; w += 32) c += __popc(bits[(int64_t)b * n_words + w]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if (lane == 0) counts[b] = c;
+}
+
+// Exclusive scan of counts[0..n) into counts (in place) and counts[n] = total; one block.
+__global__ void __launch_bounds__(1024) k_scan(int64_t* counts, int n) {
+  __shared__ long long part[32];
+  __shared__ long long carry;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < n; base += 1024) {
+    const int i = base + tid;
+    const long long v = i < n ? counts[i] : 0;
+    long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long u = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += u;
+    }
+    if (lane == 31) part[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      long long y = part[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const long long u = __shfl_up_sync(0xffffffffu, y, o);
+        if (lane >= o) y += u;
+      }
+      part[lane] = y;
+    }
+    __syncthreads();
+    const long long excl = carry + (warp ? part[warp - 1] : 0) + x - v;
+    if (i < n) counts[i] = excl;
+    __syncthreads();
+    if (tid == 0) carry += part[31];
+    __syncthreads();
+  }
+  if (tid == 0) counts[n] = carry;
+}
+
+// Writes the peaks of bin b at offsets[b] .. in ascending FFT order (one warp per bin).
+__global__ void k_scatter(const uint32_t* __restrict__ bits, int n_bins, int n_words, int bin_lo,
+                          const int64_t* __restrict__ offsets, uint32_t* __restrict__ out_fft,
+                          uint32_t* __restrict__ out_bin, int64_t cap) {
+  const int b = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (b >= n_bins) return;
+  int64_t pos0 = offsets[b];
+  for (int w0 = 0; w0 < n_words; w0 += 32) {
+    const int w = w0 + lane;
+    uint32_t word = w < n_words ? bits[(int64_t)b * n_words + w] : 0u;
+    const int c = __popc(word);
+    int x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += u;
+    }
+    int64_t pos = pos0 + x - c;
+    while (word) {
+      const int bit = __ffs(word) - 1;
+      word &= word - 1;
+      if (pos < cap) {
+        out_fft[pos] = (uint32_t)(w * 32 + bit);
+        out_bin[pos] = (uint32_t)(bin_lo + b);
+      }
+      ++pos;
+    }
+    pos0 += __shfl_sync(0xffffffffu, x, 31);
+  }
+}
+
+int ensure_scratch(gfh_ctx* c, size_t bytes) {
+  if (c->pm_bytes >= bytes) return GFH_OK;
+  if (c->pm_buf) {
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    cudaFree(c->pm_buf);
+    c->pm_buf = nullptr;
+    c->pm_bytes = 0;
+  }
+  if (cudaMalloc(&c->pm_buf, bytes) != cudaSuccess) return GFH_ERR_NOMEM;
+  c->pm_bytes = bytes;
+  return GFH_OK;
+}
+
+size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+// Equalise + select + compact from an input layout; `extra` bytes at the front of the scratch
+// buffer are reserved for the caller (the FFT output).
+template <class In>
+int run_peaks(gfh_ctx* c, In in, int n_fft, int bin_lo, int bin_hi, double theta, uint32_t* d_fft,
+              uint32_t* d_bin, int64_t cap, int64_t* h_n, size_t extra) {
+  const int n_bins = bin_hi - bin_lo + 1;
+  const int n_words = (n_fft + 31) / 32;
+  const size_t o_bits = align256(extra);
+  const size_t o_cnt = o_bits + align256((size_t)n_bins * n_words * 4);
+  const size_t total = o_cnt + align256(((size_t)n_bins + 1) * 8);
+  int rc = ensure_scratch(c, total);
+  if (rc) return rc;
+  char* base = (char*)c->pm_buf;
+  uint32_t* bits = (uint32_t*)(base + o_bits);
+  int64_t* cnt = (int64_t*)(base + o_cnt);
+  cudaStream_t st = c->stream;
+  k_equalise<In><<<(n_words + 3) / 4, 128, 0, st>>>(in, n_fft, bin_lo, bin_hi, (float)theta, bits,
+                                                   n_words);
+  GFH_CUDA_TRY(cudaGetLastError());
+  k_count<<<(n_bins + 7) / 8, 256, 0, st>>>(bits, n_bins, n_words, cnt);
+  GFH_CUDA_TRY(cudaGetLastError());
+  k_scan<<<1, 1024, 0, st>>>(cnt, n_bins);
+  GFH_CUDA_TRY(cudaGetLastError());
+  k_scatter<<<(n_bins + 7) / 8, 256, 0, st>>>(bits, n_bins, n_words, bin_lo, cnt, d_fft, d_bin,
+                                              cap);
+  GFH_CUDA_TRY(cudaGetLastError());
+  GFH_CUDA_TRY(cudaMemcpyAsync(c->h_pinned, cnt + n_bins, 8, cudaMemcpyDeviceToHost, st));
+  GFH_CUDA_TRY(cudaStreamSynchronize(st));
+  *h_n = (int64_t)c->h_pinned[0];
+  return *h_n > cap ? GFH_ERR_SIZE : GFH_OK;
+}
+
+bool band_ok(int n_fft, int bin_lo, int bin_hi) {
+  return n_fft >= 1 && bin_lo - 1 - kWarm >= 1 && bin_hi >= bin_lo;
+}
+
+}  // namespace
+
+extern "C" int gfh_peaks_from_power(gfh_ctx* ctx, const float* d_power, int64_t ld, int32_t n_fft,
+                                    int32_t bin_lo, int32_t bin_hi, double theta,
+                                    uint32_t* d_fft_idx, uint32_t* d_bin, int64_t cap,
+                                    int64_t* h_n_peaks) {
+  if (!ctx || !d_power || !h_n_peaks || cap < 0 || (cap > 0 && (!d_fft_idx || !d_bin)) ||
+      !band_ok(n_fft, bin_lo, bin_hi) || ld < (int64_t)bin_hi + 2)
+    return GFH_ERR_ARG;
+  GFH_CUDA_TRY(cudaSetDevice(ctx->device));
+  return run_peaks(ctx, PowerIn{d_power, ld}, n_fft, bin_lo, bin_hi, theta, d_fft_idx, d_bin, cap,
+                   h_n_peaks, 0);
+}
+
+extern "C" int gfh_peakmap(gfh_ctx* ctx, const float* d_series, int64_t n_samples, double fs,
+                           double t_fft, int32_t bin_lo, int32_t bin_hi, double theta,
+                           uint32_t* d_fft_idx, uint32_t* d_bin, int64_t cap,
+                           int64_t* h_n_peaks) {
+  if (!ctx || !d_series || !h_n_peaks || cap < 0 || (cap > 0 && (!d_fft_idx || !d_bin)) ||
+      !(fs > 0.0) || !(t_fft > 0.0))
+    return GFH_ERR_ARG;
+  const double nd = fs * t_fft;
+  if (!(nd >= 4.0) || nd > 1.0e8) return GFH_ERR_ARG;
+  const int N = (int)(nd + 0.5);
+  if (N % 2) return GFH_ERR_ARG;
+  const int hop = N / 2;
+  if (n_samples < N) return GFH_ERR_ARG;
+  const int64_t nf64 = (n_samples - N) / hop + 1;
+  if (nf64 > 0x7fffffff) return GFH_ERR_SIZE;
+  const int n_fft = (int)nf64;
+  const int nc = N / 2 + 1;
+  if (!band_ok(n_fft, bin_lo, bin_hi) || bin_hi + 1 > N / 2) return GFH_ERR_ARG;
+  GFH_CUDA_TRY(cudaSetDevice(ctx->device));
+  if (!ctx->fft_valid || ctx->fft_n != N || ctx->fft_hop != hop || ctx->fft_batch != n_fft) {
+    if (ctx->fft_valid) { cufftDestroy(ctx->fft_plan); ctx->fft_valid = false; }
+    int n[1] = {N};
+    int inembed[1] = {N};
+    int onembed[1] = {nc};
+    if (cufftPlanMany(&ctx->fft_plan, 1, n, inembed, 1, hop, onembed, 1, nc, CUFFT_R2C, n_fft) !=
+        CUFFT_SUCCESS)
+      return GFH_ERR_CUDA;
+    ctx->fft_valid = true;
+    ctx->fft_n = N;
+    ctx->fft_hop = hop;
+    ctx->fft_batch = n_fft;
+  }
+  if (cufftSetStream(ctx->fft_plan, ctx->stream) != CUFFT_SUCCESS) return GFH_ERR_CUDA;
+  // Scratch layout: [complex spectra | peak bit matrix | bin counts]; sized once, up front.
+  const size_t spec_bytes = (size_t)n_fft * nc * sizeof(float2);
+  const int n_words = (n_fft + 31) / 32;
+  const size_t need = align256(spec_bytes) +
+                      align256((size_t)(bin_hi - bin_lo + 1) * n_words * 4) +
+                      align256(((size_t)(bin_hi - bin_lo + 2)) * 8);
+  int rc = ensure_scratch(ctx, need);
+  if (rc) return rc;
+  float2* spec = (float2*)ctx->pm_buf;
+  if (cufftExecR2C(ctx->fft_plan, const_cast<float*>(d_series), (cufftComplex*)spec) !=
+      CUFFT_SUCCESS)
+    return GFH_ERR_CUDA;
+  return run_peaks(ctx, ComplexIn{spec, nc}, n_fft, bin_lo, bin_hi, theta, d_fft_idx, d_bin, cap,
+                   h_n_peaks, spec_bytes);
+}

@@ -9,8 +9,10 @@ Every array is a deterministic function of its seed (numpy PCG64).
 """
 from __future__ import annotations
 
+import concurrent.futures
 import dataclasses
 import math
+import os
 
 import numpy as np
 
@@ -62,15 +64,22 @@ def strain_series(n_samples: int, fs: float, seed: int, injections=(), sigma: fl
     Noise comes from numpy PCG64(seed); injections are added in float64 before rounding.
     """
     rng = np.random.Generator(np.random.PCG64(seed))
+    noise = [rng.standard_normal(min(n_samples, s0 + chunk) - s0) * sigma
+             for s0 in range(0, n_samples, chunk)]
     out = np.empty(n_samples, dtype=np.float32)
-    for s0 in range(0, n_samples, chunk):
-        s1 = min(n_samples, s0 + chunk)
-        x = rng.standard_normal(s1 - s0) * sigma
+
+    def fill(ci):
+        s0 = ci * chunk
+        x = noise[ci]
         if injections:
-            t = np.arange(s0, s1, dtype=np.float64) / fs
+            t = np.arange(s0, s0 + x.size, dtype=np.float64) / fs
             for inj in injections:
                 x += inj.amp * np.sin(powerlaw_phase(t, inj.f0, inj.k, inj.n) + inj.phase0)
-        out[s0:s1] = x
+        out[s0:s0 + x.size] = x
+
+    # chunks are independent (numpy ufuncs release the GIL): same result for any thread count
+    with concurrent.futures.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        list(ex.map(fill, range(len(noise))))
     return out
 
 

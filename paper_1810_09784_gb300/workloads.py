@@ -1,0 +1,128 @@
+"""The synthetic workloads, shaped like the paper's searches (sizes, seeds, bands, k grids).
+
+Numbers only: every quantity derived from them (x0 step, k step, map sizes, tables) is computed by
+the library's planner.  t0 is the start of the data and FFT i is stamped at its centre.
+
+  plain_small     fs 1024 Hz, 1800 s, T_FFT 2 s, 50% overlap (1799 FFTs), band 100-400 Hz, one
+                  n = 5 injection at f0 = 350 Hz with spectral SNR 4; Hough at n = 5 with 500 k rows.
+  plain_paper     fs 4096 Hz, 10080 s (2.8 h), T_FFT 4 s (5039 FFTs), 50-2000 Hz, 20 injections;
+                  Hough at n = 5, 2000 k rows, in 100 Hz analysis bands whose peakmap band extends
+                  50 Hz upwards (Sec. IV: the peakmap band is wider than the analysed band), top
+                  candidate per 1 Hz.
+  batched_n       the plain_small peakmap at 51 braking indices n = 2.0 .. 7.0, fewer k rows at
+                  higher n (4000 -> 1000), one map per n.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+from . import synth
+
+
+@dataclasses.dataclass
+class SeriesSpec:
+    fs: float
+    t_obs: float
+    t_fft: float
+    seed: int
+    injections: tuple = ()
+
+    @property
+    def n_samples(self) -> int:
+        return int(round(self.fs * self.t_obs))
+
+    @property
+    def n_per_fft(self) -> int:
+        return int(round(self.fs * self.t_fft))
+
+    @property
+    def n_fft(self) -> int:
+        N = self.n_per_fft
+        return (self.n_samples - N) // (N // 2) + 1
+
+    @property
+    def df(self) -> float:
+        return 1.0 / self.t_fft
+
+    @property
+    def t_first(self) -> float:
+        return self.t_fft / 2.0
+
+    @property
+    def t_hop(self) -> float:
+        return self.t_fft / 2.0
+
+    def series(self) -> np.ndarray:
+        return synth.strain_series(self.n_samples, self.fs, self.seed, self.injections)
+
+
+def grid_fields(spec: SeriesSpec, n: float, bin_lo: int, bin_hi: int, n_k: int, ana_lo: float,
+                ana_hi: float, band_hz: float = 1.0, list_idx: int = 0) -> dict:
+    """Request fields of one Hough map over the given peakmap band (k_min = 0, default steps)."""
+    return dict(n=n, df=spec.df, bin_lo=bin_lo, bin_hi=bin_hi, n_fft=spec.n_fft,
+                t_first=spec.t_first, t_hop=spec.t_hop, t_obs=spec.t_obs, n_k=n_k,
+                k_min=0.0, dk=0.0, f_max=0.0, ana_lo=ana_lo, ana_hi=ana_hi, band_hz=band_hz,
+                list=list_idx)
+
+
+# ---- plain_small ------------------------------------------------------------------------------
+
+def plain_small(seed: int = 1):
+    fs, t_obs, t_fft, n = 1024.0, 1800.0, 2.0, 5.0
+    N = int(fs * t_fft)
+    # k on row 300 of the default grid: dk = dx0 / ((n-1) T_obs), dx0 = (n-1) df / f_max^n
+    f_max = 799 * 0.5
+    dk = (n - 1.0) * 0.5 / f_max ** n / ((n - 1.0) * t_obs)
+    inj = synth.Injection(f0=350.0, k=300 * dk, n=n, amp=synth.amplitude_for_snr(4.0, 1.0, N))
+    spec = SeriesSpec(fs, t_obs, t_fft, seed, (inj,))
+    pm = dict(bin_lo=200, bin_hi=799)
+    grids = [grid_fields(spec, n, 200, 799, 500, 100.0, 400.0)]
+    return spec, pm, grids
+
+
+# ---- plain_paper ------------------------------------------------------------------------------
+
+def paper_injections(seed: int, n_inj: int = 20, snr: float = 4.0, fs: float = 4096.0,
+                     t_fft: float = 4.0):
+    rng = np.random.Generator(np.random.PCG64(seed + 1000))
+    out = []
+    N = int(fs * t_fft)
+    for _ in range(n_inj):
+        f0 = rng.uniform(500.0, 1800.0)
+        n = rng.uniform(2.5, 7.0)
+        fdot = min(10 ** rng.uniform(-4.0, -1.0), 1.0 / t_fft ** 2)   # Sec. VI.D: fdot <= 1/T_FFT^2
+        k = fdot / f0 ** n
+        out.append(synth.Injection(f0=f0, k=k, n=n, amp=synth.amplitude_for_snr(snr, 1.0, N),
+                                   phase0=rng.uniform(0, 2 * math.pi)))
+    return tuple(out)
+
+
+def plain_paper(seed: int = 2, n_k: int = 2000, n: float = 5.0):
+    fs, t_obs, t_fft = 4096.0, 10080.0, 4.0
+    spec = SeriesSpec(fs, t_obs, t_fft, seed, paper_injections(seed))
+    df = spec.df
+    f_lo, f_hi, width, ext = 50.0, 2000.0, 100.0, 50.0
+    pm = dict(bin_lo=int(round(f_lo / df)), bin_hi=int(round(f_hi / df)) - 1)
+    grids = []
+    a = f_lo
+    while a < f_hi - 1e-9:
+        b = min(a + width, f_hi)
+        top = min(b + ext, f_hi)
+        grids.append(grid_fields(spec, n, int(round(a / df)), int(round(top / df)) - 1, n_k, a, b))
+        a = b
+    return spec, pm, grids
+
+
+# ---- batched_n --------------------------------------------------------------------------------
+
+def batched_n(seed: int = 1):
+    spec, pm, _ = plain_small(seed)
+    grids = []
+    for i in range(51):
+        n = round(2.0 + 0.1 * i, 10)
+        n_k = int(round(4000 - 3000 * (n - 2.0) / 5.0))
+        grids.append(grid_fields(spec, n, pm["bin_lo"], pm["bin_hi"], n_k, 100.0, 400.0))
+    return spec, pm, grids
