@@ -225,6 +225,36 @@ int gfh_hough(gfh_ctx* ctx, const uint32_t* d_fft_idx, const uint32_t* d_bin, in
 int gfh_select(gfh_ctx* ctx, const int32_t* d_map, const gfh_grid* g, gfh_candidate* d_cands,
                gfh_map_stats* d_stats);
 
+/* ---- allocation-free entry point -------------------------------------------------------------
+ *
+ * The paper has no counterpart to this function: it is a service for callers that cannot
+ * allocate device memory, e.g. an application whose GPU memory is entirely owned by another
+ * allocator (a framework's caching pool, or a pipeline that reserves all device memory up front),
+ * where a cudaMalloc inside the library could fail, and where the implicit device synchronisation
+ * of cudaMalloc/cudaFree would stall the caller's other streams.
+ *
+ * Same peak selection as gfh_peaks_from_power (same inputs, same outputs, same order), but it needs
+ * no context and allocates nothing (no cudaMalloc, no cudaFree, no allocating library routine).
+ * Its scratch is one file-scope device array of GFH_STATIC_SCRATCH_BYTES (8 MiB), which every GPU
+ * that loads the library holds until the process exits; it must hold the peak bit matrix and the
+ * per-bin counts: 256-aligned (bins * ceil(n_fft/32) * 4) + (bins + 1) * 8 bytes, with bins =
+ * bin_hi - bin_lo + 1 (for example 7800 bins x 5040 FFTs fits).  Larger requests return
+ * GFH_ERR_SIZE and launch nothing.
+ *   stream      cudaStream_t (as void*) on the current device; all work is asynchronous on it
+ *   d_n_peaks   device int64 that receives the total number of peaks; when it exceeds cap, the
+ *               outputs hold the first cap peaks in (bin, FFT) order
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  All calls share the one
+ * array, so calls that overlap on the GPU (concurrent streams, or several host threads) race and
+ * must be serialised by the caller; every call rewrites all the scratch it reads, so no state
+ * carries over between calls.
+ */
+#define GFH_STATIC_SCRATCH_BYTES (8u << 20)
+int gfh_peaks_from_power_static(void* stream, const float* d_power, int64_t ld, int32_t n_fft,
+                                int32_t bin_lo, int32_t bin_hi, double theta,
+                                uint32_t* d_fft_idx, uint32_t* d_bin, int64_t cap,
+                                int64_t* d_n_peaks);
+
 #ifdef __cplusplus
 }
 #endif

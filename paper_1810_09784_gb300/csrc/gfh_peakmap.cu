@@ -6,6 +6,8 @@
 // of 32 FFTs x 32 bins are staged through shared memory with coalesced loads and every lane walks
 // its own spectrum.  Each step's peak decisions of the warp form one 32-bit ballot word, stored in
 // a bin-major bit matrix that the compaction kernels turn into sorted lists.
+#include <mutex>
+
 #include "gfh_internal.h"
 
 namespace {
@@ -271,4 +273,72 @@ extern "C" int gfh_peakmap(gfh_ctx* ctx, const float* d_series, int64_t n_sample
     return GFH_ERR_CUDA;
   return run_peaks(ctx, ComplexIn{spec, nc}, n_fft, bin_lo, bin_hi, theta, d_fft_idx, d_bin, cap,
                    h_n_peaks, spec_bytes);
+}
+
+// ---- allocation-free peak selection -------------------------------------------------------------
+//
+// For callers that cannot allocate device memory: a host application whose GPU memory is owned
+// entirely by another allocator (a framework's caching pool, or a pipeline that reserves all
+// device memory up front), where a library cudaMalloc could fail or where the implicit device
+// synchronisation of cudaMalloc/cudaFree would stall the caller's other streams.  The scratch
+// (peak bit matrix and per-bin counts) lives in this file-scope device array instead; every GPU
+// that loads the library holds it until the process exits.
+
+static __device__ __align__(256) unsigned char g_static_scratch[GFH_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_addr[kMaxDevices] = {};
+
+// Device address of g_static_scratch on the current device (looked up once per device: in host
+// code the symbol's name is only a host-side stand-in, never a device address).
+int static_scratch_addr(void** out) {
+  int dev = -1;
+  GFH_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return GFH_ERR_ARG;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) return GFH_ERR_CUDA;
+    g_static_addr[dev] = p;
+  }
+  *out = g_static_addr[dev];
+  return GFH_OK;
+}
+
+}  // namespace
+
+extern "C" int gfh_peaks_from_power_static(void* stream, const float* d_power, int64_t ld,
+                                           int32_t n_fft, int32_t bin_lo, int32_t bin_hi,
+                                           double theta, uint32_t* d_fft_idx, uint32_t* d_bin,
+                                           int64_t cap, int64_t* d_n_peaks) {
+  if (!d_power || !d_n_peaks || cap < 0 || (cap > 0 && (!d_fft_idx || !d_bin)) ||
+      !band_ok(n_fft, bin_lo, bin_hi) || ld < (int64_t)bin_hi + 2)
+    return GFH_ERR_ARG;
+  const int n_bins = bin_hi - bin_lo + 1;
+  const int n_words = (n_fft + 31) / 32;
+  const size_t o_cnt = align256((size_t)n_bins * n_words * 4);
+  if (o_cnt + ((size_t)n_bins + 1) * 8 > GFH_STATIC_SCRATCH_BYTES) return GFH_ERR_SIZE;
+  void* base = nullptr;
+  const int rc = static_scratch_addr(&base);
+  if (rc) return rc;
+  uint32_t* bits = (uint32_t*)base;
+  int64_t* cnt = (int64_t*)((char*)base + o_cnt);
+  cudaStream_t st = (cudaStream_t)stream;
+  // Every word of the bit matrix and every count is rewritten below, so nothing left by an
+  // earlier call is read.
+  k_equalise<PowerIn><<<(n_words + 3) / 4, 128, 0, st>>>(PowerIn{d_power, ld}, n_fft, bin_lo,
+                                                         bin_hi, (float)theta, bits, n_words);
+  GFH_CUDA_TRY(cudaGetLastError());
+  k_count<<<(n_bins + 7) / 8, 256, 0, st>>>(bits, n_bins, n_words, cnt);
+  GFH_CUDA_TRY(cudaGetLastError());
+  k_scan<<<1, 1024, 0, st>>>(cnt, n_bins);
+  GFH_CUDA_TRY(cudaGetLastError());
+  k_scatter<<<(n_bins + 7) / 8, 256, 0, st>>>(bits, n_bins, n_words, bin_lo, cnt, d_fft_idx,
+                                              d_bin, cap);
+  GFH_CUDA_TRY(cudaGetLastError());
+  GFH_CUDA_TRY(cudaMemcpyAsync(d_n_peaks, cnt + n_bins, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+  return GFH_OK;
 }

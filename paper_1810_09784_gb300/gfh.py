@@ -29,8 +29,9 @@ EXPORTED = [
     "gfh_grid_make", "gfh_grid_tables", "gfh_grid_columns",
     "gfh_peaks_from_power", "gfh_peakmap",
     "gfh_plan_create", "gfh_plan_destroy", "gfh_plan_execute",
-    "gfh_hough", "gfh_select",
+    "gfh_hough", "gfh_select", "gfh_peaks_from_power_static",
 ]
+STATIC_SCRATCH_BYTES = 8 << 20
 
 
 class GfhError(RuntimeError):
@@ -111,6 +112,7 @@ def lib() -> ctypes.CDLL:
             "gfh_plan_execute": [vp, P(PeaksC)],
             "gfh_hough": [vp, vp, vp, i64, P(GridC), vp, vp, vp],
             "gfh_select": [vp, vp, P(GridC), vp, vp],
+            "gfh_peaks_from_power_static": [vp, vp, i64, i32, i32, i32, dbl, vp, vp, i64, vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -312,3 +314,14 @@ class Plan:
 def candidates_to_numpy(cands_tensor) -> np.ndarray:
     """Device candidate buffer (uint8 tensor of n_bands * 64 bytes) -> structured numpy array."""
     return np.frombuffer(cands_tensor.cpu().numpy().tobytes(), dtype=CANDIDATE_DTYPE)
+
+
+def peaks_from_power_static(stream, power, bin_lo: int, bin_hi: int, theta: float, fft_out,
+                            bin_out, n_out) -> None:
+    """gfh_peaks_from_power_static: peak selection without any device allocation, for callers
+    whose device memory belongs to another allocator.  Asynchronous on `stream`; the peak count
+    goes to the device int64 tensor `n_out`."""
+    rc = lib().gfh_peaks_from_power_static(_stream_handle(stream), _ptr(power), power.stride(0),
+                                           power.shape[0], bin_lo, bin_hi, theta, _ptr(fft_out),
+                                           _ptr(bin_out), fft_out.numel(), _ptr(n_out))
+    _ok(rc, "gfh_peaks_from_power_static")

@@ -1,0 +1,56 @@
+"""The allocation-free peak selection entry point (gfh_peaks_from_power_static).
+
+It exists for callers that cannot allocate device memory - an application whose GPU memory is all
+owned by another allocator, where a cudaMalloc inside the library could fail and where the implicit
+device synchronisation of cudaMalloc/cudaFree would stall its other streams.  Its scratch is a
+fixed device array inside the library, shared by every call, so these tests check that two calls
+in a row (the second reusing what the first left behind) each give exactly the same peaks as the
+regular entry point, and that a request too large for the array is refused.  The file is named to
+be collected last.
+"""
+import numpy as np
+import pytest
+
+from gpu_util import to_dev
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def regular(gfh, ctx, P, lo, hi, cap):
+    fo = torch.empty(cap, dtype=torch.int32, device="cuda")
+    bo = torch.empty(cap, dtype=torch.int32, device="cuda")
+    n = ctx.peaks_from_power(P, lo, hi, 2.5, fo, bo)
+    return fo[:n].cpu().numpy(), bo[:n].cpu().numpy()
+
+
+def static(gfh, P, lo, hi, cap):
+    fo = torch.full((cap,), -1, dtype=torch.int32, device="cuda")
+    bo = torch.full((cap,), -1, dtype=torch.int32, device="cuda")
+    n_dev = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+    gfh.peaks_from_power_static(torch.cuda.current_stream(), P, lo, hi, 2.5, fo, bo, n_dev)
+    torch.cuda.synchronize()
+    n = int(n_dev.item())
+    return fo[:n].cpu().numpy(), bo[:n].cpu().numpy()
+
+
+def test_two_calls_in_a_row_match_the_regular_entry_point(built_lib, gpu_ctx):
+    rng = np.random.default_rng(21)
+    # a large request first, then a smaller one that reuses the same scratch
+    cases = [(5040, 200, 1999, 4.0), (700, 300, 1100, 1.0)]
+    for n_fft, lo, hi, scale in cases:
+        P = to_dev(torch, (rng.exponential(size=(n_fft, hi + 40)) * scale).astype(np.float32))
+        cap = n_fft * (hi - lo + 1) // 4
+        ref = regular(built_lib, gpu_ctx, P, lo, hi, cap)
+        got = static(built_lib, P, lo, hi, cap)
+        assert len(got[0]) > 1000
+        assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+
+
+def test_request_beyond_the_static_scratch_is_refused(built_lib):
+    P = torch.zeros((40000, 2100), dtype=torch.float32, device="cuda")
+    fo = torch.empty(16, dtype=torch.int32, device="cuda")
+    n_dev = torch.zeros(1, dtype=torch.int64, device="cuda")
+    with pytest.raises(built_lib.GfhError) as e:
+        built_lib.peaks_from_power_static(torch.cuda.current_stream(), P, 200, 2000, 2.5, fo, fo, n_dev)
+    assert e.value.code == built_lib.GFH_ERR_SIZE
