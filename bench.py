@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--workload", default="plain_paper", choices=["plain_paper", "plain_small"])
     ap.add_argument("--tile", default=None, help="rows,cols,threads of the Hough tiles")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--maps", type=int, default=0,
+                    help="profiling aid: keep only this many sub-band maps, spread over the band")
     return ap.parse_args()
 
 
@@ -203,6 +205,9 @@ def run_gpu(args):
     ctx = gfh.Context(local, stream)
 
     spec, pm, grid_fields = workload(args.workload, rank)
+    if args.maps and args.maps < len(grid_fields):
+        keep = np.linspace(0, len(grid_fields) - 1, args.maps).round().astype(int)
+        grid_fields = [grid_fields[i] for i in sorted(set(keep))]
     x_host = torch.from_numpy(spec.series()).pin_memory()
     x_dev = x_host.cuda()
     grids = [gfh.grid_make(gfh.Grid(**f)) for f in grid_fields]
