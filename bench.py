@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--workload", default="plain_paper", choices=["plain_paper", "plain_small"])
     ap.add_argument("--tile", default=None, help="rows,cols,threads of the Hough tiles")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--maps", type=int, default=0,
                     help="profiling aid: keep only this many sub-band maps, spread over the band")
     return ap.parse_args()
@@ -245,6 +246,13 @@ def run_gpu(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    tuned, t_tune = None, 0.0
+    if not args.no_autotune and tile is None:
+        t_tune = time.perf_counter()
+        tuned, _ = plan.autotune(fo, bo, off, 1, reps=2)
+        t_tune = time.perf_counter() - t_tune
+        step()
+        torch.cuda.synchronize()
     if ctx.check() != gfh.GFH_OK:
         raise RuntimeError("input check failed")
     # updates of this rank's step: peaks inside each map's band x its k rows
@@ -318,7 +326,9 @@ def run_gpu(args):
                    "maps": len(grids), "peaks": state["n"], "updates_per_step": updates,
                    "cells": int(sum(g.n_k * g.n_x0 for g in grids)),
                    "l2": "inputs larger than L2: 165 MB series and 0.9 GB of maps per step" if args.workload == "plain_paper" else "small workload",
-                   "tile": list(tile) if tile else "default", "plan_build_s": round(t_plan, 3)},
+                   "tile": list(tile) if tile else (list(tuned) if tuned else "default"),
+                   "tile_source": "given" if tile else ("autotuned" if tuned else "default"),
+                   "plan_build_s": round(t_plan, 3), "autotune_s": round(t_tune, 3)},
         "breakdown_ms": {"step": ms, "hough_select": ms_hough, "peakmap": ms - ms_hough},
         "roofline": {"bound": "smem_atomic", "kernel": "k_hough", "achieved": achieved,
                      "peak": SMEM_ATOMIC_PEAK, "unit": "Gatomic/s", "frac": achieved / SMEM_ATOMIC_PEAK,

@@ -128,10 +128,11 @@ typedef struct gfh_peaks {
   int32_t n_lists;
 } gfh_peaks;
 
-/* Tile shape of the Hough kernel; zero fields pick the library default (gfh_autotune finds one). */
+/* Tile shape of the Hough kernel; zero fields pick the library default (16 x 3072, 512).  The
+ * tile (rows x (cols + 2) int32 plus the candidate keys) must fit in 227 KB of shared memory. */
 typedef struct gfh_tile_config {
-  int32_t rows;     /* k rows per tile: 8, 16 or 32 */
-  int32_t cols;     /* x0 columns per tile, multiple of 128 */
+  int32_t rows;     /* k rows per tile: 4, 8, 16 or 32 */
+  int32_t cols;     /* x0 columns per tile: multiple of 128, at most 4096 */
   int32_t threads;  /* threads per block: 256 or 512 */
   int32_t reserved;
 } gfh_tile_config;
@@ -213,6 +214,16 @@ int gfh_plan_destroy(gfh_plan* plan);
  * so it can be captured in a CUDA graph.  Input errors are reported through gfh_check.
  */
 int gfh_plan_execute(gfh_plan* plan, const gfh_peaks* peaks);
+
+/*
+ * Autotuner: times gfh_plan_execute on these peaks (reps runs each, CUDA events on the context's
+ * stream) for the current tile shape and for every shape of rows {4, 8, 16} x cols {1024, 2048,
+ * 3072, 4096} x threads {256, 512} that fits in shared memory, then rebuilds the plan with the
+ * fastest.  The results are unchanged by the shape (the maps are exact).  Synchronises; writes
+ * the bound outputs.  h_best / h_best_ms (may be NULL) receive the chosen shape and its time.
+ */
+int gfh_plan_autotune(gfh_plan* plan, const gfh_peaks* peaks, int32_t reps,
+                      gfh_tile_config* h_best, float* h_best_ms);
 
 /* Convenience: one grid, one peak list of n_peaks entries; plan, execute, destroy. */
 int gfh_hough(gfh_ctx* ctx, const uint32_t* d_fft_idx, const uint32_t* d_bin, int64_t n_peaks,

@@ -250,7 +250,7 @@ extern "C" int gfh_plan_create(gfh_ctx* ctx, int32_t n_maps, const gfh_grid* gri
     if (cfg->cols) tc.cols = cfg->cols;
     if (cfg->threads) tc.threads = cfg->threads;
   }
-  if (!(tc.rows == 8 || tc.rows == 16 || tc.rows == 32) || tc.cols < 128 || tc.cols % 128 ||
+  if (!(tc.rows == 4 || tc.rows == 8 || tc.rows == 16 || tc.rows == 32) || tc.cols < 128 || tc.cols % 128 ||
       tc.cols > 4096 || !(tc.threads == 256 || tc.threads == 512))
     return GFH_ERR_ARG;
   const int nwarps = tc.threads / 32;
@@ -301,6 +301,11 @@ extern "C" int gfh_plan_create(gfh_ctx* ctx, int32_t n_maps, const gfh_grid* gri
       }
     }
   }
+  // The tile must fit in shared memory (layout of k_hough: tile, row-0 chunk sums, band keys).
+  const bool select = h_cands != nullptr || d_stats != nullptr;
+  const size_t smem = (size_t)tc.rows * (tc.cols + 2) * 4 + 32 * 4 +
+                      (select ? (size_t)max_tile_bands * 8 : 0);
+  if (smem > 227 * 1024) return GFH_ERR_SIZE;
   // Longest work first: bins x rows.
   std::stable_sort(tiles.begin(), tiles.end(), [](const TileDev& a, const TileDev& b) {
     const int64_t wa = (int64_t)std::max(0, a.bin_b - a.bin_a + 1) * a.nrows;
@@ -320,9 +325,9 @@ extern "C" int gfh_plan_create(gfh_ctx* ctx, int32_t n_maps, const gfh_grid* gri
   std::vector<size_t> o_U(n_maps), o_B(n_maps), o_S(n_maps), o_band(n_maps), o_f0(n_maps),
       o_f0n(n_maps), o_csr(n_maps);
   for (int m = 0; m < n_maps; ++m) {
-    o_U[m] = take(sizeof(int64_t) * hms[m].U.size());
-    o_B[m] = take(sizeof(int64_t) * hms[m].B.size());
-    o_S[m] = take(sizeof(int64_t) * hms[m].S.size());
+    o_U[m] = take(2 * sizeof(int64_t) * (hms[m].U.size() - 1));
+    o_B[m] = take(2 * sizeof(int64_t) * hms[m].B.size());
+    o_S[m] = 0;
     o_band[m] = take(sizeof(int32_t) * hms[m].band.size());
     o_f0[m] = take(sizeof(double) * hms[m].f0.size());
     o_f0n[m] = take(sizeof(double) * hms[m].f0n.size());
@@ -351,9 +356,8 @@ extern "C" int gfh_plan_create(gfh_ctx* ctx, int32_t n_maps, const gfh_grid* gri
     HostMap& hm = hms[m];
     MapDev& md = mds[m];
     md.out = h_maps[m];
-    md.U = (const int64_t*)(base + o_U[m]);
-    md.B = (const int64_t*)(base + o_B[m]);
-    md.S = (const int64_t*)(base + o_S[m]);
+    md.UP = (const longlong2*)(base + o_U[m]);
+    md.BS = (const longlong2*)(base + o_B[m]);
     md.col_band = (const int32_t*)(base + o_band[m]);
     md.f0c = (const double*)(base + o_f0[m]);
     md.f0n = (const double*)(base + o_f0n[m]);
@@ -377,9 +381,11 @@ extern "C" int gfh_plan_create(gfh_ctx* ctx, int32_t n_maps, const gfh_grid* gri
     md.list = g.list;
     md.n_bands = g.n_bands;
     md.csr_base = (int32_t)csr_map.size();
-    std::memcpy(h.data() + o_U[m], hm.U.data(), sizeof(int64_t) * hm.U.size());
-    std::memcpy(h.data() + o_B[m], hm.B.data(), sizeof(int64_t) * hm.B.size());
-    std::memcpy(h.data() + o_S[m], hm.S.data(), sizeof(int64_t) * hm.S.size());
+    // paired tables: one 16-byte load per bin and one per FFT in the kernel
+    int64_t* up = (int64_t*)(h.data() + o_U[m]);
+    for (size_t j = 0; j + 1 < hm.U.size(); ++j) { up[2 * j] = hm.U[j + 1]; up[2 * j + 1] = hm.U[j]; }
+    int64_t* bs = (int64_t*)(h.data() + o_B[m]);
+    for (size_t i = 0; i < hm.B.size(); ++i) { bs[2 * i] = hm.B[i]; bs[2 * i + 1] = hm.S[i]; }
     std::memcpy(h.data() + o_band[m], hm.band.data(), sizeof(int32_t) * hm.band.size());
     std::memcpy(h.data() + o_f0[m], hm.f0.data(), sizeof(double) * hm.f0.size());
     std::memcpy(h.data() + o_f0n[m], hm.f0n.data(), sizeof(double) * hm.f0n.size());
@@ -402,6 +408,9 @@ extern "C" int gfh_plan_create(gfh_ctx* ctx, int32_t n_maps, const gfh_grid* gri
   p->d_csr_map = (int32_t*)(base + o_csrmap);
   p->select = h_cands != nullptr || d_stats != nullptr;
   p->d_offsets_single = (int64_t*)(base + o_single);
+  p->h_maps.assign(h_maps, h_maps + n_maps);
+  if (h_cands) p->h_cands.assign(h_cands, h_cands + n_maps);
+  p->d_stats = d_stats;
   *out = p;
   return GFH_OK;
 }
@@ -412,4 +421,72 @@ extern "C" int gfh_plan_execute(gfh_plan* p, const gfh_peaks* peaks) {
   for (const gfh_grid& g : p->grids)
     if (g.list < 0 || g.list >= peaks->n_lists) return GFH_ERR_ARG;
   return gfh_launch_plan(p, peaks);
+}
+
+// ---- autotuner ----------------------------------------------------------------------------------
+
+namespace {
+
+// Mean time of `reps` executions of plan q on its stream (after one untimed run), in ms.
+int time_plan(gfh_plan* q, const gfh_peaks* peaks, int reps, float* ms) {
+  cudaStream_t st = q->ctx->stream;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+    if (a) cudaEventDestroy(a);
+    return GFH_ERR_CUDA;
+  }
+  int rc = gfh_plan_execute(q, peaks);
+  if (!rc && cudaEventRecord(a, st) != cudaSuccess) rc = GFH_ERR_CUDA;
+  for (int i = 0; i < reps && !rc; ++i) rc = gfh_plan_execute(q, peaks);
+  if (!rc && cudaEventRecord(b, st) != cudaSuccess) rc = GFH_ERR_CUDA;
+  if (!rc && cudaEventSynchronize(b) != cudaSuccess) rc = GFH_ERR_CUDA;
+  if (!rc && cudaEventElapsedTime(ms, a, b) != cudaSuccess) rc = GFH_ERR_CUDA;
+  if (!rc) *ms /= (float)reps;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return rc;
+}
+
+}  // namespace
+
+extern "C" int gfh_plan_autotune(gfh_plan* p, const gfh_peaks* peaks, int32_t reps,
+                                 gfh_tile_config* h_best, float* h_best_ms) {
+  if (!p || !peaks || reps < 1) return GFH_ERR_ARG;
+  static const int kRowsList[] = {4, 8, 16};
+  static const int kColsList[] = {1024, 2048, 3072, 4096};
+  static const int kThreadsList[] = {256, 512};
+  gfh_tile_config best = p->cfg;
+  float best_ms = 0.f;
+  int rc = time_plan(p, peaks, reps, &best_ms);
+  if (rc) return rc;
+  for (int r : kRowsList)
+    for (int c : kColsList)
+      for (int t : kThreadsList) {
+        gfh_tile_config cfg{r, c, t, 0};
+        if (cfg.rows == p->cfg.rows && cfg.cols == p->cfg.cols && cfg.threads == p->cfg.threads)
+          continue;
+        gfh_plan* q = nullptr;
+        const int crc = gfh_plan_create(p->ctx, p->n_maps, p->grids.data(), p->h_maps.data(),
+                                        p->h_cands.empty() ? nullptr : p->h_cands.data(),
+                                        p->d_stats, &cfg, &q);
+        if (crc == GFH_ERR_SIZE || crc == GFH_ERR_ARG) continue;   // shape does not fit
+        if (crc) return crc;
+        float ms = 0.f;
+        rc = time_plan(q, peaks, reps, &ms);
+        gfh_plan_destroy(q);
+        if (rc) return rc;
+        if (ms < best_ms) { best_ms = ms; best = cfg; }
+      }
+  if (best.rows != p->cfg.rows || best.cols != p->cfg.cols || best.threads != p->cfg.threads) {
+    gfh_plan* q = nullptr;
+    rc = gfh_plan_create(p->ctx, p->n_maps, p->grids.data(), p->h_maps.data(),
+                         p->h_cands.empty() ? nullptr : p->h_cands.data(), p->d_stats, &best, &q);
+    if (rc) return rc;
+    if (p->ctx->stream) cudaStreamSynchronize(p->ctx->stream);
+    std::swap(*p, *q);      // p takes the tuned tables; q holds the old ones and is freed
+    gfh_plan_destroy(q);
+  }
+  if (h_best) *h_best = best;
+  if (h_best_ms) *h_best_ms = best_ms;
+  return GFH_OK;
 }

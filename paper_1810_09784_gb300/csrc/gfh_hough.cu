@@ -77,96 +77,151 @@ __global__ void k_set_offsets(int64_t* off, int64_t n) {
   if (threadIdx.x == 0) { off[0] = 0; off[1] = n; }
 }
 
-// ---- the accumulation + prefix + select kernel ------------------------------------------------
+// Interval of peak p on the tile's first row: [A, B1 + 1) in 2^-32 columns, and its per-row shift
+// S.  Returns false (and flags the input) for an out-of-range FFT index or a bin outside the map
+// band, which only an unsorted peak list can put in a tile's range.
+__device__ __forceinline__ bool peak_interval(const MapDev& md, int row0, uint32_t f, int bin,
+                                              uint32_t nfft, unsigned jmax, unsigned int* flag,
+                                              int64_t& A, int64_t& B1, int64_t& S) {
+  const unsigned jl = (unsigned)(bin - md.bin_lo);
+  if (f >= nfft) { atomicOr(flag, GFH_FLAG_FFT_RANGE); return false; }
+  if (jl > jmax) { atomicOr(flag, GFH_FLAG_UNSORTED); return false; }
+  const longlong2 bs = __ldg(md.BS + f);
+  const longlong2 up = __ldg(md.UP + jl);
+  S = bs.y;
+  const int64_t base = bs.x + (int64_t)row0 * S;
+  A = up.x - base;        // interval start (upper-f edge)
+  B1 = up.y - base - 1;   // interval end - 1 (lower-f edge)
+  return true;
+}
 
-// Shared memory: D[R][C] int32 differential tile | tot[R][32] chunk sums | skey[bands] candidates.
+// ---- the accumulation + running sums + select kernel --------------------------------------------
+
+// A tile is R k rows x C columns.  Lane l draws its own peaks on all R rows.
+//
+// Shared memory holds G[R][C+2] int32, a mixed differential of the tile:
+//   row 0:     along x0 - +1 at the first column an interval covers, -1 after its last, so that
+//              M[0][m] = sum_{m' <= m} G[0][m'];
+//   row r > 0: along k - +1 at each column the interval newly covers on row r, -1 at each column it
+//              covered on row r-1 but no longer does, so that M[r][m] = M[r-1][m] + G[r][m].
+// Along k a peak's interval shifts left by S_i < 1 column per row with the default k step, so on
+// most rows it enters no column and leaves none: rows after the first cost about one event per
+// (peak, row) instead of two.  Intervals are clamped to the tile and to the map's last column;
+// an interval entering from the left of the tile on row 0 is a per-thread carry into column c0.
+//
+// Shared memory: G[R][C+2] | tot[32] row-0 chunk sums | skey[bands] candidate keys.
 template <int R, int NT, bool SELECT>
-__global__ void __launch_bounds__(NT, 1)
+__global__ void __launch_bounds__(NT, R <= 4 ? 3 : (R == 8 ? 2 : 1))
 k_hough(const MapDev* __restrict__ maps, const TileDev* __restrict__ tiles,
         const uint32_t* __restrict__ fft_idx, const uint32_t* __restrict__ bins,
         unsigned int* __restrict__ flag, int c_max) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int NW = NT / kLane;
+  constexpr int UNR = R >= 16 ? 2 : 1;  // peaks in flight per thread
   const TileDev t = tiles[blockIdx.x];
   const MapDev& md = maps[t.map];
   const int C = t.ncols;
-  int* D = reinterpret_cast<int*>(smem);
-  int* tot = D + R * c_max;
-  unsigned long long* skey = reinterpret_cast<unsigned long long*>(tot + R * kLane);
+  const int lds = C + 2;
+  int* G = reinterpret_cast<int*>(smem);
+  int* tot = G + R * (c_max + 2);
+  unsigned long long* skey = reinterpret_cast<unsigned long long*>(tot + kLane);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nb_tile = t.band_hi >= t.band_lo ? t.band_hi - t.band_lo + 1 : 0;
 
-  for (int i = tid; i < R * C / 4; i += NT) reinterpret_cast<int4*>(D)[i] = make_int4(0, 0, 0, 0);
+  for (int i = tid; i < R * lds / 2; i += NT) reinterpret_cast<int2*>(G)[i] = make_int2(0, 0);
   if (SELECT)
     for (int i = tid; i < nb_tile; i += NT) skey[i] = 0ull;
   __syncthreads();
 
-  // ---- accumulate: +1 / -1 at the first / one-past-last covered column of every (peak, row)
-  int carry[R];
-#pragma unroll
-  for (int rr = 0; rr < R; ++rr) carry[rr] = 0;
+  // ---- accumulate
   if (t.bin_a <= t.bin_b) {
     const int64_t pb = md.csr[t.bin_a - md.bin_lo];
     const int64_t pe = md.csr[t.bin_b - md.bin_lo + 1];
     const int wm1 = (int)md.W - 1;
-    const int c0 = (int)t.col0, c1 = c0 + C;
-    const int nrows = t.nrows;
-    const int64_t* __restrict__ U = md.U;
-    const int64_t* __restrict__ Bt = md.B;
-    const int64_t* __restrict__ St = md.S;
+    const int c0 = (int)t.col0;
+    const int c1m1 = c0 + C - 1;                 // last column of the tile
     const uint32_t nfft = (uint32_t)md.n_fft;
-    for (int64_t p = pb + tid; p < pe; p += NT) {
-      const uint32_t f = __ldg(fft_idx + p);
-      const int jl = (int)__ldg(bins + p) - md.bin_lo;
-      if (f >= nfft) { atomicOr(flag, GFH_FLAG_FFT_RANGE); continue; }
-      if ((unsigned)jl > (unsigned)(md.bin_hi - md.bin_lo)) {  // only if the list is unsorted
-        atomicOr(flag, GFH_FLAG_UNSORTED);
-        continue;
-      }
-      const int64_t s_i = __ldg(St + f);
-      const int64_t base = __ldg(Bt + f) + (int64_t)t.row0 * s_i;
-      int64_t a = __ldg(U + jl + 1) - base;       // interval start on row row0
-      int64_t b1 = __ldg(U + jl) - base - 1;      // interval end - 1
+    const unsigned jmax = (unsigned)(md.bin_hi - md.bin_lo);
+    int* const G0 = G - c0;                      // rows indexed by absolute column
+    int carry = 0;
+    // UNR peaks per thread per pass: their loads are all issued before any is drawn
+    for (int64_t pbase = pb + tid; pbase < pe; pbase += (int64_t)UNR * NT) {
+      uint32_t fq[UNR];
+      int jq[UNR];
 #pragma unroll
-      for (int rr = 0; rr < R; ++rr) {
-        if (rr < nrows) {
-          const int lo = max((int)(a >> GFH_FRAC_BITS), 0);
-          const int hi = min((int)(b1 >> GFH_FRAC_BITS), wm1);
-          if (lo <= hi && hi >= c0 && lo < c1) {
-            if (lo < c0) carry[rr] += 1;
-            else atomicAdd(&D[rr * C + (lo - c0)], 1);
-            if (hi + 1 < c1) atomicAdd(&D[rr * C + (hi + 1 - c0)], -1);
-          }
+      for (int u = 0; u < UNR; ++u) {
+        const int64_t p = pbase + (int64_t)u * NT;
+        fq[u] = p < pe ? __ldg(fft_idx + p) : 0xffffffffu;
+        jq[u] = p < pe ? (int)__ldg(bins + p) : md.bin_lo;
+      }
+      int64_t aq[UNR], bq[UNR], sq[UNR];
+      bool okq[UNR];
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) {
+        okq[u] = fq[u] != 0xffffffffu &&
+                 peak_interval(md, t.row0, fq[u], jq[u], nfft, jmax, flag, aq[u], bq[u], sq[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) {
+      if (!okq[u]) continue;
+      int64_t a = aq[u], b1 = bq[u];
+      const int64_t s = sq[u];
+      // row 0: first / last covered column, clamped to the map's last column and to the tile
+      int lo = (int)(a >> GFH_FRAC_BITS);
+      int hi = min((int)(b1 >> GFH_FRAC_BITS), wm1);
+      int o1 = max(lo, c0), o2 = min(hi, c1m1);
+      if (o1 <= o2) {
+        if (lo < c0) carry += 1;
+        else atomicAdd(G0 + o1, 1);
+        if (hi < c1m1) atomicAdd(G0 + hi + 1, -1);
+      }
+      // rows 1 .. R-1 (rows past the map's last k row are drawn too: they exist in shared
+      // memory and are never stored)
+#pragma unroll
+      for (int rr = 1; rr < R; ++rr) {
+        a -= s;
+        b1 -= s;
+        lo = (int)(a >> GFH_FRAC_BITS);
+        hi = min((int)(b1 >> GFH_FRAC_BITS), wm1);
+        const int n1 = max(lo, c0), n2 = min(hi, c1m1);
+        int* const Gr = G0 + rr * lds;
+        // columns entered: [n1, min(n2, o1 - 1)];  columns left: [max(o1, n2 + 1), o2]
+        const int e2 = min(n2, o1 - 1);
+        const int f1 = max(o1, n2 + 1);
+        if (n1 <= e2) {
+          atomicAdd(Gr + n1, 1);
+          for (int m = n1 + 1; m <= e2; ++m) atomicAdd(Gr + m, 1);   // only for shifts > 1 column
         }
-        a -= s_i;
-        b1 -= s_i;
+        if (f1 <= o2) {
+          atomicAdd(Gr + f1, -1);
+          for (int m = f1 + 1; m <= o2; ++m) atomicAdd(Gr + m, -1);
+        }
+        o1 = n1;
+        o2 = n2;
+      }
       }
     }
-  }
-#pragma unroll
-  for (int rr = 0; rr < R; ++rr) {
-    const int v = warp_sum(carry[rr]);
-    if (lane == 0 && v) atomicAdd(&D[rr * C], v);
+    const int v = warp_sum(carry);
+    if (lane == 0 && v) atomicAdd(G, v);
   }
   __syncthreads();
 
-  // ---- chunk sums: chunk = 128 columns (32 lanes x 4); warp w owns chunks w, w+NW, ...
+  // ---- row-0 chunk sums: chunk = 128 columns (32 lanes x 4); warp w owns chunks w, w+NW, ...
   const int nch = (C + 127) / 128;
   for (int ch = warp; ch < nch; ch += NW) {
     const int col = ch * 128 + lane * 4;
-    for (int rr = 0; rr < t.nrows; ++rr) {
-      int s = 0;
-      if (col < C) {
-        const int4 v = *reinterpret_cast<const int4*>(&D[rr * C + col]);
-        s = v.x + v.y + v.z + v.w;
-      }
-      s = warp_sum(s);
-      if (lane == 0) tot[rr * kLane + ch] = s;
+    int s = 0;
+    if (col < C) {
+      const int2 u = *reinterpret_cast<const int2*>(&G[col]);
+      const int2 w = *reinterpret_cast<const int2*>(&G[col + 2]);
+      s = u.x + u.y + w.x + w.y;
     }
+    s = warp_sum(s);
+    if (lane == 0) tot[ch] = s;
   }
   __syncthreads();
 
-  // ---- running sum along x0, store, candidates
+  // ---- row 0: running sum along x0; rows r > 0: running sum along k; store; candidates
   long long s1 = 0, s2 = 0;
   const uint32_t W32 = (uint32_t)md.W;
   for (int ch = warp; ch < nch; ch += NW) {
@@ -178,15 +233,23 @@ k_hough(const MapDev* __restrict__ maps, const TileDev* __restrict__ tiles,
       const int4 bv = __ldg(reinterpret_cast<const int4*>(md.col_band + t.col0 + col));
       band[0] = bv.x; band[1] = bv.y; band[2] = bv.z; band[3] = bv.w;
     }
+    const int cin = warp_sum((lane < ch) ? tot[lane] : 0);
+    int4 v = make_int4(0, 0, 0, 0);
     for (int rr = 0; rr < t.nrows; ++rr) {
-      int cin = (lane < ch) ? tot[rr * kLane + lane] : 0;
-      cin = warp_sum(cin);
-      int4 v = make_int4(0, 0, 0, 0);
-      if (in) v = *reinterpret_cast<const int4*>(&D[rr * C + col]);
-      v.y += v.x; v.z += v.y; v.w += v.z;
-      const int incl = warp_incl_scan(v.w, lane);
-      const int add = cin + incl - v.w;
-      v.x += add; v.y += add; v.z += add; v.w += add;
+      int4 g = make_int4(0, 0, 0, 0);
+      if (in) {
+        const int2 u = *reinterpret_cast<const int2*>(&G[rr * lds + col]);
+        const int2 w = *reinterpret_cast<const int2*>(&G[rr * lds + col + 2]);
+        g = make_int4(u.x, u.y, w.x, w.y);
+      }
+      if (rr == 0) {
+        g.y += g.x; g.z += g.y; g.w += g.z;
+        const int incl = warp_incl_scan(g.w, lane);
+        const int add = cin + incl - g.w;
+        v = make_int4(g.x + add, g.y + add, g.z + add, g.w + add);
+      } else {
+        v.x += g.x; v.y += g.y; v.z += g.z; v.w += g.w;
+      }
       if (in) {
         const int64_t row = t.row0 + rr;
         __stcs(reinterpret_cast<int4*>(md.out + row * md.ld + t.col0 + col), v);
@@ -313,21 +376,21 @@ int launch_hough_t(gfh_plan* p, const gfh_peaks* peaks, size_t smem) {
 }
 
 template <int R, int NT>
-int launch_hough_r(gfh_plan* p, const gfh_peaks* peaks, size_t smem) {
+int launch_hough_sel(gfh_plan* p, const gfh_peaks* peaks, size_t smem) {
   return p->select ? launch_hough_t<R, NT, true>(p, peaks, smem)
                    : launch_hough_t<R, NT, false>(p, peaks, smem);
 }
 
 template <int R>
-int launch_hough_nt(gfh_plan* p, const gfh_peaks* peaks, size_t smem) {
-  return p->cfg.threads == 256 ? launch_hough_r<R, 256>(p, peaks, smem)
-                               : launch_hough_r<R, 512>(p, peaks, smem);
+int launch_hough_r(gfh_plan* p, const gfh_peaks* peaks, size_t smem) {
+  return p->cfg.threads == 256 ? launch_hough_sel<R, 256>(p, peaks, smem)
+                               : launch_hough_sel<R, 512>(p, peaks, smem);
 }
 
 }  // namespace
 
 size_t gfh_hough_smem_bytes(const gfh_plan* p) {
-  return (size_t)p->cfg.rows * p->cfg.cols * 4 + (size_t)p->cfg.rows * kLane * 4 +
+  return (size_t)p->cfg.rows * (p->cfg.cols + 2) * 4 + (size_t)kLane * 4 +
          (p->select ? (size_t)p->max_tile_bands * 8 : 0);
 }
 
@@ -348,9 +411,10 @@ int gfh_launch_plan(gfh_plan* p, const gfh_peaks* peaks) {
   if (p->select)
     GFH_CUDA_TRY(cudaMemsetAsync(p->d_keys, 0, p->key_words * sizeof(unsigned long long), st));
   if (p->n_tiles > 0) {
-    int rc = p->cfg.rows == 8    ? launch_hough_nt<8>(p, peaks, smem)
-             : p->cfg.rows == 16 ? launch_hough_nt<16>(p, peaks, smem)
-                                 : launch_hough_nt<32>(p, peaks, smem);
+    int rc = p->cfg.rows == 4    ? launch_hough_r<4>(p, peaks, smem)
+             : p->cfg.rows == 8  ? launch_hough_r<8>(p, peaks, smem)
+             : p->cfg.rows == 16 ? launch_hough_r<16>(p, peaks, smem)
+                                 : launch_hough_r<32>(p, peaks, smem);
     if (rc) return rc;
   }
   if (p->select) {

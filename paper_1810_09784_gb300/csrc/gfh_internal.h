@@ -39,9 +39,8 @@ struct gfh_ctx {
 // One map as the kernels see it.
 struct MapDev {
   int32_t* out;             // [K][ld]
-  const int64_t* U;         // J + 1 edge positions
-  const int64_t* B;         // n_fft
-  const int64_t* S;         // n_fft
+  const longlong2* UP;      // J: {U[j+1], U[j]} edge positions of bin j (upper f, lower f)
+  const longlong2* BS;      // n_fft: {B_i, S_i}
   const int32_t* col_band;  // ld entries, -1 outside the analysis band / beyond n_x0
   const double* f0c;        // n_x0
   const double* f0n;        // n_x0
@@ -92,6 +91,10 @@ struct gfh_plan {
   int32_t* d_csr_map = nullptr;           // per CSR entry: map index
   bool select = false;
   int64_t* d_offsets_single = nullptr;    // scratch offsets for gfh_hough
+  // the bound outputs, kept so that the autotuner can rebuild the plan with another tile shape
+  std::vector<int32_t*> h_maps;
+  std::vector<gfh_candidate*> h_cands;
+  gfh_map_stats* d_stats = nullptr;
 };
 
 // Host-side planning (gfh_host.cpp).

@@ -46,15 +46,23 @@ __global__ void __launch_bounds__(128) k_equalise(In in, int n_fft, int bin_lo, 
   const int j0 = bin_lo - 1 - kWarm;    // first warm-up bin
   const int j_end = bin_hi + 1;         // last equalised bin
   float S = 0.f, r_m2 = 0.f, r_m1 = 0.f;
+  // The next chunk (32 FFTs x 32 bins) is loaded into registers while the current one is
+  // processed from shared memory, so the load latency hides behind the recurrence.
+  float nxt[32];
+#pragma unroll
+  for (int r = 0; r < 32; ++r) {
+    const int f = fft0 + r, j = j0 + lane;
+    nxt[r] = (f < n_fft && j <= j_end) ? in.at(f, j) : 0.f;
+  }
   for (int cb = j0; cb <= j_end; cb += 32) {
-    // stage 32 FFTs x 32 bins
-#pragma unroll 4
-    for (int r = 0; r < 32; ++r) {
-      const int f = fft0 + r;
-      const int j = cb + lane;
-      tile[wib][r][lane] = (f < n_fft && j <= j_end) ? in.at(f, j) : 0.f;
-    }
+#pragma unroll
+    for (int r = 0; r < 32; ++r) tile[wib][r][lane] = nxt[r];
     __syncwarp();
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+      const int f = fft0 + r, j = cb + 32 + lane;
+      nxt[r] = (f < n_fft && j <= j_end) ? in.at(f, j) : 0.f;
+    }
     const int nq = min(32, j_end - cb + 1);
     for (int q = 0; q < nq; ++q) {
       const int j = cb + q;

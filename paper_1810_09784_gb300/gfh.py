@@ -28,7 +28,7 @@ EXPORTED = [
     "gfh_create", "gfh_destroy", "gfh_set_stream", "gfh_check", "gfh_strerror",
     "gfh_grid_make", "gfh_grid_tables", "gfh_grid_columns",
     "gfh_peaks_from_power", "gfh_peakmap",
-    "gfh_plan_create", "gfh_plan_destroy", "gfh_plan_execute",
+    "gfh_plan_create", "gfh_plan_destroy", "gfh_plan_execute", "gfh_plan_autotune",
     "gfh_hough", "gfh_select", "gfh_peaks_from_power_static",
 ]
 STATIC_SCRATCH_BYTES = 8 << 20
@@ -110,6 +110,7 @@ def lib() -> ctypes.CDLL:
             "gfh_plan_create": [vp, i32, P(GridC), P(vp), P(vp), vp, P(TileConfigC), P(vp)],
             "gfh_plan_destroy": [vp],
             "gfh_plan_execute": [vp, P(PeaksC)],
+            "gfh_plan_autotune": [vp, P(PeaksC), i32, P(TileConfigC), P(ctypes.c_float)],
             "gfh_hough": [vp, vp, vp, i64, P(GridC), vp, vp, vp],
             "gfh_select": [vp, vp, P(GridC), vp, vp],
             "gfh_peaks_from_power_static": [vp, vp, i64, i32, i32, i32, dbl, vp, vp, i64, vp],
@@ -287,7 +288,7 @@ class Plan:
         self._grids_c = (GridC * n)(*[g.to_c() for g in grids])
         self._maps = (ctypes.c_void_p * n)(*[_ptr(m) for m in maps])
         self._cands = (ctypes.c_void_p * n)(*[_ptr(c) for c in cands]) if cands is not None else None
-        self._tile = TileConfigC(*tile, 0) if tile is not None else None
+        self._tile = TileConfigC(*(tuple(tile) + (0,) * (4 - len(tile)))) if tile is not None else None
         self._h = ctypes.c_void_p()
         self.ctx = ctx
         rc = lib().gfh_plan_create(ctx.handle, n, self._grids_c, self._maps, self._cands,
@@ -298,6 +299,15 @@ class Plan:
     def execute(self, fft_idx, bins, offsets, n_lists: int) -> None:
         pk = PeaksC(_ptr(fft_idx), _ptr(bins), _ptr(offsets), n_lists)
         _ok(lib().gfh_plan_execute(self._h, ctypes.byref(pk)), "gfh_plan_execute")
+
+    def autotune(self, fft_idx, bins, offsets, n_lists: int, reps: int = 3):
+        """gfh_plan_autotune: returns ((rows, cols, threads), ms per execute) of the chosen shape."""
+        pk = PeaksC(_ptr(fft_idx), _ptr(bins), _ptr(offsets), n_lists)
+        best = TileConfigC()
+        ms = ctypes.c_float()
+        _ok(lib().gfh_plan_autotune(self._h, ctypes.byref(pk), reps, ctypes.byref(best),
+                                    ctypes.byref(ms)), "gfh_plan_autotune")
+        return (best.rows, best.cols, best.threads), ms.value
 
     def close(self) -> None:
         if self._h:

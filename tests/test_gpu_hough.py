@@ -50,8 +50,8 @@ def medium_case(seed, n=5.0, n_k=37, n_fft=60, nb=300, bin_lo=200, density=0.08,
     return fields, fi, bj
 
 
-TILES = [(8, 128, 256), (16, 1024, 512), (32, 512, 256), (16, 3072, 512), (32, 1536, 512),
-         (8, 4096, 256)]
+TILES = [(8, 128, 256), (16, 1024, 512), (16, 3072, 512), (32, 640, 256), (8, 4096, 512),
+         (32, 1536, 256), (16, 384, 512)]
 
 
 @pytest.mark.parametrize("tile", TILES, ids=str)
@@ -73,6 +73,24 @@ def test_plain_small_full_map(built_lib, gpu_ctx):
     # the injection (row 300, f0 = 350 Hz) is the loudest candidate
     best = c[np.argmax(c["count"])]
     assert int(best["row"]) == pytest.approx(300, abs=2) and abs(best["f0"] - 350.0) < 1.0
+
+
+def test_autotuned_plan_gives_the_same_map(built_lib, gpu_ctx):
+    """The autotuner only changes the tile shape: the map and candidates stay bit-exact."""
+    fields, fi, bj = medium_case(5, n_k=45, nb=400)
+    g = built_lib.grid_make(built_lib.Grid(**fields))
+    hmap, cands, stats = alloc_outputs(torch, g)
+    dfi, dbj = to_dev(torch, fi), to_dev(torch, bj)
+    off = to_dev(torch, np.array([0, len(fi)], np.int64))
+    plan = built_lib.Plan(gpu_ctx, [g], [hmap], [cands], stats)
+    best, ms = plan.autotune(dfi, dbj, off, 1, reps=1)
+    assert best[0] in (4, 8, 16, 32) and ms > 0
+    hmap.fill_(-7)
+    plan.execute(dfi, dbj, off, 1)
+    torch.cuda.synchronize()
+    plan.close()
+    check_against_oracle(g, hmap.cpu().numpy(), read_cands(built_lib, cands),
+                         read_stats(built_lib, stats), fields, fi, bj)
 
 
 def test_edge_cases(built_lib, gpu_ctx):
