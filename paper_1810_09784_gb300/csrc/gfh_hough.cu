@@ -95,6 +95,56 @@ __device__ __forceinline__ bool peak_interval(const MapDev& md, int row0, uint32
   return true;
 }
 
+// Events of one peak on the R rows of a tile (layout described at k_hough below).  The interval
+// on row 0 is [a, b1 + 1) in 2^-32 columns and moves left by s per row.
+template <int R>
+__device__ __forceinline__ void draw_peak(int* G0, int lds, int64_t a, int64_t b1, int64_t s,
+                                          int c0, int c1m1, int wm1, int& carry) {
+  // row 0: first / last covered column, clamped to the map's last column and to the tile
+  int lo = (int)(a >> GFH_FRAC_BITS);
+  int hi = min((int)(b1 >> GFH_FRAC_BITS), wm1);
+  int o1 = max(lo, c0), o2 = min(hi, c1m1);
+  if (o1 <= o2) {
+    if (lo < c0) carry += 1;
+    else atomicAdd(G0 + o1, 1);
+    if (hi < c1m1) atomicAdd(G0 + hi + 1, -1);
+  }
+  // rows 1 .. R-1 (rows past the map's last k row are drawn too: they exist in shared memory
+  // and are never stored).  Columns entered: [n1, min(n2, o1 - 1)]; columns left:
+  // [max(o1, n2 + 1), o2].  A shift below one column per row enters and leaves at most one
+  // column per row: that common case is branch-free.
+  if (s < (int64_t(1) << GFH_FRAC_BITS)) {
+#pragma unroll
+    for (int rr = 1; rr < R; ++rr) {
+      a -= s;
+      b1 -= s;
+      lo = (int)(a >> GFH_FRAC_BITS);
+      hi = min((int)(b1 >> GFH_FRAC_BITS), wm1);
+      const int n1 = max(lo, c0), n2 = min(hi, c1m1);
+      int* const Gr = G0 + rr * lds;
+      const int f1 = max(o1, n2 + 1);
+      if ((n1 < o1) & (n1 <= n2)) atomicAdd(Gr + n1, 1);
+      if (f1 <= o2) atomicAdd(Gr + f1, -1);
+      o1 = n1;
+      o2 = n2;
+    }
+  } else {
+    for (int rr = 1; rr < R; ++rr) {
+      a -= s;
+      b1 -= s;
+      lo = (int)(a >> GFH_FRAC_BITS);
+      hi = min((int)(b1 >> GFH_FRAC_BITS), wm1);
+      const int n1 = max(lo, c0), n2 = min(hi, c1m1);
+      int* const Gr = G0 + rr * lds;
+      const int e2 = min(n2, o1 - 1);
+      for (int m = n1; m <= e2; ++m) atomicAdd(Gr + m, 1);
+      for (int m = max(o1, n2 + 1); m <= o2; ++m) atomicAdd(Gr + m, -1);
+      o1 = n1;
+      o2 = n2;
+    }
+  }
+}
+
 // ---- the accumulation + running sums + select kernel --------------------------------------------
 
 // A tile is R k rows x C columns.  Lane l draws its own peaks on all R rows.
@@ -117,7 +167,6 @@ k_hough(const MapDev* __restrict__ maps, const TileDev* __restrict__ tiles,
         unsigned int* __restrict__ flag, int c_max) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int NW = NT / kLane;
-  constexpr int UNR = R >= 16 ? 2 : 1;  // peaks in flight per thread
   const TileDev t = tiles[blockIdx.x];
   const MapDev& md = maps[t.map];
   const int C = t.ncols;
@@ -144,62 +193,28 @@ k_hough(const MapDev* __restrict__ maps, const TileDev* __restrict__ tiles,
     const unsigned jmax = (unsigned)(md.bin_hi - md.bin_lo);
     int* const G0 = G - c0;                      // rows indexed by absolute column
     int carry = 0;
-    // UNR peaks per thread per pass: their loads are all issued before any is drawn
-    for (int64_t pbase = pb + tid; pbase < pe; pbase += (int64_t)UNR * NT) {
-      uint32_t fq[UNR];
-      int jq[UNR];
-#pragma unroll
-      for (int u = 0; u < UNR; ++u) {
-        const int64_t p = pbase + (int64_t)u * NT;
-        fq[u] = p < pe ? __ldg(fft_idx + p) : 0xffffffffu;
-        jq[u] = p < pe ? (int)__ldg(bins + p) : md.bin_lo;
-      }
-      int64_t aq[UNR], bq[UNR], sq[UNR];
-      bool okq[UNR];
-#pragma unroll
-      for (int u = 0; u < UNR; ++u) {
-        okq[u] = fq[u] != 0xffffffffu &&
-                 peak_interval(md, t.row0, fq[u], jq[u], nfft, jmax, flag, aq[u], bq[u], sq[u]);
-      }
-#pragma unroll
-      for (int u = 0; u < UNR; ++u) {
-      if (!okq[u]) continue;
-      int64_t a = aq[u], b1 = bq[u];
-      const int64_t s = sq[u];
-      // row 0: first / last covered column, clamped to the map's last column and to the tile
-      int lo = (int)(a >> GFH_FRAC_BITS);
-      int hi = min((int)(b1 >> GFH_FRAC_BITS), wm1);
-      int o1 = max(lo, c0), o2 = min(hi, c1m1);
-      if (o1 <= o2) {
-        if (lo < c0) carry += 1;
-        else atomicAdd(G0 + o1, 1);
-        if (hi < c1m1) atomicAdd(G0 + hi + 1, -1);
-      }
-      // rows 1 .. R-1 (rows past the map's last k row are drawn too: they exist in shared
-      // memory and are never stored)
-#pragma unroll
-      for (int rr = 1; rr < R; ++rr) {
-        a -= s;
-        b1 -= s;
-        lo = (int)(a >> GFH_FRAC_BITS);
-        hi = min((int)(b1 >> GFH_FRAC_BITS), wm1);
-        const int n1 = max(lo, c0), n2 = min(hi, c1m1);
-        int* const Gr = G0 + rr * lds;
-        // columns entered: [n1, min(n2, o1 - 1)];  columns left: [max(o1, n2 + 1), o2]
-        const int e2 = min(n2, o1 - 1);
-        const int f1 = max(o1, n2 + 1);
-        if (n1 <= e2) {
-          atomicAdd(Gr + n1, 1);
-          for (int m = n1 + 1; m <= e2; ++m) atomicAdd(Gr + m, 1);   // only for shifts > 1 column
-        }
-        if (f1 <= o2) {
-          atomicAdd(Gr + f1, -1);
-          for (int m = f1 + 1; m <= o2; ++m) atomicAdd(Gr + m, -1);
-        }
-        o1 = n1;
-        o2 = n2;
-      }
-      }
+    // Software pipeline over this thread's peaks p, p + NT, ...: the indices are loaded two
+    // peaks ahead and the table rows one peak ahead of the peak being drawn.
+    int64_t p = pb + tid;
+    uint32_t f_nx = 0xffffffffu;                 // indices of peak p + NT
+    int j_nx = 0;
+    int64_t a_cu = 0, b_cu = 0, s_cu = 0;        // interval of peak p
+    bool ok_cu = false;
+    if (p < pe) {
+      ok_cu = peak_interval(md, t.row0, __ldg(fft_idx + p), (int)__ldg(bins + p), nfft, jmax,
+                            flag, a_cu, b_cu, s_cu);
+    }
+    if (p + NT < pe) { f_nx = __ldg(fft_idx + p + NT); j_nx = (int)__ldg(bins + p + NT); }
+    for (; p < pe; p += NT) {
+      uint32_t f_nn = 0xffffffffu;               // indices of peak p + 2 NT
+      int j_nn = 0;
+      if (p + 2 * NT < pe) { f_nn = __ldg(fft_idx + p + 2 * NT); j_nn = (int)__ldg(bins + p + 2 * NT); }
+      int64_t a_nx = 0, b_nx = 0, s_nx = 0;
+      const bool ok_nx = f_nx != 0xffffffffu &&
+                         peak_interval(md, t.row0, f_nx, j_nx, nfft, jmax, flag, a_nx, b_nx, s_nx);
+      if (ok_cu) draw_peak<R>(G0, lds, a_cu, b_cu, s_cu, c0, c1m1, wm1, carry);
+      a_cu = a_nx; b_cu = b_nx; s_cu = s_nx; ok_cu = ok_nx;
+      f_nx = f_nn; j_nx = j_nn;
     }
     const int v = warp_sum(carry);
     if (lane == 0 && v) atomicAdd(G, v);

@@ -33,57 +33,107 @@ struct ComplexIn {
 };
 
 // bits[(b - bin_lo) * n_words + w], bit l: FFT 32 w + l has a peak in bin b.
+//
+// One block of kEqWarps warps per 32 FFTs (lane l = FFT 32 w + l), over chunks of 32 bins:
+//   warp 0      runs only the recurrence of chunk c (the mean each bin is divided by, then the
+//               update: four dependent operations per bin, the one serial part) and leaves the
+//               means in shared memory;
+//   warps 1..H  load chunk c+1, divide chunk c-1 (helper h takes bins h-1, h-1+H, ...), meet at a
+//               named barrier, then take the peak decisions of chunk c-1 one bin late (bin b needs
+//               R at b+1), one ballot word per bin.
+// Rings: three power tiles, two mean tiles, two equalised tiles; one block barrier per chunk.
+constexpr int kEqWarps = 8;
+constexpr int kEqHelpers = kEqWarps - 1;
+
 template <class In>
-__global__ void __launch_bounds__(128) k_equalise(In in, int n_fft, int bin_lo, int bin_hi,
-                                                  float theta, uint32_t* __restrict__ bits,
-                                                  int n_words) {
-  __shared__ float tile[4][32][33];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int gw = blockIdx.x * 4 + wib;   // global warp = word index
-  if (gw >= n_words) return;            // whole warp leaves together
+__global__ void __launch_bounds__(32 * kEqWarps) k_equalise(In in, int n_fft, int bin_lo,
+                                                            int bin_hi, float theta,
+                                                            uint32_t* __restrict__ bits,
+                                                            int n_words) {
+  __shared__ float Pt[3][32][33];   // [chunk ring][fft][bin]
+  __shared__ float Sm[2][32][33];   // [chunk ring][fft][bin]: mean each bin is divided by
+  __shared__ float Rt[2][32][32];   // [chunk ring][bin][fft]: equalised values
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int gw = blockIdx.x;        // word index: FFTs 32 gw .. 32 gw + 31
   const int fft0 = gw * 32;
   const int my_fft = fft0 + lane;
   const int j0 = bin_lo - 1 - kWarm;    // first warm-up bin
   const int j_end = bin_hi + 1;         // last equalised bin
-  float S = 0.f, r_m2 = 0.f, r_m1 = 0.f;
-  // The next chunk (32 FFTs x 32 bins) is loaded into registers while the current one is
-  // processed from shared memory, so the load latency hides behind the recurrence.
-  float nxt[32];
-#pragma unroll
-  for (int r = 0; r < 32; ++r) {
+  const int n_chunks = (j_end - j0 + 32) / 32;
+  for (int r = warp; r < 32; r += kEqWarps) {             // chunk 0
     const int f = fft0 + r, j = j0 + lane;
-    nxt[r] = (f < n_fft && j <= j_end) ? in.at(f, j) : 0.f;
+    Pt[0][r][lane] = (f < n_fft && j <= j_end) ? in.at(f, j) : 0.f;
   }
-  for (int cb = j0; cb <= j_end; cb += 32) {
+  __syncthreads();
+  float S = 0.f;                        // warp 0: running mean of FFT my_fft
+  for (int c = 0; c <= n_chunks; ++c) {
+    if (warp == 0) {
+      if (c < n_chunks) {
+        const int cb = j0 + 32 * c;
+        const int nq = min(32, j_end - cb + 1);
+        const float* row = Pt[c % 3][lane];
+        float* srow = Sm[c & 1][lane];
 #pragma unroll
-    for (int r = 0; r < 32; ++r) tile[wib][r][lane] = nxt[r];
-    __syncwarp();
+        for (int q = 0; q < 32; ++q) {
+          if (q < nq) {
+            const int j = cb + q;
+            const float P = row[q];
+            srow[q] = S;
+            if (j < bin_lo - 1) {
+              S = __fadd_rn(S, P);
+              if (j == bin_lo - 2) S = __fmul_rn(S, 1.0f / kWarm);
+            } else {
+              const float u = fminf(__fmul_rn(P, kGain), __fmul_rn(S, kClipGain));
+              S = __fadd_rn(S, __fmul_rn(kArWeight, __fsub_rn(u, S)));
+            }
+          }
+        }
+      }
+    } else {
+      const int h = warp - 1;
+      // loads of chunk c+1 (rows h, h+H, ...) go out first
+      constexpr int kRowsPerHelper = (32 + kEqHelpers - 1) / kEqHelpers;
+      float nxt[kRowsPerHelper];
+      const bool load = c + 1 < n_chunks;
+      if (load) {
 #pragma unroll
-    for (int r = 0; r < 32; ++r) {
-      const int f = fft0 + r, j = cb + 32 + lane;
-      nxt[r] = (f < n_fft && j <= j_end) ? in.at(f, j) : 0.f;
-    }
-    const int nq = min(32, j_end - cb + 1);
-    for (int q = 0; q < nq; ++q) {
-      const int j = cb + q;
-      const float P = tile[wib][lane][q];
-      if (j < bin_lo - 1) {
-        S = __fadd_rn(S, P);
-        if (j == bin_lo - 2) S = __fmul_rn(S, 1.0f / kWarm);
-        continue;
+        for (int i = 0; i < kRowsPerHelper; ++i) {
+          const int r = h + i * kEqHelpers;
+          const int f = fft0 + r, j = j0 + 32 * (c + 1) + lane;
+          nxt[i] = (r < 32 && f < n_fft && j <= j_end) ? in.at(f, j) : 0.f;
+        }
       }
-      const float R = __fdiv_rn(P, S);
-      const float u = fminf(__fmul_rn(P, kGain), __fmul_rn(S, kClipGain));
-      S = __fadd_rn(S, __fmul_rn(kArWeight, __fsub_rn(u, S)));
-      if (j >= bin_lo + 1) {  // decide bin j-1 with its two neighbours
-        const bool pk = my_fft < n_fft && r_m1 > theta && r_m1 > r_m2 && r_m1 > R;
-        const uint32_t word = __ballot_sync(0xffffffffu, pk);
-        if (lane == 0) bits[(int64_t)(j - 1 - bin_lo) * n_words + gw] = word;
+      if (c >= 1) {
+        const int cp = c - 1;
+        const int cb = j0 + 32 * cp;
+        const int nq = min(32, j_end - cb + 1);
+        // equalised values of this helper's bins: R_j = P_j / S_(j-1)
+        for (int q = h; q < nq; q += kEqHelpers)
+          if (cb + q >= bin_lo - 1)
+            Rt[cp & 1][q][lane] = __fdiv_rn(Pt[cp % 3][lane][q], Sm[cp & 1][lane][q]);
+        asm volatile("bar.sync 1, %0;" ::"n"(32 * kEqHelpers));
+        // decisions for bins b = cb + q - 1: neighbours b-1, b, b+1 (the first two may sit in
+        // the previous chunk's tile)
+        for (int q = h; q < nq; q += kEqHelpers) {
+          const int b = cb + q - 1;
+          if (b < bin_lo || b > bin_hi) continue;
+          const float rl = q >= 2 ? Rt[cp & 1][q - 2][lane] : Rt[(cp + 1) & 1][q + 30][lane];
+          const float rc = q >= 1 ? Rt[cp & 1][q - 1][lane] : Rt[(cp + 1) & 1][31][lane];
+          const float rr = Rt[cp & 1][q][lane];
+          const bool pk = my_fft < n_fft && rc > theta && rc > rl && rc > rr;
+          const uint32_t word = __ballot_sync(0xffffffffu, pk);
+          if (lane == 0) bits[(int64_t)(b - bin_lo) * n_words + gw] = word;
+        }
       }
-      r_m2 = r_m1;
-      r_m1 = R;
+      if (load) {
+#pragma unroll
+        for (int i = 0; i < kRowsPerHelper; ++i) {
+          const int r = h + i * kEqHelpers;
+          if (r < 32) Pt[(c + 1) % 3][r][lane] = nxt[i];
+        }
+      }
     }
-    __syncwarp();
+    __syncthreads();
   }
 }
 
@@ -200,7 +250,8 @@ int run_peaks(gfh_ctx* c, In in, int n_fft, int bin_lo, int bin_hi, double theta
   uint32_t* bits = (uint32_t*)(base + o_bits);
   int64_t* cnt = (int64_t*)(base + o_cnt);
   cudaStream_t st = c->stream;
-  k_equalise<In><<<(n_words + 3) / 4, 128, 0, st>>>(in, n_fft, bin_lo, bin_hi, (float)theta, bits,
+  k_equalise<In><<<n_words, 32 * kEqWarps, 0, st>>>(
+      in, n_fft, bin_lo, bin_hi, (float)theta, bits,
                                                    n_words);
   GFH_CUDA_TRY(cudaGetLastError());
   k_count<<<(n_bins + 7) / 8, 256, 0, st>>>(bits, n_bins, n_words, cnt);
@@ -337,7 +388,8 @@ extern "C" int gfh_peaks_from_power_static(void* stream, const float* d_power, i
   cudaStream_t st = (cudaStream_t)stream;
   // Every word of the bit matrix and every count is rewritten below, so nothing left by an
   // earlier call is read.
-  k_equalise<PowerIn><<<(n_words + 3) / 4, 128, 0, st>>>(PowerIn{d_power, ld}, n_fft, bin_lo,
+  k_equalise<PowerIn><<<n_words, 32 * kEqWarps, 0, st>>>(
+      PowerIn{d_power, ld}, n_fft, bin_lo,
                                                          bin_hi, (float)theta, bits, n_words);
   GFH_CUDA_TRY(cudaGetLastError());
   k_count<<<(n_bins + 7) / 8, 256, 0, st>>>(bits, n_bins, n_words, cnt);
