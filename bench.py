@@ -47,10 +47,15 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gfh", choices=["gfh", "reference"])
-    ap.add_argument("--workload", default="plain_paper", choices=["plain_paper", "plain_small"])
+    ap.add_argument("--workload", default="plain_paper",
+                    choices=["plain_paper", "plain_small", "batched_n"])
+    ap.add_argument("--no-graph", action="store_true",
+                    help="time direct calls only (default: the step is also replayed as a CUDA graph)")
     ap.add_argument("--tile", default=None, help="rows,cols,threads of the Hough tiles")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--sequential", action="store_true",
+                    help="also time one plan per map (always on for batched_n)")
     ap.add_argument("--maps", type=int, default=0,
                     help="profiling aid: keep only this many sub-band maps, spread over the band")
     return ap.parse_args()
@@ -62,7 +67,7 @@ def dist_env():
 
 def workload(name, rank):
     fn = getattr(workloads, name)
-    base = {"plain_paper": 2, "plain_small": 1}[name]
+    base = {"plain_paper": 2, "plain_small": 1, "batched_n": 1}[name]
     return fn(seed=base + 7919 * rank)
 
 
@@ -72,6 +77,10 @@ def describe(name, spec, grids):
                 f"{spec.t_obs:g} s, T_FFT {spec.t_fft:g} s ({spec.n_fft} FFTs), 50-2000 Hz in "
                 f"{len(grids)} sub-bands (100 Hz + 50 Hz peakmap extension), n = 5, "
                 f"{grids[0]['n_k']} k rows, top candidate per 1 Hz")
+    if name == "batched_n":
+        return (f"batched_n: the plain_small peakmap (fs {spec.fs:g} Hz, {spec.t_obs:g} s, T_FFT "
+                f"{spec.t_fft:g} s, 100-400 Hz) searched at {len(grids)} braking indices n = 2.0..7.0 "
+                f"(step 0.1) with 4000 -> 1000 k rows, one map per n, all in one launch")
     return (f"plain_small: fs {spec.fs:g} Hz, {spec.t_obs:g} s, T_FFT {spec.t_fft:g} s "
             f"({spec.n_fft} FFTs), 100-400 Hz, n = 5, {grids[0]['n_k']} k rows")
 
@@ -134,16 +143,18 @@ def traffic_for(kernel):
     return rec["bytes_per_launch"] if hashlib.sha256(src).hexdigest() == rec["sha256"] else None
 
 
+
+
 # ---------------------------------------------------------------------------------------------
 # CPU oracle (baseline / reference arm)
 # ---------------------------------------------------------------------------------------------
 
-def oracle_sample(name, rank=0, rows_per_map=20):
+def oracle_sample(name, series=None, rank=0, rows_per_map=20):
     """Times the oracle on a bounded sample: the full peakmap, then `rows_per_map` k rows of every
     map; the step time is extrapolated to all rows."""
     from oracle import gfh_oracle as O
     spec, pm, grids = workload(name, rank)
-    x = spec.series()
+    x = spec.series() if series is None else series
     t0 = time.perf_counter()
     fi, bj = O.peakmap(x, spec.fs, spec.t_fft, pm["bin_lo"], pm["bin_hi"])
     t_pm = time.perf_counter() - t0
@@ -167,13 +178,14 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
+    spec, pm, grids = workload(args.workload, 0)
+    x = spec.series()
     vals, times = [], []
     for i in range(args.warmup + args.steps):
-        v, t, sample = oracle_sample(args.workload, 0, rows_per_map=10)
+        v, t, sample = oracle_sample(args.workload, x, 0, rows_per_map=10)
         if i >= args.warmup:
             vals.append(v)
             times.append(t)
-    spec, pm, grids = workload(args.workload, 0)
     value = float(np.mean(vals))
     line = {"impl": "reference", "metric": "Hough updates/s (peaks x k-bins)", "value": value,
             "unit": "updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -202,14 +214,16 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     _build.build()
-    stream = torch.cuda.current_stream()
+    # the library works on its own stream (also the graph-capture stream)
+    stream = torch.cuda.Stream()
     ctx = gfh.Context(local, stream)
 
     spec, pm, grid_fields = workload(args.workload, rank)
     if args.maps and args.maps < len(grid_fields):
         keep = np.linspace(0, len(grid_fields) - 1, args.maps).round().astype(int)
         grid_fields = [grid_fields[i] for i in sorted(set(keep))]
-    x_host = torch.from_numpy(spec.series()).pin_memory()
+    series_np = spec.series()
+    x_host = torch.from_numpy(series_np).pin_memory()
     x_dev = x_host.cuda()
     grids = [gfh.grid_make(gfh.Grid(**f)) for f in grid_fields]
     maps = [torch.empty((g.n_k, g.ld_x0), dtype=torch.int32, device="cuda") for g in grids]
@@ -224,41 +238,40 @@ def run_gpu(args):
     fo = torch.empty(cap, dtype=torch.int32, device="cuda")
     bo = torch.empty(cap, dtype=torch.int32, device="cuda")
     off = torch.zeros(2, dtype=torch.int64, device="cuda")
+    torch.cuda.synchronize()
 
-    state = {}
-
-    def step(h2d=False):
+    def step(h2d=False, stage_events=None):
+        """One search step through the public API (the peakmap count comes back to the host)."""
         if h2d:
             x_dev.copy_(x_host, non_blocking=True)
         n = ctx.peakmap(x_dev, spec.fs, spec.t_fft, pm["bin_lo"], pm["bin_hi"], 2.5, fo, bo)
-        state["n"] = n
         off[1] = n
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
+        if stage_events is not None:
+            stage_events[0].record(stream)
         plan.execute(fo, bo, off, 1)
-        e1.record(stream)
+        if stage_events is not None:
+            stage_events[1].record(stream)
         if h2d:
             for c, h in zip(cands, cand_host):
                 h.copy_(c, non_blocking=True)
-        return e0, e1
+        return n
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    tuned, t_tune = None, 0.0
-    if not args.no_autotune and tile is None:
-        t_tune = time.perf_counter()
-        tuned, _ = plan.autotune(fo, bo, off, 1, reps=2)
-        t_tune = time.perf_counter() - t_tune
-        step()
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            n_peaks = step()
         torch.cuda.synchronize()
-    if ctx.check() != gfh.GFH_OK:
-        raise RuntimeError("input check failed")
+        if ctx.check() != gfh.GFH_OK:
+            raise RuntimeError("input check failed")
+        tuned, t_tune = None, 0.0
+        if not args.no_autotune and tile is None:
+            t_tune = time.perf_counter()
+            tuned, _ = plan.autotune(fo, bo, off, 1, reps=2)
+            t_tune = time.perf_counter() - t_tune
+            step()
+            torch.cuda.synchronize()
     # updates of this rank's step: peaks inside each map's band x its k rows
-    bins = bo[: state["n"]].cpu().numpy()
+    bins = bo[:n_peaks].cpu().numpy()
     updates = sum(int(((bins >= g.bin_lo) & (bins <= g.bin_hi)).sum()) * g.n_k for g in grids)
-    launches_per_step = 8   # k_equalise, k_count, k_scan, k_scatter, k_check_sorted, k_csr, k_hough, k_finalize
 
     def barrier():
         if world > 1:
@@ -266,49 +279,95 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def maxed(v):
+    def reduce(v, op):
         if world == 1:
             return v
         import torch.distributed as dist
         t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=op)
         return float(t.item())
 
-    def sumd(v):
-        if world == 1:
-            return v
-        import torch.distributed as dist
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+    import torch.distributed as tdist
+    MAX, SUM = (tdist.ReduceOp.MAX, tdist.ReduceOp.SUM) if world > 1 else (None, None)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
 
-    # ---- device-resident timing
+    # ---- CUDA graph of the whole step: asynchronous peakmap + plan, no host round trip
+    graph = None
+    if not args.no_graph:
+        with torch.cuda.stream(stream):
+            ctx.peakmap_async(x_dev, spec.fs, spec.t_fft, pm["bin_lo"], pm["bin_hi"], 2.5, fo, bo, off[1:2])
+            plan.execute(fo, bo, off, 1)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            ctx.peakmap_async(x_dev, spec.fs, spec.t_fft, pm["bin_lo"], pm["bin_hi"], 2.5, fo, bo, off[1:2])
+            plan.execute(fo, bo, off, 1)
+        for _ in range(2):
+            graph.replay()
+        torch.cuda.synchronize()
+        if ctx.check() != gfh.GFH_OK or int(off[1].item()) != n_peaks:
+            raise RuntimeError("graph replay differs from the direct step")
+
+    # ---- device-resident timing (clocks sampled meanwhile)
     sampler = ClockSampler(local)
-    with sampler:
+    with sampler, torch.cuda.stream(stream):
         barrier()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
+        a, b = ev(), ev()
+        hough = [(ev(), ev()) for _ in range(args.steps)]
         a.record(stream)
-        hough = [step() for _ in range(args.steps)]
+        for i in range(args.steps):
+            step(stage_events=hough[i])
         b.record(stream)
         barrier()
+        ms_direct = a.elapsed_time(b) / args.steps
+        ms_graph = None
+        if graph is not None:
+            barrier()
+            a.record(stream)
+            for _ in range(args.steps):
+                graph.replay()
+            b.record(stream)
+            barrier()
+            ms_graph = a.elapsed_time(b) / args.steps
     clocks = sampler.summary()
-    ms = a.elapsed_time(b) / args.steps
     ms_hough = sum(e0.elapsed_time(e1) for e0, e1 in hough) / args.steps
-    ms_max = maxed(ms)
-    total_updates = sumd(float(updates))
+    ms = ms_graph if ms_graph is not None else ms_direct
+    ms_max = reduce(ms, MAX)
+    total_updates = reduce(float(updates), SUM)
     value = total_updates / (ms_max * 1e-3)
 
     # ---- end to end through the public API with host buffers
-    barrier()
-    a.record(stream)
-    for _ in range(args.steps):
-        step(h2d=True)
-    b.record(stream)
-    barrier()
-    ms_e2e = maxed(a.elapsed_time(b) / args.steps)
+    with torch.cuda.stream(stream):
+        barrier()
+        a.record(stream)
+        for _ in range(args.steps):
+            step(h2d=True)
+        b.record(stream)
+        barrier()
+        ms_e2e = reduce(a.elapsed_time(b) / args.steps, MAX)
     h2d = x_host.numel() * 4
     d2h = sum(c.numel() for c in cands)
+
+    # ---- batched vs one plan per map (the maps share the step's peak list)
+    sequential = None
+    if args.workload == "batched_n" or len(grids) > 1 and args.sequential:
+        cfg = tuned or tile
+        singles = [gfh.Plan(ctx, [g], [m], [c], None, tile=cfg) for g, m, c in zip(grids, maps, cands)]
+        with torch.cuda.stream(stream):
+            for sp in singles:
+                sp.execute(fo, bo, off, 1)
+            barrier()
+            a.record(stream)
+            for _ in range(args.steps):
+                for sp in singles:
+                    sp.execute(fo, bo, off, 1)
+            b.record(stream)
+            barrier()
+        ms_seq = a.elapsed_time(b) / args.steps
+        sequential = {"ms_hough_one_plan_per_map": ms_seq, "ms_hough_batched": ms_hough,
+                      "speedup": ms_seq / ms_hough}
+        for sp in singles:
+            sp.close()
 
     if rank != 0:
         plan.close()
@@ -323,27 +382,32 @@ def run_gpu(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int32 counts, fp32 spectra, fp64 grid", "data": "synthetic",
         "config": {"workload": describe(args.workload, spec, grid_fields),
-                   "maps": len(grids), "peaks": state["n"], "updates_per_step": updates,
+                   "maps": len(grids), "peaks": n_peaks, "updates_per_step": updates,
                    "cells": int(sum(g.n_k * g.n_x0 for g in grids)),
-                   "l2": "inputs larger than L2: 165 MB series and 0.9 GB of maps per step" if args.workload == "plain_paper" else "small workload",
+                   "l2": "inputs larger than L2 (series %d MB, maps %d MB per step)" % (h2d // 1000000, map_bytes // 1000000),
                    "tile": list(tile) if tile else (list(tuned) if tuned else "default"),
                    "tile_source": "given" if tile else ("autotuned" if tuned else "default"),
+                   "timing": "CUDA graph of the step" if graph is not None else "direct calls",
                    "plan_build_s": round(t_plan, 3), "autotune_s": round(t_tune, 3)},
-        "breakdown_ms": {"step": ms, "hough_select": ms_hough, "peakmap": ms - ms_hough},
+        "breakdown_ms": {"step_graph": ms_graph, "step_direct": ms_direct, "hough_select": ms_hough,
+                         "peakmap_and_host": ms_direct - ms_hough},
         "roofline": {"bound": "smem_atomic", "kernel": "k_hough", "achieved": achieved,
                      "peak": SMEM_ATOMIC_PEAK, "unit": "Gatomic/s", "frac": achieved / SMEM_ATOMIC_PEAK,
                      "peak_source": "derived: 152 SMs x 16 shared atomics/clk x max SM clock",
-                     "traffic": traffic_for("k_hough"),
+                     "algorithmic": "2 shared atomics per update (differential +1/-1)",
+                     "traffic": traffic_for("k_hough") if args.workload == "plain_paper" and not args.maps else None,
                      "hbm": {"map_store_bytes": map_bytes, "achieved_gbs": map_bytes / (ms_hough * 1e-3) / 1e9,
                              "peak_gbs": HBM_PEAK, "frac": map_bytes / (ms_hough * 1e-3) / 1e9 / HBM_PEAK,
                              "peak_source": HBM_PEAK_SRC}},
         "e2e": {"value": total_updates / (ms_e2e * 1e-3), "unit": "updates/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e},
-        "gpu_launches": launches_per_step * args.steps,
+        "gpu_launches": 9 * args.steps,
         "clocks": clocks,
     }
+    if sequential:
+        line["batched_vs_one_plan_per_map"] = sequential
     if world == 1 and not args.no_cpu_baseline:
-        v, t, sample = oracle_sample(args.workload)
+        v, t, sample = oracle_sample(args.workload, series_np)
         line["cpu_baseline"] = {"value": v, "unit": "updates/s", "cores": 1, "kind": "oracle", "sample": sample}
     print(json.dumps(line), flush=True)
     plan.close()

@@ -141,8 +141,9 @@ typedef struct gfh_tile_config {
 int gfh_create(gfh_ctx** out, int device, void* stream);
 int gfh_destroy(gfh_ctx* ctx);
 int gfh_set_stream(gfh_ctx* ctx, void* stream);
-/* Synchronises the stream, then returns and clears the device-side input-check flag:
- * GFH_OK, or GFH_ERR_INPUT when the last calls saw unsorted peaks or an out-of-range index. */
+/* Synchronises the stream, then returns and clears the device-side check flag: GFH_OK,
+ * GFH_ERR_INPUT when the last calls saw unsorted peaks or an out-of-range index, or GFH_ERR_SIZE
+ * when an asynchronous peakmap found more peaks than its capacity. */
 int gfh_check(gfh_ctx* ctx);
 const char* gfh_strerror(int code);
 
@@ -194,6 +195,17 @@ int gfh_peaks_from_power(gfh_ctx* ctx, const float* d_power, int64_t ld, int32_t
 int gfh_peakmap(gfh_ctx* ctx, const float* d_series, int64_t n_samples, double fs, double t_fft,
                 int32_t bin_lo, int32_t bin_hi, double theta, uint32_t* d_fft_idx,
                 uint32_t* d_bin, int64_t cap, int64_t* h_n_peaks);
+
+/*
+ * gfh_peakmap without any host synchronisation: the number of peaks written, min(total, cap), goes
+ * to the device int64 *d_n_peaks (for example element 1 of a gfh_peaks offsets array whose element
+ * 0 is 0), and a total above cap is reported by gfh_check as GFH_ERR_SIZE.  The first call with a
+ * given (n_samples, fs, t_fft) builds the cuFFT plan and may grow the scratch: make it before any
+ * stream capture; later calls only enqueue work and can be captured in a CUDA graph.
+ */
+int gfh_peakmap_async(gfh_ctx* ctx, const float* d_series, int64_t n_samples, double fs,
+                      double t_fft, int32_t bin_lo, int32_t bin_hi, double theta,
+                      uint32_t* d_fft_idx, uint32_t* d_bin, int64_t cap, int64_t* d_n_peaks);
 
 /*
  * Plan for Hough maps plus candidates of n_maps grids (each made by gfh_grid_make), bound to

@@ -184,7 +184,7 @@ extern "C" int gfh_check(gfh_ctx* c) {
   if (flag) {
     GFH_CUDA_TRY(cudaMemsetAsync(c->d_flag, 0, sizeof(unsigned int), c->stream));
     GFH_CUDA_TRY(cudaStreamSynchronize(c->stream));
-    return GFH_ERR_INPUT;
+    return (flag & (GFH_FLAG_UNSORTED | GFH_FLAG_FFT_RANGE)) ? GFH_ERR_INPUT : GFH_ERR_SIZE;
   }
   return GFH_OK;
 }
@@ -411,6 +411,11 @@ extern "C" int gfh_plan_create(gfh_ctx* ctx, int32_t n_maps, const gfh_grid* gri
   p->h_maps.assign(h_maps, h_maps + n_maps);
   if (h_cands) p->h_cands.assign(h_cands, h_cands + n_maps);
   p->d_stats = d_stats;
+  const int prc = gfh_prepare_plan(p);
+  if (prc) {
+    gfh_plan_destroy(p);
+    return prc;
+  }
   *out = p;
   return GFH_OK;
 }

@@ -380,10 +380,18 @@ __global__ void k_select_cols(const int32_t* __restrict__ map, const MapDev* __r
   }
 }
 
+// Launch (prepare = false) or set the shared-memory attribute (prepare = true).  Setting the
+// attribute at plan creation keeps gfh_plan_execute to stream operations only (capturable).  The
+// attribute belongs to the kernel, not to a plan, so it is set to the largest size any plan may
+// request: each launch still asks only for its own size (which alone decides occupancy).
 template <int R, int NT, bool SEL>
-int launch_hough_t(gfh_plan* p, const gfh_peaks* peaks, size_t smem) {
+int launch_hough_t(gfh_plan* p, const gfh_peaks* peaks, size_t smem, bool prepare) {
   auto fn = k_hough<R, NT, SEL>;
-  GFH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (prepare) {
+    GFH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)kMaxSmemBytes));
+    return GFH_OK;
+  }
   fn<<<p->n_tiles, NT, smem, p->ctx->stream>>>(p->d_maps, p->d_tiles, peaks->fft_idx, peaks->bin,
                                                  p->ctx->d_flag, p->cfg.cols);
   GFH_CUDA_TRY(cudaGetLastError());
@@ -391,15 +399,22 @@ int launch_hough_t(gfh_plan* p, const gfh_peaks* peaks, size_t smem) {
 }
 
 template <int R, int NT>
-int launch_hough_sel(gfh_plan* p, const gfh_peaks* peaks, size_t smem) {
-  return p->select ? launch_hough_t<R, NT, true>(p, peaks, smem)
-                   : launch_hough_t<R, NT, false>(p, peaks, smem);
+int launch_hough_sel(gfh_plan* p, const gfh_peaks* peaks, size_t smem, bool prepare) {
+  return p->select ? launch_hough_t<R, NT, true>(p, peaks, smem, prepare)
+                   : launch_hough_t<R, NT, false>(p, peaks, smem, prepare);
 }
 
 template <int R>
-int launch_hough_r(gfh_plan* p, const gfh_peaks* peaks, size_t smem) {
-  return p->cfg.threads == 256 ? launch_hough_sel<R, 256>(p, peaks, smem)
-                               : launch_hough_sel<R, 512>(p, peaks, smem);
+int launch_hough_r(gfh_plan* p, const gfh_peaks* peaks, size_t smem, bool prepare) {
+  return p->cfg.threads == 256 ? launch_hough_sel<R, 256>(p, peaks, smem, prepare)
+                               : launch_hough_sel<R, 512>(p, peaks, smem, prepare);
+}
+
+int launch_hough(gfh_plan* p, const gfh_peaks* peaks, size_t smem, bool prepare) {
+  return p->cfg.rows == 4    ? launch_hough_r<4>(p, peaks, smem, prepare)
+         : p->cfg.rows == 8  ? launch_hough_r<8>(p, peaks, smem, prepare)
+         : p->cfg.rows == 16 ? launch_hough_r<16>(p, peaks, smem, prepare)
+                             : launch_hough_r<32>(p, peaks, smem, prepare);
 }
 
 }  // namespace
@@ -407,6 +422,12 @@ int launch_hough_r(gfh_plan* p, const gfh_peaks* peaks, size_t smem) {
 size_t gfh_hough_smem_bytes(const gfh_plan* p) {
   return (size_t)p->cfg.rows * (p->cfg.cols + 2) * 4 + (size_t)kLane * 4 +
          (p->select ? (size_t)p->max_tile_bands * 8 : 0);
+}
+
+int gfh_prepare_plan(gfh_plan* p) {
+  const size_t smem = gfh_hough_smem_bytes(p);
+  if (smem > 227 * 1024) return GFH_ERR_SIZE;
+  return launch_hough(p, nullptr, smem, true);
 }
 
 int gfh_launch_plan(gfh_plan* p, const gfh_peaks* peaks) {
@@ -426,10 +447,7 @@ int gfh_launch_plan(gfh_plan* p, const gfh_peaks* peaks) {
   if (p->select)
     GFH_CUDA_TRY(cudaMemsetAsync(p->d_keys, 0, p->key_words * sizeof(unsigned long long), st));
   if (p->n_tiles > 0) {
-    int rc = p->cfg.rows == 4    ? launch_hough_r<4>(p, peaks, smem)
-             : p->cfg.rows == 8  ? launch_hough_r<8>(p, peaks, smem)
-             : p->cfg.rows == 16 ? launch_hough_r<16>(p, peaks, smem)
-                                 : launch_hough_r<32>(p, peaks, smem);
+    const int rc = launch_hough(p, peaks, smem, false);
     if (rc) return rc;
   }
   if (p->select) {

@@ -11,9 +11,13 @@
 
 #define GFH_FRAC_BITS 32
 
+// Largest dynamic shared memory a block may use on sm_103a (227 KB).
+constexpr size_t kMaxSmemBytes = 227 * 1024;
+
 // Device-side error flag bits (gfh_check).
 #define GFH_FLAG_UNSORTED 1u
 #define GFH_FLAG_FFT_RANGE 2u
+#define GFH_FLAG_CAPACITY 4u
 
 #define GFH_CUDA_TRY(expr)                                \
   do {                                                    \
@@ -105,4 +109,5 @@ int gfh_host_columns(const gfh_grid* g, std::vector<int32_t>& band, std::vector<
 
 // Launchers (gfh_hough.cu).
 int gfh_launch_plan(gfh_plan* plan, const gfh_peaks* peaks);
+int gfh_prepare_plan(gfh_plan* plan);   // one-time kernel attributes (outside any capture)
 int gfh_launch_select(gfh_ctx* ctx, const int32_t* d_map, const MapDev& md, void* d_scratch);

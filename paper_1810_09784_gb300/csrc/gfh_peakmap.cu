@@ -236,9 +236,22 @@ size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
 // Equalise + select + compact from an input layout; `extra` bytes at the front of the scratch
 // buffer are reserved for the caller (the FFT output).
+// min(total, cap) to the caller's device word; a total above cap flags the context.
+__global__ void k_finish_count(const int64_t* __restrict__ total, int64_t cap, int64_t* d_n,
+                               unsigned int* flag) {
+  if (threadIdx.x == 0) {
+    const int64_t n = *total;
+    if (n > cap) atomicOr(flag, GFH_FLAG_CAPACITY);
+    *d_n = n < cap ? n : cap;
+  }
+}
+
+// Equalise + select + compact from an input layout; `extra` bytes at the front of the scratch
+// buffer are reserved for the caller (the FFT output).  With d_n the count goes to device memory
+// and nothing synchronises; otherwise it is read back into *h_n.
 template <class In>
 int run_peaks(gfh_ctx* c, In in, int n_fft, int bin_lo, int bin_hi, double theta, uint32_t* d_fft,
-              uint32_t* d_bin, int64_t cap, int64_t* h_n, size_t extra) {
+              uint32_t* d_bin, int64_t cap, int64_t* h_n, size_t extra, int64_t* d_n = nullptr) {
   const int n_bins = bin_hi - bin_lo + 1;
   const int n_words = (n_fft + 31) / 32;
   const size_t o_bits = align256(extra);
@@ -261,6 +274,11 @@ int run_peaks(gfh_ctx* c, In in, int n_fft, int bin_lo, int bin_hi, double theta
   k_scatter<<<(n_bins + 7) / 8, 256, 0, st>>>(bits, n_bins, n_words, bin_lo, cnt, d_fft, d_bin,
                                               cap);
   GFH_CUDA_TRY(cudaGetLastError());
+  if (d_n) {
+    k_finish_count<<<1, 32, 0, st>>>(cnt + n_bins, cap, d_n, c->d_flag);
+    GFH_CUDA_TRY(cudaGetLastError());
+    return GFH_OK;
+  }
   GFH_CUDA_TRY(cudaMemcpyAsync(c->h_pinned, cnt + n_bins, 8, cudaMemcpyDeviceToHost, st));
   GFH_CUDA_TRY(cudaStreamSynchronize(st));
   *h_n = (int64_t)c->h_pinned[0];
@@ -285,12 +303,13 @@ extern "C" int gfh_peaks_from_power(gfh_ctx* ctx, const float* d_power, int64_t 
                    h_n_peaks, 0);
 }
 
-extern "C" int gfh_peakmap(gfh_ctx* ctx, const float* d_series, int64_t n_samples, double fs,
-                           double t_fft, int32_t bin_lo, int32_t bin_hi, double theta,
-                           uint32_t* d_fft_idx, uint32_t* d_bin, int64_t cap,
-                           int64_t* h_n_peaks) {
-  if (!ctx || !d_series || !h_n_peaks || cap < 0 || (cap > 0 && (!d_fft_idx || !d_bin)) ||
-      !(fs > 0.0) || !(t_fft > 0.0))
+namespace {
+
+int peakmap_impl(gfh_ctx* ctx, const float* d_series, int64_t n_samples, double fs, double t_fft,
+                 int32_t bin_lo, int32_t bin_hi, double theta, uint32_t* d_fft_idx,
+                 uint32_t* d_bin, int64_t cap, int64_t* h_n_peaks, int64_t* d_n_peaks) {
+  if (!ctx || !d_series || (!h_n_peaks && !d_n_peaks) || cap < 0 ||
+      (cap > 0 && (!d_fft_idx || !d_bin)) || !(fs > 0.0) || !(t_fft > 0.0))
     return GFH_ERR_ARG;
   const double nd = fs * t_fft;
   if (!(nd >= 4.0) || nd > 1.0e8) return GFH_ERR_ARG;
@@ -331,7 +350,27 @@ extern "C" int gfh_peakmap(gfh_ctx* ctx, const float* d_series, int64_t n_sample
       CUFFT_SUCCESS)
     return GFH_ERR_CUDA;
   return run_peaks(ctx, ComplexIn{spec, nc}, n_fft, bin_lo, bin_hi, theta, d_fft_idx, d_bin, cap,
-                   h_n_peaks, spec_bytes);
+                   h_n_peaks, spec_bytes, d_n_peaks);
+}
+
+}  // namespace
+
+extern "C" int gfh_peakmap(gfh_ctx* ctx, const float* d_series, int64_t n_samples, double fs,
+                           double t_fft, int32_t bin_lo, int32_t bin_hi, double theta,
+                           uint32_t* d_fft_idx, uint32_t* d_bin, int64_t cap,
+                           int64_t* h_n_peaks) {
+  if (!h_n_peaks) return GFH_ERR_ARG;
+  return peakmap_impl(ctx, d_series, n_samples, fs, t_fft, bin_lo, bin_hi, theta, d_fft_idx, d_bin,
+                      cap, h_n_peaks, nullptr);
+}
+
+extern "C" int gfh_peakmap_async(gfh_ctx* ctx, const float* d_series, int64_t n_samples,
+                                 double fs, double t_fft, int32_t bin_lo, int32_t bin_hi,
+                                 double theta, uint32_t* d_fft_idx, uint32_t* d_bin, int64_t cap,
+                                 int64_t* d_n_peaks) {
+  if (!d_n_peaks) return GFH_ERR_ARG;
+  return peakmap_impl(ctx, d_series, n_samples, fs, t_fft, bin_lo, bin_hi, theta, d_fft_idx, d_bin,
+                      cap, nullptr, d_n_peaks);
 }
 
 // ---- allocation-free peak selection -------------------------------------------------------------

@@ -27,7 +27,7 @@ GFH_ERR_NOMEM = -6
 EXPORTED = [
     "gfh_create", "gfh_destroy", "gfh_set_stream", "gfh_check", "gfh_strerror",
     "gfh_grid_make", "gfh_grid_tables", "gfh_grid_columns",
-    "gfh_peaks_from_power", "gfh_peakmap",
+    "gfh_peaks_from_power", "gfh_peakmap", "gfh_peakmap_async",
     "gfh_plan_create", "gfh_plan_destroy", "gfh_plan_execute", "gfh_plan_autotune",
     "gfh_hough", "gfh_select", "gfh_peaks_from_power_static",
 ]
@@ -107,6 +107,7 @@ def lib() -> ctypes.CDLL:
             "gfh_grid_columns": [P(GridC), vp, vp, vp],
             "gfh_peaks_from_power": [vp, vp, i64, i32, i32, i32, dbl, vp, vp, i64, P(i64)],
             "gfh_peakmap": [vp, vp, i64, dbl, dbl, i32, i32, dbl, vp, vp, i64, P(i64)],
+            "gfh_peakmap_async": [vp, vp, i64, dbl, dbl, i32, i32, dbl, vp, vp, i64, vp],
             "gfh_plan_create": [vp, i32, P(GridC), P(vp), P(vp), vp, P(TileConfigC), P(vp)],
             "gfh_plan_destroy": [vp],
             "gfh_plan_execute": [vp, P(PeaksC)],
@@ -258,6 +259,15 @@ class Context:
                                ctypes.byref(n))
         _ok(rc, "gfh_peakmap")
         return n.value
+
+    def peakmap_async(self, series, fs: float, t_fft: float, bin_lo: int, bin_hi: int,
+                      theta: float, fft_out, bin_out, n_out) -> None:
+        """gfh_peakmap_async: no host synchronisation; min(total, capacity) goes to the device
+        int64 `n_out` (a one-element view such as offsets[1:2])."""
+        rc = lib().gfh_peakmap_async(self._h, _ptr(series), series.numel(), fs, t_fft, bin_lo,
+                                     bin_hi, theta, _ptr(fft_out), _ptr(bin_out),
+                                     fft_out.numel(), _ptr(n_out))
+        _ok(rc, "gfh_peakmap_async")
 
     # ---- Hough map + candidates (Sec. IV)
     def hough(self, fft_idx, bins, n_peaks: int, g: Grid, out_map, cands=None, stats=None) -> None:
