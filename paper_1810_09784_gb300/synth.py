@@ -83,6 +83,55 @@ def strain_series(n_samples: int, fs: float, seed: int, injections=(), sigma: fl
     return out
 
 
+def statistical_peaklist(n_fft: int, bin_lo: int, bin_hi: int, p_noise: float, seed: int,
+                         tracks=(), p_track: float = 0.6):
+    """Peak list (fft_idx, bin) sorted by (bin, fft) from a statistical model of a peakmap.
+
+    Every (FFT, bin) cell is a noise peak independently with probability `p_noise` (drawn as a
+    Bernoulli process along the FFTs of each bin through geometric gaps, so the cost follows the
+    number of peaks, not of cells).  Each track is an array of bins, one per FFT (negative for none),
+    whose cell is made a peak with probability `p_track`.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    nb = bin_hi - bin_lo + 1
+    expect = n_fft * p_noise
+    g = int(expect + 6.0 * math.sqrt(expect + 1.0) + 16)
+    fft_parts, bin_parts = [], []
+    chunk = max(1, (1 << 24) // max(g, 1))
+    for b0 in range(0, nb, chunk):
+        b1 = min(nb, b0 + chunk)
+        while True:
+            pos = np.cumsum(rng.geometric(p_noise, size=(b1 - b0, g)), axis=1) - 1
+            if np.all(pos[:, -1] >= n_fft):     # every bin's process ran past the last FFT
+                break
+            g *= 2
+        rows, cols = np.nonzero(pos < n_fft)
+        fft_parts.append(pos[rows, cols].astype(np.int64))
+        bin_parts.append((rows + b0 + bin_lo).astype(np.int64))
+    fi = np.concatenate(fft_parts) if fft_parts else np.zeros(0, np.int64)
+    bj = np.concatenate(bin_parts) if bin_parts else np.zeros(0, np.int64)
+    key = bj * n_fft + fi                        # sorted by (bin, fft), one peak per cell
+    extra = []
+    for tr in tracks:
+        tr = np.asarray(tr, dtype=np.int64)
+        i = np.nonzero((tr >= bin_lo) & (tr <= bin_hi) & (rng.random(tr.size) < p_track))[0]
+        extra.append(tr[i] * n_fft + i)
+    if extra:
+        add = np.unique(np.concatenate(extra))
+        pos = np.searchsorted(key, add)
+        new = (pos >= key.size) | (key[np.minimum(pos, key.size - 1)] != add) if key.size else np.ones(add.size, bool)
+        key = np.insert(key, pos[new], add[new])
+    return (key % n_fft).astype(np.uint32), (key // n_fft).astype(np.uint32)
+
+
+def powerlaw_track(f0: float, k: float, n: float, df: float, n_fft: int, t_first: float,
+                   t_hop: float) -> np.ndarray:
+    """Bin holding f(t_i) = f0 (1 + (n-1) k f0^(n-1) t_i)^(-1/(n-1)) at each FFT time t_i."""
+    t = t_first + t_hop * np.arange(n_fft)
+    f = f0 / (1.0 + (n - 1.0) * k * f0 ** (n - 1.0) * t) ** (1.0 / (n - 1.0))
+    return np.floor(f / df + 0.5).astype(np.int64)
+
+
 def random_peaklist(n_fft: int, bin_lo: int, bin_hi: int, density: float, seed: int):
     """Random (fft_idx, bin) pairs sorted by (bin, fft_idx), at most one per cell.
 

@@ -126,3 +126,67 @@ def batched_n(seed: int = 1):
         n_k = int(round(4000 - 3000 * (n - 2.0) / 5.0))
         grids.append(grid_fields(spec, n, pm["bin_lo"], pm["bin_hi"], n_k, 100.0, 400.0))
     return spec, pm, grids
+
+
+# ---- uneven ------------------------------------------------------------------------------------
+
+P0_THETA_2_5 = 0.0755      # noise peak probability of a strict local maximum above 2.5 (exp(1) power)
+
+
+def uneven(seed: int = 4, n_maps: int = 256, hours=(1.0, 24.0), width_hz=(20.0, 1950.0),
+           n_k: int = 1000, p_track: float = 0.6):
+    """Independent peakmaps of uneven size (statistical peakmap model, no time series): duration
+    log-uniform in `hours`, T_FFT in {1, 2, 4, 8} s, a band of log-uniform width inside 50-2000 Hz,
+    0-3 power-law injections (n in [2, 7], |fdot0| log-uniform up to 1/T_FFT^2).  Each peakmap is
+    searched in 100 Hz analysis bands (peakmap band 50 Hz wider, capped at the band top) at the
+    braking index of its first injection (else uniform in [2, 7]) with `n_k` k rows.
+
+    Returns (lists, grids, truth): lists[l] = (fft_idx, bin); grids[m]['list'] = its peakmap.
+    """
+    import concurrent.futures
+    import os
+
+    specs = []
+    for m in range(n_maps):
+        rng = np.random.Generator(np.random.PCG64(seed * 100003 + m))
+        t_obs = 3600.0 * math.exp(rng.uniform(math.log(hours[0]), math.log(hours[1])))
+        t_fft = float(rng.choice([1.0, 2.0, 4.0, 8.0]))
+        df = 1.0 / t_fft
+        n_fft = int((t_obs - t_fft) // (t_fft / 2.0)) + 1
+        w = math.exp(rng.uniform(math.log(width_hz[0]), math.log(width_hz[1])))
+        f_lo = rng.uniform(50.0, 2000.0 - w)
+        f_hi = f_lo + w
+        bin_lo, bin_hi = int(math.ceil(f_lo / df)), int(math.floor(f_hi / df)) - 1
+        injs = []
+        for _ in range(int(rng.integers(0, 4))):
+            n = rng.uniform(2.0, 7.0)
+            f0 = rng.uniform(f_lo + 0.2 * w, f_hi)
+            fdot = math.exp(rng.uniform(math.log(1e-4), math.log(1.0 / t_fft ** 2)))
+            injs.append((f0, fdot / f0 ** n, n))
+        n_hough = injs[0][2] if injs else rng.uniform(2.0, 7.0)
+        specs.append(dict(t_obs=t_obs, t_fft=t_fft, df=df, n_fft=n_fft, bin_lo=bin_lo, bin_hi=bin_hi,
+                          f_lo=bin_lo * df, f_hi=(bin_hi + 1) * df, injs=injs, n=n_hough, seed=seed * 100003 + m))
+
+    def make_list(s):
+        tracks = [synth.powerlaw_track(f0, k, n, s["df"], s["n_fft"], s["t_fft"] / 2, s["t_fft"] / 2)
+                  for f0, k, n in s["injs"]]
+        return synth.statistical_peaklist(s["n_fft"], s["bin_lo"], s["bin_hi"], P0_THETA_2_5,
+                                          s["seed"], tracks, p_track)
+
+    with concurrent.futures.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        lists = list(ex.map(make_list, specs))
+    grids = []
+    for l, s in enumerate(specs):
+        a = s["f_lo"]
+        while a < s["f_hi"] - 1e-9:
+            b = min(a + 100.0, s["f_hi"])
+            top = min(b + 50.0, s["f_hi"])
+            lo_bin = int(round(a / s["df"]))
+            hi_bin = int(round(top / s["df"])) - 1
+            if hi_bin >= lo_bin:
+                grids.append(dict(n=s["n"], df=s["df"], bin_lo=lo_bin, bin_hi=hi_bin, n_fft=s["n_fft"],
+                                  t_first=s["t_fft"] / 2, t_hop=s["t_fft"] / 2, t_obs=s["t_obs"],
+                                  n_k=n_k, k_min=0.0, dk=0.0, f_max=0.0, ana_lo=a, ana_hi=b,
+                                  band_hz=1.0, list=l))
+            a = b
+    return lists, grids, specs

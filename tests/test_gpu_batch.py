@@ -61,6 +61,33 @@ def test_batched_braking_indices_one_launch(built_lib, gpu_ctx, small_peaks):
     plan.close()
 
 
+def test_uneven_peakmaps_scaled_down(built_lib, gpu_ctx):
+    """The uneven workload's generator at small sizes (minutes of data, narrow bands): every
+    sub-band map of every peakmap, from one launch, equals the oracle's."""
+    gfh = built_lib
+    lists, fields, _ = workloads.uneven(seed=11, n_maps=6, hours=(0.05, 0.3), width_hz=(20.0, 160.0),
+                                        n_k=24)
+    off = np.cumsum([0] + [len(f) for f, _ in lists]).astype(np.int64)
+    all_fi = np.concatenate([f for f, _ in lists]).astype(np.uint32)
+    all_bj = np.concatenate([b for _, b in lists]).astype(np.uint32)
+    gs = [gfh.grid_make(gfh.Grid(**f)) for f in fields]
+    assert len(gs) > len(lists)                       # several sub-bands for some peakmaps
+    maps = [torch.full((g.n_k, g.ld_x0), -7, dtype=torch.int32, device="cuda") for g in gs]
+    cands = [torch.zeros(g.n_bands * 64, dtype=torch.uint8, device="cuda") for g in gs]
+    plan = gfh.Plan(gpu_ctx, gs, maps, cands, None)
+    plan.execute(to_dev(torch, all_fi), to_dev(torch, all_bj), to_dev(torch, off), len(lists))
+    torch.cuda.synchronize()
+    assert gpu_ctx.check() == gfh.GFH_OK
+    for m, (f, g) in enumerate(zip(fields, gs)):
+        fi, bj = lists[f["list"]]
+        o = oracle_grid(f)
+        ref = O.hough_map(o, fi, bj)
+        assert np.array_equal(maps[m].cpu().numpy()[:, : g.n_x0], ref), m
+        oc, _ = O.select_candidates(o, ref)
+        assert_candidates_equal(read_cands(gfh, cands[m]), oc, g.n_bands)
+    plan.close()
+
+
 def test_plans_of_different_sizes_interleave(built_lib, gpu_ctx):
     """Plans with different shared-memory needs for the same kernel shape can be created in any
     order and executed in any order (the kernel attribute is not per plan)."""
