@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gfh", choices=["gfh", "reference"])
     ap.add_argument("--workload", default="plain_paper",
-                    choices=["plain_paper", "plain_small", "batched_n", "uneven"])
+                    choices=["plain_paper", "plain_small", "batched_n", "uneven", "proposer"])
     ap.add_argument("--no-graph", action="store_true",
                     help="time direct calls only (default: the step is also replayed as a CUDA graph)")
     ap.add_argument("--tile", default=None, help="rows,cols,threads of the Hough tiles")
@@ -56,6 +56,10 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--sequential", action="store_true",
                     help="also time one plan per map (always on for batched_n)")
+    ap.add_argument("--epochs", type=int, default=3,
+                    help="proposer: training passes over the 100,000 training maps")
+    ap.add_argument("--eval-maps", type=int, default=51 * 196,
+                    help="proposer: held-out maps for the recall measurement (multiple of 51)")
     ap.add_argument("--maps", type=int, default=0,
                     help="profiling aid: keep only this many sub-band maps, spread over the band")
     return ap.parse_args()
@@ -174,10 +178,46 @@ def oracle_sample(name, series=None, rank=0, rows_per_map=20):
     return updates / t_step, t_step, sample
 
 
+def reference_proposer(args):
+    """Reference arm of the proposer workload: the oracle's full exact Hough (the search the
+    proposer prunes) on k rows of the n = 5 map of the first held-out batch, extrapolated."""
+    from oracle import gfh_oracle as O
+    from paper_1810_09784_gb300 import proposer as PR
+    from paper_1810_09784_gb300 import synth
+    spec = PR.ProposerSpec()
+    s = 100011 + 30
+    smp = PR.draw(spec, [s])
+    fi, bj = synth.hashed_peaklist(spec.seed, s, spec.n_fft, spec.bin_lo, spec.bin_hi,
+                                   spec.p_noise24, int(smp.p_track24[0]), smp.tracks[0])
+    o = O.make_grid(O.Grid(**{k: v for k, v in spec.grid_fields(5.0).items() if k != "list"}))
+    vals = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        rows = 0
+        while time.perf_counter() - t0 < 2.0 and rows < o.n_k:
+            O.hough_row(o, fi, bj, rows)
+            rows += 1
+        if i >= args.warmup:
+            vals.append(fi.size * rows / (time.perf_counter() - t0))
+    value = float(np.mean(vals))
+    sample = f"oracle full exact Hough, k rows of one n = 5 held-out map ({fi.size} peaks), 2 s per step, numpy, 1 thread"
+    print(json.dumps({"impl": "reference", "metric": "Hough updates/s (peaks x k-bins), full-search equivalent",
+                      "value": value, "unit": "updates/s", "n_gpus": args.gpus, "steps": args.steps,
+                      "warmup": args.warmup, "ms_per_step": 2000.0, "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "int32 counts, fp64 grid",
+                      "data": "synthetic", "config": {"workload": "proposer (full exact search on the CPU)"},
+                      "cpu_baseline": {"value": value, "unit": "updates/s", "cores": 1, "kind": "oracle",
+                                       "sample": sample},
+                      "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0,
+                              "d2h_bytes_per_step": 0}}), flush=True)
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
+    if args.workload == "proposer":
+        return reference_proposer(args)
     spec, pm, grids = workload(args.workload, 0)
     x = spec.series()
     vals, times = [], []
@@ -552,12 +592,176 @@ def run_gpu_lists(args):
     ctx.close()
 
 
+def run_proposer(args):
+    """Learned proposer + exact Hough.  The network is trained first (untimed, on the GPU by the
+    library's kernels), tau is chosen on validation maps as the largest threshold whose recall is
+    at least 0.995, and recall is then measured on the held-out maps.  A step is one batch of 51
+    held-out maps (one per braking index): the plain full exact Hough of all 51 maps, and the
+    pruned search (images, network, proposals, exact Hough on the top 32 coarse tiles, full search
+    of the maps above tau) on the same resident peak lists; both are timed with CUDA events."""
+    import torch
+
+    from paper_1810_09784_gb300 import build as _build
+    from paper_1810_09784_gb300 import gfh
+    from paper_1810_09784_gb300 import proposer as PR
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    _build.build()
+    stream = torch.cuda.Stream()
+    ctx = gfh.Context(local, stream)
+    spec = PR.ProposerSpec()
+    nl = len(PR.N_GRID)
+    held0 = 100011 + 51 * 400 * rank          # held-out maps of this rank (multiples of 51)
+    val0 = 200022 + 51 * 400 * rank
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        net = gfh.Cnn(ctx, 256, seed=1)
+        t0 = time.perf_counter()
+        losses = PR.train_default(ctx, net, spec, epochs=args.epochs)
+        torch.cuda.synchronize()
+        t_train = time.perf_counter() - t0
+        bank = PR.HoughBank(ctx, spec)
+        val = PR.evaluate(ctx, net, spec, val0, 51 * 40, bank)
+        taus = [0.01, 0.02, 0.03, 0.05, 0.075, 0.1, 0.15, 0.2, 0.3]
+        ok = [t for t in taus if PR.summarize(val, t)["recall"] >= 0.995]
+        tau = max(ok) if ok else 0.0
+        t0 = time.perf_counter()
+        rec = PR.evaluate(ctx, net, spec, held0, args.eval_maps, bank)
+        t_eval = time.perf_counter() - t0
+        summ = PR.summarize(rec, tau)
+        search = PR.PrunedSearch(ctx, net, bank, tau)
+        # timed steps: each a new batch of held-out maps, peak lists resident before timing
+        t_full, t_pr, t_fwd, upd, fb = [], [], [], 0, 0
+        a, b, c, d = ev(), ev(), ev(), ev()
+        sampler = ClockSampler(local)
+        with sampler:
+            for st in range(args.warmup + args.steps):
+                smp = PR.draw(spec, np.arange(held0 + nl * st, held0 + nl * (st + 1)))
+                bank.load_peaks(smp)
+                torch.cuda.synchronize()
+                a.record(stream)
+                bank.full()
+                b.record(stream)
+                torch.cuda.synchronize()
+                c.record(stream)
+                nfb = search.run()
+                d.record(stream)
+                torch.cuda.synchronize()
+                f0_, f1_ = ev(), ev()
+                f0_.record(stream)
+                search.propose()
+                f1_.record(stream)
+                torch.cuda.synchronize()
+                if st >= args.warmup:
+                    t_full.append(a.elapsed_time(b))
+                    t_pr.append(c.elapsed_time(d))
+                    t_fwd.append(f0_.elapsed_time(f1_))
+                    upd += bank.updates()
+                    fb += nfb
+        clocks = sampler.summary()
+        # end to end through the API: peak lists from pinned host memory, candidates to the host
+        fi_h = bank.fft_c.cpu().pin_memory()
+        bj_h = bank.bin_c.cpu().pin_memory()
+        cand_h = [torch.empty_like(x, device="cpu").pin_memory() for x in bank.cands]
+        torch.cuda.synchronize()
+        t_e2e = []
+        for st in range(max(2, args.steps)):
+            c.record(stream)
+            bank.fft_c.copy_(fi_h, non_blocking=True)
+            bank.bin_c.copy_(bj_h, non_blocking=True)
+            search.run()
+            for x, h in zip(bank.cands, cand_h):
+                h.copy_(x, non_blocking=True)
+            d.record(stream)
+            torch.cuda.synchronize()
+            t_e2e.append(c.elapsed_time(d))
+    ms_full = float(np.sum(t_full)) / args.steps
+    ms_pr = float(np.sum(t_pr)) / args.steps
+    ms_fwd = float(np.mean(t_fwd))
+    upd_step = upd / args.steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_pr], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t[0])
+    else:
+        ms_max = ms_pr
+    if rank != 0:
+        return
+    cpu = None
+    if not args.no_cpu_baseline:
+        from oracle import gfh_oracle as O
+        g = bank.grids[30]                                   # n = 5
+        o = O.make_grid(O.Grid(**{k: getattr(g, k) for k in ("n", "df", "bin_lo", "bin_hi", "n_fft",
+                                  "t_first", "t_hop", "t_obs", "n_k", "k_min", "dk", "f_max",
+                                  "ana_lo", "ana_hi", "band_hz")}))
+        o0, o1 = bank.offs_host[30], bank.offs_host[31]
+        fi = bank.fft_c[o0:o1].cpu().numpy().view(np.uint32)
+        bj = bank.bin_c[o0:o1].cpu().numpy().view(np.uint32)
+        t0 = time.perf_counter()
+        rows = 0
+        while time.perf_counter() - t0 < 10.0 and rows < o.n_k:
+            O.hough_row(o, fi, bj, rows)
+            rows += 1
+        dt = time.perf_counter() - t0
+        cpu = {"value": fi.size * rows / dt, "unit": "updates/s", "cores": 1, "kind": "oracle",
+               "sample": f"oracle Hough of {rows} k rows of the n = 5 map of one held-out batch "
+                         f"({fi.size} peaks), numpy, 1 thread"}
+    flops_img = 2.0 * (65536 * 32 * 18 + 16384 * 32 * 288 + 16384 * 64 * 288 + 4096 * 64 * 576 * 2
+                       + 64 * 64 * 192)
+    fwd_tflops = flops_img * nl / (ms_fwd * 1e-3) / 1e12
+    bf16_peak = PEAKS.get("bf16_tflops")
+    line = {
+        "metric": "Hough updates/s (peaks x k-bins), full-search equivalent",
+        "value": world * upd_step / (ms_max * 1e-3), "unit": "updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32 counts; bf16 network, fp32 accumulate",
+        "data": "synthetic (statistical peakmap model, hashed per cell)",
+        "config": {"workload": "proposer: 51 maps per step (n = 2.0..7.0), plain_small-shaped "
+                               "(1799 FFTs, 100-400 Hz, 500 k rows), half with one power-law "
+                               "injection (SNR 2-8); top 32 of 64 x 64 coarse tiles, full search "
+                               "of maps with resid > tau",
+                   "n_sel": 32, "tau": tau, "recall": summ["recall"], "agreement": summ["agreement"],
+                   "held_out_maps": summ["maps"], "injected": summ["injected"],
+                   "detected_full": summ["det_full"], "detected_kept": summ["det_kept"],
+                   "fallback_frac": summ["fallback_frac"], "truth_in_top32": summ["truth_in_top"],
+                   "fallback_frac_timed": fb / (nl * args.steps),
+                   "updates_per_step": upd_step, "train_maps": 100000 * args.epochs,
+                   "train_s": round(t_train, 1), "final_loss": float(np.mean(losses[-20:])),
+                   "eval_s": round(t_eval, 1),
+                   "l2": "inputs larger than L2 (9.8 GB of maps written by the full search per step)"},
+        "speedup_vs_full_exact": ms_full / ms_pr,
+        "ms_full_exact_per_step": ms_full, "ms_pruned_per_step": ms_pr,
+        "roofline": {"bound": "tensor", "kernel": "network forward (k_conv1_fwd .. k_head_fwd)",
+                     "achieved": fwd_tflops, "peak": bf16_peak,
+                     "unit": "TFLOP/s", "frac": fwd_tflops / bf16_peak if bf16_peak else None,
+                     "peak_source": "measured cuBLAS bf16 (burst)" if bf16_peak else "none",
+                     "algorithmic": f"{flops_img / 1e9:.3f} GFLOP per image", "traffic": None,
+                     "ms_forward_51_maps": ms_fwd},
+        "e2e": {"value": world * upd_step / (float(np.mean(t_e2e)) * 1e-3), "unit": "updates/s",
+                "h2d_bytes_per_step": int(bank.fft_c.numel() * 8),
+                "d2h_bytes_per_step": int(sum(x.numel() for x in bank.cands)),
+                "ms_per_step": float(np.mean(t_e2e))},
+        # per step: full search 4 kernels; pruned: 2 image + 7 network + 1 proposal + 5 Hough
+        # kernels, and 4 per map searched in full
+        "gpu_launches": args.steps * (4 + 15) + 4 * fb, "clocks": clocks}
+    if cpu:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "uneven":
         run_gpu_lists(args)
+    elif args.workload == "proposer":
+        run_proposer(args)
     else:
         run_gpu(args)
 

@@ -248,6 +248,111 @@ int gfh_hough(gfh_ctx* ctx, const uint32_t* d_fft_idx, const uint32_t* d_bin, in
 int gfh_select(gfh_ctx* ctx, const int32_t* d_map, const gfh_grid* g, gfh_candidate* d_cands,
                gfh_map_stats* d_stats);
 
+/* ---- statistical peakmaps and the learned tile proposer ------------------------------------------
+ *
+ * The paper proposes machine learning for future work (Sec. VIII); here a small convolutional
+ * network ranks coarse (x0, k) tiles so that the exact Hough (above) can run on the best tiles only.
+ * It never replaces the exact Hough: candidates always come from exact counts.
+ *
+ * Statistical peakmap model (training and evaluation data): cell (FFT i, bin j) of sample s is a
+ * peak when u0(i, j) < p_noise24, or when j = track[i] and u1(i, j) < p_track24, where the 24-bit
+ * uniforms u_stream(i, j) come from the splitmix64 finaliser mix(z) (Steele, Lea, Flood 2014):
+ *   key = mix(seed ^ (s * 0xD1B54A32D192ED03) ^ (stream << 56)),  u = mix(key ^ (i << 32 | j)) >> 40.
+ * p_*24 are probabilities times 2^24; track[i] is the bin of the injected power law in FFT i, or -1.
+ */
+
+/* Peak list (sorted by bin, then FFT) of sample `sample` for bins bin_lo..bin_hi; d_track has n_fft
+ * entries or is NULL.  Synchronises; GFH_ERR_SIZE when the peaks exceed cap (count in *h_n_peaks). */
+int gfh_synth_peaks(gfh_ctx* ctx, uint64_t seed, int64_t sample, int32_t n_fft, int32_t bin_lo,
+                    int32_t bin_hi, uint32_t p_noise24, uint32_t p_track24, const int32_t* d_track,
+                    uint32_t* d_fft_idx, uint32_t* d_bin, int64_t cap, int64_t* h_n_peaks);
+
+/* Images of samples sample0 .. sample0 + batch - 1, bf16 [batch][256][256][2] (NHWC): pixel (tb, fb)
+ * counts the peaks of FFTs [tb n_fft/256, (tb+1) n_fft/256) and bins bin_lo + [fb nb/256,
+ * (fb+1) nb/256) (nb = bin_hi - bin_lo + 1 >= 256, n_fft >= 256); channel 0 = log(1 + count),
+ * channel 1 = d_nplane[b].  d_tracks: [batch][n_fft]; d_p_track24: [batch]. */
+int gfh_synth_images(gfh_ctx* ctx, uint64_t seed, int64_t sample0, int32_t batch, int32_t n_fft,
+                     int32_t bin_lo, int32_t bin_hi, uint32_t p_noise24,
+                     const uint32_t* d_p_track24, const int32_t* d_tracks, const float* d_nplane,
+                     void* d_images);
+
+/* The same images from peak lists: list l of `peaks` (each sorted by bin) into image l of d_images
+ * [n_lists][256][256][2]; all maps share the band bin_lo..bin_hi and n_fft FFTs; d_nplane [n_lists].
+ * Peaks outside the band are skipped; an FFT index >= n_fft sets the input flag (gfh_check).
+ * Asynchronous. */
+int gfh_peaks_to_images(gfh_ctx* ctx, const gfh_peaks* peaks, int32_t n_fft, int32_t bin_lo,
+                        int32_t bin_hi, const float* d_nplane, void* d_images);
+
+/*
+ * The network (layer list in csrc/gfh_cnn.cu): input bf16 [B][256][256][2]; output 4097 logits per
+ * image.  Class d * 64 + xt: a track starts (t = t0) in x0 tile xt (64 equal f0 ranges of the
+ * analysis band, = 4 image columns when the image band is the analysis band) and drifts, over the
+ * observation, between d K/64 and (d + 1) K/64 bins, K the map's k rows; a track on k row r
+ * drifts r (f0 / f_max)^n bins (one x0 column per k row per t_obs with the default k step; one
+ * column spans (f / f_max)^n bins, Eq. transform).  Class 4096 = no signal.
+ * Parameters are one fp32 vector (gfh_cnn_param_count entries); the layout is fixed: for each 3x3
+ * layer l = 1..5 its weights [cout][3][3][cin] then bias [cout]; the head [64][3][64] and bias [64];
+ * the no-signal bias.  Weights start He-uniform from `seed`; AdamW (beta 0.9, 0.999, eps 1e-8).
+ * All device memory (weights, optimiser state, activations for max_batch) is owned by the network.
+ */
+typedef struct gfh_cnn gfh_cnn;
+int gfh_cnn_create(gfh_ctx* ctx, int32_t max_batch, uint64_t seed, gfh_cnn** out);
+int gfh_cnn_destroy(gfh_cnn* net);
+int64_t gfh_cnn_param_count(const gfh_cnn* net);
+/* Host copies of the parameters and of the last gradients (either pointer may be NULL); sync. */
+int gfh_cnn_get_params(gfh_cnn* net, float* h_params, float* h_grads);
+/* Replace the parameters (and reset the optimiser state); sync. */
+int gfh_cnn_set_params(gfh_cnn* net, const float* h_params);
+/* Logits [batch][4097] fp32 into d_logits (may be NULL: kept inside). */
+int gfh_cnn_forward(gfh_cnn* net, const void* d_images, int32_t batch, float* d_logits);
+/* Gradients of the mean softmax cross-entropy for labels d_labels [batch] (int32 class); *h_loss =
+ * mean loss (sync when h_loss is not NULL). */
+int gfh_cnn_gradients(gfh_cnn* net, const void* d_images, const int32_t* d_labels, int32_t batch,
+                      float* h_loss);
+/* gfh_cnn_gradients followed by one AdamW step. */
+int gfh_cnn_train_step(gfh_cnn* net, const void* d_images, const int32_t* d_labels, int32_t batch,
+                       float lr, float weight_decay, float* h_loss);
+
+/*
+ * Coarse-tile proposals from logits [batch][4097]: p = softmax(logits); class (d, xt) spreads p
+ * evenly over k tiles kt in [floor(d gb), max(lo, ceil((d + 1) ga) - 1)] (both clamped to 63),
+ * with d_gain [batch][64][2] = (ga, gb) = ((f_max / f_a)^n, (f_max / f_b)^n) for x0 tile xt over
+ * [f_a, f_b).  Writes the k best coarse tiles kt * 64 + xt per map to d_top [batch][k] (score
+ * descending, ties to the lower id; NaN scores rank last) and d_resid [batch] = max(0, 1 -
+ * p(no signal) - their score sum): the probability the proposal misses a track.  Asynchronous.
+ */
+int gfh_propose_tiles(gfh_ctx* ctx, const float* d_logits, int32_t batch, const float* d_gain,
+                      int32_t k, int32_t* d_top, float* d_resid);
+
+/*
+ * One 3x3 layer alone (tests): mode 0 forward out = relu(conv(in) + bias) into d_res (bf16 NHWC);
+ * mode 1 input gradient into d_res (bf16) from d_dout masked by d_out > 0; mode 2 weight gradient
+ * added into d_res (fp32 [cout][3][3][cin]) and bias gradient added into d_db.  (cin, cout, stride)
+ * is one of (32, 32, 2), (32, 64, 1), (64, 64, 2), (64, 64, 1); h = input height = width.
+ */
+int gfh_conv3x3(gfh_ctx* ctx, int32_t mode, int32_t cin, int32_t cout, int32_t stride,
+                int32_t batch, int32_t h, const void* d_in, const void* d_w, const float* d_bias,
+                const void* d_out, const void* d_dout, void* d_res, float* d_db);
+
+/*
+ * Exact Hough restricted to coarse tiles.  Each map of the plan is split into coarse_k x coarse_x
+ * coarse tiles: k tile kt holds the rows r with floor(r coarse_k / K) = kt; x0 tile xt holds the
+ * analysis columns whose centre f0 satisfies floor((f0 - ana_lo) / (ana_hi - ana_lo) * coarse_x) =
+ * xt (clamped to [0, coarse_x - 1]); the coarse tile id is kt * coarse_x + xt.
+ * gfh_plan_set_coarse builds, on the host, the plan's fine tiles (the plan's tile shape) that cover
+ * every coarse tile, column ranges widened to multiples of 4; it must follow gfh_plan_create and may
+ * be called again (an autotuned plan rebuilds them itself).  max_sel bounds n_sel below.
+ * gfh_plan_execute_tiles computes the cells of the coarse tiles listed in d_coarse [n_maps][n_sel]
+ * (device; ids outside [0, coarse_k coarse_x), e.g. -1, select nothing) exactly as gfh_plan_execute
+ * does, and writes no other cell.  Candidates are the best computed cell of each band (count -1
+ * where no cell of the band was computed).  cr and the statistics come from sums over the computed
+ * cells only (a cell computed twice counts twice) with the map's full cell count: they are not
+ * comparable with those of gfh_plan_execute.  Asynchronous, allocation-free, capturable.
+ */
+int gfh_plan_set_coarse(gfh_plan* plan, int32_t coarse_k, int32_t coarse_x, int32_t max_sel);
+int gfh_plan_execute_tiles(gfh_plan* plan, const gfh_peaks* peaks, const int32_t* d_coarse,
+                           int32_t n_sel);
+
 /* ---- allocation-free entry point -------------------------------------------------------------
  *
  * The paper has no counterpart to this function: it is a service for callers that cannot

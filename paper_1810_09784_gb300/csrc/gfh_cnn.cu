@@ -1,0 +1,1038 @@
+// Learned tile proposer: a small convolutional network that ranks coarse (x0, k) tiles of a Hough
+// map from an image of the peakmap, so that the exact Hough can run on the top tiles only.  The
+// paper names machine learning as future work (Sec. VIII); the network here is a search aid, never a
+// detection statistic: every candidate still comes from the exact Hough.
+//
+// Architecture (bf16 activations and weights, fp32 accumulation, NHWC layout):
+//   input  [B][256 t][256 f][2]   log(1 + peak count) per (t, f) cell and a constant (n - 2) / 5
+//   L1 3x3  2 -> 32, stride 1, ReLU       (direct convolution, CUDA cores)
+//   L2 3x3 32 -> 32, stride 2, ReLU       (implicit GEMM on mma.sync bf16 tensor cores)
+//   L3 3x3 32 -> 64, stride 1, ReLU
+//   L4 3x3 64 -> 64, stride 2, ReLU
+//   L5 3x3 64 -> 64, stride 1, ReLU       -> [B][64 t][64 f][64]
+//   mean over t                           -> [B][64 f][64]
+//   head: 1-D conv over f, width 3, 64 -> 64 k tiles  -> logits[b][kt * 64 + f], plus one
+//   "no signal" logit: 4097 classes, softmax cross-entropy.
+// The gradient of every layer is computed by hand-written kernels (dgrad and wgrad of L2-L5 on
+// tensor cores, L1 and the head on CUDA cores); AdamW updates fp32 master weights and refreshes the
+// bf16 copies.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "gfh_internal.h"
+
+namespace {
+
+constexpr int kImg = 256;
+constexpr int kTiles = 64;
+constexpr int kClasses = kTiles * kTiles + 1;
+
+// ---- parameter layout (flat fp32 vector) --------------------------------------------------------
+struct Layout {
+  size_t w[5], b[5], wh, bh, bnull, total;
+};
+constexpr int kCin[5] = {2, 32, 32, 64, 64};
+constexpr int kCout[5] = {32, 32, 64, 64, 64};
+constexpr int kStride[5] = {1, 2, 1, 2, 1};
+
+Layout make_layout() {
+  Layout L{};
+  size_t o = 0;
+  for (int l = 0; l < 5; ++l) {
+    L.w[l] = o; o += (size_t)kCout[l] * 9 * kCin[l];
+    L.b[l] = o; o += kCout[l];
+  }
+  L.wh = o; o += (size_t)kTiles * 3 * 64;
+  L.bh = o; o += kTiles;
+  L.bnull = o; o += 1;
+  L.total = o;
+  return L;
+}
+
+// Channel 0 of a pixel holding `count` peaks: bf16(float(log(1 + count))), log taken in double.
+__device__ __forceinline__ uint32_t pixel_word(uint32_t count, float nplane) {
+  const __nv_bfloat16 a = __float2bfloat16_rn((float)log1p((double)count));
+  const __nv_bfloat16 b = __float2bfloat16_rn(nplane);
+  return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
+// Image of sample b: pixel (tb, fb) counts the peaks in FFTs [tb n_fft/256, (tb+1) n_fft/256) and
+// bins bin_lo + [fb nb/256, (fb+1) nb/256); channel 0 = log(1 + count), channel 1 = nplane[b].
+__global__ void k_synth_images(uint64_t seed, int64_t sample0, int n_fft, int bin_lo, int nb,
+                               uint32_t p_noise24, const uint32_t* __restrict__ p_track24,
+                               const int32_t* __restrict__ tracks, const float* __restrict__ nplane,
+                               uint32_t* __restrict__ img) {
+  const int b = blockIdx.y;
+  const int pix = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pix >= kImg * kImg) return;
+  const int tb = pix / kImg, fb = pix % kImg;
+  const int i0 = (int)((int64_t)tb * n_fft / kImg), i1 = (int)((int64_t)(tb + 1) * n_fft / kImg);
+  const int j0 = bin_lo + (int)((int64_t)fb * nb / kImg), j1 = bin_lo + (int)((int64_t)(fb + 1) * nb / kImg);
+  const uint64_t sample = (uint64_t)(sample0 + b);
+  const int32_t* tr = tracks + (int64_t)b * n_fft;
+  const uint32_t pt = p_track24[b];
+  uint32_t cnt = 0;
+  for (int i = i0; i < i1; ++i) {
+    const int tbin = tr[i];
+    for (int j = j0; j < j1; ++j)
+      cnt += gfh_synth_peak(seed, sample, (uint32_t)i, (uint32_t)j, p_noise24, tbin, pt);
+  }
+  img[(int64_t)b * kImg * kImg + pix] = pixel_word(cnt, nplane[b]);
+}
+
+// Counts peaks per pixel: list l of the peak lists into image l (one 32-bit word per pixel,
+// zeroed before).
+__global__ void k_image_count(const uint32_t* __restrict__ fft_idx, const uint32_t* __restrict__ bin,
+                              const int64_t* __restrict__ offsets, int n_fft, int bin_lo, int nb,
+                              uint32_t* __restrict__ img, unsigned int* flag) {
+  const int l = blockIdx.y;
+  uint32_t* im = img + (int64_t)l * kImg * kImg;
+  const int64_t p1 = offsets[l + 1];
+  for (int64_t p = offsets[l] + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < p1;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t i = fft_idx[p];
+    const int64_t jl = (int64_t)bin[p] - bin_lo;
+    if (i >= (uint32_t)n_fft) { atomicOr(flag, GFH_FLAG_FFT_RANGE); continue; }
+    if (jl < 0 || jl >= nb) continue;
+    // pixel whose range [tb N / 256, (tb + 1) N / 256) holds i: tb = (256 (i + 1) - 1) / N
+    const int tb = (int)(((int64_t)kImg * (i + 1) - 1) / n_fft);
+    const int fb = (int)(((int64_t)kImg * (jl + 1) - 1) / nb);
+    atomicAdd(im + tb * kImg + fb, 1u);
+  }
+}
+
+__global__ void k_image_finish(uint32_t* __restrict__ img, const float* __restrict__ nplane) {
+  const int pix = blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t* im = img + (int64_t)blockIdx.y * kImg * kImg;
+  if (pix < kImg * kImg) im[pix] = pixel_word(im[pix], nplane[blockIdx.y]);
+}
+
+// Tile proposals of one map per block.  The logits give p(d, xt) (softmax over the 4096 + 1
+// classes): drift class d, x0 tile xt.  Drift class d holds tracks whose drift over the
+// observation, in units of K / 64 bins, lies in [d, d + 1); on x0 tile xt (f0 in [f_a, f_b)) that
+// is k tiles [floor(d gb), ceil((d + 1) ga) - 1] with ga = (f_max / f_a)^n, gb = (f_max / f_b)^n,
+// since one k row drifts (f0 / f_max)^n bins.  Each class spreads its probability evenly over its
+// k tiles; the k best tiles (ties to the lower id kt * 64 + xt) go to top, and resid = 1 - p(null)
+// - their score sum (at least 0).
+__global__ void k_propose(const float* __restrict__ logits, const float* __restrict__ gain, int k,
+                          int32_t* __restrict__ top, float* __restrict__ resid) {
+  constexpr int NT = 256, NCT = kTiles * kTiles, PER = NCT / NT;
+  __shared__ float pr[NCT];                // p(d, xt) at d * 64 + xt
+  __shared__ float sc[NCT];                // score of coarse tile kt * 64 + xt
+  __shared__ unsigned char taken[NCT];
+  __shared__ float ga[kTiles], gb[kTiles];
+  __shared__ float rv[NT / 32];
+  __shared__ int ri[NT / 32];
+  __shared__ float red[NT];
+  const float* l = logits + (int64_t)blockIdx.x * kClasses;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid < kTiles) {
+    ga[tid] = gain[((int64_t)blockIdx.x * kTiles + tid) * 2];
+    gb[tid] = gain[((int64_t)blockIdx.x * kTiles + tid) * 2 + 1];
+  }
+  float mx = -INFINITY;
+  for (int c = tid; c < kClasses; c += NT) mx = fmaxf(mx, l[c]);
+  red[tid] = mx;
+  __syncthreads();
+  for (int s = NT / 2; s > 0; s >>= 1) {
+    if (tid < s) red[tid] = fmaxf(red[tid], red[tid + s]);
+    __syncthreads();
+  }
+  mx = red[0];
+  __syncthreads();
+  float sum = 0.f;
+  for (int c = tid; c < kClasses; c += NT) sum += expf(l[c] - mx);
+  red[tid] = sum;
+  __syncthreads();
+  for (int s = NT / 2; s > 0; s >>= 1) {
+    if (tid < s) red[tid] += red[tid + s];
+    __syncthreads();
+  }
+  const float lse = mx + logf(red[0]);
+  for (int c = tid; c < NCT; c += NT) { pr[c] = expf(l[c] - lse); taken[c] = 0; }
+  __syncthreads();
+  for (int c = tid; c < NCT; c += NT) {
+    const int kt = c / kTiles, xt = c % kTiles;
+    float s = 0.f;
+    for (int d = 0; d < kTiles; ++d) {
+      const int lo = min(kTiles - 1, (int)floorf((float)d * gb[xt]));
+      const int hi = min(kTiles - 1, max(lo, (int)ceilf((float)(d + 1) * ga[xt]) - 1));
+      if (kt >= lo && kt <= hi) s += pr[d * kTiles + xt] / (float)(hi - lo + 1);
+    }
+    sc[c] = isnan(s) ? -INFINITY : s;
+  }
+  __syncthreads();
+  float picked = 0.f;
+  for (int q = 0; q < k; ++q) {
+    float bv = 0.f;
+    int bi = -1;
+    for (int e = 0; e < PER; ++e) {
+      const int c = e * NT + tid;
+      if (taken[c]) continue;
+      if (bi < 0 || sc[c] > bv || (sc[c] == bv && c < bi)) { bv = sc[c]; bi = c; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (oi >= 0 && (bi < 0 || ov > bv || (ov == bv && oi < bi))) { bv = ov; bi = oi; }
+    }
+    if (lane == 0) { rv[warp] = bv; ri[warp] = bi; }
+    __syncthreads();
+    if (tid == 0) {
+      float b2 = rv[0];
+      int i2 = ri[0];
+      for (int w = 1; w < NT / 32; ++w)
+        if (ri[w] >= 0 && (i2 < 0 || rv[w] > b2 || (rv[w] == b2 && ri[w] < i2))) { b2 = rv[w]; i2 = ri[w]; }
+      top[(int64_t)blockIdx.x * k + q] = i2;
+      taken[i2] = 1;
+      picked += fmaxf(b2, 0.f);
+    }
+    __syncthreads();
+  }
+  if (tid == 0) resid[blockIdx.x] = fmaxf(0.f, 1.f - expf(l[kClasses - 1] - lse) - picked);
+}
+
+// ---- tensor-core helpers --------------------------------------------------------------------------
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t ld_u32(const __nv_bfloat16* p) {
+  return *reinterpret_cast<const uint32_t*>(p);
+}
+
+// Keeps each bf16 half of g where the matching half of the post-ReLU activation is positive.
+__device__ __forceinline__ uint32_t relu_mask(uint32_t g, uint32_t act) {
+  const uint32_t lo = ((act & 0xffffu) != 0u && !(act & 0x8000u)) ? 0xffffu : 0u;
+  const uint32_t hi = ((act >> 16) != 0u && !(act & 0x80000000u)) ? 0xffff0000u : 0u;
+  return g & (lo | hi);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// ---- L2-L5 forward: out[m][n] = relu(bias[n] + sum_k A[m][k] W[n][k]) -----------------------------
+// m = output pixel (b, y, x); k = tap * CIN + ci with tap = 3 dy + dx; A[m][k] = in[b][y S + dy - 1]
+// [x S + dx - 1][ci] (zero outside).  A warp computes 16 pixels x COUT.
+template <int CIN, int COUT, int S>
+__global__ void __launch_bounds__(256) k_conv_fwd(const __nv_bfloat16* __restrict__ in,
+                                                  const __nv_bfloat16* __restrict__ w,
+                                                  const float* __restrict__ bias,
+                                                  __nv_bfloat16* __restrict__ out, int B, int H) {
+  constexpr int K = 9 * CIN, KP = K + 8, NT8 = COUT / 8;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __nv_bfloat16* ws = reinterpret_cast<__nv_bfloat16*>(smem_raw);
+  for (int e = threadIdx.x; e < COUT * K; e += blockDim.x) ws[(e / K) * KP + e % K] = w[e];
+  __syncthreads();
+  const int Ho = H / S;
+  const int64_t M = (int64_t)B * Ho * Ho;
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  for (int64_t m0 = ((int64_t)blockIdx.x * 8 + (threadIdx.x >> 5)) * 16; m0 < M;
+       m0 += (int64_t)gridDim.x * 8 * 16) {
+    float acc[NT8][4];
+#pragma unroll
+    for (int n = 0; n < NT8; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+    int yy[2], xx[2], bb[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t m = m0 + g + 8 * h;
+      bb[h] = (int)(m / (Ho * Ho));
+      const int r = (int)(m % (Ho * Ho));
+      yy[h] = (r / Ho) * S - 1;
+      xx[h] = (r % Ho) * S - 1;
+    }
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      const __nv_bfloat16* p[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int yi = yy[h] + tap / 3, xi = xx[h] + tap % 3;
+        p[h] = (yi >= 0 && yi < H && xi >= 0 && xi < H)
+                   ? in + (((int64_t)bb[h] * H + yi) * H + xi) * CIN : nullptr;
+      }
+#pragma unroll
+      for (int cc = 0; cc < CIN / 16; ++cc) {
+        const int c = cc * 16 + 2 * t;
+        uint32_t a[4];
+        a[0] = p[0] ? ld_u32(p[0] + c) : 0u;
+        a[1] = p[1] ? ld_u32(p[1] + c) : 0u;
+        a[2] = p[0] ? ld_u32(p[0] + c + 8) : 0u;
+        a[3] = p[1] ? ld_u32(p[1] + c + 8) : 0u;
+        const int k0 = tap * CIN + cc * 16 + 2 * t;
+#pragma unroll
+        for (int n = 0; n < NT8; ++n) {
+          const __nv_bfloat16* wr = ws + (n * 8 + g) * KP + k0;
+          mma_bf16(acc[n], a, ld_u32(wr), ld_u32(wr + 8));
+        }
+      }
+    }
+#pragma unroll
+    for (int n = 0; n < NT8; ++n) {
+      const int col = n * 8 + 2 * t;
+      const float b0 = bias[col], b1 = bias[col + 1];
+      *reinterpret_cast<uint32_t*>(out + (m0 + g) * COUT + col) =
+          pack_bf16(fmaxf(acc[n][0] + b0, 0.f), fmaxf(acc[n][1] + b1, 0.f));
+      *reinterpret_cast<uint32_t*>(out + (m0 + g + 8) * COUT + col) =
+          pack_bf16(fmaxf(acc[n][2] + b0, 0.f), fmaxf(acc[n][3] + b1, 0.f));
+    }
+  }
+}
+
+// ---- L2-L5 input gradient: din[m][ci] = sum_{tap, co} G[src(m, tap)][co] W[co][tap][ci] ----------
+// m = input pixel (b, y, x); the output pixel that reads it through tap (dy, dx) is
+// ((y - dy + 1)/S, (x - dx + 1)/S) when that divides exactly and lies inside; G = dout masked by
+// the layer's ReLU.
+template <int CIN, int COUT, int S>
+__global__ void __launch_bounds__(256) k_conv_dgrad(const __nv_bfloat16* __restrict__ dout,
+                                                    const __nv_bfloat16* __restrict__ out,
+                                                    const __nv_bfloat16* __restrict__ w,
+                                                    __nv_bfloat16* __restrict__ din, int B, int H) {
+  constexpr int K = 9 * COUT, KP = K + 8, NT8 = CIN / 8;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __nv_bfloat16* wt = reinterpret_cast<__nv_bfloat16*>(smem_raw);   // [ci][tap * COUT + co]
+  for (int e = threadIdx.x; e < COUT * 9 * CIN; e += blockDim.x) {
+    const int co = e / (9 * CIN), r = e % (9 * CIN), tap = r / CIN, ci = r % CIN;
+    wt[ci * KP + tap * COUT + co] = w[e];
+  }
+  __syncthreads();
+  const int Ho = H / S;
+  const int64_t M = (int64_t)B * H * H;
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  for (int64_t m0 = ((int64_t)blockIdx.x * 8 + (threadIdx.x >> 5)) * 16; m0 < M;
+       m0 += (int64_t)gridDim.x * 8 * 16) {
+    float acc[NT8][4];
+#pragma unroll
+    for (int n = 0; n < NT8; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+    int yy[2], xx[2], bb[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t m = m0 + g + 8 * h;
+      bb[h] = (int)(m / (H * H));
+      const int r = (int)(m % (H * H));
+      yy[h] = r / H + 1;
+      xx[h] = r % H + 1;
+    }
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      int64_t o[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int ny = yy[h] - tap / 3, nx = xx[h] - tap % 3;   // = yo * S, xo * S
+        const bool ok = ny >= 0 && nx >= 0 && ny % S == 0 && nx % S == 0 && ny / S < Ho && nx / S < Ho;
+        o[h] = ok ? (((int64_t)bb[h] * Ho + ny / S) * Ho + nx / S) * COUT : -1;
+      }
+#pragma unroll
+      for (int cc = 0; cc < COUT / 16; ++cc) {
+        const int c = cc * 16 + 2 * t;
+        uint32_t a[4];
+        a[0] = o[0] >= 0 ? relu_mask(ld_u32(dout + o[0] + c), ld_u32(out + o[0] + c)) : 0u;
+        a[1] = o[1] >= 0 ? relu_mask(ld_u32(dout + o[1] + c), ld_u32(out + o[1] + c)) : 0u;
+        a[2] = o[0] >= 0 ? relu_mask(ld_u32(dout + o[0] + c + 8), ld_u32(out + o[0] + c + 8)) : 0u;
+        a[3] = o[1] >= 0 ? relu_mask(ld_u32(dout + o[1] + c + 8), ld_u32(out + o[1] + c + 8)) : 0u;
+        const int k0 = tap * COUT + cc * 16 + 2 * t;
+#pragma unroll
+        for (int n = 0; n < NT8; ++n) {
+          const __nv_bfloat16* wr = wt + (n * 8 + g) * KP + k0;
+          mma_bf16(acc[n], a, ld_u32(wr), ld_u32(wr + 8));
+        }
+      }
+    }
+#pragma unroll
+    for (int n = 0; n < NT8; ++n) {
+      const int col = n * 8 + 2 * t;
+      *reinterpret_cast<uint32_t*>(din + (m0 + g) * CIN + col) = pack_bf16(acc[n][0], acc[n][1]);
+      *reinterpret_cast<uint32_t*>(din + (m0 + g + 8) * CIN + col) = pack_bf16(acc[n][2], acc[n][3]);
+    }
+  }
+}
+
+// ---- L2-L5 weight gradient: dW[co][kc] += sum_p G[p][co] patch[p][kc] ---------------------------
+// A block owns 64 patch columns kc in [n0, n0 + 64) and a range of output pixels; both operands are
+// staged transposed (pixels contiguous) in shared memory, 64 pixels at a time, for mma.sync.  Pixel
+// coordinates of a chunk are decoded once into shared memory (32-bit: B (H/S)^2 < 2^31).
+template <int CIN, int COUT, int S>
+__global__ void __launch_bounds__(256) k_conv_wgrad(const __nv_bfloat16* __restrict__ dout,
+                                                    const __nv_bfloat16* __restrict__ out,
+                                                    const __nv_bfloat16* __restrict__ in,
+                                                    float* __restrict__ dw, int B, int H,
+                                                    int pix_per_block) {
+  constexpr int PC = 64, LD = PC + 8;
+  constexpr int MT = COUT / 16;            // m tiles of 16 output channels
+  __shared__ __align__(16) __nv_bfloat16 Gt[COUT][LD];
+  __shared__ __align__(16) __nv_bfloat16 Pt[64][LD];
+  __shared__ int pb[PC], py[PC], px[PC];   // image, first input row / column of the pixel's patch
+  const int Ho = H / S;
+  const int M = B * Ho * Ho;
+  const int n0 = blockIdx.y * 64;
+  const int p_begin = blockIdx.x * pix_per_block;
+  const int p_end = min(p_begin + pix_per_block, M);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  // warp -> (m tile, n half); with COUT = 32 only warps 0..3 compute
+  const int mt = warp % 4, nh = warp / 4;
+  const bool active = mt < MT;
+  float acc[4][4];
+#pragma unroll
+  for (int n = 0; n < 4; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+  for (int p0 = p_begin; p0 < p_end; p0 += PC) {
+    __syncthreads();
+    if (threadIdx.x < PC) {
+      const int p = p0 + threadIdx.x;
+      const int b = p / (Ho * Ho), r = p - b * (Ho * Ho), yo = r / Ho, xo = r - yo * Ho;
+      pb[threadIdx.x] = p < p_end ? b : -1;
+      py[threadIdx.x] = yo * S - 1;
+      px[threadIdx.x] = xo * S - 1;
+    }
+    for (int e = threadIdx.x; e < PC * COUT; e += blockDim.x) {
+      const int pl = e / COUT, co = e % COUT;
+      const int p = p0 + pl;
+      __nv_bfloat16 v = __float2bfloat16_rn(0.f);
+      if (p < p_end) {
+        const __nv_bfloat16 gv = dout[(int64_t)p * COUT + co], av = out[(int64_t)p * COUT + co];
+        v = __bfloat162float(av) > 0.f ? gv : __float2bfloat16_rn(0.f);
+      }
+      Gt[co][pl] = v;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < PC * 64; e += blockDim.x) {
+      const int pl = e >> 6, j = e & 63;
+      const int kc = n0 + j, tap = kc / CIN, ci = kc % CIN;
+      const int dy = tap / 3, dx = tap - 3 * dy;
+      const int b = pb[pl], yi = py[pl] + dy, xi = px[pl] + dx;
+      __nv_bfloat16 v = __float2bfloat16_rn(0.f);
+      if (b >= 0 && kc < 9 * CIN && yi >= 0 && yi < H && xi >= 0 && xi < H)
+        v = in[(((int64_t)b * H + yi) * H + xi) * CIN + ci];
+      Pt[j][pl] = v;
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll
+      for (int ks = 0; ks < PC / 16; ++ks) {
+        const int k = ks * 16 + 2 * t;
+        uint32_t a[4];
+        a[0] = ld_u32(&Gt[mt * 16 + g][k]);
+        a[1] = ld_u32(&Gt[mt * 16 + g + 8][k]);
+        a[2] = ld_u32(&Gt[mt * 16 + g][k + 8]);
+        a[3] = ld_u32(&Gt[mt * 16 + g + 8][k + 8]);
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+          const __nv_bfloat16* pr = &Pt[nh * 32 + n * 8 + g][k];
+          mma_bf16(acc[n], a, ld_u32(pr), ld_u32(pr + 8));
+        }
+      }
+    }
+  }
+  if (active) {
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+      const int kc = n0 + nh * 32 + n * 8 + 2 * t;
+      const int co = mt * 16 + g;
+      if (kc < 9 * CIN) {
+        atomicAdd(&dw[co * 9 * CIN + kc], acc[n][0]);
+        atomicAdd(&dw[(co + 8) * 9 * CIN + kc], acc[n][2]);
+      }
+      if (kc + 1 < 9 * CIN) {
+        atomicAdd(&dw[co * 9 * CIN + kc + 1], acc[n][1]);
+        atomicAdd(&dw[(co + 8) * 9 * CIN + kc + 1], acc[n][3]);
+      }
+    }
+  }
+}
+
+// Bias gradient of a ReLU layer: db[co] += sum_p G[p][co].
+__global__ void k_bias_grad(const __nv_bfloat16* __restrict__ dout,
+                            const __nv_bfloat16* __restrict__ out, float* __restrict__ db,
+                            int64_t M, int C) {
+  const int co = threadIdx.x % C, rows = blockDim.x / C;
+  float s = 0.f;
+  for (int64_t p = (int64_t)blockIdx.x * rows + threadIdx.x / C; p < M; p += (int64_t)gridDim.x * rows)
+    if (__bfloat162float(out[p * C + co]) > 0.f) s += __bfloat162float(dout[p * C + co]);
+  atomicAdd(&db[co], s);
+}
+
+// ---- L1 (2 input channels) on tensor cores: K = 9 taps x 2 channels = 18, padded to 32 ---------
+// k = 2 tap + ci, so one 32-bit A register holds both channels of one tap's pixel.  A warp computes
+// 16 pixels x 32 output channels (2 k-steps x 4 n-tiles).
+__global__ void __launch_bounds__(256) k_conv1_fwd(const __nv_bfloat16* __restrict__ in,
+                                                   const __nv_bfloat16* __restrict__ w,
+                                                   const float* __restrict__ bias,
+                                                   __nv_bfloat16* __restrict__ out, int B) {
+  constexpr int KP = 40;                   // 32 + 8 bf16 per output channel row
+  __shared__ __align__(16) __nv_bfloat16 ws[32 * KP];
+  for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+    const int co = e / 32, k = e % 32;
+    ws[co * KP + k] = k < 18 ? w[co * 18 + k] : __float2bfloat16_rn(0.f);
+  }
+  __syncthreads();
+  const int64_t M = (int64_t)B * kImg * kImg;
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  for (int64_t m0 = ((int64_t)blockIdx.x * 8 + (threadIdx.x >> 5)) * 16; m0 < M;
+       m0 += (int64_t)gridDim.x * 8 * 16) {
+    float acc[4][4];
+#pragma unroll
+    for (int n = 0; n < 4; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+    int yy[2], xx[2], bb[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t m = m0 + g + 8 * h;
+      bb[h] = (int)(m / (kImg * kImg));
+      const int r = (int)(m % (kImg * kImg));
+      yy[h] = r / kImg - 1;
+      xx[h] = r % kImg - 1;
+    }
+    // A value of tap `tap` for pixel half h (zero outside the image and for tap >= 9)
+    auto a_val = [&](int h, int tap) -> uint32_t {
+      if (tap >= 9) return 0u;
+      const int yi = yy[h] + tap / 3, xi = xx[h] + tap % 3;
+      if (yi < 0 || yi >= kImg || xi < 0 || xi >= kImg) return 0u;
+      return ld_u32(in + (((int64_t)bb[h] * kImg + yi) * kImg + xi) * 2);
+    };
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk) {
+      uint32_t a[4];
+      a[0] = a_val(0, kk * 8 + t);
+      a[1] = a_val(1, kk * 8 + t);
+      a[2] = a_val(0, kk * 8 + t + 4);
+      a[3] = a_val(1, kk * 8 + t + 4);
+      const int k0 = kk * 16 + 2 * t;
+#pragma unroll
+      for (int n = 0; n < 4; ++n) {
+        const __nv_bfloat16* wr = ws + (n * 8 + g) * KP + k0;
+        mma_bf16(acc[n], a, ld_u32(wr), ld_u32(wr + 8));
+      }
+    }
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+      const int col = n * 8 + 2 * t;
+      const float b0 = bias[col], b1 = bias[col + 1];
+      *reinterpret_cast<uint32_t*>(out + (m0 + g) * 32 + col) =
+          pack_bf16(fmaxf(acc[n][0] + b0, 0.f), fmaxf(acc[n][1] + b1, 0.f));
+      *reinterpret_cast<uint32_t*>(out + (m0 + g + 8) * 32 + col) =
+          pack_bf16(fmaxf(acc[n][2] + b0, 0.f), fmaxf(acc[n][3] + b1, 0.f));
+    }
+  }
+}
+
+// dW1[co][tap][ci] += sum_p G1[p][co] in[src(p, tap)][ci]; a block reduces a range of pixels for
+// all 576 weights (thread = (co, tap), both input channels).
+__global__ void k_conv1_wgrad(const __nv_bfloat16* __restrict__ dout,
+                              const __nv_bfloat16* __restrict__ out,
+                              const __nv_bfloat16* __restrict__ in, float* __restrict__ dw, int B,
+                              int pix_per_block) {
+  const int co = threadIdx.x / 9, tap = threadIdx.x % 9;   // 288 threads
+  const int64_t M = (int64_t)B * kImg * kImg;
+  const int64_t p0 = (int64_t)blockIdx.x * pix_per_block;
+  const int64_t p1 = p0 + pix_per_block < M ? p0 + pix_per_block : M;
+  float s0 = 0.f, s1 = 0.f;
+  for (int64_t p = p0; p < p1; ++p) {
+    const float a = __bfloat162float(out[p * 32 + co]);
+    if (!(a > 0.f)) continue;
+    const float gv = __bfloat162float(dout[p * 32 + co]);
+    const int b = (int)(p / (kImg * kImg)), r = (int)(p % (kImg * kImg));
+    const int yi = r / kImg + tap / 3 - 1, xi = r % kImg + tap % 3 - 1;
+    if (yi < 0 || yi >= kImg || xi < 0 || xi >= kImg) continue;
+    const __nv_bfloat16* q = in + (((int64_t)b * kImg + yi) * kImg + xi) * 2;
+    s0 += gv * __bfloat162float(q[0]);
+    s1 += gv * __bfloat162float(q[1]);
+  }
+  atomicAdd(&dw[co * 18 + tap * 2], s0);
+  atomicAdd(&dw[co * 18 + tap * 2 + 1], s1);
+}
+
+// ---- mean over t, head, loss --------------------------------------------------------------------
+// pooled[b][f][c] = mean_t a5[b][t][f][c]
+__global__ void k_pool(const __nv_bfloat16* __restrict__ a5, float* __restrict__ pooled, int B) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;   // (b, f, c)
+  if (e >= B * 64 * 64) return;
+  const int b = e / 4096, fc = e % 4096;
+  float s = 0.f;
+  for (int tt = 0; tt < 64; ++tt) s += __bfloat162float(a5[((int64_t)b * 64 + tt) * 4096 + fc]);
+  pooled[e] = s * (1.0f / 64.0f);
+}
+
+// logits[b][kt * 64 + f] = bh[kt] + sum_{d, c} wh[kt][d][c] pooled[b][f + d - 1][c]; logits[b][4096]
+// = bnull.  One block per image: pooled (zero-padded rows -1 and 64) in shared memory; a thread owns
+// one kt and 16 consecutive f, so each weight is loaded once for 16 products and each pooled value
+// once per (c, row) for up to 3 taps.
+__global__ void __launch_bounds__(256) k_head_fwd(const float* __restrict__ pooled,
+                                                  const float* __restrict__ wh,
+                                                  const float* __restrict__ bh,
+                                                  const float* __restrict__ bnull,
+                                                  float* __restrict__ logits) {
+  constexpr int LDP = 65;                  // padded row: rows differing in f fall in other banks
+  __shared__ float pp[66 * LDP];
+  const int b = blockIdx.x;
+  for (int e = threadIdx.x; e < 66 * 64; e += blockDim.x) {
+    const int row = e / 64, c = e % 64;
+    const int f = row - 1;
+    pp[row * LDP + c] = (f >= 0 && f < 64) ? pooled[((int64_t)b * 64 + f) * 64 + c] : 0.f;
+  }
+  __syncthreads();
+  const int kt = threadIdx.x >> 2, f0 = (threadIdx.x & 3) * 16;
+  float acc[16];
+  const float bias = bh[kt];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) acc[j] = bias;
+  const float* w = wh + kt * 192;
+  for (int c = 0; c < 64; ++c) {
+    const float w0 = w[c], w1 = w[64 + c], w2 = w[128 + c];
+    float v[18];
+#pragma unroll
+    for (int j = 0; j < 18; ++j) v[j] = pp[(f0 + j) * LDP + c];   // rows f0 .. f0 + 17 = f - 1 ..
+#pragma unroll
+    for (int j = 0; j < 16; ++j) acc[j] += w0 * v[j] + w1 * v[j + 1] + w2 * v[j + 2];
+  }
+  float* o = logits + (int64_t)b * kClasses + kt * 64 + f0;
+#pragma unroll
+  for (int j = 0; j < 16; ++j) o[j] = acc[j];
+  if (threadIdx.x == 0) logits[(int64_t)b * kClasses + kClasses - 1] = bnull[0];
+}
+
+// Softmax cross-entropy per sample (one block of 256 threads per sample): loss[b], and dlogits =
+// (softmax - onehot) / B.
+__global__ void k_softmax_ce(const float* __restrict__ logits, const int32_t* __restrict__ labels,
+                             float* __restrict__ dlogits, float* __restrict__ loss, int B) {
+  const int b = blockIdx.x;
+  const float* l = logits + (int64_t)b * kClasses;
+  __shared__ float red[256];
+  float mx = -INFINITY;
+  for (int c = threadIdx.x; c < kClasses; c += blockDim.x) mx = fmaxf(mx, l[c]);
+  red[threadIdx.x] = mx;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + s]);
+    __syncthreads();
+  }
+  mx = red[0];
+  __syncthreads();
+  float sum = 0.f;
+  for (int c = threadIdx.x; c < kClasses; c += blockDim.x) sum += expf(l[c] - mx);
+  red[threadIdx.x] = sum;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  const float lse = mx + logf(red[0]);
+  const int y = labels[b];
+  if (threadIdx.x == 0) loss[b] = lse - l[y];
+  if (dlogits)
+    for (int c = threadIdx.x; c < kClasses; c += blockDim.x)
+      dlogits[(int64_t)b * kClasses + c] = (expf(l[c] - lse) - (c == y ? 1.f : 0.f)) / (float)B;
+}
+
+// Head weight/bias gradients: one thread per (kt, d, c) weight, plus bias and null bias.
+__global__ void k_head_wgrad(const float* __restrict__ dlogits, const float* __restrict__ pooled,
+                             float* __restrict__ dwh, float* __restrict__ dbh,
+                             float* __restrict__ dbnull, int B) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < 64 * 3 * 64) {
+    const int kt = e / 192, d = (e / 64) % 3, c = e % 64;
+    float s = 0.f;
+    for (int b = 0; b < B; ++b)
+      for (int f = 0; f < 64; ++f) {
+        const int ff = f + d - 1;
+        if (ff < 0 || ff >= 64) continue;
+        s += dlogits[(int64_t)b * kClasses + kt * 64 + f] * pooled[((int64_t)b * 64 + ff) * 64 + c];
+      }
+    dwh[e] += s;
+  } else if (e < 64 * 3 * 64 + 64) {
+    const int kt = e - 64 * 3 * 64;
+    float s = 0.f;
+    for (int b = 0; b < B; ++b)
+      for (int f = 0; f < 64; ++f) s += dlogits[(int64_t)b * kClasses + kt * 64 + f];
+    dbh[kt] += s;
+  } else if (e == 64 * 3 * 64 + 64) {
+    float s = 0.f;
+    for (int b = 0; b < B; ++b) s += dlogits[(int64_t)b * kClasses + kClasses - 1];
+    dbnull[0] += s;
+  }
+}
+
+// d a5[b][t][f][c] = (1/64) sum_{kt, d} dlogits[b][kt * 64 + f - d + 1] wh[kt][d][c]  (same for all t)
+__global__ void k_head_dgrad(const float* __restrict__ dlogits, const float* __restrict__ wh,
+                             __nv_bfloat16* __restrict__ da5, int B) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;   // (b, f, c)
+  if (e >= B * 4096) return;
+  const int b = e / 4096, f = (e / 64) % 64, c = e % 64;
+  float s = 0.f;
+  for (int kt = 0; kt < 64; ++kt)
+    for (int d = 0; d < 3; ++d) {
+      const int fo = f - d + 1;
+      if (fo < 0 || fo >= 64) continue;
+      s += dlogits[(int64_t)b * kClasses + kt * 64 + fo] * wh[(kt * 3 + d) * 64 + c];
+    }
+  const __nv_bfloat16 v = __float2bfloat16_rn(s * (1.0f / 64.0f));
+  for (int tt = 0; tt < 64; ++tt) da5[((int64_t)b * 64 + tt) * 4096 + f * 64 + c] = v;
+}
+
+// AdamW on the fp32 master weights; refreshes the bf16 copies of L2-L5 (index map in bf16_of).
+__global__ void k_adamw(float* __restrict__ w, const float* __restrict__ gw, float* __restrict__ m,
+                        float* __restrict__ v, int64_t n, float lr, float b1, float b2, float eps,
+                        float wd, float c1, float c2) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = gw[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  w[i] -= lr * ((mi / c1) / (sqrtf(vi / c2) + eps) + wd * w[i]);
+}
+
+__global__ void k_to_bf16(const float* __restrict__ a, __nv_bfloat16* __restrict__ b, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = __float2bfloat16_rn(a[i]);
+}
+
+// ---- launch helpers -------------------------------------------------------------------------------
+
+template <int CIN, int COUT, int S>
+int conv_fwd(const __nv_bfloat16* in, const __nv_bfloat16* w, const float* bias,
+             __nv_bfloat16* out, int B, int H, int sms, cudaStream_t st) {
+  const size_t smem = (size_t)COUT * (9 * CIN + 8) * 2;
+  auto fn = k_conv_fwd<CIN, COUT, S>;
+  GFH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int64_t tiles = (int64_t)B * (H / S) * (H / S) / 16;
+  const int grid = (int)std::min<int64_t>((tiles + 7) / 8, (int64_t)sms * 8);
+  fn<<<grid, 256, smem, st>>>(in, w, bias, out, B, H);
+  GFH_CUDA_TRY(cudaGetLastError());
+  return GFH_OK;
+}
+
+template <int CIN, int COUT, int S>
+int conv_dgrad(const __nv_bfloat16* dout, const __nv_bfloat16* out, const __nv_bfloat16* w,
+               __nv_bfloat16* din, int B, int H, int sms, cudaStream_t st) {
+  const size_t smem = (size_t)CIN * (9 * COUT + 8) * 2;
+  auto fn = k_conv_dgrad<CIN, COUT, S>;
+  GFH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int64_t tiles = (int64_t)B * H * H / 16;
+  const int grid = (int)std::min<int64_t>((tiles + 7) / 8, (int64_t)sms * 8);
+  fn<<<grid, 256, smem, st>>>(dout, out, w, din, B, H);
+  GFH_CUDA_TRY(cudaGetLastError());
+  return GFH_OK;
+}
+
+template <int CIN, int COUT, int S>
+int conv_wgrad(const __nv_bfloat16* dout, const __nv_bfloat16* out, const __nv_bfloat16* in,
+               float* dw, float* db, int B, int H, int sms, cudaStream_t st) {
+  const int64_t M = (int64_t)B * (H / S) * (H / S);
+  if (M >= INT32_MAX) return GFH_ERR_SIZE;
+  const int ppb = 4096;
+  dim3 grid((unsigned)((M + ppb - 1) / ppb), (9 * CIN + 63) / 64);
+  k_conv_wgrad<CIN, COUT, S><<<grid, 256, 0, st>>>(dout, out, in, dw, B, H, ppb);
+  GFH_CUDA_TRY(cudaGetLastError());
+  k_bias_grad<<<sms * 2, 256, 0, st>>>(dout, out, db, M, COUT);
+  GFH_CUDA_TRY(cudaGetLastError());
+  return GFH_OK;
+}
+
+}  // namespace
+
+// ---- the network object -------------------------------------------------------------------------
+
+struct gfh_cnn {
+  gfh_ctx* ctx = nullptr;
+  int max_batch = 0;
+  Layout L{};
+  int64_t step = 0;
+  void* buf = nullptr;
+  float *w = nullptr, *gw = nullptr, *m = nullptr, *v = nullptr;   // fp32 params, grads, Adam
+  __nv_bfloat16* wb[5] = {};                                       // bf16 copies of W1..W5
+  __nv_bfloat16* act[6] = {};                                      // a0 (input copy) .. a5
+  __nv_bfloat16* dact[6] = {};                                     // d a1 .. d a5 (index 1..5)
+  float *pooled = nullptr, *logits = nullptr, *dlogits = nullptr, *loss = nullptr;
+};
+
+namespace {
+
+size_t act_elems(int l, int B) {   // activation l (0 = input) element count
+  static const int hw[6] = {256, 256, 128, 128, 64, 64};
+  static const int ch[6] = {2, 32, 32, 64, 64, 64};
+  return (size_t)B * hw[l] * hw[l] * ch[l];
+}
+
+void init_params(float* h, const Layout& L, uint64_t seed) {
+  std::memset(h, 0, L.total * sizeof(float));
+  uint64_t ctr = 0;
+  auto uni = [&]() {   // uniform in [-1, 1) from the same splitmix64 finaliser
+    return (double)(gfh_mix64(seed ^ (ctr++ * 0xD1B54A32D192ED03ull)) >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+  };
+  for (int l = 0; l < 5; ++l) {
+    const double bound = std::sqrt(6.0 / (9.0 * kCin[l]));   // He-uniform for ReLU
+    for (int e = 0; e < kCout[l] * 9 * kCin[l]; ++e) h[L.w[l] + e] = (float)(bound * uni());
+  }
+  const double bh = std::sqrt(3.0 / (3.0 * 64.0));
+  for (int e = 0; e < 64 * 3 * 64; ++e) h[L.wh + e] = (float)(bh * uni());
+}
+
+int refresh_bf16(gfh_cnn* n) {
+  for (int l = 0; l < 5; ++l) {
+    const int64_t cnt = (int64_t)kCout[l] * 9 * kCin[l];
+    k_to_bf16<<<(unsigned)((cnt + 255) / 256), 256, 0, n->ctx->stream>>>(n->w + n->L.w[l], n->wb[l], cnt);
+    GFH_CUDA_TRY(cudaGetLastError());
+  }
+  return GFH_OK;
+}
+
+int forward(gfh_cnn* n, const __nv_bfloat16* img, int B) {
+  cudaStream_t st = n->ctx->stream;
+  const int sms = n->ctx->num_sms;
+  const Layout& L = n->L;
+  const int64_t P1 = (int64_t)B * kImg * kImg;
+  {
+    const int grid = (int)std::min<int64_t>((P1 / 16 + 7) / 8, (int64_t)sms * 8);
+    k_conv1_fwd<<<grid, 256, 0, st>>>(img, n->wb[0], n->w + L.b[0], n->act[1], B);
+  }
+  GFH_CUDA_TRY(cudaGetLastError());
+  int rc = conv_fwd<32, 32, 2>(n->act[1], n->wb[1], n->w + L.b[1], n->act[2], B, 256, sms, st);
+  if (!rc) rc = conv_fwd<32, 64, 1>(n->act[2], n->wb[2], n->w + L.b[2], n->act[3], B, 128, sms, st);
+  if (!rc) rc = conv_fwd<64, 64, 2>(n->act[3], n->wb[3], n->w + L.b[3], n->act[4], B, 128, sms, st);
+  if (!rc) rc = conv_fwd<64, 64, 1>(n->act[4], n->wb[4], n->w + L.b[4], n->act[5], B, 64, sms, st);
+  if (rc) return rc;
+  k_pool<<<(B * 4096 + 255) / 256, 256, 0, st>>>(n->act[5], n->pooled, B);
+  k_head_fwd<<<B, 256, 0, st>>>(n->pooled, n->w + L.wh, n->w + L.bh, n->w + L.bnull, n->logits);
+  GFH_CUDA_TRY(cudaGetLastError());
+  return GFH_OK;
+}
+
+// Gradients of the mean loss into n->gw (zeroed first); per-sample losses in n->loss.
+int backward(gfh_cnn* n, const __nv_bfloat16* img, const int32_t* labels, int B) {
+  cudaStream_t st = n->ctx->stream;
+  const int sms = n->ctx->num_sms;
+  const Layout& L = n->L;
+  GFH_CUDA_TRY(cudaMemsetAsync(n->gw, 0, L.total * sizeof(float), st));
+  k_softmax_ce<<<B, 256, 0, st>>>(n->logits, labels, n->dlogits, n->loss, B);
+  k_head_wgrad<<<(64 * 3 * 64 + 65 + 255) / 256, 256, 0, st>>>(n->dlogits, n->pooled, n->gw + L.wh,
+                                                               n->gw + L.bh, n->gw + L.bnull, B);
+  k_head_dgrad<<<(B * 4096 + 255) / 256, 256, 0, st>>>(n->dlogits, n->w + L.wh, n->dact[5], B);
+  GFH_CUDA_TRY(cudaGetLastError());
+  int rc = conv_wgrad<64, 64, 1>(n->dact[5], n->act[5], n->act[4], n->gw + L.w[4], n->gw + L.b[4], B, 64, sms, st);
+  if (!rc) rc = conv_dgrad<64, 64, 1>(n->dact[5], n->act[5], n->wb[4], n->dact[4], B, 64, sms, st);
+  if (!rc) rc = conv_wgrad<64, 64, 2>(n->dact[4], n->act[4], n->act[3], n->gw + L.w[3], n->gw + L.b[3], B, 128, sms, st);
+  if (!rc) rc = conv_dgrad<64, 64, 2>(n->dact[4], n->act[4], n->wb[3], n->dact[3], B, 128, sms, st);
+  if (!rc) rc = conv_wgrad<32, 64, 1>(n->dact[3], n->act[3], n->act[2], n->gw + L.w[2], n->gw + L.b[2], B, 128, sms, st);
+  if (!rc) rc = conv_dgrad<32, 64, 1>(n->dact[3], n->act[3], n->wb[2], n->dact[2], B, 128, sms, st);
+  if (!rc) rc = conv_wgrad<32, 32, 2>(n->dact[2], n->act[2], n->act[1], n->gw + L.w[1], n->gw + L.b[1], B, 256, sms, st);
+  if (!rc) rc = conv_dgrad<32, 32, 2>(n->dact[2], n->act[2], n->wb[1], n->dact[1], B, 256, sms, st);
+  if (rc) return rc;
+  const int ppb = 2048;
+  const int64_t P1 = (int64_t)B * kImg * kImg;
+  k_conv1_wgrad<<<(unsigned)((P1 + ppb - 1) / ppb), 288, 0, st>>>(n->dact[1], n->act[1], img,
+                                                                  n->gw + L.w[0], B, ppb);
+  k_bias_grad<<<sms * 2, 256, 0, st>>>(n->dact[1], n->act[1], n->gw + L.b[0], P1, 32);
+  GFH_CUDA_TRY(cudaGetLastError());
+  return GFH_OK;
+}
+
+}  // namespace
+
+extern "C" int gfh_cnn_create(gfh_ctx* ctx, int32_t max_batch, uint64_t seed, gfh_cnn** out) {
+  if (!ctx || !out || max_batch < 1 || max_batch > 4096) return GFH_ERR_ARG;
+  *out = nullptr;
+  gfh_cnn* n = new (std::nothrow) gfh_cnn();
+  if (!n) return GFH_ERR_NOMEM;
+  n->ctx = ctx;
+  n->max_batch = max_batch;
+  n->L = make_layout();
+  const int B = max_batch;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off = (off + bytes + 255) / 256 * 256; return o; };
+  const size_t o_w = take(n->L.total * 4), o_gw = take(n->L.total * 4), o_m = take(n->L.total * 4),
+               o_v = take(n->L.total * 4);
+  size_t o_wb[5], o_act[6], o_dact[6];
+  for (int l = 0; l < 5; ++l) o_wb[l] = take((size_t)kCout[l] * 9 * kCin[l] * 2);
+  for (int l = 1; l < 6; ++l) { o_act[l] = take(act_elems(l, B) * 2); o_dact[l] = take(act_elems(l, B) * 2); }
+  const size_t o_pool = take((size_t)B * 4096 * 4), o_log = take((size_t)B * kClasses * 4),
+               o_dlog = take((size_t)B * kClasses * 4), o_loss = take((size_t)B * 4);
+  if (cudaSetDevice(ctx->device) != cudaSuccess) { delete n; return GFH_ERR_CUDA; }
+  if (cudaMalloc(&n->buf, off) != cudaSuccess) { delete n; return GFH_ERR_NOMEM; }
+  char* base = (char*)n->buf;
+  n->w = (float*)(base + o_w); n->gw = (float*)(base + o_gw);
+  n->m = (float*)(base + o_m); n->v = (float*)(base + o_v);
+  for (int l = 0; l < 5; ++l) n->wb[l] = (__nv_bfloat16*)(base + o_wb[l]);
+  for (int l = 1; l < 6; ++l) {
+    n->act[l] = (__nv_bfloat16*)(base + o_act[l]);
+    n->dact[l] = (__nv_bfloat16*)(base + o_dact[l]);
+  }
+  n->pooled = (float*)(base + o_pool); n->logits = (float*)(base + o_log);
+  n->dlogits = (float*)(base + o_dlog); n->loss = (float*)(base + o_loss);
+  float* h = new (std::nothrow) float[n->L.total];
+  if (!h) { cudaFree(n->buf); delete n; return GFH_ERR_NOMEM; }
+  init_params(h, n->L, seed);
+  cudaError_t e = cudaMemcpy(n->w, h, n->L.total * 4, cudaMemcpyHostToDevice);
+  delete[] h;
+  if (e == cudaSuccess) e = cudaMemset(n->m, 0, n->L.total * 4);
+  if (e == cudaSuccess) e = cudaMemset(n->v, 0, n->L.total * 4);
+  if (e != cudaSuccess || refresh_bf16(n) != GFH_OK || cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+    cudaFree(n->buf);
+    delete n;
+    return GFH_ERR_CUDA;
+  }
+  *out = n;
+  return GFH_OK;
+}
+
+extern "C" int gfh_cnn_destroy(gfh_cnn* n) {
+  if (!n) return GFH_OK;
+  cudaSetDevice(n->ctx->device);
+  if (n->ctx->stream) cudaStreamSynchronize(n->ctx->stream);
+  if (n->buf) cudaFree(n->buf);
+  delete n;
+  return GFH_OK;
+}
+
+extern "C" int64_t gfh_cnn_param_count(const gfh_cnn* n) { return n ? (int64_t)n->L.total : -1; }
+
+extern "C" int gfh_cnn_get_params(gfh_cnn* n, float* h_params, float* h_grads) {
+  if (!n) return GFH_ERR_ARG;
+  GFH_CUDA_TRY(cudaStreamSynchronize(n->ctx->stream));
+  if (h_params) GFH_CUDA_TRY(cudaMemcpy(h_params, n->w, n->L.total * 4, cudaMemcpyDeviceToHost));
+  if (h_grads) GFH_CUDA_TRY(cudaMemcpy(h_grads, n->gw, n->L.total * 4, cudaMemcpyDeviceToHost));
+  return GFH_OK;
+}
+
+extern "C" int gfh_cnn_set_params(gfh_cnn* n, const float* h_params) {
+  if (!n || !h_params) return GFH_ERR_ARG;
+  GFH_CUDA_TRY(cudaStreamSynchronize(n->ctx->stream));
+  GFH_CUDA_TRY(cudaMemcpy(n->w, h_params, n->L.total * 4, cudaMemcpyHostToDevice));
+  GFH_CUDA_TRY(cudaMemset(n->m, 0, n->L.total * 4));
+  GFH_CUDA_TRY(cudaMemset(n->v, 0, n->L.total * 4));
+  n->step = 0;
+  return refresh_bf16(n);
+}
+
+extern "C" int gfh_cnn_forward(gfh_cnn* n, const void* d_images, int32_t batch, float* d_logits) {
+  if (!n || !d_images || batch < 1 || batch > n->max_batch) return GFH_ERR_ARG;
+  GFH_CUDA_TRY(cudaSetDevice(n->ctx->device));
+  int rc = forward(n, (const __nv_bfloat16*)d_images, batch);
+  if (rc) return rc;
+  if (d_logits)
+    GFH_CUDA_TRY(cudaMemcpyAsync(d_logits, n->logits, (size_t)batch * kClasses * 4,
+                                 cudaMemcpyDeviceToDevice, n->ctx->stream));
+  return GFH_OK;
+}
+
+extern "C" int gfh_cnn_gradients(gfh_cnn* n, const void* d_images, const int32_t* d_labels,
+                                 int32_t batch, float* h_loss) {
+  if (!n || !d_images || !d_labels || batch < 1 || batch > n->max_batch) return GFH_ERR_ARG;
+  GFH_CUDA_TRY(cudaSetDevice(n->ctx->device));
+  int rc = forward(n, (const __nv_bfloat16*)d_images, batch);
+  if (!rc) rc = backward(n, (const __nv_bfloat16*)d_images, d_labels, batch);
+  if (rc) return rc;
+  if (h_loss) {
+    float* tmp = new (std::nothrow) float[batch];
+    if (!tmp) return GFH_ERR_NOMEM;
+    cudaError_t e = cudaMemcpyAsync(tmp, n->loss, (size_t)batch * 4, cudaMemcpyDeviceToHost, n->ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(n->ctx->stream);
+    double s = 0.0;
+    for (int b = 0; b < batch; ++b) s += tmp[b];
+    delete[] tmp;
+    if (e != cudaSuccess) return GFH_ERR_CUDA;
+    *h_loss = (float)(s / batch);
+  }
+  return GFH_OK;
+}
+
+extern "C" int gfh_cnn_train_step(gfh_cnn* n, const void* d_images, const int32_t* d_labels,
+                                  int32_t batch, float lr, float weight_decay, float* h_loss) {
+  int rc = gfh_cnn_gradients(n, d_images, d_labels, batch, h_loss);
+  if (rc) return rc;
+  n->step += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - std::pow(b1, (float)n->step), c2 = 1.f - std::pow(b2, (float)n->step);
+  const int64_t cnt = (int64_t)n->L.total;
+  k_adamw<<<(unsigned)((cnt + 255) / 256), 256, 0, n->ctx->stream>>>(n->w, n->gw, n->m, n->v, cnt, lr,
+                                                                    b1, b2, 1e-8f, weight_decay, c1, c2);
+  GFH_CUDA_TRY(cudaGetLastError());
+  return refresh_bf16(n);
+}
+
+extern "C" int gfh_synth_images(gfh_ctx* ctx, uint64_t seed, int64_t sample0, int32_t batch,
+                                int32_t n_fft, int32_t bin_lo, int32_t bin_hi, uint32_t p_noise24,
+                                const uint32_t* d_p_track24, const int32_t* d_tracks,
+                                const float* d_nplane, void* d_images) {
+  if (!ctx || batch < 1 || n_fft < kImg || bin_lo < 0 || bin_hi < bin_lo ||
+      bin_hi - bin_lo + 1 < kImg || !d_p_track24 || !d_tracks || !d_nplane || !d_images ||
+      batch > 65535)
+    return GFH_ERR_ARG;
+  GFH_CUDA_TRY(cudaSetDevice(ctx->device));
+  dim3 grid((kImg * kImg + 255) / 256, batch);
+  k_synth_images<<<grid, 256, 0, ctx->stream>>>(seed, sample0, n_fft, bin_lo, bin_hi - bin_lo + 1,
+                                                p_noise24, d_p_track24, d_tracks, d_nplane,
+                                                (uint32_t*)d_images);
+  GFH_CUDA_TRY(cudaGetLastError());
+  return GFH_OK;
+}
+
+extern "C" int gfh_peaks_to_images(gfh_ctx* ctx, const gfh_peaks* peaks, int32_t n_fft,
+                                   int32_t bin_lo, int32_t bin_hi, const float* d_nplane,
+                                   void* d_images) {
+  if (!ctx || !peaks || !peaks->offsets || peaks->n_lists < 1 || peaks->n_lists > 65535 ||
+      !peaks->fft_idx || !peaks->bin || n_fft < kImg || bin_lo < 0 || bin_hi < bin_lo ||
+      bin_hi - bin_lo + 1 < kImg || !d_nplane || !d_images)
+    return GFH_ERR_ARG;
+  GFH_CUDA_TRY(cudaSetDevice(ctx->device));
+  const int L = peaks->n_lists;
+  uint32_t* img = (uint32_t*)d_images;
+  GFH_CUDA_TRY(cudaMemsetAsync(img, 0, (size_t)L * kImg * kImg * 4, ctx->stream));
+  const int gx = std::max(1, std::min(64, ctx->num_sms * 8 / L));
+  k_image_count<<<dim3(gx, L), 256, 0, ctx->stream>>>(peaks->fft_idx, peaks->bin, peaks->offsets,
+                                                       n_fft, bin_lo, bin_hi - bin_lo + 1, img,
+                                                       ctx->d_flag);
+  GFH_CUDA_TRY(cudaGetLastError());
+  k_image_finish<<<dim3(kImg * kImg / 256, L), 256, 0, ctx->stream>>>(img, d_nplane);
+  GFH_CUDA_TRY(cudaGetLastError());
+  return GFH_OK;
+}
+
+extern "C" int gfh_propose_tiles(gfh_ctx* ctx, const float* d_logits, int32_t batch,
+                                 const float* d_gain, int32_t k, int32_t* d_top, float* d_resid) {
+  if (!ctx || !d_logits || !d_gain || !d_top || !d_resid || batch < 1 || k < 1 ||
+      k > kTiles * kTiles)
+    return GFH_ERR_ARG;
+  GFH_CUDA_TRY(cudaSetDevice(ctx->device));
+  k_propose<<<batch, 256, 0, ctx->stream>>>(d_logits, d_gain, k, d_top, d_resid);
+  GFH_CUDA_TRY(cudaGetLastError());
+  return GFH_OK;
+}
+
+// One 3x3 layer in isolation (for tests): mode 0 forward, 1 input gradient, 2 weight gradient.
+extern "C" int gfh_conv3x3(gfh_ctx* ctx, int32_t mode, int32_t cin, int32_t cout, int32_t stride,
+                           int32_t batch, int32_t h, const void* d_in, const void* d_w,
+                           const float* d_bias, const void* d_out, const void* d_dout, void* d_res,
+                           float* d_db) {
+  if (!ctx || batch < 1 || h < 16 || h % 16) return GFH_ERR_ARG;
+  GFH_CUDA_TRY(cudaSetDevice(ctx->device));
+  const int sms = ctx->num_sms;
+  cudaStream_t st = ctx->stream;
+  const auto* in = (const __nv_bfloat16*)d_in;
+  const auto* w = (const __nv_bfloat16*)d_w;
+  const auto* out = (const __nv_bfloat16*)d_out;
+  const auto* dout = (const __nv_bfloat16*)d_dout;
+#define GFH_CONV_CASE(CI, CO, S)                                                                   \
+  if (cin == CI && cout == CO && stride == S) {                                                    \
+    if (mode == 0) return conv_fwd<CI, CO, S>(in, w, d_bias, (__nv_bfloat16*)d_res, batch, h, sms, st); \
+    if (mode == 1) return conv_dgrad<CI, CO, S>(dout, out, w, (__nv_bfloat16*)d_res, batch, h, sms, st); \
+    if (mode == 2) return conv_wgrad<CI, CO, S>(dout, out, in, (float*)d_res, d_db, batch, h, sms, st); \
+    return GFH_ERR_ARG;                                                                            \
+  }
+  GFH_CONV_CASE(32, 32, 2)
+  GFH_CONV_CASE(32, 64, 1)
+  GFH_CONV_CASE(64, 64, 2)
+  GFH_CONV_CASE(64, 64, 1)
+#undef GFH_CONV_CASE
+  return GFH_ERR_ARG;
+}

@@ -234,6 +234,7 @@ extern "C" int gfh_plan_destroy(gfh_plan* p) {
     if (p->ctx->stream) cudaStreamSynchronize(p->ctx->stream);
   }
   if (p->d_buf) cudaFree(p->d_buf);
+  if (p->d_coarse_buf) cudaFree(p->d_coarse_buf);
   delete p;
   return GFH_OK;
 }
@@ -428,6 +429,120 @@ extern "C" int gfh_plan_execute(gfh_plan* p, const gfh_peaks* peaks) {
   return gfh_launch_plan(p, peaks);
 }
 
+// ---- coarse tiles --------------------------------------------------------------------------------
+
+extern "C" int gfh_plan_set_coarse(gfh_plan* p, int32_t coarse_k, int32_t coarse_x,
+                                   int32_t max_sel) {
+  if (!p || coarse_k < 1 || coarse_x < 1 || coarse_k > 4096 || coarse_x > 4096 || max_sel < 1 ||
+      (int64_t)max_sel > (int64_t)coarse_k * coarse_x)
+    return GFH_ERR_ARG;
+  const int nct = coarse_k * coarse_x;
+  const int R = p->cfg.rows, C = p->cfg.cols;
+  std::vector<TileDev> fine;
+  std::vector<int32_t> first;
+  first.reserve((size_t)p->n_maps * nct + 1);
+  int max_fine = 0, max_bands = p->max_tile_bands;
+  for (int m = 0; m < p->n_maps; ++m) {
+    const gfh_grid& g = p->grids[m];
+    HostMap hm;
+    int rc = gfh_host_tables(&g, hm.U, hm.B, hm.S);
+    if (rc) return rc;
+    rc = gfh_host_columns(&g, hm.band, hm.f0, hm.f0n);
+    if (rc) return rc;
+    // columns of each f0 tile: analysis columns only; f0 falls with the column, so each range is
+    // contiguous
+    std::vector<int64_t> cmin(coarse_x, INT64_MAX), cmax(coarse_x, -1);
+    const double span = g.ana_hi - g.ana_lo;
+    for (int64_t c = 0; c < g.n_x0; ++c) {
+      if (hm.band[c] < 0) continue;
+      int xt = (int)std::floor((hm.f0[c] - g.ana_lo) / span * coarse_x);
+      xt = std::min(std::max(xt, 0), coarse_x - 1);
+      cmin[xt] = std::min(cmin[xt], c);
+      cmax[xt] = std::max(cmax[xt], c);
+    }
+    for (int kt = 0; kt < coarse_k; ++kt) {
+      // rows r with floor(r coarse_k / K) = kt
+      const int r0 = (int)(((int64_t)kt * g.n_k + coarse_k - 1) / coarse_k);
+      const int r1 = (int)(((int64_t)(kt + 1) * g.n_k + coarse_k - 1) / coarse_k);
+      for (int xt = 0; xt < coarse_x; ++xt) {
+        first.push_back((int32_t)fine.size());
+        if (r1 <= r0 || cmax[xt] < 0) continue;
+        // 16-byte aligned column range (vector stores): neighbouring tiles may share <= 3 columns
+        const int64_t c_lo = cmin[xt] & ~int64_t(3);
+        const int64_t c_hi = std::min<int64_t>(g.ld_x0, (cmax[xt] + 4) & ~int64_t(3));
+        int cnt = 0;
+        for (int rr = r0; rr < r1; rr += R) {
+          const int nr = std::min(R, r1 - rr);
+          const int64_t s_min = hm.B[0] + (int64_t)rr * hm.S[0];
+          const int64_t s_max = hm.B[g.n_fft - 1] + (int64_t)(rr + nr - 1) * hm.S[g.n_fft - 1];
+          for (int64_t c0 = c_lo; c0 < c_hi; c0 += C) {
+            TileDev t{};
+            t.map = m;
+            t.row0 = rr;
+            t.nrows = nr;
+            t.col0 = c0;
+            t.ncols = (int32_t)std::min<int64_t>(C, c_hi - c0);
+            tile_bins(g, hm, s_min, s_max, c0, c0 + t.ncols, &t.bin_a, &t.bin_b);
+            t.band_lo = INT32_MAX;
+            t.band_hi = -1;
+            for (int64_t c = c0; c < c0 + t.ncols; ++c) {
+              const int32_t b = hm.band[c];
+              if (b >= 0) { t.band_lo = std::min(t.band_lo, b); t.band_hi = std::max(t.band_hi, b); }
+            }
+            if (t.band_hi < 0) t.band_lo = 0;
+            else max_bands = std::max(max_bands, t.band_hi - t.band_lo + 1);
+            fine.push_back(t);
+            ++cnt;
+          }
+        }
+        max_fine = std::max(max_fine, cnt);
+      }
+    }
+  }
+  first.push_back((int32_t)fine.size());
+  if ((int64_t)p->n_maps * max_sel * std::max(max_fine, 1) > INT32_MAX) return GFH_ERR_SIZE;
+  const size_t smem = (size_t)R * (C + 2) * 4 + 32 * 4 + (p->select ? (size_t)max_bands * 8 : 0);
+  if (smem > 227 * 1024) return GFH_ERR_SIZE;
+
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
+  const size_t o_fine = take(sizeof(TileDev) * std::max<size_t>(fine.size(), 1));
+  const size_t o_first = take(sizeof(int32_t) * first.size());
+  const size_t o_sel = take(sizeof(TileDev) * (size_t)p->n_maps * max_sel * std::max(max_fine, 1));
+  GFH_CUDA_TRY(cudaSetDevice(p->ctx->device));
+  if (p->ctx->stream) GFH_CUDA_TRY(cudaStreamSynchronize(p->ctx->stream));
+  void* buf = nullptr;
+  if (cudaMalloc(&buf, off) != cudaSuccess) return GFH_ERR_NOMEM;
+  char* base = (char*)buf;
+  cudaError_t e = cudaSuccess;
+  if (!fine.empty())
+    e = cudaMemcpy(base + o_fine, fine.data(), sizeof(TileDev) * fine.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(base + o_first, first.data(), sizeof(int32_t) * first.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) { cudaFree(buf); return GFH_ERR_CUDA; }
+  if (p->d_coarse_buf) cudaFree(p->d_coarse_buf);
+  p->d_coarse_buf = buf;
+  p->d_fine = (TileDev*)(base + o_fine);
+  p->d_coarse_first = (int32_t*)(base + o_first);
+  p->d_sel_tiles = (TileDev*)(base + o_sel);
+  p->coarse_k = coarse_k;
+  p->coarse_x = coarse_x;
+  p->max_sel = max_sel;
+  p->max_fine = max_fine;
+  p->max_tile_bands = max_bands;
+  return GFH_OK;
+}
+
+extern "C" int gfh_plan_execute_tiles(gfh_plan* p, const gfh_peaks* peaks, const int32_t* d_coarse,
+                                      int32_t n_sel) {
+  if (!p || !peaks || !peaks->fft_idx || !peaks->bin || !peaks->offsets || peaks->n_lists < 1 ||
+      p->coarse_k < 1 || n_sel < 0 || n_sel > p->max_sel || (n_sel > 0 && !d_coarse))
+    return GFH_ERR_ARG;
+  for (const gfh_grid& g : p->grids)
+    if (g.list < 0 || g.list >= peaks->n_lists) return GFH_ERR_ARG;
+  return gfh_launch_plan_tiles(p, peaks, d_coarse, n_sel);
+}
+
 // ---- autotuner ----------------------------------------------------------------------------------
 
 namespace {
@@ -488,8 +603,13 @@ extern "C" int gfh_plan_autotune(gfh_plan* p, const gfh_peaks* peaks, int32_t re
                          p->h_cands.empty() ? nullptr : p->h_cands.data(), p->d_stats, &best, &q);
     if (rc) return rc;
     if (p->ctx->stream) cudaStreamSynchronize(p->ctx->stream);
+    const int ck = p->coarse_k, cx = p->coarse_x, ms = p->max_sel;
     std::swap(*p, *q);      // p takes the tuned tables; q holds the old ones and is freed
     gfh_plan_destroy(q);
+    if (ck > 0) {           // coarse tiles follow the tile shape
+      rc = gfh_plan_set_coarse(p, ck, cx, ms);
+      if (rc) return rc;
+    }
   }
   if (h_best) *h_best = best;
   if (h_best_ms) *h_best_ms = best_ms;

@@ -168,6 +168,7 @@ k_hough(const MapDev* __restrict__ maps, const TileDev* __restrict__ tiles,
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int NW = NT / kLane;
   const TileDev t = tiles[blockIdx.x];
+  if (t.nrows <= 0) return;                      // an unused slot of a coarse-tile launch
   const MapDev& md = maps[t.map];
   const int C = t.ncols;
   const int lds = C + 2;
@@ -385,36 +386,64 @@ __global__ void k_select_cols(const int32_t* __restrict__ map, const MapDev* __r
 // attribute belongs to the kernel, not to a plan, so it is set to the largest size any plan may
 // request: each launch still asks only for its own size (which alone decides occupancy).
 template <int R, int NT, bool SEL>
-int launch_hough_t(gfh_plan* p, const gfh_peaks* peaks, size_t smem, bool prepare) {
+int launch_hough_t(gfh_plan* p, const gfh_peaks* peaks, const TileDev* tiles, int n_tiles,
+                   size_t smem, bool prepare) {
   auto fn = k_hough<R, NT, SEL>;
   if (prepare) {
     GFH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)kMaxSmemBytes));
     return GFH_OK;
   }
-  fn<<<p->n_tiles, NT, smem, p->ctx->stream>>>(p->d_maps, p->d_tiles, peaks->fft_idx, peaks->bin,
-                                                 p->ctx->d_flag, p->cfg.cols);
+  fn<<<n_tiles, NT, smem, p->ctx->stream>>>(p->d_maps, tiles, peaks->fft_idx, peaks->bin,
+                                            p->ctx->d_flag, p->cfg.cols);
   GFH_CUDA_TRY(cudaGetLastError());
   return GFH_OK;
 }
 
 template <int R, int NT>
-int launch_hough_sel(gfh_plan* p, const gfh_peaks* peaks, size_t smem, bool prepare) {
-  return p->select ? launch_hough_t<R, NT, true>(p, peaks, smem, prepare)
-                   : launch_hough_t<R, NT, false>(p, peaks, smem, prepare);
+int launch_hough_sel(gfh_plan* p, const gfh_peaks* peaks, const TileDev* tiles, int n_tiles,
+                     size_t smem, bool prepare) {
+  return p->select ? launch_hough_t<R, NT, true>(p, peaks, tiles, n_tiles, smem, prepare)
+                   : launch_hough_t<R, NT, false>(p, peaks, tiles, n_tiles, smem, prepare);
 }
 
 template <int R>
-int launch_hough_r(gfh_plan* p, const gfh_peaks* peaks, size_t smem, bool prepare) {
-  return p->cfg.threads == 256 ? launch_hough_sel<R, 256>(p, peaks, smem, prepare)
-                               : launch_hough_sel<R, 512>(p, peaks, smem, prepare);
+int launch_hough_r(gfh_plan* p, const gfh_peaks* peaks, const TileDev* tiles, int n_tiles,
+                   size_t smem, bool prepare) {
+  return p->cfg.threads == 256 ? launch_hough_sel<R, 256>(p, peaks, tiles, n_tiles, smem, prepare)
+                               : launch_hough_sel<R, 512>(p, peaks, tiles, n_tiles, smem, prepare);
 }
 
-int launch_hough(gfh_plan* p, const gfh_peaks* peaks, size_t smem, bool prepare) {
-  return p->cfg.rows == 4    ? launch_hough_r<4>(p, peaks, smem, prepare)
-         : p->cfg.rows == 8  ? launch_hough_r<8>(p, peaks, smem, prepare)
-         : p->cfg.rows == 16 ? launch_hough_r<16>(p, peaks, smem, prepare)
-                             : launch_hough_r<32>(p, peaks, smem, prepare);
+int launch_hough(gfh_plan* p, const gfh_peaks* peaks, const TileDev* tiles, int n_tiles,
+                 size_t smem, bool prepare) {
+  return p->cfg.rows == 4    ? launch_hough_r<4>(p, peaks, tiles, n_tiles, smem, prepare)
+         : p->cfg.rows == 8  ? launch_hough_r<8>(p, peaks, tiles, n_tiles, smem, prepare)
+         : p->cfg.rows == 16 ? launch_hough_r<16>(p, peaks, tiles, n_tiles, smem, prepare)
+                             : launch_hough_r<32>(p, peaks, tiles, n_tiles, smem, prepare);
+}
+
+// Copies the fine tiles of each map's selected coarse tiles into max_fine slots per selection;
+// unused slots get empty tiles (no rows), which k_hough skips.
+__global__ void k_gather_tiles(const TileDev* __restrict__ fine, const int32_t* __restrict__ first,
+                               const int32_t* __restrict__ coarse, int n_sel, int nct,
+                               int max_fine, TileDev* __restrict__ out) {
+  const int m = blockIdx.y, s = blockIdx.x;
+  const int id = coarse[(int64_t)m * n_sel + s];
+  int b = 0, e = 0;
+  if (id >= 0 && id < nct) {
+    b = first[(int64_t)m * nct + id];
+    e = first[(int64_t)m * nct + id + 1];
+  }
+  for (int q = threadIdx.x; q < max_fine; q += blockDim.x) {
+    TileDev t;
+    if (b + q < e) {
+      t = fine[b + q];
+    } else {
+      t.map = m; t.row0 = 0; t.nrows = 0; t.ncols = 0; t.col0 = 0;
+      t.bin_a = 1; t.bin_b = 0; t.band_lo = 0; t.band_hi = -1;
+    }
+    out[((int64_t)m * n_sel + s) * max_fine + q] = t;
+  }
 }
 
 }  // namespace
@@ -427,14 +456,13 @@ size_t gfh_hough_smem_bytes(const gfh_plan* p) {
 int gfh_prepare_plan(gfh_plan* p) {
   const size_t smem = gfh_hough_smem_bytes(p);
   if (smem > 227 * 1024) return GFH_ERR_SIZE;
-  return launch_hough(p, nullptr, smem, true);
+  return launch_hough(p, nullptr, nullptr, 0, smem, true);
 }
 
-int gfh_launch_plan(gfh_plan* p, const gfh_peaks* peaks) {
+// Per-execute preparation shared by the full and the coarse-tile forms: input check, per-map CSR
+// over bins, zeroed candidate keys.
+static int launch_prologue(gfh_plan* p, const gfh_peaks* peaks) {
   gfh_ctx* ctx = p->ctx;
-  GFH_CUDA_TRY(cudaSetDevice(ctx->device));
-  const size_t smem = gfh_hough_smem_bytes(p);
-  if (smem > 227 * 1024) return GFH_ERR_SIZE;
   cudaStream_t st = ctx->stream;
   {
     dim3 grid(64, peaks->n_lists);
@@ -446,18 +474,49 @@ int gfh_launch_plan(gfh_plan* p, const gfh_peaks* peaks) {
   GFH_CUDA_TRY(cudaGetLastError());
   if (p->select)
     GFH_CUDA_TRY(cudaMemsetAsync(p->d_keys, 0, p->key_words * sizeof(unsigned long long), st));
-  if (p->n_tiles > 0) {
-    const int rc = launch_hough(p, peaks, smem, false);
-    if (rc) return rc;
-  }
+  return GFH_OK;
+}
+
+static int launch_epilogue(gfh_plan* p) {
   if (p->select) {
     int maxb = 1;
     for (const gfh_grid& g : p->grids) maxb = g.n_bands > maxb ? g.n_bands : maxb;
     dim3 grid((maxb + 127) / 128, p->n_maps);
-    k_finalize<<<grid, 128, 0, st>>>(p->d_maps);
+    k_finalize<<<grid, 128, 0, p->ctx->stream>>>(p->d_maps);
     GFH_CUDA_TRY(cudaGetLastError());
   }
   return GFH_OK;
+}
+
+int gfh_launch_plan(gfh_plan* p, const gfh_peaks* peaks) {
+  GFH_CUDA_TRY(cudaSetDevice(p->ctx->device));
+  const size_t smem = gfh_hough_smem_bytes(p);
+  if (smem > 227 * 1024) return GFH_ERR_SIZE;
+  int rc = launch_prologue(p, peaks);
+  if (rc) return rc;
+  if (p->n_tiles > 0) {
+    rc = launch_hough(p, peaks, p->d_tiles, p->n_tiles, smem, false);
+    if (rc) return rc;
+  }
+  return launch_epilogue(p);
+}
+
+int gfh_launch_plan_tiles(gfh_plan* p, const gfh_peaks* peaks, const int32_t* d_coarse, int n_sel) {
+  GFH_CUDA_TRY(cudaSetDevice(p->ctx->device));
+  const size_t smem = gfh_hough_smem_bytes(p);
+  if (smem > 227 * 1024) return GFH_ERR_SIZE;
+  int rc = launch_prologue(p, peaks);
+  if (rc) return rc;
+  const int nct = p->coarse_k * p->coarse_x;
+  if (n_sel > 0 && p->max_fine > 0) {
+    dim3 grid(n_sel, p->n_maps);
+    k_gather_tiles<<<grid, 128, 0, p->ctx->stream>>>(p->d_fine, p->d_coarse_first, d_coarse, n_sel,
+                                                     nct, p->max_fine, p->d_sel_tiles);
+    GFH_CUDA_TRY(cudaGetLastError());
+    rc = launch_hough(p, peaks, p->d_sel_tiles, p->n_maps * n_sel * p->max_fine, smem, false);
+    if (rc) return rc;
+  }
+  return launch_epilogue(p);
 }
 
 extern "C" int gfh_hough(gfh_ctx* ctx, const uint32_t* d_fft_idx, const uint32_t* d_bin,

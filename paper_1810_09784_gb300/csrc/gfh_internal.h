@@ -14,6 +14,31 @@
 // Largest dynamic shared memory a block may use on sm_103a (227 KB).
 constexpr size_t kMaxSmemBytes = 227 * 1024;
 
+// Counter-based generator of the statistical peakmap model: the splitmix64 finaliser (Steele, Lea
+// and Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014) applied to a key built
+// from (seed, sample, stream, FFT i, bin j); the top 24 bits are the cell's uniform.
+__host__ __device__ __forceinline__ uint64_t gfh_mix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__host__ __device__ __forceinline__ uint32_t gfh_cell_u24(uint64_t seed, uint64_t sample,
+                                                         uint32_t stream, uint32_t i, uint32_t j) {
+  const uint64_t s = gfh_mix64(seed ^ (sample * 0xD1B54A32D192ED03ull) ^ ((uint64_t)stream << 56));
+  return (uint32_t)(gfh_mix64(s ^ (((uint64_t)i << 32) | j)) >> 40);
+}
+
+// (FFT i, bin j) is a peak of the sample: a noise peak (stream 0 below p_noise24), or the cell of
+// the injected track in FFT i and a track hit (stream 1 below p_track24).
+__host__ __device__ __forceinline__ bool gfh_synth_peak(uint64_t seed, uint64_t sample, uint32_t i,
+                                                       uint32_t j, uint32_t p_noise24,
+                                                       int track_bin, uint32_t p_track24) {
+  if (gfh_cell_u24(seed, sample, 0, i, j) < p_noise24) return true;
+  return (int)j == track_bin && gfh_cell_u24(seed, sample, 1, i, j) < p_track24;
+}
+
 // Device-side error flag bits (gfh_check).
 #define GFH_FLAG_UNSORTED 1u
 #define GFH_FLAG_FFT_RANGE 2u
@@ -99,6 +124,12 @@ struct gfh_plan {
   std::vector<int32_t*> h_maps;
   std::vector<gfh_candidate*> h_cands;
   gfh_map_stats* d_stats = nullptr;
+  // coarse tiles (gfh_plan_set_coarse): per (map, coarse tile) the fine tiles that cover it
+  int coarse_k = 0, coarse_x = 0, max_sel = 0, max_fine = 0;
+  void* d_coarse_buf = nullptr;
+  TileDev* d_fine = nullptr;           // fine tiles, grouped by (map, coarse tile)
+  int32_t* d_coarse_first = nullptr;   // n_maps * coarse_k * coarse_x + 1 group offsets
+  TileDev* d_sel_tiles = nullptr;      // n_maps * max_sel * max_fine gathered tiles
 };
 
 // Host-side planning (gfh_host.cpp).
@@ -109,5 +140,7 @@ int gfh_host_columns(const gfh_grid* g, std::vector<int32_t>& band, std::vector<
 
 // Launchers (gfh_hough.cu).
 int gfh_launch_plan(gfh_plan* plan, const gfh_peaks* peaks);
+int gfh_launch_plan_tiles(gfh_plan* plan, const gfh_peaks* peaks, const int32_t* d_coarse,
+                          int n_sel);
 int gfh_prepare_plan(gfh_plan* plan);   // one-time kernel attributes (outside any capture)
 int gfh_launch_select(gfh_ctx* ctx, const int32_t* d_map, const MapDev& md, void* d_scratch);

@@ -373,6 +373,58 @@ extern "C" int gfh_peakmap_async(gfh_ctx* ctx, const float* d_series, int64_t n_
                       cap, nullptr, d_n_peaks);
 }
 
+// ---- statistical peakmaps (training and evaluation data of the tile proposer) -------------------
+
+namespace {
+
+// bits[(j - bin_lo) * n_words + w], bit l: FFT 32 w + l is a peak of the sample (one warp per word).
+__global__ void k_synth_bits(uint64_t seed, uint64_t sample, int n_fft, int bin_lo, int n_bins,
+                             int n_words, uint32_t p_noise24, uint32_t p_track24,
+                             const int32_t* __restrict__ track, uint32_t* __restrict__ bits) {
+  const int64_t q = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (q >= (int64_t)n_bins * n_words) return;
+  const int jl = (int)(q / n_words), w = (int)(q % n_words);
+  const int i = w * 32 + lane;
+  const bool pk = i < n_fft && gfh_synth_peak(seed, sample, (uint32_t)i, (uint32_t)(bin_lo + jl),
+                                             p_noise24, track ? track[i] : -1, p_track24);
+  const uint32_t word = __ballot_sync(0xffffffffu, pk);
+  if (lane == 0) bits[q] = word;
+}
+
+}  // namespace
+
+extern "C" int gfh_synth_peaks(gfh_ctx* ctx, uint64_t seed, int64_t sample, int32_t n_fft,
+                               int32_t bin_lo, int32_t bin_hi, uint32_t p_noise24,
+                               uint32_t p_track24, const int32_t* d_track, uint32_t* d_fft_idx,
+                               uint32_t* d_bin, int64_t cap, int64_t* h_n_peaks) {
+  if (!ctx || n_fft < 1 || bin_lo < 0 || bin_hi < bin_lo || !h_n_peaks || cap < 0 ||
+      (cap > 0 && (!d_fft_idx || !d_bin)) || p_noise24 > (1u << 24) || p_track24 > (1u << 24))
+    return GFH_ERR_ARG;
+  GFH_CUDA_TRY(cudaSetDevice(ctx->device));
+  const int n_bins = bin_hi - bin_lo + 1;
+  const int n_words = (n_fft + 31) / 32;
+  const size_t o_cnt = align256((size_t)n_bins * n_words * 4);
+  int rc = ensure_scratch(ctx, o_cnt + align256(((size_t)n_bins + 1) * 8));
+  if (rc) return rc;
+  uint32_t* bits = (uint32_t*)ctx->pm_buf;
+  int64_t* cnt = (int64_t*)((char*)ctx->pm_buf + o_cnt);
+  cudaStream_t st = ctx->stream;
+  const int64_t warps = (int64_t)n_bins * n_words;
+  k_synth_bits<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(seed, (uint64_t)sample, n_fft, bin_lo,
+                                                            n_bins, n_words, p_noise24, p_track24,
+                                                            d_track, bits);
+  GFH_CUDA_TRY(cudaGetLastError());
+  k_count<<<(n_bins + 7) / 8, 256, 0, st>>>(bits, n_bins, n_words, cnt);
+  k_scan<<<1, 1024, 0, st>>>(cnt, n_bins);
+  k_scatter<<<(n_bins + 7) / 8, 256, 0, st>>>(bits, n_bins, n_words, bin_lo, cnt, d_fft_idx, d_bin, cap);
+  GFH_CUDA_TRY(cudaGetLastError());
+  GFH_CUDA_TRY(cudaMemcpyAsync(ctx->h_pinned, cnt + n_bins, 8, cudaMemcpyDeviceToHost, st));
+  GFH_CUDA_TRY(cudaStreamSynchronize(st));
+  *h_n_peaks = (int64_t)ctx->h_pinned[0];
+  return *h_n_peaks > cap ? GFH_ERR_SIZE : GFH_OK;
+}
+
 // ---- allocation-free peak selection -------------------------------------------------------------
 //
 // For callers that cannot allocate device memory: a host application whose GPU memory is owned

@@ -30,7 +30,14 @@ EXPORTED = [
     "gfh_peaks_from_power", "gfh_peakmap", "gfh_peakmap_async",
     "gfh_plan_create", "gfh_plan_destroy", "gfh_plan_execute", "gfh_plan_autotune",
     "gfh_hough", "gfh_select", "gfh_peaks_from_power_static",
+    "gfh_plan_set_coarse", "gfh_plan_execute_tiles",
+    "gfh_synth_peaks", "gfh_synth_images", "gfh_peaks_to_images",
+    "gfh_cnn_create", "gfh_cnn_destroy", "gfh_cnn_param_count", "gfh_cnn_get_params",
+    "gfh_cnn_set_params", "gfh_cnn_forward", "gfh_cnn_gradients", "gfh_cnn_train_step",
+    "gfh_propose_tiles", "gfh_conv3x3",
 ]
+N_CLASSES = 4097        # 64 x 64 coarse tiles + no signal
+IMG = 256
 STATIC_SCRATCH_BYTES = 8 << 20
 
 
@@ -96,6 +103,7 @@ def lib() -> ctypes.CDLL:
                                "`python -m paper_1810_09784_gb300.build`")
         L = ctypes.CDLL(str(_LIB_PATH))
         vp, i32, i64, dbl = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        u32, u64 = ctypes.c_uint32, ctypes.c_uint64
         P = ctypes.POINTER
         sig = {
             "gfh_create": [P(vp), ctypes.c_int, vp],
@@ -115,11 +123,28 @@ def lib() -> ctypes.CDLL:
             "gfh_hough": [vp, vp, vp, i64, P(GridC), vp, vp, vp],
             "gfh_select": [vp, vp, P(GridC), vp, vp],
             "gfh_peaks_from_power_static": [vp, vp, i64, i32, i32, i32, dbl, vp, vp, i64, vp],
+            "gfh_plan_set_coarse": [vp, i32, i32, i32],
+            "gfh_plan_execute_tiles": [vp, P(PeaksC), vp, i32],
+            "gfh_synth_peaks": [vp, u64, i64, i32, i32, i32, u32, u32, vp, vp, vp, i64, P(i64)],
+            "gfh_synth_images": [vp, u64, i64, i32, i32, i32, i32, u32, vp, vp, vp, vp],
+            "gfh_peaks_to_images": [vp, P(PeaksC), i32, i32, i32, vp, vp],
+            "gfh_cnn_create": [vp, i32, u64, P(vp)],
+            "gfh_cnn_destroy": [vp],
+            "gfh_cnn_get_params": [vp, vp, vp],
+            "gfh_cnn_set_params": [vp, vp],
+            "gfh_cnn_forward": [vp, vp, i32, vp],
+            "gfh_cnn_gradients": [vp, vp, vp, i32, P(ctypes.c_float)],
+            "gfh_cnn_train_step": [vp, vp, vp, i32, ctypes.c_float, ctypes.c_float,
+                                   P(ctypes.c_float)],
+            "gfh_propose_tiles": [vp, vp, i32, vp, i32, vp, vp],
+            "gfh_conv3x3": [vp, i32, i32, i32, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
             fn.argtypes = args
             fn.restype = ctypes.c_int
+        L.gfh_cnn_param_count.argtypes = [vp]
+        L.gfh_cnn_param_count.restype = i64
         L.gfh_strerror.argtypes = [ctypes.c_int]
         L.gfh_strerror.restype = ctypes.c_char_p
         _lib = L
@@ -319,6 +344,15 @@ class Plan:
                                     ctypes.byref(ms)), "gfh_plan_autotune")
         return (best.rows, best.cols, best.threads), ms.value
 
+    def set_coarse(self, coarse_k: int, coarse_x: int, max_sel: int) -> None:
+        _ok(lib().gfh_plan_set_coarse(self._h, coarse_k, coarse_x, max_sel), "gfh_plan_set_coarse")
+
+    def execute_tiles(self, fft_idx, bins, offsets, n_lists: int, coarse, n_sel: int) -> None:
+        """Exact Hough on the coarse tiles listed in the int32 device tensor coarse [maps][n_sel]."""
+        pk = PeaksC(_ptr(fft_idx), _ptr(bins), _ptr(offsets), n_lists)
+        _ok(lib().gfh_plan_execute_tiles(self._h, ctypes.byref(pk), _ptr(coarse), n_sel),
+            "gfh_plan_execute_tiles")
+
     def close(self) -> None:
         if self._h:
             lib().gfh_plan_destroy(self._h)
@@ -345,3 +379,104 @@ def peaks_from_power_static(stream, power, bin_lo: int, bin_hi: int, theta: floa
                                            power.shape[0], bin_lo, bin_hi, theta, _ptr(fft_out),
                                            _ptr(bin_out), fft_out.numel(), _ptr(n_out))
     _ok(rc, "gfh_peaks_from_power_static")
+
+
+# ---- statistical peakmaps, images, the proposal network ------------------------------------------
+
+def synth_peaks(ctx: Context, seed: int, sample: int, n_fft: int, bin_lo: int, bin_hi: int,
+                p_noise24: int, p_track24: int, track, fft_out, bin_out) -> int:
+    """gfh_synth_peaks: the peak list of one sample of the statistical model; returns its length."""
+    n = ctypes.c_int64()
+    rc = lib().gfh_synth_peaks(ctx.handle, seed, sample, n_fft, bin_lo, bin_hi, p_noise24,
+                               p_track24, _ptr(track), _ptr(fft_out), _ptr(bin_out),
+                               fft_out.numel(), ctypes.byref(n))
+    _ok(rc, "gfh_synth_peaks")
+    return n.value
+
+
+def synth_images(ctx: Context, seed: int, sample0: int, n_fft: int, bin_lo: int, bin_hi: int,
+                 p_noise24: int, p_track24, tracks, nplane, images) -> None:
+    """gfh_synth_images into the bf16 tensor images [B][256][256][2]."""
+    rc = lib().gfh_synth_images(ctx.handle, seed, sample0, images.shape[0], n_fft, bin_lo, bin_hi,
+                                p_noise24, _ptr(p_track24), _ptr(tracks), _ptr(nplane),
+                                _ptr(images))
+    _ok(rc, "gfh_synth_images")
+
+
+def peaks_to_images(ctx: Context, fft_idx, bins, offsets, n_lists: int, n_fft: int, bin_lo: int,
+                    bin_hi: int, nplane, images) -> None:
+    """gfh_peaks_to_images: image l from peak list l (device offsets [n_lists + 1])."""
+    pk = PeaksC(_ptr(fft_idx), _ptr(bins), _ptr(offsets), n_lists)
+    rc = lib().gfh_peaks_to_images(ctx.handle, ctypes.byref(pk), n_fft, bin_lo, bin_hi,
+                                   _ptr(nplane), _ptr(images))
+    _ok(rc, "gfh_peaks_to_images")
+
+
+def propose_tiles(ctx: Context, logits, gain, k: int, top, resid) -> None:
+    """gfh_propose_tiles: the k best coarse tiles per map and the missed probability."""
+    rc = lib().gfh_propose_tiles(ctx.handle, _ptr(logits), logits.shape[0], _ptr(gain), k,
+                                 _ptr(top), _ptr(resid))
+    _ok(rc, "gfh_propose_tiles")
+
+
+def conv3x3(ctx: Context, mode: int, cin: int, cout: int, stride: int, batch: int, h: int,
+            inp=None, w=None, bias=None, out=None, dout=None, res=None, db=None) -> None:
+    """gfh_conv3x3: one 3x3 layer alone (0 forward, 1 input gradient, 2 weight gradient)."""
+    rc = lib().gfh_conv3x3(ctx.handle, mode, cin, cout, stride, batch, h, _ptr(inp), _ptr(w),
+                           _ptr(bias), _ptr(out), _ptr(dout), _ptr(res), _ptr(db))
+    _ok(rc, "gfh_conv3x3")
+
+
+class Cnn:
+    """The proposal network (gfh_cnn_*): device-resident fp32 master weights, bf16 copies."""
+
+    def __init__(self, ctx: Context, max_batch: int, seed: int):
+        self.ctx = ctx
+        self._h = ctypes.c_void_p()
+        _ok(lib().gfh_cnn_create(ctx.handle, max_batch, seed, ctypes.byref(self._h)),
+            "gfh_cnn_create")
+        self.n_params = int(lib().gfh_cnn_param_count(self._h))
+
+    def params(self) -> np.ndarray:
+        out = np.empty(self.n_params, np.float32)
+        _ok(lib().gfh_cnn_get_params(self._h, out.ctypes.data, None), "gfh_cnn_get_params")
+        return out
+
+    def grads(self) -> np.ndarray:
+        out = np.empty(self.n_params, np.float32)
+        _ok(lib().gfh_cnn_get_params(self._h, None, out.ctypes.data), "gfh_cnn_get_params")
+        return out
+
+    def set_params(self, params: np.ndarray) -> None:
+        a = np.ascontiguousarray(params, dtype=np.float32)
+        assert a.size == self.n_params
+        _ok(lib().gfh_cnn_set_params(self._h, a.ctypes.data), "gfh_cnn_set_params")
+
+    def forward(self, images, logits=None) -> None:
+        _ok(lib().gfh_cnn_forward(self._h, _ptr(images), images.shape[0], _ptr(logits)),
+            "gfh_cnn_forward")
+
+    def gradients(self, images, labels) -> float:
+        loss = ctypes.c_float()
+        _ok(lib().gfh_cnn_gradients(self._h, _ptr(images), _ptr(labels), images.shape[0],
+                                    ctypes.byref(loss)), "gfh_cnn_gradients")
+        return loss.value
+
+    def train_step(self, images, labels, lr: float, weight_decay: float = 0.0,
+                   want_loss: bool = True):
+        loss = ctypes.c_float()
+        _ok(lib().gfh_cnn_train_step(self._h, _ptr(images), _ptr(labels), images.shape[0], lr,
+                                     weight_decay, ctypes.byref(loss) if want_loss else None),
+            "gfh_cnn_train_step")
+        return loss.value if want_loss else None
+
+    def close(self) -> None:
+        if self._h:
+            lib().gfh_cnn_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,393 @@
+"""The learned tile proposer around the exact Hough: data, training and evaluation.
+
+The paper names machine learning as future work (Sec. VIII).  Here a small convolutional network
+looks at a coarse image of a peakmap and ranks the coarse (x0, k) tiles of its Hough map (Sec. IV),
+so that the exact Hough runs on the best 32 of 64 x 64 tiles only.  Candidates always come from
+exact counts; a map whose proposal leaves more than `tau` probability outside the chosen tiles is
+searched in full instead (the exact Hough is the fallback and the judge of recall).
+
+Workload: maps shaped like the small plain search (1024 Hz sampling, 1800 s, T_FFT 2 s, 1799 FFTs,
+band 100-400 Hz, 500 k rows), one braking index per map from n = 2.0, 2.1, ..., 7.0 (sample s has
+index s mod 51), half of them with one power-law injection (Sec. II Eq. powlaws) of spectral SNR
+uniform in [2, 8], f0 uniform over the band, k on a uniformly drawn row of the map's k grid.
+Peakmaps come from the statistical model of `synth` (noise peaks with the probability p0 of an
+equalised exponential spectrum above 2.5 that is a local maximum; the track's cell is a peak with
+the probability that a signal of that SNR exceeds 2.5), drawn on the GPU cell by cell.
+
+Labels: class d * 64 + xt, xt = floor((f0 - ana_lo) / (ana_hi - ana_lo) * 64) and drift class
+d = floor(r (f0 / f_max)^n * 64 / K) (a track on k row r drifts r x0 columns over the observation,
+one column spanning (f / f_max)^n bins), or 4096 without a signal.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+from . import gfh, synth
+
+N_GRID = tuple(round(2.0 + 0.1 * i, 10) for i in range(51))
+TILES = 64
+NULL_CLASS = TILES * TILES
+THETA = 2.5
+
+
+@dataclasses.dataclass(frozen=True)
+class ProposerSpec:
+    fs: float = 1024.0
+    t_obs: float = 1800.0
+    t_fft: float = 2.0
+    bin_lo: int = 200
+    bin_hi: int = 799
+    n_k: int = 500
+    ana_lo: float = 100.0
+    ana_hi: float = 400.0
+    p_noise: float = 0.0755         # strict local maximum of an exp(1) spectrum above 2.5
+    snr_lo: float = 2.0
+    snr_hi: float = 8.0
+    p_signal: float = 0.5
+    seed: int = 20181023
+
+    @property
+    def n_fft(self) -> int:
+        N = int(round(self.fs * self.t_fft))
+        return (int(round(self.fs * self.t_obs)) - N) // (N // 2) + 1
+
+    @property
+    def df(self) -> float:
+        return 1.0 / self.t_fft
+
+    @property
+    def p_noise24(self) -> int:
+        return int(round(self.p_noise * 2 ** 24))
+
+    def grid_fields(self, n: float, list_idx: int = 0) -> dict:
+        return dict(n=n, df=self.df, bin_lo=self.bin_lo, bin_hi=self.bin_hi, n_fft=self.n_fft,
+                    t_first=self.t_fft / 2, t_hop=self.t_fft / 2, t_obs=self.t_obs, n_k=self.n_k,
+                    k_min=0.0, dk=0.0, f_max=0.0, ana_lo=self.ana_lo, ana_hi=self.ana_hi,
+                    band_hz=1.0, list=list_idx)
+
+
+def track_probability(snr) -> np.ndarray:
+    """P(|X|^2 / E|noise|^2 > 2.5) for a bin holding a signal of power `snr` noise units: half a
+    non-central chi-square of 2 degrees of freedom and non-centrality 2 snr."""
+    import scipy.stats
+    return scipy.stats.ncx2.sf(2 * THETA, 2, 2 * np.asarray(snr, np.float64))
+
+
+_GRIDS: dict = {}
+
+
+def grid_of(spec: ProposerSpec, n: float) -> gfh.Grid:
+    key = (spec, n)
+    if key not in _GRIDS:
+        _GRIDS[key] = gfh.grid_make(gfh.Grid(**spec.grid_fields(n)))
+    return _GRIDS[key]
+
+
+@dataclasses.dataclass
+class Samples:
+    index: np.ndarray       # sample ids
+    n: np.ndarray
+    signal: np.ndarray      # bool
+    f0: np.ndarray
+    row: np.ndarray         # k row of the injection (-1 without)
+    k: np.ndarray
+    snr: np.ndarray
+    p_track24: np.ndarray   # uint32
+    tracks: np.ndarray      # [B][n_fft] int32 bin per FFT or -1
+    labels: np.ndarray      # int32 class
+    col: np.ndarray         # x0 column of the injection (-1 without)
+    nplane: np.ndarray      # float32
+    gain: np.ndarray        # [B][64][2] float32 (ga, gb)
+
+
+def draw(spec: ProposerSpec, index) -> Samples:
+    """Parameters, tracks and labels of samples `index` (deterministic functions of the ids)."""
+    s = np.asarray(index, np.int64)
+    u = [synth.hashed_uniform(spec.seed, s.astype(np.uint64), 2, slot) for slot in range(5)]
+    n = np.array([N_GRID[i % len(N_GRID)] for i in s])
+    signal = u[0] < spec.p_signal
+    f_top = spec.bin_hi * spec.df
+    f0 = spec.ana_lo + u[1] * (f_top - spec.ana_lo)
+    row = np.minimum((u[2] * spec.n_k).astype(np.int64), spec.n_k - 1)
+    snr = spec.snr_lo + u[3] * (spec.snr_hi - spec.snr_lo)
+    p24 = np.where(signal, np.round(track_probability(snr) * 2 ** 24), 0).astype(np.uint32)
+    B = s.size
+    tracks = np.full((B, spec.n_fft), -1, np.int32)
+    labels = np.full(B, NULL_CLASS, np.int32)
+    col = np.full(B, -1, np.int64)
+    k = np.zeros(B)
+    gain = np.zeros((B, TILES, 2), np.float32)
+    xt_w = (spec.ana_hi - spec.ana_lo) / TILES
+    fa = spec.ana_lo + xt_w * np.arange(TILES)
+    for b in range(B):
+        g = grid_of(spec, float(n[b]))
+        f_max = g.f_max
+        gain[b, :, 0] = (f_max / fa) ** n[b]
+        gain[b, :, 1] = (f_max / (fa + xt_w)) ** n[b]
+        if not signal[b]:
+            row[b] = -1
+            continue
+        k[b] = g.k_min + row[b] * g.dk
+        tr = synth.powerlaw_track(float(f0[b]), float(k[b]), float(n[b]), spec.df, spec.n_fft,
+                                  spec.t_fft / 2, spec.t_fft / 2)
+        tr[(tr < spec.bin_lo) | (tr > spec.bin_hi)] = -1
+        tracks[b] = tr
+        xt = min(TILES - 1, int((f0[b] - spec.ana_lo) / (spec.ana_hi - spec.ana_lo) * TILES))
+        d = min(TILES - 1, int(row[b] * (f0[b] / f_max) ** n[b] * TILES / spec.n_k))
+        labels[b] = d * TILES + xt
+        col[b] = int(math.floor((f0[b] ** (1.0 - n[b]) - g.x0_min) / g.dx0))
+    return Samples(s, n, signal, f0, row, k, snr, p24, tracks, labels, col,
+                   ((n - 2.0) / 5.0).astype(np.float32), gain)
+
+
+class DeviceBatch:
+    """Device buffers of one batch: images, labels, tracks, per-sample scalars."""
+
+    def __init__(self, spec: ProposerSpec, batch: int, device="cuda"):
+        import torch
+        self.torch = torch
+        self.images = torch.empty((batch, 256, 256, 2), dtype=torch.bfloat16, device=device)
+        self.labels = torch.empty(batch, dtype=torch.int32, device=device)
+        self.tracks = torch.empty((batch, spec.n_fft), dtype=torch.int32, device=device)
+        self.p24 = torch.empty(batch, dtype=torch.int32, device=device)
+        self.nplane = torch.empty(batch, dtype=torch.float32, device=device)
+        self.gain = torch.empty((batch, TILES, 2), dtype=torch.float32, device=device)
+        self.logits = torch.empty((batch, gfh.N_CLASSES), dtype=torch.float32, device=device)
+
+    def load(self, ctx: gfh.Context, spec: ProposerSpec, smp: Samples) -> int:
+        """Uploads a draw and renders its images on the GPU; returns the batch size."""
+        torch = self.torch
+        B = smp.index.size
+        self.labels[:B].copy_(torch.from_numpy(smp.labels))
+        self.tracks[:B].copy_(torch.from_numpy(smp.tracks))
+        self.p24[:B].copy_(torch.from_numpy(smp.p_track24.view(np.int32)))
+        self.nplane[:B].copy_(torch.from_numpy(smp.nplane))
+        self.gain[:B].copy_(torch.from_numpy(smp.gain))
+        assert np.all(np.diff(smp.index) == 1)
+        gfh.synth_images(ctx, spec.seed, int(smp.index[0]), spec.n_fft, spec.bin_lo, spec.bin_hi,
+                         spec.p_noise24, self.p24[:B], self.tracks[:B], self.nplane[:B],
+                         self.images[:B])
+        return B
+
+
+def train(ctx: gfh.Context, net: gfh.Cnn, spec: ProposerSpec, first: int, count: int,
+          batch: int = 256, lr: float = 2e-3, weight_decay: float = 1e-4, log=None) -> list:
+    """AdamW over samples [first, first + count) in order, cosine learning-rate decay; returns the
+    loss of every step."""
+    buf = DeviceBatch(spec, batch)
+    steps = (count + batch - 1) // batch
+    losses = []
+    for st in range(steps):
+        s0 = first + st * batch
+        B = min(batch, first + count - s0)
+        smp = draw(spec, np.arange(s0, s0 + B))
+        buf.load(ctx, spec, smp)
+        lr_t = lr * 0.5 * (1.0 + math.cos(math.pi * st / steps))
+        loss = net.train_step(buf.images[:B], buf.labels[:B], lr_t, weight_decay)
+        losses.append(loss)
+        if log and (st % 50 == 0 or st == steps - 1):
+            log(f"step {st}/{steps} loss {loss:.4f} lr {lr_t:.2e}")
+    return losses
+
+
+# ---- evaluation against the full exact Hough ---------------------------------------------------------
+
+class HoughBank:
+    """One batched plan over the 51 braking indices (map b reads list b), and one single-map plan
+    per index for full-search fallbacks; all plans share candidates buffers per map."""
+
+    def __init__(self, ctx: gfh.Context, spec: ProposerSpec, n_sel: int = 32, tile=None):
+        import torch
+        self.torch = torch
+        self.spec = spec
+        self.ctx = ctx
+        self.grids = [gfh.grid_make(gfh.Grid(**spec.grid_fields(n, i))) for i, n in enumerate(N_GRID)]
+        self.maps = [torch.empty((g.n_k, g.ld_x0), dtype=torch.int32, device="cuda") for g in self.grids]
+        self.cands = [torch.empty(g.n_bands * 64, dtype=torch.uint8, device="cuda") for g in self.grids]
+        self.plan = gfh.Plan(ctx, self.grids, self.maps, self.cands, tile=tile)
+        self.plan.set_coarse(TILES, TILES, n_sel)
+        self.n_sel = n_sel
+        self.single = []
+        for i, g in enumerate(self.grids):
+            g0 = dataclasses.replace(g, list=0)
+            self.single.append(gfh.Plan(ctx, [g0], [self.maps[i]], [self.cands[i]], tile=tile))
+        cap = int(spec.n_fft * (spec.bin_hi - spec.bin_lo + 1) * 0.1) + 4096
+        self.cap = cap
+        nl = len(N_GRID)
+        self.fft = torch.empty(nl * cap, dtype=torch.int32, device="cuda")
+        self.bin = torch.empty(nl * cap, dtype=torch.int32, device="cuda")
+        self.offsets = torch.zeros(nl + 1, dtype=torch.int64, device="cuda")
+        self.coarse = torch.full((nl, n_sel), -1, dtype=torch.int32, device="cuda")
+        self.counts = np.zeros(nl, np.int64)
+
+    def load_peaks(self, smp: Samples) -> None:
+        """Peak lists of the 51 samples smp (sample i -> list i), drawn on the GPU."""
+        spec = self.spec
+        torch = self.torch
+        tracks = torch.from_numpy(smp.tracks).cuda()
+        offs = [0]
+        for i in range(smp.index.size):
+            o = i * self.cap
+            n = gfh.synth_peaks(self.ctx, spec.seed, int(smp.index[i]), spec.n_fft, spec.bin_lo,
+                                spec.bin_hi, spec.p_noise24, int(smp.p_track24[i]), tracks[i],
+                                self.fft[o:o + self.cap], self.bin[o:o + self.cap])
+            self.counts[i] = n
+        # lists live at fixed strides; compact them so list i starts at offsets[i]
+        parts_f, parts_b = [], []
+        for i in range(smp.index.size):
+            o = i * self.cap
+            parts_f.append(self.fft[o:o + self.counts[i]])
+            parts_b.append(self.bin[o:o + self.counts[i]])
+            offs.append(offs[-1] + int(self.counts[i]))
+        self.fft_c = torch.cat(parts_f)
+        self.bin_c = torch.cat(parts_b)
+        self.offsets.copy_(torch.tensor(offs, dtype=torch.int64))
+        self.offs_host = offs
+        self.single_off = torch.tensor([[0, offs[i + 1] - offs[i]] for i in range(len(offs) - 1)],
+                                       dtype=torch.int64, device="cuda")
+
+    def updates(self) -> int:
+        """Hough updates of the full search of the loaded lists: peaks x k rows per map."""
+        return int(sum(self.counts[i] * g.n_k for i, g in enumerate(self.grids)))
+
+    def full(self) -> None:
+        self.plan.execute(self.fft_c, self.bin_c, self.offsets, len(N_GRID))
+
+    def pruned(self, coarse) -> None:
+        self.plan.execute_tiles(self.fft_c, self.bin_c, self.offsets, len(N_GRID), coarse, self.n_sel)
+
+    def full_one(self, i: int) -> None:
+        """Full exact search of map i alone (its own single-map plan)."""
+        o0, o1 = self.offs_host[i], self.offs_host[i + 1]
+        self.single[i].execute(self.fft_c[o0:o1], self.bin_c[o0:o1], self.single_off[i], 1)
+
+    def candidates(self) -> list:
+        return [gfh.candidates_to_numpy(c) for c in self.cands]
+
+
+def detected(cands: np.ndarray, col: int, row: int, radius: float = 3.0) -> bool:
+    """A candidate within distance `radius` (x0 columns, k rows) of the injection (Sec. IV)."""
+    ok = cands["count"] >= 0
+    d2 = (cands["col"][ok] - col) ** 2 + (cands["row"][ok] - row) ** 2
+    return bool(np.any(d2 <= radius * radius))
+
+
+def evaluate(ctx: gfh.Context, net: gfh.Cnn, spec: ProposerSpec, first: int, count: int,
+             bank: HoughBank, n_sel: int = 32, log=None) -> dict:
+    """Per-map records of the proposal (top n_sel coarse tiles) against the full exact Hough on
+    samples [first, first + count), in batches of 51 maps (first and count multiples of 51, so that
+    sample s lands on the bank's map s mod 51).  summarize() turns them into recall and fallback
+    rates for a threshold tau."""
+    torch = bank.torch
+    nl = len(N_GRID)
+    # sample s has braking index N_GRID[s % 51] = the grid of map s % 51 of the bank
+    assert first % nl == 0 and count % nl == 0, "evaluate whole batches of 51 maps"
+    buf = DeviceBatch(spec, nl)
+    top = torch.empty((nl, n_sel), dtype=torch.int32, device="cuda")
+    resid = torch.empty(nl, dtype=torch.float32, device="cuda")
+    rec = {k: [] for k in ("signal", "resid", "det_full", "det_pruned", "agree", "truth_in_top",
+                           "f0", "n", "row")}
+    for b0 in range(first, first + count, nl):
+        smp = draw(spec, np.arange(b0, b0 + nl))
+        buf.load(ctx, spec, smp)
+        net.forward(buf.images, buf.logits)
+        gfh.propose_tiles(ctx, buf.logits, buf.gain, n_sel, top, resid)
+        bank.load_peaks(smp)
+        bank.full()
+        full = bank.candidates()
+        bank.pruned(top)
+        pr = bank.candidates()
+        r = resid.cpu().numpy()
+        tp = top.cpu().numpy()
+        for i in range(nl):
+            rec["signal"].append(bool(smp.signal[i]))
+            rec["resid"].append(float(r[i]))
+            rec["f0"].append(float(smp.f0[i]))
+            rec["n"].append(float(smp.n[i]))
+            rec["row"].append(int(smp.row[i]))
+            if not smp.signal[i]:
+                for k in ("det_full", "det_pruned", "agree", "truth_in_top"):
+                    rec[k].append(False)
+                continue
+            kt = int(smp.row[i]) * TILES // spec.n_k
+            xt = min(TILES - 1, int((smp.f0[i] - spec.ana_lo) / (spec.ana_hi - spec.ana_lo) * TILES))
+            rec["truth_in_top"].append(kt * TILES + xt in set(tp[i].tolist()))
+            cf, cp = full[i], pr[i]
+            rec["det_full"].append(detected(cf, int(smp.col[i]), int(smp.row[i])))
+            rec["det_pruned"].append(detected(cp, int(smp.col[i]), int(smp.row[i])))
+            band = int(math.floor(smp.f0[i] - spec.ana_lo))
+            rec["agree"].append(bool(0 <= band < cf.size and cp["count"][band] == cf["count"][band]))
+        if log and ((b0 - first) // nl) % 20 == 0:
+            log(f"eval {b0 + nl - first}/{count}")
+    return {k: np.array(v) for k, v in rec.items()}
+
+
+def summarize(rec: dict, tau: float) -> dict:
+    """Recall (detections of the full search kept by the pruned search, a map whose resid exceeds
+    tau being searched in full), agreement of the injection band's top count, fallback rates."""
+    fb = rec["resid"] > tau
+    sig = rec["signal"]
+    det_full = rec["det_full"] & sig
+    kept = det_full & (fb | rec["det_pruned"])
+    agree = sig & (fb | rec["agree"])
+    return dict(tau=tau, maps=int(sig.size), injected=int(sig.sum()),
+                det_full=int(det_full.sum()), det_kept=int(kept.sum()),
+                recall=float(kept.sum() / max(1, det_full.sum())),
+                agreement=float(agree.sum() / max(1, sig.sum())),
+                fallback_frac=float(fb.mean()), fallback_injected=float(fb[sig].mean()),
+                fallback_noise=float(fb[~sig].mean()) if (~sig).any() else 0.0,
+                truth_in_top=float(rec["truth_in_top"][sig].mean()))
+
+
+def train_default(ctx: gfh.Context, net: gfh.Cnn, spec: ProposerSpec, epochs: int = 3,
+                  n_train: int = 100000, batch: int = 256, lr: float = 2e-3, log=None) -> list:
+    """The training schedule of the proposer: `epochs` passes over samples [0, n_train), each a
+    cosine decay from lr / 2^epoch."""
+    losses = []
+    for e in range(epochs):
+        losses += train(ctx, net, spec, 0, n_train, batch=batch, lr=lr * 0.5 ** e, log=log)
+    return losses
+
+
+class PrunedSearch:
+    """The proposer-guided search of the bank's 51 loaded peak lists: images from the peak lists,
+    the network, the proposals, the exact Hough on the proposed coarse tiles, and the full exact
+    Hough of every map whose proposal leaves more than tau probability outside its tiles."""
+
+    def __init__(self, ctx: gfh.Context, net: gfh.Cnn, bank: HoughBank, tau: float,
+                 n_sel: int = 32):
+        import torch
+        spec = bank.spec
+        nl = len(N_GRID)
+        self.ctx, self.net, self.bank, self.tau, self.n_sel = ctx, net, bank, tau, n_sel
+        smp = draw(spec, np.arange(nl))            # gains and n planes depend on the map slot only
+        self.gain = torch.from_numpy(smp.gain).cuda()
+        self.nplane = torch.from_numpy(smp.nplane).cuda()
+        self.images = torch.empty((nl, 256, 256, 2), dtype=torch.bfloat16, device="cuda")
+        self.logits = torch.empty((nl, gfh.N_CLASSES), dtype=torch.float32, device="cuda")
+        self.top = torch.empty((nl, n_sel), dtype=torch.int32, device="cuda")
+        self.resid = torch.empty(nl, dtype=torch.float32, device="cuda")
+        self.resid_host = torch.empty(nl, dtype=torch.float32).pin_memory()
+        self.fallbacks = 0
+
+    def propose(self) -> None:
+        spec, bank = self.bank.spec, self.bank
+        gfh.peaks_to_images(self.ctx, bank.fft_c, bank.bin_c, bank.offsets, len(N_GRID),
+                            spec.n_fft, spec.bin_lo, spec.bin_hi, self.nplane, self.images)
+        self.net.forward(self.images, self.logits)
+        gfh.propose_tiles(self.ctx, self.logits, self.gain, self.n_sel, self.top, self.resid)
+
+    def run(self) -> int:
+        """One search of the loaded lists; returns the number of maps searched in full."""
+        self.propose()
+        self.bank.pruned(self.top)
+        self.resid_host.copy_(self.resid, non_blocking=True)
+        self.bank.torch.cuda.current_stream().synchronize()
+        fb = np.nonzero(self.resid_host.numpy() > self.tau)[0]
+        for i in fb:
+            self.bank.full_one(int(i))
+        self.fallbacks += fb.size
+        return int(fb.size)

@@ -147,3 +147,62 @@ def random_peaklist(n_fft: int, bin_lo: int, bin_hi: int, density: float, seed: 
         occ[:, j] &= ~occ[:, j - 1]
     b_idx, f_idx = np.nonzero(occ.T)    # row-major over [bin][fft]: sorted by bin, then fft
     return f_idx.astype(np.uint32), (b_idx + bin_lo).astype(np.uint32)
+
+
+# ---- counter-based statistical peakmaps ------------------------------------------------------------
+#
+# The same model as statistical_peaklist, with every draw a pure function of (seed, sample, stream,
+# FFT i, bin j) so that a GPU kernel can draw any cell on its own: the splitmix64 finaliser of
+# Steele, Lea and Flood ("Fast splittable pseudorandom number generators", OOPSLA 2014) applied to
+#   key = mix(seed ^ sample * 0xD1B54A32D192ED03 ^ stream << 56),  u = mix(key ^ (i << 32 | j)) >> 40
+# (all arithmetic mod 2^64).  Cell (i, j) of a sample is a peak when u(stream 0) < p_noise24, or when
+# j is the track's bin in FFT i and u(stream 1) < p_track24 (probabilities times 2^24).
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_MIX1 = np.uint64(0xBF58476D1CE4E5B9)
+_MIX2 = np.uint64(0x94D049BB133111EB)
+_SAMPLE_MUL = np.uint64(0xD1B54A32D192ED03)
+
+
+def mix64(z) -> np.ndarray:
+    """The splitmix64 finaliser, elementwise on uint64 (wrapping arithmetic)."""
+    z = np.asarray(z, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = z + _GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * _MIX1
+        z = (z ^ (z >> np.uint64(27))) * _MIX2
+    return z ^ (z >> np.uint64(31))
+
+
+def sample_key(seed: int, sample, stream: int) -> np.ndarray:
+    s = np.asarray(sample, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        return mix64(np.uint64(seed) ^ (s * _SAMPLE_MUL) ^ (np.uint64(stream) << np.uint64(56)))
+
+
+def cell_u24(seed: int, sample, stream: int, i, j) -> np.ndarray:
+    """24-bit uniform of cell (i, j) (broadcasting over sample, i, j)."""
+    key = sample_key(seed, sample, stream)
+    lin = (np.asarray(i, dtype=np.uint64) << np.uint64(32)) | np.asarray(j, dtype=np.uint64)
+    return (mix64(key ^ lin) >> np.uint64(40)).astype(np.uint32)
+
+
+def hashed_peaklist(seed: int, sample: int, n_fft: int, bin_lo: int, bin_hi: int, p_noise24: int,
+                    p_track24: int = 0, track=None):
+    """Peak list (fft_idx, bin) of one sample, sorted by (bin, fft); track: bin per FFT or -1."""
+    j = np.arange(bin_lo, bin_hi + 1, dtype=np.uint64)[:, None]
+    i = np.arange(n_fft, dtype=np.uint64)[None, :]
+    peak = cell_u24(seed, sample, 0, i, j) < np.uint32(p_noise24)
+    if track is not None:
+        tr = np.asarray(track, dtype=np.int64)
+        ii = np.nonzero((tr >= bin_lo) & (tr <= bin_hi))[0]
+        hit = cell_u24(seed, sample, 1, ii.astype(np.uint64), tr[ii].astype(np.uint64)) < np.uint32(p_track24)
+        peak[tr[ii[hit]] - bin_lo, ii[hit]] = True
+    jj, ff = np.nonzero(peak)
+    return ff.astype(np.uint32), (jj + bin_lo).astype(np.uint32)
+
+
+def hashed_uniform(seed: int, sample, stream: int, slot: int = 0) -> np.ndarray:
+    """Uniform double in [0, 1) per sample from 53 bits of mix(key ^ slot) (sample parameters)."""
+    key = sample_key(seed, sample, stream)
+    return (mix64(key ^ np.uint64(slot)) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53

@@ -15,7 +15,7 @@ HEADER = pathlib.Path(__file__).resolve().parent.parent / "include" / "gfh.h"
 
 def declared_functions():
     text = HEADER.read_text()
-    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(gfh_\w+)\s*\(", text, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:int|int64_t|const char\*)\s+(gfh_\w+)\s*\(", text, re.M)))
 
 
 def test_every_declared_symbol_is_exported(built_lib):

@@ -1,0 +1,249 @@
+"""The proposal network's kernels against the CPU oracle: the counter-based peakmap generator and the
+images (bit-exact), each 3x3 layer's forward, input-gradient and weight-gradient kernel (within the
+fp32-accumulation and bf16-rounding bound derived below), the whole network's logits and gradients,
+one AdamW step, and the tile proposals."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import cnn_oracle as C
+from paper_1810_09784_gb300 import proposer as PR
+from paper_1810_09784_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24          # fp32 unit roundoff
+
+
+def bf16_tensor(bits: np.ndarray):
+    return torch.from_numpy(np.ascontiguousarray(bits).view(np.int16)).cuda().view(torch.bfloat16)
+
+
+def tensor_bits(t) -> np.ndarray:
+    return t.view(torch.int16).cpu().numpy().view(np.uint16)
+
+
+def rand_bf16(rng, shape, scale=1.0, relu=False):
+    v = rng.standard_normal(shape) * scale
+    if relu:
+        v = np.maximum(v, 0.0)
+    return C.bf16_bits(v)
+
+
+def ulp_bf16(v):
+    v = np.maximum(np.abs(v), 2.0 ** -126)
+    return 2.0 ** (np.floor(np.log2(v)) - 7)
+
+
+def assert_bf16_close(gpu, exact, err):
+    """gpu = bf16(a) with |a - exact| <= err: |gpu - exact| <= half an ulp of |exact| + err + err."""
+    bound = 0.5 * ulp_bf16(np.abs(exact) + err) + err
+    bad = np.abs(gpu - exact) > bound
+    assert not bad.any(), (int(bad.sum()), np.argwhere(bad)[:3], gpu[bad][:3], exact[bad][:3])
+
+
+# ---- generator and images ------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", [(300, 40, 339, 0.05, 0, None), (1799, 200, 799, 0.0755, 1 << 23, 450)])
+def test_synth_peaks_bit_exact(built_lib, gpu_ctx, case):
+    gfh = built_lib
+    n_fft, lo, hi, p, pt, tb = case
+    track = np.full(n_fft, -1, np.int32)
+    if tb is not None:
+        track[:] = tb - (np.arange(n_fft) // 7)
+    p24 = int(p * 2 ** 24)
+    cap = n_fft * (hi - lo + 1)
+    fo = torch.empty(cap, dtype=torch.int32, device="cuda")
+    bo = torch.empty(cap, dtype=torch.int32, device="cuda")
+    n = gfh.synth_peaks(gpu_ctx, 99, 12, n_fft, lo, hi, p24, pt, torch.from_numpy(track).cuda(), fo, bo)
+    rf, rb = synth.hashed_peaklist(99, 12, n_fft, lo, hi, p24, pt, track)
+    assert n == rf.size
+    assert np.array_equal(fo[:n].cpu().numpy().astype(np.uint32), rf)
+    assert np.array_equal(bo[:n].cpu().numpy().astype(np.uint32), rb)
+
+
+def test_images_bit_exact(built_lib, gpu_ctx):
+    """gfh_synth_images (cells drawn in the kernel) and gfh_peaks_to_images (from peak lists, one
+    launch for all lists) both equal the oracle's binning of the generator's peak list."""
+    gfh = built_lib
+    spec = PR.ProposerSpec()
+    smp = PR.draw(spec, np.arange(40, 46))
+    buf = PR.DeviceBatch(spec, 6)
+    buf.load(gpu_ctx, spec, smp)
+    img2 = torch.zeros((6, 256, 256, 2), dtype=torch.bfloat16, device="cuda")
+    got = tensor_bits(buf.images)
+    lists = []
+    for b in range(6):
+        rf, rb = synth.hashed_peaklist(spec.seed, int(smp.index[b]), spec.n_fft, spec.bin_lo,
+                                       spec.bin_hi, spec.p_noise24, int(smp.p_track24[b]),
+                                       smp.tracks[b])
+        ref = C.image_bits(C.image_counts(rf, rb, spec.n_fft, spec.bin_lo, spec.bin_hi),
+                           float(smp.nplane[b]))
+        assert np.array_equal(got[b], ref), b
+        lists.append((rf, rb))
+    fi = torch.from_numpy(np.concatenate([l[0] for l in lists]).view(np.int32)).cuda()
+    bj = torch.from_numpy(np.concatenate([l[1] for l in lists]).view(np.int32)).cuda()
+    off = torch.from_numpy(np.cumsum([0] + [l[0].size for l in lists]).astype(np.int64)).cuda()
+    gfh.peaks_to_images(gpu_ctx, fi, bj, off, 6, spec.n_fft, spec.bin_lo, spec.bin_hi,
+                        buf.nplane[:6], img2)
+    torch.cuda.synchronize()
+    assert np.array_equal(tensor_bits(img2), got)
+
+
+# ---- single layers ---------------------------------------------------------------------------------
+
+LAYERS = [(32, 32, 2), (32, 64, 1), (64, 64, 2), (64, 64, 1)]
+
+
+@pytest.mark.parametrize("cin,cout,S", LAYERS)
+def test_conv_forward(built_lib, gpu_ctx, cin, cout, S):
+    """relu(conv + bias) rounded to bf16: the fp32 sum of K = 9 cin + 1 terms is within
+    K u sum|terms| of the exact one (u = 2^-24), then one bf16 rounding."""
+    gfh = built_lib
+    rng = np.random.default_rng(cin + cout + S)
+    B, H = 2, 48
+    xb = rand_bf16(rng, (B, H, H, cin), relu=True)
+    wb = rand_bf16(rng, (cout, 3, 3, cin), scale=math.sqrt(2.0 / (9 * cin)))
+    bias = rng.uniform(-0.1, 0.1, cout).astype(np.float32)
+    out = torch.empty((B, H // S, H // S, cout), dtype=torch.bfloat16, device="cuda")
+    gfh.conv3x3(gpu_ctx, 0, cin, cout, S, B, H, inp=bf16_tensor(xb), w=bf16_tensor(wb),
+                bias=torch.from_numpy(bias).cuda(), res=out)
+    torch.cuda.synchronize()
+    x, W = C.bf16_value(xb), C.bf16_value(wb)
+    exact = np.maximum(C.conv3x3(x, W, S) + bias.astype(np.float64), 0.0)
+    err = (9 * cin + 1) * U32 * (C.conv3x3(np.abs(x), np.abs(W), S) + np.abs(bias))
+    assert_bf16_close(C.bf16_value(tensor_bits(out)), exact, err)
+
+
+@pytest.mark.parametrize("cin,cout,S", LAYERS)
+def test_conv_input_gradient(built_lib, gpu_ctx, cin, cout, S):
+    gfh = built_lib
+    rng = np.random.default_rng(100 + cin + cout + S)
+    B, H = 2, 48
+    Ho = H // S
+    gb = rand_bf16(rng, (B, Ho, Ho, cout), scale=0.01)
+    ob = rand_bf16(rng, (B, Ho, Ho, cout), relu=True)      # layer output: ReLU mask
+    wb = rand_bf16(rng, (cout, 3, 3, cin), scale=math.sqrt(2.0 / (9 * cin)))
+    din = torch.empty((B, H, H, cin), dtype=torch.bfloat16, device="cuda")
+    gfh.conv3x3(gpu_ctx, 1, cin, cout, S, B, H, w=bf16_tensor(wb), out=bf16_tensor(ob),
+                dout=bf16_tensor(gb), res=din)
+    torch.cuda.synchronize()
+    G = C.bf16_value(gb) * (C.bf16_value(ob) > 0)
+    W = C.bf16_value(wb)
+    exact = C.conv3x3_input_grad(G, W, S, H)
+    err = 9 * cout * U32 * C.conv3x3_input_grad(np.abs(G), np.abs(W), S, H)
+    assert_bf16_close(C.bf16_value(tensor_bits(din)), exact, err)
+
+
+@pytest.mark.parametrize("cin,cout,S", LAYERS)
+def test_conv_weight_gradient(built_lib, gpu_ctx, cin, cout, S):
+    """fp32 sums over M = B (H/S)^2 pixels (tensor-core partial sums, then fp32 atomics across
+    blocks): within (M + 64) u sum|terms| of the exact sum; bias gradient likewise."""
+    gfh = built_lib
+    rng = np.random.default_rng(200 + cin + cout + S)
+    B, H = 3, 48
+    Ho = H // S
+    xb = rand_bf16(rng, (B, H, H, cin), relu=True)
+    gb = rand_bf16(rng, (B, Ho, Ho, cout), scale=0.01)
+    ob = rand_bf16(rng, (B, Ho, Ho, cout), relu=True)
+    dw = torch.zeros((cout, 3, 3, cin), dtype=torch.float32, device="cuda")
+    db = torch.zeros(cout, dtype=torch.float32, device="cuda")
+    gfh.conv3x3(gpu_ctx, 2, cin, cout, S, B, H, inp=bf16_tensor(xb), out=bf16_tensor(ob),
+                dout=bf16_tensor(gb), res=dw, db=db)
+    torch.cuda.synchronize()
+    G = C.bf16_value(gb) * (C.bf16_value(ob) > 0)
+    x = C.bf16_value(xb)
+    M = B * Ho * Ho
+    exact = C.conv3x3_weight_grad(G, x, S)
+    err = (M + 64) * U32 * C.conv3x3_weight_grad(np.abs(G), np.abs(x), S)
+    assert np.all(np.abs(dw.cpu().numpy() - exact) <= err + 1e-30)
+    eb = G.sum(axis=(0, 1, 2))
+    errb = (M + 64) * U32 * np.abs(G).sum(axis=(0, 1, 2))
+    assert np.all(np.abs(db.cpu().numpy() - eb) <= errb + 1e-30)
+
+
+# ---- the whole network -------------------------------------------------------------------------
+
+def _batch(gpu_ctx, idx):
+    spec = PR.ProposerSpec()
+    smp = PR.draw(spec, np.asarray(idx))
+    buf = PR.DeviceBatch(spec, len(idx))
+    buf.load(gpu_ctx, spec, smp)
+    return smp, buf
+
+
+def test_network_logits_and_gradients(built_lib, gpu_ctx):
+    """The GPU network against the oracle evaluated with the same bf16 storage points.  The two
+    differ by fp32-vs-fp64 accumulation, which can move a stored bf16 value by one ulp (2^-8
+    relative); about ten stored tensors lie on each gradient path, so each parameter block must
+    agree to a few percent in relative L2 norm and in direction (cosine > 0.998)."""
+    gfh = built_lib
+    net = gfh.Cnn(gpu_ctx, 4, seed=3)
+    # a signal and a noise-only sample
+    idx = [i for i in range(0, 40) if PR.draw(PR.ProposerSpec(), [i]).signal[0]][:1] + \
+          [i for i in range(0, 40) if not PR.draw(PR.ProposerSpec(), [i]).signal[0]][:1]
+    smp, buf = _batch(gpu_ctx, idx)
+    p0 = net.params()
+    loss = net.gradients(buf.images, buf.labels)
+    g = net.grads().astype(np.float64)
+    net.forward(buf.images, buf.logits)
+    torch.cuda.synchronize()
+    img = C.bf16_value(tensor_bits(buf.images))
+    cache = C.forward(p0.astype(np.float64), img, mirror=True)
+    lo, go = C.backward(cache, smp.labels.astype(np.int64))
+    lg = buf.logits.cpu().numpy()
+    scale = np.abs(cache["logits"]).max()
+    assert np.abs(lg - cache["logits"]).max() <= 2e-2 * scale
+    assert math.isclose(loss, lo, rel_tol=1e-2)
+    off, _ = C.layout()
+    for name, (o, sh) in off.items():
+        a = g[o:o + int(np.prod(sh))]
+        b = go[o:o + int(np.prod(sh))]
+        nb = np.linalg.norm(b)
+        if nb == 0:
+            assert np.linalg.norm(a) <= 1e-6, name
+            continue
+        rel = np.linalg.norm(a - b) / nb
+        cos = float(a @ b) / (np.linalg.norm(a) * nb)
+        assert rel < 5e-2 and cos > 0.998, (name, rel, cos)
+    net.close()
+
+
+def test_adamw_step(built_lib, gpu_ctx):
+    """One AdamW step on the GPU's own gradient equals the fp64 formula within fp32 rounding."""
+    gfh = built_lib
+    net = gfh.Cnn(gpu_ctx, 2, seed=4)
+    _, buf = _batch(gpu_ctx, [7, 8])
+    p0 = net.params().astype(np.float64)
+    lr, wd = 1e-3, 1e-2
+    net.train_step(buf.images, buf.labels, lr, wd)
+    p1 = net.params().astype(np.float64)
+    g = net.grads().astype(np.float64)
+    ref, _, _ = C.adamw(p0, g, np.zeros_like(p0), np.zeros_like(p0), 1, lr, wd)
+    assert np.all(np.abs(p1 - ref) <= 8 * U32 * (np.abs(p0) + lr) + 1e-12)
+    net.close()
+
+
+def test_proposals(built_lib, gpu_ctx):
+    gfh = built_lib
+    spec = PR.ProposerSpec()
+    smp = PR.draw(spec, np.arange(100, 108))
+    rng = np.random.default_rng(9)
+    logits = (rng.standard_normal((8, gfh.N_CLASSES)) * 3).astype(np.float32)
+    logits[3, 4096] = 40.0                                     # confident "no signal"
+    lt = torch.from_numpy(logits).cuda()
+    gain = torch.from_numpy(smp.gain).cuda()
+    top = torch.empty((8, 32), dtype=torch.int32, device="cuda")
+    resid = torch.empty(8, dtype=torch.float32, device="cuda")
+    gfh.propose_tiles(gpu_ctx, lt, gain, 32, top, resid)
+    torch.cuda.synchronize()
+    tp, rs = top.cpu().numpy(), resid.cpu().numpy()
+    for b in range(8):
+        sc, pnull = C.tile_scores(logits[b].astype(np.float64), smp.gain[b].astype(np.float64))
+        kth = np.sort(sc)[::-1][31]
+        assert len(set(tp[b].tolist())) == 32
+        assert np.all(sc[tp[b]] >= kth - 1e-6 * sc.max())     # the best 32 up to fp32 near-ties
+        assert abs(rs[b] - max(0.0, 1 - pnull - sc[tp[b]].sum())) <= 1e-4
+    assert rs[3] < 1e-3

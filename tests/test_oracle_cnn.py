@@ -1,0 +1,175 @@
+"""Pins of the proposal-network oracle against what mathematics and independent library routines
+fix: cross-correlation (scipy), adjoint identities, finite differences, closed forms of the loss
+and of the optimiser, round-to-nearest-even bf16 (torch's conversion), brute-force image binning,
+mass conservation of the tile proposals, and the published first output of splitmix64."""
+import math
+
+import numpy as np
+import pytest
+import scipy.signal
+import torch
+
+from oracle import cnn_oracle as C
+from paper_1810_09784_gb300 import synth
+
+
+def test_splitmix64_published_vector():
+    # SplitMix64 seeded with 0: the first output is the finaliser of 0 + golden gamma
+    assert int(synth.mix64(np.uint64(0))) == 0xE220A8397B1DCDAF
+
+
+def test_bf16_rounding_matches_torch():
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.standard_normal(20000) * 10.0 ** rng.integers(-30, 30, 20000),
+                        [1.0, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, -0.0, 0.0, 65504.0]])
+    ref = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).view(torch.int16).numpy()
+    assert np.array_equal(C.bf16_bits(x), ref.view(np.uint16))
+    assert C.bf16_bits(1.0 + 2 ** -8) == 0x3F80          # tie to even
+    assert C.bf16_bits(1.0 + 3 * 2 ** -8) == 0x3F82
+
+
+@pytest.mark.parametrize("S", [1, 2])
+def test_conv3x3_is_cross_correlation(S):
+    rng = np.random.default_rng(S)
+    x = rng.standard_normal((2, 12, 12, 3))
+    W = rng.standard_normal((4, 3, 3, 3))
+    out = C.conv3x3(x, W, S)
+    for b in range(2):
+        for o in range(4):
+            ref = sum(scipy.signal.correlate2d(x[b, :, :, c], W[o, :, :, c], mode="same")
+                      for c in range(3))
+            np.testing.assert_allclose(out[b, :, :, o], ref[::S, ::S], rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("S", [1, 2])
+def test_conv3x3_adjoints(S):
+    rng = np.random.default_rng(10 + S)
+    x = rng.standard_normal((2, 16, 16, 5))
+    W = rng.standard_normal((6, 3, 3, 5))
+    G = rng.standard_normal((2, 16 // S, 16 // S, 6))
+    y = C.conv3x3(x, W, S)
+    lhs = float((y * G).sum())
+    assert math.isclose(lhs, float((x * C.conv3x3_input_grad(G, W, S, 16)).sum()), rel_tol=1e-11)
+    assert math.isclose(lhs, float((W * C.conv3x3_weight_grad(G, x, S)).sum()), rel_tol=1e-11)
+
+
+def test_softmax_ce_closed_forms():
+    logits = np.zeros((3, 257))
+    loss, d = C.softmax_ce(logits, np.array([0, 5, 256]))
+    np.testing.assert_allclose(loss, math.log(257), rtol=1e-14)
+    np.testing.assert_allclose(d.sum(axis=1), 0.0, atol=1e-15)
+    assert math.isclose(d[1, 5], (1 / 257 - 1) / 3, rel_tol=1e-12)
+
+
+def test_head_against_loops():
+    rng = np.random.default_rng(3)
+    pooled = rng.standard_normal((2, 5, 64))
+    WH = rng.standard_normal((64, 3, 64))
+    bH = rng.standard_normal(64)
+    out = C.head(pooled, WH, bH, 0.25)
+    for b in range(2):
+        for kt in (0, 17, 63):
+            for f in range(5):
+                s = bH[kt]
+                for d in range(3):
+                    if 0 <= f + d - 1 < 5:
+                        s += WH[kt, d] @ pooled[b, f + d - 1]
+                assert math.isclose(out[b, kt * 5 + f], s, rel_tol=1e-12, abs_tol=1e-12)
+    assert np.all(out[:, -1] == 0.25)
+
+
+def _small_params(seed):
+    off, total = C.layout()
+    rng = np.random.default_rng(seed)
+    p = np.zeros(total)
+    for l in range(5):
+        o, sh = off[f"W{l + 1}"]
+        p[o:o + np.prod(sh)] = rng.uniform(-1, 1, np.prod(sh)) * math.sqrt(6.0 / (9 * C.CIN[l]))
+        o, sh = off[f"b{l + 1}"]
+        p[o:o + np.prod(sh)] = rng.uniform(0.0, 0.1, np.prod(sh))
+    o, sh = off["WH"]
+    p[o:o + np.prod(sh)] = rng.uniform(-1, 1, np.prod(sh)) * 0.1
+    return p
+
+
+def test_network_gradient_finite_differences():
+    """Directional derivative of the exact (fp64) loss against the oracle's backward pass."""
+    rng = np.random.default_rng(5)
+    params = _small_params(5)
+    images = rng.uniform(0, 2, (2, 16, 16, 2))
+    labels = np.array([3 * 4 + 1, 64 * 4])
+    cache = C.forward(params, images, mirror=False)
+    loss, g = C.backward(cache, labels)
+    for trial in range(3):
+        v = rng.standard_normal(params.size)
+        eps = 1e-6
+        lp, _ = C.softmax_ce(C.forward(params + eps * v, images, mirror=False)["logits"], labels)
+        lm, _ = C.softmax_ce(C.forward(params - eps * v, images, mirror=False)["logits"], labels)
+        fd = (lp.mean() - lm.mean()) / (2 * eps)
+        assert math.isclose(fd, float(g @ v), rel_tol=1e-6, abs_tol=1e-9)
+    # each block on its own (a wrong index in one layer's gradient cannot hide behind the others)
+    off, _ = C.layout()
+    for name, (o, sh) in off.items():
+        v = np.zeros(params.size)
+        v[o:o + np.prod(sh)] = rng.standard_normal(np.prod(sh))
+        eps = 1e-6
+        lp, _ = C.softmax_ce(C.forward(params + eps * v, images, mirror=False)["logits"], labels)
+        lm, _ = C.softmax_ce(C.forward(params - eps * v, images, mirror=False)["logits"], labels)
+        fd = (lp.mean() - lm.mean()) / (2 * eps)
+        assert math.isclose(fd, float(g @ v), rel_tol=1e-5, abs_tol=1e-9), name
+
+
+def test_adamw_first_step_closed_form():
+    w = np.array([1.0, -2.0, 0.5])
+    g = np.array([0.3, -4.0, 1e-3])
+    w1, m, v = C.adamw(w, g, np.zeros(3), np.zeros(3), 1, lr=0.01, wd=0.0)
+    # bias-corrected first step: m/c1 = g, sqrt(v/c2) = |g|
+    np.testing.assert_allclose(w1, w - 0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12)
+    w2, _, _ = C.adamw(w, np.zeros(3), np.zeros(3), np.zeros(3), 1, lr=0.01, wd=0.1)
+    np.testing.assert_allclose(w2, w * (1 - 0.001), rtol=1e-12)
+
+
+def test_image_counts_brute_force():
+    n_fft, lo, hi = 300, 40, 339       # 300 FFTs, 300 bins over 256 pixels: uneven ranges
+    f, b = synth.hashed_peaklist(7, 3, n_fft, lo, hi, int(0.05 * 2 ** 24))
+    counts = C.image_counts(f, b, n_fft, lo, hi)
+    ref = np.zeros((256, 256), np.int64)
+    for fi, bj in zip(f.tolist(), b.tolist()):
+        tb = next(t for t in range(256) if t * n_fft // 256 <= fi < (t + 1) * n_fft // 256)
+        fb = next(x for x in range(256) if x * 300 // 256 <= bj - lo < (x + 1) * 300 // 256)
+        ref[tb, fb] += 1
+    assert np.array_equal(counts, ref)
+    assert counts.sum() == f.size
+    bits = C.image_bits(counts, 0.6)
+    assert np.all(bits[..., 1] == C.bf16_bits(np.float32(0.6)))
+    assert np.all(C.bf16_value(bits[..., 0])[counts == 0] == 0.0)
+
+
+def test_hashed_peaklist_density_and_track():
+    p24 = int(0.0755 * 2 ** 24)
+    f, b = synth.hashed_peaklist(1, 0, 1799, 200, 799, p24)
+    cells = 1799 * 600
+    p = p24 / 2 ** 24
+    assert abs(f.size - cells * p) < 5 * math.sqrt(cells * p * (1 - p))
+    assert np.all(np.diff(b.astype(np.int64) * 1799 + f) > 0)      # sorted by (bin, fft), unique
+    track = np.full(1799, -1)
+    track[::2] = 500
+    f2, b2 = synth.hashed_peaklist(1, 0, 1799, 200, 799, p24, 1 << 24, track)
+    on = (b2 == 500) & (f2 % 2 == 0)
+    assert on.sum() == 900                                           # p_track = 1: every cell
+
+
+def test_proposal_mass_and_identity_gain():
+    rng = np.random.default_rng(2)
+    logits = rng.standard_normal(4097) * 3
+    gain = np.stack([np.linspace(3.0, 1.0, 64), np.linspace(2.5, 0.9, 64)], axis=1)
+    sc, pnull = C.tile_scores(logits, gain)
+    assert math.isclose(sc.sum() + pnull, 1.0, rel_tol=1e-12)
+    # ga = gb = 1: class (d, xt) is k tile d of x0 tile xt
+    sc1, _ = C.tile_scores(logits, np.ones((64, 2)))
+    p = np.exp(logits - logits.max())
+    p /= p.sum()
+    np.testing.assert_allclose(sc1, p[:4096], rtol=1e-12)
+    top, resid = C.propose(logits, np.ones((64, 2)), 32)
+    assert list(top) == list(np.argsort(-p[:4096], kind="stable")[:32])
+    assert math.isclose(resid, max(0.0, 1 - p[4096] - p[top].sum()), rel_tol=1e-9, abs_tol=1e-12)
