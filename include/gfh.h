@@ -317,12 +317,15 @@ int gfh_cnn_train_step(gfh_cnn* net, const void* d_images, const int32_t* d_labe
  * Coarse-tile proposals from logits [batch][4097]: p = softmax(logits); class (d, xt) spreads p
  * evenly over k tiles kt in [floor(d gb), max(lo, ceil((d + 1) ga) - 1)] (both clamped to 63),
  * with d_gain [batch][64][2] = (ga, gb) = ((f_max / f_a)^n, (f_max / f_b)^n) for x0 tile xt over
- * [f_a, f_b).  Writes the k best coarse tiles kt * 64 + xt per map to d_top [batch][k] (score
- * descending, ties to the lower id; NaN scores rank last) and d_resid [batch] = max(0, 1 -
- * p(no signal) - their score sum): the probability the proposal misses a track.  Asynchronous.
+ * [f_a, f_b).  Tiles kt * 64 + xt are ranked by score (descending, ties to the lower id; NaN
+ * scores last); the first n leave resid_n = max(0, 1 - p(no signal) - their score sum), the
+ * probability that the proposal misses a track.  tau >= 0: d_top [batch][k] keeps the first n
+ * tiles for the smallest n <= k with resid_n <= tau (the rest -1); d_resid = resid_n; d_full (may
+ * be NULL) = 1 where even resid_k > tau (the map needs the full search).  tau < 0: all k tiles,
+ * resid_k, d_full = 0.  Asynchronous.
  */
 int gfh_propose_tiles(gfh_ctx* ctx, const float* d_logits, int32_t batch, const float* d_gain,
-                      int32_t k, int32_t* d_top, float* d_resid);
+                      int32_t k, float tau, int32_t* d_top, float* d_resid, int32_t* d_full);
 
 /*
  * One 3x3 layer alone (tests): mode 0 forward out = relu(conv(in) + bias) into d_res (bf16 NHWC);
@@ -343,15 +346,20 @@ int gfh_conv3x3(gfh_ctx* ctx, int32_t mode, int32_t cin, int32_t cout, int32_t s
  * every coarse tile, column ranges widened to multiples of 4; it must follow gfh_plan_create and may
  * be called again (an autotuned plan rebuilds them itself).  max_sel bounds n_sel below.
  * gfh_plan_execute_tiles computes the cells of the coarse tiles listed in d_coarse [n_maps][n_sel]
- * (device; ids outside [0, coarse_k coarse_x), e.g. -1, select nothing) exactly as gfh_plan_execute
- * does, and writes no other cell.  Candidates are the best computed cell of each band (count -1
- * where no cell of the band was computed).  cr and the statistics come from sums over the computed
- * cells only (a cell computed twice counts twice) with the map's full cell count: they are not
- * comparable with those of gfh_plan_execute.  Asynchronous, allocation-free, capturable.
+ * (device; ids outside [0, coarse_k coarse_x), e.g. -1, select nothing; an id listed twice for a
+ * map is computed twice, and lists longer than the plan's tile capacity set the capacity flag
+ * (gfh_check: GFH_ERR_SIZE) and are cut) exactly as gfh_plan_execute
+ * does, and writes no other cell; a map with d_full[m] != 0 (d_full: device [n_maps], may be NULL)
+ * is searched in full instead, exactly as by gfh_plan_execute.  All selected tiles of all maps run
+ * in one launch of persistent blocks.  Candidates are the best computed cell of each band (count
+ * -1 where no cell of the band was computed).  cr and the statistics come from sums over the
+ * computed cells only (a cell computed twice counts twice) with the map's full cell count: they
+ * are comparable with those of gfh_plan_execute only for maps searched in full.  Asynchronous,
+ * allocation-free, capturable.
  */
 int gfh_plan_set_coarse(gfh_plan* plan, int32_t coarse_k, int32_t coarse_x, int32_t max_sel);
 int gfh_plan_execute_tiles(gfh_plan* plan, const gfh_peaks* peaks, const int32_t* d_coarse,
-                           int32_t n_sel);
+                           int32_t n_sel, const int32_t* d_full);
 
 /* ---- allocation-free entry point -------------------------------------------------------------
  *

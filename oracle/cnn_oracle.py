@@ -20,8 +20,9 @@ What is written here is the plain definition of each step:
   loss       mean softmax cross-entropy
   AdamW      m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2; w -= lr (m/c1 / (sqrt(v/c2) + eps) + wd w)
   proposal   p = softmax(logits); class (d, xt) spreads p evenly over k tiles
-             [floor(d gb), max(lo, ceil((d+1) ga) - 1)] (clamped to 63); the k best tiles, ties to the
-             lower id; resid = max(0, 1 - p_null - their sum)
+             [floor(d gb), max(lo, ceil((d+1) ga) - 1)] (clamped to 63); tiles ranked by score, ties
+             to the lower id; the first n leave resid_n = max(0, 1 - p_null - their sum); with
+             tau >= 0 the list stops at the first n with resid_n <= tau
 
 `forward(..., mirror=True)` rounds the tensors the kernels store in bf16 (activations, activation
 gradients, the bf16 weight copies) at the same points, in fp64 otherwise; with
@@ -251,7 +252,18 @@ def tile_scores(logits: np.ndarray, gain: np.ndarray):
     return sc.reshape(-1), p[TILES * TILES]
 
 
-def propose(logits: np.ndarray, gain: np.ndarray, k: int):
+def propose(logits: np.ndarray, gain: np.ndarray, k: int, tau: float = -1.0):
+    """(tiles, resid, full): the ranked tiles (cut at the first n with resid_n <= tau when
+    tau >= 0, padded with -1 to k), resid of the kept list, and whether even k tiles leave more
+    than tau."""
     sc, pnull = tile_scores(logits, gain)
     order = sorted(range(sc.size), key=lambda c: (-sc[c], c))[:k]
-    return np.array(order), max(0.0, 1.0 - pnull - sc[order].sum())
+    cum, n, res = 0.0, k, 1.0
+    for q in range(k):
+        cum += max(sc[order[q]], 0.0)
+        res = max(0.0, 1.0 - pnull - cum)
+        if tau >= 0 and res <= tau:
+            n = q + 1
+            break
+    tiles = np.array(order[:n] + [-1] * (k - n))
+    return tiles, res, bool(tau >= 0 and res > tau)

@@ -116,20 +116,23 @@ __global__ void k_image_finish(uint32_t* __restrict__ img, const float* __restri
 // observation, in units of K / 64 bins, lies in [d, d + 1); on x0 tile xt (f0 in [f_a, f_b)) that
 // is k tiles [floor(d gb), ceil((d + 1) ga) - 1] with ga = (f_max / f_a)^n, gb = (f_max / f_b)^n,
 // since one k row drifts (f0 / f_max)^n bins.  Each class spreads its probability evenly over its
-// k tiles; the k best tiles (ties to the lower id kt * 64 + xt) go to top, and resid = 1 - p(null)
-// - their score sum (at least 0).
-__global__ void k_propose(const float* __restrict__ logits, const float* __restrict__ gain, int k,
-                          int32_t* __restrict__ top, float* __restrict__ resid) {
-  constexpr int NT = 256, NCT = kTiles * kTiles, PER = NCT / NT;
+// k tiles.  The tiles are ranked by score (ties to the lower id kt * 64 + xt; bitonic sort in
+// shared memory); the first n tiles leave resid_n = max(0, 1 - p(null) - their score sum).  With
+// tau >= 0 the list stops at the smallest n <= k with resid_n <= tau (the rest of top is -1), and a
+// map whose resid_k exceeds tau is flagged for a full search; with tau < 0 all k tiles are kept.
+__global__ void __launch_bounds__(256) k_propose(const float* __restrict__ logits,
+                                                 const float* __restrict__ gain, int k, float tau,
+                                                 int32_t* __restrict__ top,
+                                                 float* __restrict__ resid,
+                                                 int32_t* __restrict__ full) {
+  constexpr int NT = 256, NCT = kTiles * kTiles;
   __shared__ float pr[NCT];                // p(d, xt) at d * 64 + xt
-  __shared__ float sc[NCT];                // score of coarse tile kt * 64 + xt
-  __shared__ unsigned char taken[NCT];
+  __shared__ float sc[NCT];                // score, then sorted scores
+  __shared__ uint16_t id[NCT];             // tile id kt * 64 + xt, sorted with sc
   __shared__ float ga[kTiles], gb[kTiles];
-  __shared__ float rv[NT / 32];
-  __shared__ int ri[NT / 32];
   __shared__ float red[NT];
   const float* l = logits + (int64_t)blockIdx.x * kClasses;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
   if (tid < kTiles) {
     ga[tid] = gain[((int64_t)blockIdx.x * kTiles + tid) * 2];
     gb[tid] = gain[((int64_t)blockIdx.x * kTiles + tid) * 2 + 1];
@@ -153,7 +156,7 @@ __global__ void k_propose(const float* __restrict__ logits, const float* __restr
     __syncthreads();
   }
   const float lse = mx + logf(red[0]);
-  for (int c = tid; c < NCT; c += NT) { pr[c] = expf(l[c] - lse); taken[c] = 0; }
+  for (int c = tid; c < NCT; c += NT) pr[c] = expf(l[c] - lse);
   __syncthreads();
   for (int c = tid; c < NCT; c += NT) {
     const int kt = c / kTiles, xt = c % kTiles;
@@ -164,37 +167,43 @@ __global__ void k_propose(const float* __restrict__ logits, const float* __restr
       if (kt >= lo && kt <= hi) s += pr[d * kTiles + xt] / (float)(hi - lo + 1);
     }
     sc[c] = isnan(s) ? -INFINITY : s;
+    id[c] = (uint16_t)c;
   }
   __syncthreads();
-  float picked = 0.f;
-  for (int q = 0; q < k; ++q) {
-    float bv = 0.f;
-    int bi = -1;
-    for (int e = 0; e < PER; ++e) {
-      const int c = e * NT + tid;
-      if (taken[c]) continue;
-      if (bi < 0 || sc[c] > bv || (sc[c] == bv && c < bi)) { bv = sc[c]; bi = c; }
+  // bitonic sort: higher score first, ties to the lower id
+  for (int kk = 2; kk <= NCT; kk <<= 1) {
+    for (int j = kk >> 1; j > 0; j >>= 1) {
+      for (int i = tid; i < NCT; i += NT) {
+        const int o = i ^ j;
+        if (o > i) {
+          const float si = sc[i], so = sc[o];
+          const int ii = id[i], io = id[o];
+          const bool o_first = so > si || (so == si && io < ii);
+          if (((i & kk) == 0) ? o_first : !o_first) {
+            sc[i] = so; sc[o] = si;
+            id[i] = (uint16_t)io; id[o] = (uint16_t)ii;
+          }
+        }
+      }
+      __syncthreads();
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float ov = __shfl_xor_sync(0xffffffffu, bv, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (oi >= 0 && (bi < 0 || ov > bv || (ov == bv && oi < bi))) { bv = ov; bi = oi; }
-    }
-    if (lane == 0) { rv[warp] = bv; ri[warp] = bi; }
-    __syncthreads();
-    if (tid == 0) {
-      float b2 = rv[0];
-      int i2 = ri[0];
-      for (int w = 1; w < NT / 32; ++w)
-        if (ri[w] >= 0 && (i2 < 0 || rv[w] > b2 || (rv[w] == b2 && ri[w] < i2))) { b2 = rv[w]; i2 = ri[w]; }
-      top[(int64_t)blockIdx.x * k + q] = i2;
-      taken[i2] = 1;
-      picked += fmaxf(b2, 0.f);
-    }
-    __syncthreads();
   }
-  if (tid == 0) resid[blockIdx.x] = fmaxf(0.f, 1.f - expf(l[kClasses - 1] - lse) - picked);
+  __shared__ int n_keep;
+  if (tid == 0) {
+    const float pnull = expf(l[kClasses - 1] - lse);
+    float cum = 0.f, res = 1.f;
+    int n = k;
+    for (int q = 0; q < k; ++q) {
+      cum += fmaxf(sc[q], 0.f);
+      res = fmaxf(0.f, 1.f - pnull - cum);
+      if (tau >= 0.f && res <= tau) { n = q + 1; break; }
+    }
+    n_keep = n;
+    resid[blockIdx.x] = res;
+    if (full) full[blockIdx.x] = (tau >= 0.f && res > tau) ? 1 : 0;
+  }
+  __syncthreads();
+  for (int q = tid; q < k; q += NT) top[(int64_t)blockIdx.x * k + q] = q < n_keep ? (int32_t)id[q] : -1;
 }
 
 // ---- tensor-core helpers --------------------------------------------------------------------------
@@ -999,12 +1008,13 @@ extern "C" int gfh_peaks_to_images(gfh_ctx* ctx, const gfh_peaks* peaks, int32_t
 }
 
 extern "C" int gfh_propose_tiles(gfh_ctx* ctx, const float* d_logits, int32_t batch,
-                                 const float* d_gain, int32_t k, int32_t* d_top, float* d_resid) {
+                                 const float* d_gain, int32_t k, float tau, int32_t* d_top,
+                                 float* d_resid, int32_t* d_full) {
   if (!ctx || !d_logits || !d_gain || !d_top || !d_resid || batch < 1 || k < 1 ||
-      k > kTiles * kTiles)
+      k > kTiles * kTiles || !(tau == tau))
     return GFH_ERR_ARG;
   GFH_CUDA_TRY(cudaSetDevice(ctx->device));
-  k_propose<<<batch, 256, 0, ctx->stream>>>(d_logits, d_gain, k, d_top, d_resid);
+  k_propose<<<batch, 256, 0, ctx->stream>>>(d_logits, d_gain, k, tau, d_top, d_resid, d_full);
   GFH_CUDA_TRY(cudaGetLastError());
   return GFH_OK;
 }

@@ -2,6 +2,7 @@
 // plans.  Compiled with -ffp-contract=off so that every double expression rounds exactly as
 // written (no fused multiply-add), which the bit-exact tables rely on.
 #include <algorithm>
+#include <functional>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -225,6 +226,37 @@ void tile_bins(const gfh_grid& g, const HostMap& hm, int64_t s_min, int64_t s_ma
   *jb = g.bin_lo + b;
 }
 
+// Tiles of map m covering rows [r0, r1) x columns [c_lo, c_hi) (c_lo, c_hi multiples of 4) with
+// the plan's tile shape; appended to `tiles`.
+void map_tiles(const gfh_grid& g, const HostMap& hm, int m, const gfh_tile_config& tc, int r0,
+               int r1, int64_t c_lo, int64_t c_hi, std::vector<TileDev>& tiles, int& max_bands) {
+  for (int rr = r0; rr < r1; rr += tc.rows) {
+    const int nr = std::min(tc.rows, r1 - rr);
+    // B and S are non-decreasing in i (k_min >= 0, dk > 0, t_i non-decreasing), so the smallest
+    // shift of the row block is at (i = 0, rr) and the largest at (last i, last row).
+    const int64_t s_min = hm.B[0] + (int64_t)rr * hm.S[0];
+    const int64_t s_max = hm.B[g.n_fft - 1] + (int64_t)(rr + nr - 1) * hm.S[g.n_fft - 1];
+    for (int64_t c0 = c_lo; c0 < c_hi; c0 += tc.cols) {
+      TileDev t{};
+      t.map = m;
+      t.row0 = rr;
+      t.nrows = nr;
+      t.col0 = c0;
+      t.ncols = (int32_t)std::min<int64_t>(tc.cols, c_hi - c0);
+      tile_bins(g, hm, s_min, s_max, c0, c0 + t.ncols, &t.bin_a, &t.bin_b);
+      t.band_lo = INT32_MAX;
+      t.band_hi = -1;
+      for (int64_t c = c0; c < c0 + t.ncols; ++c) {
+        const int32_t b = hm.band[c];
+        if (b >= 0) { t.band_lo = std::min(t.band_lo, b); t.band_hi = std::max(t.band_hi, b); }
+      }
+      if (t.band_hi < 0) t.band_lo = 0;
+      else max_bands = std::max(max_bands, t.band_hi - t.band_lo + 1);
+      tiles.push_back(t);
+    }
+  }
+}
+
 }  // namespace
 
 extern "C" int gfh_plan_destroy(gfh_plan* p) {
@@ -276,31 +308,7 @@ extern "C" int gfh_plan_create(gfh_ctx* ctx, int32_t n_maps, const gfh_grid* gri
     hm.cells = ana_cols * g.n_k;
     csr_entries += (size_t)(g.bin_hi - g.bin_lo + 2);
     if (((uintptr_t)h_maps[m]) % 16) return GFH_ERR_ARG;  // 16-byte vector stores
-    for (int r0 = 0; r0 < g.n_k; r0 += tc.rows) {
-      const int nr = std::min(tc.rows, g.n_k - r0);
-      // B and S are non-decreasing in i (k_min >= 0, dk > 0, t_i non-decreasing), so the
-      // smallest shift of the row block is at (i = 0, r0) and the largest at (last i, last row).
-      const int64_t s_min = hm.B[0] + (int64_t)r0 * hm.S[0];
-      const int64_t s_max = hm.B[g.n_fft - 1] + (int64_t)(r0 + nr - 1) * hm.S[g.n_fft - 1];
-      for (int64_t c0 = 0; c0 < g.ld_x0; c0 += tc.cols) {
-        TileDev t{};
-        t.map = m;
-        t.row0 = r0;
-        t.nrows = nr;
-        t.col0 = c0;
-        t.ncols = (int32_t)std::min<int64_t>(tc.cols, g.ld_x0 - c0);
-        tile_bins(g, hm, s_min, s_max, c0, c0 + t.ncols, &t.bin_a, &t.bin_b);
-        t.band_lo = INT32_MAX;
-        t.band_hi = -1;
-        for (int64_t c = c0; c < c0 + t.ncols; ++c) {
-          const int32_t b = hm.band[c];
-          if (b >= 0) { t.band_lo = std::min(t.band_lo, b); t.band_hi = std::max(t.band_hi, b); }
-        }
-        if (t.band_hi < 0) t.band_lo = 0;
-        else max_tile_bands = std::max(max_tile_bands, t.band_hi - t.band_lo + 1);
-        tiles.push_back(t);
-      }
-    }
+    map_tiles(g, hm, m, tc, 0, g.n_k, 0, g.ld_x0, tiles, max_tile_bands);
   }
   // The tile must fit in shared memory (layout of k_hough: tile, row-0 chunk sums, band keys).
   const bool select = h_cands != nullptr || d_stats != nullptr;
@@ -437,11 +445,11 @@ extern "C" int gfh_plan_set_coarse(gfh_plan* p, int32_t coarse_k, int32_t coarse
       (int64_t)max_sel > (int64_t)coarse_k * coarse_x)
     return GFH_ERR_ARG;
   const int nct = coarse_k * coarse_x;
-  const int R = p->cfg.rows, C = p->cfg.cols;
   std::vector<TileDev> fine;
   std::vector<int32_t> first;
-  first.reserve((size_t)p->n_maps * nct + 1);
+  first.reserve((size_t)p->n_maps * (nct + 1) + 1);
   int max_fine = 0, max_bands = p->max_tile_bands;
+  size_t worst = 0;                        // longest gathered list: every map at its largest
   for (int m = 0; m < p->n_maps; ++m) {
     const gfh_grid& g = p->grids[m];
     HostMap hm;
@@ -460,55 +468,47 @@ extern "C" int gfh_plan_set_coarse(gfh_plan* p, int32_t coarse_k, int32_t coarse
       cmin[xt] = std::min(cmin[xt], c);
       cmax[xt] = std::max(cmax[xt], c);
     }
+    std::vector<int> sizes;
     for (int kt = 0; kt < coarse_k; ++kt) {
       // rows r with floor(r coarse_k / K) = kt
       const int r0 = (int)(((int64_t)kt * g.n_k + coarse_k - 1) / coarse_k);
       const int r1 = (int)(((int64_t)(kt + 1) * g.n_k + coarse_k - 1) / coarse_k);
       for (int xt = 0; xt < coarse_x; ++xt) {
         first.push_back((int32_t)fine.size());
-        if (r1 <= r0 || cmax[xt] < 0) continue;
-        // 16-byte aligned column range (vector stores): neighbouring tiles may share <= 3 columns
-        const int64_t c_lo = cmin[xt] & ~int64_t(3);
-        const int64_t c_hi = std::min<int64_t>(g.ld_x0, (cmax[xt] + 4) & ~int64_t(3));
-        int cnt = 0;
-        for (int rr = r0; rr < r1; rr += R) {
-          const int nr = std::min(R, r1 - rr);
-          const int64_t s_min = hm.B[0] + (int64_t)rr * hm.S[0];
-          const int64_t s_max = hm.B[g.n_fft - 1] + (int64_t)(rr + nr - 1) * hm.S[g.n_fft - 1];
-          for (int64_t c0 = c_lo; c0 < c_hi; c0 += C) {
-            TileDev t{};
-            t.map = m;
-            t.row0 = rr;
-            t.nrows = nr;
-            t.col0 = c0;
-            t.ncols = (int32_t)std::min<int64_t>(C, c_hi - c0);
-            tile_bins(g, hm, s_min, s_max, c0, c0 + t.ncols, &t.bin_a, &t.bin_b);
-            t.band_lo = INT32_MAX;
-            t.band_hi = -1;
-            for (int64_t c = c0; c < c0 + t.ncols; ++c) {
-              const int32_t b = hm.band[c];
-              if (b >= 0) { t.band_lo = std::min(t.band_lo, b); t.band_hi = std::max(t.band_hi, b); }
-            }
-            if (t.band_hi < 0) t.band_lo = 0;
-            else max_bands = std::max(max_bands, t.band_hi - t.band_lo + 1);
-            fine.push_back(t);
-            ++cnt;
-          }
+        const size_t before = fine.size();
+        if (r1 > r0 && cmax[xt] >= 0) {
+          // 16-byte aligned column range (vector stores): neighbouring tiles may share <= 3 columns
+          const int64_t c_lo = cmin[xt] & ~int64_t(3);
+          const int64_t c_hi = std::min<int64_t>(g.ld_x0, (cmax[xt] + 4) & ~int64_t(3));
+          map_tiles(g, hm, m, p->cfg, r0, r1, c_lo, c_hi, fine, max_bands);
         }
+        const int cnt = (int)(fine.size() - before);
         max_fine = std::max(max_fine, cnt);
+        sizes.push_back(cnt);
       }
     }
+    // group nct: the whole map, as gfh_plan_execute tiles it
+    first.push_back((int32_t)fine.size());
+    const size_t before = fine.size();
+    map_tiles(g, hm, m, p->cfg, 0, g.n_k, 0, g.ld_x0, fine, max_bands);
+    const size_t whole = fine.size() - before;
+    std::sort(sizes.begin(), sizes.end(), std::greater<int>());
+    size_t top = 0;
+    for (int i = 0; i < max_sel && i < (int)sizes.size(); ++i) top += sizes[i];
+    worst += std::max(whole, top);
   }
   first.push_back((int32_t)fine.size());
-  if ((int64_t)p->n_maps * max_sel * std::max(max_fine, 1) > INT32_MAX) return GFH_ERR_SIZE;
-  const size_t smem = (size_t)R * (C + 2) * 4 + 32 * 4 + (p->select ? (size_t)max_bands * 8 : 0);
+  if (fine.size() > (size_t)INT32_MAX || worst > (size_t)INT32_MAX) return GFH_ERR_SIZE;
+  const size_t smem = (size_t)p->cfg.rows * (p->cfg.cols + 2) * 4 + 32 * 4 +
+                      (p->select ? (size_t)max_bands * 8 : 0);
   if (smem > 227 * 1024) return GFH_ERR_SIZE;
 
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
   const size_t o_fine = take(sizeof(TileDev) * std::max<size_t>(fine.size(), 1));
   const size_t o_first = take(sizeof(int32_t) * first.size());
-  const size_t o_sel = take(sizeof(TileDev) * (size_t)p->n_maps * max_sel * std::max(max_fine, 1));
+  const size_t o_sel = take(sizeof(TileDev) * std::max<size_t>(worst, 1));
+  const size_t o_cnt = take(2 * sizeof(int));
   GFH_CUDA_TRY(cudaSetDevice(p->ctx->device));
   if (p->ctx->stream) GFH_CUDA_TRY(cudaStreamSynchronize(p->ctx->stream));
   void* buf = nullptr;
@@ -525,6 +525,8 @@ extern "C" int gfh_plan_set_coarse(gfh_plan* p, int32_t coarse_k, int32_t coarse
   p->d_fine = (TileDev*)(base + o_fine);
   p->d_coarse_first = (int32_t*)(base + o_first);
   p->d_sel_tiles = (TileDev*)(base + o_sel);
+  p->d_sel_count = (int*)(base + o_cnt);
+  p->sel_cap = (int)std::max<size_t>(worst, 1);
   p->coarse_k = coarse_k;
   p->coarse_x = coarse_x;
   p->max_sel = max_sel;
@@ -534,13 +536,13 @@ extern "C" int gfh_plan_set_coarse(gfh_plan* p, int32_t coarse_k, int32_t coarse
 }
 
 extern "C" int gfh_plan_execute_tiles(gfh_plan* p, const gfh_peaks* peaks, const int32_t* d_coarse,
-                                      int32_t n_sel) {
+                                      int32_t n_sel, const int32_t* d_full) {
   if (!p || !peaks || !peaks->fft_idx || !peaks->bin || !peaks->offsets || peaks->n_lists < 1 ||
       p->coarse_k < 1 || n_sel < 0 || n_sel > p->max_sel || (n_sel > 0 && !d_coarse))
     return GFH_ERR_ARG;
   for (const gfh_grid& g : p->grids)
     if (g.list < 0 || g.list >= peaks->n_lists) return GFH_ERR_ARG;
-  return gfh_launch_plan_tiles(p, peaks, d_coarse, n_sel);
+  return gfh_launch_plan_tiles(p, peaks, d_coarse, n_sel, d_full);
 }
 
 // ---- autotuner ----------------------------------------------------------------------------------

@@ -15,6 +15,7 @@
 namespace {
 
 constexpr int kLane = 32;
+constexpr size_t kListStaticSmem = 64;   // bound on k_hough_list's static shared memory
 
 __device__ __forceinline__ int warp_sum(int v) {
 #pragma unroll
@@ -161,14 +162,12 @@ __device__ __forceinline__ void draw_peak(int* G0, int lds, int64_t a, int64_t b
 //
 // Shared memory: G[R][C+2] | tot[32] row-0 chunk sums | skey[bands] candidate keys.
 template <int R, int NT, bool SELECT>
-__global__ void __launch_bounds__(NT, R <= 4 ? 3 : (R == 8 ? 2 : 1))
-k_hough(const MapDev* __restrict__ maps, const TileDev* __restrict__ tiles,
-        const uint32_t* __restrict__ fft_idx, const uint32_t* __restrict__ bins,
-        unsigned int* __restrict__ flag, int c_max) {
-  extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void hough_tile(const MapDev* __restrict__ maps, const TileDev t,
+                                           const uint32_t* __restrict__ fft_idx,
+                                           const uint32_t* __restrict__ bins,
+                                           unsigned int* __restrict__ flag, int c_max,
+                                           unsigned char* smem) {
   constexpr int NW = NT / kLane;
-  const TileDev t = tiles[blockIdx.x];
-  if (t.nrows <= 0) return;                      // an unused slot of a coarse-tile launch
   const MapDev& md = maps[t.map];
   const int C = t.ncols;
   const int lds = C + 2;
@@ -308,6 +307,40 @@ k_hough(const MapDev* __restrict__ maps, const TileDev* __restrict__ tiles,
   }
 }
 
+// One block per tile of the plan.
+template <int R, int NT, bool SELECT>
+__global__ void __launch_bounds__(NT, R <= 4 ? 3 : (R == 8 ? 2 : 1))
+k_hough(const MapDev* __restrict__ maps, const TileDev* __restrict__ tiles,
+        const uint32_t* __restrict__ fft_idx, const uint32_t* __restrict__ bins,
+        unsigned int* __restrict__ flag, int c_max) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const TileDev t = tiles[blockIdx.x];
+  if (t.nrows <= 0) return;
+  hough_tile<R, NT, SELECT>(maps, t, fft_idx, bins, flag, c_max, smem);
+}
+
+// Persistent blocks over a tile list whose length is known on the device only (the coarse-tile
+// search): each block takes the next tile from a counter until the list is exhausted.
+template <int R, int NT, bool SELECT>
+__global__ void __launch_bounds__(NT, R <= 4 ? 3 : (R == 8 ? 2 : 1))
+k_hough_list(const MapDev* __restrict__ maps, const TileDev* __restrict__ tiles,
+             const int* __restrict__ count, int* __restrict__ next, int cap,
+             const uint32_t* __restrict__ fft_idx, const uint32_t* __restrict__ bins,
+             unsigned int* __restrict__ flag, int c_max) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int cur;
+  const int n = min(*count, cap);
+  for (;;) {
+    if (threadIdx.x == 0) cur = atomicAdd(next, 1);
+    __syncthreads();
+    const int ti = cur;
+    __syncthreads();
+    if (ti >= n) break;
+    const TileDev t = tiles[ti];
+    if (t.nrows > 0) hough_tile<R, NT, SELECT>(maps, t, fft_idx, bins, flag, c_max, smem);
+  }
+}
+
 // ---- candidate records ----------------------------------------------------------------------------
 
 // One thread per (map, band).  Every floating-point step uses an explicitly rounded intrinsic so
@@ -385,17 +418,34 @@ __global__ void k_select_cols(const int32_t* __restrict__ map, const MapDev* __r
 // attribute at plan creation keeps gfh_plan_execute to stream operations only (capturable).  The
 // attribute belongs to the kernel, not to a plan, so it is set to the largest size any plan may
 // request: each launch still asks only for its own size (which alone decides occupancy).
+// n_tiles < 0: the persistent list form over p->d_sel_tiles with its device-side count.
 template <int R, int NT, bool SEL>
 int launch_hough_t(gfh_plan* p, const gfh_peaks* peaks, const TileDev* tiles, int n_tiles,
                    size_t smem, bool prepare) {
   auto fn = k_hough<R, NT, SEL>;
+  auto fl = k_hough_list<R, NT, SEL>;
   if (prepare) {
+    // the list kernel also holds a few bytes of static shared memory
+    cudaFuncAttributes fa{};
+    GFH_CUDA_TRY(cudaFuncGetAttributes(&fa, fl));
     GFH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)kMaxSmemBytes));
+    GFH_CUDA_TRY(cudaFuncSetAttribute(fl, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(kMaxSmemBytes - fa.sharedSizeBytes)));
     return GFH_OK;
   }
-  fn<<<n_tiles, NT, smem, p->ctx->stream>>>(p->d_maps, tiles, peaks->fft_idx, peaks->bin,
-                                            p->ctx->d_flag, p->cfg.cols);
+  if (n_tiles < 0 && smem + kListStaticSmem > kMaxSmemBytes) return GFH_ERR_SIZE;
+  if (n_tiles >= 0) {
+    fn<<<n_tiles, NT, smem, p->ctx->stream>>>(p->d_maps, tiles, peaks->fft_idx, peaks->bin,
+                                              p->ctx->d_flag, p->cfg.cols);
+  } else {
+    int per_sm = 0;
+    GFH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fl, NT, smem));
+    const int grid = p->ctx->num_sms * (per_sm > 0 ? per_sm : 1);
+    fl<<<grid, NT, smem, p->ctx->stream>>>(p->d_maps, tiles, p->d_sel_count, p->d_sel_count + 1,
+                                           p->sel_cap, peaks->fft_idx, peaks->bin, p->ctx->d_flag,
+                                           p->cfg.cols);
+  }
   GFH_CUDA_TRY(cudaGetLastError());
   return GFH_OK;
 }
@@ -422,28 +472,32 @@ int launch_hough(gfh_plan* p, const gfh_peaks* peaks, const TileDev* tiles, int 
                              : launch_hough_r<32>(p, peaks, tiles, n_tiles, smem, prepare);
 }
 
-// Copies the fine tiles of each map's selected coarse tiles into max_fine slots per selection;
-// unused slots get empty tiles (no rows), which k_hough skips.
+// Appends to one compact list the fine tiles of each map's selected coarse tiles, or, for a map
+// flagged for a full search, all tiles of the map (group nct of the map).  count[0] = list length.
+// The list holds at most cap tiles (enough unless a map lists a coarse tile twice): slots are
+// claimed in contiguous ranges, every claimed slot below cap is written, and an overflow sets the
+// capacity flag (the list kernel reads min(count, cap) tiles).
 __global__ void k_gather_tiles(const TileDev* __restrict__ fine, const int32_t* __restrict__ first,
-                               const int32_t* __restrict__ coarse, int n_sel, int nct,
-                               int max_fine, TileDev* __restrict__ out) {
+                               const int32_t* __restrict__ coarse, const int32_t* __restrict__ full,
+                               int n_sel, int nct, TileDev* __restrict__ out, int* count, int cap,
+                               unsigned int* flag) {
   const int m = blockIdx.y, s = blockIdx.x;
-  const int id = coarse[(int64_t)m * n_sel + s];
-  int b = 0, e = 0;
-  if (id >= 0 && id < nct) {
-    b = first[(int64_t)m * nct + id];
-    e = first[(int64_t)m * nct + id + 1];
+  const bool whole = full && full[m] != 0;
+  int id;
+  if (whole) id = s == 0 ? nct : -1;                // one block copies the whole map
+  else if (s < n_sel) id = coarse[(int64_t)m * n_sel + s];
+  else return;
+  if (id < 0 || id > nct || (id == nct && !whole)) return;
+  const int b = first[(int64_t)m * (nct + 1) + id];
+  const int e = first[(int64_t)m * (nct + 1) + id + 1];
+  if (e <= b) return;
+  __shared__ int base;
+  if (threadIdx.x == 0) {
+    base = atomicAdd(count, e - b);
+    if (base + (e - b) > cap) atomicOr(flag, GFH_FLAG_CAPACITY);
   }
-  for (int q = threadIdx.x; q < max_fine; q += blockDim.x) {
-    TileDev t;
-    if (b + q < e) {
-      t = fine[b + q];
-    } else {
-      t.map = m; t.row0 = 0; t.nrows = 0; t.ncols = 0; t.col0 = 0;
-      t.bin_a = 1; t.bin_b = 0; t.band_lo = 0; t.band_hi = -1;
-    }
-    out[((int64_t)m * n_sel + s) * max_fine + q] = t;
-  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < e - b && base + q < cap; q += blockDim.x) out[base + q] = fine[b + q];
 }
 
 }  // namespace
@@ -501,19 +555,23 @@ int gfh_launch_plan(gfh_plan* p, const gfh_peaks* peaks) {
   return launch_epilogue(p);
 }
 
-int gfh_launch_plan_tiles(gfh_plan* p, const gfh_peaks* peaks, const int32_t* d_coarse, int n_sel) {
+int gfh_launch_plan_tiles(gfh_plan* p, const gfh_peaks* peaks, const int32_t* d_coarse, int n_sel,
+                          const int32_t* d_full) {
   GFH_CUDA_TRY(cudaSetDevice(p->ctx->device));
   const size_t smem = gfh_hough_smem_bytes(p);
   if (smem > 227 * 1024) return GFH_ERR_SIZE;
   int rc = launch_prologue(p, peaks);
   if (rc) return rc;
   const int nct = p->coarse_k * p->coarse_x;
-  if (n_sel > 0 && p->max_fine > 0) {
-    dim3 grid(n_sel, p->n_maps);
-    k_gather_tiles<<<grid, 128, 0, p->ctx->stream>>>(p->d_fine, p->d_coarse_first, d_coarse, n_sel,
-                                                     nct, p->max_fine, p->d_sel_tiles);
+  cudaStream_t st = p->ctx->stream;
+  GFH_CUDA_TRY(cudaMemsetAsync(p->d_sel_count, 0, 2 * sizeof(int), st));
+  const int gx = n_sel > 0 ? n_sel : 1;
+  if (n_sel > 0 || d_full) {
+    k_gather_tiles<<<dim3(gx, p->n_maps), 128, 0, st>>>(p->d_fine, p->d_coarse_first, d_coarse,
+                                                       d_full, n_sel, nct, p->d_sel_tiles,
+                                                       p->d_sel_count, p->sel_cap, p->ctx->d_flag);
     GFH_CUDA_TRY(cudaGetLastError());
-    rc = launch_hough(p, peaks, p->d_sel_tiles, p->n_maps * n_sel * p->max_fine, smem, false);
+    rc = launch_hough(p, peaks, p->d_sel_tiles, -1, smem, false);
     if (rc) return rc;
   }
   return launch_epilogue(p);

@@ -125,11 +125,14 @@ struct gfh_plan {
   std::vector<gfh_candidate*> h_cands;
   gfh_map_stats* d_stats = nullptr;
   // coarse tiles (gfh_plan_set_coarse): per (map, coarse tile) the fine tiles that cover it
+  // (group coarse_k * coarse_x of a map = all of the map's tiles, for a full search)
   int coarse_k = 0, coarse_x = 0, max_sel = 0, max_fine = 0;
   void* d_coarse_buf = nullptr;
   TileDev* d_fine = nullptr;           // fine tiles, grouped by (map, coarse tile)
-  int32_t* d_coarse_first = nullptr;   // n_maps * coarse_k * coarse_x + 1 group offsets
-  TileDev* d_sel_tiles = nullptr;      // n_maps * max_sel * max_fine gathered tiles
+  int32_t* d_coarse_first = nullptr;   // n_maps * (coarse_k * coarse_x + 1) + 1 group offsets
+  TileDev* d_sel_tiles = nullptr;      // the gathered tile list (worst case: every map in full)
+  int* d_sel_count = nullptr;          // [0] list length, [1] next tile (persistent blocks)
+  int sel_cap = 0;                     // capacity of d_sel_tiles
 };
 
 // Host-side planning (gfh_host.cpp).
@@ -141,6 +144,6 @@ int gfh_host_columns(const gfh_grid* g, std::vector<int32_t>& band, std::vector<
 // Launchers (gfh_hough.cu).
 int gfh_launch_plan(gfh_plan* plan, const gfh_peaks* peaks);
 int gfh_launch_plan_tiles(gfh_plan* plan, const gfh_peaks* peaks, const int32_t* d_coarse,
-                          int n_sel);
+                          int n_sel, const int32_t* d_full);
 int gfh_prepare_plan(gfh_plan* plan);   // one-time kernel attributes (outside any capture)
 int gfh_launch_select(gfh_ctx* ctx, const int32_t* d_map, const MapDev& md, void* d_scratch);

@@ -10,6 +10,7 @@ from __future__ import annotations
 import ctypes
 import dataclasses
 import pathlib
+import weakref
 
 import numpy as np
 
@@ -124,7 +125,7 @@ def lib() -> ctypes.CDLL:
             "gfh_select": [vp, vp, P(GridC), vp, vp],
             "gfh_peaks_from_power_static": [vp, vp, i64, i32, i32, i32, dbl, vp, vp, i64, vp],
             "gfh_plan_set_coarse": [vp, i32, i32, i32],
-            "gfh_plan_execute_tiles": [vp, P(PeaksC), vp, i32],
+            "gfh_plan_execute_tiles": [vp, P(PeaksC), vp, i32, vp],
             "gfh_synth_peaks": [vp, u64, i64, i32, i32, i32, u32, u32, vp, vp, vp, i64, P(i64)],
             "gfh_synth_images": [vp, u64, i64, i32, i32, i32, i32, u32, vp, vp, vp, vp],
             "gfh_peaks_to_images": [vp, P(PeaksC), i32, i32, i32, vp, vp],
@@ -136,7 +137,7 @@ def lib() -> ctypes.CDLL:
             "gfh_cnn_gradients": [vp, vp, vp, i32, P(ctypes.c_float)],
             "gfh_cnn_train_step": [vp, vp, vp, i32, ctypes.c_float, ctypes.c_float,
                                    P(ctypes.c_float)],
-            "gfh_propose_tiles": [vp, vp, i32, vp, i32, vp, vp],
+            "gfh_propose_tiles": [vp, vp, i32, vp, i32, ctypes.c_float, vp, vp, vp],
             "gfh_conv3x3": [vp, i32, i32, i32, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp],
         }
         for name, args in sig.items():
@@ -243,6 +244,10 @@ class Context:
         self._h = ctypes.c_void_p()
         _ok(lib().gfh_create(ctypes.byref(self._h), device, _stream_handle(stream)), "gfh_create")
         self.device = device
+        self._children = weakref.WeakSet()     # plans and networks: destroyed before the context
+
+    def _adopt(self, child) -> None:
+        self._children.add(child)
 
     @property
     def handle(self):
@@ -257,6 +262,8 @@ class Context:
 
     def close(self) -> None:
         if self._h:
+            for c in list(self._children):
+                c.close()
             lib().gfh_destroy(self._h)
             self._h = ctypes.c_void_p()
 
@@ -330,6 +337,7 @@ class Plan:
                                    _ptr(stats), ctypes.byref(self._tile) if self._tile else None,
                                    ctypes.byref(self._h))
         _ok(rc, "gfh_plan_create")
+        ctx._adopt(self)
 
     def execute(self, fft_idx, bins, offsets, n_lists: int) -> None:
         pk = PeaksC(_ptr(fft_idx), _ptr(bins), _ptr(offsets), n_lists)
@@ -347,11 +355,13 @@ class Plan:
     def set_coarse(self, coarse_k: int, coarse_x: int, max_sel: int) -> None:
         _ok(lib().gfh_plan_set_coarse(self._h, coarse_k, coarse_x, max_sel), "gfh_plan_set_coarse")
 
-    def execute_tiles(self, fft_idx, bins, offsets, n_lists: int, coarse, n_sel: int) -> None:
-        """Exact Hough on the coarse tiles listed in the int32 device tensor coarse [maps][n_sel]."""
+    def execute_tiles(self, fft_idx, bins, offsets, n_lists: int, coarse, n_sel: int,
+                      full=None) -> None:
+        """Exact Hough on the coarse tiles listed in the int32 device tensor coarse [maps][n_sel];
+        maps flagged in the int32 device tensor `full` are searched in full."""
         pk = PeaksC(_ptr(fft_idx), _ptr(bins), _ptr(offsets), n_lists)
-        _ok(lib().gfh_plan_execute_tiles(self._h, ctypes.byref(pk), _ptr(coarse), n_sel),
-            "gfh_plan_execute_tiles")
+        _ok(lib().gfh_plan_execute_tiles(self._h, ctypes.byref(pk), _ptr(coarse), n_sel,
+                                         _ptr(full)), "gfh_plan_execute_tiles")
 
     def close(self) -> None:
         if self._h:
@@ -412,10 +422,12 @@ def peaks_to_images(ctx: Context, fft_idx, bins, offsets, n_lists: int, n_fft: i
     _ok(rc, "gfh_peaks_to_images")
 
 
-def propose_tiles(ctx: Context, logits, gain, k: int, top, resid) -> None:
-    """gfh_propose_tiles: the k best coarse tiles per map and the missed probability."""
-    rc = lib().gfh_propose_tiles(ctx.handle, _ptr(logits), logits.shape[0], _ptr(gain), k,
-                                 _ptr(top), _ptr(resid))
+def propose_tiles(ctx: Context, logits, gain, k: int, top, resid, tau: float = -1.0,
+                  full=None) -> None:
+    """gfh_propose_tiles: the best coarse tiles per map (cut at resid <= tau when tau >= 0), the
+    probability left outside them, and the maps that need the full search."""
+    rc = lib().gfh_propose_tiles(ctx.handle, _ptr(logits), logits.shape[0], _ptr(gain), k, tau,
+                                 _ptr(top), _ptr(resid), _ptr(full))
     _ok(rc, "gfh_propose_tiles")
 
 
@@ -435,6 +447,7 @@ class Cnn:
         self._h = ctypes.c_void_p()
         _ok(lib().gfh_cnn_create(ctx.handle, max_batch, seed, ctypes.byref(self._h)),
             "gfh_cnn_create")
+        ctx._adopt(self)
         self.n_params = int(lib().gfh_cnn_param_count(self._h))
 
     def params(self) -> np.ndarray:

@@ -196,10 +196,10 @@ def train(ctx: gfh.Context, net: gfh.Cnn, spec: ProposerSpec, first: int, count:
 # ---- evaluation against the full exact Hough ---------------------------------------------------------
 
 class HoughBank:
-    """One batched plan over the 51 braking indices (map b reads list b), and one single-map plan
-    per index for full-search fallbacks; all plans share candidates buffers per map."""
+    """One batched plan over the 51 braking indices (map b reads peak list b, coarse tiles 64 x 64)
+    with its maps and candidate buffers."""
 
-    def __init__(self, ctx: gfh.Context, spec: ProposerSpec, n_sel: int = 32, tile=None):
+    def __init__(self, ctx: gfh.Context, spec: ProposerSpec, max_sel: int = 256, tile=None):
         import torch
         self.torch = torch
         self.spec = spec
@@ -208,19 +208,14 @@ class HoughBank:
         self.maps = [torch.empty((g.n_k, g.ld_x0), dtype=torch.int32, device="cuda") for g in self.grids]
         self.cands = [torch.empty(g.n_bands * 64, dtype=torch.uint8, device="cuda") for g in self.grids]
         self.plan = gfh.Plan(ctx, self.grids, self.maps, self.cands, tile=tile)
-        self.plan.set_coarse(TILES, TILES, n_sel)
-        self.n_sel = n_sel
-        self.single = []
-        for i, g in enumerate(self.grids):
-            g0 = dataclasses.replace(g, list=0)
-            self.single.append(gfh.Plan(ctx, [g0], [self.maps[i]], [self.cands[i]], tile=tile))
+        self.plan.set_coarse(TILES, TILES, max_sel)
+        self.max_sel = max_sel
         cap = int(spec.n_fft * (spec.bin_hi - spec.bin_lo + 1) * 0.1) + 4096
         self.cap = cap
         nl = len(N_GRID)
         self.fft = torch.empty(nl * cap, dtype=torch.int32, device="cuda")
         self.bin = torch.empty(nl * cap, dtype=torch.int32, device="cuda")
         self.offsets = torch.zeros(nl + 1, dtype=torch.int64, device="cuda")
-        self.coarse = torch.full((nl, n_sel), -1, dtype=torch.int32, device="cuda")
         self.counts = np.zeros(nl, np.int64)
 
     def load_peaks(self, smp: Samples) -> None:
@@ -235,7 +230,7 @@ class HoughBank:
                                 spec.bin_hi, spec.p_noise24, int(smp.p_track24[i]), tracks[i],
                                 self.fft[o:o + self.cap], self.bin[o:o + self.cap])
             self.counts[i] = n
-        # lists live at fixed strides; compact them so list i starts at offsets[i]
+        # lists were drawn at fixed strides; compact them so that list i starts at offsets[i]
         parts_f, parts_b = [], []
         for i in range(smp.index.size):
             o = i * self.cap
@@ -246,8 +241,6 @@ class HoughBank:
         self.bin_c = torch.cat(parts_b)
         self.offsets.copy_(torch.tensor(offs, dtype=torch.int64))
         self.offs_host = offs
-        self.single_off = torch.tensor([[0, offs[i + 1] - offs[i]] for i in range(len(offs) - 1)],
-                                       dtype=torch.int64, device="cuda")
 
     def updates(self) -> int:
         """Hough updates of the full search of the loaded lists: peaks x k rows per map."""
@@ -256,13 +249,9 @@ class HoughBank:
     def full(self) -> None:
         self.plan.execute(self.fft_c, self.bin_c, self.offsets, len(N_GRID))
 
-    def pruned(self, coarse) -> None:
-        self.plan.execute_tiles(self.fft_c, self.bin_c, self.offsets, len(N_GRID), coarse, self.n_sel)
-
-    def full_one(self, i: int) -> None:
-        """Full exact search of map i alone (its own single-map plan)."""
-        o0, o1 = self.offs_host[i], self.offs_host[i + 1]
-        self.single[i].execute(self.fft_c[o0:o1], self.bin_c[o0:o1], self.single_off[i], 1)
+    def pruned(self, coarse, n_sel: int, full_flags=None) -> None:
+        self.plan.execute_tiles(self.fft_c, self.bin_c, self.offsets, len(N_GRID), coarse, n_sel,
+                                full_flags)
 
     def candidates(self) -> list:
         return [gfh.candidates_to_numpy(c) for c in self.cands]
@@ -275,36 +264,67 @@ def detected(cands: np.ndarray, col: int, row: int, radius: float = 3.0) -> bool
     return bool(np.any(d2 <= radius * radius))
 
 
+class PrunedSearch:
+    """The proposer-guided search of the bank's loaded peak lists, all on the device without a
+    host round trip: images from the peak lists, the network, the proposals (at most n_sel tiles,
+    cut where the probability left outside is at most tau), and one exact-Hough launch over the
+    proposed coarse tiles of every map and all tiles of the maps whose proposal cannot reach tau."""
+
+    def __init__(self, ctx: gfh.Context, net: gfh.Cnn, bank: HoughBank, tau: float,
+                 n_sel: int = 32):
+        import torch
+        spec = bank.spec
+        nl = len(N_GRID)
+        assert n_sel <= bank.max_sel
+        self.ctx, self.net, self.bank, self.tau, self.n_sel = ctx, net, bank, tau, n_sel
+        smp = draw(spec, np.arange(nl))            # gains and n planes depend on the map slot only
+        self.gain = torch.from_numpy(smp.gain).cuda()
+        self.nplane = torch.from_numpy(smp.nplane).cuda()
+        self.images = torch.empty((nl, 256, 256, 2), dtype=torch.bfloat16, device="cuda")
+        self.logits = torch.empty((nl, gfh.N_CLASSES), dtype=torch.float32, device="cuda")
+        self.top = torch.empty((nl, n_sel), dtype=torch.int32, device="cuda")
+        self.resid = torch.empty(nl, dtype=torch.float32, device="cuda")
+        self.full = torch.empty(nl, dtype=torch.int32, device="cuda")
+
+    def propose(self) -> None:
+        spec, bank = self.bank.spec, self.bank
+        gfh.peaks_to_images(self.ctx, bank.fft_c, bank.bin_c, bank.offsets, len(N_GRID),
+                            spec.n_fft, spec.bin_lo, spec.bin_hi, self.nplane, self.images)
+        self.net.forward(self.images, self.logits)
+        gfh.propose_tiles(self.ctx, self.logits, self.gain, self.n_sel, self.top, self.resid,
+                          self.tau, self.full)
+
+    def run(self) -> None:
+        self.propose()
+        self.bank.pruned(self.top, self.n_sel, self.full)
+
+
 def evaluate(ctx: gfh.Context, net: gfh.Cnn, spec: ProposerSpec, first: int, count: int,
-             bank: HoughBank, n_sel: int = 32, log=None) -> dict:
-    """Per-map records of the proposal (top n_sel coarse tiles) against the full exact Hough on
-    samples [first, first + count), in batches of 51 maps (first and count multiples of 51, so that
-    sample s lands on the bank's map s mod 51).  summarize() turns them into recall and fallback
-    rates for a threshold tau."""
-    torch = bank.torch
+             bank: HoughBank, tau: float, n_sel: int = 32, log=None) -> dict:
+    """Per-map records of the pruned search (PrunedSearch) against the full exact Hough on samples
+    [first, first + count), in batches of 51 maps (first and count multiples of 51, so that
+    sample s lands on the bank's map s mod 51)."""
     nl = len(N_GRID)
     # sample s has braking index N_GRID[s % 51] = the grid of map s % 51 of the bank
     assert first % nl == 0 and count % nl == 0, "evaluate whole batches of 51 maps"
-    buf = DeviceBatch(spec, nl)
-    top = torch.empty((nl, n_sel), dtype=torch.int32, device="cuda")
-    resid = torch.empty(nl, dtype=torch.float32, device="cuda")
-    rec = {k: [] for k in ("signal", "resid", "det_full", "det_pruned", "agree", "truth_in_top",
-                           "f0", "n", "row")}
+    search = PrunedSearch(ctx, net, bank, tau, n_sel)
+    rec = {k: [] for k in ("signal", "resid", "full", "tiles", "det_full", "det_pruned", "agree",
+                           "truth_in_top", "f0", "n", "row")}
     for b0 in range(first, first + count, nl):
         smp = draw(spec, np.arange(b0, b0 + nl))
-        buf.load(ctx, spec, smp)
-        net.forward(buf.images, buf.logits)
-        gfh.propose_tiles(ctx, buf.logits, buf.gain, n_sel, top, resid)
         bank.load_peaks(smp)
         bank.full()
         full = bank.candidates()
-        bank.pruned(top)
+        search.run()
         pr = bank.candidates()
-        r = resid.cpu().numpy()
-        tp = top.cpu().numpy()
+        r = search.resid.cpu().numpy()
+        fl = search.full.cpu().numpy()
+        tp = search.top.cpu().numpy()
         for i in range(nl):
             rec["signal"].append(bool(smp.signal[i]))
             rec["resid"].append(float(r[i]))
+            rec["full"].append(bool(fl[i]))
+            rec["tiles"].append(4096 if fl[i] else int((tp[i] >= 0).sum()))
             rec["f0"].append(float(smp.f0[i]))
             rec["n"].append(float(smp.n[i]))
             rec["row"].append(int(smp.row[i]))
@@ -314,7 +334,7 @@ def evaluate(ctx: gfh.Context, net: gfh.Cnn, spec: ProposerSpec, first: int, cou
                 continue
             kt = int(smp.row[i]) * TILES // spec.n_k
             xt = min(TILES - 1, int((smp.f0[i] - spec.ana_lo) / (spec.ana_hi - spec.ana_lo) * TILES))
-            rec["truth_in_top"].append(kt * TILES + xt in set(tp[i].tolist()))
+            rec["truth_in_top"].append(bool(fl[i]) or kt * TILES + xt in set(tp[i].tolist()))
             cf, cp = full[i], pr[i]
             rec["det_full"].append(detected(cf, int(smp.col[i]), int(smp.row[i])))
             rec["det_pruned"].append(detected(cp, int(smp.col[i]), int(smp.row[i])))
@@ -325,21 +345,32 @@ def evaluate(ctx: gfh.Context, net: gfh.Cnn, spec: ProposerSpec, first: int, cou
     return {k: np.array(v) for k, v in rec.items()}
 
 
-def summarize(rec: dict, tau: float) -> dict:
-    """Recall (detections of the full search kept by the pruned search, a map whose resid exceeds
-    tau being searched in full), agreement of the injection band's top count, fallback rates."""
-    fb = rec["resid"] > tau
+def summarize(rec: dict) -> dict:
+    """Recall (detections of the full search that the pruned search keeps), agreement of the
+    injection band's top count, fallback (full-search) rates, tiles searched per map."""
     sig = rec["signal"]
     det_full = rec["det_full"] & sig
-    kept = det_full & (fb | rec["det_pruned"])
-    agree = sig & (fb | rec["agree"])
-    return dict(tau=tau, maps=int(sig.size), injected=int(sig.sum()),
+    kept = det_full & rec["det_pruned"]
+    return dict(maps=int(sig.size), injected=int(sig.sum()),
                 det_full=int(det_full.sum()), det_kept=int(kept.sum()),
                 recall=float(kept.sum() / max(1, det_full.sum())),
-                agreement=float(agree.sum() / max(1, sig.sum())),
-                fallback_frac=float(fb.mean()), fallback_injected=float(fb[sig].mean()),
-                fallback_noise=float(fb[~sig].mean()) if (~sig).any() else 0.0,
-                truth_in_top=float(rec["truth_in_top"][sig].mean()))
+                agreement=float((rec["agree"] & sig).sum() / max(1, sig.sum())),
+                fallback_frac=float(rec["full"].mean()),
+                fallback_injected=float(rec["full"][sig].mean()) if sig.any() else 0.0,
+                fallback_noise=float(rec["full"][~sig].mean()) if (~sig).any() else 0.0,
+                mean_tiles_pruned=float(rec["tiles"][~rec["full"]].mean()) if (~rec["full"]).any() else 0.0,
+                truth_in_top=float(rec["truth_in_top"][sig].mean()) if sig.any() else 0.0)
+
+
+def choose_tau(ctx: gfh.Context, net: gfh.Cnn, spec: ProposerSpec, first: int, count: int,
+               bank: HoughBank, n_sel: int, target: float = 0.995,
+               taus=(0.3, 0.2, 0.15, 0.1, 0.075, 0.05, 0.03, 0.02, 0.01, 0.005)) -> tuple:
+    """The largest tau whose recall on the validation samples reaches `target`."""
+    for tau in taus:
+        sm = summarize(evaluate(ctx, net, spec, first, count, bank, tau, n_sel))
+        if sm["recall"] >= target:
+            return tau, sm
+    return 0.0, summarize(evaluate(ctx, net, spec, first, count, bank, 0.0, n_sel))
 
 
 def train_default(ctx: gfh.Context, net: gfh.Cnn, spec: ProposerSpec, epochs: int = 3,
@@ -350,44 +381,3 @@ def train_default(ctx: gfh.Context, net: gfh.Cnn, spec: ProposerSpec, epochs: in
     for e in range(epochs):
         losses += train(ctx, net, spec, 0, n_train, batch=batch, lr=lr * 0.5 ** e, log=log)
     return losses
-
-
-class PrunedSearch:
-    """The proposer-guided search of the bank's 51 loaded peak lists: images from the peak lists,
-    the network, the proposals, the exact Hough on the proposed coarse tiles, and the full exact
-    Hough of every map whose proposal leaves more than tau probability outside its tiles."""
-
-    def __init__(self, ctx: gfh.Context, net: gfh.Cnn, bank: HoughBank, tau: float,
-                 n_sel: int = 32):
-        import torch
-        spec = bank.spec
-        nl = len(N_GRID)
-        self.ctx, self.net, self.bank, self.tau, self.n_sel = ctx, net, bank, tau, n_sel
-        smp = draw(spec, np.arange(nl))            # gains and n planes depend on the map slot only
-        self.gain = torch.from_numpy(smp.gain).cuda()
-        self.nplane = torch.from_numpy(smp.nplane).cuda()
-        self.images = torch.empty((nl, 256, 256, 2), dtype=torch.bfloat16, device="cuda")
-        self.logits = torch.empty((nl, gfh.N_CLASSES), dtype=torch.float32, device="cuda")
-        self.top = torch.empty((nl, n_sel), dtype=torch.int32, device="cuda")
-        self.resid = torch.empty(nl, dtype=torch.float32, device="cuda")
-        self.resid_host = torch.empty(nl, dtype=torch.float32).pin_memory()
-        self.fallbacks = 0
-
-    def propose(self) -> None:
-        spec, bank = self.bank.spec, self.bank
-        gfh.peaks_to_images(self.ctx, bank.fft_c, bank.bin_c, bank.offsets, len(N_GRID),
-                            spec.n_fft, spec.bin_lo, spec.bin_hi, self.nplane, self.images)
-        self.net.forward(self.images, self.logits)
-        gfh.propose_tiles(self.ctx, self.logits, self.gain, self.n_sel, self.top, self.resid)
-
-    def run(self) -> int:
-        """One search of the loaded lists; returns the number of maps searched in full."""
-        self.propose()
-        self.bank.pruned(self.top)
-        self.resid_host.copy_(self.resid, non_blocking=True)
-        self.bank.torch.cuda.current_stream().synchronize()
-        fb = np.nonzero(self.resid_host.numpy() > self.tau)[0]
-        for i in fb:
-            self.bank.full_one(int(i))
-        self.fallbacks += fb.size
-        return int(fb.size)

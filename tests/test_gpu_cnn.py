@@ -227,23 +227,37 @@ def test_adamw_step(built_lib, gpu_ctx):
 
 
 def test_proposals(built_lib, gpu_ctx):
+    """Ranked tiles, the cut at tau and the full-search flags against the oracle (ranks compared up
+    to fp32 near-ties of the scores)."""
     gfh = built_lib
     spec = PR.ProposerSpec()
     smp = PR.draw(spec, np.arange(100, 108))
     rng = np.random.default_rng(9)
     logits = (rng.standard_normal((8, gfh.N_CLASSES)) * 3).astype(np.float32)
     logits[3, 4096] = 40.0                                     # confident "no signal"
+    logits[5, 64 * 2 + 40] = 25.0                              # one confident class
     lt = torch.from_numpy(logits).cuda()
     gain = torch.from_numpy(smp.gain).cuda()
-    top = torch.empty((8, 32), dtype=torch.int32, device="cuda")
-    resid = torch.empty(8, dtype=torch.float32, device="cuda")
-    gfh.propose_tiles(gpu_ctx, lt, gain, 32, top, resid)
-    torch.cuda.synchronize()
-    tp, rs = top.cpu().numpy(), resid.cpu().numpy()
-    for b in range(8):
-        sc, pnull = C.tile_scores(logits[b].astype(np.float64), smp.gain[b].astype(np.float64))
-        kth = np.sort(sc)[::-1][31]
-        assert len(set(tp[b].tolist())) == 32
-        assert np.all(sc[tp[b]] >= kth - 1e-6 * sc.max())     # the best 32 up to fp32 near-ties
-        assert abs(rs[b] - max(0.0, 1 - pnull - sc[tp[b]].sum())) <= 1e-4
-    assert rs[3] < 1e-3
+    for k, tau in ((32, -1.0), (256, 0.05), (32, 0.5)):
+        top = torch.empty((8, k), dtype=torch.int32, device="cuda")
+        resid = torch.empty(8, dtype=torch.float32, device="cuda")
+        full = torch.empty(8, dtype=torch.int32, device="cuda")
+        gfh.propose_tiles(gpu_ctx, lt, gain, k, top, resid, tau, full)
+        torch.cuda.synchronize()
+        tp, rs, fl = top.cpu().numpy(), resid.cpu().numpy(), full.cpu().numpy()
+        for b in range(8):
+            sc, pnull = C.tile_scores(logits[b].astype(np.float64), smp.gain[b].astype(np.float64))
+            otop, ores, ofull = C.propose(logits[b].astype(np.float64), smp.gain[b].astype(np.float64), k, tau)
+            kept = tp[b][tp[b] >= 0]
+            okept = otop[otop >= 0]
+            srt = np.sort(sc)[::-1]
+            assert len(set(kept.tolist())) == kept.size
+            # the same prefix length unless the cut falls within fp32 rounding of the leftover
+            if abs(kept.size - okept.size) > 0:
+                assert tau >= 0 and abs(ores - tau) < 1e-4, (k, tau, b, kept.size, okept.size)
+            n = min(kept.size, okept.size)
+            assert np.all(sc[kept[:n]] >= srt[n - 1] - 1e-6 * srt[0])
+            assert abs(rs[b] - max(0.0, 1 - pnull - sc[kept].sum())) <= 1e-4
+            assert bool(fl[b]) == ofull or abs(ores - tau) < 1e-4
+        if tau < 0:
+            assert rs[3] < 1e-3 and np.all(fl == 0)

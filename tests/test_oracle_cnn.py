@@ -170,6 +170,14 @@ def test_proposal_mass_and_identity_gain():
     p = np.exp(logits - logits.max())
     p /= p.sum()
     np.testing.assert_allclose(sc1, p[:4096], rtol=1e-12)
-    top, resid = C.propose(logits, np.ones((64, 2)), 32)
-    assert list(top) == list(np.argsort(-p[:4096], kind="stable")[:32])
+    top, resid, full = C.propose(logits, np.ones((64, 2)), 32)
+    order = np.argsort(-p[:4096], kind="stable")
+    assert list(top) == list(order[:32]) and not full
     assert math.isclose(resid, max(0.0, 1 - p[4096] - p[top].sum()), rel_tol=1e-9, abs_tol=1e-12)
+    # a threshold cuts the list at the first prefix whose leftover is within it
+    cut = 1 - p[4096] - np.cumsum(p[order[:32]])
+    n = int(np.argmax(cut <= cut[9])) + 1
+    top2, resid2, full2 = C.propose(logits, np.ones((64, 2)), 32, tau=float(cut[9]))
+    assert list(top2[:n]) == list(order[:n]) and np.all(top2[n:] == -1) and not full2
+    _, _, full3 = C.propose(logits, np.ones((64, 2)), 32, tau=float(cut[31]) / 2)
+    assert full3
