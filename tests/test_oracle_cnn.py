@@ -181,3 +181,34 @@ def test_proposal_mass_and_identity_gain():
     assert list(top2[:n]) == list(order[:n]) and np.all(top2[n:] == -1) and not full2
     _, _, full3 = C.propose(logits, np.ones((64, 2)), 32, tau=float(cut[31]) / 2)
     assert full3
+
+
+def test_labels_follow_the_drift_and_gains_cover_the_true_row():
+    """The proposer's labels against the physics of the grid: the drift class is the first-order
+    drift k f0^n T_obs (Eq. diff_powlaws) in units of K/64 bins, which bounds the power law's actual
+    drift from above (the spin-down slows as f falls) and matches it while the drift is small; and
+    the k-tile range that the proposal assigns to the label's class holds the true row's k tile."""
+    from paper_1810_09784_gb300 import proposer as PR
+    spec = PR.ProposerSpec()
+    smp = PR.draw(spec, np.arange(0, 400))
+    checked = 0
+    for b in np.nonzero(smp.signal)[0]:
+        n, f0, r = smp.n[b], smp.f0[b], smp.row[b]
+        d, xt = divmod(int(smp.labels[b]), 64)
+        ga, gb = smp.gain[b, xt]
+        kt = r * 64 // spec.n_k
+        lo = min(63, math.floor(d * gb))
+        hi = min(63, max(lo, math.ceil((d + 1) * ga) - 1))
+        assert lo <= kt <= hi, (b, d, xt, kt, lo, hi)
+        lin = smp.k[b] * f0 ** n * spec.t_obs / spec.df * 64 / spec.n_k
+        if d < 63:
+            assert d <= lin < d + 1 + 1e-9, (b, d, lin)
+        # actual drift from f(t0) to f(t_obs) in bins, in units of K/64 bins (Eq. powlaws)
+        f_end = f0 / (1 + (n - 1) * smp.k[b] * f0 ** (n - 1) * spec.t_obs) ** (1 / (n - 1))
+        drift = (f0 - f_end) / spec.df * 64 / spec.n_k
+        assert drift <= lin * (1 + 1e-12)
+        # second order: 1 - (1 + (n-1) u)^(-1/(n-1)) >= u - n u^2 / 2 with u = k f0^(n-1) T_obs
+        u = smp.k[b] * f0 ** (n - 1) * spec.t_obs
+        assert drift >= lin * (1 - n * u / 2) - 1e-9, (b, lin, drift, u)
+        checked += 1
+    assert checked > 150
