@@ -29,7 +29,7 @@ import numpy as np
 ROOT = pathlib.Path(__file__).resolve().parent
 sys.path.insert(0, str(ROOT))
 
-from paper_1810_09784_gb300 import workloads  # noqa: E402
+from paper_1810_09784_gb300 import ranks, workloads  # noqa: E402
 
 PEAKS = json.loads((ROOT / "MEASURED_PEAKS.json").read_text()) if (ROOT / "MEASURED_PEAKS.json").exists() else {}
 HBM_PEAK = PEAKS.get("hbm_gbs", 6800.0)
@@ -66,13 +66,13 @@ def parse():
 
 
 def dist_env():
-    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+    return ranks.rank_env()
 
 
 def workload(name, rank):
     fn = getattr(workloads, name)
     base = {"plain_paper": 2, "plain_small": 1, "batched_n": 1}[name]
-    return fn(seed=base + 7919 * rank)
+    return fn(seed=ranks.rank_seed(base, rank))
 
 
 def describe(name, spec, grids):
@@ -372,8 +372,7 @@ def run_gpu(args):
     clocks = sampler.summary()
     ms_hough = sum(e0.elapsed_time(e1) for e0, e1 in hough) / args.steps
     ms = ms_graph if ms_graph is not None else ms_direct
-    ms_max = reduce(ms, MAX)
-    total_updates = reduce(float(updates), SUM)
+    ms_max, total_updates = ranks.combine(ms, float(updates), device="cuda")
     value = total_updates / (ms_max * 1e-3)
 
     # ---- end to end through the public API with host buffers
@@ -471,7 +470,7 @@ def run_gpu_lists(args):
     stream = torch.cuda.Stream()
     ctx = gfh.Context(local, stream)
     t_gen = time.perf_counter()
-    lists, grid_fields, specs = workloads.uneven(seed=4 + 7919 * rank)
+    lists, grid_fields, specs = workloads.uneven(seed=ranks.rank_seed(4, rank))
     t_gen = time.perf_counter() - t_gen
     off_np = np.cumsum([0] + [len(f) for f, _ in lists]).astype(np.int64)
     fi_host = torch.from_numpy(np.concatenate([f for f, _ in lists]).view(np.int32)).pin_memory()
@@ -548,15 +547,7 @@ def run_gpu_lists(args):
         ms_seq = a.elapsed_time(b_)
         for sp in singles:
             sp.close()
-    ms_max = ms
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms, float(updates)], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
-        ms_max, total = float(t[0]), float(t[1])
-    else:
-        total = float(updates)
+    ms_max, total = ranks.combine(ms, float(updates), device="cuda")
     if rank == 0:
         map_bytes = sum(g.n_k * g.ld_x0 * 4 for g in grids)
         achieved = 2.0 * updates / (ms * 1e-3) / 1e9
@@ -684,13 +675,7 @@ def run_proposer(args):
             torch.cuda.synchronize()
             t_e2e.append(c.elapsed_time(d))
     ms_pr = r["ms_pr"]
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms_pr], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t[0])
-    else:
-        ms_max = ms_pr
+    ms_max, total_upd = ranks.combine(ms_pr, r["upd_step"], device="cuda")
     if rank != 0:
         return
     cpu = None
@@ -720,7 +705,7 @@ def run_proposer(args):
     r256 = res[256]
     line = {
         "metric": "Hough updates/s (peaks x k-bins), full-search equivalent",
-        "value": world * r["upd_step"] / (ms_max * 1e-3), "unit": "updates/s", "n_gpus": world,
+        "value": total_upd / (ms_max * 1e-3), "unit": "updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32 counts; bf16 network, fp32 accumulate",
         "data": "synthetic (statistical peakmap model, hashed per cell)",
