@@ -96,15 +96,18 @@ __device__ __forceinline__ bool peak_interval(const MapDev& md, int row0, uint32
   return true;
 }
 
+
 // Events of one peak on the R rows of a tile (layout described at k_hough below).  The interval
-// on row 0 is [a, b1 + 1) in 2^-32 columns and moves left by s per row.
+// on row 0 is [a, b1 + 1) in 2^-32 columns and moves left by s per row.  G0 + m is column m of row
+// 0 in absolute column numbering (the tile's first column is c0); ub = min(last column of the
+// tile, last column of the map).
 template <int R>
 __device__ __forceinline__ void draw_peak(int* G0, int lds, int64_t a, int64_t b1, int64_t s,
-                                          int c0, int c1m1, int wm1, int& carry) {
+                                          int c0, int c1m1, int ub, int& carry) {
   // row 0: first / last covered column, clamped to the map's last column and to the tile
   int lo = (int)(a >> GFH_FRAC_BITS);
-  int hi = min((int)(b1 >> GFH_FRAC_BITS), wm1);
-  int o1 = max(lo, c0), o2 = min(hi, c1m1);
+  int hi = min((int)(b1 >> GFH_FRAC_BITS), ub);
+  int o1 = max(lo, c0), o2 = hi;
   if (o1 <= o2) {
     if (lo < c0) carry += 1;
     else atomicAdd(G0 + o1, 1);
@@ -120,8 +123,7 @@ __device__ __forceinline__ void draw_peak(int* G0, int lds, int64_t a, int64_t b
       a -= s;
       b1 -= s;
       lo = (int)(a >> GFH_FRAC_BITS);
-      hi = min((int)(b1 >> GFH_FRAC_BITS), wm1);
-      const int n1 = max(lo, c0), n2 = min(hi, c1m1);
+      const int n1 = max(lo, c0), n2 = min((int)(b1 >> GFH_FRAC_BITS), ub);
       int* const Gr = G0 + rr * lds;
       const int f1 = max(o1, n2 + 1);
       if ((n1 < o1) & (n1 <= n2)) atomicAdd(Gr + n1, 1);
@@ -134,8 +136,7 @@ __device__ __forceinline__ void draw_peak(int* G0, int lds, int64_t a, int64_t b
       a -= s;
       b1 -= s;
       lo = (int)(a >> GFH_FRAC_BITS);
-      hi = min((int)(b1 >> GFH_FRAC_BITS), wm1);
-      const int n1 = max(lo, c0), n2 = min(hi, c1m1);
+      const int n1 = max(lo, c0), n2 = min((int)(b1 >> GFH_FRAC_BITS), ub);
       int* const Gr = G0 + rr * lds;
       const int e2 = min(n2, o1 - 1);
       for (int m = n1; m <= e2; ++m) atomicAdd(Gr + m, 1);
@@ -189,6 +190,7 @@ __device__ __forceinline__ void hough_tile(const MapDev* __restrict__ maps, cons
     const int wm1 = (int)md.W - 1;
     const int c0 = (int)t.col0;
     const int c1m1 = c0 + C - 1;                 // last column of the tile
+    const int ub = min(c1m1, wm1);
     const uint32_t nfft = (uint32_t)md.n_fft;
     const unsigned jmax = (unsigned)(md.bin_hi - md.bin_lo);
     int* const G0 = G - c0;                      // rows indexed by absolute column
@@ -212,7 +214,7 @@ __device__ __forceinline__ void hough_tile(const MapDev* __restrict__ maps, cons
       int64_t a_nx = 0, b_nx = 0, s_nx = 0;
       const bool ok_nx = f_nx != 0xffffffffu &&
                          peak_interval(md, t.row0, f_nx, j_nx, nfft, jmax, flag, a_nx, b_nx, s_nx);
-      if (ok_cu) draw_peak<R>(G0, lds, a_cu, b_cu, s_cu, c0, c1m1, wm1, carry);
+      if (ok_cu) draw_peak<R>(G0, lds, a_cu, b_cu, s_cu, c0, c1m1, ub, carry);
       a_cu = a_nx; b_cu = b_nx; s_cu = s_nx; ok_cu = ok_nx;
       f_nx = f_nn; j_nx = j_nn;
     }
