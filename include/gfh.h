@@ -248,6 +248,31 @@ int gfh_hough(gfh_ctx* ctx, const uint32_t* d_fft_idx, const uint32_t* d_bin, in
 int gfh_select(gfh_ctx* ctx, const int32_t* d_map, const gfh_grid* g, gfh_candidate* d_cands,
                gfh_map_stats* d_stats);
 
+/*
+ * Candidates per "square" of an existing map d_map [n_k][ld_x0] (Sec. IV): the analysis-band
+ * columns (contiguous: f0 falls with the column; GFH_ERR_ARG otherwise) are split into n_sx equal
+ * chunks and the k rows into n_sk (chunk i of an axis of length L is [i L / n, (i + 1) L / n)).
+ * Square q = j * n_sx + i (k chunk j, x0 chunk i) writes d_out[2 q] = its highest count (ties to the
+ * lowest row, then column) and d_out[2 q + 1] = the highest count among its cells at least min_dk
+ * rows from the first (Sec. IV: about 3 bins); band = q, reserved = 0 / 1; count = -1 where the
+ * square has no cell (or no far row).  cr from the mean and deviation over all analysis cells,
+ * which also go to d_stats (may be NULL).  n_k <= 65535.  Synchronous (allocates its scratch).
+ */
+int gfh_select_squares(gfh_ctx* ctx, const int32_t* d_map, const gfh_grid* g, int32_t n_sx,
+                       int32_t n_sk, int32_t min_dk, gfh_candidate* d_out, gfh_map_stats* d_stats);
+
+/*
+ * Coincidences (Sec. IV) between candidate sets a [na] and b [nb] (device, e.g. two detectors'
+ * candidates on the same grid): for candidate i of a, d_match[i] = the index of the nearest
+ * candidate of b by d = sqrt(((x0_b - x0_a)/dx0)^2 + ((k_b - k_a)/dk)^2) (ties to the lower
+ * index) when d <= radius, else -1; d_dist[i] = that distance (-1 when a[i] or all of b have
+ * count -1).  Records with count -1 take no part.  fp64, each operation IEEE-rounded.
+ * Asynchronous.
+ */
+int gfh_coincide(gfh_ctx* ctx, const gfh_candidate* d_a, int32_t na, const gfh_candidate* d_b,
+                 int32_t nb, double dx0, double dk, double radius, int32_t* d_match,
+                 double* d_dist);
+
 /* ---- statistical peakmaps and the learned tile proposer ------------------------------------------
  *
  * The paper proposes machine learning for future work (Sec. VIII); here a small convolutional

@@ -314,6 +314,81 @@ def select_candidates(g: Grid, hmap: np.ndarray):
     return out, (s1, s2, n_cells)
 
 
+def _record(g: Grid, hmap, r: int, m: int, mu: float, sigma: float, f0c, f0n, **extra):
+    y = int(hmap[r, m])
+    k = g.k_min + r * g.dk
+    return dict(row=r, col=m, count=y, cr=(y - mu) / sigma if sigma > 0.0 else 0.0,
+                x0=g.x0_min + (m + 0.5) * g.dx0, k=k, f0=float(f0c[m]),
+                fdot0=-(k * float(f0n[m])), **extra)
+
+
+def select_squares(g: Grid, hmap: np.ndarray, n_sx: int, n_sk: int, min_dk: int = 3):
+    """Candidates per "square" (Sec. IV): the analysis columns and the k rows are each split into
+    equal chunks (n_sx along x0, n_sk along k; chunk i of an axis of length L is [i L / n, (i+1) L / n)),
+    and each square gives its highest count (ties to the lowest row, then column) and a second one:
+    the highest count among its cells at least min_dk k rows away from the first.  The analysis
+    columns are contiguous (f0 falls monotonically with the column).
+
+    Returns {(square, which): record} for which = 0, 1 (squares without cells, or without cells far
+    enough for a second candidate, give no record) and the CR statistics as in select_candidates.
+    """
+    f0c, f0n, band = column_bands(g)
+    ana = np.nonzero(band >= 0)[0]
+    K = g.n_k
+    n_cells = K * ana.size
+    sub = hmap[:, ana].astype(np.int64)
+    s1, s2 = int(sub.sum()), int((sub * sub).sum())
+    if n_cells > 0:
+        mu = float(s1) / float(n_cells)
+        var = float(s2) / float(n_cells) - mu * mu
+        sigma = math.sqrt(var) if var > 0.0 else 0.0
+    else:
+        mu, sigma = 0.0, 0.0
+    out = {}
+    if ana.size == 0:
+        return out, (s1, s2, n_cells)
+    ca, wa = int(ana[0]), int(ana.size)
+    assert ana[-1] - ana[0] + 1 == wa                  # contiguous
+    for j in range(n_sk):
+        r0, r1 = j * K // n_sk, (j + 1) * K // n_sk
+        for i in range(n_sx):
+            c0, c1 = ca + i * wa // n_sx, ca + (i + 1) * wa // n_sx
+            if r1 <= r0 or c1 <= c0:
+                continue
+            sq = j * n_sx + i
+            block = hmap[r0:r1, c0:c1]
+            flat = int(np.argmax(block))
+            rr, cc = divmod(flat, c1 - c0)
+            out[(sq, 0)] = _record(g, hmap, r0 + rr, c0 + cc, mu, sigma, f0c, f0n, square=sq)
+            far = np.abs(np.arange(r0, r1) - (r0 + rr)) >= min_dk
+            if far.any():
+                rows = np.arange(r0, r1)[far]
+                blk2 = hmap[rows, c0:c1]
+                flat2 = int(np.argmax(blk2))
+                r2, c2 = divmod(flat2, c1 - c0)
+                out[(sq, 1)] = _record(g, hmap, int(rows[r2]), c0 + c2, mu, sigma, f0c, f0n, square=sq)
+    return out, (s1, s2, n_cells)
+
+
+def coincidences(a: list, b: list, dx0: float, dk: float, radius: float = 3.0):
+    """For each candidate of set a: the index of the nearest candidate of set b by the Sec. IV
+    distance d = sqrt(((x0_b - x0_a)/dx0)^2 + ((k_b - k_a)/dk)^2) (ties to the lower index) and that
+    distance; the index is -1 when the nearest lies farther than `radius` (coincidence within
+    `radius` bins, Sec. IV uses 3) or when b is empty."""
+    match, dist = [], []
+    for ca in a:
+        best, bj = math.inf, -1
+        for j, cb in enumerate(b):
+            dxn = (cb["x0"] - ca["x0"]) / dx0
+            dkn = (cb["k"] - ca["k"]) / dk
+            d = math.sqrt(dxn * dxn + dkn * dkn)
+            if d < best:
+                best, bj = d, j
+        match.append(bj if best <= radius else -1)
+        dist.append(best if bj >= 0 else -1.0)
+    return match, dist
+
+
 # ----------------------------------------------------------------------------------------------
 # Sec. III peakmap
 # ----------------------------------------------------------------------------------------------

@@ -35,7 +35,7 @@ EXPORTED = [
     "gfh_synth_peaks", "gfh_synth_images", "gfh_peaks_to_images",
     "gfh_cnn_create", "gfh_cnn_destroy", "gfh_cnn_param_count", "gfh_cnn_get_params",
     "gfh_cnn_set_params", "gfh_cnn_forward", "gfh_cnn_gradients", "gfh_cnn_train_step",
-    "gfh_propose_tiles", "gfh_conv3x3",
+    "gfh_propose_tiles", "gfh_conv3x3", "gfh_select_squares", "gfh_coincide",
 ]
 N_CLASSES = 4097        # 64 x 64 coarse tiles + no signal
 IMG = 256
@@ -139,6 +139,8 @@ def lib() -> ctypes.CDLL:
                                    P(ctypes.c_float)],
             "gfh_propose_tiles": [vp, vp, i32, vp, i32, ctypes.c_float, vp, vp, vp],
             "gfh_conv3x3": [vp, i32, i32, i32, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp],
+            "gfh_select_squares": [vp, vp, P(GridC), i32, i32, i32, vp, vp],
+            "gfh_coincide": [vp, vp, i32, vp, i32, dbl, dbl, dbl, vp, vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -307,6 +309,20 @@ class Context:
         rc = lib().gfh_hough(self._h, _ptr(fft_idx), _ptr(bins), n_peaks, ctypes.byref(c),
                              _ptr(out_map), _ptr(cands), _ptr(stats))
         _ok(rc, "gfh_hough")
+
+    def select_squares(self, hmap, g: Grid, n_sx: int, n_sk: int, out, min_dk: int = 3,
+                       stats=None) -> None:
+        """gfh_select_squares: two candidates per square into out (uint8 tensor of
+        2 n_sx n_sk x 64 bytes)."""
+        gc = g.to_c()
+        _ok(lib().gfh_select_squares(self._h, _ptr(hmap), ctypes.byref(gc), n_sx, n_sk, min_dk,
+                                     _ptr(out), _ptr(stats)), "gfh_select_squares")
+
+    def coincide(self, a, na: int, b, nb: int, dx0: float, dk: float, radius: float, match,
+                 dist) -> None:
+        """gfh_coincide: nearest candidate of b for each candidate of a (device buffers)."""
+        _ok(lib().gfh_coincide(self._h, _ptr(a), na, _ptr(b), nb, dx0, dk, radius, _ptr(match),
+                               _ptr(dist)), "gfh_coincide")
 
     def select(self, hmap, g: Grid, cands, stats=None) -> None:
         c = g.to_c()

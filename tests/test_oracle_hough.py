@@ -216,3 +216,69 @@ def test_candidate_recovers_injection():
     assert best["f0"] == pytest.approx(f0, abs=g.df)
     assert best["fdot0"] == pytest.approx(-k * f0 ** n, rel=1e-2)
     assert best["cr"] > 10
+
+
+# ---- squares (Sec. IV) and coincidences ------------------------------------------------------------
+
+def _tiny_map(seed=3, n_k=11):
+    from paper_1810_09784_gb300 import synth
+    g = O.make_grid(O.Grid(n=4.0, df=0.5, bin_lo=100, bin_hi=140, n_fft=30, t_first=1.0,
+                           t_hop=1.0, t_obs=31.0, n_k=n_k, ana_lo=51.0, ana_hi=69.0, band_hz=1.0))
+    fi, bj = synth.random_peaklist(30, 98, 142, 0.2, seed)
+    return g, O.hough_map(g, fi, bj)
+
+
+def test_squares_brute_force():
+    g, hm = _tiny_map()
+    out, (s1, s2, n) = O.select_squares(g, hm, 3, 2, min_dk=3)
+    _, _, band = O.column_bands(g)
+    cols = [m for m in range(g.n_x0) if band[m] >= 0]
+    wa = len(cols)
+    for j in range(2):
+        rows = list(range(j * g.n_k // 2, (j + 1) * g.n_k // 2))
+        for i in range(3):
+            cs = cols[i * wa // 3:(i + 1) * wa // 3]
+            sq = j * 3 + i
+            best = None
+            for r in rows:                      # row-major scan: first maximum wins
+                for m in cs:
+                    if best is None or hm[r, m] > hm[best[0], best[1]]:
+                        best = (r, m)
+            rec = out[(sq, 0)]
+            assert (rec["row"], rec["col"], rec["count"]) == (best[0], best[1], int(hm[best]))
+            best2 = None
+            for r in rows:
+                if abs(r - best[0]) < 3:
+                    continue
+                for m in cs:
+                    if best2 is None or hm[r, m] > hm[best2[0], best2[1]]:
+                        best2 = (r, m)
+            if best2 is None:
+                assert (sq, 1) not in out
+            else:
+                rec2 = out[(sq, 1)]
+                assert (rec2["row"], rec2["col"]) == best2 and rec2["count"] <= rec["count"]
+                assert abs(rec2["row"] - rec["row"]) >= 3
+
+
+def test_one_square_is_the_global_maximum_of_the_band_candidates():
+    g, hm = _tiny_map(seed=8)
+    out, stats = O.select_squares(g, hm, 1, 1)
+    bands, stats_b = O.select_candidates(g, hm)
+    assert stats == stats_b
+    top = max(bands, key=lambda c: (c["count"], -c["row"], -c["col"]))
+    rec = out[(0, 0)]
+    assert (rec["count"], rec["row"], rec["col"], rec["cr"]) == (top["count"], top["row"], top["col"], top["cr"])
+
+
+def test_coincidence_distance_and_radius():
+    a = [dict(x0=1.0, k=2.0), dict(x0=10.0, k=5.0), dict(x0=-4.0, k=0.0)]
+    b = [dict(x0=1.0 + 3 * 0.5, k=2.0 + 4 * 0.25), dict(x0=10.0, k=5.0 + 2.9 * 0.25),
+         dict(x0=1.0 - 3 * 0.5, k=2.0 - 4 * 0.25)]
+    match, dist = O.coincidences(a, b, dx0=0.5, dk=0.25, radius=3.0)
+    assert dist[0] == 5.0 and match[0] == -1             # 3-4-5 triangle, beyond 3 bins; tie -> index 0
+    assert match[1] == 1 and abs(dist[1] - 2.9) < 1e-12
+    assert match[2] == -1
+    match2, dist2 = O.coincidences(a, b, dx0=0.5, dk=0.25, radius=5.0)
+    assert match2[0] == 0 and dist2[0] == 5.0             # equal distances: the lower index
+    assert O.coincidences(a, [], 0.5, 0.25) == ([-1, -1, -1], [-1.0, -1.0, -1.0])
