@@ -245,7 +245,9 @@ __device__ __forceinline__ void hough_tile(const MapDev* __restrict__ maps, cons
     const int col = ch * 128 + lane * 4;
     const bool in = col < C;
     int band[4] = {-1, -1, -1, -1};
-    unsigned long long best[4] = {0ull, 0ull, 0ull, 0ull};
+    // per column: best count over the rows so far and its row (strictly greater, so the first
+    // row reaching the best count wins: the lowest cell index)
+    int bc[4] = {-1, -1, -1, -1}, br[4] = {0, 0, 0, 0};
     if (SELECT && in) {
       const int4 bv = __ldg(reinterpret_cast<const int4*>(md.col_band + t.col0 + col));
       band[0] = bv.x; band[1] = bv.y; band[2] = bv.z; band[3] = bv.w;
@@ -271,21 +273,23 @@ __device__ __forceinline__ void hough_tile(const MapDev* __restrict__ maps, cons
         const int64_t row = t.row0 + rr;
         __stcs(reinterpret_cast<int4*>(md.out + row * md.ld + t.col0 + col), v);
         if (SELECT) {
-          const uint32_t lin0 = (uint32_t)row * W32 + (uint32_t)(t.col0 + col);
           const int vals[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             if (band[q] >= 0) {
               s1 += vals[q];
               s2 += (long long)vals[q] * vals[q];
-              const unsigned long long k = cand_key(vals[q], lin0 + q);
-              best[q] = k > best[q] ? k : best[q];
+              if (vals[q] > bc[q]) { bc[q] = vals[q]; br[q] = rr; }
             }
           }
         }
       }
     }
     if (SELECT) {
+      unsigned long long best[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        best[q] = cand_key(bc[q], (uint32_t)(t.row0 + br[q]) * W32 + (uint32_t)(t.col0 + col + q));
       // merge equal-band neighbours among the lane's 4 columns, then one shared atomic per run
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
