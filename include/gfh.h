@@ -166,6 +166,37 @@ int gfh_grid_tables(const gfh_grid* g, int64_t* h_U, int64_t* h_B, int64_t* h_S)
 /* Per column m < n_x0: candidate band (-1 outside the analysis band), f0 and f0^n of its centre. */
 int gfh_grid_columns(const gfh_grid* g, int32_t* h_band, double* h_f0, double* h_f0n);
 
+/*
+ * Braking-index grid of Eq. dn_powlaws (Sec. VI.A): n_0 = n_lo, then n_{j+1} = n_j + dn_j with dn_j
+ * the largest step (bisection to a relative 1e-9) for which the Eq. powlaws frequencies of n_j and
+ * n_j + dn_j, at the same f0 and |fdot0| (k = |fdot0| / f0^n), differ by at most df over the
+ * observation.  The difference is f0 |g(n2, u) - g(n1, u)| with g(n, u) = (1 + (n-1) u)^(-1/(n-1))
+ * and u = |fdot0| t / f0; its maximum is taken over 64 f0 log-spaced in [f_min, f_max] and 256 equal
+ * steps of u in [0, fdot_hi t_obs / f0].  The last point is n_hi.  Writes at most cap points to
+ * h_n and their number to *n_out; GFH_ERR_SIZE when cap is too small (*n_out = points so far).
+ */
+int gfh_n_grid(double n_lo, double n_hi, double df, double f_min, double f_max, double fdot_hi,
+               double t_obs, int32_t cap, double* h_n, int32_t* n_out);
+
+/*
+ * The k grid of Eq. dkeqn (Sec. VI.B) as uniform segments, each usable as the k grid of a
+ * gfh_grid (k_min, dk, n_k): k runs from fdot_lo / f_max^n to the first row at or above
+ * fdot_hi / f_min^n; the Eq. dkeqn step at k is |dk(k)| = k (1 - (1 + df/f_max)^(-n)) (the paper's
+ * dk is negative; its size is used).  A segment starting at k_s has the step dk_s = |dk(k_s)| and
+ * floor((growth - 1) / (1 - (1 + df/f_max)^(-n))) + 1 rows (at most max_rows), so no row is coarser
+ * than growth times what the equation asks; the next segment starts one step after the last row.
+ * growth = 1 gives one row per segment: the Eq. dkeqn grid itself.
+ */
+typedef struct gfh_k_segment {
+  double k_min;
+  double dk;
+  int32_t n_k;
+  int32_t reserved;
+} gfh_k_segment;
+int gfh_k_segments(double n, double df, double f_min, double f_max, double fdot_lo, double fdot_hi,
+                   double growth, int32_t max_rows, int32_t cap, gfh_k_segment* h_out,
+                   int32_t* n_out);
+
 /* ---- GPU entry points ----------------------------------------------------------------------- */
 
 /*

@@ -82,6 +82,79 @@ def dk_step(k: float, df: float, f0max: float, n: float) -> float:
     return k * ((1.0 + df / f0max) ** (-n) - 1.0)
 
 
+# ---- Sec. VI grids on n and k -------------------------------------------------------------------
+
+def powlaw_ratio(n: float, u):
+    """f(t)/f0 of Eq. powlaws as a function of u = |fdot0| t / f0 (k = |fdot0| / f0^n):
+    (1 + (n-1) u)^(-1/(n-1))."""
+    u = np.asarray(u, dtype=np.float64)
+    return np.exp(-np.log1p((n - 1.0) * u) / (n - 1.0))
+
+
+def dn_max_df(n1: float, n2: float, f_min: float, f_max: float, fdot_hi: float, t_obs: float,
+              n_f: int = 64, n_u: int = 256) -> float:
+    """Largest frequency difference (Eq. dn_powlaws) between the power laws of braking indices n1
+    and n2 with the same f0 and fdot0, over f0 on n_f log-spaced values in [f_min, f_max] and u =
+    |fdot0| t / f0 on n_u equal steps in [0, fdot_hi t_obs / f0]."""
+    best = 0.0
+    for a in range(n_f):
+        f0 = f_min * (f_max / f_min) ** (a / (n_f - 1)) if n_f > 1 else f_min
+        u = fdot_hi * t_obs / f0 * np.arange(n_u) / (n_u - 1)
+        d = f0 * np.abs(powlaw_ratio(n2, u) - powlaw_ratio(n1, u))
+        best = max(best, float(d.max()))
+    return best
+
+
+def n_grid(n_lo: float, n_hi: float, df: float, f_min: float, f_max: float, fdot_hi: float,
+           t_obs: float, rel_tol: float = 1e-9, max_points: int = 100000):
+    """Braking indices from n_lo: each step dn the largest (bisection) keeping the Eq. dn_powlaws
+    frequency difference within df over the observation; the last point is n_hi or the first
+    point beyond it."""
+    out = [n_lo]
+    n = n_lo
+    while n < n_hi and len(out) < max_points:
+        span = n_hi - n
+        if dn_max_df(n, n + span, f_min, f_max, fdot_hi, t_obs) <= df:
+            out.append(n_hi)
+            break
+        lo, hi = 0.0, span
+        while hi - lo > rel_tol * hi:
+            mid = 0.5 * (lo + hi)
+            if dn_max_df(n, n + mid, f_min, f_max, fdot_hi, t_obs) <= df:
+                lo = mid
+            else:
+                hi = mid
+        if lo <= 0.0:
+            raise ValueError("no braking-index step keeps the frequency difference within df")
+        n = n + lo
+        out.append(n)
+    return out
+
+
+def k_segments(n: float, df: float, f_min: float, f_max: float, fdot_lo: float, fdot_hi: float,
+               growth: float = 1.0, max_rows: int = 1 << 30):
+    """Eq. dkeqn k grid (Sec. VI.B) as uniform segments [(k_start, dk, rows)].  |dk(k)| =
+    k (1 - (1 + df/f_max)^(-n)); a segment starting at k_s has step |dk(k_s)| and the rows m whose
+    k_s + m dk_s keeps |dk| within growth dk_s (m <= (growth - 1) / c, at most max_rows); the next
+    starts one step after its last row; the grid ends at the first row >= k_hi."""
+    c = 1.0 - (1.0 + df / f_max) ** (-n)
+    k_lo, k_hi = fdot_lo / f_max ** n, fdot_hi / f_min ** n
+    rows_full = min(int(math.floor((growth - 1.0) / c)) + 1, max_rows)
+    out, k = [], k_lo
+    while True:
+        dk = k * c
+        rows = rows_full
+        # stop at the first row >= k_hi
+        need = int(math.ceil((k_hi - k) / dk)) + 1 if k < k_hi else 1
+        rows = max(1, min(rows, need))
+        out.append((k, dk, rows))
+        last = k + (rows - 1) * dk
+        if last >= k_hi:
+            break
+        k = k + rows * dk
+    return out
+
+
 def coincidence_distance(x0_a, k_a, x0_b, k_b, dx0: float, dk: float):
     """Sec. IV distance between two points of the (x0, k) plane in units of bins."""
     return np.sqrt(((np.asarray(x0_b) - x0_a) / dx0) ** 2 + ((np.asarray(k_b) - k_a) / dk) ** 2)

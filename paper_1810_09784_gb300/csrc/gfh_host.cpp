@@ -190,6 +190,96 @@ extern "C" int gfh_check(gfh_ctx* c) {
   return GFH_OK;
 }
 
+// ---- grids on n and k (Sec. VI) -------------------------------------------------------------------
+
+namespace {
+
+// f(t) / f0 of Eq. powlaws at u = |fdot0| t / f0.
+double powlaw_ratio(double n, double u) { return std::exp(-std::log1p((n - 1.0) * u) / (n - 1.0)); }
+
+// Largest |f_{n2} - f_{n1}| over the f0 and u lattice of gfh_n_grid.
+double dn_max_df(double n1, double n2, double f_min, double f_max, double fdot_hi, double t_obs) {
+  constexpr int kF = 64, kU = 256;
+  double best = 0.0;
+  for (int a = 0; a < kF; ++a) {
+    const double f0 = f_min * std::pow(f_max / f_min, (double)a / (kF - 1));
+    const double umax = fdot_hi * t_obs / f0;
+    for (int b = 0; b < kU; ++b) {
+      const double u = umax * b / (kU - 1);
+      const double d = f0 * std::fabs(powlaw_ratio(n2, u) - powlaw_ratio(n1, u));
+      if (d > best) best = d;
+    }
+  }
+  return best;
+}
+
+}  // namespace
+
+extern "C" int gfh_n_grid(double n_lo, double n_hi, double df, double f_min, double f_max,
+                          double fdot_hi, double t_obs, int32_t cap, double* h_n, int32_t* n_out) {
+  if (!h_n || !n_out || cap < 1 || !(n_lo > 1.0) || !(n_hi >= n_lo) || !(df > 0.0) ||
+      !(f_min > 0.0) || !(f_max >= f_min) || !(fdot_hi >= 0.0) || !(t_obs > 0.0))
+    return GFH_ERR_ARG;
+  int32_t cnt = 0;
+  h_n[cnt++] = n_lo;
+  double n = n_lo;
+  while (n < n_hi) {
+    if (cnt >= cap) { *n_out = cnt; return GFH_ERR_SIZE; }
+    const double span = n_hi - n;
+    if (dn_max_df(n, n + span, f_min, f_max, fdot_hi, t_obs) <= df) {
+      h_n[cnt++] = n_hi;
+      break;
+    }
+    double lo = 0.0, hi = span;
+    while (hi - lo > 1e-9 * hi) {
+      const double mid = 0.5 * (lo + hi);
+      if (dn_max_df(n, n + mid, f_min, f_max, fdot_hi, t_obs) <= df) lo = mid;
+      else hi = mid;
+    }
+    if (lo <= 0.0) { *n_out = cnt; return GFH_ERR_ARG; }
+    n = n + lo;
+    h_n[cnt++] = n;
+  }
+  *n_out = cnt;
+  return GFH_OK;
+}
+
+extern "C" int gfh_k_segments(double n, double df, double f_min, double f_max, double fdot_lo,
+                              double fdot_hi, double growth, int32_t max_rows, int32_t cap,
+                              gfh_k_segment* h_out, int32_t* n_out) {
+  if (!h_out || !n_out || cap < 1 || !(n > 1.0) || !(df > 0.0) || !(f_min > 0.0) ||
+      !(f_max >= f_min) || !(fdot_lo > 0.0) || !(fdot_hi >= fdot_lo) || !(growth >= 1.0) ||
+      max_rows < 1)
+    return GFH_ERR_ARG;
+  const double c = 1.0 - std::pow(1.0 + df / f_max, -n);
+  const double k_lo = fdot_lo / std::pow(f_max, n), k_hi = fdot_hi / std::pow(f_min, n);
+  const double full = std::floor((growth - 1.0) / c) + 1.0;
+  const int32_t rows_full = full > (double)max_rows ? max_rows : (int32_t)full;
+  int32_t cnt = 0;
+  double k = k_lo;
+  for (;;) {
+    if (cnt >= cap) { *n_out = cnt; return GFH_ERR_SIZE; }
+    const double dk = k * c;
+    int32_t rows = rows_full;
+    if (k < k_hi) {
+      const double need = std::ceil((k_hi - k) / dk) + 1.0;
+      if (need < (double)rows) rows = (int32_t)need;
+    } else {
+      rows = 1;
+    }
+    if (rows < 1) rows = 1;
+    h_out[cnt].k_min = k;
+    h_out[cnt].dk = dk;
+    h_out[cnt].n_k = rows;
+    h_out[cnt].reserved = 0;
+    ++cnt;
+    if (k + (rows - 1) * dk >= k_hi) break;
+    k = k + rows * dk;
+  }
+  *n_out = cnt;
+  return GFH_OK;
+}
+
 // ---- plans --------------------------------------------------------------------------------------
 
 namespace {

@@ -36,6 +36,7 @@ EXPORTED = [
     "gfh_cnn_create", "gfh_cnn_destroy", "gfh_cnn_param_count", "gfh_cnn_get_params",
     "gfh_cnn_set_params", "gfh_cnn_forward", "gfh_cnn_gradients", "gfh_cnn_train_step",
     "gfh_propose_tiles", "gfh_conv3x3", "gfh_select_squares", "gfh_coincide",
+    "gfh_n_grid", "gfh_k_segments",
 ]
 N_CLASSES = 4097        # 64 x 64 coarse tiles + no signal
 IMG = 256
@@ -141,6 +142,8 @@ def lib() -> ctypes.CDLL:
             "gfh_conv3x3": [vp, i32, i32, i32, i32, i32, i32, vp, vp, vp, vp, vp, vp, vp],
             "gfh_select_squares": [vp, vp, P(GridC), i32, i32, i32, vp, vp],
             "gfh_coincide": [vp, vp, i32, vp, i32, dbl, dbl, dbl, vp, vp],
+            "gfh_n_grid": [dbl, dbl, dbl, dbl, dbl, dbl, dbl, i32, vp, P(i32)],
+            "gfh_k_segments": [dbl, dbl, dbl, dbl, dbl, dbl, dbl, i32, i32, vp, P(i32)],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -224,6 +227,29 @@ def grid_tables(g: Grid):
     _ok(lib().gfh_grid_tables(ctypes.byref(c), U.ctypes.data, B.ctypes.data, S.ctypes.data),
         "gfh_grid_tables")
     return U, B, S
+
+
+def n_grid(n_lo: float, n_hi: float, df: float, f_min: float, f_max: float, fdot_hi: float,
+           t_obs: float, cap: int = 100000) -> np.ndarray:
+    """gfh_n_grid: braking indices of Eq. dn_powlaws (Sec. VI.A)."""
+    out = np.empty(cap, np.float64)
+    n = ctypes.c_int32()
+    _ok(lib().gfh_n_grid(n_lo, n_hi, df, f_min, f_max, fdot_hi, t_obs, cap, out.ctypes.data,
+                         ctypes.byref(n)), "gfh_n_grid")
+    return out[: n.value].copy()
+
+
+K_SEGMENT_DTYPE = np.dtype([("k_min", "<f8"), ("dk", "<f8"), ("n_k", "<i4"), ("reserved", "<i4")])
+
+
+def k_segments(n: float, df: float, f_min: float, f_max: float, fdot_lo: float, fdot_hi: float,
+               growth: float = 1.0, max_rows: int = 1 << 30, cap: int = 1 << 20) -> np.ndarray:
+    """gfh_k_segments: the Eq. dkeqn k grid (Sec. VI.B) as uniform segments."""
+    out = np.zeros(cap, K_SEGMENT_DTYPE)
+    cnt = ctypes.c_int32()
+    _ok(lib().gfh_k_segments(n, df, f_min, f_max, fdot_lo, fdot_hi, growth, max_rows, cap,
+                             out.ctypes.data, ctypes.byref(cnt)), "gfh_k_segments")
+    return out[: cnt.value].copy()
 
 
 def grid_columns(g: Grid):

@@ -83,3 +83,32 @@ def test_invalid_requests_are_rejected(built_lib):
         with pytest.raises(built_lib.GfhError) as e:
             built_lib.grid_make(built_lib.Grid(**dict(base, **bad)))
         assert e.value.code == built_lib.GFH_ERR_ARG
+
+
+def test_n_grid_matches_oracle(built_lib):
+    args = (2.5, 7.0, 0.5, 100.0, 400.0, 0.02, 1800.0)
+    got = built_lib.n_grid(*args)
+    ref = np.array(O.n_grid(*args))
+    assert got.size == ref.size
+    assert np.allclose(got, ref, rtol=0, atol=1e-7)     # libm vs numpy exp/log1p: last-ulp level
+    assert got[0] == 2.5 and got[-1] == 7.0
+
+
+@pytest.mark.parametrize("growth", [1.0, 1.5, 2.0, 4.0])
+def test_k_segments_match_oracle(built_lib, growth):
+    args = (5.0, 0.5, 100.0, 400.0, 1e-6, 1e-3)
+    got = built_lib.k_segments(*args, growth=growth)
+    ref = O.k_segments(*args, growth=growth)
+    assert got.size == len(ref)
+    for g, (k0, dk, rows) in zip(got, ref):
+        assert (float(g["k_min"]), float(g["dk"]), int(g["n_k"])) == (k0, dk, rows)
+
+
+def test_k_segments_feed_grids(built_lib):
+    """Each segment is a valid k grid of a map: grid_make accepts it and keeps its step."""
+    segs = built_lib.k_segments(4.0, 0.5, 100.0, 400.0, 1e-5, 1e-4, growth=2.0, max_rows=400)
+    _, _, grids = workloads.plain_small()
+    for s in segs[:5]:
+        g = built_lib.grid_make(built_lib.Grid(**dict(grids[0], n=4.0, k_min=float(s["k_min"]),
+                                                      dk=float(s["dk"]), n_k=int(s["n_k"]))))
+        assert g.dk == float(s["dk"]) and g.n_k == int(s["n_k"])

@@ -107,3 +107,62 @@ def test_amplitude_for_snr():
     t = np.arange(N)
     X = np.fft.rfft(A * np.sin(2 * np.pi * 100 * t / N))
     assert abs(X[100]) ** 2 == pytest.approx(snr * N, rel=1e-9)
+
+
+# ---- Sec. VI grids on n (Eq. dn_powlaws) and k (Eq. dkeqn) ---------------------------------------
+
+def test_powlaw_ratio_is_the_power_law():
+    # f(t) / f0 of Eq. powlaws with k = fdot0 / f0^n, against the formula written in f0, k, t
+    for n, f0, fdot0, t in ((2.5, 300.0, 1e-2, 1000.0), (7.0, 120.0, 3e-3, 5000.0), (4.0, 50.0, 1e-4, 10.0)):
+        k = fdot0 / f0 ** n
+        ref = O.powerlaw_f(t, f0, k, n) / f0
+        assert abs(float(O.powlaw_ratio(n, fdot0 * t / f0)) - ref) < 1e-14
+
+
+def test_n_grid_small_spindown_closed_form():
+    """For u = fdot0 t / f0 << 1 the two power laws differ by dn u^2 f0 / 2 (second order of
+    Eq. powlaws in n), largest at f_min: the first step is dn = 2 df f_min / (fdot T)^2."""
+    df, fmin, fmax, fdot, T = 5e-5, 100.0, 400.0, 1e-5, 1e4      # u <= 1e-3, dn ~ 1
+    grid = O.n_grid(3.0, 7.0, df, fmin, fmax, fdot, T)
+    dn0 = grid[1] - grid[0]
+    ref = 2 * df * fmin / (fdot * T) ** 2
+    assert abs(dn0 / ref - 1) < 0.01
+
+
+def test_n_grid_steps_are_maximal():
+    df, fmin, fmax, fdot, T = 0.5, 100.0, 400.0, 0.02, 1800.0
+    grid = O.n_grid(2.5, 7.0, df, fmin, fmax, fdot, T)
+    assert grid[0] == 2.5 and grid[-1] == 7.0
+    assert all(b > a for a, b in zip(grid, grid[1:]))
+    for a, b in list(zip(grid, grid[1:]))[:-1][:6]:
+        assert O.dn_max_df(a, b, fmin, fmax, fdot, T) <= df * (1 + 1e-9)
+        assert O.dn_max_df(a, a + (b - a) * 1.01, fmin, fmax, fdot, T) > df
+        # a denser evaluation does not find a larger difference than 1 % above df
+        assert O.dn_max_df(a, b, fmin, fmax, fdot, T, n_f=257, n_u=1025) <= df * 1.01
+    # steps grow with n (higher n decelerates faster: fewer points, Sec. VI.A)
+    steps = np.diff(grid[:-1])
+    assert steps[-1] > steps[0]
+
+
+def test_k_segments_reproduce_eq_dkeqn():
+    n, df, fmin, fmax = 5.0, 0.5, 100.0, 400.0
+    fdot_lo, fdot_hi = 1e-6, 1e-3
+    c = 1 - (1 + df / fmax) ** (-n)
+    # growth 1: one row per segment, k_{r+1} = k_r + |dk(k_r)| = k_r (2 - (1 + df/f_max)^-n)
+    seg = O.k_segments(n, df, fmin, fmax, fdot_lo, fdot_hi, growth=1.0)
+    ks = np.array([s[0] for s in seg])
+    assert all(s[2] == 1 for s in seg)
+    assert np.allclose(ks[1:] / ks[:-1], 2 - (1 + df / fmax) ** (-n), rtol=1e-12, atol=0)
+    assert ks[0] == fdot_lo / fmax ** n and ks[-1] >= fdot_hi / fmin ** n > ks[-2]
+    # Taylor form of Eq. dkeqn: |dk| ~ n k df / f_max
+    assert abs(seg[0][1] / (n * ks[0] * df / fmax) - 1) < n * df / fmax
+    # growth 2: uniform segments never coarser than Eq. dkeqn, contiguous, covering k_hi
+    seg2 = O.k_segments(n, df, fmin, fmax, fdot_lo, fdot_hi, growth=2.0)
+    for (k0, dk, rows), nxt in zip(seg2, seg2[1:] + [None]):
+        assert dk == k0 * c
+        last = k0 + (rows - 1) * dk
+        assert last * c <= 2.0 * dk * (1 + 1e-12)       # every row's Eq. dkeqn step >= dk / 1
+        if nxt is not None:
+            assert nxt[0] == k0 + rows * dk
+    assert seg2[-1][0] + (seg2[-1][2] - 1) * seg2[-1][1] >= fdot_hi / fmin ** n
+    assert sum(r for _, _, r in seg2) < 1.5 * len(seg)
