@@ -617,6 +617,8 @@ def run_proposer(args):
         torch.cuda.synchronize()
         t_train = time.perf_counter() - t0
         bank = PR.HoughBank(ctx, spec, max_sel=256)
+        bank.load_peaks(PR.draw(spec, np.arange(val0, val0 + nl)))
+        tuned, _ = bank.autotune()
         res = {}
         for cap in (32, 256):
             tau, val = PR.choose_tau(ctx, net, spec, val0, 51 * 40, bank, cap)
@@ -632,13 +634,22 @@ def run_proposer(args):
                     smp = PR.draw(spec, np.arange(held0 + nl * st, held0 + nl * (st + 1)))
                     bank.load_peaks(smp)
                     torch.cuda.synchronize()
+                    timed = st >= args.warmup and cap == 32
+                    if timed:
+                        torch.cuda.nvtx.range_push("full_exact")
                     a.record(stream)
                     bank.full()
                     b.record(stream)
                     torch.cuda.synchronize()
+                    if timed:
+                        torch.cuda.nvtx.range_pop()
+                        torch.cuda.nvtx.range_push("pruned")
                     c.record(stream)
                     search.run()
                     d.record(stream)
+                    if timed:
+                        torch.cuda.synchronize()
+                        torch.cuda.nvtx.range_pop()
                     torch.cuda.synchronize()
                     f0_, f1_ = ev(), ev()
                     f0_.record(stream)
@@ -713,7 +724,7 @@ def run_proposer(args):
                                "(1799 FFTs, 100-400 Hz, 500 k rows), half with one power-law "
                                "injection (SNR 2-8); at most 32 of 64 x 64 coarse tiles per map, "
                                "full search of maps whose proposal leaves more than tau",
-                   "n_sel": 32, "tau": r["tau"], "recall": summ["recall"], "agreement": summ["agreement"],
+                   "n_sel": 32, "tile": list(tuned), "tau": r["tau"], "recall": summ["recall"], "agreement": summ["agreement"],
                    "held_out_maps": summ["maps"], "injected": summ["injected"],
                    "detected_full": summ["det_full"], "detected_kept": summ["det_kept"],
                    "fallback_frac": summ["fallback_frac"], "fallback_injected": summ["fallback_injected"],

@@ -53,11 +53,15 @@ Layout make_layout() {
   return L;
 }
 
-// Channel 0 of a pixel holding `count` peaks: bf16(float(log(1 + count))), log taken in double.
-__device__ __forceinline__ uint32_t pixel_word(uint32_t count, float nplane) {
-  const __nv_bfloat16 a = __float2bfloat16_rn((float)log1p((double)count));
+// Channel 0 of a pixel holding `count` peaks: bf16(float(log(1 + count))), log taken in double
+// (a host-built table for small counts; fp64 is slow on this part).
+__device__ __forceinline__ uint32_t pixel_word(uint32_t count, float nplane,
+                                               const uint16_t* __restrict__ log_tab) {
+  const uint32_t a = count < (uint32_t)kLogTable
+                         ? (uint32_t)__ldg(log_tab + count)
+                         : (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn((float)log1p((double)count)));
   const __nv_bfloat16 b = __float2bfloat16_rn(nplane);
-  return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+  return a | ((uint32_t)__bfloat16_as_ushort(b) << 16);
 }
 
 // Image of sample b: pixel (tb, fb) counts the peaks in FFTs [tb n_fft/256, (tb+1) n_fft/256) and
@@ -65,7 +69,7 @@ __device__ __forceinline__ uint32_t pixel_word(uint32_t count, float nplane) {
 __global__ void k_synth_images(uint64_t seed, int64_t sample0, int n_fft, int bin_lo, int nb,
                                uint32_t p_noise24, const uint32_t* __restrict__ p_track24,
                                const int32_t* __restrict__ tracks, const float* __restrict__ nplane,
-                               uint32_t* __restrict__ img) {
+                               const uint16_t* __restrict__ log_tab, uint32_t* __restrict__ img) {
   const int b = blockIdx.y;
   const int pix = blockIdx.x * blockDim.x + threadIdx.x;
   if (pix >= kImg * kImg) return;
@@ -81,7 +85,7 @@ __global__ void k_synth_images(uint64_t seed, int64_t sample0, int n_fft, int bi
     for (int j = j0; j < j1; ++j)
       cnt += gfh_synth_peak(seed, sample, (uint32_t)i, (uint32_t)j, p_noise24, tbin, pt);
   }
-  img[(int64_t)b * kImg * kImg + pix] = pixel_word(cnt, nplane[b]);
+  img[(int64_t)b * kImg * kImg + pix] = pixel_word(cnt, nplane[b], log_tab);
 }
 
 // Counts peaks per pixel: list l of the peak lists into image l (one 32-bit word per pixel,
@@ -105,10 +109,11 @@ __global__ void k_image_count(const uint32_t* __restrict__ fft_idx, const uint32
   }
 }
 
-__global__ void k_image_finish(uint32_t* __restrict__ img, const float* __restrict__ nplane) {
+__global__ void k_image_finish(uint32_t* __restrict__ img, const float* __restrict__ nplane,
+                               const uint16_t* __restrict__ log_tab) {
   const int pix = blockIdx.x * blockDim.x + threadIdx.x;
   uint32_t* im = img + (int64_t)blockIdx.y * kImg * kImg;
-  if (pix < kImg * kImg) im[pix] = pixel_word(im[pix], nplane[blockIdx.y]);
+  if (pix < kImg * kImg) im[pix] = pixel_word(im[pix], nplane[blockIdx.y], log_tab);
 }
 
 // Tile proposals of one map per block.  The logits give p(d, xt) (softmax over the 4096 + 1
@@ -981,7 +986,7 @@ extern "C" int gfh_synth_images(gfh_ctx* ctx, uint64_t seed, int64_t sample0, in
   dim3 grid((kImg * kImg + 255) / 256, batch);
   k_synth_images<<<grid, 256, 0, ctx->stream>>>(seed, sample0, n_fft, bin_lo, bin_hi - bin_lo + 1,
                                                 p_noise24, d_p_track24, d_tracks, d_nplane,
-                                                (uint32_t*)d_images);
+                                                ctx->d_log1p, (uint32_t*)d_images);
   GFH_CUDA_TRY(cudaGetLastError());
   return GFH_OK;
 }
@@ -1002,7 +1007,7 @@ extern "C" int gfh_peaks_to_images(gfh_ctx* ctx, const gfh_peaks* peaks, int32_t
                                                        n_fft, bin_lo, bin_hi - bin_lo + 1, img,
                                                        ctx->d_flag);
   GFH_CUDA_TRY(cudaGetLastError());
-  k_image_finish<<<dim3(kImg * kImg / 256, L), 256, 0, ctx->stream>>>(img, d_nplane);
+  k_image_finish<<<dim3(kImg * kImg / 256, L), 256, 0, ctx->stream>>>(img, d_nplane, ctx->d_log1p);
   GFH_CUDA_TRY(cudaGetLastError());
   return GFH_OK;
 }

@@ -153,6 +153,20 @@ extern "C" int gfh_create(gfh_ctx** out, int device, void* stream) {
     gfh_destroy(c);
     return GFH_ERR_CUDA;
   }
+  // image channel 0 for small peak counts: bf16 (round to nearest even) of float(log1p(count))
+  std::vector<uint16_t> tab(kLogTable);
+  for (int i = 0; i < kLogTable; ++i) {
+    const float f = (float)std::log1p((double)i);
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    tab[i] = (uint16_t)((u + 0x7fffu + ((u >> 16) & 1u)) >> 16);
+  }
+  if (cudaMalloc(&c->d_log1p, kLogTable * sizeof(uint16_t)) != cudaSuccess ||
+      cudaMemcpy(c->d_log1p, tab.data(), kLogTable * sizeof(uint16_t), cudaMemcpyHostToDevice) !=
+          cudaSuccess) {
+    gfh_destroy(c);
+    return GFH_ERR_CUDA;
+  }
   *out = c;
   return GFH_OK;
 }
@@ -165,6 +179,7 @@ extern "C" int gfh_destroy(gfh_ctx* c) {
   if (c->pm_buf) cudaFree(c->pm_buf);
   if (c->d_flag) cudaFree(c->d_flag);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
+  if (c->d_log1p) cudaFree(c->d_log1p);
   delete c;
   return GFH_OK;
 }

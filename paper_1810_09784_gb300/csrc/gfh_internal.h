@@ -63,7 +63,11 @@ struct gfh_ctx {
   int fft_n = 0, fft_hop = 0, fft_batch = 0;
   // pinned host word for returning counts
   long long* h_pinned = nullptr;
+  // bf16 bits of float(log(1 + c)) for c < kLogTable (image channel 0), built on the host
+  uint16_t* d_log1p = nullptr;
 };
+
+constexpr int kLogTable = 4096;
 
 // One map as the kernels see it.
 struct MapDev {

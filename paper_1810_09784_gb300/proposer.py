@@ -246,6 +246,10 @@ class HoughBank:
         """Hough updates of the full search of the loaded lists: peaks x k rows per map."""
         return int(sum(self.counts[i] * g.n_k for i, g in enumerate(self.grids)))
 
+    def autotune(self, reps: int = 2):
+        """Tile shape of the plan timed on the loaded peak lists (the coarse tiles follow it)."""
+        return self.plan.autotune(self.fft_c, self.bin_c, self.offsets, len(N_GRID), reps)
+
     def full(self) -> None:
         self.plan.execute(self.fft_c, self.bin_c, self.offsets, len(N_GRID))
 
