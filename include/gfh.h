@@ -142,6 +142,7 @@ int gfh_create(gfh_ctx** out, int device, void* stream);
 int gfh_destroy(gfh_ctx* ctx);
 int gfh_set_stream(gfh_ctx* ctx, void* stream);
 /* Synchronises the stream, then returns and clears the device-side check flag: GFH_OK,
+ * GFH_ERR_TIMEOUT when a bounded device-side wait (tensor-core completion) ran out,
  * GFH_ERR_INPUT when the last calls saw unsorted peaks or an out-of-range index, or GFH_ERR_SIZE
  * when an asynchronous peakmap found more peaks than its capacity. */
 int gfh_check(gfh_ctx* ctx);

@@ -28,6 +28,7 @@
 namespace {
 
 constexpr int kImg = 256;
+constexpr size_t kSmemPerSm = 228 * 1024;   // shared memory of one SM
 constexpr int kTiles = 64;
 constexpr int kClasses = kTiles * kTiles + 1;
 
@@ -238,71 +239,279 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return *reinterpret_cast<const uint32_t*>(&v);
 }
 
-// ---- L2-L5 forward: out[m][n] = relu(bias[n] + sum_k A[m][k] W[n][k]) -----------------------------
-// m = output pixel (b, y, x); k = tap * CIN + ci with tap = 3 dy + dx; A[m][k] = in[b][y S + dy - 1]
-// [x S + dx - 1][ci] (zero outside).  A warp computes 16 pixels x COUT.
+// ---- tcgen05 helpers (5th-generation tensor cores, accumulator in tensor memory) --------------------
+//
+// Operands live in shared memory K-major without swizzle: "core matrices" of 8 rows x 16 bytes
+// (8 bf16 along K); within a 16-wide K slice the two K halves are 128 bytes apart (leading byte
+// offset) and consecutive 8-row groups 256 bytes apart (stride byte offset).
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Byte offset of element (row, k) of a K-major operand of `rows` rows in that layout.
+__device__ __forceinline__ uint32_t cm_off(int row, int k, int rows) {
+  return (uint32_t)((k >> 4) * (rows >> 3) * 256 + (row >> 3) * 256 + ((k >> 3) & 1) * 128 +
+                    (row & 7) * 16 + (k & 7) * 2);
+}
+
+// Shared-memory matrix descriptor: start address, leading / stride byte offsets, fixed version 1,
+// no swizzle.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(128u >> 4) << 16) |
+         ((uint64_t)(256u >> 4) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: fp32 accumulator, bf16 A and B, both K-major, M x N.
+__host__ __device__ constexpr uint32_t umma_idesc_bf16(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(mbar)));
+}
+
+// Waits for the phase of parity `parity` of the mbarrier, at most ~2e9 cycles (about a second).
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(mbar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > 2000000000ll) return false;
+  }
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Asynchronous global -> shared copies (16 or 4 bytes); src_bytes = 0 fills the destination with
+// zeros (the source address is then not read).
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void async_proxy_fence() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// ---- L1-L5 forward on tcgen05: out[m][n] = relu(bias[n] + sum_k A[m][k] W[n][k]) ----------------
+// Implicit GEMM: m = output pixel (b, y, x), k = tap * CIN + ci (tap = 3 dy + dx, padded with zeros
+// to a multiple of 16), A[m][k] = in[b][y S + dy - 1][x S + dx - 1][ci] (zero outside the image).
+// Persistent blocks of 256 threads keep the weights in shared memory.  Per tile of 128 pixels the
+// threads stage A with asynchronous copies (zero-filled outside the image; each thread owns fixed
+// pixels and one 16-byte channel chunk, so its copies need no index arithmetic beyond a per-tap
+// offset), one thread issues the K/16 MMAs of M = 128, N = COUT into tensor memory and commits
+// them to an mbarrier, and once they have completed the next tile's copies are started before the
+// 8 warps read the accumulator back (warp w: rows 32 (w % 4) .., half w / 4 of the columns), add
+// the bias, apply the ReLU and store bf16.
 template <int CIN, int COUT, int S>
-__global__ void __launch_bounds__(256) k_conv_fwd(const __nv_bfloat16* __restrict__ in,
-                                                  const __nv_bfloat16* __restrict__ w,
-                                                  const float* __restrict__ bias,
-                                                  __nv_bfloat16* __restrict__ out, int B, int H) {
-  constexpr int K = 9 * CIN, KP = K + 8, NT8 = COUT / 8;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __nv_bfloat16* ws = reinterpret_cast<__nv_bfloat16*>(smem_raw);
-  for (int e = threadIdx.x; e < COUT * K; e += blockDim.x) ws[(e / K) * KP + e % K] = w[e];
-  __syncthreads();
+__global__ void __launch_bounds__(256) k_conv_fwd_tc(const __nv_bfloat16* __restrict__ in,
+                                                     const __nv_bfloat16* __restrict__ w,
+                                                     const float* __restrict__ bias,
+                                                     __nv_bfloat16* __restrict__ out, int B, int H,
+                                                     unsigned int* flag) {
+  constexpr int KR = 9 * CIN;                        // real K
+  constexpr int K = (KR + 15) / 16 * 16;             // padded K
+  constexpr int NSL = K / 16;
+  constexpr int A_SL = 128 / 8 * 256, B_SL = COUT / 8 * 256;
+  constexpr int TCOLS = COUT < 32 ? 32 : COUT;
+  constexpr uint32_t IDESC = umma_idesc_bf16(128, COUT);
+  // staging assignment.  CIN % 8 == 0: lane = (pixel of 16 per warp, low bit of the 16-byte chunk),
+  // so a warp's copies read whole 32-byte sectors and write shared memory in the minimum 4
+  // wavefronts; each thread owns one pixel and chunks q_lo, q_lo + 2, ...  CIN = 2: thread =
+  // (pixel, tap parity), 8 taps (9..15 are zero padding).
+  constexpr int QC = CIN % 8 == 0 ? CIN / 8 : 1;
+  constexpr int NPX = 1;
+  extern __shared__ __align__(1024) unsigned char smem_tc[];
+  unsigned char* sa = smem_tc;
+  unsigned char* sb = smem_tc + NSL * A_SL;
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tslot;
+  __shared__ float sbias[COUT];
+  __shared__ int s_ok;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int Ho = H / S;
-  const int64_t M = (int64_t)B * Ho * Ho;
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  for (int64_t m0 = ((int64_t)blockIdx.x * 8 + (threadIdx.x >> 5)) * 16; m0 < M;
-       m0 += (int64_t)gridDim.x * 8 * 16) {
-    float acc[NT8][4];
-#pragma unroll
-    for (int n = 0; n < NT8; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-    int yy[2], xx[2], bb[2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int64_t m = m0 + g + 8 * h;
-      bb[h] = (int)(m / (Ho * Ho));
-      const int r = (int)(m % (Ho * Ho));
-      yy[h] = (r / Ho) * S - 1;
-      xx[h] = (r % Ho) * S - 1;
+  const int M = B * Ho * Ho;
+  const int n_tiles = (M + 127) / 128;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tslot)), "r"(TCOLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  // weights, K-major rows of the output channel, zero-padded K
+  if (CIN % 8 == 0) {
+    for (int e = tid; e < COUT * (KR / 8); e += blockDim.x) {
+      const int co = e / (KR / 8), k = (e % (KR / 8)) * 8;
+      *reinterpret_cast<int4*>(sb + cm_off(co, k, COUT)) =
+          __ldg(reinterpret_cast<const int4*>(w + co * KR + k));
     }
+  } else {
+    for (int e = tid; e < COUT * K; e += blockDim.x) {
+      const int co = e / K, k = e % K;
+      *reinterpret_cast<__nv_bfloat16*>(sb + cm_off(co, k, COUT)) =
+          k < KR ? w[co * KR + k] : __float2bfloat16_rn(0.f);
+    }
+  }
+  for (int c = tid; c < COUT; c += blockDim.x) sbias[c] = bias[c];
+  if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
+  const uint32_t sa32 = smem_u32(sa), sb32 = smem_u32(sb);
+  const int q = CIN % 8 == 0 ? (lane & 1) : 0;     // first chunk of the thread
+  const int pslot = CIN % 8 == 0 ? warp * 16 + (lane >> 1) : tid & 127;
+  // the thread's pixels of a tile: source of tap (0, 0) and the validity of the 3 rows / columns
+  const __nv_bfloat16* src0[NPX];
+  uint32_t rv[NPX], cv[NPX];
+  auto coords = [&](int t) {
 #pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-      const __nv_bfloat16* p[2];
+    for (int j = 0; j < NPX; ++j) {
+      const int p = pslot;
+      const int m = t * 128 + p;
+      const int b = m / (Ho * Ho), r = m - b * (Ho * Ho), yo = r / Ho, xo = r - yo * Ho;
+      const int y0 = yo * S - 1, x0 = xo * S - 1;
+      uint32_t rr = 0, cc = 0;
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int yi = yy[h] + tap / 3, xi = xx[h] + tap % 3;
-        p[h] = (yi >= 0 && yi < H && xi >= 0 && xi < H)
-                   ? in + (((int64_t)bb[h] * H + yi) * H + xi) * CIN : nullptr;
+      for (int d = 0; d < 3; ++d) {
+        rr |= (m < M && y0 + d >= 0 && y0 + d < H) ? (1u << d) : 0u;
+        cc |= (x0 + d >= 0 && x0 + d < H) ? (1u << d) : 0u;
       }
+      rv[j] = rr;
+      cv[j] = cc;
+      src0[j] = in + (((int64_t)b * H + y0) * H + x0) * CIN + q * 8;
+    }
+  };
+  auto stage = [&]() {
+    if (CIN % 8 == 0) {
+      const uint32_t poff = (uint32_t)((pslot >> 3) * 256 + (pslot & 7) * 16);
 #pragma unroll
-      for (int cc = 0; cc < CIN / 16; ++cc) {
-        const int c = cc * 16 + 2 * t;
-        uint32_t a[4];
-        a[0] = p[0] ? ld_u32(p[0] + c) : 0u;
-        a[1] = p[1] ? ld_u32(p[1] + c) : 0u;
-        a[2] = p[0] ? ld_u32(p[0] + c + 8) : 0u;
-        a[3] = p[1] ? ld_u32(p[1] + c + 8) : 0u;
-        const int k0 = tap * CIN + cc * 16 + 2 * t;
+      for (int tap = 0; tap < 9; ++tap) {
+        const int dy = tap / 3, dx = tap % 3;
+        const bool inside = ((rv[0] >> dy) & (cv[0] >> dx) & 1u) != 0u;
+        const int64_t toff = ((int64_t)dy * H + dx) * CIN;
 #pragma unroll
-        for (int n = 0; n < NT8; ++n) {
-          const __nv_bfloat16* wr = ws + (n * 8 + g) * KP + k0;
-          mma_bf16(acc[n], a, ld_u32(wr), ld_u32(wr + 8));
+        for (int qh = 0; qh < QC / 2; ++qh) {
+          const int k = tap * CIN + (q + 2 * qh) * 8;
+          const uint32_t kof = (uint32_t)((k >> 4) * A_SL + ((k >> 3) & 1) * 128);
+          cp_async16(sa32 + kof + poff,
+                     inside ? (const void*)(src0[0] + toff + 16 * qh) : (const void*)in,
+                     inside ? 16u : 0u);
+        }
+      }
+    } else {                                         // CIN = 2: k = 2 tap + ci, taps 0..15
+      const int par = tid >> 7;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int tap = par + 2 * i;
+        const int dy = tap / 3, dx = tap % 3;
+        const bool inside = tap < 9 && ((rv[0] >> dy) & (cv[0] >> dx) & 1u) != 0u;
+        const int64_t toff = ((int64_t)dy * H + dx) * CIN;
+        cp_async4(sa32 + cm_off(pslot, 2 * tap, 128),
+                  inside ? (const void*)(src0[0] + toff) : (const void*)in, inside ? 4u : 0u);
+      }
+    }
+  };
+  uint32_t parity = 0;
+  int tile = blockIdx.x;
+  if (tile < n_tiles) {
+    coords(tile);
+    stage();
+  }
+  cp_async_wait_all();
+  async_proxy_fence();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tslot;
+  const uint64_t ad0 = umma_desc(sa32), bd0 = umma_desc(sb32);
+  for (; tile < n_tiles; tile += gridDim.x) {
+    const int m0 = tile * 128;
+    if (tid == 0) {
+#pragma unroll 4
+      for (int s = 0; s < NSL; ++s)
+        umma_bf16(tmem, ad0 + (uint64_t)((s * A_SL) >> 4), bd0 + (uint64_t)((s * B_SL) >> 4),
+                  IDESC, s > 0 ? 1u : 0u);
+      umma_commit(&mbar);
+    }
+    if (warp == 0) {
+      const bool mine = mbar_wait(&mbar, parity);
+      const bool all = __all_sync(0xffffffffu, mine) != 0;
+      if (lane == 0) {
+        s_ok = all ? 1 : 0;
+        if (!all) atomicOr(flag, GFH_FLAG_TIMEOUT);
+      }
+    }
+    parity ^= 1u;
+    __syncthreads();
+    const bool ok = s_ok != 0;
+    tc_fence_after();
+    // A is free: the next tile's copies fly while this tile's accumulator is read back
+    const int next = tile + gridDim.x;
+    if (ok && next < n_tiles) {
+      coords(next);
+      stage();
+    }
+    if (ok) {
+      const int quarter = warp & 3, half = warp >> 2;
+      const int p = quarter * 32 + lane;
+      const int m = m0 + p;
+#pragma unroll
+      for (int c0 = half * (COUT / 2); c0 < (half + 1) * (COUT / 2); c0 += 16) {
+        uint32_t v[16];
+        tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
+        uint32_t pk[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          pk[j] = pack_bf16(fmaxf(__uint_as_float(v[2 * j]) + sbias[c0 + 2 * j], 0.f),
+                            fmaxf(__uint_as_float(v[2 * j + 1]) + sbias[c0 + 2 * j + 1], 0.f));
+        if (m < M) {
+          int4* o = reinterpret_cast<int4*>(out + (int64_t)m * COUT + c0);
+          o[0] = make_int4(pk[0], pk[1], pk[2], pk[3]);
+          o[1] = make_int4(pk[4], pk[5], pk[6], pk[7]);
         }
       }
     }
-#pragma unroll
-    for (int n = 0; n < NT8; ++n) {
-      const int col = n * 8 + 2 * t;
-      const float b0 = bias[col], b1 = bias[col + 1];
-      *reinterpret_cast<uint32_t*>(out + (m0 + g) * COUT + col) =
-          pack_bf16(fmaxf(acc[n][0] + b0, 0.f), fmaxf(acc[n][1] + b1, 0.f));
-      *reinterpret_cast<uint32_t*>(out + (m0 + g + 8) * COUT + col) =
-          pack_bf16(fmaxf(acc[n][2] + b0, 0.f), fmaxf(acc[n][3] + b1, 0.f));
-    }
+    cp_async_wait_all();
+    async_proxy_fence();
+    tc_fence_before();
+    __syncthreads();                                 // accumulator read, next A in place
+    tc_fence_after();
+    if (!ok) break;
   }
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
 }
 
 // ---- L2-L5 input gradient: din[m][ci] = sum_{tap, co} G[src(m, tap)][co] W[co][tap][ci] ----------
@@ -474,69 +683,6 @@ __global__ void k_bias_grad(const __nv_bfloat16* __restrict__ dout,
   for (int64_t p = (int64_t)blockIdx.x * rows + threadIdx.x / C; p < M; p += (int64_t)gridDim.x * rows)
     if (__bfloat162float(out[p * C + co]) > 0.f) s += __bfloat162float(dout[p * C + co]);
   atomicAdd(&db[co], s);
-}
-
-// ---- L1 (2 input channels) on tensor cores: K = 9 taps x 2 channels = 18, padded to 32 ---------
-// k = 2 tap + ci, so one 32-bit A register holds both channels of one tap's pixel.  A warp computes
-// 16 pixels x 32 output channels (2 k-steps x 4 n-tiles).
-__global__ void __launch_bounds__(256) k_conv1_fwd(const __nv_bfloat16* __restrict__ in,
-                                                   const __nv_bfloat16* __restrict__ w,
-                                                   const float* __restrict__ bias,
-                                                   __nv_bfloat16* __restrict__ out, int B) {
-  constexpr int KP = 40;                   // 32 + 8 bf16 per output channel row
-  __shared__ __align__(16) __nv_bfloat16 ws[32 * KP];
-  for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
-    const int co = e / 32, k = e % 32;
-    ws[co * KP + k] = k < 18 ? w[co * 18 + k] : __float2bfloat16_rn(0.f);
-  }
-  __syncthreads();
-  const int64_t M = (int64_t)B * kImg * kImg;
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  for (int64_t m0 = ((int64_t)blockIdx.x * 8 + (threadIdx.x >> 5)) * 16; m0 < M;
-       m0 += (int64_t)gridDim.x * 8 * 16) {
-    float acc[4][4];
-#pragma unroll
-    for (int n = 0; n < 4; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-    int yy[2], xx[2], bb[2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int64_t m = m0 + g + 8 * h;
-      bb[h] = (int)(m / (kImg * kImg));
-      const int r = (int)(m % (kImg * kImg));
-      yy[h] = r / kImg - 1;
-      xx[h] = r % kImg - 1;
-    }
-    // A value of tap `tap` for pixel half h (zero outside the image and for tap >= 9)
-    auto a_val = [&](int h, int tap) -> uint32_t {
-      if (tap >= 9) return 0u;
-      const int yi = yy[h] + tap / 3, xi = xx[h] + tap % 3;
-      if (yi < 0 || yi >= kImg || xi < 0 || xi >= kImg) return 0u;
-      return ld_u32(in + (((int64_t)bb[h] * kImg + yi) * kImg + xi) * 2);
-    };
-#pragma unroll
-    for (int kk = 0; kk < 2; ++kk) {
-      uint32_t a[4];
-      a[0] = a_val(0, kk * 8 + t);
-      a[1] = a_val(1, kk * 8 + t);
-      a[2] = a_val(0, kk * 8 + t + 4);
-      a[3] = a_val(1, kk * 8 + t + 4);
-      const int k0 = kk * 16 + 2 * t;
-#pragma unroll
-      for (int n = 0; n < 4; ++n) {
-        const __nv_bfloat16* wr = ws + (n * 8 + g) * KP + k0;
-        mma_bf16(acc[n], a, ld_u32(wr), ld_u32(wr + 8));
-      }
-    }
-#pragma unroll
-    for (int n = 0; n < 4; ++n) {
-      const int col = n * 8 + 2 * t;
-      const float b0 = bias[col], b1 = bias[col + 1];
-      *reinterpret_cast<uint32_t*>(out + (m0 + g) * 32 + col) =
-          pack_bf16(fmaxf(acc[n][0] + b0, 0.f), fmaxf(acc[n][1] + b1, 0.f));
-      *reinterpret_cast<uint32_t*>(out + (m0 + g + 8) * 32 + col) =
-          pack_bf16(fmaxf(acc[n][2] + b0, 0.f), fmaxf(acc[n][3] + b1, 0.f));
-    }
-  }
 }
 
 // dW1[co][tap][ci] += sum_p G1[p][co] in[src(p, tap)][ci]; a block reduces a range of pixels for
@@ -715,13 +861,23 @@ __global__ void k_to_bf16(const float* __restrict__ a, __nv_bfloat16* __restrict
 
 template <int CIN, int COUT, int S>
 int conv_fwd(const __nv_bfloat16* in, const __nv_bfloat16* w, const float* bias,
-             __nv_bfloat16* out, int B, int H, int sms, cudaStream_t st) {
-  const size_t smem = (size_t)COUT * (9 * CIN + 8) * 2;
-  auto fn = k_conv_fwd<CIN, COUT, S>;
+             __nv_bfloat16* out, int B, int H, int sms, cudaStream_t st, unsigned int* flag) {
+  constexpr int K = (9 * CIN + 15) / 16 * 16;
+  const size_t smem = (size_t)(K / 16) * (128 / 8 * 256) + (size_t)(K / 16) * (COUT / 8 * 256);
+  auto fn = k_conv_fwd_tc<CIN, COUT, S>;
   GFH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const int64_t tiles = (int64_t)B * (H / S) * (H / S) / 16;
-  const int grid = (int)std::min<int64_t>((tiles + 7) / 8, (int64_t)sms * 8);
-  fn<<<grid, 256, smem, st>>>(in, w, bias, out, B, H);
+  GFH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+  // resident blocks per SM: shared memory (with the static part and the per-block reservation),
+  // registers, 8 warps of 2048 threads, tensor-memory columns
+  constexpr int TCOLS = COUT < 32 ? 32 : COUT;
+  cudaFuncAttributes fa{};
+  GFH_CUDA_TRY(cudaFuncGetAttributes(&fa, fn));
+  const int regs = std::max(1, (fa.numRegs + 7) / 8 * 8);
+  const int per_sm = std::max(1, std::min({(int)(kSmemPerSm / (smem + fa.sharedSizeBytes + 1024)),
+                                           65536 / (regs * 256), 8, 512 / TCOLS}));
+  const int64_t tiles = ((int64_t)B * (H / S) * (H / S) + 127) / 128;
+  const int grid = (int)std::min<int64_t>(tiles, (int64_t)sms * per_sm);
+  fn<<<grid, 256, smem, st>>>(in, w, bias, out, B, H, flag);
   GFH_CUDA_TRY(cudaGetLastError());
   return GFH_OK;
 }
@@ -805,16 +961,12 @@ int forward(gfh_cnn* n, const __nv_bfloat16* img, int B) {
   cudaStream_t st = n->ctx->stream;
   const int sms = n->ctx->num_sms;
   const Layout& L = n->L;
-  const int64_t P1 = (int64_t)B * kImg * kImg;
-  {
-    const int grid = (int)std::min<int64_t>((P1 / 16 + 7) / 8, (int64_t)sms * 8);
-    k_conv1_fwd<<<grid, 256, 0, st>>>(img, n->wb[0], n->w + L.b[0], n->act[1], B);
-  }
-  GFH_CUDA_TRY(cudaGetLastError());
-  int rc = conv_fwd<32, 32, 2>(n->act[1], n->wb[1], n->w + L.b[1], n->act[2], B, 256, sms, st);
-  if (!rc) rc = conv_fwd<32, 64, 1>(n->act[2], n->wb[2], n->w + L.b[2], n->act[3], B, 128, sms, st);
-  if (!rc) rc = conv_fwd<64, 64, 2>(n->act[3], n->wb[3], n->w + L.b[3], n->act[4], B, 128, sms, st);
-  if (!rc) rc = conv_fwd<64, 64, 1>(n->act[4], n->wb[4], n->w + L.b[4], n->act[5], B, 64, sms, st);
+  unsigned int* flag = n->ctx->d_flag;
+  int rc = conv_fwd<2, 32, 1>(img, n->wb[0], n->w + L.b[0], n->act[1], B, 256, sms, st, flag);
+  if (!rc) rc = conv_fwd<32, 32, 2>(n->act[1], n->wb[1], n->w + L.b[1], n->act[2], B, 256, sms, st, flag);
+  if (!rc) rc = conv_fwd<32, 64, 1>(n->act[2], n->wb[2], n->w + L.b[2], n->act[3], B, 128, sms, st, flag);
+  if (!rc) rc = conv_fwd<64, 64, 2>(n->act[3], n->wb[3], n->w + L.b[3], n->act[4], B, 128, sms, st, flag);
+  if (!rc) rc = conv_fwd<64, 64, 1>(n->act[4], n->wb[4], n->w + L.b[4], n->act[5], B, 64, sms, st, flag);
   if (rc) return rc;
   k_pool<<<(B * 4096 + 255) / 256, 256, 0, st>>>(n->act[5], n->pooled, B);
   k_head_fwd<<<B, 256, 0, st>>>(n->pooled, n->w + L.wh, n->w + L.bh, n->w + L.bnull, n->logits);
@@ -1039,7 +1191,7 @@ extern "C" int gfh_conv3x3(gfh_ctx* ctx, int32_t mode, int32_t cin, int32_t cout
   const auto* dout = (const __nv_bfloat16*)d_dout;
 #define GFH_CONV_CASE(CI, CO, S)                                                                   \
   if (cin == CI && cout == CO && stride == S) {                                                    \
-    if (mode == 0) return conv_fwd<CI, CO, S>(in, w, d_bias, (__nv_bfloat16*)d_res, batch, h, sms, st); \
+    if (mode == 0) return conv_fwd<CI, CO, S>(in, w, d_bias, (__nv_bfloat16*)d_res, batch, h, sms, st, ctx->d_flag); \
     if (mode == 1) return conv_dgrad<CI, CO, S>(dout, out, w, (__nv_bfloat16*)d_res, batch, h, sms, st); \
     if (mode == 2) return conv_wgrad<CI, CO, S>(dout, out, in, (float*)d_res, d_db, batch, h, sms, st); \
     return GFH_ERR_ARG;                                                                            \

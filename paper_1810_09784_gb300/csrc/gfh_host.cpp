@@ -200,6 +200,7 @@ extern "C" int gfh_check(gfh_ctx* c) {
   if (flag) {
     GFH_CUDA_TRY(cudaMemsetAsync(c->d_flag, 0, sizeof(unsigned int), c->stream));
     GFH_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (flag & GFH_FLAG_TIMEOUT) return GFH_ERR_TIMEOUT;
     return (flag & (GFH_FLAG_UNSORTED | GFH_FLAG_FFT_RANGE)) ? GFH_ERR_INPUT : GFH_ERR_SIZE;
   }
   return GFH_OK;

@@ -43,6 +43,7 @@ __host__ __device__ __forceinline__ bool gfh_synth_peak(uint64_t seed, uint64_t 
 #define GFH_FLAG_UNSORTED 1u
 #define GFH_FLAG_FFT_RANGE 2u
 #define GFH_FLAG_CAPACITY 4u
+#define GFH_FLAG_TIMEOUT 8u
 
 #define GFH_CUDA_TRY(expr)                                \
   do {                                                    \
