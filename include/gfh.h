@@ -418,6 +418,14 @@ int gfh_plan_set_coarse(gfh_plan* plan, int32_t coarse_k, int32_t coarse_x, int3
 int gfh_plan_execute_tiles(gfh_plan* plan, const gfh_peaks* peaks, const int32_t* d_coarse,
                            int32_t n_sel, const int32_t* d_full);
 
+/*
+ * Failure-path check of the bounded device waits (the tensor-core kernels wait on mbarriers with a
+ * limit of about a second): one block waits `cycles` SM cycles on an mbarrier that nothing arrives
+ * at, then raises the timeout flag, so the next gfh_check returns GFH_ERR_TIMEOUT and clears it;
+ * the context stays usable.  Asynchronous.  cycles <= 4e9.
+ */
+int gfh_wait_check(gfh_ctx* ctx, int64_t cycles);
+
 /* ---- allocation-free entry point -------------------------------------------------------------
  *
  * The paper has no counterpart to this function: it is a service for callers that cannot

@@ -255,11 +255,12 @@ __device__ __forceinline__ uint32_t cm_off(int row, int k, int rows) {
                     (row & 7) * 16 + (k & 7) * 2);
 }
 
-// Shared-memory matrix descriptor: start address, leading / stride byte offsets, fixed version 1,
-// no swizzle.
-__device__ __forceinline__ uint64_t umma_desc(uint32_t addr) {
-  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(128u >> 4) << 16) |
-         ((uint64_t)(256u >> 4) << 32) | (1ull << 46);
+// Shared-memory matrix descriptor: start address, leading (K-direction) / stride (M/N-direction)
+// byte offsets between core matrices, fixed version 1, no swizzle.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo = 128u,
+                                              uint32_t sbo = 256u) {
+  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
 // Instruction descriptor of kind::f16: fp32 accumulator, bf16 A and B, both K-major, M x N.
@@ -280,8 +281,10 @@ __device__ __forceinline__ void umma_commit(uint64_t* mbar) {
                    smem_u32(mbar)));
 }
 
-// Waits for the phase of parity `parity` of the mbarrier, at most ~2e9 cycles (about a second).
-__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
+// Waits for the phase of parity `parity` of the mbarrier, at most `budget` cycles (default about a
+// second at the maximum clock).
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity,
+                                          long long budget = 2000000000ll) {
   const long long t0 = clock64();
   for (;;) {
     uint32_t done;
@@ -292,8 +295,17 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
         : "r"(smem_u32(mbar)), "r"(parity)
         : "memory");
     if (done) return true;
-    if (clock64() - t0 > 2000000000ll) return false;
+    if (clock64() - t0 > budget) return false;
   }
+}
+
+// Failure-path check of the bounded wait: one block waits on an mbarrier that nothing arrives at,
+// gives up after `budget` cycles and raises the timeout flag, as the tensor-core kernels do.
+__global__ void k_wait_unsignalled(long long budget, unsigned int* flag) {
+  __shared__ __align__(8) uint64_t mbar;
+  if (threadIdx.x == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait(&mbar, 0, budget)) atomicOr(flag, GFH_FLAG_TIMEOUT);
 }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
@@ -333,34 +345,37 @@ __device__ __forceinline__ void async_proxy_fence() {
 // ---- L1-L5 forward on tcgen05: out[m][n] = relu(bias[n] + sum_k A[m][k] W[n][k]) ----------------
 // Implicit GEMM: m = output pixel (b, y, x), k = tap * CIN + ci (tap = 3 dy + dx, padded with zeros
 // to a multiple of 16), A[m][k] = in[b][y S + dy - 1][x S + dx - 1][ci] (zero outside the image).
-// Persistent blocks of 256 threads keep the weights in shared memory.  Per tile of 128 pixels the
-// threads stage A with asynchronous copies (zero-filled outside the image; each thread owns fixed
-// pixels and one 16-byte channel chunk, so its copies need no index arithmetic beyond a per-tap
-// offset), one thread issues the K/16 MMAs of M = 128, N = COUT into tensor memory and commits
-// them to an mbarrier, and once they have completed the next tile's copies are started before the
-// 8 warps read the accumulator back (warp w: rows 32 (w % 4) .., half w / 4 of the columns), add
-// the bias, apply the ReLU and store bf16.
+// Persistent blocks of 256 threads keep the weights in shared memory; one thread issues the MMAs
+// (M = 128, N = COUT, K = 16) into tensor memory and commits them to an mbarrier; after they
+// complete the next tile's asynchronous copies (zero-filled outside the image) start before the 8
+// warps read the accumulator back (warp w: rows 32 (w % 4) .., half w / 4 of the columns), add the
+// bias, apply the ReLU and store bf16.
+//
+// CIN % 8 == 0: a tile is RT output rows (RT = 2 when W_out <= 64, else 1; W_out <= 128), each row
+// one M = 128 MMA chain into its own accumulator (MMA rows past W_out are computed and dropped).
+// The (RT - 1) S + 3 input rows a tile reads are staged once, as 16-byte rows (8 channels) per
+// input pixel: [row][chunk][parity][entry], entry j = input column j - 1 (S = 1) or, for S = 2,
+// the odd columns 2j - 1 (parity 0) and the even columns 2j (parity 1), NP = W_out + 2 entries.
+// Tap (dy, dx) of output column x is entry x + dx (S = 1) or O[x], E[x], O[x + 1] (S = 2): the
+// MMA's A descriptor starts at that entry (any 16-byte row), 8-row groups 128 bytes apart, K
+// halves one chunk block apart; the over-read of the dropped rows stays inside a tail pad.
+// CIN = 2: a tile is 128 consecutive pixels staged im2col (k = 2 tap + ci, one 4-byte pair per tap).
 template <int CIN, int COUT, int S>
 __global__ void __launch_bounds__(256) k_conv_fwd_tc(const __nv_bfloat16* __restrict__ in,
                                                      const __nv_bfloat16* __restrict__ w,
                                                      const float* __restrict__ bias,
                                                      __nv_bfloat16* __restrict__ out, int B, int H,
-                                                     unsigned int* flag) {
+                                                     int tcols, unsigned int* flag) {
+  constexpr bool HALO = CIN % 8 == 0;
   constexpr int KR = 9 * CIN;                        // real K
   constexpr int K = (KR + 15) / 16 * 16;             // padded K
   constexpr int NSL = K / 16;
+  constexpr int QC = HALO ? CIN / 8 : 1;             // 16-byte chunks per pixel
   constexpr int A_SL = 128 / 8 * 256, B_SL = COUT / 8 * 256;
-  constexpr int TCOLS = COUT < 32 ? 32 : COUT;
   constexpr uint32_t IDESC = umma_idesc_bf16(128, COUT);
-  // staging assignment.  CIN % 8 == 0: lane = (pixel of 16 per warp, low bit of the 16-byte chunk),
-  // so a warp's copies read whole 32-byte sectors and write shared memory in the minimum 4
-  // wavefronts; each thread owns one pixel and chunks q_lo, q_lo + 2, ...  CIN = 2: thread =
-  // (pixel, tap parity), 8 taps (9..15 are zero padding).
-  constexpr int QC = CIN % 8 == 0 ? CIN / 8 : 1;
-  constexpr int NPX = 1;
   extern __shared__ __align__(1024) unsigned char smem_tc[];
-  unsigned char* sa = smem_tc;
-  unsigned char* sb = smem_tc + NSL * A_SL;
+  unsigned char* sb = smem_tc;                       // weights
+  unsigned char* sa = smem_tc + NSL * B_SL;          // A (halo or im2col)
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tslot;
   __shared__ float sbias[COUT];
@@ -368,14 +383,17 @@ __global__ void __launch_bounds__(256) k_conv_fwd_tc(const __nv_bfloat16* __rest
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int Ho = H / S;
   const int M = B * Ho * Ho;
-  const int n_tiles = (M + 127) / 128;
+  const int RT = Ho <= 64 ? 2 : 1;                   // output rows per tile (halo form)
+  const int NP = Ho + 2;                             // halo entries per (row, chunk, parity)
+  const int HBLK = S * NP * 16;                      // bytes per (row, chunk)
+  const int n_tiles = HALO ? B * (Ho / RT) : (M + 127) / 128;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(&tslot)), "r"(TCOLS));
+                     smem_u32(&tslot)), "r"(tcols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   // weights, K-major rows of the output channel, zero-padded K
-  if (CIN % 8 == 0) {
+  if (HALO) {
     for (int e = tid; e < COUT * (KR / 8); e += blockDim.x) {
       const int co = e / (KR / 8), k = (e % (KR / 8)) * 8;
       *reinterpret_cast<int4*>(sb + cm_off(co, k, COUT)) =
@@ -391,79 +409,86 @@ __global__ void __launch_bounds__(256) k_conv_fwd_tc(const __nv_bfloat16* __rest
   for (int c = tid; c < COUT; c += blockDim.x) sbias[c] = bias[c];
   if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
   const uint32_t sa32 = smem_u32(sa), sb32 = smem_u32(sb);
-  const int q = CIN % 8 == 0 ? (lane & 1) : 0;     // first chunk of the thread
-  const int pslot = CIN % 8 == 0 ? warp * 16 + (lane >> 1) : tid & 127;
-  // the thread's pixels of a tile: source of tap (0, 0) and the validity of the 3 rows / columns
-  const __nv_bfloat16* src0[NPX];
-  uint32_t rv[NPX], cv[NPX];
-  auto coords = [&](int t) {
-#pragma unroll
-    for (int j = 0; j < NPX; ++j) {
-      const int p = pslot;
+
+  auto stage = [&](int t) {
+    if (HALO) {
+      // tile = rows y0 .. y0 + RT - 1 of image b; input rows y0 S - 1 + ri, ri < (RT - 1) S + 3
+      const int b = t / (Ho / RT), y0 = (t - b * (Ho / RT)) * RT;
+      const int rin = (RT - 1) * S + 3;
+      const int jb_n = (NP + 15) / 16;               // blocks of 16 entries
+      const int tot = rin * S * (QC / 2) * jb_n * 32;
+      for (int e = tid; e < tot; e += blockDim.x) {
+        const int qlo = e & 1, jj = (e >> 1) & 15;
+        int blk = e >> 5;
+        const int jb = blk % jb_n; blk /= jb_n;
+        const int qh = blk % (QC / 2); blk /= (QC / 2);
+        const int par = blk % S, ri = blk / S;
+        const int j = jb * 16 + jj;
+        if (j >= NP) continue;
+        const int q = 2 * qh + qlo;
+        const int yi = y0 * S - 1 + ri;
+        const int xi = S == 1 ? j - 1 : (par == 0 ? 2 * j - 1 : 2 * j);
+        const bool inside = yi >= 0 && yi < H && xi >= 0 && xi < H;
+        const __nv_bfloat16* src = inside ? in + (((int64_t)b * H + yi) * H + xi) * CIN + q * 8 : in;
+        cp_async16(sa32 + (uint32_t)(((ri * QC + q) * S + par) * NP * 16 + j * 16), src,
+                   inside ? 16u : 0u);
+      }
+    } else {                                         // CIN = 2: k = 2 tap + ci, taps 0..15
+      const int p = tid & 127, par = tid >> 7;
       const int m = t * 128 + p;
       const int b = m / (Ho * Ho), r = m - b * (Ho * Ho), yo = r / Ho, xo = r - yo * Ho;
       const int y0 = yo * S - 1, x0 = xo * S - 1;
-      uint32_t rr = 0, cc = 0;
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        rr |= (m < M && y0 + d >= 0 && y0 + d < H) ? (1u << d) : 0u;
-        cc |= (x0 + d >= 0 && x0 + d < H) ? (1u << d) : 0u;
-      }
-      rv[j] = rr;
-      cv[j] = cc;
-      src0[j] = in + (((int64_t)b * H + y0) * H + x0) * CIN + q * 8;
-    }
-  };
-  auto stage = [&]() {
-    if (CIN % 8 == 0) {
-      const uint32_t poff = (uint32_t)((pslot >> 3) * 256 + (pslot & 7) * 16);
-#pragma unroll
-      for (int tap = 0; tap < 9; ++tap) {
-        const int dy = tap / 3, dx = tap % 3;
-        const bool inside = ((rv[0] >> dy) & (cv[0] >> dx) & 1u) != 0u;
-        const int64_t toff = ((int64_t)dy * H + dx) * CIN;
-#pragma unroll
-        for (int qh = 0; qh < QC / 2; ++qh) {
-          const int k = tap * CIN + (q + 2 * qh) * 8;
-          const uint32_t kof = (uint32_t)((k >> 4) * A_SL + ((k >> 3) & 1) * 128);
-          cp_async16(sa32 + kof + poff,
-                     inside ? (const void*)(src0[0] + toff + 16 * qh) : (const void*)in,
-                     inside ? 16u : 0u);
-        }
-      }
-    } else {                                         // CIN = 2: k = 2 tap + ci, taps 0..15
-      const int par = tid >> 7;
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int tap = par + 2 * i;
         const int dy = tap / 3, dx = tap % 3;
-        const bool inside = tap < 9 && ((rv[0] >> dy) & (cv[0] >> dx) & 1u) != 0u;
-        const int64_t toff = ((int64_t)dy * H + dx) * CIN;
-        cp_async4(sa32 + cm_off(pslot, 2 * tap, 128),
-                  inside ? (const void*)(src0[0] + toff) : (const void*)in, inside ? 4u : 0u);
+        const bool inside = tap < 9 && m < M && y0 + dy >= 0 && y0 + dy < H && x0 + dx >= 0 &&
+                            x0 + dx < H;
+        const __nv_bfloat16* src =
+            inside ? in + (((int64_t)b * H + y0 + dy) * H + x0 + dx) * CIN : in;
+        cp_async4(sa32 + cm_off(p, 2 * tap, 128), src, inside ? 4u : 0u);
       }
     }
   };
+
   uint32_t parity = 0;
   int tile = blockIdx.x;
-  if (tile < n_tiles) {
-    coords(tile);
-    stage();
-  }
+  if (tile < n_tiles) stage(tile);
   cp_async_wait_all();
   async_proxy_fence();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tslot;
-  const uint64_t ad0 = umma_desc(sa32), bd0 = umma_desc(sb32);
+  const uint64_t bd0 = umma_desc(sb32);
   for (; tile < n_tiles; tile += gridDim.x) {
-    const int m0 = tile * 128;
     if (tid == 0) {
-#pragma unroll 4
-      for (int s = 0; s < NSL; ++s)
-        umma_bf16(tmem, ad0 + (uint64_t)((s * A_SL) >> 4), bd0 + (uint64_t)((s * B_SL) >> 4),
-                  IDESC, s > 0 ? 1u : 0u);
+      if (HALO) {
+        constexpr int SPT = CIN / 16;                // K slices per tap
+        for (int r = 0; r < RT; ++r) {
+#pragma unroll 1
+          for (int tap = 0; tap < 9; ++tap) {
+            const int dy = tap / 3, dx = tap % 3;
+            const int par = S == 1 ? 0 : (dx == 1 ? 1 : 0);
+            const int jo = S == 1 ? dx : (dx == 2 ? 1 : 0);
+            const int ri = r * S + dy;
+#pragma unroll
+            for (int sp = 0; sp < SPT; ++sp) {
+              const uint32_t a_addr =
+                  sa32 + (uint32_t)(((ri * QC + 2 * sp) * S + par) * NP * 16 + jo * 16);
+              const int sl = tap * SPT + sp;
+              umma_bf16(tmem + (uint32_t)(r * COUT), umma_desc(a_addr, (uint32_t)HBLK, 128u),
+                        bd0 + (uint64_t)((sl * B_SL) >> 4), IDESC, sl > 0 ? 1u : 0u);
+            }
+          }
+        }
+      } else {
+        const uint64_t ad0 = umma_desc(sa32);
+#pragma unroll 1
+        for (int sl = 0; sl < NSL; ++sl)
+          umma_bf16(tmem, ad0 + (uint64_t)((sl * A_SL) >> 4), bd0 + (uint64_t)((sl * B_SL) >> 4),
+                    IDESC, sl > 0 ? 1u : 0u);
+      }
       umma_commit(&mbar);
     }
     if (warp == 0) {
@@ -480,27 +505,38 @@ __global__ void __launch_bounds__(256) k_conv_fwd_tc(const __nv_bfloat16* __rest
     tc_fence_after();
     // A is free: the next tile's copies fly while this tile's accumulator is read back
     const int next = tile + gridDim.x;
-    if (ok && next < n_tiles) {
-      coords(next);
-      stage();
-    }
+    if (ok && next < n_tiles) stage(next);
     if (ok) {
       const int quarter = warp & 3, half = warp >> 2;
       const int p = quarter * 32 + lane;
-      const int m = m0 + p;
+      // RT = 2: warp half h reads accumulator h (all columns); RT = 1: column half h
+      const int r = HALO && RT == 2 ? half : 0;
+      const int cb = HALO && RT == 2 ? 0 : half * (COUT / 2);
+      const int ce = HALO && RT == 2 ? COUT : cb + COUT / 2;
+      int64_t m;
+      bool valid;
+      if (HALO) {
+        const int b = tile / (Ho / RT), y = (tile - b * (Ho / RT)) * RT + r;
+        m = ((int64_t)b * Ho + y) * Ho + p;
+        valid = p < Ho;
+      } else {
+        m = (int64_t)tile * 128 + p;
+        valid = m < M;
+      }
+      if (!(HALO && RT == 2 && quarter * 32 >= Ho)) {   // whole warp past the row: nothing to read
+        for (int c0 = cb; c0 < ce; c0 += 16) {
+          uint32_t v[16];
+          tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(r * COUT + c0), v);
+          uint32_t pk[8];
 #pragma unroll
-      for (int c0 = half * (COUT / 2); c0 < (half + 1) * (COUT / 2); c0 += 16) {
-        uint32_t v[16];
-        tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
-        uint32_t pk[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-          pk[j] = pack_bf16(fmaxf(__uint_as_float(v[2 * j]) + sbias[c0 + 2 * j], 0.f),
-                            fmaxf(__uint_as_float(v[2 * j + 1]) + sbias[c0 + 2 * j + 1], 0.f));
-        if (m < M) {
-          int4* o = reinterpret_cast<int4*>(out + (int64_t)m * COUT + c0);
-          o[0] = make_int4(pk[0], pk[1], pk[2], pk[3]);
-          o[1] = make_int4(pk[4], pk[5], pk[6], pk[7]);
+          for (int j = 0; j < 8; ++j)
+            pk[j] = pack_bf16(fmaxf(__uint_as_float(v[2 * j]) + sbias[c0 + 2 * j], 0.f),
+                              fmaxf(__uint_as_float(v[2 * j + 1]) + sbias[c0 + 2 * j + 1], 0.f));
+          if (valid) {
+            int4* o = reinterpret_cast<int4*>(out + m * COUT + c0);
+            o[0] = make_int4(pk[0], pk[1], pk[2], pk[3]);
+            o[1] = make_int4(pk[4], pk[5], pk[6], pk[7]);
+          }
         }
       }
     }
@@ -511,7 +547,7 @@ __global__ void __launch_bounds__(256) k_conv_fwd_tc(const __nv_bfloat16* __rest
     tc_fence_after();
     if (!ok) break;
   }
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols));
 }
 
 // ---- L2-L5 input gradient: din[m][ci] = sum_{tap, co} G[src(m, tap)][co] W[co][tap][ci] ----------
@@ -862,22 +898,31 @@ __global__ void k_to_bf16(const float* __restrict__ a, __nv_bfloat16* __restrict
 template <int CIN, int COUT, int S>
 int conv_fwd(const __nv_bfloat16* in, const __nv_bfloat16* w, const float* bias,
              __nv_bfloat16* out, int B, int H, int sms, cudaStream_t st, unsigned int* flag) {
+  constexpr bool HALO = CIN % 8 == 0;
   constexpr int K = (9 * CIN + 15) / 16 * 16;
-  const size_t smem = (size_t)(K / 16) * (128 / 8 * 256) + (size_t)(K / 16) * (COUT / 8 * 256);
+  const int Ho = H / S;
+  if (HALO && (Ho > 128 || (Ho <= 64 && Ho % 2))) return GFH_ERR_ARG;   // tiles are output rows
+  const int RT = HALO && Ho <= 64 ? 2 : 1;
+  // halo: rows x chunks x parities x (W_out + 2) entries of 16 bytes, plus the dropped rows'
+  // over-read (at most 128 entries past a block start); im2col: K/16 slices of 128 x 16
+  const size_t a_bytes = HALO ? (size_t)((RT - 1) * S + 3) * (CIN / 8) * S * (Ho + 2) * 16 + 128 * 16
+                              : (size_t)(K / 16) * (128 / 8 * 256);
+  const size_t smem = (size_t)(K / 16) * (COUT / 8 * 256) + a_bytes;
+  if (smem > kMaxSmemBytes - 4096) return GFH_ERR_SIZE;
+  const int tcols = RT * COUT < 32 ? 32 : RT * COUT;                   // power of two here
   auto fn = k_conv_fwd_tc<CIN, COUT, S>;
   GFH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   GFH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   // resident blocks per SM: shared memory (with the static part and the per-block reservation),
   // registers, 8 warps of 2048 threads, tensor-memory columns
-  constexpr int TCOLS = COUT < 32 ? 32 : COUT;
   cudaFuncAttributes fa{};
   GFH_CUDA_TRY(cudaFuncGetAttributes(&fa, fn));
   const int regs = std::max(1, (fa.numRegs + 7) / 8 * 8);
   const int per_sm = std::max(1, std::min({(int)(kSmemPerSm / (smem + fa.sharedSizeBytes + 1024)),
-                                           65536 / (regs * 256), 8, 512 / TCOLS}));
-  const int64_t tiles = ((int64_t)B * (H / S) * (H / S) + 127) / 128;
+                                           65536 / (regs * 256), 8, 512 / tcols}));
+  const int64_t tiles = HALO ? (int64_t)B * (Ho / RT) : ((int64_t)B * Ho * Ho + 127) / 128;
   const int grid = (int)std::min<int64_t>(tiles, (int64_t)sms * per_sm);
-  fn<<<grid, 256, smem, st>>>(in, w, bias, out, B, H, flag);
+  fn<<<grid, 256, smem, st>>>(in, w, bias, out, B, H, tcols, flag);
   GFH_CUDA_TRY(cudaGetLastError());
   return GFH_OK;
 }
@@ -1172,6 +1217,14 @@ extern "C" int gfh_propose_tiles(gfh_ctx* ctx, const float* d_logits, int32_t ba
     return GFH_ERR_ARG;
   GFH_CUDA_TRY(cudaSetDevice(ctx->device));
   k_propose<<<batch, 256, 0, ctx->stream>>>(d_logits, d_gain, k, tau, d_top, d_resid, d_full);
+  GFH_CUDA_TRY(cudaGetLastError());
+  return GFH_OK;
+}
+
+extern "C" int gfh_wait_check(gfh_ctx* ctx, int64_t cycles) {
+  if (!ctx || cycles < 0 || cycles > 4000000000ll) return GFH_ERR_ARG;
+  GFH_CUDA_TRY(cudaSetDevice(ctx->device));
+  k_wait_unsignalled<<<1, 32, 0, ctx->stream>>>((long long)cycles, ctx->d_flag);
   GFH_CUDA_TRY(cudaGetLastError());
   return GFH_OK;
 }

@@ -36,7 +36,7 @@ EXPORTED = [
     "gfh_cnn_create", "gfh_cnn_destroy", "gfh_cnn_param_count", "gfh_cnn_get_params",
     "gfh_cnn_set_params", "gfh_cnn_forward", "gfh_cnn_gradients", "gfh_cnn_train_step",
     "gfh_propose_tiles", "gfh_conv3x3", "gfh_select_squares", "gfh_coincide",
-    "gfh_n_grid", "gfh_k_segments",
+    "gfh_n_grid", "gfh_k_segments", "gfh_wait_check",
 ]
 N_CLASSES = 4097        # 64 x 64 coarse tiles + no signal
 IMG = 256
@@ -143,6 +143,7 @@ def lib() -> ctypes.CDLL:
             "gfh_select_squares": [vp, vp, P(GridC), i32, i32, i32, vp, vp],
             "gfh_coincide": [vp, vp, i32, vp, i32, dbl, dbl, dbl, vp, vp],
             "gfh_n_grid": [dbl, dbl, dbl, dbl, dbl, dbl, dbl, i32, vp, P(i32)],
+            "gfh_wait_check": [vp, i64],
             "gfh_k_segments": [dbl, dbl, dbl, dbl, dbl, dbl, dbl, i32, i32, vp, P(i32)],
         }
         for name, args in sig.items():
@@ -335,6 +336,10 @@ class Context:
         rc = lib().gfh_hough(self._h, _ptr(fft_idx), _ptr(bins), n_peaks, ctypes.byref(c),
                              _ptr(out_map), _ptr(cands), _ptr(stats))
         _ok(rc, "gfh_hough")
+
+    def wait_check(self, cycles: int) -> None:
+        """gfh_wait_check: a bounded device wait that runs out (the next check() reports it)."""
+        _ok(lib().gfh_wait_check(self._h, cycles), "gfh_wait_check")
 
     def select_squares(self, hmap, g: Grid, n_sx: int, n_sk: int, out, min_dk: int = 3,
                        stats=None) -> None:

@@ -261,3 +261,20 @@ def test_proposals(built_lib, gpu_ctx):
             assert bool(fl[b]) == ofull or abs(ores - tau) < 1e-4
         if tau < 0:
             assert rs[3] < 1e-3 and np.all(fl == 0)
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(built_lib, gpu_ctx):
+    """A device wait that nothing ends gives up after its limit and raises the timeout status;
+    the context then works normally (the same network forward as before, no fault)."""
+    gfh = built_lib
+    assert gpu_ctx.check() == gfh.GFH_OK
+    gpu_ctx.wait_check(2_000_000)                 # ~1 ms at the maximum SM clock
+    assert gpu_ctx.check() == gfh.GFH_ERR_TIMEOUT
+    assert gpu_ctx.check() == gfh.GFH_OK          # cleared
+    net = gfh.Cnn(gpu_ctx, 2, seed=5)
+    _, buf = _batch(gpu_ctx, [1, 2])
+    net.forward(buf.images, buf.logits)
+    torch.cuda.synchronize()
+    assert gpu_ctx.check() == gfh.GFH_OK
+    assert torch.isfinite(buf.logits).all()
+    net.close()
