@@ -288,7 +288,8 @@ int gfh_select(gfh_ctx* ctx, const int32_t* d_map, const gfh_grid* g, gfh_candid
  * lowest row, then column) and d_out[2 q + 1] = the highest count among its cells at least min_dk
  * rows from the first (Sec. IV: about 3 bins); band = q, reserved = 0 / 1; count = -1 where the
  * square has no cell (or no far row).  cr from the mean and deviation over all analysis cells,
- * which also go to d_stats (may be NULL).  n_k <= 65535.  Synchronous (allocates its scratch).
+ * which also go to d_stats (may be NULL).  n_k <= 65535.  Synchronous; its scratch is the
+ * context's (shared with the peakmap builder, grown on demand).
  */
 int gfh_select_squares(gfh_ctx* ctx, const int32_t* d_map, const gfh_grid* g, int32_t n_sx,
                        int32_t n_sk, int32_t min_dk, gfh_candidate* d_out, gfh_map_stats* d_stats);
@@ -399,7 +400,8 @@ int gfh_conv3x3(gfh_ctx* ctx, int32_t mode, int32_t cin, int32_t cout, int32_t s
  * coarse tiles: k tile kt holds the rows r with floor(r coarse_k / K) = kt; x0 tile xt holds the
  * analysis columns whose centre f0 satisfies floor((f0 - ana_lo) / (ana_hi - ana_lo) * coarse_x) =
  * xt (clamped to [0, coarse_x - 1]); the coarse tile id is kt * coarse_x + xt.
- * gfh_plan_set_coarse builds, on the host, the plan's fine tiles (the plan's tile shape) that cover
+ * gfh_plan_set_coarse (GFH_ERR_ARG for a plan with a map whose line moves more than two x0
+ * columns per k row) builds, on the host, the plan's fine tiles (the plan's tile shape) that cover
  * every coarse tile, column ranges widened to multiples of 4; it must follow gfh_plan_create and may
  * be called again (an autotuned plan rebuilds them itself).  max_sel bounds n_sel below.
  * gfh_plan_execute_tiles computes the cells of the coarse tiles listed in d_coarse [n_maps][n_sel]

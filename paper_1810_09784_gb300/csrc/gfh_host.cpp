@@ -396,7 +396,8 @@ extern "C" int gfh_plan_create(gfh_ctx* ctx, int32_t n_maps, const gfh_grid* gri
   if ((tc.cols / 128 + nwarps - 1) / nwarps > 4) return GFH_ERR_ARG;  // <= 4 chunks per warp
 
   std::vector<HostMap> hms(n_maps);
-  std::vector<TileDev> tiles;
+  std::vector<TileDev> tiles, tiles_x;
+  std::vector<char> map_xd(n_maps, 0);
   int max_tile_bands = 1;
   size_t csr_entries = 0;
   for (int m = 0; m < n_maps; ++m) {
@@ -414,19 +415,27 @@ extern "C" int gfh_plan_create(gfh_ctx* ctx, int32_t n_maps, const gfh_grid* gri
     hm.cells = ana_cols * g.n_k;
     csr_entries += (size_t)(g.bin_hi - g.bin_lo + 2);
     if (((uintptr_t)h_maps[m]) % 16) return GFH_ERR_ARG;  // 16-byte vector stores
-    map_tiles(g, hm, m, tc, 0, g.n_k, 0, g.ld_x0, tiles, max_tile_bands);
+    // A line moving more than two columns per k row (coarse k steps, e.g. Eq. dkeqn's) costs
+    // fewer events differenced along x0 on every row (2 per row) than along k (the columns it
+    // crosses): such maps use the x-direction form.
+    map_xd[m] = hm.S[g.n_fft - 1] > (int64_t(2) << GFH_FRAC_BITS);
+    map_tiles(g, hm, m, tc, 0, g.n_k, 0, g.ld_x0, map_xd[m] ? tiles_x : tiles, max_tile_bands);
   }
-  // The tile must fit in shared memory (layout of k_hough: tile, row-0 chunk sums, band keys).
+  // The tile must fit in shared memory (layout of k_hough: tile, chunk sums, band keys).
   const bool select = h_cands != nullptr || d_stats != nullptr;
-  const size_t smem = (size_t)tc.rows * (tc.cols + 2) * 4 + 32 * 4 +
+  const size_t smem = (size_t)tc.rows * (tc.cols + 2) * 4 + 32 * 4 * (tiles_x.empty() ? 1 : tc.rows) +
                       (select ? (size_t)max_tile_bands * 8 : 0);
   if (smem > 227 * 1024) return GFH_ERR_SIZE;
-  // Longest work first: bins x rows.
-  std::stable_sort(tiles.begin(), tiles.end(), [](const TileDev& a, const TileDev& b) {
+  // Longest work first: bins x rows; the x-direction tiles form a second list after the others.
+  auto by_work = [](const TileDev& a, const TileDev& b) {
     const int64_t wa = (int64_t)std::max(0, a.bin_b - a.bin_a + 1) * a.nrows;
     const int64_t wb = (int64_t)std::max(0, b.bin_b - b.bin_a + 1) * b.nrows;
     return wa > wb;
-  });
+  };
+  std::stable_sort(tiles.begin(), tiles.end(), by_work);
+  std::stable_sort(tiles_x.begin(), tiles_x.end(), by_work);
+  const int n_tiles_k = (int)tiles.size();
+  tiles.insert(tiles.end(), tiles_x.begin(), tiles_x.end());
 
   // One device buffer: map descriptors | tiles | csr map index | keys | per-map tables.
   size_t off = 0;
@@ -515,7 +524,9 @@ extern "C" int gfh_plan_create(gfh_ctx* ctx, int32_t n_maps, const gfh_grid* gri
   }
   p->d_maps = (MapDev*)(base + o_maps);
   p->d_tiles = (TileDev*)(base + o_tiles);
-  p->n_tiles = (int)tiles.size();
+  p->n_tiles = n_tiles_k;
+  p->n_tiles_x = (int)tiles.size() - n_tiles_k;
+  p->map_xd = map_xd;
   p->max_tile_bands = max_tile_bands;
   p->d_keys = (unsigned long long*)(base + o_keys);
   p->key_words = key_words;
@@ -550,6 +561,7 @@ extern "C" int gfh_plan_set_coarse(gfh_plan* p, int32_t coarse_k, int32_t coarse
   if (!p || coarse_k < 1 || coarse_x < 1 || coarse_k > 4096 || coarse_x > 4096 || max_sel < 1 ||
       (int64_t)max_sel > (int64_t)coarse_k * coarse_x)
     return GFH_ERR_ARG;
+  if (p->n_tiles_x > 0) return GFH_ERR_ARG;     // coarse tiles need lines moving <= 2 columns per row
   const int nct = coarse_k * coarse_x;
   std::vector<TileDev> fine;
   std::vector<int32_t> first;

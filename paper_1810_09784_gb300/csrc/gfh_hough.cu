@@ -147,6 +147,28 @@ __device__ __forceinline__ void draw_peak(int* G0, int lds, int64_t a, int64_t b
   }
 }
 
+// Events of one peak on the R rows of a tile in the x-direction form: every row differenced along
+// x0 (+1 at its first column, -1 after its last), so a row costs two events whatever the shift per
+// row; an interval entering from the left of the tile counts in that row's carry.
+template <int R>
+__device__ __forceinline__ void draw_peak_x(int* G0, int lds, int64_t a, int64_t b1, int64_t s,
+                                            int c0, int c1m1, int ub, int (&carry)[R]) {
+#pragma unroll
+  for (int rr = 0; rr < R; ++rr) {
+    const int lo = (int)(a >> GFH_FRAC_BITS);
+    const int hi = min((int)(b1 >> GFH_FRAC_BITS), ub);
+    const int o1 = max(lo, c0);
+    int* const Gr = G0 + rr * lds;
+    if (o1 <= hi) {
+      if (lo < c0) carry[rr] += 1;
+      else atomicAdd(Gr + o1, 1);
+      if (hi < c1m1) atomicAdd(Gr + hi + 1, -1);
+    }
+    a -= s;
+    b1 -= s;
+  }
+}
+
 // ---- the accumulation + running sums + select kernel --------------------------------------------
 
 // A tile is R k rows x C columns.  Lane l draws its own peaks on all R rows.
@@ -162,7 +184,9 @@ __device__ __forceinline__ void draw_peak(int* G0, int lds, int64_t a, int64_t b
 // an interval entering from the left of the tile on row 0 is a per-thread carry into column c0.
 //
 // Shared memory: G[R][C+2] | tot[32] row-0 chunk sums | skey[bands] candidate keys.
-template <int R, int NT, bool SELECT>
+// XD (maps whose line moves more than two x0 columns per k row): every row differenced along x0
+// and scanned on its own; chunk sums tot[R][32].
+template <int R, int NT, bool SELECT, bool XD = false>
 __device__ __forceinline__ void hough_tile(const MapDev* __restrict__ maps, const TileDev t,
                                            const uint32_t* __restrict__ fft_idx,
                                            const uint32_t* __restrict__ bins,
@@ -174,7 +198,7 @@ __device__ __forceinline__ void hough_tile(const MapDev* __restrict__ maps, cons
   const int lds = C + 2;
   int* G = reinterpret_cast<int*>(smem);
   int* tot = G + R * (c_max + 2);
-  unsigned long long* skey = reinterpret_cast<unsigned long long*>(tot + kLane);
+  unsigned long long* skey = reinterpret_cast<unsigned long long*>(tot + (XD ? R : 1) * kLane);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nb_tile = t.band_hi >= t.band_lo ? t.band_hi - t.band_lo + 1 : 0;
 
@@ -195,6 +219,7 @@ __device__ __forceinline__ void hough_tile(const MapDev* __restrict__ maps, cons
     const unsigned jmax = (unsigned)(md.bin_hi - md.bin_lo);
     int* const G0 = G - c0;                      // rows indexed by absolute column
     int carry = 0;
+    int carry_x[XD ? R : 1] = {};
     // Software pipeline over this thread's peaks p, p + NT, ...: the indices are loaded two
     // peaks ahead and the table rows one peak ahead of the peak being drawn.
     int64_t p = pb + tid;
@@ -214,27 +239,40 @@ __device__ __forceinline__ void hough_tile(const MapDev* __restrict__ maps, cons
       int64_t a_nx = 0, b_nx = 0, s_nx = 0;
       const bool ok_nx = f_nx != 0xffffffffu &&
                          peak_interval(md, t.row0, f_nx, j_nx, nfft, jmax, flag, a_nx, b_nx, s_nx);
-      if (ok_cu) draw_peak<R>(G0, lds, a_cu, b_cu, s_cu, c0, c1m1, ub, carry);
+      if (ok_cu) {
+        if constexpr (XD) draw_peak_x<R>(G0, lds, a_cu, b_cu, s_cu, c0, c1m1, ub, carry_x);
+        else draw_peak<R>(G0, lds, a_cu, b_cu, s_cu, c0, c1m1, ub, carry);
+      }
       a_cu = a_nx; b_cu = b_nx; s_cu = s_nx; ok_cu = ok_nx;
       f_nx = f_nn; j_nx = j_nn;
     }
-    const int v = warp_sum(carry);
-    if (lane == 0 && v) atomicAdd(G, v);
+    if constexpr (XD) {
+#pragma unroll
+      for (int rr = 0; rr < (XD ? R : 1); ++rr) {
+        const int v = warp_sum(carry_x[rr]);
+        if (lane == 0 && v) atomicAdd(G + rr * lds, v);
+      }
+    } else {
+      const int v = warp_sum(carry);
+      if (lane == 0 && v) atomicAdd(G, v);
+    }
   }
   __syncthreads();
 
   // ---- row-0 chunk sums: chunk = 128 columns (32 lanes x 4); warp w owns chunks w, w+NW, ...
   const int nch = (C + 127) / 128;
-  for (int ch = warp; ch < nch; ch += NW) {
+  const int nsum = XD ? t.nrows * nch : nch;     // (row, chunk) sums: row 0 only, or every row
+  for (int idx = warp; idx < nsum; idx += NW) {
+    const int rr = idx / nch, ch = idx - rr * nch;
     const int col = ch * 128 + lane * 4;
     int s = 0;
     if (col < C) {
-      const int2 u = *reinterpret_cast<const int2*>(&G[col]);
-      const int2 w = *reinterpret_cast<const int2*>(&G[col + 2]);
+      const int2 u = *reinterpret_cast<const int2*>(&G[rr * lds + col]);
+      const int2 w = *reinterpret_cast<const int2*>(&G[rr * lds + col + 2]);
       s = u.x + u.y + w.x + w.y;
     }
     s = warp_sum(s);
-    if (lane == 0) tot[ch] = s;
+    if (lane == 0) tot[rr * kLane + ch] = s;
   }
   __syncthreads();
 
@@ -252,7 +290,7 @@ __device__ __forceinline__ void hough_tile(const MapDev* __restrict__ maps, cons
       const int4 bv = __ldg(reinterpret_cast<const int4*>(md.col_band + t.col0 + col));
       band[0] = bv.x; band[1] = bv.y; band[2] = bv.z; band[3] = bv.w;
     }
-    const int cin = warp_sum((lane < ch) ? tot[lane] : 0);
+    const int cin = XD ? 0 : warp_sum((lane < ch) ? tot[lane] : 0);
     int4 v = make_int4(0, 0, 0, 0);
     for (int rr = 0; rr < t.nrows; ++rr) {
       int4 g = make_int4(0, 0, 0, 0);
@@ -261,10 +299,11 @@ __device__ __forceinline__ void hough_tile(const MapDev* __restrict__ maps, cons
         const int2 w = *reinterpret_cast<const int2*>(&G[rr * lds + col + 2]);
         g = make_int4(u.x, u.y, w.x, w.y);
       }
-      if (rr == 0) {
+      if (XD || rr == 0) {
+        const int cr = XD ? warp_sum((lane < ch) ? tot[rr * kLane + lane] : 0) : cin;
         g.y += g.x; g.z += g.y; g.w += g.z;
         const int incl = warp_incl_scan(g.w, lane);
-        const int add = cin + incl - g.w;
+        const int add = cr + incl - g.w;
         v = make_int4(g.x + add, g.y + add, g.z + add, g.w + add);
       } else {
         v.x += g.x; v.y += g.y; v.z += g.z; v.w += g.w;
@@ -314,7 +353,7 @@ __device__ __forceinline__ void hough_tile(const MapDev* __restrict__ maps, cons
 }
 
 // One block per tile of the plan.
-template <int R, int NT, bool SELECT>
+template <int R, int NT, bool SELECT, bool XD>
 __global__ void __launch_bounds__(NT, R <= 4 ? 3 : (R == 8 ? 2 : 1))
 k_hough(const MapDev* __restrict__ maps, const TileDev* __restrict__ tiles,
         const uint32_t* __restrict__ fft_idx, const uint32_t* __restrict__ bins,
@@ -322,7 +361,7 @@ k_hough(const MapDev* __restrict__ maps, const TileDev* __restrict__ tiles,
   extern __shared__ __align__(16) unsigned char smem[];
   const TileDev t = tiles[blockIdx.x];
   if (t.nrows <= 0) return;
-  hough_tile<R, NT, SELECT>(maps, t, fft_idx, bins, flag, c_max, smem);
+  hough_tile<R, NT, SELECT, XD>(maps, t, fft_idx, bins, flag, c_max, smem);
 }
 
 // Persistent blocks over a tile list whose length is known on the device only (the coarse-tile
@@ -425,16 +464,21 @@ __global__ void k_select_cols(const int32_t* __restrict__ map, const MapDev* __r
 // attribute belongs to the kernel, not to a plan, so it is set to the largest size any plan may
 // request: each launch still asks only for its own size (which alone decides occupancy).
 // n_tiles < 0: the persistent list form over p->d_sel_tiles with its device-side count.
+// xd: the x-direction form (tiles of maps with large shifts per k row).
 template <int R, int NT, bool SEL>
 int launch_hough_t(gfh_plan* p, const gfh_peaks* peaks, const TileDev* tiles, int n_tiles,
-                   size_t smem, bool prepare) {
-  auto fn = k_hough<R, NT, SEL>;
+                   size_t smem, bool prepare, bool xd) {
+  auto fn = xd ? k_hough<R, NT, SEL, true> : k_hough<R, NT, SEL, false>;
   auto fl = k_hough_list<R, NT, SEL>;
   if (prepare) {
     // the list kernel also holds a few bytes of static shared memory
     cudaFuncAttributes fa{};
     GFH_CUDA_TRY(cudaFuncGetAttributes(&fa, fl));
-    GFH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    GFH_CUDA_TRY(cudaFuncSetAttribute(k_hough<R, NT, SEL, false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)kMaxSmemBytes));
+    GFH_CUDA_TRY(cudaFuncSetAttribute(k_hough<R, NT, SEL, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)kMaxSmemBytes));
     GFH_CUDA_TRY(cudaFuncSetAttribute(fl, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(kMaxSmemBytes - fa.sharedSizeBytes)));
@@ -458,24 +502,25 @@ int launch_hough_t(gfh_plan* p, const gfh_peaks* peaks, const TileDev* tiles, in
 
 template <int R, int NT>
 int launch_hough_sel(gfh_plan* p, const gfh_peaks* peaks, const TileDev* tiles, int n_tiles,
-                     size_t smem, bool prepare) {
-  return p->select ? launch_hough_t<R, NT, true>(p, peaks, tiles, n_tiles, smem, prepare)
-                   : launch_hough_t<R, NT, false>(p, peaks, tiles, n_tiles, smem, prepare);
+                     size_t smem, bool prepare, bool xd) {
+  return p->select ? launch_hough_t<R, NT, true>(p, peaks, tiles, n_tiles, smem, prepare, xd)
+                   : launch_hough_t<R, NT, false>(p, peaks, tiles, n_tiles, smem, prepare, xd);
 }
 
 template <int R>
 int launch_hough_r(gfh_plan* p, const gfh_peaks* peaks, const TileDev* tiles, int n_tiles,
-                   size_t smem, bool prepare) {
-  return p->cfg.threads == 256 ? launch_hough_sel<R, 256>(p, peaks, tiles, n_tiles, smem, prepare)
-                               : launch_hough_sel<R, 512>(p, peaks, tiles, n_tiles, smem, prepare);
+                   size_t smem, bool prepare, bool xd) {
+  return p->cfg.threads == 256
+             ? launch_hough_sel<R, 256>(p, peaks, tiles, n_tiles, smem, prepare, xd)
+             : launch_hough_sel<R, 512>(p, peaks, tiles, n_tiles, smem, prepare, xd);
 }
 
 int launch_hough(gfh_plan* p, const gfh_peaks* peaks, const TileDev* tiles, int n_tiles,
-                 size_t smem, bool prepare) {
-  return p->cfg.rows == 4    ? launch_hough_r<4>(p, peaks, tiles, n_tiles, smem, prepare)
-         : p->cfg.rows == 8  ? launch_hough_r<8>(p, peaks, tiles, n_tiles, smem, prepare)
-         : p->cfg.rows == 16 ? launch_hough_r<16>(p, peaks, tiles, n_tiles, smem, prepare)
-                             : launch_hough_r<32>(p, peaks, tiles, n_tiles, smem, prepare);
+                 size_t smem, bool prepare, bool xd = false) {
+  return p->cfg.rows == 4    ? launch_hough_r<4>(p, peaks, tiles, n_tiles, smem, prepare, xd)
+         : p->cfg.rows == 8  ? launch_hough_r<8>(p, peaks, tiles, n_tiles, smem, prepare, xd)
+         : p->cfg.rows == 16 ? launch_hough_r<16>(p, peaks, tiles, n_tiles, smem, prepare, xd)
+                             : launch_hough_r<32>(p, peaks, tiles, n_tiles, smem, prepare, xd);
 }
 
 // Appends to one compact list the fine tiles of each map's selected coarse tiles, or, for a map
@@ -508,13 +553,13 @@ __global__ void k_gather_tiles(const TileDev* __restrict__ fine, const int32_t* 
 
 }  // namespace
 
-size_t gfh_hough_smem_bytes(const gfh_plan* p) {
-  return (size_t)p->cfg.rows * (p->cfg.cols + 2) * 4 + (size_t)kLane * 4 +
+size_t gfh_hough_smem_bytes(const gfh_plan* p, bool xd) {
+  return (size_t)p->cfg.rows * (p->cfg.cols + 2) * 4 + (size_t)kLane * 4 * (xd ? p->cfg.rows : 1) +
          (p->select ? (size_t)p->max_tile_bands * 8 : 0);
 }
 
 int gfh_prepare_plan(gfh_plan* p) {
-  const size_t smem = gfh_hough_smem_bytes(p);
+  const size_t smem = gfh_hough_smem_bytes(p, p->n_tiles_x > 0);
   if (smem > 227 * 1024) return GFH_ERR_SIZE;
   return launch_hough(p, nullptr, nullptr, 0, smem, true);
 }
@@ -550,12 +595,17 @@ static int launch_epilogue(gfh_plan* p) {
 
 int gfh_launch_plan(gfh_plan* p, const gfh_peaks* peaks) {
   GFH_CUDA_TRY(cudaSetDevice(p->ctx->device));
-  const size_t smem = gfh_hough_smem_bytes(p);
-  if (smem > 227 * 1024) return GFH_ERR_SIZE;
+  const size_t smem = gfh_hough_smem_bytes(p, false);
+  const size_t smem_x = gfh_hough_smem_bytes(p, true);
+  if (smem > 227 * 1024 || (p->n_tiles_x > 0 && smem_x > 227 * 1024)) return GFH_ERR_SIZE;
   int rc = launch_prologue(p, peaks);
   if (rc) return rc;
   if (p->n_tiles > 0) {
     rc = launch_hough(p, peaks, p->d_tiles, p->n_tiles, smem, false);
+    if (rc) return rc;
+  }
+  if (p->n_tiles_x > 0) {
+    rc = launch_hough(p, peaks, p->d_tiles + p->n_tiles, p->n_tiles_x, smem_x, false, true);
     if (rc) return rc;
   }
   return launch_epilogue(p);
@@ -564,7 +614,7 @@ int gfh_launch_plan(gfh_plan* p, const gfh_peaks* peaks) {
 int gfh_launch_plan_tiles(gfh_plan* p, const gfh_peaks* peaks, const int32_t* d_coarse, int n_sel,
                           const int32_t* d_full) {
   GFH_CUDA_TRY(cudaSetDevice(p->ctx->device));
-  const size_t smem = gfh_hough_smem_bytes(p);
+  const size_t smem = gfh_hough_smem_bytes(p, false);
   if (smem > 227 * 1024) return GFH_ERR_SIZE;
   int rc = launch_prologue(p, peaks);
   if (rc) return rc;

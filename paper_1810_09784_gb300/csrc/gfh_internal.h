@@ -116,8 +116,10 @@ struct gfh_plan {
   void* d_buf = nullptr;       // tables, map descriptors, tiles
   size_t buf_bytes = 0;
   MapDev* d_maps = nullptr;
-  TileDev* d_tiles = nullptr;
-  int n_tiles = 0;
+  TileDev* d_tiles = nullptr;          // tiles of x-direction maps follow the others
+  int n_tiles = 0;                     // tiles differenced along k (rows > 0)
+  int n_tiles_x = 0;                   // tiles of maps moving > 2 columns per k row: along x0
+  std::vector<char> map_xd;            // per map: drawn in the x-direction form
   int max_tile_bands = 0;
   unsigned long long* d_keys = nullptr;  // all maps' keys and sums (zeroed per execute)
   size_t key_words = 0;
@@ -145,6 +147,9 @@ int gfh_host_tables(const gfh_grid* g, std::vector<int64_t>& U, std::vector<int6
                     std::vector<int64_t>& S);
 int gfh_host_columns(const gfh_grid* g, std::vector<int32_t>& band, std::vector<double>& f0,
                      std::vector<double>& f0n);
+
+// The context's scratch buffer (gfh_peakmap.cu), grown on demand.
+int ensure_scratch(gfh_ctx* c, size_t bytes);
 
 // Launchers (gfh_hough.cu).
 int gfh_launch_plan(gfh_plan* plan, const gfh_peaks* peaks);

@@ -219,19 +219,6 @@ __global__ void k_scatter(const uint32_t* __restrict__ bits, int n_bins, int n_w
   }
 }
 
-int ensure_scratch(gfh_ctx* c, size_t bytes) {
-  if (c->pm_bytes >= bytes) return GFH_OK;
-  if (c->pm_buf) {
-    if (c->stream) cudaStreamSynchronize(c->stream);
-    cudaFree(c->pm_buf);
-    c->pm_buf = nullptr;
-    c->pm_bytes = 0;
-  }
-  if (cudaMalloc(&c->pm_buf, bytes) != cudaSuccess) return GFH_ERR_NOMEM;
-  c->pm_bytes = bytes;
-  return GFH_OK;
-}
-
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
 // Equalise + select + compact from an input layout; `extra` bytes at the front of the scratch
@@ -290,6 +277,20 @@ bool band_ok(int n_fft, int bin_lo, int bin_hi) {
 }
 
 }  // namespace
+
+// The context's scratch buffer, grown on demand (a growth waits for the stream first).
+int ensure_scratch(gfh_ctx* c, size_t bytes) {
+  if (c->pm_bytes >= bytes) return GFH_OK;
+  if (c->pm_buf) {
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    cudaFree(c->pm_buf);
+    c->pm_buf = nullptr;
+    c->pm_bytes = 0;
+  }
+  if (cudaMalloc(&c->pm_buf, bytes) != cudaSuccess) return GFH_ERR_NOMEM;
+  c->pm_bytes = bytes;
+  return GFH_OK;
+}
 
 extern "C" int gfh_peaks_from_power(gfh_ctx* ctx, const float* d_power, int64_t ld, int32_t n_fft,
                                     int32_t bin_lo, int32_t bin_hi, double theta,

@@ -186,8 +186,9 @@ extern "C" int gfh_select_squares(gfh_ctx* ctx, const int32_t* d_map, const gfh_
   auto take = [&](size_t b) { size_t o = off; off = (off + b + 255) / 256 * 256; return o; };
   const size_t o_d = take(sizeof(SqDev)), o_keys = take((size_t)n_sx * g->n_k * 8),
                o_sums = take(16), o_f0 = take(f0.size() * 8), o_f0n = take(f0n.size() * 8);
-  char* buf = nullptr;
-  if (cudaMalloc(&buf, off) != cudaSuccess) return GFH_ERR_NOMEM;
+  rc = ensure_scratch(ctx, off);
+  if (rc) return rc;
+  char* buf = (char*)ctx->pm_buf;
   SqDev d{};
   d.map = d_map;
   d.ld = g->ld_x0;
@@ -225,7 +226,6 @@ extern "C" int gfh_select_squares(gfh_ctx* ctx, const int32_t* d_map, const gfh_
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host vectors must outlive the copies
-  cudaFree(buf);
   return e == cudaSuccess ? GFH_OK : GFH_ERR_CUDA;
 }
 

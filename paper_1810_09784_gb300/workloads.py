@@ -11,6 +11,9 @@ the library's planner.  t0 is the start of the data and FFT i is stamped at its 
                   candidate per 1 Hz.
   batched_n       the plain_small peakmap at 51 braking indices n = 2.0 .. 7.0, fewer k rows at
                   higher n (4000 -> 1000), one map per n.
+  paper_grids     the plain_small peakmap on the paper's own grids: braking indices of
+                  Eq. dn_powlaws over n = 2.5 .. 7 and, for each, the Eq. dkeqn k grid (|fdot|
+                  1e-4 .. 1e-2 Hz/s) as uniform segments, one map per (n, segment).
 """
 from __future__ import annotations
 
@@ -125,6 +128,21 @@ def batched_n(seed: int = 1):
         n = round(2.0 + 0.1 * i, 10)
         n_k = int(round(4000 - 3000 * (n - 2.0) / 5.0))
         grids.append(grid_fields(spec, n, pm["bin_lo"], pm["bin_hi"], n_k, 100.0, 400.0))
+    return spec, pm, grids
+
+
+# ---- paper_grids -----------------------------------------------------------------------------
+
+def paper_grids(seed: int = 1, fdot=(1e-4, 1e-2), n_range=(2.5, 7.0), growth: float = 2.0,
+                max_rows: int = 512):
+    from . import gfh                 # the library's grid planners (Sec. VI)
+    spec, pm, base = plain_small(seed)
+    df, f_min, f_max = spec.df, 100.0, pm["bin_hi"] * spec.df
+    grids = []
+    for n in gfh.n_grid(n_range[0], n_range[1], df, f_min, f_max, fdot[1], spec.t_obs):
+        for sg in gfh.k_segments(float(n), df, f_min, f_max, fdot[0], fdot[1], growth, max_rows):
+            grids.append(dict(base[0], n=float(n), k_min=float(sg["k_min"]), dk=float(sg["dk"]),
+                              n_k=int(sg["n_k"])))
     return spec, pm, grids
 
 

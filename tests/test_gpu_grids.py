@@ -55,3 +55,33 @@ def test_paper_grids_in_one_plan(built_lib, gpu_ctx):
               for c in r)
     assert own >= 0.9 * best[0]
     plan.close()
+
+
+def test_coarse_and_fine_k_steps_in_one_plan(built_lib, gpu_ctx):
+    """Maps whose lines move less than two x0 columns per k row (differenced along k) and maps
+    with coarse k steps (differenced along x0 on every row) in one plan: both bit-exact against
+    the oracle, maps and candidates; the coarse-tile search refuses such a plan."""
+    from gpu_util import assert_candidates_equal
+    gfh = built_lib
+    spec, pm, base = workloads.plain_small()
+    fi, bj = synth.random_peaklist(spec.n_fft, pm["bin_lo"], pm["bin_hi"], 0.0755, 9)
+    g_fine = gfh.grid_make(gfh.Grid(**dict(base[0], n_k=40)))
+    fields = [dict(base[0], n_k=40),                                   # default step
+              dict(base[0], n_k=23, dk=g_fine.dk * 7.5),               # 7.5 columns per row
+              dict(base[0], n=3.0, n_k=17, k_min=g_fine.dk, dk=1.3e-11)]   # ~3 columns per row
+    gs = [gfh.grid_make(gfh.Grid(**f)) for f in fields]
+    maps = [torch.full((g.n_k, g.ld_x0), -7, dtype=torch.int32, device="cuda") for g in gs]
+    cands = [torch.zeros(g.n_bands * 64, dtype=torch.uint8, device="cuda") for g in gs]
+    plan = gfh.Plan(gpu_ctx, gs, maps, cands, tile=(8, 2048, 512))
+    plan.execute(to_dev(torch, fi), to_dev(torch, bj), to_dev(torch, np.array([0, fi.size], np.int64)), 1)
+    torch.cuda.synchronize()
+    assert gpu_ctx.check() == gfh.GFH_OK
+    for f, g, m, c in zip(fields, gs, maps, cands):
+        o = oracle_grid(f)
+        ref = O.hough_map(o, fi, bj)
+        assert np.array_equal(m.cpu().numpy()[:, : g.n_x0], ref), f["n_k"]
+        oc, _ = O.select_candidates(o, ref)
+        assert_candidates_equal(read_cands(gfh, c), oc, g.n_bands)
+    with pytest.raises(gfh.GfhError):
+        plan.set_coarse(64, 64, 8)
+    plan.close()
