@@ -10,6 +10,9 @@ only for the brute-force checks on tiny inputs), written from the paper's equati
   Sec. II   k = |fdot0| / f0^n
   Sec. III  peakmap: equalised spectra, peaks above a threshold that are local maxima
   Sec. IV   Eq. transform  x = 1/f^(n-1), x0 = 1/f0^(n-1);  line x = x0 + (n-1) k (t - t0)
+  Sec. III  Eq. fdotslope  (original FrequencyHough, n = 0 here) f0 = f - fdot (t - t0): taken as
+            x = -f, x0 = -f0, k = -fdot, so that x0 = x - k (t - t0) has the orientation of
+            Eq. transform's x0 = x - (n-1) k (t - t0) with (n-1) replaced by 1
   Sec. IV   each peak is a line in the (x0, k) plane; the Hough map is the histogram of lines
   Sec. IV   candidates per region of the map, critical ratio CR = (y - mu)/sigma, distance d
   Sec. VI.B Eq. dkeqn  dk = k((1 + df/f0max)^(-n) - 1)
@@ -68,13 +71,25 @@ def k_from_spindown(f0: float, fdot0: float, n: float) -> float:
 
 
 def x_of_f(f, n: float):
-    """Sec. IV Eq. transform: x = 1 / f^(n-1)."""
-    return np.asarray(f, dtype=np.float64) ** (1.0 - n)
+    """Sec. IV Eq. transform: x = 1 / f^(n-1); for n = 0 (original FrequencyHough, Sec. III
+    Eq. fdotslope) x = -f."""
+    f = np.asarray(f, dtype=np.float64)
+    return -f if n == 0.0 else f ** (1.0 - n)
 
 
 def f_of_x(x, n: float):
-    """Inverse of Sec. IV Eq. transform: f = x^(-1/(n-1))."""
-    return np.asarray(x, dtype=np.float64) ** (-1.0 / (n - 1.0))
+    """Inverse of Sec. IV Eq. transform: f = x^(-1/(n-1)); for n = 0, f = -x."""
+    x = np.asarray(x, dtype=np.float64)
+    return -x if n == 0.0 else x ** (-1.0 / (n - 1.0))
+
+
+def slope(n: float) -> float:
+    """Factor of k t in x0 = x - slope k t: n - 1 (Eq. transform), 1 for n = 0 (Eq. fdotslope)."""
+    return 1.0 if n == 0.0 else n - 1.0
+
+
+def _x_scalar(f: float, n: float) -> float:
+    return -f if n == 0.0 else math.pow(f, 1.0 - n)
 
 
 def dk_step(k: float, df: float, f0max: float, n: float) -> float:
@@ -197,24 +212,30 @@ class Grid:
 def make_grid(g: Grid) -> Grid:
     """Fill the derived fields: dx0 (Sec. VI.C, finest step at f_max), dk, x0_min, n_x0.
 
-    x0_min is one column left of the lowest x0 any peak can reach, x(f_top edge) - (n-1) k_max t_max;
-    n_x0 reaches one column past x(f_bottom edge).
+    x0_min is one column left of the lowest x0 any peak can reach, x(f_top edge) - (n-1) k_max t_max
+    (no move for k_max <= 0); n_x0 reaches one column past the highest, x(f_bottom edge), moved by
+    -(n-1) k_min t_max when k_min < 0.  n = 0 is the original FrequencyHough (x = -f, slope 1,
+    dx0 = df, default dk = df / T_obs); only it takes k_min < 0 (spin-up).
     """
     g = dataclasses.replace(g)
     n = g.n
-    if not (n > 1.0) or g.bin_lo < 1 or g.bin_hi < g.bin_lo or g.n_fft < 1 or g.n_k < 1:
+    if not (n > 1.0 or n == 0.0) or g.bin_lo < 1 or g.bin_hi < g.bin_lo or g.n_fft < 1 or g.n_k < 1:
         raise ValueError("invalid grid request")
+    if g.k_min < 0.0 and n != 0.0:
+        raise ValueError("k_min < 0 needs n = 0")
+    m = slope(n)
     if g.f_max <= 0.0:
         g.f_max = g.bin_hi * g.df
-    g.dx0 = (n - 1.0) * g.df / math.pow(g.f_max, n)
+    g.dx0 = m * g.df / math.pow(g.f_max, n)
     if g.dk <= 0.0:
-        g.dk = g.dx0 / ((n - 1.0) * g.t_obs)
+        g.dk = g.dx0 / (m * g.t_obs)
     k_max = g.k_min + (g.n_k - 1) * g.dk
     t_max = g.t_first + (g.n_fft - 1) * g.t_hop
-    x_top = math.pow((g.bin_hi + 0.5) * g.df, 1.0 - n)
-    x_bot = math.pow((g.bin_lo - 0.5) * g.df, 1.0 - n)
-    g.x0_min = x_top - (n - 1.0) * k_max * t_max - g.dx0
-    g.n_x0 = int(math.ceil((x_bot - g.x0_min) / g.dx0)) + 1
+    x_top = _x_scalar((g.bin_hi + 0.5) * g.df, n)
+    x_bot = _x_scalar((g.bin_lo - 0.5) * g.df, n)
+    g.x0_min = x_top - m * max(k_max, 0.0) * t_max - g.dx0
+    x0_hi = x_bot - m * g.k_min * t_max if g.k_min < 0.0 else x_bot
+    g.n_x0 = int(math.ceil((x0_hi - g.x0_min) / g.dx0)) + 1
     return g
 
 
@@ -230,19 +251,20 @@ def edge_positions(g: Grid) -> list:
     J = g.bin_hi - g.bin_lo + 1
     out = []
     for e in range(J + 1):
-        x = math.pow((g.bin_lo + e - 0.5) * g.df, 1.0 - g.n)
+        x = _x_scalar((g.bin_lo + e - 0.5) * g.df, g.n)
         out.append(fixed_floor((x - g.x0_min) / g.dx0))
     return out
 
 
 def fft_shifts(g: Grid):
-    """(B_i, S_i): the shift (n-1) k t_i / dx0 of Sec. IV's line, for k = k_min (B) and per k row (S),
-    on the 2^-32 column lattice.  t_i = t_first + i t_hop."""
+    """(B_i, S_i): the shift (n-1) k t_i / dx0 of Sec. IV's line (k t_i / dx0 for n = 0), for
+    k = k_min (B) and per k row (S), on the 2^-32 column lattice.  t_i = t_first + i t_hop."""
     B, S = [], []
+    m = slope(g.n)
     for i in range(g.n_fft):
         t = g.t_first + i * g.t_hop
-        B.append(fixed_floor((g.n - 1.0) * g.k_min * t / g.dx0))
-        S.append(fixed_floor((g.n - 1.0) * g.dk * t / g.dx0))
+        B.append(fixed_floor(m * g.k_min * t / g.dx0))
+        S.append(fixed_floor(m * g.dk * t / g.dx0))
     return B, S
 
 
@@ -333,12 +355,16 @@ def column_bands(g: Grid):
     f0c = np.zeros(W)
     f0n = np.zeros(W)
     band = np.full(W, -1, dtype=np.int64)
-    e = -1.0 / (g.n - 1.0)
     for m in range(W):
         x0c = g.x0_min + (m + 0.5) * g.dx0
-        if x0c <= 0.0:
+        if g.n == 0.0:
+            f = -x0c
+        elif x0c > 0.0:
+            f = math.pow(x0c, -1.0 / (g.n - 1.0))
+        else:
             continue
-        f = math.pow(x0c, e)
+        if f <= 0.0:
+            continue
         f0c[m] = f
         f0n[m] = math.pow(f, g.n)
         if g.ana_lo <= f < g.ana_hi:
@@ -520,3 +546,80 @@ def peaks_from_power(P: np.ndarray, bin_lo: int, bin_hi: int, theta: float = THE
 def peakmap(series, fs: float, t_fft: float, bin_lo: int, bin_hi: int, theta: float = THETA):
     """Sec. III: time series -> interlaced FFTs -> equalised spectra -> thresholded local maxima."""
     return peaks_from_power(short_power_spectra(series, fs, t_fft), bin_lo, bin_hi, theta)
+
+
+# ----------------------------------------------------------------------------------------------
+# Sec. V follow-up: heterodyne correction, longer-FFT peakmap of the corrected series, original
+# FrequencyHough on it (n = 0 grids above), projection of the corrected peakmap onto frequency
+# ----------------------------------------------------------------------------------------------
+def spindown_cycles(t, f0: float, k: float, n: float):
+    """Residual phase of Sec. V Eq. phcor in cycles: integral from t0 to t of (f(t') - f0) dt' with
+    f from Eq. powlaws, i.e. F(t) - f0 t where F is the integral of f.  With a = (n-1) k f0^(n-1):
+    F(t) = f0 (n-1) / ((n-2) a) ((1 + a t)^((n-2)/(n-1)) - 1) for n != 2 and (f0 / a) ln(1 + a t)
+    for n = 2 (t measured from t0)."""
+    t = np.asarray(t, dtype=np.float64)
+    a = (n - 1.0) * k * f0 ** (n - 1.0)
+    if a == 0.0:
+        return np.zeros_like(t)
+    L = np.log1p(a * t)
+    if n == 2.0:
+        F = (f0 / a) * L
+    else:
+        F = f0 * (n - 1.0) / ((n - 2.0) * a) * np.expm1((n - 2.0) / (n - 1.0) * L)
+    return F - f0 * t
+
+
+def heterodyne(series, fs: float, t_start: float, f0: float, k: float, n: float):
+    """Sec. V: h'(t) = h(t) exp(-2 pi j (F(t) - f0 t)) at t = t_start + s / fs, so that the power
+    law of (f0, k, n) becomes a constant line at f0 (complex128).  The sign makes the positive-
+    frequency part of a real signal monochromatic (the paper writes e^{j phi_sd} with its own
+    convention)."""
+    h = np.asarray(series, dtype=np.float64)
+    t = t_start + np.arange(h.size, dtype=np.float64) / fs
+    c = spindown_cycles(t, f0, k, n)
+    return h * np.exp(-2j * np.pi * c)
+
+
+def complex_power_spectra(z, fs: float, t_fft: float):
+    """Interlaced (50% overlap) boxcar FFTs of length N = fs T_FFT of a complex series (fp64,
+    numpy's complex FFT); |X|^2 rounded to float32, [n_fft][N] (bin j = frequency j / T_FFT for
+    j < N/2)."""
+    z = np.asarray(z, dtype=np.complex128)
+    N = int(round(fs * t_fft))
+    hop = N // 2
+    n_fft = (z.size - N) // hop + 1
+    frames = np.lib.stride_tricks.as_strided(z, shape=(n_fft, N), strides=(hop * 16, 16))
+    X = np.fft.fft(frames, axis=1)
+    return (X.real * X.real + X.imag * X.imag).astype(np.float32)
+
+
+def peakmap_complex(z, fs: float, t_fft: float, bin_lo: int, bin_hi: int, theta: float = THETA):
+    """Sec. III peakmap of a complex (heterodyned) series: complex FFTs, then the same equaliser and
+    peak test as the real series."""
+    return peaks_from_power(complex_power_spectra(z, fs, t_fft), bin_lo, bin_hi, theta)
+
+
+def bin_shift(i, t_first: float, t_hop: float, df: float, fdot: float):
+    """Sec. V correction of a peakmap by shifting bins: FFT i (time t_i = t_first + i t_hop) moves
+    by floor(fdot t_i / df + 1/2) bins, the rounded drift of the line f0 + fdot t."""
+    t = t_first + np.asarray(i, dtype=np.float64) * t_hop
+    return np.floor(fdot * t / df + 0.5).astype(np.int64)
+
+
+def project_peaks(fft_idx, bins, t_first: float, t_hop: float, df: float, fdot: float, bin_lo: int,
+                  bin_hi: int):
+    """Sec. V projection: every peak (i, j) is moved to bin j - shift_i (bin_shift) and counted per
+    bin; returns the counts of bins bin_lo..bin_hi (int64)."""
+    j = np.asarray(bins, dtype=np.int64) - bin_shift(fft_idx, t_first, t_hop, df, fdot)
+    keep = (j >= bin_lo) & (j <= bin_hi)
+    return np.bincount(j[keep] - bin_lo, minlength=bin_hi - bin_lo + 1).astype(np.int64)
+
+
+def projection_cr(counts, j: int):
+    """Sec. V: CR = (y - mu) / sigma of the projected count y at local bin j, mu and sigma the
+    population mean and standard deviation of the counts of all other bins (the noise)."""
+    c = np.asarray(counts, dtype=np.float64)
+    rest = np.delete(c, j)
+    mu = float(rest.mean())
+    sigma = float(rest.std())
+    return (float(c[j]) - mu) / sigma if sigma > 0.0 else 0.0

@@ -19,10 +19,23 @@ int64_t floor_shift(int64_t v) { return v >> GFH_FRAC_BITS; }  // arithmetic shi
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// n = 0 selects the original FrequencyHough (Sec. III Eq. fdotslope): x = -f, x0 = -f0 and
+// x0 = x - k t with k = -fdot, the orientation and slope convention of Eq. transform's
+// x0 = x - (n-1) k t with (n-1) replaced by 1.  Only this form accepts k < 0 (spin-up).
+bool original_fh(const gfh_grid* g) { return g->n == 0.0; }
+
+double slope_of(const gfh_grid* g) { return original_fh(g) ? 1.0 : g->n - 1.0; }
+
+// x of frequency f: Eq. transform (n > 1) or -f (n = 0).
+double x_of_f(const gfh_grid* g, double f) {
+  return original_fh(g) ? -f : std::pow(f, 1.0 - g->n);
+}
+
 bool grid_request_ok(const gfh_grid* g) {
-  return g && g->n > 1.0 && g->df > 0.0 && g->bin_lo >= 1 && g->bin_hi >= g->bin_lo &&
-         g->n_fft >= 1 && g->n_k >= 1 && g->t_first >= 0.0 && g->t_hop >= 0.0 &&
-         g->t_obs > 0.0 && g->k_min >= 0.0 && g->ana_hi > g->ana_lo && g->band_hz > 0.0 &&
+  return g && (g->n > 1.0 || g->n == 0.0) && g->df > 0.0 && g->bin_lo >= 1 &&
+         g->bin_hi >= g->bin_lo && g->n_fft >= 1 && g->n_k >= 1 && g->t_first >= 0.0 &&
+         g->t_hop >= 0.0 && g->t_obs > 0.0 && (g->k_min >= 0.0 || g->n == 0.0) &&
+         std::isfinite(g->k_min) && g->ana_hi > g->ana_lo && g->band_hz > 0.0 &&
          std::isfinite(g->n) && std::isfinite(g->df);
 }
 
@@ -51,15 +64,19 @@ extern "C" const char* gfh_strerror(int code) {
 extern "C" int gfh_grid_make(gfh_grid* g) {
   if (!grid_request_ok(g)) return GFH_ERR_ARG;
   const double n = g->n;
+  const double m = slope_of(g);
   if (!(g->f_max > 0.0)) g->f_max = (double)g->bin_hi * g->df;
-  g->dx0 = (n - 1.0) * g->df / std::pow(g->f_max, n);               // Sec. VI.C
-  if (!(g->dk > 0.0)) g->dk = g->dx0 / ((n - 1.0) * g->t_obs);
+  g->dx0 = m * g->df / std::pow(g->f_max, n);                        // Sec. VI.C (df for n = 0)
+  if (!(g->dk > 0.0)) g->dk = g->dx0 / (m * g->t_obs);
   const double k_max = g->k_min + (double)(g->n_k - 1) * g->dk;
   const double t_max = g->t_first + (double)(g->n_fft - 1) * g->t_hop;
-  const double x_top = std::pow(((double)g->bin_hi + 0.5) * g->df, 1.0 - n);  // Eq. transform
-  const double x_bot = std::pow(((double)g->bin_lo - 0.5) * g->df, 1.0 - n);
-  g->x0_min = x_top - (n - 1.0) * k_max * t_max - g->dx0;
-  const double w = std::ceil((x_bot - g->x0_min) / g->dx0);
+  const double x_top = x_of_f(g, ((double)g->bin_hi + 0.5) * g->df);  // Eq. transform
+  const double x_bot = x_of_f(g, ((double)g->bin_lo - 0.5) * g->df);
+  // lowest x0 of any line: x_top moved by the largest positive k; highest: x_bot moved by the most
+  // negative k (none for k_min >= 0)
+  g->x0_min = x_top - m * (k_max > 0.0 ? k_max : 0.0) * t_max - g->dx0;
+  const double x0_hi = g->k_min < 0.0 ? x_bot - m * g->k_min * t_max : x_bot;
+  const double w = std::ceil((x0_hi - g->x0_min) / g->dx0);
   if (!(g->dx0 > 0.0) || !std::isfinite(w) || w < 0.0 || w > 2.0e9) return GFH_ERR_SIZE;
   g->n_x0 = (int64_t)w + 1;
   g->ld_x0 = (g->n_x0 + 31) / 32 * 32;
@@ -76,15 +93,16 @@ int gfh_host_tables(const gfh_grid* g, std::vector<int64_t>& U, std::vector<int6
   U.resize((size_t)J + 1);
   for (int e = 0; e <= J; ++e) {
     const double f = ((double)(g->bin_lo + e) - 0.5) * g->df;
-    const double x = std::pow(f, 1.0 - g->n);
+    const double x = x_of_f(g, f);
     U[e] = fixed_floor((x - g->x0_min) / g->dx0);
   }
   B.resize(g->n_fft);
   S.resize(g->n_fft);
+  const double m = slope_of(g);
   for (int i = 0; i < g->n_fft; ++i) {
     const double t = g->t_first + (double)i * g->t_hop;
-    B[i] = fixed_floor((g->n - 1.0) * g->k_min * t / g->dx0);
-    S[i] = fixed_floor((g->n - 1.0) * g->dk * t / g->dx0);
+    B[i] = fixed_floor(m * g->k_min * t / g->dx0);
+    S[i] = fixed_floor(m * g->dk * t / g->dx0);
   }
   return GFH_OK;
 }
@@ -99,8 +117,8 @@ int gfh_host_columns(const gfh_grid* g, std::vector<int32_t>& band, std::vector<
   const double e = -1.0 / (g->n - 1.0);
   for (int64_t m = 0; m < W; ++m) {
     const double x0c = g->x0_min + ((double)m + 0.5) * g->dx0;
-    if (!(x0c > 0.0)) continue;
-    const double f = std::pow(x0c, e);
+    const double f = original_fh(g) ? -x0c : (x0c > 0.0 ? std::pow(x0c, e) : 0.0);
+    if (!(f > 0.0)) continue;
     f0[m] = f;
     f0n[m] = std::pow(f, g->n);
     if (g->ana_lo <= f && f < g->ana_hi) {
@@ -338,10 +356,20 @@ void map_tiles(const gfh_grid& g, const HostMap& hm, int m, const gfh_tile_confi
                int r1, int64_t c_lo, int64_t c_hi, std::vector<TileDev>& tiles, int& max_bands) {
   for (int rr = r0; rr < r1; rr += tc.rows) {
     const int nr = std::min(tc.rows, r1 - rr);
-    // B and S are non-decreasing in i (k_min >= 0, dk > 0, t_i non-decreasing), so the smallest
-    // shift of the row block is at (i = 0, rr) and the largest at (last i, last row).
-    const int64_t s_min = hm.B[0] + (int64_t)rr * hm.S[0];
-    const int64_t s_max = hm.B[g.n_fft - 1] + (int64_t)(rr + nr - 1) * hm.S[g.n_fft - 1];
+    // With k_min >= 0, B and S are non-decreasing in i (dk > 0, t_i non-decreasing), so the
+    // smallest shift of the row block is at (i = 0, rr) and the largest at (last i, last row).
+    // With k_min < 0 (n = 0 only) B falls with i: the shift of FFT i is linear in the row, so
+    // its extremes over the block are at the block's first and last rows, taken over every i.
+    int64_t s_min = hm.B[0] + (int64_t)rr * hm.S[0];
+    int64_t s_max = hm.B[g.n_fft - 1] + (int64_t)(rr + nr - 1) * hm.S[g.n_fft - 1];
+    if (g.k_min < 0.0) {
+      for (int i = 0; i < g.n_fft; ++i) {
+        const int64_t a = hm.B[i] + (int64_t)rr * hm.S[i];
+        const int64_t b = hm.B[i] + (int64_t)(rr + nr - 1) * hm.S[i];
+        s_min = std::min(s_min, std::min(a, b));
+        s_max = std::max(s_max, std::max(a, b));
+      }
+    }
     for (int64_t c0 = c_lo; c0 < c_hi; c0 += tc.cols) {
       TileDev t{};
       t.map = m;

@@ -41,6 +41,10 @@ def _pairs():
     _, _, grids = workloads.batched_n()
     out += [grids[0], grids[13], grids[-1]]
     out.append(dict(grids[5], k_min=3e-19, dk=5e-18, f_max=401.0, band_hz=0.5))
+    # original FrequencyHough (n = 0): spin-down only, and both signs of fdot
+    base = workloads.plain_small()[2][0]
+    out.append(dict(base, n=0.0, n_k=64))
+    out.append(dict(base, n=0.0, n_k=64, k_min=-32 * 0.5 / 1800.0, ana_lo=150.0, ana_hi=350.0))
     return out
 
 
@@ -79,10 +83,14 @@ def test_invalid_requests_are_rejected(built_lib):
     _, _, grids = workloads.plain_small()
     base = grids[0]
     for bad in (dict(n=1.0), dict(bin_hi=base["bin_lo"] - 1), dict(n_k=0), dict(df=0.0),
-                dict(ana_hi=base["ana_lo"]), dict(band_hz=0.0), dict(k_min=-1.0)):
+                dict(ana_hi=base["ana_lo"]), dict(band_hz=0.0), dict(k_min=-1.0), dict(n=0.5),
+                dict(n=-1.0)):
         with pytest.raises(built_lib.GfhError) as e:
             built_lib.grid_make(built_lib.Grid(**dict(base, **bad)))
         assert e.value.code == built_lib.GFH_ERR_ARG
+    # k < 0 (spin-up) is the original FrequencyHough's alone
+    g = built_lib.grid_make(built_lib.Grid(**dict(base, n=0.0, k_min=-1e-3)))
+    assert g.dx0 == base["df"]
 
 
 def test_n_grid_matches_oracle(built_lib):
