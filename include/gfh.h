@@ -50,7 +50,12 @@ typedef struct gfh_plan gfh_plan;
 
 /*
  * One Hough map (Sec. IV-VI).  The caller fills the request fields; gfh_grid_make fills the rest.
- *   n            braking index, n > 1 (Sec. I Eq. 1; Sec. II Eq. diff_powlaws fdot = -k f^n)
+ *   n            braking index, n > 1 (Sec. I Eq. 1; Sec. II Eq. diff_powlaws fdot = -k f^n), or
+ *                n = 0: the original FrequencyHough of Sec. III Eq. fdotslope (lines f0 = f - fdot t
+ *                in the (f0, fdot) plane), mapped onto the same accumulator as x = -f, x0 = -f0,
+ *                k = -fdot and x0 = x - k t (Eq. transform's x0 = x - (n-1) k t with (n-1) -> 1):
+ *                dx0 = df, default dk = df / t_obs, candidates' x0 = -f0 and fdot0 = -k; only
+ *                n = 0 accepts k_min < 0 (spin-up)
  *   df           frequency bin width 1/T_FFT [Hz]
  *   bin_lo..hi   peakmap band of this map, inclusive bins (f_j = j df); peaks outside are ignored
  *   n_fft        number of FFTs; t_first, t_hop give t_i = t_first + i t_hop from t0 [s]
@@ -62,8 +67,9 @@ typedef struct gfh_plan gfh_plan;
  *                inside it (Sec. IV: the peakmap band is wider than the analysed band)
  *   band_hz      candidate band width in f0 [Hz]: one candidate per band
  *   list         index of the peak list this map reads (gfh_plan_execute)
- * Derived: dx0 = (n-1) df / f_max^n; x0_min = x(f_top edge) - (n-1) k_max t_max - dx0;
- *   n_x0 = ceil((x(f_bottom edge) - x0_min)/dx0) + 1; ld_x0 = n_x0 rounded up to 32;
+ * Derived: dx0 = (n-1) df / f_max^n; x0_min = x(f_top edge) - (n-1) max(k_max, 0) t_max - dx0;
+ *   n_x0 = ceil((x(f_bottom edge) - (n-1) min(k_min, 0) t_max - x0_min)/dx0) + 1 (with 1 for
+ *   n - 1 when n = 0); ld_x0 = n_x0 rounded up to 32;
  *   n_bands = ceil((ana_hi - ana_lo)/band_hz).
  */
 typedef struct gfh_grid {
@@ -305,6 +311,58 @@ int gfh_select_squares(gfh_ctx* ctx, const int32_t* d_map, const gfh_grid* g, in
 int gfh_coincide(gfh_ctx* ctx, const gfh_candidate* d_a, int32_t na, const gfh_candidate* d_b,
                  int32_t nb, double dx0, double dk, double radius, int32_t* d_match,
                  double* d_dist);
+
+/* ---- follow-up of a candidate (Sec. V) ----------------------------------------------------------
+ *
+ * A candidate (f0, k, n) of the generalized search is followed up on the strain series: the series
+ * is corrected by the candidate's spin-down phase (gfh_heterodyne), a peakmap with longer FFTs is
+ * built from the corrected complex series (gfh_peakmap_complex), the original FrequencyHough (a grid
+ * with n = 0) finds the residual (f0, fdot), and the peakmap corrected by that residual is projected
+ * onto the frequency axis (gfh_project_peaks) for a new critical ratio.
+ */
+
+/*
+ * Heterodyne correction (Sec. V Eq. phcor): d_out[s] = d_h[s] exp(-2 pi j c(t_s)) with t_s =
+ * t_start + s / fs (seconds from t0 of Eq. powlaws) and c(t) = F(t) - f0 t, F the integral from t0
+ * to t of f(t') = f0 / (1 + k (n-1) f0^(n-1) t')^(1/(n-1)):
+ *   F = f0 (n-1) / ((n-2) a) ((1 + a t)^((n-2)/(n-1)) - 1), a = (n-1) k f0^(n-1)  (n != 2),
+ *   F = (f0 / a) ln(1 + a t)                                                  (n = 2),
+ * so that a power law of these parameters becomes a line at f0 (the sign makes the positive-
+ * frequency half of a real signal monochromatic; the paper writes e^{j phi_sd} in its convention).
+ *   d_h     float32 [n_samples] on the device (a 16-byte aligned pointer takes the vector path)
+ *   d_out   complex64 [n_samples] as interleaved float32 pairs (re, im), caller-owned
+ * Needs n > 1, k >= 0, t_start >= 0, f0 > 0.  Phase accuracy: c is exact in fp64 at anchors every
+ * 1024 samples and continued by its Taylor series to fourth order; GFH_ERR_ARG when the spin-down
+ * is too fast for that span (second..fourth-order terms above 1/8 cycle or a fifth-order term
+ * above 1e-9 cycle over 1024 samples at t_start).  The applied phase is the cycle fraction rounded
+ * to 2^-32 and then to float32.  Asynchronous; uses the context's scratch (1024x fewer anchors
+ * than samples, 32 bytes each).
+ */
+int gfh_heterodyne(gfh_ctx* ctx, const float* d_h, int64_t n_samples, double fs, double t_start,
+                   double f0, double k, double n, float* d_out);
+
+/*
+ * Peakmap of a complex series (Sec. III applied to the heterodyned series of Sec. V): d_z complex64
+ * [n_samples] (interleaved re, im) at fs Hz; complex-to-complex FFTs (cuFFT, forward,
+ * unnormalised) of the interlaced boxcar frames of gfh_peakmap (N = round(fs t_fft), hop N/2),
+ * |X|^2 in float32, then the equaliser and peak test of gfh_peaks_from_power.  Bin j is frequency
+ * j / t_fft for j < N/2; bin_hi + 1 <= N - 1.  Same outputs, errors and synchronisation as
+ * gfh_peakmap.
+ */
+int gfh_peakmap_complex(gfh_ctx* ctx, const float* d_z, int64_t n_samples, double fs, double t_fft,
+                        int32_t bin_lo, int32_t bin_hi, double theta, uint32_t* d_fft_idx,
+                        uint32_t* d_bin, int64_t cap, int64_t* h_n_peaks);
+
+/*
+ * Projection of a bin-shifted peakmap onto frequency (Sec. V): peak (i, j) of the list (device
+ * arrays of n_peaks) moves to bin j - floor(fdot t_i / df + 1/2), t_i = t_first + i t_hop (each
+ * fp64 operation IEEE-rounded in that order), and d_counts[b - bin_lo] (int32, bin_hi - bin_lo + 1
+ * <= 12288 entries, caller-owned) counts the peaks that land on bin b.  A line f0 + fdot t becomes
+ * one column of the corrected peakmap.  Asynchronous.
+ */
+int gfh_project_peaks(gfh_ctx* ctx, const uint32_t* d_fft_idx, const uint32_t* d_bin,
+                      int64_t n_peaks, double t_first, double t_hop, double df, double fdot,
+                      int32_t bin_lo, int32_t bin_hi, int32_t* d_counts);
 
 /* ---- statistical peakmaps and the learned tile proposer ------------------------------------------
  *

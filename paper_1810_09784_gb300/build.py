@@ -17,7 +17,8 @@ ROOT = PKG.parent
 CSRC = PKG / "csrc"
 BUILD = ROOT / "_build"
 LIB = PKG / "libgfh.so"
-SOURCES = ["gfh_host.cpp", "gfh_hough.cu", "gfh_peakmap.cu", "gfh_cnn.cu", "gfh_squares.cu"]
+SOURCES = ["gfh_host.cpp", "gfh_hough.cu", "gfh_peakmap.cu", "gfh_cnn.cu", "gfh_squares.cu",
+           "gfh_followup.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,0 +1,187 @@
+// Follow-up of a candidate (Sec. V) on sm_103a: the heterodyne correction of the strain series by
+// the candidate's spin-down phase (Eq. phcor) and the projection of a bin-shifted peakmap onto the
+// frequency axis.  (The longer-FFT peakmap of the corrected series is gfh_peakmap_complex; the
+// original FrequencyHough on it is the accumulator with an n = 0 grid.)
+//
+// Heterodyne.  The residual phase c(t) = F(t) - f0 t (F the integral of Eq. powlaws) reaches 1e6-1e7
+// cycles over a long observation, so it needs fp64 - and fp64 is the slow pipe of this GPU.  It is
+// therefore evaluated in fp64 only at anchors every kAnchor samples (closed form, one thread per
+// anchor), together with its first four derivatives.  Each sample then adds, modulo one cycle, the
+// exact linear term on a 64-bit fixed-point lattice (integer multiply-add: no fp64) and the small
+// quadratic..quartic terms in fp32; the fraction of a cycle feeds sincospif.  The kernel moves
+// 4 bytes in and 8 bytes out per sample and is bound by HBM.
+#include <algorithm>
+#include <cmath>
+
+#include "gfh_internal.h"
+
+namespace {
+
+constexpr int kAnchorLog2 = 10;
+constexpr int64_t kAnchor = int64_t(1) << kAnchorLog2;
+
+struct HetAnchor {
+  unsigned long long C;   // c(t_a) mod 1 in units of 2^-64 cycles
+  unsigned long long Q;   // (f(t_a) - f0) / fs mod 1: cycles per sample, 2^-64 units
+  float e2, e3, e4;       // fdot/2, fddot/6, f'''/24 over fs^2, fs^3, fs^4: cycles per sample^k
+  float pad;
+};
+
+struct HetParams {
+  double fs, t_start, f0, k, n;
+};
+
+// x mod 1 on the 2^-64 lattice (x finite).
+__device__ __forceinline__ unsigned long long frac64(double x) {
+  double y = x - floor(x);
+  if (!(y < 1.0)) y = 0.0;
+  return __double2ull_rz(ldexp(y, 64));
+}
+
+// One thread per anchor: the residual phase and the derivatives of f at t_a = t_start + a kAnchor/fs.
+__global__ void k_het_anchor(HetParams p, int64_t n_anchor, HetAnchor* __restrict__ out) {
+  const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n_anchor) return;
+  const double t = p.t_start + (double)(a * kAnchor) / p.fs;
+  const double m1 = p.n - 1.0;
+  const double acoef = m1 * p.k * pow(p.f0, m1);   // a of Eq. powlaws: 1 + a t
+  double c = 0.0, d1 = 0.0, fd = 0.0, fdd = 0.0, fddd = 0.0;
+  if (acoef != 0.0) {
+    const double L = log1p(acoef * t);
+    const double F = p.n == 2.0 ? (p.f0 / acoef) * L
+                                : p.f0 * m1 / ((p.n - 2.0) * acoef) * expm1((p.n - 2.0) / m1 * L);
+    c = F - p.f0 * t;
+    const double f = p.f0 * exp(-L / m1);             // Eq. powlaws
+    d1 = p.f0 * expm1(-L / m1);                       // f - f0 without cancellation
+    const double g = p.k * pow(f, m1);                // k f^(n-1): fdot = -g f (Eq. diff_powlaws)
+    fd = -g * f;
+    fdd = p.n * g * g * f;
+    fddd = -p.n * (2.0 * p.n - 1.0) * g * g * g * f;
+  }
+  HetAnchor h;
+  h.C = frac64(c);
+  h.Q = frac64(d1 / p.fs);
+  const double i1 = 1.0 / p.fs;
+  h.e2 = (float)(0.5 * fd * i1 * i1);
+  h.e3 = (float)(fdd / 6.0 * i1 * i1 * i1);
+  h.e4 = (float)(fddd / 24.0 * i1 * i1 * i1 * i1);
+  h.pad = 0.f;
+  out[a] = h;
+}
+
+// z = h exp(-2 pi j c) for one sample m samples after its anchor.
+__device__ __forceinline__ float2 het_sample(float h, const HetAnchor& A, int m) {
+  const float mf = (float)m;
+  const float small = mf * mf * (A.e2 + mf * (A.e3 + mf * A.e4));      // |small| < 1/8 (host)
+  const long long sf = __float2ll_rn(small * 0x1p62f);
+  const unsigned long long ph = A.C + (unsigned long long)m * A.Q + ((unsigned long long)sf << 2);
+  const int top = (int)(ph >> 32);                                      // cycles in [-1/2, 1/2)
+  float sn, cs;
+  sincospif((float)top * 0x1p-31f, &sn, &cs);
+  return make_float2(h * cs, -h * sn);
+}
+
+// Four samples per thread: float4 in, two float4 out (16-byte aligned buffers); a ragged tail is
+// taken sample by sample.
+__global__ void k_heterodyne(const float* __restrict__ h, int64_t n,
+                             const HetAnchor* __restrict__ anchors, float2* __restrict__ out,
+                             bool vec) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q * 4 < n; q += stride) {
+    const int64_t s0 = q * 4;
+    const HetAnchor A = anchors[s0 >> kAnchorLog2];
+    const int m0 = (int)(s0 & (kAnchor - 1));
+    if (vec && s0 + 4 <= n) {
+      const float4 v = __ldcs(reinterpret_cast<const float4*>(h + s0));
+      const float2 z0 = het_sample(v.x, A, m0), z1 = het_sample(v.y, A, m0 + 1);
+      const float2 z2 = het_sample(v.z, A, m0 + 2), z3 = het_sample(v.w, A, m0 + 3);
+      float4* o = reinterpret_cast<float4*>(out + s0);
+      __stcs(o, make_float4(z0.x, z0.y, z1.x, z1.y));
+      __stcs(o + 1, make_float4(z2.x, z2.y, z3.x, z3.y));
+    } else {
+      for (int j = 0; j < 4 && s0 + j < n; ++j) out[s0 + j] = het_sample(h[s0 + j], A, m0 + j);
+    }
+  }
+}
+
+// Projection of bin-shifted peaks: one shared-memory histogram per block, then one global atomic
+// per non-zero bin.  Every fp64 step is an explicitly rounded intrinsic (no contraction), so the
+// shift equals the plain IEEE evaluation floor(fdot t_i / df + 1/2).
+__global__ void k_project(const uint32_t* __restrict__ fft_idx, const uint32_t* __restrict__ bins,
+                          int64_t n, double t_first, double t_hop, double df, double fdot,
+                          int bin_lo, int n_bins, int32_t* __restrict__ counts) {
+  extern __shared__ int hist[];
+  for (int i = threadIdx.x; i < n_bins; i += blockDim.x) hist[i] = 0;
+  __syncthreads();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
+    const double t = __dadd_rn(t_first, __dmul_rn((double)fft_idx[p], t_hop));
+    const double x = __dadd_rn(__ddiv_rn(__dmul_rn(fdot, t), df), 0.5);
+    const long long j = (long long)bins[p] - (long long)floor(x) - bin_lo;
+    if (j >= 0 && j < n_bins) atomicAdd(&hist[j], 1);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n_bins; i += blockDim.x)
+    if (hist[i]) atomicAdd(&counts[i], hist[i]);
+}
+
+}  // namespace
+
+extern "C" int gfh_heterodyne(gfh_ctx* ctx, const float* d_h, int64_t n_samples, double fs,
+                              double t_start, double f0, double k, double n, float* d_out) {
+  if (!ctx || n_samples < 0 || (n_samples > 0 && (!d_h || !d_out)) || !(fs > 0.0) ||
+      !std::isfinite(fs) || !std::isfinite(t_start) || t_start < 0.0 || !(f0 > 0.0) ||
+      !std::isfinite(f0) || !(k >= 0.0) || !std::isfinite(k) || !(n > 1.0) || !std::isfinite(n))
+    return GFH_ERR_ARG;
+  if (n_samples == 0) return GFH_OK;
+  // |fdot| and its derivatives are largest at the start (f falls with t): the quadratic..quartic
+  // terms over one anchor span stay below 1/8 cycle, and the first neglected (quintic) term below
+  // 1e-9 cycle.  Larger spin-downs call for a shorter anchor span than this kernel takes.
+  {
+    const double m1 = n - 1.0;
+    const double f = f0 / std::pow(1.0 + m1 * k * std::pow(f0, m1) * t_start, 1.0 / m1);
+    const double g = k * std::pow(f, m1);
+    const double tau = (double)kAnchor / fs;
+    const double t2 = 0.5 * g * f * tau * tau;
+    const double t3 = n * g * g * f / 6.0 * tau * tau * tau;
+    const double t4 = n * (2.0 * n - 1.0) * g * g * g * f / 24.0 * tau * tau * tau * tau;
+    const double t5 = n * (2.0 * n - 1.0) * (3.0 * n - 2.0) * g * g * g * g * f / 120.0 *
+                      tau * tau * tau * tau * tau;
+    if (!(t2 + t3 + t4 < 0.125) || !(t5 < 1e-9)) return GFH_ERR_ARG;
+  }
+  GFH_CUDA_TRY(cudaSetDevice(ctx->device));
+  const int64_t n_anchor = (n_samples + kAnchor - 1) / kAnchor;
+  int rc = ensure_scratch(ctx, (size_t)n_anchor * sizeof(HetAnchor));
+  if (rc) return rc;
+  HetAnchor* anchors = (HetAnchor*)ctx->pm_buf;
+  cudaStream_t st = ctx->stream;
+  k_het_anchor<<<(unsigned)((n_anchor + 127) / 128), 128, 0, st>>>(HetParams{fs, t_start, f0, k, n},
+                                                                   n_anchor, anchors);
+  GFH_CUDA_TRY(cudaGetLastError());
+  const bool vec = ((uintptr_t)d_h % 16 == 0) && ((uintptr_t)d_out % 16 == 0);
+  const int64_t quads = (n_samples + 3) / 4;
+  const int64_t blocks = std::min<int64_t>((quads + 255) / 256, (int64_t)ctx->num_sms * 8);
+  k_heterodyne<<<(unsigned)blocks, 256, 0, st>>>(d_h, n_samples, anchors, (float2*)d_out, vec);
+  GFH_CUDA_TRY(cudaGetLastError());
+  return GFH_OK;
+}
+
+extern "C" int gfh_project_peaks(gfh_ctx* ctx, const uint32_t* d_fft_idx, const uint32_t* d_bin,
+                                 int64_t n_peaks, double t_first, double t_hop, double df,
+                                 double fdot, int32_t bin_lo, int32_t bin_hi, int32_t* d_counts) {
+  if (!ctx || n_peaks < 0 || (n_peaks > 0 && (!d_fft_idx || !d_bin)) || !d_counts ||
+      bin_hi < bin_lo || !(df > 0.0) || !std::isfinite(t_first) || !std::isfinite(t_hop) ||
+      !std::isfinite(fdot))
+    return GFH_ERR_ARG;
+  const int64_t nb = (int64_t)bin_hi - bin_lo + 1;
+  if (nb > 12288) return GFH_ERR_SIZE;   // one shared-memory histogram per block (48 KB)
+  GFH_CUDA_TRY(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  GFH_CUDA_TRY(cudaMemsetAsync(d_counts, 0, (size_t)nb * sizeof(int32_t), st));
+  if (n_peaks == 0) return GFH_OK;
+  const int64_t blocks = std::min<int64_t>((n_peaks + 255) / 256, (int64_t)ctx->num_sms * 4);
+  k_project<<<(unsigned)blocks, 256, (size_t)nb * sizeof(int), st>>>(
+      d_fft_idx, d_bin, n_peaks, t_first, t_hop, df, fdot, bin_lo, (int)nb, d_counts);
+  GFH_CUDA_TRY(cudaGetLastError());
+  return GFH_OK;
+}

@@ -194,6 +194,7 @@ extern "C" int gfh_destroy(gfh_ctx* c) {
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->fft_valid) cufftDestroy(c->fft_plan);
+  if (c->cfft_valid) cufftDestroy(c->cfft_plan);
   if (c->pm_buf) cudaFree(c->pm_buf);
   if (c->d_flag) cudaFree(c->d_flag);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
@@ -206,6 +207,7 @@ extern "C" int gfh_set_stream(gfh_ctx* c, void* stream) {
   if (!c) return GFH_ERR_ARG;
   c->stream = (cudaStream_t)stream;
   if (c->fft_valid && cufftSetStream(c->fft_plan, c->stream) != CUFFT_SUCCESS) return GFH_ERR_CUDA;
+  if (c->cfft_valid && cufftSetStream(c->cfft_plan, c->stream) != CUFFT_SUCCESS) return GFH_ERR_CUDA;
   return GFH_OK;
 }
 

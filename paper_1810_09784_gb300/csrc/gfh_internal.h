@@ -62,6 +62,10 @@ struct gfh_ctx {
   cufftHandle fft_plan = 0;
   bool fft_valid = false;
   int fft_n = 0, fft_hop = 0, fft_batch = 0;
+  // complex-to-complex plan of the heterodyned series (follow-up peakmaps)
+  cufftHandle cfft_plan = 0;
+  bool cfft_valid = false;
+  int cfft_n = 0, cfft_batch = 0;
   // pinned host word for returning counts
   long long* h_pinned = nullptr;
   // bf16 bits of float(log(1 + c)) for c < kLogTable (image channel 0), built on the host

@@ -374,6 +374,54 @@ extern "C" int gfh_peakmap_async(gfh_ctx* ctx, const float* d_series, int64_t n_
                       cap, nullptr, d_n_peaks);
 }
 
+// Peakmap of a complex series (the heterodyned series of the follow-up, Sec. V): complex-to-complex
+// FFTs of the same interlaced boxcar frames, then the equaliser and peak test of the real path.
+extern "C" int gfh_peakmap_complex(gfh_ctx* ctx, const float* d_z, int64_t n_samples, double fs,
+                                   double t_fft, int32_t bin_lo, int32_t bin_hi, double theta,
+                                   uint32_t* d_fft_idx, uint32_t* d_bin, int64_t cap,
+                                   int64_t* h_n_peaks) {
+  if (!ctx || !d_z || !h_n_peaks || cap < 0 || (cap > 0 && (!d_fft_idx || !d_bin)) ||
+      !(fs > 0.0) || !(t_fft > 0.0))
+    return GFH_ERR_ARG;
+  const double nd = fs * t_fft;
+  if (!(nd >= 4.0) || nd > 1.0e8) return GFH_ERR_ARG;
+  const int N = (int)(nd + 0.5);
+  if (N % 2) return GFH_ERR_ARG;
+  const int hop = N / 2;
+  if (n_samples < N) return GFH_ERR_ARG;
+  const int64_t nf64 = (n_samples - N) / hop + 1;
+  if (nf64 > 0x7fffffff) return GFH_ERR_SIZE;
+  const int n_fft = (int)nf64;
+  if (!band_ok(n_fft, bin_lo, bin_hi) || bin_hi + 1 > N - 1) return GFH_ERR_ARG;
+  GFH_CUDA_TRY(cudaSetDevice(ctx->device));
+  if (!ctx->cfft_valid || ctx->cfft_n != N || ctx->cfft_batch != n_fft) {
+    if (ctx->cfft_valid) { cufftDestroy(ctx->cfft_plan); ctx->cfft_valid = false; }
+    int n[1] = {N};
+    int inembed[1] = {N};
+    int onembed[1] = {N};
+    if (cufftPlanMany(&ctx->cfft_plan, 1, n, inembed, 1, hop, onembed, 1, N, CUFFT_C2C, n_fft) !=
+        CUFFT_SUCCESS)
+      return GFH_ERR_CUDA;
+    ctx->cfft_valid = true;
+    ctx->cfft_n = N;
+    ctx->cfft_batch = n_fft;
+  }
+  if (cufftSetStream(ctx->cfft_plan, ctx->stream) != CUFFT_SUCCESS) return GFH_ERR_CUDA;
+  const size_t spec_bytes = (size_t)n_fft * N * sizeof(float2);
+  const int n_words = (n_fft + 31) / 32;
+  const size_t need = align256(spec_bytes) +
+                      align256((size_t)(bin_hi - bin_lo + 1) * n_words * 4) +
+                      align256(((size_t)(bin_hi - bin_lo + 2)) * 8);
+  int rc = ensure_scratch(ctx, need);
+  if (rc) return rc;
+  float2* spec = (float2*)ctx->pm_buf;
+  if (cufftExecC2C(ctx->cfft_plan, (cufftComplex*)const_cast<float*>(d_z), (cufftComplex*)spec,
+                   CUFFT_FORWARD) != CUFFT_SUCCESS)
+    return GFH_ERR_CUDA;
+  return run_peaks(ctx, ComplexIn{spec, N}, n_fft, bin_lo, bin_hi, theta, d_fft_idx, d_bin, cap,
+                   h_n_peaks, spec_bytes);
+}
+
 // ---- statistical peakmaps (training and evaluation data of the tile proposer) -------------------
 
 namespace {

@@ -37,6 +37,7 @@ EXPORTED = [
     "gfh_cnn_set_params", "gfh_cnn_forward", "gfh_cnn_gradients", "gfh_cnn_train_step",
     "gfh_propose_tiles", "gfh_conv3x3", "gfh_select_squares", "gfh_coincide",
     "gfh_n_grid", "gfh_k_segments", "gfh_wait_check",
+    "gfh_heterodyne", "gfh_peakmap_complex", "gfh_project_peaks",
 ]
 N_CLASSES = 4097        # 64 x 64 coarse tiles + no signal
 IMG = 256
@@ -145,6 +146,9 @@ def lib() -> ctypes.CDLL:
             "gfh_n_grid": [dbl, dbl, dbl, dbl, dbl, dbl, dbl, i32, vp, P(i32)],
             "gfh_wait_check": [vp, i64],
             "gfh_k_segments": [dbl, dbl, dbl, dbl, dbl, dbl, dbl, i32, i32, vp, P(i32)],
+            "gfh_heterodyne": [vp, vp, i64, dbl, dbl, dbl, dbl, dbl, vp],
+            "gfh_peakmap_complex": [vp, vp, i64, dbl, dbl, i32, i32, dbl, vp, vp, i64, P(i64)],
+            "gfh_project_peaks": [vp, vp, vp, i64, dbl, dbl, dbl, dbl, i32, i32, vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -320,6 +324,33 @@ class Context:
                                ctypes.byref(n))
         _ok(rc, "gfh_peakmap")
         return n.value
+
+    # ---- follow-up of a candidate (Sec. V)
+    def heterodyne(self, series, fs: float, t_start: float, f0: float, k: float, n: float,
+                   out) -> None:
+        """gfh_heterodyne: out (complex64, as many samples as series) = series corrected by the
+        spin-down phase of (f0, k, n)."""
+        if out.numel() * out.element_size() < 8 * series.numel():
+            raise ValueError("output smaller than the series")
+        _ok(lib().gfh_heterodyne(self._h, _ptr(series), series.numel(), fs, t_start, f0, k, n,
+                                 _ptr(out)), "gfh_heterodyne")
+
+    def peakmap_complex(self, z, fs: float, t_fft: float, bin_lo: int, bin_hi: int, theta: float,
+                        fft_out, bin_out) -> int:
+        """gfh_peakmap_complex on a complex64 series z; returns the number of peaks."""
+        n = ctypes.c_int64()
+        n_samples = z.numel() * z.element_size() // 8
+        rc = lib().gfh_peakmap_complex(self._h, _ptr(z), n_samples, fs, t_fft, bin_lo, bin_hi,
+                                       theta, _ptr(fft_out), _ptr(bin_out), fft_out.numel(),
+                                       ctypes.byref(n))
+        _ok(rc, "gfh_peakmap_complex")
+        return n.value
+
+    def project_peaks(self, fft_idx, bins, n_peaks: int, t_first: float, t_hop: float, df: float,
+                      fdot: float, bin_lo: int, bin_hi: int, counts) -> None:
+        """gfh_project_peaks: counts (int32, bin_hi - bin_lo + 1) of the bin-shifted peaks."""
+        _ok(lib().gfh_project_peaks(self._h, _ptr(fft_idx), _ptr(bins), n_peaks, t_first, t_hop,
+                                    df, fdot, bin_lo, bin_hi, _ptr(counts)), "gfh_project_peaks")
 
     def peakmap_async(self, series, fs: float, t_fft: float, bin_lo: int, bin_hi: int,
                       theta: float, fft_out, bin_out, n_out) -> None:

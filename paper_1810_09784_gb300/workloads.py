@@ -14,6 +14,9 @@ the library's planner.  t0 is the start of the data and FFT i is stamped at its 
   paper_grids     the plain_small peakmap on the paper's own grids: braking indices of
                   Eq. dn_powlaws over n = 2.5 .. 7 and, for each, the Eq. dkeqn k grid (|fdot|
                   1e-4 .. 1e-2 Hz/s) as uniform segments, one map per (n, segment).
+  followup        Sec. V follow-up of each plain_paper injection (or of plain_small's): heterodyne
+                  by the candidate's (f0, k, n), FFTs twice as long, original FrequencyHough in
+                  f0 +- 5 Hz over 32 fdot rows, projection.
 """
 from __future__ import annotations
 
@@ -144,6 +147,28 @@ def paper_grids(seed: int = 1, fdot=(1e-4, 1e-2), n_range=(2.5, 7.0), growth: fl
             grids.append(dict(base[0], n=float(n), k_min=float(sg["k_min"]), dk=float(sg["dk"]),
                               n_k=int(sg["n_k"])))
     return spec, pm, grids
+
+
+# ---- followup ----------------------------------------------------------------------------------
+
+def followup_fields(inj, t_obs: float, t_fft: float, half_band: float = 5.0, n_k: int = 32,
+                    t_first=None) -> tuple:
+    """Sec. V follow-up of an injection: the series corrected by (f0, k, n) is searched with FFTs of
+    length t_fft in f0 +- half_band by the original FrequencyHough (n = 0) over n_k fdot rows
+    centred on 0 (the residual spin-down of a correction off by about one bin).  Returns the
+    peakmap band (bin_lo, bin_hi) and the n = 0 grid request."""
+    df = 1.0 / t_fft
+    N_hop = t_fft / 2.0
+    n_fft = int((t_obs - t_fft) // N_hop) + 1
+    bin_lo = int(math.floor((inj.f0 - half_band) / df))
+    bin_hi = int(math.ceil((inj.f0 + half_band) / df))
+    dk = df / t_obs
+    fields = dict(n=0.0, df=df, bin_lo=bin_lo, bin_hi=bin_hi, n_fft=n_fft,
+                  t_first=t_fft / 2.0 if t_first is None else t_first, t_hop=N_hop, t_obs=t_obs,
+                  n_k=n_k, k_min=-(n_k // 2) * dk, dk=dk, f_max=0.0,
+                  ana_lo=inj.f0 - half_band + 1.0, ana_hi=inj.f0 + half_band - 1.0,
+                  band_hz=2.0 * half_band, list=0)
+    return (bin_lo, bin_hi), fields
 
 
 # ---- uneven ------------------------------------------------------------------------------------

@@ -33,6 +33,11 @@ def test_null_handles_are_rejected(built_lib):
     assert L.gfh_select_squares(None, None, ctypes.byref(g), 5, 5, 3, None, None) == E
     assert L.gfh_coincide(None, None, 0, None, 0, 1.0, 1.0, 3.0, None, None) == E
     assert L.gfh_wait_check(None, 10) == E
+    assert L.gfh_heterodyne(None, None, 10, 4096.0, 0.0, 300.0, 1e-12, 5.0, None) == E
+    n = ctypes.c_int64()
+    assert L.gfh_peakmap_complex(None, None, 4096, 1024.0, 2.0, 200, 300, 2.5, None, None, 0,
+                                 ctypes.byref(n)) == E
+    assert L.gfh_project_peaks(None, None, None, 0, 1.0, 2.0, 0.5, 0.0, 10, 20, None) == E
 
 
 def test_grid_generators_reject_invalid_requests(built_lib):
