@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--impl", default="gfh", choices=["gfh", "reference"])
     ap.add_argument("--workload", default="plain_paper",
                     choices=["plain_paper", "plain_small", "batched_n", "paper_grids", "uneven",
-                             "proposer", "followup"])
+                             "proposer", "followup", "splice"])
     ap.add_argument("--no-graph", action="store_true",
                     help="time direct calls only (default: the step is also replayed as a CUDA graph)")
     ap.add_argument("--tile", default=None, help="rows,cols,threads of the Hough tiles")
@@ -227,6 +227,8 @@ def run_reference(args):
         return reference_proposer(args)
     if args.workload == "followup":
         return reference_followup(args)
+    if args.workload == "splice":
+        return reference_splice(args)
     spec, pm, grids = workload(args.workload, 0)
     x = spec.series()
     vals, times = [], []
@@ -997,6 +999,225 @@ def run_followup(args):
     ctx.close()
 
 
+# ---------------------------------------------------------------------------------------------
+# Longer FFTs for later times (Sec. VI.D)
+# ---------------------------------------------------------------------------------------------
+
+def splice_setup(spec):
+    """The plain_paper series split by the Sec. VI.D planner for the family n = 5, f0 <= 2000 Hz,
+    |fdot0| <= 1/(2 s)^2, starting from 2 s FFTs (three levels): each portion searched in the 19
+    sub-band maps of plain_paper above 100 Hz (100 Hz analysis bands + 50 Hz extension, 2000 k
+    rows)."""
+    from paper_1810_09784_gb300 import gfh, splice
+    portions = gfh.tfft_portions(5.0, 2000.0, 0.25, 2.0, spec.t_obs, 3)
+    bands = []
+    a = 100.0             # the equaliser's 128-bin warm-up needs bin_lo >= 130 at 2 s FFTs
+    while a < 2000.0 - 1e-9:
+        bands.append((a, min(a + 100.0, 2000.0)))
+        a += 100.0
+    plan = splice.portion_plan(portions, spec.fs, spec.n_samples, 5.0, bands, 2000, ext=50.0)
+    for P in plan:        # the extension stops at the band's top, as in plain_paper
+        for f in P.fields:
+            f["bin_hi"] = min(f["bin_hi"], int(round(2000.0 * P.t_fft)) - 1)
+    return plan
+
+
+def reference_splice(args):
+    from oracle import gfh_oracle as O
+    spec, _, _ = workloads.plain_paper(seed=2)
+    x = spec.series()
+    plan = splice_setup(spec)
+    vals, times = [], []
+    for i in range(args.warmup + args.steps):
+        t_step, updates = 0.0, 0
+        for P in plan:
+            lo = min(f["bin_lo"] for f in P.fields)
+            hi = max(f["bin_hi"] for f in P.fields)
+            t0 = time.perf_counter()
+            fi, bj = O.peakmap(x[P.s_begin:P.s_end], spec.fs, P.t_fft, lo, hi)
+            t_step += time.perf_counter() - t0
+            for f in P.fields:
+                og = O.make_grid(O.Grid(**{k: v for k, v in f.items() if k != "list"}))
+                sel = (bj >= og.bin_lo) & (bj <= og.bin_hi)
+                updates += int(sel.sum()) * og.n_k
+                t1 = time.perf_counter()
+                O.hough_row(og, fi, bj, og.n_k // 2)
+                t_step += (time.perf_counter() - t1) * og.n_k
+        if i >= args.warmup:
+            vals.append(updates / t_step)
+            times.append(t_step)
+    value = float(np.mean(vals))
+    sample = ("oracle peakmaps of every portion + one k row of each map, extrapolated to all rows; "
+              "numpy, 1 thread")
+    print(json.dumps({"impl": "reference", "metric": "Hough updates/s (peaks x k-bins)",
+                      "value": value, "unit": "updates/s", "n_gpus": args.gpus,
+                      "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None,
+                      "dtype": "int32 counts, fp32 spectra, fp64 grid", "data": "synthetic",
+                      "config": {"workload": "splice (CPU oracle)"},
+                      "cpu_baseline": {"value": value, "unit": "updates/s", "cores": 1,
+                                       "kind": "oracle", "sample": sample},
+                      "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0,
+                              "d2h_bytes_per_step": 0}}), flush=True)
+
+
+def run_splice(args):
+    """Sec. VI.D on the plain_paper series: one step = every portion's peakmap (its own FFT length,
+    on its samples) and its 20 sub-band maps with candidates, then the coincidences of each
+    sub-band's candidates between consecutive portions."""
+    import torch
+
+    from paper_1810_09784_gb300 import build as _build
+    from paper_1810_09784_gb300 import gfh, splice
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    _build.build()
+    stream = torch.cuda.Stream()
+    ctx = gfh.Context(local, stream)
+    spec, _, _ = workloads.plain_paper(seed=ranks.rank_seed(2, rank))
+    series_np = spec.series()
+    x_host = torch.from_numpy(series_np).pin_memory()
+    x_dev = x_host.cuda()
+    plan = splice_setup(spec)
+    parts = []
+    for P in plan:
+        grids = [gfh.grid_make(gfh.Grid(**f)) for f in P.fields]
+        maps = [torch.empty((g.n_k, g.ld_x0), dtype=torch.int32, device="cuda") for g in grids]
+        cands = [torch.empty(g.n_bands * gfh.CANDIDATE_BYTES, dtype=torch.uint8, device="cuda")
+                 for g in grids]
+        hp = gfh.Plan(ctx, grids, maps, cands, None, tile=(8, 3072, 512))
+        lo = min(f["bin_lo"] for f in P.fields)
+        hi = max(f["bin_hi"] for f in P.fields)
+        n_fft = P.fields[0]["n_fft"]
+        cap = int(n_fft * (hi - lo + 1) * 0.12) + 1024
+        fo = torch.empty(cap, dtype=torch.int32, device="cuda")
+        bo = torch.empty(cap, dtype=torch.int32, device="cuda")
+        off = torch.zeros(2, dtype=torch.int64, device="cuda")
+        parts.append(dict(P=P, grids=grids, maps=maps, cands=cands, plan=hp, lo=lo, hi=hi, fo=fo,
+                          bo=bo, off=off))
+    n_bands_total = [sum(g.n_bands for g in p["grids"]) for p in parts]
+    match = torch.empty(max(n_bands_total), dtype=torch.int32, device="cuda")
+    dist_t = torch.empty(max(n_bands_total), dtype=torch.float64, device="cuda")
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def step(h2d=False, hough_events=None):
+        if h2d:
+            x_dev.copy_(x_host, non_blocking=True)
+        for q, p in enumerate(parts):
+            P = p["P"]
+            n = ctx.peakmap_async(x_dev[P.s_begin:P.s_end], spec.fs, P.t_fft, p["lo"], p["hi"],
+                                  2.5, p["fo"], p["bo"], p["off"][1:2])
+            if hough_events is not None:
+                hough_events[q][0].record(stream)
+            p["plan"].execute(p["fo"], p["bo"], p["off"], 1)
+            if hough_events is not None:
+                hough_events[q][1].record(stream)
+        for pa, pb in zip(parts, parts[1:]):
+            for ga, ca, gb, cb in zip(pa["grids"], pa["cands"], pb["grids"], pb["cands"]):
+                ctx.coincide(ca, ga.n_bands, cb, gb.n_bands, max(ga.dx0, gb.dx0),
+                             max(ga.dk, gb.dk), 3.0, match, dist_t)
+        if h2d:
+            for p in parts:
+                for c in p["cands"]:
+                    c.cpu()
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        if ctx.check() != gfh.GFH_OK:
+            raise RuntimeError("input check failed")
+    updates = 0
+    for p in parts:
+        n = int(p["off"][1].item())
+        updates += splice.update_count(p["grids"], p["bo"][:n].cpu().numpy())
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    with sampler, torch.cuda.stream(stream):
+        barrier()
+        a, b = ev(), ev()
+        hev = [[(ev(), ev()) for _ in parts] for _ in range(args.steps)]
+        a.record(stream)
+        for i in range(args.steps):
+            step(hough_events=hev[i])
+        b.record(stream)
+        barrier()
+        ms = a.elapsed_time(b) / args.steps
+    clocks = sampler.summary()
+    ms_hough = sum(e0.elapsed_time(e1) for st in hev for e0, e1 in st) / args.steps
+    ms_max, total = ranks.combine(ms, float(updates), device="cuda")
+    value = total / (ms_max * 1e-3)
+    with torch.cuda.stream(stream):
+        barrier()
+        a.record(stream)
+        for _ in range(args.steps):
+            step(h2d=True)
+        b.record(stream)
+        barrier()
+        ms_e2e = a.elapsed_time(b) / args.steps
+    # coincidences of the injections between the two portions (top candidate of each band)
+    coinc = None
+    if len(parts) >= 2:
+        pa, pb = parts[0], parts[1]
+        hits, tot = 0, 0
+        for ga, ca, gb, cb in zip(pa["grids"], pa["cands"], pb["grids"], pb["cands"]):
+            m_, d_ = splice.coincide(ctx, ca, ga, cb, gb)
+            ra = gfh.candidates_to_numpy(ca)
+            m_ = m_.cpu().numpy()
+            strong = ra["cr"] > 6.0
+            tot += int(strong.sum())
+            hits += int((strong & (m_ >= 0)).sum())
+        coinc = {"strong_candidates_first_portion": tot, "with_a_coincidence_in_the_second": hits}
+    if rank != 0:
+        ctx.close()
+        return
+    atomics = 2.0 * updates
+    achieved = atomics / (ms_hough * 1e-3) / 1e9
+    line = {
+        "metric": "Hough updates/s (peaks x k-bins)", "value": value, "unit": "updates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32 counts, fp32 spectra, fp64 grid", "data": "synthetic",
+        "config": {"workload": "splice: the plain_paper series in Sec. VI.D portions (n = 5, f0 <= 2000 Hz, "
+                               "|fdot0| <= 0.25 Hz/s, T_FFT 2 s then 4 s), 19 sub-band maps (100-2000 Hz) "
+                               "of 2000 k rows per portion, coincidences between the portions",
+                   "portions": [[p["P"].t_fft, p["P"].s_begin / spec.fs, p["P"].s_end / spec.fs]
+                                for p in parts],
+                   "maps": sum(len(p["grids"]) for p in parts), "updates_per_step": updates,
+                   "tile": [8, 3072, 512],
+                   "l2": "inputs larger than L2 (series 165 MB, maps %d MB per step)"
+                         % (sum(g.n_k * g.ld_x0 * 4 for p in parts for g in p["grids"]) // 1000000),
+                   "timing": "direct calls"},
+        "breakdown_ms": {"step": ms, "hough_select": ms_hough, "rest": ms - ms_hough},
+        "roofline": {"bound": "smem_atomic", "kernel": "k_hough", "achieved": achieved,
+                     "peak": SMEM_ATOMIC_PEAK, "unit": "Gatomic/s", "frac": achieved / SMEM_ATOMIC_PEAK,
+                     "peak_source": "derived: 152 SMs x 16 shared atomics/clk x max SM clock",
+                     "algorithmic": "2 shared atomics per update (differential +1/-1)", "traffic": None},
+        "coincidences": coinc,
+        "e2e": {"value": total / (ms_e2e * 1e-3), "unit": "updates/s",
+                "h2d_bytes_per_step": series_np.size * 4,
+                "d2h_bytes_per_step": sum(c.numel() for p in parts for c in p["cands"]),
+                "ms_per_step": ms_e2e},
+        "gpu_launches": (len(parts) * 9 + len(parts[0]["grids"]) * (len(parts) - 1)) * args.steps,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    for p in parts:
+        p["plan"].close()
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -1007,6 +1228,8 @@ def main():
         run_proposer(args)
     elif args.workload == "followup":
         run_followup(args)
+    elif args.workload == "splice":
+        run_splice(args)
     else:
         run_gpu(args)
 

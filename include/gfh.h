@@ -204,6 +204,31 @@ int gfh_k_segments(double n, double df, double f_min, double f_max, double fdot_
                    double growth, int32_t max_rows, int32_t cap, gfh_k_segment* h_out,
                    int32_t* n_out);
 
+/*
+ * Longer FFTs for later times (Sec. VI.D): the data from t0 to t_obs are split into portions
+ * analysed with T_FFT = 2^L t_fft0, L = 0 .. max_levels-1.  With T_FFT a signal stays within one
+ * frequency bin while |fdot| <= 1/T_FFT^2 (Eq. dot_tfft); once the spin-down has fallen by a factor
+ * 4, T_FFT can double.  The spin-down is the largest any power law of braking index n with
+ * f0 <= f_hi and |fdot0| <= fdot_hi can have at time t (Eq. powlaws): the fastest member's
+ * fdot_hi (1 + (n-1) fdot_hi t / f_hi)^(-n/(n-1)) while t fdot_hi < f_hi, f_hi n^(-n/(n-1)) / t after
+ * that (a slower member overtakes it).  Portion L spans [t_L, t_(L+1)) with t_L the first time that
+ * bound falls to 1/T_L^2 (the last level runs to t_obs; times clipped to t_obs); levels whose span is
+ * shorter than one T_FFT are left out, and data before the first portion (spin-down above
+ * 1/t_fft0^2) is not analysed.  Every portion is searched with its own peakmap and maps on the common
+ * t0 (grid t_first = portion start + T_FFT/2), so one signal has the same (x0, k) in all portions
+ * and candidates of consecutive portions are compared with gfh_coincide (Sec. VI.D: coincidences
+ * between the portions).  Host only.  GFH_ERR_SIZE when more than cap portions result.
+ */
+typedef struct gfh_portion {
+  int32_t level;
+  int32_t reserved;
+  double t_begin;   /* [s from t0] */
+  double t_end;
+  double t_fft;
+} gfh_portion;
+int gfh_tfft_portions(double n, double f_hi, double fdot_hi, double t_fft0, double t_obs,
+                      int32_t max_levels, int32_t cap, gfh_portion* h_out, int32_t* n_out);
+
 /* ---- GPU entry points ----------------------------------------------------------------------- */
 
 /*

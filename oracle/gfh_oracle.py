@@ -623,3 +623,51 @@ def projection_cr(counts, j: int):
     mu = float(rest.mean())
     sigma = float(rest.std())
     return (float(c[j]) - mu) / sigma if sigma > 0.0 else 0.0
+
+
+# ----------------------------------------------------------------------------------------------
+# Sec. VI.D: longer FFTs for later times (T_FFT splicing)
+# ----------------------------------------------------------------------------------------------
+def max_spindown_at(t, n: float, f_hi: float, fdot_hi: float):
+    """Largest |fdot(t)| over the power laws of braking index n (Eq. powlaws) with f0 <= f_hi and
+    |fdot0| <= fdot_hi.  A member's |fdot(t)| = fdot0 (1 + u)^(-n/(n-1)) with u = (n-1) fdot0 t / f0
+    grows with f0 and, over fdot0, peaks at u = n-1, i.e. fdot0 = f0 / t; so the bound is the
+    fastest member's fdot_hi (1 + (n-1) fdot_hi t / f_hi)^(-n/(n-1)) while f_hi / t > fdot_hi, and
+    f_hi n^(-n/(n-1)) / t after that."""
+    t = np.asarray(t, dtype=np.float64)
+    early = fdot_hi * (1.0 + (n - 1.0) * fdot_hi * t / f_hi) ** (-n / (n - 1.0))
+    with np.errstate(divide="ignore"):
+        late = f_hi * n ** (-n / (n - 1.0)) / t
+    return np.where(t * fdot_hi < f_hi, early, late)
+
+
+def time_of_spindown(fdot: float, n: float, f_hi: float, fdot_hi: float) -> float:
+    """First time at which max_spindown_at falls to fdot (0 when it starts at or below it)."""
+    if fdot_hi <= fdot:
+        return 0.0
+    t1 = ((fdot_hi / fdot) ** ((n - 1.0) / n) - 1.0) * f_hi / ((n - 1.0) * fdot_hi)
+    if t1 * fdot_hi < f_hi:
+        return t1
+    return f_hi * n ** (-n / (n - 1.0)) / fdot
+
+
+def tfft_portions(n: float, f_hi: float, fdot_hi: float, t_fft0: float, t_obs: float,
+                  max_levels: int):
+    """Sec. VI.D: the data from t0 to t_obs split into portions analysed with T_FFT = 2^L t_fft0,
+    L = 0 .. max_levels-1.  Eq. dot_tfft: with T_FFT a signal stays within one bin while
+    |fdot| <= 1/T_FFT^2; once the family's largest spin-down (max_spindown_at) has fallen by 4,
+    T_FFT doubles.  Portion L spans [t_L, t_(L+1)) with t_L = time_of_spindown(1/T_L^2) (the last
+    level runs to t_obs); levels whose span is empty or shorter than one FFT are left out, and the
+    data before t_0 (spin-down above 1/t_fft0^2) is not analysed.  Returns a list of
+    (level, t_begin, t_end, t_fft)."""
+    out = []
+    for L in range(max_levels):
+        T = t_fft0 * 2.0 ** L
+        a = min(time_of_spindown(1.0 / T ** 2, n, f_hi, fdot_hi), t_obs)
+        if L + 1 < max_levels:
+            b = min(time_of_spindown(1.0 / (2.0 * T) ** 2, n, f_hi, fdot_hi), t_obs)
+        else:
+            b = t_obs
+        if b - a >= T:
+            out.append((L, a, b, T))
+    return out

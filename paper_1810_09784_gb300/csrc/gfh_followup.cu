@@ -81,25 +81,30 @@ __device__ __forceinline__ float2 het_sample(float h, const HetAnchor& A, int m)
   return make_float2(h * cs, -h * sn);
 }
 
-// Four samples per thread: float4 in, two float4 out (16-byte aligned buffers); a ragged tail is
-// taken sample by sample.
+// Eight samples per thread: two float4 loads in flight, four float4 stores (16-byte aligned
+// buffers); a ragged tail is taken sample by sample.
 __global__ void k_heterodyne(const float* __restrict__ h, int64_t n,
                              const HetAnchor* __restrict__ anchors, float2* __restrict__ out,
                              bool vec) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q * 4 < n; q += stride) {
-    const int64_t s0 = q * 4;
-    const HetAnchor A = anchors[s0 >> kAnchorLog2];
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q * 8 < n; q += stride) {
+    const int64_t s0 = q * 8;
+    const HetAnchor A = anchors[s0 >> kAnchorLog2];     // 8 samples never straddle an anchor
     const int m0 = (int)(s0 & (kAnchor - 1));
-    if (vec && s0 + 4 <= n) {
-      const float4 v = __ldcs(reinterpret_cast<const float4*>(h + s0));
-      const float2 z0 = het_sample(v.x, A, m0), z1 = het_sample(v.y, A, m0 + 1);
-      const float2 z2 = het_sample(v.z, A, m0 + 2), z3 = het_sample(v.w, A, m0 + 3);
+    if (vec && s0 + 8 <= n) {
+      const float4 v0 = __ldcs(reinterpret_cast<const float4*>(h + s0));
+      const float4 v1 = __ldcs(reinterpret_cast<const float4*>(h + s0 + 4));
       float4* o = reinterpret_cast<float4*>(out + s0);
-      __stcs(o, make_float4(z0.x, z0.y, z1.x, z1.y));
-      __stcs(o + 1, make_float4(z2.x, z2.y, z3.x, z3.y));
+      float2 a = het_sample(v0.x, A, m0), b = het_sample(v0.y, A, m0 + 1);
+      __stcs(o, make_float4(a.x, a.y, b.x, b.y));
+      a = het_sample(v0.z, A, m0 + 2); b = het_sample(v0.w, A, m0 + 3);
+      __stcs(o + 1, make_float4(a.x, a.y, b.x, b.y));
+      a = het_sample(v1.x, A, m0 + 4); b = het_sample(v1.y, A, m0 + 5);
+      __stcs(o + 2, make_float4(a.x, a.y, b.x, b.y));
+      a = het_sample(v1.z, A, m0 + 6); b = het_sample(v1.w, A, m0 + 7);
+      __stcs(o + 3, make_float4(a.x, a.y, b.x, b.y));
     } else {
-      for (int j = 0; j < 4 && s0 + j < n; ++j) out[s0 + j] = het_sample(h[s0 + j], A, m0 + j);
+      for (int j = 0; j < 8 && s0 + j < n; ++j) out[s0 + j] = het_sample(h[s0 + j], A, m0 + j);
     }
   }
 }
@@ -159,8 +164,8 @@ extern "C" int gfh_heterodyne(gfh_ctx* ctx, const float* d_h, int64_t n_samples,
                                                                    n_anchor, anchors);
   GFH_CUDA_TRY(cudaGetLastError());
   const bool vec = ((uintptr_t)d_h % 16 == 0) && ((uintptr_t)d_out % 16 == 0);
-  const int64_t quads = (n_samples + 3) / 4;
-  const int64_t blocks = std::min<int64_t>((quads + 255) / 256, (int64_t)ctx->num_sms * 8);
+  const int64_t octs = (n_samples + 7) / 8;
+  const int64_t blocks = std::min<int64_t>((octs + 255) / 256, (int64_t)ctx->num_sms * 8);
   k_heterodyne<<<(unsigned)blocks, 256, 0, st>>>(d_h, n_samples, anchors, (float2*)d_out, vec);
   GFH_CUDA_TRY(cudaGetLastError());
   return GFH_OK;

@@ -193,8 +193,8 @@ extern "C" int gfh_destroy(gfh_ctx* c) {
   if (!c) return GFH_OK;
   cudaSetDevice(c->device);
   if (c->stream) cudaStreamSynchronize(c->stream);
-  if (c->fft_valid) cufftDestroy(c->fft_plan);
-  if (c->cfft_valid) cufftDestroy(c->cfft_plan);
+  for (auto& f : c->fft)
+    if (f.valid) cufftDestroy(f.h);
   if (c->pm_buf) cudaFree(c->pm_buf);
   if (c->d_flag) cudaFree(c->d_flag);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
@@ -206,8 +206,8 @@ extern "C" int gfh_destroy(gfh_ctx* c) {
 extern "C" int gfh_set_stream(gfh_ctx* c, void* stream) {
   if (!c) return GFH_ERR_ARG;
   c->stream = (cudaStream_t)stream;
-  if (c->fft_valid && cufftSetStream(c->fft_plan, c->stream) != CUFFT_SUCCESS) return GFH_ERR_CUDA;
-  if (c->cfft_valid && cufftSetStream(c->cfft_plan, c->stream) != CUFFT_SUCCESS) return GFH_ERR_CUDA;
+  for (auto& f : c->fft)
+    if (f.valid && cufftSetStream(f.h, c->stream) != CUFFT_SUCCESS) return GFH_ERR_CUDA;
   return GFH_OK;
 }
 
@@ -311,6 +311,53 @@ extern "C" int gfh_k_segments(double n, double df, double f_min, double f_max, d
     ++cnt;
     if (k + (rows - 1) * dk >= k_hi) break;
     k = k + rows * dk;
+  }
+  *n_out = cnt;
+  return GFH_OK;
+}
+
+// ---- Sec. VI.D: longer FFTs for later times ---------------------------------------------------
+
+namespace {
+
+// First time at which the largest |fdot(t)| over the power laws of braking index n with
+// f0 <= f_hi and |fdot0| <= fdot_hi falls to fdot.  A member's |fdot(t)| = fdot0 (1 + u)^(-n/(n-1)),
+// u = (n-1) fdot0 t / f0, peaks over fdot0 at u = n-1: the bound is the fastest member's while
+// t fdot_hi < f_hi and f_hi n^(-n/(n-1)) / t after that.
+double time_of_spindown(double fdot, double n, double f_hi, double fdot_hi) {
+  if (fdot_hi <= fdot) return 0.0;
+  const double t1 = (std::pow(fdot_hi / fdot, (n - 1.0) / n) - 1.0) * f_hi / ((n - 1.0) * fdot_hi);
+  if (t1 * fdot_hi < f_hi) return t1;
+  return f_hi * std::pow(n, -n / (n - 1.0)) / fdot;
+}
+
+}  // namespace
+
+extern "C" int gfh_tfft_portions(double n, double f_hi, double fdot_hi, double t_fft0,
+                                 double t_obs, int32_t max_levels, int32_t cap,
+                                 gfh_portion* h_out, int32_t* n_out) {
+  if (!h_out || !n_out || cap < 1 || !(n > 1.0) || !std::isfinite(n) || !(f_hi > 0.0) ||
+      !(fdot_hi > 0.0) || !(t_fft0 > 0.0) || !(t_obs > 0.0) || max_levels < 1 || max_levels > 30)
+    return GFH_ERR_ARG;
+  int32_t cnt = 0;
+  for (int L = 0; L < max_levels; ++L) {
+    const double T = t_fft0 * std::ldexp(1.0, L);                    // Eq. dot_tfft: fdot <= 1/T^2
+    double a = time_of_spindown(1.0 / (T * T), n, f_hi, fdot_hi);
+    if (a > t_obs) a = t_obs;
+    double b = t_obs;
+    if (L + 1 < max_levels) {
+      b = time_of_spindown(1.0 / ((2.0 * T) * (2.0 * T)), n, f_hi, fdot_hi);
+      if (b > t_obs) b = t_obs;
+    }
+    if (b - a >= T) {
+      if (cnt >= cap) { *n_out = cnt; return GFH_ERR_SIZE; }
+      h_out[cnt].level = L;
+      h_out[cnt].reserved = 0;
+      h_out[cnt].t_begin = a;
+      h_out[cnt].t_end = b;
+      h_out[cnt].t_fft = T;
+      ++cnt;
+    }
   }
   *n_out = cnt;
   return GFH_OK;

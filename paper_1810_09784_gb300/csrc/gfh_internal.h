@@ -59,13 +59,18 @@ struct gfh_ctx {
   // peakmap scratch (library-owned, grows on demand)
   void* pm_buf = nullptr;
   size_t pm_bytes = 0;
-  cufftHandle fft_plan = 0;
-  bool fft_valid = false;
-  int fft_n = 0, fft_hop = 0, fft_batch = 0;
-  // complex-to-complex plan of the heterodyned series (follow-up peakmaps)
-  cufftHandle cfft_plan = 0;
-  bool cfft_valid = false;
-  int cfft_n = 0, cfft_batch = 0;
+  // cuFFT plans of the interlaced frames (R2C for series, C2C for heterodyned series), kept for
+  // the last few shapes so that searches alternating FFT lengths (Sec. VI.D portions) plan once
+  struct FftPlan {
+    cufftHandle h = 0;
+    bool valid = false;
+    bool c2c = false;
+    int n = 0, batch = 0;
+    unsigned long long used = 0;
+  };
+  static constexpr int kFftPlans = 4;
+  FftPlan fft[kFftPlans];
+  unsigned long long fft_clock = 0;
   // pinned host word for returning counts
   long long* h_pinned = nullptr;
   // bf16 bits of float(log(1 + c)) for c < kLogTable (image channel 0), built on the host
@@ -154,6 +159,8 @@ int gfh_host_columns(const gfh_grid* g, std::vector<int32_t>& band, std::vector<
 
 // The context's scratch buffer (gfh_peakmap.cu), grown on demand.
 int ensure_scratch(gfh_ctx* c, size_t bytes);
+// A cuFFT plan of `batch` interlaced frames of N samples (hop N/2) on the context's stream.
+int gfh_fft_plan(gfh_ctx* c, int N, int batch, bool c2c, cufftHandle* out);
 
 // Launchers (gfh_hough.cu).
 int gfh_launch_plan(gfh_plan* plan, const gfh_peaks* peaks);

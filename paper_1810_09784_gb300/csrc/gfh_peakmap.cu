@@ -292,6 +292,40 @@ int ensure_scratch(gfh_ctx* c, size_t bytes) {
   return GFH_OK;
 }
 
+int gfh_fft_plan(gfh_ctx* c, int N, int batch, bool c2c, cufftHandle* out) {
+  gfh_ctx::FftPlan* slot = nullptr;
+  for (auto& f : c->fft)
+    if (f.valid && f.c2c == c2c && f.n == N && f.batch == batch) { slot = &f; break; }
+  if (!slot) {
+    slot = &c->fft[0];                       // a free slot, else the least recently used
+    for (auto& f : c->fft) {
+      if (!f.valid) { slot = &f; break; }
+      if (f.used < slot->used) slot = &f;
+    }
+    if (slot->valid) {
+      if (c->stream) cudaStreamSynchronize(c->stream);
+      cufftDestroy(slot->h);
+      slot->valid = false;
+    }
+    const int hop = N / 2;
+    const int bins = c2c ? N : N / 2 + 1;
+    int n[1] = {N};
+    int inembed[1] = {N};
+    int onembed[1] = {bins};
+    if (cufftPlanMany(&slot->h, 1, n, inembed, 1, hop, onembed, 1, bins,
+                      c2c ? CUFFT_C2C : CUFFT_R2C, batch) != CUFFT_SUCCESS)
+      return GFH_ERR_CUDA;
+    slot->valid = true;
+    slot->c2c = c2c;
+    slot->n = N;
+    slot->batch = batch;
+  }
+  slot->used = ++c->fft_clock;
+  if (cufftSetStream(slot->h, c->stream) != CUFFT_SUCCESS) return GFH_ERR_CUDA;
+  *out = slot->h;
+  return GFH_OK;
+}
+
 extern "C" int gfh_peaks_from_power(gfh_ctx* ctx, const float* d_power, int64_t ld, int32_t n_fft,
                                     int32_t bin_lo, int32_t bin_hi, double theta,
                                     uint32_t* d_fft_idx, uint32_t* d_bin, int64_t cap,
@@ -324,20 +358,9 @@ int peakmap_impl(gfh_ctx* ctx, const float* d_series, int64_t n_samples, double 
   const int nc = N / 2 + 1;
   if (!band_ok(n_fft, bin_lo, bin_hi) || bin_hi + 1 > N / 2) return GFH_ERR_ARG;
   GFH_CUDA_TRY(cudaSetDevice(ctx->device));
-  if (!ctx->fft_valid || ctx->fft_n != N || ctx->fft_hop != hop || ctx->fft_batch != n_fft) {
-    if (ctx->fft_valid) { cufftDestroy(ctx->fft_plan); ctx->fft_valid = false; }
-    int n[1] = {N};
-    int inembed[1] = {N};
-    int onembed[1] = {nc};
-    if (cufftPlanMany(&ctx->fft_plan, 1, n, inembed, 1, hop, onembed, 1, nc, CUFFT_R2C, n_fft) !=
-        CUFFT_SUCCESS)
-      return GFH_ERR_CUDA;
-    ctx->fft_valid = true;
-    ctx->fft_n = N;
-    ctx->fft_hop = hop;
-    ctx->fft_batch = n_fft;
-  }
-  if (cufftSetStream(ctx->fft_plan, ctx->stream) != CUFFT_SUCCESS) return GFH_ERR_CUDA;
+  cufftHandle plan;
+  int rc0 = gfh_fft_plan(ctx, N, n_fft, false, &plan);
+  if (rc0) return rc0;
   // Scratch layout: [complex spectra | peak bit matrix | bin counts]; sized once, up front.
   const size_t spec_bytes = (size_t)n_fft * nc * sizeof(float2);
   const int n_words = (n_fft + 31) / 32;
@@ -347,7 +370,7 @@ int peakmap_impl(gfh_ctx* ctx, const float* d_series, int64_t n_samples, double 
   int rc = ensure_scratch(ctx, need);
   if (rc) return rc;
   float2* spec = (float2*)ctx->pm_buf;
-  if (cufftExecR2C(ctx->fft_plan, const_cast<float*>(d_series), (cufftComplex*)spec) !=
+  if (cufftExecR2C(plan, const_cast<float*>(d_series), (cufftComplex*)spec) !=
       CUFFT_SUCCESS)
     return GFH_ERR_CUDA;
   return run_peaks(ctx, ComplexIn{spec, nc}, n_fft, bin_lo, bin_hi, theta, d_fft_idx, d_bin, cap,
@@ -394,19 +417,9 @@ extern "C" int gfh_peakmap_complex(gfh_ctx* ctx, const float* d_z, int64_t n_sam
   const int n_fft = (int)nf64;
   if (!band_ok(n_fft, bin_lo, bin_hi) || bin_hi + 1 > N - 1) return GFH_ERR_ARG;
   GFH_CUDA_TRY(cudaSetDevice(ctx->device));
-  if (!ctx->cfft_valid || ctx->cfft_n != N || ctx->cfft_batch != n_fft) {
-    if (ctx->cfft_valid) { cufftDestroy(ctx->cfft_plan); ctx->cfft_valid = false; }
-    int n[1] = {N};
-    int inembed[1] = {N};
-    int onembed[1] = {N};
-    if (cufftPlanMany(&ctx->cfft_plan, 1, n, inembed, 1, hop, onembed, 1, N, CUFFT_C2C, n_fft) !=
-        CUFFT_SUCCESS)
-      return GFH_ERR_CUDA;
-    ctx->cfft_valid = true;
-    ctx->cfft_n = N;
-    ctx->cfft_batch = n_fft;
-  }
-  if (cufftSetStream(ctx->cfft_plan, ctx->stream) != CUFFT_SUCCESS) return GFH_ERR_CUDA;
+  cufftHandle plan;
+  int rc0 = gfh_fft_plan(ctx, N, n_fft, true, &plan);
+  if (rc0) return rc0;
   const size_t spec_bytes = (size_t)n_fft * N * sizeof(float2);
   const int n_words = (n_fft + 31) / 32;
   const size_t need = align256(spec_bytes) +
@@ -415,7 +428,7 @@ extern "C" int gfh_peakmap_complex(gfh_ctx* ctx, const float* d_z, int64_t n_sam
   int rc = ensure_scratch(ctx, need);
   if (rc) return rc;
   float2* spec = (float2*)ctx->pm_buf;
-  if (cufftExecC2C(ctx->cfft_plan, (cufftComplex*)const_cast<float*>(d_z), (cufftComplex*)spec,
+  if (cufftExecC2C(plan, (cufftComplex*)const_cast<float*>(d_z), (cufftComplex*)spec,
                    CUFFT_FORWARD) != CUFFT_SUCCESS)
     return GFH_ERR_CUDA;
   return run_peaks(ctx, ComplexIn{spec, N}, n_fft, bin_lo, bin_hi, theta, d_fft_idx, d_bin, cap,

@@ -37,7 +37,7 @@ EXPORTED = [
     "gfh_cnn_set_params", "gfh_cnn_forward", "gfh_cnn_gradients", "gfh_cnn_train_step",
     "gfh_propose_tiles", "gfh_conv3x3", "gfh_select_squares", "gfh_coincide",
     "gfh_n_grid", "gfh_k_segments", "gfh_wait_check",
-    "gfh_heterodyne", "gfh_peakmap_complex", "gfh_project_peaks",
+    "gfh_heterodyne", "gfh_peakmap_complex", "gfh_project_peaks", "gfh_tfft_portions",
 ]
 N_CLASSES = 4097        # 64 x 64 coarse tiles + no signal
 IMG = 256
@@ -149,6 +149,7 @@ def lib() -> ctypes.CDLL:
             "gfh_heterodyne": [vp, vp, i64, dbl, dbl, dbl, dbl, dbl, vp],
             "gfh_peakmap_complex": [vp, vp, i64, dbl, dbl, i32, i32, dbl, vp, vp, i64, P(i64)],
             "gfh_project_peaks": [vp, vp, vp, i64, dbl, dbl, dbl, dbl, i32, i32, vp],
+            "gfh_tfft_portions": [dbl, dbl, dbl, dbl, dbl, i32, i32, vp, P(i32)],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -254,6 +255,20 @@ def k_segments(n: float, df: float, f_min: float, f_max: float, fdot_lo: float, 
     cnt = ctypes.c_int32()
     _ok(lib().gfh_k_segments(n, df, f_min, f_max, fdot_lo, fdot_hi, growth, max_rows, cap,
                              out.ctypes.data, ctypes.byref(cnt)), "gfh_k_segments")
+    return out[: cnt.value].copy()
+
+
+PORTION_DTYPE = np.dtype([("level", "<i4"), ("reserved", "<i4"), ("t_begin", "<f8"),
+                          ("t_end", "<f8"), ("t_fft", "<f8")])
+
+
+def tfft_portions(n: float, f_hi: float, fdot_hi: float, t_fft0: float, t_obs: float,
+                  max_levels: int, cap: int = 64) -> np.ndarray:
+    """gfh_tfft_portions: the Sec. VI.D time portions and their FFT lengths."""
+    out = np.zeros(cap, PORTION_DTYPE)
+    cnt = ctypes.c_int32()
+    _ok(lib().gfh_tfft_portions(n, f_hi, fdot_hi, t_fft0, t_obs, max_levels, cap,
+                                out.ctypes.data, ctypes.byref(cnt)), "gfh_tfft_portions")
     return out[: cnt.value].copy()
 
 
