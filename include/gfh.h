@@ -356,12 +356,13 @@ int gfh_coincide(gfh_ctx* ctx, const gfh_candidate* d_a, int32_t na, const gfh_c
  * frequency half of a real signal monochromatic; the paper writes e^{j phi_sd} in its convention).
  *   d_h     float32 [n_samples] on the device (a 16-byte aligned pointer takes the vector path)
  *   d_out   complex64 [n_samples] as interleaved float32 pairs (re, im), caller-owned
- * Needs n > 1, k >= 0, t_start >= 0, f0 > 0.  Phase accuracy: c is exact in fp64 at anchors every
- * 1024 samples and continued by its Taylor series to fourth order; GFH_ERR_ARG when the spin-down
- * is too fast for that span (second..fourth-order terms above 1/8 cycle or a fifth-order term
- * above 1e-9 cycle over 1024 samples at t_start).  The applied phase is the cycle fraction rounded
- * to 2^-32 and then to float32.  Asynchronous; uses the context's scratch (1024x fewer anchors
- * than samples, 32 bytes each).
+ * Needs n > 1, k >= 0, t_start >= 0, f0 > 0.  Phase accuracy: c is exact in fp64 at anchors and
+ * continued by its Taylor series to fourth order (the linear term exactly on a 2^-64 cycle lattice,
+ * the others in float32); the anchor span is the longest power of two from 2^10 to 2^14 samples
+ * over which the second..fourth-order terms stay below 1/8 cycle and the fifth-order term below
+ * 1e-9 cycle at t_start (where the spin-down is fastest); GFH_ERR_ARG when even 2^10 samples is
+ * too long.  The applied phase is the cycle fraction rounded to 2^-32 and then to float32.
+ * Asynchronous; uses the context's scratch (one 32-byte anchor per span).
  */
 int gfh_heterodyne(gfh_ctx* ctx, const float* d_h, int64_t n_samples, double fs, double t_start,
                    double f0, double k, double n, float* d_out);

@@ -5,10 +5,11 @@
 //
 // Heterodyne.  The residual phase c(t) = F(t) - f0 t (F the integral of Eq. powlaws) reaches 1e6-1e7
 // cycles over a long observation, so it needs fp64 - and fp64 is the slow pipe of this GPU.  It is
-// therefore evaluated in fp64 only at anchors every kAnchor samples (closed form, one thread per
+// therefore evaluated in fp64 only at anchors every 2^10..2^14 samples (closed form, one thread per
 // anchor), together with its first four derivatives.  Each sample then adds, modulo one cycle, the
 // exact linear term on a 64-bit fixed-point lattice (integer multiply-add: no fp64) and the small
-// quadratic..quartic terms in fp32; the fraction of a cycle feeds sincospif.  The kernel moves
+// quadratic..quartic terms in fp32; the fraction of a cycle, as an angle in [-pi, pi), feeds the
+// hardware sine and cosine (absolute error 2^-21.4 there).  The kernel moves
 // 4 bytes in and 8 bytes out per sample and is bound by HBM.
 #include <algorithm>
 #include <cmath>
@@ -17,8 +18,8 @@
 
 namespace {
 
-constexpr int kAnchorLog2 = 10;
-constexpr int64_t kAnchor = int64_t(1) << kAnchorLog2;
+// Anchor spans are powers of two from 2^10 to 2^14 samples, the longest the Taylor bounds allow.
+constexpr int kMinSpanLog2 = 10, kMaxSpanLog2 = 14;
 
 struct HetAnchor {
   unsigned long long C;   // c(t_a) mod 1 in units of 2^-64 cycles
@@ -38,11 +39,12 @@ __device__ __forceinline__ unsigned long long frac64(double x) {
   return __double2ull_rz(ldexp(y, 64));
 }
 
-// One thread per anchor: the residual phase and the derivatives of f at t_a = t_start + a kAnchor/fs.
-__global__ void k_het_anchor(HetParams p, int64_t n_anchor, HetAnchor* __restrict__ out) {
+// One thread per anchor: the residual phase and the derivatives of f at t_a = t_start + a span/fs.
+__global__ void k_het_anchor(HetParams p, int64_t n_anchor, int span_log2,
+                             HetAnchor* __restrict__ out) {
   const int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= n_anchor) return;
-  const double t = p.t_start + (double)(a * kAnchor) / p.fs;
+  const double t = p.t_start + (double)(a << span_log2) / p.fs;
   const double m1 = p.n - 1.0;
   const double acoef = m1 * p.k * pow(p.f0, m1);   // a of Eq. powlaws: 1 + a t
   double c = 0.0, d1 = 0.0, fd = 0.0, fdd = 0.0, fddd = 0.0;
@@ -69,42 +71,40 @@ __global__ void k_het_anchor(HetParams p, int64_t n_anchor, HetAnchor* __restric
   out[a] = h;
 }
 
-// z = h exp(-2 pi j c) for one sample m samples after its anchor.
+// z = h exp(-2 pi j c) for one sample m samples after its anchor.  The small terms (below 1/8
+// cycle, host-checked) go onto the lattice through a 32-bit conversion (2^-34 cycle steps): a
+// 64-bit float-to-integer conversion would run on the fp64 pipe.
 __device__ __forceinline__ float2 het_sample(float h, const HetAnchor& A, int m) {
   const float mf = (float)m;
-  const float small = mf * mf * (A.e2 + mf * (A.e3 + mf * A.e4));      // |small| < 1/8 (host)
-  const long long sf = __float2ll_rn(small * 0x1p62f);
-  const unsigned long long ph = A.C + (unsigned long long)m * A.Q + ((unsigned long long)sf << 2);
+  const float small = mf * mf * (A.e2 + mf * (A.e3 + mf * A.e4));
+  const int sf = __float2int_rn(small * 0x1p34f);
+  const unsigned long long ph =
+      A.C + (unsigned long long)m * A.Q + ((unsigned long long)(long long)sf << 30);
   const int top = (int)(ph >> 32);                                      // cycles in [-1/2, 1/2)
   float sn, cs;
-  sincospif((float)top * 0x1p-31f, &sn, &cs);
+  __sincosf((float)top * 0x1p-32f * 6.28318530717958647692f, &sn, &cs);   // |angle| <= pi
   return make_float2(h * cs, -h * sn);
 }
 
-// Eight samples per thread: two float4 loads in flight, four float4 stores (16-byte aligned
-// buffers); a ragged tail is taken sample by sample.
+// Four samples per thread: float4 in, two float4 out (16-byte aligned buffers); a ragged tail is
+// taken sample by sample.
 __global__ void k_heterodyne(const float* __restrict__ h, int64_t n,
-                             const HetAnchor* __restrict__ anchors, float2* __restrict__ out,
-                             bool vec) {
+                             const HetAnchor* __restrict__ anchors, int span_log2,
+                             float2* __restrict__ out, bool vec) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q * 8 < n; q += stride) {
-    const int64_t s0 = q * 8;
-    const HetAnchor A = anchors[s0 >> kAnchorLog2];     // 8 samples never straddle an anchor
-    const int m0 = (int)(s0 & (kAnchor - 1));
-    if (vec && s0 + 8 <= n) {
-      const float4 v0 = __ldcs(reinterpret_cast<const float4*>(h + s0));
-      const float4 v1 = __ldcs(reinterpret_cast<const float4*>(h + s0 + 4));
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q * 4 < n; q += stride) {
+    const int64_t s0 = q * 4;
+    const HetAnchor A = anchors[s0 >> span_log2];       // 4 samples never straddle an anchor
+    const int m0 = (int)(s0 & ((int64_t(1) << span_log2) - 1));
+    if (vec && s0 + 4 <= n) {
+      const float4 v = __ldcs(reinterpret_cast<const float4*>(h + s0));
+      const float2 z0 = het_sample(v.x, A, m0), z1 = het_sample(v.y, A, m0 + 1);
+      const float2 z2 = het_sample(v.z, A, m0 + 2), z3 = het_sample(v.w, A, m0 + 3);
       float4* o = reinterpret_cast<float4*>(out + s0);
-      float2 a = het_sample(v0.x, A, m0), b = het_sample(v0.y, A, m0 + 1);
-      __stcs(o, make_float4(a.x, a.y, b.x, b.y));
-      a = het_sample(v0.z, A, m0 + 2); b = het_sample(v0.w, A, m0 + 3);
-      __stcs(o + 1, make_float4(a.x, a.y, b.x, b.y));
-      a = het_sample(v1.x, A, m0 + 4); b = het_sample(v1.y, A, m0 + 5);
-      __stcs(o + 2, make_float4(a.x, a.y, b.x, b.y));
-      a = het_sample(v1.z, A, m0 + 6); b = het_sample(v1.w, A, m0 + 7);
-      __stcs(o + 3, make_float4(a.x, a.y, b.x, b.y));
+      __stcs(o, make_float4(z0.x, z0.y, z1.x, z1.y));
+      __stcs(o + 1, make_float4(z2.x, z2.y, z3.x, z3.y));
     } else {
-      for (int j = 0; j < 8 && s0 + j < n; ++j) out[s0 + j] = het_sample(h[s0 + j], A, m0 + j);
+      for (int j = 0; j < 4 && s0 + j < n; ++j) out[s0 + j] = het_sample(h[s0 + j], A, m0 + j);
     }
   }
 }
@@ -139,34 +139,43 @@ extern "C" int gfh_heterodyne(gfh_ctx* ctx, const float* d_h, int64_t n_samples,
       !std::isfinite(f0) || !(k >= 0.0) || !std::isfinite(k) || !(n > 1.0) || !std::isfinite(n))
     return GFH_ERR_ARG;
   if (n_samples == 0) return GFH_OK;
-  // |fdot| and its derivatives are largest at the start (f falls with t): the quadratic..quartic
-  // terms over one anchor span stay below 1/8 cycle, and the first neglected (quintic) term below
-  // 1e-9 cycle.  Larger spin-downs call for a shorter anchor span than this kernel takes.
+  // |fdot| and its derivatives are largest at the start (f falls with t).  The anchor span is the
+  // longest power of two (2^10 .. 2^14 samples) over which the quadratic..quartic terms stay below
+  // 1/8 cycle and the first neglected (quintic) term below 1e-9 cycle; GFH_ERR_ARG when even 2^10
+  // is too long.
+  int span_log2 = -1;
   {
     const double m1 = n - 1.0;
     const double f = f0 / std::pow(1.0 + m1 * k * std::pow(f0, m1) * t_start, 1.0 / m1);
     const double g = k * std::pow(f, m1);
-    const double tau = (double)kAnchor / fs;
-    const double t2 = 0.5 * g * f * tau * tau;
-    const double t3 = n * g * g * f / 6.0 * tau * tau * tau;
-    const double t4 = n * (2.0 * n - 1.0) * g * g * g * f / 24.0 * tau * tau * tau * tau;
-    const double t5 = n * (2.0 * n - 1.0) * (3.0 * n - 2.0) * g * g * g * g * f / 120.0 *
-                      tau * tau * tau * tau * tau;
-    if (!(t2 + t3 + t4 < 0.125) || !(t5 < 1e-9)) return GFH_ERR_ARG;
+    for (int L = kMaxSpanLog2; L >= kMinSpanLog2 && span_log2 < 0; --L) {
+      const double tau = std::ldexp(1.0, L) / fs;
+      const double t2 = 0.5 * g * f * tau * tau;
+      const double t3 = n * g * g * f / 6.0 * tau * tau * tau;
+      const double t4 = n * (2.0 * n - 1.0) * g * g * g * f / 24.0 * tau * tau * tau * tau;
+      const double t5 = n * (2.0 * n - 1.0) * (3.0 * n - 2.0) * g * g * g * g * f / 120.0 *
+                        tau * tau * tau * tau * tau;
+      if (t2 + t3 + t4 < 0.125 && t5 < 1e-9) span_log2 = L;
+    }
   }
+  if (span_log2 < 0) return GFH_ERR_ARG;
   GFH_CUDA_TRY(cudaSetDevice(ctx->device));
-  const int64_t n_anchor = (n_samples + kAnchor - 1) / kAnchor;
+  const int64_t n_anchor = ((n_samples - 1) >> span_log2) + 1;
   int rc = ensure_scratch(ctx, (size_t)n_anchor * sizeof(HetAnchor));
   if (rc) return rc;
   HetAnchor* anchors = (HetAnchor*)ctx->pm_buf;
   cudaStream_t st = ctx->stream;
   k_het_anchor<<<(unsigned)((n_anchor + 127) / 128), 128, 0, st>>>(HetParams{fs, t_start, f0, k, n},
-                                                                   n_anchor, anchors);
+                                                                   n_anchor, span_log2, anchors);
   GFH_CUDA_TRY(cudaGetLastError());
   const bool vec = ((uintptr_t)d_h % 16 == 0) && ((uintptr_t)d_out % 16 == 0);
-  const int64_t octs = (n_samples + 7) / 8;
-  const int64_t blocks = std::min<int64_t>((octs + 255) / 256, (int64_t)ctx->num_sms * 8);
-  k_heterodyne<<<(unsigned)blocks, 256, 0, st>>>(d_h, n_samples, anchors, (float2*)d_out, vec);
+  const int64_t quads = (n_samples + 3) / 4;
+  int per_sm = 0;
+  GFH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_heterodyne, 256, 0));
+  const int64_t blocks = std::min<int64_t>((quads + 255) / 256,
+                                           (int64_t)ctx->num_sms * (per_sm > 0 ? per_sm : 1));
+  k_heterodyne<<<(unsigned)blocks, 256, 0, st>>>(d_h, n_samples, anchors, span_log2,
+                                                 (float2*)d_out, vec);
   GFH_CUDA_TRY(cudaGetLastError());
   return GFH_OK;
 }

@@ -15,11 +15,15 @@ from gpu_util import alloc_outputs, assert_candidates_equal, oracle_grid, read_c
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-# Heterodyne bound, relative to |h|: the phase is exact in fp64 at the anchors (~1e-9 cycle), its
-# fraction is rounded to 2^-32 and then to 24 bits (< 1.5e-8 cycle: 2 pi x 1.6e-8 < 1.1e-7 rad);
-# sincospif is within 2 ulp (2.4e-7) per component and the products h cos, h sin add one rounding
-# (6e-8): |dz| / |h| < 1.1e-7 + 2 x 2.4e-7 + 2 x 6e-8 < 8e-7.  Taken with a factor two.
-HET_TOL = 1.6e-6
+# Heterodyne bound, relative to |h|: the phase is exact in fp64 at the anchors (~1e-9 cycle), the
+# second..fourth-order terms (< 1/8 cycle) carry three float32 roundings (< 3 x 2^-24 / 8 = 2.3e-8
+# cycle) and a 2^-34 step, the fraction is rounded to 2^-32 cycle, and the angle 2 pi x fraction
+# (|angle| <= pi) is formed in float32 with two roundings (< 2 x 2^-24 x pi = 3.8e-7 rad): in all
+# < 2 pi x 2.4e-8 + 3.8e-7 = 5.3e-7 rad.  The hardware sine and cosine are within 2^-21.41 =
+# 3.7e-7 absolutely on [-pi, pi] (sqrt 2 x 3.7e-7 = 5.3e-7 on the complex factor) and the products
+# h cos, h sin add one rounding each (2 x 6e-8): |dz| / |h| < 5.3e-7 + 5.3e-7 + 1.2e-7 = 1.2e-6.
+# Taken with a factor two.
+HET_TOL = 2.4e-6
 
 
 def run_plan(gfh, ctx, fields, fi, bj, tile):
