@@ -30,6 +30,7 @@ struct HetAnchor {
 
 struct HetParams {
   double fs, t_start, f0, k, n;
+  double acoef;           // a = (n-1) k f0^(n-1) of Eq. powlaws: f = f0 (1 + a t)^(-1/(n-1))
 };
 
 // x mod 1 on the 2^-64 lattice (x finite).
@@ -46,7 +47,7 @@ __global__ void k_het_anchor(HetParams p, int64_t n_anchor, int span_log2,
   if (a >= n_anchor) return;
   const double t = p.t_start + (double)(a << span_log2) / p.fs;
   const double m1 = p.n - 1.0;
-  const double acoef = m1 * p.k * pow(p.f0, m1);   // a of Eq. powlaws: 1 + a t
+  const double acoef = p.acoef;
   double c = 0.0, d1 = 0.0, fd = 0.0, fdd = 0.0, fddd = 0.0;
   if (acoef != 0.0) {
     const double L = log1p(acoef * t);
@@ -54,8 +55,8 @@ __global__ void k_het_anchor(HetParams p, int64_t n_anchor, int span_log2,
                                 : p.f0 * m1 / ((p.n - 2.0) * acoef) * expm1((p.n - 2.0) / m1 * L);
     c = F - p.f0 * t;
     const double f = p.f0 * exp(-L / m1);             // Eq. powlaws
-    d1 = p.f0 * expm1(-L / m1);                       // f - f0 without cancellation
-    const double g = p.k * pow(f, m1);                // k f^(n-1): fdot = -g f (Eq. diff_powlaws)
+    d1 = f - p.f0;
+    const double g = acoef / (m1 * (1.0 + acoef * t));  // k f^(n-1): fdot = -g f (Eq. diff_powlaws)
     fd = -g * f;
     fdd = p.n * g * g * f;
     fddd = -p.n * (2.0 * p.n - 1.0) * g * g * g * f;
@@ -165,8 +166,9 @@ extern "C" int gfh_heterodyne(gfh_ctx* ctx, const float* d_h, int64_t n_samples,
   if (rc) return rc;
   HetAnchor* anchors = (HetAnchor*)ctx->pm_buf;
   cudaStream_t st = ctx->stream;
-  k_het_anchor<<<(unsigned)((n_anchor + 127) / 128), 128, 0, st>>>(HetParams{fs, t_start, f0, k, n},
-                                                                   n_anchor, span_log2, anchors);
+  const double acoef = (n - 1.0) * k * std::pow(f0, n - 1.0);
+  k_het_anchor<<<(unsigned)((n_anchor + 127) / 128), 128, 0, st>>>(
+      HetParams{fs, t_start, f0, k, n, acoef}, n_anchor, span_log2, anchors);
   GFH_CUDA_TRY(cudaGetLastError());
   const bool vec = ((uintptr_t)d_h % 16 == 0) && ((uintptr_t)d_out % 16 == 0);
   const int64_t quads = (n_samples + 3) / 4;
