@@ -122,72 +122,103 @@ __global__ void k_image_finish(uint32_t* __restrict__ img, const float* __restri
 // observation, in units of K / 64 bins, lies in [d, d + 1); on x0 tile xt (f0 in [f_a, f_b)) that
 // is k tiles [floor(d gb), ceil((d + 1) ga) - 1] with ga = (f_max / f_a)^n, gb = (f_max / f_b)^n,
 // since one k row drifts (f0 / f_max)^n bins.  Each class spreads its probability evenly over its
-// k tiles.  The tiles are ranked by score (ties to the lower id kt * 64 + xt; bitonic sort in
-// shared memory); the first n tiles leave resid_n = max(0, 1 - p(null) - their score sum).  With
-// tau >= 0 the list stops at the smallest n <= k with resid_n <= tau (the rest of top is -1), and a
-// map whose resid_k exceeds tau is flagged for a full search; with tau < 0 all k tiles are kept.
-__global__ void __launch_bounds__(256) k_propose(const float* __restrict__ logits,
-                                                 const float* __restrict__ gain, int k, float tau,
-                                                 int32_t* __restrict__ top,
-                                                 float* __restrict__ resid,
-                                                 int32_t* __restrict__ full) {
-  constexpr int NT = 256, NCT = kTiles * kTiles;
-  __shared__ float pr[NCT];                // p(d, xt) at d * 64 + xt
-  __shared__ float sc[NCT];                // score, then sorted scores
-  __shared__ uint16_t id[NCT];             // tile id kt * 64 + xt, sorted with sc
+// k tiles (a tile's score sums its classes' shares in increasing d).  The tiles are ranked by score
+// (ties to the lower id kt * 64 + xt): a bitonic sort in shared memory of 64-bit keys, score bits
+// over the complemented id; the first n tiles leave resid_n = max(0, 1 - p(null) - their score
+// sum).  With tau >= 0 the list stops at the smallest n <= k with resid_n <= tau (the rest of top is
+// -1), and a map whose resid_k exceeds tau is flagged for a full search; with tau < 0 all k tiles
+// are kept.  1024 threads per map: the class ranges and shares are computed once per class.
+__global__ void __launch_bounds__(1024) k_propose(const float* __restrict__ logits,
+                                                  const float* __restrict__ gain, int k, float tau,
+                                                  int32_t* __restrict__ top,
+                                                  float* __restrict__ resid,
+                                                  int32_t* __restrict__ full) {
+  constexpr int NT = 1024, NCT = kTiles * kTiles, PER = NCT / NT;
+  // one 32 KB region: first the classes' shares and ranges, then the tiles' sort keys
+  __shared__ __align__(16) unsigned char sbuf[NCT * 8];
+  unsigned long long* key = reinterpret_cast<unsigned long long*>(sbuf);  // score bits << 32 | (0xffff - tile id)
+  float* w = reinterpret_cast<float*>(sbuf);          // class (d, xt) at d * 64 + xt: share per k tile
+  unsigned char* clo = sbuf + NCT * 4;                // its k tile range
+  unsigned char* chi = sbuf + NCT * 5;
   __shared__ float ga[kTiles], gb[kTiles];
-  __shared__ float red[NT];
+  __shared__ float red[NT / 32];
+  __shared__ float s_bcast;
   const float* l = logits + (int64_t)blockIdx.x * kClasses;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid < kTiles) {
     ga[tid] = gain[((int64_t)blockIdx.x * kTiles + tid) * 2];
     gb[tid] = gain[((int64_t)blockIdx.x * kTiles + tid) * 2 + 1];
   }
+  // softmax: max, then sum of exponentials (warp shuffles, then across the 32 warps)
   float mx = -INFINITY;
   for (int c = tid; c < kClasses; c += NT) mx = fmaxf(mx, l[c]);
-  red[tid] = mx;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) red[warp] = mx;
   __syncthreads();
-  for (int s = NT / 2; s > 0; s >>= 1) {
-    if (tid < s) red[tid] = fmaxf(red[tid], red[tid + s]);
-    __syncthreads();
+  if (warp == 0) {
+    float v = red[lane];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) s_bcast = v;
   }
-  mx = red[0];
   __syncthreads();
+  mx = s_bcast;
   float sum = 0.f;
   for (int c = tid; c < kClasses; c += NT) sum += expf(l[c] - mx);
-  red[tid] = sum;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  __syncthreads();                          // everyone has read s_bcast
+  if (lane == 0) red[warp] = sum;
   __syncthreads();
-  for (int s = NT / 2; s > 0; s >>= 1) {
-    if (tid < s) red[tid] += red[tid + s];
-    __syncthreads();
+  if (warp == 0) {
+    float v = red[lane];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) s_bcast = v;
   }
-  const float lse = mx + logf(red[0]);
-  for (int c = tid; c < NCT; c += NT) pr[c] = expf(l[c] - lse);
   __syncthreads();
+  const float lse = mx + logf(s_bcast);
+  // each class: its k tile range and its share
   for (int c = tid; c < NCT; c += NT) {
+    const int d = c / kTiles, xt = c % kTiles;
+    const int lo = min(kTiles - 1, (int)floorf((float)d * gb[xt]));
+    const int hi = min(kTiles - 1, max(lo, (int)ceilf((float)(d + 1) * ga[xt]) - 1));
+    clo[c] = (unsigned char)lo;
+    chi[c] = (unsigned char)hi;
+    w[c] = expf(l[c] - lse) / (float)(hi - lo + 1);
+  }
+  __syncthreads();
+  // each tile: the shares of the classes covering it, in increasing d (keys held in registers
+  // until every thread has read the shares, whose storage they then take over)
+  unsigned long long kreg[PER];
+#pragma unroll
+  for (int r = 0; r < PER; ++r) {
+    const int c = tid + r * NT;
     const int kt = c / kTiles, xt = c % kTiles;
     float s = 0.f;
+#pragma unroll 8
     for (int d = 0; d < kTiles; ++d) {
-      const int lo = min(kTiles - 1, (int)floorf((float)d * gb[xt]));
-      const int hi = min(kTiles - 1, max(lo, (int)ceilf((float)(d + 1) * ga[xt]) - 1));
-      if (kt >= lo && kt <= hi) s += pr[d * kTiles + xt] / (float)(hi - lo + 1);
+      const int q = d * kTiles + xt;
+      if (kt >= clo[q] && kt <= chi[q]) s += w[q];
     }
-    sc[c] = isnan(s) ? -INFINITY : s;
-    id[c] = (uint16_t)c;
+    const uint32_t bits = s > 0.f ? __float_as_uint(s) : 0u;   // NaN and 0 rank last
+    kreg[r] = ((unsigned long long)bits << 32) | (unsigned long long)(0xffffu - (uint32_t)c);
   }
   __syncthreads();
-  // bitonic sort: higher score first, ties to the lower id
+#pragma unroll
+  for (int r = 0; r < PER; ++r) key[tid + r * NT] = kreg[r];
+  __syncthreads();
+  // bitonic sort, descending keys
   for (int kk = 2; kk <= NCT; kk <<= 1) {
     for (int j = kk >> 1; j > 0; j >>= 1) {
       for (int i = tid; i < NCT; i += NT) {
         const int o = i ^ j;
         if (o > i) {
-          const float si = sc[i], so = sc[o];
-          const int ii = id[i], io = id[o];
-          const bool o_first = so > si || (so == si && io < ii);
-          if (((i & kk) == 0) ? o_first : !o_first) {
-            sc[i] = so; sc[o] = si;
-            id[i] = (uint16_t)io; id[o] = (uint16_t)ii;
+          const unsigned long long ki = key[i], ko = key[o];
+          if (((i & kk) == 0) ? (ko > ki) : (ko < ki)) {
+            key[i] = ko;
+            key[o] = ki;
           }
         }
       }
@@ -200,7 +231,7 @@ __global__ void __launch_bounds__(256) k_propose(const float* __restrict__ logit
     float cum = 0.f, res = 1.f;
     int n = k;
     for (int q = 0; q < k; ++q) {
-      cum += fmaxf(sc[q], 0.f);
+      cum += __uint_as_float((uint32_t)(key[q] >> 32));
       res = fmaxf(0.f, 1.f - pnull - cum);
       if (tau >= 0.f && res <= tau) { n = q + 1; break; }
     }
@@ -209,7 +240,9 @@ __global__ void __launch_bounds__(256) k_propose(const float* __restrict__ logit
     if (full) full[blockIdx.x] = (tau >= 0.f && res > tau) ? 1 : 0;
   }
   __syncthreads();
-  for (int q = tid; q < k; q += NT) top[(int64_t)blockIdx.x * k + q] = q < n_keep ? (int32_t)id[q] : -1;
+  for (int q = tid; q < k; q += NT)
+    top[(int64_t)blockIdx.x * k + q] =
+        q < n_keep ? (int32_t)(0xffffu - (uint32_t)(key[q] & 0xffffull)) : -1;
 }
 
 // ---- tensor-core helpers --------------------------------------------------------------------------
@@ -1216,7 +1249,7 @@ extern "C" int gfh_propose_tiles(gfh_ctx* ctx, const float* d_logits, int32_t ba
       k > kTiles * kTiles || !(tau == tau))
     return GFH_ERR_ARG;
   GFH_CUDA_TRY(cudaSetDevice(ctx->device));
-  k_propose<<<batch, 256, 0, ctx->stream>>>(d_logits, d_gain, k, tau, d_top, d_resid, d_full);
+  k_propose<<<batch, 1024, 0, ctx->stream>>>(d_logits, d_gain, k, tau, d_top, d_resid, d_full);
   GFH_CUDA_TRY(cudaGetLastError());
   return GFH_OK;
 }
