@@ -380,6 +380,25 @@ int gfh_peakmap_complex(gfh_ctx* ctx, const float* d_z, int64_t n_samples, doubl
                         uint32_t* d_bin, int64_t cap, int64_t* h_n_peaks);
 
 /*
+ * gfh_heterodyne followed by gfh_peakmap_complex in one pass that never forms the corrected series
+ * or the full spectra (Sec. V Eq. phcor, Sec. III): only the bins the peak search reads, bin_lo - 129
+ * .. bin_hi + 1, are computed for every frame, straight from the float32 series d_h.  Each frame's
+ * bins j0 + k (j0 = bin_lo - 129, k < J, J = 256 or 512 as the band needs) are the first J outputs
+ * of the frame's DFT after a rotation by j0 bins (added exactly to the phase lattice; it changes a
+ * frame's spectrum by a constant phase, not its power): a decimated DFT of N = P J points (P / 32
+ * groups of 32 residues, each a J-point radix-2 transform in shared memory, then a twiddled sum over
+ * the residues).  Same arguments, outputs and synchronisation as the two calls, with
+ * N = round(fs t_fft) a power of two >= 32 J (GFH_ERR_SIZE otherwise) and bin_hi + 1 <= N/2 - 1.
+ * Accuracy: the heterodyne's (gfh_heterodyne), plus float32 transforms with sincospif twiddles
+ * whose residue steps are 32-step recurrences; peak decisions then match the two-call path except
+ * within rounding of a tie or of theta.  Uses the context's scratch (J bins x 8 bytes per frame).
+ */
+int gfh_heterodyne_band_peaks(gfh_ctx* ctx, const float* d_h, int64_t n_samples, double fs,
+                              double t_start, double f0, double k, double n, double t_fft,
+                              int32_t bin_lo, int32_t bin_hi, double theta, uint32_t* d_fft_idx,
+                              uint32_t* d_bin, int64_t cap, int64_t* h_n_peaks);
+
+/*
  * Projection of a bin-shifted peakmap onto frequency (Sec. V): peak (i, j) of the list (device
  * arrays of n_peaks) moves to bin j - floor(fdot t_i / df + 1/2), t_i = t_first + i t_hop (each
  * fp64 operation IEEE-rounded in that order), and d_counts[b - bin_lo] (int32, bin_hi - bin_lo + 1

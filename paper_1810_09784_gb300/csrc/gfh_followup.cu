@@ -87,6 +87,106 @@ __device__ __forceinline__ float2 het_sample(float h, const HetAnchor& A, int m)
   return make_float2(h * cs, -h * sn);
 }
 
+// As het_sample, with an extra rotation rot (cycles on the 2^-64 lattice) added to the phase.
+__device__ __forceinline__ float2 het_sample_rot(float h, const HetAnchor& A, int m,
+                                                 unsigned long long rot) {
+  const float mf = (float)m;
+  const float small = mf * mf * (A.e2 + mf * (A.e3 + mf * A.e4));
+  const int sf = __float2int_rn(small * 0x1p34f);
+  const unsigned long long ph = A.C + (unsigned long long)m * A.Q +
+                                ((unsigned long long)(long long)sf << 30) + rot;
+  const int top = (int)(ph >> 32);
+  float sn, cs;
+  __sincosf((float)top * 0x1p-32f * 6.28318530717958647692f, &sn, &cs);
+  return make_float2(h * cs, -h * sn);
+}
+
+// ---- band spectra of the heterodyned frames ------------------------------------------------------
+//
+// Frame f covers samples s0 = f hop .. s0 + N - 1 (N = 2^log2N, hop = N/2), and the follow-up needs
+// its complex DFT only at bins j0 .. j0 + J - 1.  With y[s] = z[s] e^{-2 pi i j0 s / N} (z the
+// heterodyned series; the rotation is added to the phase lattice exactly, and changes each frame's
+// spectrum by a constant phase only) the wanted outputs are the first J bins of the frame's DFT of
+// y.  Writing n = P m + r (P = N / J): X[k] = sum_r W_N^(k r) Y_r[k] with Y_r the J-point DFT of
+// y[s0 + P m + r] over m.  A block takes one frame: the residues in groups of 32 are staged as
+// [m (bit-reversed)][r] (33-entry rows), transformed along m by radix-2 butterflies (each lane one
+// residue), and thread k adds its output's share W_N^(k r) Y_r[k] (W_N^(k r0) by sincospif once per
+// group, the 32 steps of W_N^k by recurrence).  No FFT of the whole frame is formed.
+template <int J>
+__global__ void __launch_bounds__(J) k_band_dft(const float* __restrict__ h,
+                                                const HetAnchor* __restrict__ anchors,
+                                                int span_log2, int log2N, int hop, int n_frames,
+                                                int j0, float2* __restrict__ X) {
+  constexpr int RG = 32, LD = RG + 1;
+  constexpr int LOGJ = J == 256 ? 8 : 9;
+  extern __shared__ float2 tile[];                   // [J][LD]
+  __shared__ float2 tw[J / 2];                       // W_J^q = e^{-2 pi i q / J}
+  const int tid = threadIdx.x;
+  const int N = 1 << log2N, P = N >> LOGJ;
+  const unsigned long long span_mask = (1ull << span_log2) - 1;
+  for (int q = tid; q < J / 2; q += J) {
+    float sn, cs;
+    sincospif(-2.0f * (float)q / (float)J, &sn, &cs);
+    tw[q] = make_float2(cs, sn);
+  }
+  // W_N^k for this thread's output k = tid
+  float wks, wkc;
+  sincospif(-2.0f * (float)tid / (float)N, &wks, &wkc);
+  for (int f = blockIdx.x; f < n_frames; f += gridDim.x) {
+    const int64_t s0 = (int64_t)f * hop;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int r0 = 0; r0 < P; r0 += RG) {
+      __syncthreads();                               // tile free (previous group consumed)
+      // stage y[s0 + P m + r0 + rl] at row bitrev(m)
+#pragma unroll 4
+      for (int e = tid; e < J * RG; e += J) {
+        const int m = e >> 5, rl = e & 31;
+        const int64_t s = s0 + (int64_t)P * m + r0 + rl;
+        const unsigned long long rot =
+            (((unsigned long long)j0 * (unsigned long long)s) & (unsigned long long)(N - 1))
+            << (64 - log2N);
+        const float2 y = het_sample_rot(__ldg(h + s), anchors[s >> span_log2],
+                                        (int)((unsigned long long)s & span_mask), rot);
+        const int mr = (int)(__brev((unsigned)m) >> (32 - LOGJ));
+        tile[mr * LD + rl] = y;
+      }
+      __syncthreads();
+      // radix-2 decimation in time along m, one residue per lane (stages unrolled: every index
+      // split is a shift)
+#pragma unroll
+      for (int lg = 1; lg <= LOGJ; ++lg) {
+        const int half = 1 << (lg - 1), step = J >> lg;
+#pragma unroll
+        for (int it = 0; it < (J / 2) * RG / J; ++it) {
+          const int e = tid + it * J;
+          const int b = e >> 5, rl = e & 31;
+          const int grp = b >> (lg - 1), pos = b & (half - 1);
+          const int i = (grp << lg) + pos, j = i + half;
+          const float2 w = tw[pos * step];
+          const float2 u = tile[i * LD + rl], v0 = tile[j * LD + rl];
+          const float2 v = make_float2(v0.x * w.x - v0.y * w.y, v0.x * w.y + v0.y * w.x);
+          tile[i * LD + rl] = make_float2(u.x + v.x, u.y + v.y);
+          tile[j * LD + rl] = make_float2(u.x - v.x, u.y - v.y);
+        }
+        __syncthreads();
+      }
+      // X[k] += sum_rl W_N^(k (r0 + rl)) Y_(r0 + rl)[k], k = tid
+      float bs, bc;
+      const int q0 = (int)(((long long)tid * r0) & (N - 1));
+      sincospif(-2.0f * (float)q0 / (float)N, &bs, &bc);
+      float2 wr = make_float2(bc, bs);               // W_N^(k r), r = r0 + rl
+#pragma unroll 4
+      for (int rl = 0; rl < RG; ++rl) {
+        const float2 yv = tile[tid * LD + rl];
+        acc.x += yv.x * wr.x - yv.y * wr.y;
+        acc.y += yv.x * wr.y + yv.y * wr.x;
+        wr = make_float2(wr.x * wkc - wr.y * wks, wr.x * wks + wr.y * wkc);
+      }
+    }
+    X[(int64_t)f * J + tid] = acc;
+  }
+}
+
 // Four samples per thread: float4 in, two float4 out (16-byte aligned buffers); a ragged tail is
 // taken sample by sample.
 __global__ void k_heterodyne(const float* __restrict__ h, int64_t n,
@@ -200,4 +300,79 @@ extern "C" int gfh_project_peaks(gfh_ctx* ctx, const uint32_t* d_fft_idx, const 
       d_fft_idx, d_bin, n_peaks, t_first, t_hop, df, fdot, bin_lo, (int)nb, d_counts);
   GFH_CUDA_TRY(cudaGetLastError());
   return GFH_OK;
+}
+
+extern "C" int gfh_heterodyne_band_peaks(gfh_ctx* ctx, const float* d_h, int64_t n_samples,
+                                         double fs, double t_start, double f0, double k, double n,
+                                         double t_fft, int32_t bin_lo, int32_t bin_hi, double theta,
+                                         uint32_t* d_fft_idx, uint32_t* d_bin, int64_t cap,
+                                         int64_t* h_n_peaks) {
+  if (!ctx || !d_h || !h_n_peaks || cap < 0 || (cap > 0 && (!d_fft_idx || !d_bin)) ||
+      !(fs > 0.0) || !(t_fft > 0.0) || !std::isfinite(t_start) || t_start < 0.0 ||
+      !(f0 > 0.0) || !std::isfinite(f0) || !(k >= 0.0) || !std::isfinite(k) || !(n > 1.0) ||
+      !std::isfinite(n))
+    return GFH_ERR_ARG;
+  const double nd = fs * t_fft;
+  if (!(nd >= 1024.0) || nd > 1048576.0) return GFH_ERR_ARG;
+  const int N = (int)(nd + 0.5);
+  if ((N & (N - 1)) != 0) return GFH_ERR_ARG;            // a power of two
+  int log2N = 0;
+  while ((1 << log2N) < N) ++log2N;
+  const int hop = N / 2;
+  if (n_samples < N) return GFH_ERR_ARG;
+  const int64_t nf64 = (n_samples - N) / hop + 1;
+  if (nf64 > 0x7fffffff) return GFH_ERR_SIZE;
+  const int n_fft = (int)nf64;
+  // the equaliser reads bins bin_lo - 129 .. bin_hi + 1: J = 256 or 512 of them from j0
+  const int j0 = bin_lo - 129;
+  const int need = bin_hi + 1 - j0 + 1;
+  if (j0 < 1 || bin_hi < bin_lo || bin_hi + 1 > N / 2 - 1) return GFH_ERR_ARG;
+  const int J = need <= 256 ? 256 : 512;
+  if (need > J || N < 32 * J) return GFH_ERR_SIZE;      // residues come in groups of 32
+  int span_log2 = -1;
+  {
+    const double m1 = n - 1.0;
+    const double f = f0 / std::pow(1.0 + m1 * k * std::pow(f0, m1) * t_start, 1.0 / m1);
+    const double g = k * std::pow(f, m1);
+    for (int L = kMaxSpanLog2; L >= kMinSpanLog2 && span_log2 < 0; --L) {
+      const double tau = std::ldexp(1.0, L) / fs;
+      const double t2 = 0.5 * g * f * tau * tau;
+      const double t3 = n * g * g * f / 6.0 * tau * tau * tau;
+      const double t4 = n * (2.0 * n - 1.0) * g * g * g * f / 24.0 * tau * tau * tau * tau;
+      const double t5 = n * (2.0 * n - 1.0) * (3.0 * n - 2.0) * g * g * g * g * f / 120.0 *
+                        tau * tau * tau * tau * tau;
+      if (t2 + t3 + t4 < 0.125 && t5 < 1e-9) span_log2 = L;
+    }
+  }
+  if (span_log2 < 0) return GFH_ERR_ARG;
+  GFH_CUDA_TRY(cudaSetDevice(ctx->device));
+  const int64_t n_anchor = ((n_samples - 1) >> span_log2) + 1;
+  // scratch: [band spectra | anchors | the peak search's own]
+  const size_t x_bytes = ((size_t)n_fft * J * sizeof(float2) + 255) / 256 * 256;
+  const size_t a_bytes = ((size_t)n_anchor * sizeof(HetAnchor) + 255) / 256 * 256;
+  int rc = ensure_scratch(ctx, gfh_peaks_scratch(n_fft, bin_lo, bin_hi, x_bytes + a_bytes));
+  if (rc) return rc;
+  float2* X = (float2*)ctx->pm_buf;
+  HetAnchor* anchors = (HetAnchor*)((char*)ctx->pm_buf + x_bytes);
+  cudaStream_t st = ctx->stream;
+  const double acoef = (n - 1.0) * k * std::pow(f0, n - 1.0);
+  k_het_anchor<<<(unsigned)((n_anchor + 127) / 128), 128, 0, st>>>(
+      HetParams{fs, t_start, f0, k, n, acoef}, n_anchor, span_log2, anchors);
+  GFH_CUDA_TRY(cudaGetLastError());
+  const size_t smem = (size_t)J * 33 * sizeof(float2);
+  int per_sm = 0;
+  if (J == 256) {
+    GFH_CUDA_TRY(cudaFuncSetAttribute(k_band_dft<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GFH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_band_dft<256>, 256, smem));
+    const int grid = (int)std::min<int64_t>(n_fft, (int64_t)ctx->num_sms * std::max(per_sm, 1));
+    k_band_dft<256><<<grid, 256, smem, st>>>(d_h, anchors, span_log2, log2N, hop, n_fft, j0, X);
+  } else {
+    GFH_CUDA_TRY(cudaFuncSetAttribute(k_band_dft<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GFH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_band_dft<512>, 512, smem));
+    const int grid = (int)std::min<int64_t>(n_fft, (int64_t)ctx->num_sms * std::max(per_sm, 1));
+    k_band_dft<512><<<grid, 512, smem, st>>>(d_h, anchors, span_log2, log2N, hop, n_fft, j0, X);
+  }
+  GFH_CUDA_TRY(cudaGetLastError());
+  return gfh_band_peaks(ctx, X, J, j0, n_fft, bin_lo, bin_hi, theta, d_fft_idx, d_bin, cap,
+                        h_n_peaks, x_bytes + a_bytes);
 }

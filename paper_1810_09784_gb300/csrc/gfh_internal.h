@@ -159,6 +159,13 @@ int gfh_host_columns(const gfh_grid* g, std::vector<int32_t>& band, std::vector<
 
 // The context's scratch buffer (gfh_peakmap.cu), grown on demand.
 int ensure_scratch(gfh_ctx* c, size_t bytes);
+// Equaliser + peak test + compaction on band spectra d_x [n_fft][ld] holding bins j0 .. j0+ld-1
+// (float2), with `extra` bytes at the front of the context scratch kept for the caller; the
+// scratch that needs, to be ensured up front so that the caller's part is never reallocated.
+int gfh_band_peaks(gfh_ctx* c, const float2* d_x, int64_t ld, int32_t j0, int32_t n_fft,
+                   int32_t bin_lo, int32_t bin_hi, double theta, uint32_t* d_fft_idx,
+                   uint32_t* d_bin, int64_t cap, int64_t* h_n_peaks, size_t extra);
+size_t gfh_peaks_scratch(int32_t n_fft, int32_t bin_lo, int32_t bin_hi, size_t extra);
 // A cuFFT plan of `batch` interlaced frames of N samples (hop N/2) on the context's stream.
 int gfh_fft_plan(gfh_ctx* c, int N, int batch, bool c2c, cufftHandle* out);
 

@@ -32,6 +32,17 @@ struct ComplexIn {
   }
 };
 
+// Spectra of a band only: x [n_fft][ld] holds bins j0 .. j0 + ld - 1.
+struct BandIn {
+  const float2* x;
+  int64_t ld;
+  int64_t j0;
+  __device__ __forceinline__ float at(int64_t i, int64_t j) const {
+    const float2 v = x[i * ld + (j - j0)];
+    return __fadd_rn(__fmul_rn(v.x, v.x), __fmul_rn(v.y, v.y));
+  }
+};
+
 // bits[(b - bin_lo) * n_words + w], bit l: FFT 32 w + l has a peak in bin b.
 //
 // One block of kEqWarps warps per 32 FFTs (lane l = FFT 32 w + l), over chunks of 32 bins:
@@ -277,6 +288,24 @@ bool band_ok(int n_fft, int bin_lo, int bin_hi) {
 }
 
 }  // namespace
+
+// Equaliser, peak test and compaction on band spectra (bins j0 .. j0 + ld - 1 of each of n_fft
+// rows); `extra` bytes at the front of the context scratch belong to the caller.
+int gfh_band_peaks(gfh_ctx* c, const float2* d_x, int64_t ld, int32_t j0, int32_t n_fft,
+                   int32_t bin_lo, int32_t bin_hi, double theta, uint32_t* d_fft_idx,
+                   uint32_t* d_bin, int64_t cap, int64_t* h_n_peaks, size_t extra) {
+  if (!band_ok(n_fft, bin_lo, bin_hi) || (int64_t)bin_lo - 1 - kWarm < j0 ||
+      (int64_t)bin_hi + 1 > (int64_t)j0 + ld - 1)
+    return GFH_ERR_ARG;
+  return run_peaks(c, BandIn{d_x, ld, j0}, n_fft, bin_lo, bin_hi, theta, d_fft_idx, d_bin, cap,
+                   h_n_peaks, extra);
+}
+
+size_t gfh_peaks_scratch(int32_t n_fft, int32_t bin_lo, int32_t bin_hi, size_t extra) {
+  const int n_words = (n_fft + 31) / 32;
+  return align256(extra) + align256((size_t)(bin_hi - bin_lo + 1) * n_words * 4) +
+         align256(((size_t)(bin_hi - bin_lo + 2)) * 8);
+}
 
 // The context's scratch buffer, grown on demand (a growth waits for the stream first).
 int ensure_scratch(gfh_ctx* c, size_t bytes) {

@@ -137,26 +137,42 @@ __global__ void k_sq_final(const SqDev* __restrict__ dp) {
   sq_record(d, k2, sq, 1, mu, sigma);
 }
 
+// One warp per candidate of a: lane l scans the candidates l, l + 32, ... of b, then the warp keeps
+// the smallest distance with ties to the lowest index.  Every distance is the same IEEE
+// evaluation as a sequential scan; the square root is taken only when the squared sum improves
+// (sqrt is monotone: an equal or larger squared sum cannot give a smaller distance), so the result
+// equals the sequential nearest-neighbour scan exactly.
 __global__ void k_coincide(const gfh_candidate* __restrict__ a, int na,
                            const gfh_candidate* __restrict__ b, int nb, double dx0, double dk,
                            double radius, int32_t* __restrict__ match, double* __restrict__ dist) {
-  const int ia = blockIdx.x * blockDim.x + threadIdx.x;
-  if (ia >= na) return;
+  const int ia = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (ia >= na) return;                        // whole warps leave together
   const gfh_candidate ca = a[ia];
-  double best = 0.0;
+  double best = 0.0, best2 = 0.0;
   int bj = -1;
   if (ca.count >= 0) {
-    for (int j = 0; j < nb; ++j) {
-      const gfh_candidate cb = b[j];
-      if (cb.count < 0) continue;
-      const double dxn = __ddiv_rn(__dsub_rn(cb.x0, ca.x0), dx0);
-      const double dkn = __ddiv_rn(__dsub_rn(cb.k, ca.k), dk);
-      const double dd = __dsqrt_rn(__dadd_rn(__dmul_rn(dxn, dxn), __dmul_rn(dkn, dkn)));
-      if (bj < 0 || dd < best) { best = dd; bj = j; }
+    for (int j = lane; j < nb; j += 32) {
+      if (b[j].count < 0) continue;
+      const double dxn = __ddiv_rn(__dsub_rn(b[j].x0, ca.x0), dx0);
+      const double dkn = __ddiv_rn(__dsub_rn(b[j].k, ca.k), dk);
+      const double d2 = __dadd_rn(__dmul_rn(dxn, dxn), __dmul_rn(dkn, dkn));
+      if (bj < 0 || d2 < best2) {
+        const double dd = __dsqrt_rn(d2);
+        if (bj < 0 || dd < best) { best = dd; best2 = d2; bj = j; }
+      }
     }
   }
-  match[ia] = (bj >= 0 && best <= radius) ? bj : -1;
-  dist[ia] = bj >= 0 ? best : -1.0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oj = __shfl_xor_sync(0xffffffffu, bj, o);
+    if (oj >= 0 && (bj < 0 || ob < best || (ob == best && oj < bj))) { best = ob; bj = oj; }
+  }
+  if (lane == 0) {
+    match[ia] = (bj >= 0 && best <= radius) ? bj : -1;
+    dist[ia] = bj >= 0 ? best : -1.0;
+  }
 }
 
 }  // namespace
@@ -237,8 +253,8 @@ extern "C" int gfh_coincide(gfh_ctx* ctx, const gfh_candidate* d_a, int32_t na,
     return GFH_ERR_ARG;
   if (na == 0) return GFH_OK;
   GFH_CUDA_TRY(cudaSetDevice(ctx->device));
-  k_coincide<<<(na + 127) / 128, 128, 0, ctx->stream>>>(d_a, na, d_b, nb, dx0, dk, radius, d_match,
-                                                       d_dist);
+  k_coincide<<<(unsigned)(((int64_t)na * 32 + 255) / 256), 256, 0, ctx->stream>>>(
+      d_a, na, d_b, nb, dx0, dk, radius, d_match, d_dist);
   GFH_CUDA_TRY(cudaGetLastError());
   return GFH_OK;
 }

@@ -38,6 +38,7 @@ EXPORTED = [
     "gfh_propose_tiles", "gfh_conv3x3", "gfh_select_squares", "gfh_coincide",
     "gfh_n_grid", "gfh_k_segments", "gfh_wait_check",
     "gfh_heterodyne", "gfh_peakmap_complex", "gfh_project_peaks", "gfh_tfft_portions",
+    "gfh_heterodyne_band_peaks",
 ]
 N_CLASSES = 4097        # 64 x 64 coarse tiles + no signal
 IMG = 256
@@ -150,6 +151,8 @@ def lib() -> ctypes.CDLL:
             "gfh_peakmap_complex": [vp, vp, i64, dbl, dbl, i32, i32, dbl, vp, vp, i64, P(i64)],
             "gfh_project_peaks": [vp, vp, vp, i64, dbl, dbl, dbl, dbl, i32, i32, vp],
             "gfh_tfft_portions": [dbl, dbl, dbl, dbl, dbl, i32, i32, vp, P(i32)],
+            "gfh_heterodyne_band_peaks": [vp, vp, i64, dbl, dbl, dbl, dbl, dbl, dbl, i32, i32, dbl,
+                                          vp, vp, i64, P(i64)],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -360,6 +363,19 @@ class Context:
                                        ctypes.byref(n))
         _ok(rc, "gfh_peakmap_complex")
         return n.value
+
+    def heterodyne_band_peaks(self, series, fs: float, t_start: float, f0: float, k: float,
+                              n: float, t_fft: float, bin_lo: int, bin_hi: int, theta: float,
+                              fft_out, bin_out) -> int:
+        """gfh_heterodyne_band_peaks: the peaks of the series corrected by (f0, k, n), computed
+        from the series in one pass; returns the number of peaks."""
+        cnt = ctypes.c_int64()
+        rc = lib().gfh_heterodyne_band_peaks(self._h, _ptr(series), series.numel(), fs, t_start,
+                                             f0, k, n, t_fft, bin_lo, bin_hi, theta,
+                                             _ptr(fft_out), _ptr(bin_out), fft_out.numel(),
+                                             ctypes.byref(cnt))
+        _ok(rc, "gfh_heterodyne_band_peaks")
+        return cnt.value
 
     def project_peaks(self, fft_idx, bins, n_peaks: int, t_first: float, t_hop: float, df: float,
                       fdot: float, bin_lo: int, bin_hi: int, counts) -> None:

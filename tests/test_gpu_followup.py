@@ -238,3 +238,104 @@ def test_follow_up_chain_recovers_the_injection(built_lib, gpu_ctx):
     j = int(np.argmax(c))
     assert c[j] >= 0.4 * fields["n_fft"] and O.projection_cr(c, j) > 4.0
     assert abs((lo + j) * fields["df"] - best["f0"]) <= 2 * fields["df"]
+
+
+# ---- the one-pass form: heterodyne + band spectra + peaks ------------------------------------------
+
+# Peak decisions of the one-pass form may differ from an fp64 FFT only within its rounding: the
+# heterodyne's 1.2e-6 relative per sample, float32 radix-2 stages (log2 N levels of 2^-24) and the
+# 32-step twiddle recurrences (< 64 x 2^-24 = 3.8e-6 relative per term) bound |dX| by about
+# 1e-5 sum|h| per frame, i.e. a relative error of the power below ~1e-3 at the threshold.
+BAND_TOL = 1e-3
+
+
+def band_case(spec, inj, t_fft, half=5.0):
+    df = 1.0 / t_fft
+    return int(math.floor((inj.f0 - half) / df)), int(math.ceil((inj.f0 + half) / df))
+
+
+@pytest.mark.parametrize("dx,dkr", [(0, 0), (1, -1)])
+def test_band_peaks_match_oracle(built_lib, gpu_ctx, dx, dkr):
+    """plain_small's series corrected by its injection (or a candidate one x0 column and one k row
+    off), 8 s frames: the one-pass peaks equal the oracle's (fp64 heterodyne and FFT) and the
+    two-call GPU path's up to decisions within rounding of a tie or theta."""
+    gfh = built_lib
+    spec, _, grids = workloads.plain_small()
+    inj = spec.injections[0]
+    g0 = oracle_grid(grids[0])
+    f0 = float(O.f_of_x(float(O.x_of_f(inj.f0, inj.n)) + dx * g0.dx0, inj.n))
+    k = inj.k + dkr * g0.dk
+    h = spec.series()
+    t_fft = 8.0
+    lo, hi = band_case(spec, inj, t_fft)
+    dh = to_dev(torch, h)
+    cap = 200000
+    fo = torch.empty(cap, dtype=torch.int32, device="cuda")
+    bo = torch.empty(cap, dtype=torch.int32, device="cuda")
+    n1 = gpu_ctx.heterodyne_band_peaks(dh, spec.fs, 0.0, f0, k, inj.n, t_fft, lo, hi, 2.5, fo, bo)
+    key1 = bo[:n1].cpu().numpy().astype(np.int64)
+    f1 = fo[:n1].cpu().numpy().astype(np.int64)
+    z = O.heterodyne(h, spec.fs, 0.0, f0, k, inj.n)
+    P = O.complex_power_spectra(z, spec.fs, t_fft)
+    R = O.equalise(P, lo, hi)
+    ofi, obj = O.peaks_from_power(P, lo, hi)
+    n_fft = P.shape[0]
+    a = key1 * n_fft + f1
+    b = obj.astype(np.int64) * n_fft + ofi
+    assert np.all(np.diff(a) > 0) and len(b) > 1000
+    diff = np.concatenate([np.setdiff1d(a, b), np.setdiff1d(b, a)])
+    assert len(diff) <= max(5, len(b) // 1000)
+    if len(diff):
+        assert np.all(marginal(R, diff % n_fft, diff // n_fft, lo, tol=BAND_TOL))
+    # the two-call GPU path on the same candidate
+    zt = torch.empty(2 * h.size, dtype=torch.float32, device="cuda")
+    gpu_ctx.heterodyne(dh, spec.fs, 0.0, f0, k, inj.n, zt)
+    n2 = gpu_ctx.peakmap_complex(zt, spec.fs, t_fft, lo, hi, 2.5, fo, bo)
+    c = bo[:n2].cpu().numpy().astype(np.int64) * n_fft + fo[:n2].cpu().numpy().astype(np.int64)
+    diff2 = np.concatenate([np.setdiff1d(a, c), np.setdiff1d(c, a)])
+    assert len(diff2) <= max(5, len(c) // 1000)
+    if len(diff2):
+        assert np.all(marginal(R, diff2 % n_fft, diff2 // n_fft, lo, tol=BAND_TOL))
+
+
+def test_band_peaks_full_size_sampled_frames(built_lib, gpu_ctx):
+    """The 41.3M-sample series and its fifth injection, 8 s frames (N = 32768): the peaks of four
+    frames (first, two inner, last) equal the oracle's computed on those frames alone."""
+    gfh = built_lib
+    spec, _, _ = workloads.plain_paper()
+    inj = spec.injections[4]
+    h = spec.series()
+    t_fft = 8.0
+    lo, hi = band_case(spec, inj, t_fft)
+    fo = torch.empty(400000, dtype=torch.int32, device="cuda")
+    bo = torch.empty(400000, dtype=torch.int32, device="cuda")
+    n1 = gpu_ctx.heterodyne_band_peaks(to_dev(torch, h), spec.fs, 0.0, inj.f0, inj.k, inj.n, t_fft,
+                                       lo, hi, 2.5, fo, bo)
+    fi = fo[:n1].cpu().numpy().astype(np.int64)
+    bj = bo[:n1].cpu().numpy().astype(np.int64)
+    N = int(spec.fs * t_fft)
+    hop = N // 2
+    n_fft = (h.size - N) // hop + 1
+    for f in (0, 700, 1901, n_fft - 1):
+        s0 = f * hop
+        z = O.heterodyne(h[s0:s0 + N], spec.fs, s0 / spec.fs, inj.f0, inj.k, inj.n)
+        P = O.complex_power_spectra(z, spec.fs, t_fft)
+        R = O.equalise(P, lo, hi)
+        _, obj = O.peaks_from_power(P, lo, hi)
+        got = bj[fi == f]
+        diff = np.concatenate([np.setdiff1d(got, obj), np.setdiff1d(obj.astype(np.int64), got)])
+        assert len(diff) <= 2, (f, diff)
+        if len(diff):
+            assert np.all(marginal(R, np.zeros(len(diff), np.int64), diff, lo, tol=BAND_TOL)), f
+
+
+def test_band_peaks_reject_unsupported_shapes(built_lib, gpu_ctx):
+    gfh = built_lib
+    h = torch.zeros(1 << 16, dtype=torch.float32, device="cuda")
+    o = torch.empty(16, dtype=torch.int32, device="cuda")
+    with pytest.raises(gfh.GfhError) as e:        # N = 4096 < 32 x 256
+        gpu_ctx.heterodyne_band_peaks(h, 1024.0, 0.0, 300.0, 0.0, 5.0, 4.0, 1150, 1250, 2.5, o, o)
+    assert e.value.code == gfh.GFH_ERR_SIZE
+    with pytest.raises(gfh.GfhError) as e:        # N not a power of two
+        gpu_ctx.heterodyne_band_peaks(h, 1000.0, 0.0, 300.0, 0.0, 5.0, 8.0, 2300, 2400, 2.5, o, o)
+    assert e.value.code == gfh.GFH_ERR_ARG
