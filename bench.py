@@ -1210,6 +1210,7 @@ def run_splice(args):
         hits, tot = 0, 0
         for ga, ca, gb, cb in zip(pa["grids"], pa["cands"], pb["grids"], pb["cands"]):
             m_, d_ = splice.coincide(ctx, ca, ga, cb, gb)
+            torch.cuda.synchronize()              # the kernel ran on the library's stream
             ra = gfh.candidates_to_numpy(ca)
             m_ = m_.cpu().numpy()
             strong = ra["cr"] > 6.0

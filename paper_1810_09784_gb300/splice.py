@@ -58,7 +58,8 @@ def portion_plan(portions, fs: float, n_samples: int, n: float, bands, n_k: int,
 
 def coincide(ctx, cands_a, ga, cands_b, gb, radius: float = 3.0):
     """gfh_coincide of two portions' candidate records (device uint8 tensors of whole records) on
-    the coarser grid: returns (match, dist) host arrays for the records of `cands_a`."""
+    the coarser grid: returns the (match, dist) device tensors for the records of `cands_a`, written
+    on the context's stream (synchronise with it before reading them on another stream)."""
     import torch
     na = cands_a.numel() // gfh.CANDIDATE_BYTES
     nb = cands_b.numel() // gfh.CANDIDATE_BYTES
