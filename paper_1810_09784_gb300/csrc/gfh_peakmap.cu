@@ -17,31 +17,47 @@ constexpr float kGain = 1.08942544f;      // float32(1 / (1 - exp(-2.5)))
 constexpr float kClipGain = 2.72356367f;  // float32(2.5 / (1 - exp(-2.5)))
 constexpr int kWarm = 128;
 
-// Power of one spectrum bin from the input layout.
+// Power of one spectrum bin from the input layout: the raw element (Raw) copied to shared memory,
+// its source address, and the power computed from it.
 struct PowerIn {
+  using Raw = float;
   const float* p;
   int64_t ld;
-  __device__ __forceinline__ float at(int64_t i, int64_t j) const { return p[i * ld + j]; }
+  __device__ __forceinline__ const Raw* src(int64_t i, int64_t j) const { return p + i * ld + j; }
+  __device__ __forceinline__ static float power(Raw v) { return v; }
 };
 struct ComplexIn {
+  using Raw = float2;
   const float2* x;
   int64_t ld;
-  __device__ __forceinline__ float at(int64_t i, int64_t j) const {
-    const float2 v = x[i * ld + j];
+  __device__ __forceinline__ const Raw* src(int64_t i, int64_t j) const { return x + i * ld + j; }
+  __device__ __forceinline__ static float power(Raw v) {
+    return __fadd_rn(__fmul_rn(v.x, v.x), __fmul_rn(v.y, v.y));
+  }
+};
+// Spectra of a band only: x [n_fft][ld] holds bins j0 .. j0 + ld - 1.
+struct BandIn {
+  using Raw = float2;
+  const float2* x;
+  int64_t ld;
+  int64_t j0;
+  __device__ __forceinline__ const Raw* src(int64_t i, int64_t j) const {
+    return x + i * ld + (j - j0);
+  }
+  __device__ __forceinline__ static float power(Raw v) {
     return __fadd_rn(__fmul_rn(v.x, v.x), __fmul_rn(v.y, v.y));
   }
 };
 
-// Spectra of a band only: x [n_fft][ld] holds bins j0 .. j0 + ld - 1.
-struct BandIn {
-  const float2* x;
-  int64_t ld;
-  int64_t j0;
-  __device__ __forceinline__ float at(int64_t i, int64_t j) const {
-    const float2 v = x[i * ld + (j - j0)];
-    return __fadd_rn(__fmul_rn(v.x, v.x), __fmul_rn(v.y, v.y));
-  }
-};
+// Asynchronous copy of one raw element (4 or 8 bytes) to shared memory; ok = false fills zeros
+// (the source is then not read).
+template <class Raw>
+__device__ __forceinline__ void eq_copy(Raw* dst, const Raw* src, bool ok) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(d), "l"(src),
+               "n"((int)sizeof(Raw)), "r"(ok ? (int)sizeof(Raw) : 0)
+               : "memory");
+}
 
 // bits[(b - bin_lo) * n_words + w], bit l: FFT 32 w + l has a peak in bin b.
 //
@@ -49,18 +65,30 @@ struct BandIn {
 //   warp 0      runs only the recurrence of chunk c (the mean each bin is divided by, then the
 //               update: four dependent operations per bin, the one serial part) and leaves the
 //               means in shared memory;
-//   warps 1..H  load chunk c+1, divide chunk c-1 (helper h takes bins h-1, h-1+H, ...), meet at a
-//               named barrier, then take the peak decisions of chunk c-1 one bin late (bin b needs
-//               R at b+1), one ballot word per bin.
-// Rings: three power tiles, two mean tiles, two equalised tiles; one block barrier per chunk.
+//   warps 1..H  copy chunk c + kEqDepth into a ring in shared memory (asynchronous copies, one
+//               group per chunk, each helper its own rows), divide chunk c-1 (helper h takes bins
+//               h-1, h-1+H, ...), meet at a named barrier, take the peak decisions of chunk c-1 one
+//               bin late (bin b needs R at b+1, one ballot word per bin), then wait for their rows
+//               of chunk c+1 and turn them into powers for the recurrence.
+// Rings: kEqDepth + 1 raw tiles, three power tiles, two mean tiles, two equalised tiles; one block
+// barrier per chunk.  The copies run kEqDepth chunks ahead so that memory latency stays off the
+// recurrence.
 constexpr int kEqWarps = 8;
 constexpr int kEqHelpers = kEqWarps - 1;
+constexpr int kEqDepth = 4;
+constexpr int kEqRing = kEqDepth + 1;
+
+template <class In>
+size_t eq_smem_bytes() { return (size_t)kEqRing * 32 * 32 * sizeof(typename In::Raw); }
 
 template <class In>
 __global__ void __launch_bounds__(32 * kEqWarps) k_equalise(In in, int n_fft, int bin_lo,
                                                             int bin_hi, float theta,
                                                             uint32_t* __restrict__ bits,
                                                             int n_words) {
+  using Raw = typename In::Raw;
+  extern __shared__ __align__(16) unsigned char eq_dyn[];
+  Raw* raw = reinterpret_cast<Raw*>(eq_dyn);   // [kEqRing][32 ffts][32 bins]
   __shared__ float Pt[3][32][33];   // [chunk ring][fft][bin]
   __shared__ float Sm[2][32][33];   // [chunk ring][fft][bin]: mean each bin is divided by
   __shared__ float Rt[2][32][32];   // [chunk ring][bin][fft]: equalised values
@@ -71,9 +99,39 @@ __global__ void __launch_bounds__(32 * kEqWarps) k_equalise(In in, int n_fft, in
   const int j0 = bin_lo - 1 - kWarm;    // first warm-up bin
   const int j_end = bin_hi + 1;         // last equalised bin
   const int n_chunks = (j_end - j0 + 32) / 32;
-  for (int r = warp; r < 32; r += kEqWarps) {             // chunk 0
-    const int f = fft0 + r, j = j0 + lane;
-    Pt[0][r][lane] = (f < n_fft && j <= j_end) ? in.at(f, j) : 0.f;
+  constexpr int kRowsPerHelper = (32 + kEqHelpers - 1) / kEqHelpers;
+  const int h = warp - 1;
+  // helper: copy its rows of chunk x (zeros past the last FFT or bin), as one commit group
+  auto issue = [&](int x) {
+    if (x < n_chunks) {
+      Raw* slot = raw + (x % kEqRing) * 32 * 32;
+#pragma unroll
+      for (int i = 0; i < kRowsPerHelper; ++i) {
+        const int r = h + i * kEqHelpers;
+        if (r < 32) {
+          const int f = fft0 + r, j = j0 + 32 * x + lane;
+          const bool ok = f < n_fft && j <= j_end;
+          eq_copy(slot + r * 32 + lane, ok ? in.src(f, j) : in.src(0, j0), ok);
+        }
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  // helper: its rows of chunk x, raw -> power tile
+  auto convert = [&](int x) {
+    if (x < n_chunks) {
+      const Raw* slot = raw + (x % kEqRing) * 32 * 32;
+#pragma unroll
+      for (int i = 0; i < kRowsPerHelper; ++i) {
+        const int r = h + i * kEqHelpers;
+        if (r < 32) Pt[x % 3][r][lane] = In::power(slot[r * 32 + lane]);
+      }
+    }
+  };
+  if (warp > 0) {
+    for (int x = 0; x < kEqDepth; ++x) issue(x);
+    asm volatile("cp.async.wait_group %0;" ::"n"(kEqDepth - 1) : "memory");   // chunk 0
+    convert(0);
   }
   __syncthreads();
   float S = 0.f;                        // warp 0: running mean of FFT my_fft
@@ -101,19 +159,7 @@ __global__ void __launch_bounds__(32 * kEqWarps) k_equalise(In in, int n_fft, in
         }
       }
     } else {
-      const int h = warp - 1;
-      // loads of chunk c+1 (rows h, h+H, ...) go out first
-      constexpr int kRowsPerHelper = (32 + kEqHelpers - 1) / kEqHelpers;
-      float nxt[kRowsPerHelper];
-      const bool load = c + 1 < n_chunks;
-      if (load) {
-#pragma unroll
-        for (int i = 0; i < kRowsPerHelper; ++i) {
-          const int r = h + i * kEqHelpers;
-          const int f = fft0 + r, j = j0 + 32 * (c + 1) + lane;
-          nxt[i] = (r < 32 && f < n_fft && j <= j_end) ? in.at(f, j) : 0.f;
-        }
-      }
+      issue(c + kEqDepth);
       if (c >= 1) {
         const int cp = c - 1;
         const int cb = j0 + 32 * cp;
@@ -136,16 +182,37 @@ __global__ void __launch_bounds__(32 * kEqWarps) k_equalise(In in, int n_fft, in
           if (lane == 0) bits[(int64_t)(b - bin_lo) * n_words + gw] = word;
         }
       }
-      if (load) {
-#pragma unroll
-        for (int i = 0; i < kRowsPerHelper; ++i) {
-          const int r = h + i * kEqHelpers;
-          if (r < 32) Pt[(c + 1) % 3][r][lane] = nxt[i];
-        }
-      }
+      asm volatile("cp.async.wait_group %0;" ::"n"(kEqDepth - 1) : "memory");   // chunk c+1
+      convert(c + 1);
     }
     __syncthreads();
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// Launch of the equaliser with its dynamic shared memory (the raw ring; above the default 48 KB
+// with the static tiles, so the attribute is raised once per device and input type).
+template <class In>
+cudaError_t launch_equalise(In in, int n_fft, int bin_lo, int bin_hi, float theta, uint32_t* bits,
+                            int n_words, cudaStream_t st) {
+  static std::mutex mu;
+  static uint64_t done = 0;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const size_t dyn = eq_smem_bytes<In>();
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev < 0 || dev >= 64 || !(done >> dev & 1ull)) {
+      e = cudaFuncSetAttribute(k_equalise<In>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)dyn);
+      if (e != cudaSuccess) return e;
+      if (dev >= 0 && dev < 64) done |= 1ull << dev;
+    }
+  }
+  k_equalise<In><<<n_words, 32 * kEqWarps, dyn, st>>>(in, n_fft, bin_lo, bin_hi, theta, bits,
+                                                     n_words);
+  return cudaGetLastError();
 }
 
 // counts[b] = peaks in bin b (one warp per bin).
@@ -261,10 +328,7 @@ int run_peaks(gfh_ctx* c, In in, int n_fft, int bin_lo, int bin_hi, double theta
   uint32_t* bits = (uint32_t*)(base + o_bits);
   int64_t* cnt = (int64_t*)(base + o_cnt);
   cudaStream_t st = c->stream;
-  k_equalise<In><<<n_words, 32 * kEqWarps, 0, st>>>(
-      in, n_fft, bin_lo, bin_hi, (float)theta, bits,
-                                                   n_words);
-  GFH_CUDA_TRY(cudaGetLastError());
+  GFH_CUDA_TRY(launch_equalise(in, n_fft, bin_lo, bin_hi, (float)theta, bits, n_words, st));
   k_count<<<(n_bins + 7) / 8, 256, 0, st>>>(bits, n_bins, n_words, cnt);
   GFH_CUDA_TRY(cudaGetLastError());
   k_scan<<<1, 1024, 0, st>>>(cnt, n_bins);
@@ -570,10 +634,8 @@ extern "C" int gfh_peaks_from_power_static(void* stream, const float* d_power, i
   cudaStream_t st = (cudaStream_t)stream;
   // Every word of the bit matrix and every count is rewritten below, so nothing left by an
   // earlier call is read.
-  k_equalise<PowerIn><<<n_words, 32 * kEqWarps, 0, st>>>(
-      PowerIn{d_power, ld}, n_fft, bin_lo,
-                                                         bin_hi, (float)theta, bits, n_words);
-  GFH_CUDA_TRY(cudaGetLastError());
+  GFH_CUDA_TRY(launch_equalise(PowerIn{d_power, ld}, n_fft, bin_lo, bin_hi, (float)theta, bits,
+                               n_words, st));
   k_count<<<(n_bins + 7) / 8, 256, 0, st>>>(bits, n_bins, n_words, cnt);
   GFH_CUDA_TRY(cudaGetLastError());
   k_scan<<<1, 1024, 0, st>>>(cnt, n_bins);
