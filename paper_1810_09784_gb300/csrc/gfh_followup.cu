@@ -31,6 +31,8 @@ struct HetAnchor {
 struct HetParams {
   double fs, t_start, f0, k, n;
   double acoef;           // a = (n-1) k f0^(n-1) of Eq. powlaws: f = f0 (1 + a t)^(-1/(n-1))
+  long long rot_bins;     // extra rotation by rot_bins / 2^rot_log2 cycles per sample (0: none)
+  int rot_log2;
 };
 
 // x mod 1 on the 2^-64 lattice (x finite).
@@ -64,6 +66,13 @@ __global__ void k_het_anchor(HetParams p, int64_t n_anchor, int span_log2,
   HetAnchor h;
   h.C = frac64(c);
   h.Q = frac64(d1 / p.fs);
+  if (p.rot_bins != 0) {
+    // + rot_bins s / 2^rot_log2 cycles at sample s = a span + m: exact on the 2^-64 lattice
+    const unsigned long long nm = (1ull << p.rot_log2) - 1;
+    const int sh = 64 - p.rot_log2;
+    h.C += (((unsigned long long)p.rot_bins * ((unsigned long long)a << span_log2)) & nm) << sh;
+    h.Q += ((unsigned long long)p.rot_bins & nm) << sh;
+  }
   const double i1 = 1.0 / p.fs;
   h.e2 = (float)(0.5 * fd * i1 * i1);
   h.e3 = (float)(fdd / 6.0 * i1 * i1 * i1);
@@ -87,27 +96,13 @@ __device__ __forceinline__ float2 het_sample(float h, const HetAnchor& A, int m)
   return make_float2(h * cs, -h * sn);
 }
 
-// As het_sample, with an extra rotation rot (cycles on the 2^-64 lattice) added to the phase.
-__device__ __forceinline__ float2 het_sample_rot(float h, const HetAnchor& A, int m,
-                                                 unsigned long long rot) {
-  const float mf = (float)m;
-  const float small = mf * mf * (A.e2 + mf * (A.e3 + mf * A.e4));
-  const int sf = __float2int_rn(small * 0x1p34f);
-  const unsigned long long ph = A.C + (unsigned long long)m * A.Q +
-                                ((unsigned long long)(long long)sf << 30) + rot;
-  const int top = (int)(ph >> 32);
-  float sn, cs;
-  __sincosf((float)top * 0x1p-32f * 6.28318530717958647692f, &sn, &cs);
-  return make_float2(h * cs, -h * sn);
-}
-
 // ---- band spectra of the heterodyned frames ------------------------------------------------------
 //
 // Frame f covers samples s0 = f hop .. s0 + N - 1 (N = 2^log2N, hop = N/2), and the follow-up needs
 // its complex DFT only at bins j0 .. j0 + J - 1.  With y[s] = z[s] e^{-2 pi i j0 s / N} (z the
-// heterodyned series; the rotation is added to the phase lattice exactly, and changes each frame's
-// spectrum by a constant phase only) the wanted outputs are the first J bins of the frame's DFT of
-// y.  Writing n = P m + r (P = N / J): X[k] = sum_r W_N^(k r) Y_r[k] with Y_r the J-point DFT of
+// heterodyned series; the rotation is folded into the anchors' phase and cycles per sample,
+// exactly on the 2^-64 lattice, and changes each frame's spectrum by a constant phase only) the
+// wanted outputs are the first J bins of the frame's DFT of y.  Writing n = P m + r (P = N / J): X[k] = sum_r W_N^(k r) Y_r[k] with Y_r the J-point DFT of
 // y[s0 + P m + r] over m.  A block takes one frame: the residues in groups of 32 are staged as
 // [m (bit-reversed)][r] (33-entry rows), transformed along m by radix-2 butterflies (each lane one
 // residue), and thread k adds its output's share W_N^(k r) Y_r[k] (W_N^(k r0) by sincospif once per
@@ -142,31 +137,57 @@ __global__ void __launch_bounds__(J) k_band_dft(const float* __restrict__ h,
       for (int e = tid; e < J * RG; e += J) {
         const int m = e >> 5, rl = e & 31;
         const int64_t s = s0 + (int64_t)P * m + r0 + rl;
-        const unsigned long long rot =
-            (((unsigned long long)j0 * (unsigned long long)s) & (unsigned long long)(N - 1))
-            << (64 - log2N);
-        const float2 y = het_sample_rot(__ldg(h + s), anchors[s >> span_log2],
-                                        (int)((unsigned long long)s & span_mask), rot);
+        const float2 y = het_sample(__ldg(h + s), anchors[s >> span_log2],
+                                    (int)((unsigned long long)s & span_mask));
         const int mr = (int)(__brev((unsigned)m) >> (32 - LOGJ));
         tile[mr * LD + rl] = y;
       }
       __syncthreads();
-      // radix-2 decimation in time along m, one residue per lane (stages unrolled: every index
-      // split is a shift)
+      // radix-2 decimation in time along m, one residue per lane, two stages per pass: stages lg
+      // and lg + 1 map the four entries base + {0, L, 2L, 3L} (L = 2^(lg-1)) onto themselves, so a
+      // thread applies both stages' butterflies to them in registers (the same operations and
+      // twiddles as stage by stage)
 #pragma unroll
-      for (int lg = 1; lg <= LOGJ; ++lg) {
-        const int half = 1 << (lg - 1), step = J >> lg;
+      for (int lg = 1; lg <= LOGJ; lg += 2) {
+        const int L = 1 << (lg - 1);
+        if (lg + 1 <= LOGJ) {
 #pragma unroll
-        for (int it = 0; it < (J / 2) * RG / J; ++it) {
-          const int e = tid + it * J;
-          const int b = e >> 5, rl = e & 31;
-          const int grp = b >> (lg - 1), pos = b & (half - 1);
-          const int i = (grp << lg) + pos, j = i + half;
-          const float2 w = tw[pos * step];
-          const float2 u = tile[i * LD + rl], v0 = tile[j * LD + rl];
-          const float2 v = make_float2(v0.x * w.x - v0.y * w.y, v0.x * w.y + v0.y * w.x);
-          tile[i * LD + rl] = make_float2(u.x + v.x, u.y + v.y);
-          tile[j * LD + rl] = make_float2(u.x - v.x, u.y - v.y);
+          for (int it = 0; it < (J / 4) * RG / J; ++it) {
+            const int e = tid + it * J;
+            const int b = e >> 5, rl = e & 31;
+            const int grp = b >> (lg - 1), pp = b & (L - 1);
+            const int i0 = (grp << (lg + 1)) + pp;
+            float2 a0 = tile[i0 * LD + rl], a1 = tile[(i0 + L) * LD + rl];
+            float2 a2 = tile[(i0 + 2 * L) * LD + rl], a3 = tile[(i0 + 3 * L) * LD + rl];
+            const float2 w1 = tw[pp * (J >> lg)];
+            const float2 w2 = tw[pp * (J >> (lg + 1))];
+            const float2 w3 = tw[(pp + L) * (J >> (lg + 1))];
+            float2 v = make_float2(a1.x * w1.x - a1.y * w1.y, a1.x * w1.y + a1.y * w1.x);
+            a1 = make_float2(a0.x - v.x, a0.y - v.y);
+            a0 = make_float2(a0.x + v.x, a0.y + v.y);
+            v = make_float2(a3.x * w1.x - a3.y * w1.y, a3.x * w1.y + a3.y * w1.x);
+            a3 = make_float2(a2.x - v.x, a2.y - v.y);
+            a2 = make_float2(a2.x + v.x, a2.y + v.y);
+            v = make_float2(a2.x * w2.x - a2.y * w2.y, a2.x * w2.y + a2.y * w2.x);
+            tile[i0 * LD + rl] = make_float2(a0.x + v.x, a0.y + v.y);
+            tile[(i0 + 2 * L) * LD + rl] = make_float2(a0.x - v.x, a0.y - v.y);
+            v = make_float2(a3.x * w3.x - a3.y * w3.y, a3.x * w3.y + a3.y * w3.x);
+            tile[(i0 + L) * LD + rl] = make_float2(a1.x + v.x, a1.y + v.y);
+            tile[(i0 + 3 * L) * LD + rl] = make_float2(a1.x - v.x, a1.y - v.y);
+          }
+        } else {                                       // a last single stage (J = 512)
+#pragma unroll
+          for (int it = 0; it < (J / 2) * RG / J; ++it) {
+            const int e = tid + it * J;
+            const int b = e >> 5, rl = e & 31;
+            const int grp = b >> (lg - 1), pos = b & (L - 1);
+            const int i = (grp << lg) + pos, j = i + L;
+            const float2 w = tw[pos * (J >> lg)];
+            const float2 u = tile[i * LD + rl], v0 = tile[j * LD + rl];
+            const float2 v = make_float2(v0.x * w.x - v0.y * w.y, v0.x * w.y + v0.y * w.x);
+            tile[i * LD + rl] = make_float2(u.x + v.x, u.y + v.y);
+            tile[j * LD + rl] = make_float2(u.x - v.x, u.y - v.y);
+          }
         }
         __syncthreads();
       }
@@ -268,7 +289,7 @@ extern "C" int gfh_heterodyne(gfh_ctx* ctx, const float* d_h, int64_t n_samples,
   cudaStream_t st = ctx->stream;
   const double acoef = (n - 1.0) * k * std::pow(f0, n - 1.0);
   k_het_anchor<<<(unsigned)((n_anchor + 127) / 128), 128, 0, st>>>(
-      HetParams{fs, t_start, f0, k, n, acoef}, n_anchor, span_log2, anchors);
+      HetParams{fs, t_start, f0, k, n, acoef, 0, 0}, n_anchor, span_log2, anchors);
   GFH_CUDA_TRY(cudaGetLastError());
   const bool vec = ((uintptr_t)d_h % 16 == 0) && ((uintptr_t)d_out % 16 == 0);
   const int64_t quads = (n_samples + 3) / 4;
@@ -357,7 +378,7 @@ extern "C" int gfh_heterodyne_band_peaks(gfh_ctx* ctx, const float* d_h, int64_t
   cudaStream_t st = ctx->stream;
   const double acoef = (n - 1.0) * k * std::pow(f0, n - 1.0);
   k_het_anchor<<<(unsigned)((n_anchor + 127) / 128), 128, 0, st>>>(
-      HetParams{fs, t_start, f0, k, n, acoef}, n_anchor, span_log2, anchors);
+      HetParams{fs, t_start, f0, k, n, acoef, (long long)j0, log2N}, n_anchor, span_log2, anchors);
   GFH_CUDA_TRY(cudaGetLastError());
   const size_t smem = (size_t)J * 33 * sizeof(float2);
   int per_sm = 0;
