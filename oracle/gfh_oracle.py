@@ -17,6 +17,9 @@ only for the brute-force checks on tiny inputs), written from the paper's equati
   Sec. IV   candidates per region of the map, critical ratio CR = (y - mu)/sigma, distance d
   Sec. VI.B Eq. dkeqn  dk = k((1 + df/f0max)^(-n) - 1)
   Sec. VI.C dx0 = (n-1) df / f^n taken at the highest frequency f_max
+  Sec. VI.D Eq. dot_tfft  fdot <= 1/T_FFT^2 keeps a signal in one bin; T_FFT doubles once the
+            spin-down has fallen by 4 (portions of the data)
+  Sec. V    Eq. phcor heterodyne correction; complex-series peakmap; bin-shift projection and its CR
 
 Where the paper is silent the readings are fixed here and listed in the design notes:
   * time stamp of FFT i = its centre; t0 = start of the data (Sec. IV, Fig. hm caption)
@@ -31,8 +34,10 @@ Where the paper is silent the readings are fixed here and listed in the design n
   * CR uses the population mean / std over all analysis-band cells of the map
 
 Parity status: every function below is pinned by the CPU tests (closed forms, brute force on tiny
-maps, invariants, the noise-only peak density p0) except the equaliser's constants, whose values the
-paper does not give ("parity unpinned" beyond the p0 statistic).
+maps, invariants, the noise-only peak density p0; for n = 0 a direct count in the (f0, fdot) plane;
+for the heterodyne numerical quadrature of Eq. powlaws; for the portion planner a brute-force
+maximum over power laws) except the equaliser's constants, whose values the paper does not give
+("parity unpinned" beyond the p0 statistic).
 """
 from __future__ import annotations
 
