@@ -186,7 +186,7 @@ __device__ __forceinline__ void draw_peak_x(int* G0, int lds, int64_t a, int64_t
 // Shared memory: G[R][C+2] | tot[32] row-0 chunk sums | skey[bands] candidate keys.
 // XD (maps whose line moves more than two x0 columns per k row): every row differenced along x0
 // and scanned on its own; chunk sums tot[R][32].
-template <int R, int NT, bool SELECT, bool XD = false>
+template <int R, int NT, bool SELECT, bool XD = false, int LDS = 0>
 __device__ __forceinline__ void hough_tile(const MapDev* __restrict__ maps, const TileDev t,
                                            const uint32_t* __restrict__ fft_idx,
                                            const uint32_t* __restrict__ bins,
@@ -195,7 +195,9 @@ __device__ __forceinline__ void hough_tile(const MapDev* __restrict__ maps, cons
   constexpr int NW = NT / kLane;
   const MapDev& md = maps[t.map];
   const int C = t.ncols;
-  const int lds = C + 2;
+  // row stride: the plan's tile width + 2 when fixed at compile time (row offsets become
+  // immediates), else this tile's
+  const int lds = LDS ? LDS : C + 2;
   int* G = reinterpret_cast<int*>(smem);
   int* tot = G + R * (c_max + 2);
   unsigned long long* skey = reinterpret_cast<unsigned long long*>(tot + (XD ? R : 1) * kLane);
@@ -353,7 +355,7 @@ __device__ __forceinline__ void hough_tile(const MapDev* __restrict__ maps, cons
 }
 
 // One block per tile of the plan.
-template <int R, int NT, bool SELECT, bool XD>
+template <int R, int NT, bool SELECT, bool XD, int LDS = 0>
 __global__ void __launch_bounds__(NT, R <= 4 ? 3 : (R == 8 ? 2 : 1))
 k_hough(const MapDev* __restrict__ maps, const TileDev* __restrict__ tiles,
         const uint32_t* __restrict__ fft_idx, const uint32_t* __restrict__ bins,
@@ -361,7 +363,7 @@ k_hough(const MapDev* __restrict__ maps, const TileDev* __restrict__ tiles,
   extern __shared__ __align__(16) unsigned char smem[];
   const TileDev t = tiles[blockIdx.x];
   if (t.nrows <= 0) return;
-  hough_tile<R, NT, SELECT, XD>(maps, t, fft_idx, bins, flag, c_max, smem);
+  hough_tile<R, NT, SELECT, XD, LDS>(maps, t, fft_idx, bins, flag, c_max, smem);
 }
 
 // Persistent blocks over a tile list whose length is known on the device only (the coarse-tile
@@ -468,7 +470,13 @@ __global__ void k_select_cols(const int32_t* __restrict__ map, const MapDev* __r
 template <int R, int NT, bool SEL>
 int launch_hough_t(gfh_plan* p, const gfh_peaks* peaks, const TileDev* tiles, int n_tiles,
                    size_t smem, bool prepare, bool xd) {
+  // 8-row tiles of 2048 or 3072 columns (the shapes the autotuner picks on the paper-shaped
+  // workloads) have the row stride fixed at compile time
   auto fn = xd ? k_hough<R, NT, SEL, true> : k_hough<R, NT, SEL, false>;
+  if constexpr (R == 8 && NT == 512) {
+    if (!xd && p->cfg.cols == 3072) fn = k_hough<R, NT, SEL, false, 3074>;
+    if (!xd && p->cfg.cols == 2048) fn = k_hough<R, NT, SEL, false, 2050>;
+  }
   auto fl = k_hough_list<R, NT, SEL>;
   if (prepare) {
     // the list kernel also holds a few bytes of static shared memory
@@ -480,6 +488,9 @@ int launch_hough_t(gfh_plan* p, const gfh_peaks* peaks, const TileDev* tiles, in
     GFH_CUDA_TRY(cudaFuncSetAttribute(k_hough<R, NT, SEL, true>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)kMaxSmemBytes));
+    if (fn != k_hough<R, NT, SEL, false> && fn != k_hough<R, NT, SEL, true>)
+      GFH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)kMaxSmemBytes));
     GFH_CUDA_TRY(cudaFuncSetAttribute(fl, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(kMaxSmemBytes - fa.sharedSizeBytes)));
     return GFH_OK;
