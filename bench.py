@@ -388,15 +388,39 @@ def run_gpu(args):
     ms_max, total_updates = ranks.combine(ms, float(updates), device="cuda")
     value = total_updates / (ms_max * 1e-3)
 
-    # ---- end to end through the public API with host buffers
-    with torch.cuda.stream(stream):
-        barrier()
-        a.record(stream)
-        for _ in range(args.steps):
-            step(h2d=True)
-        b.record(stream)
-        barrier()
-        ms_e2e = reduce(a.elapsed_time(b) / args.steps, MAX)
+    # ---- end to end through the public API with host buffers: every step copies its series from
+    # pinned host memory and reads its candidates back; the copy of step i + 1 (second device
+    # buffer, copy stream) overlaps the search of step i, as a streaming pipeline would
+    x_buf = [x_dev, torch.empty_like(x_dev)]
+    copy_stream = torch.cuda.Stream()
+    copied = [torch.cuda.Event(), torch.cuda.Event()]
+    consumed = [torch.cuda.Event(), torch.cuda.Event()]
+
+    def e2e_step(i):
+        k = i & 1
+        copy_stream.wait_event(consumed[k])              # buffer k no longer read
+        with torch.cuda.stream(copy_stream):
+            x_buf[k].copy_(x_host, non_blocking=True)
+        copied[k].record(copy_stream)
+        stream.wait_event(copied[k])
+        with torch.cuda.stream(stream):
+            ctx.peakmap_async(x_buf[k], spec.fs, spec.t_fft, pm["bin_lo"], pm["bin_hi"], 2.5, fo, bo,
+                              off[1:2])
+            plan.execute(fo, bo, off, 1)
+            for c, h in zip(cands, cand_host):
+                h.copy_(c, non_blocking=True)
+        consumed[k].record(stream)
+
+    barrier()
+    a.record(stream)
+    copy_stream.wait_event(a)
+    for i in range(args.steps):
+        e2e_step(i)
+    b.record(stream)
+    barrier()
+    ms_e2e = reduce(a.elapsed_time(b) / args.steps, MAX)
+    if ctx.check() != gfh.GFH_OK or int(off[1].item()) != n_peaks:
+        raise RuntimeError("end-to-end steps differ from the direct step")
     h2d = x_host.numel() * 4
     d2h = sum(c.numel() for c in cands)
 
@@ -473,7 +497,10 @@ def run_gpu(args):
                              "peak_gbs": HBM_PEAK, "frac": map_bytes / (ms_hough * 1e-3) / 1e9 / HBM_PEAK,
                              "peak_source": HBM_PEAK_SRC}},
         "e2e": {"value": total_updates / (ms_e2e * 1e-3), "unit": "updates/s",
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e},
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e,
+                "timing": "asynchronous public calls; each step's series copied from pinned host "
+                          "memory on a copy stream into one of two device buffers (overlapping the "
+                          "previous step's search) and its candidates read back"},
         "squares_selector": squares,
         "gpu_launches": 9 * args.steps,
         "clocks": clocks,
@@ -1142,13 +1169,14 @@ def run_splice(args):
     dist_t = torch.empty(max(n_bands_total), dtype=torch.float64, device="cuda")
     ev = lambda: torch.cuda.Event(enable_timing=True)
 
-    def step(h2d=False, hough_events=None):
-        if h2d:
+    def step(h2d=False, hough_events=None, src=None):
+        if h2d and src is None:                  # the series copied on this stream
             x_dev.copy_(x_host, non_blocking=True)
+        src = x_dev if src is None else src
         for q, p in enumerate(parts):
             P = p["P"]
-            n = ctx.peakmap_async(x_dev[P.s_begin:P.s_end], spec.fs, P.t_fft, p["lo"], p["hi"],
-                                  2.5, p["fo"], p["bo"], p["off"][1:2])
+            ctx.peakmap_async(src[P.s_begin:P.s_end], spec.fs, P.t_fft, p["lo"], p["hi"],
+                              2.5, p["fo"], p["bo"], p["off"][1:2])
             if hough_events is not None:
                 hough_events[q][0].record(stream)
             p["plan"].execute(p["fo"], p["bo"], p["off"], 1)
@@ -1159,10 +1187,11 @@ def run_splice(args):
                 ctx.coincide(ca, ga.n_bands, cb, gb.n_bands, max(ga.dx0, gb.dx0),
                              max(ga.dk, gb.dk), 3.0, match, dist_t)
         if h2d:
-            for p in parts:
-                for c in p["cands"]:
-                    c.cpu()
+            for p, hc in zip(parts, cand_host):
+                for c, h in zip(p["cands"], hc):
+                    h.copy_(c, non_blocking=True)
 
+    cand_host = [[torch.empty_like(c, device="cpu").pin_memory() for c in p["cands"]] for p in parts]
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             step()
@@ -1195,14 +1224,28 @@ def run_splice(args):
     ms_hough = sum(e0.elapsed_time(e1) for st in hev for e0, e1 in st) / args.steps
     ms_max, total = ranks.combine(ms, float(updates), device="cuda")
     value = total / (ms_max * 1e-3)
-    with torch.cuda.stream(stream):
-        barrier()
-        a.record(stream)
-        for _ in range(args.steps):
-            step(h2d=True)
-        b.record(stream)
-        barrier()
-        ms_e2e = a.elapsed_time(b) / args.steps
+    # end to end: each step's series copied from pinned host memory on a copy stream into one of
+    # two device buffers (overlapping the previous step's search), its candidates read back
+    x_buf = [x_dev, torch.empty_like(x_dev)]
+    copy_stream = torch.cuda.Stream()
+    copied = [torch.cuda.Event(), torch.cuda.Event()]
+    consumed = [torch.cuda.Event(), torch.cuda.Event()]
+    barrier()
+    a.record(stream)
+    copy_stream.wait_event(a)
+    for i in range(args.steps):
+        k = i & 1
+        copy_stream.wait_event(consumed[k])
+        with torch.cuda.stream(copy_stream):
+            x_buf[k].copy_(x_host, non_blocking=True)
+        copied[k].record(copy_stream)
+        stream.wait_event(copied[k])
+        with torch.cuda.stream(stream):
+            step(h2d=True, src=x_buf[k])
+        consumed[k].record(stream)
+    b.record(stream)
+    barrier()
+    ms_e2e = a.elapsed_time(b) / args.steps
     # coincidences of the injections between the two portions (top candidate of each band)
     coinc = None
     if len(parts) >= 2:
