@@ -396,12 +396,19 @@ def run_gpu(args):
     copied = [torch.cuda.Event(), torch.cuda.Event()]
     consumed = [torch.cuda.Event(), torch.cuda.Event()]
 
-    def e2e_step(i):
+    h2d_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+
+    def e2e_step(i, timed=False):
         k = i & 1
         copy_stream.wait_event(consumed[k])              # buffer k no longer read
+        if timed:
+            h2d_ev[i][0].record(copy_stream)
         with torch.cuda.stream(copy_stream):
             x_buf[k].copy_(x_host, non_blocking=True)
         copied[k].record(copy_stream)
+        if timed:
+            h2d_ev[i][1].record(copy_stream)
         stream.wait_event(copied[k])
         with torch.cuda.stream(stream):
             ctx.peakmap_async(x_buf[k], spec.fs, spec.t_fft, pm["bin_lo"], pm["bin_hi"], 2.5, fo, bo,
@@ -411,14 +418,17 @@ def run_gpu(args):
                 h.copy_(c, non_blocking=True)
         consumed[k].record(stream)
 
+    for i in range(max(args.warmup, 2)):                # untimed: both buffers used once
+        e2e_step(i)
     barrier()
     a.record(stream)
     copy_stream.wait_event(a)
     for i in range(args.steps):
-        e2e_step(i)
+        e2e_step(i, timed=True)
     b.record(stream)
     barrier()
     ms_e2e = reduce(a.elapsed_time(b) / args.steps, MAX)
+    ms_h2d = sum(e0.elapsed_time(e1) for e0, e1 in h2d_ev) / args.steps
     if ctx.check() != gfh.GFH_OK or int(off[1].item()) != n_peaks:
         raise RuntimeError("end-to-end steps differ from the direct step")
     h2d = x_host.numel() * 4
@@ -498,9 +508,11 @@ def run_gpu(args):
                              "peak_source": HBM_PEAK_SRC}},
         "e2e": {"value": total_updates / (ms_e2e * 1e-3), "unit": "updates/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e,
-                "timing": "asynchronous public calls; each step's series copied from pinned host "
-                          "memory on a copy stream into one of two device buffers (overlapping the "
-                          "previous step's search) and its candidates read back"},
+                "h2d_ms_per_copy": ms_h2d, "h2d_gbs": h2d / (ms_h2d * 1e-3) / 1e9,
+                "timing": "asynchronous public calls after untimed warm-up steps; each step's "
+                          "series copied from pinned host memory on a copy stream into one of two "
+                          "device buffers (overlapping the previous step's search) and its "
+                          "candidates read back"},
         "squares_selector": squares,
         "gpu_launches": 9 * args.steps,
         "clocks": clocks,
@@ -1230,22 +1242,34 @@ def run_splice(args):
     copy_stream = torch.cuda.Stream()
     copied = [torch.cuda.Event(), torch.cuda.Event()]
     consumed = [torch.cuda.Event(), torch.cuda.Event()]
-    barrier()
-    a.record(stream)
-    copy_stream.wait_event(a)
-    for i in range(args.steps):
+    h2d_ev = [(ev(), ev()) for _ in range(args.steps)]
+
+    def e2e_step(i, timed=False):
         k = i & 1
-        copy_stream.wait_event(consumed[k])
+        copy_stream.wait_event(consumed[k])              # buffer k no longer read
+        if timed:
+            h2d_ev[i][0].record(copy_stream)
         with torch.cuda.stream(copy_stream):
             x_buf[k].copy_(x_host, non_blocking=True)
         copied[k].record(copy_stream)
+        if timed:
+            h2d_ev[i][1].record(copy_stream)
         stream.wait_event(copied[k])
         with torch.cuda.stream(stream):
             step(h2d=True, src=x_buf[k])
         consumed[k].record(stream)
+
+    for i in range(max(args.warmup, 2)):                # untimed: both buffers used once
+        e2e_step(i)
+    barrier()
+    a.record(stream)
+    copy_stream.wait_event(a)
+    for i in range(args.steps):
+        e2e_step(i, timed=True)
     b.record(stream)
     barrier()
     ms_e2e = a.elapsed_time(b) / args.steps
+    ms_h2d = sum(e0.elapsed_time(e1) for e0, e1 in h2d_ev) / args.steps
     # coincidences of the injections between the two portions (top candidate of each band)
     coinc = None
     if len(parts) >= 2:
@@ -1289,7 +1313,12 @@ def run_splice(args):
         "e2e": {"value": total / (ms_e2e * 1e-3), "unit": "updates/s",
                 "h2d_bytes_per_step": series_np.size * 4,
                 "d2h_bytes_per_step": sum(c.numel() for p in parts for c in p["cands"]),
-                "ms_per_step": ms_e2e},
+                "ms_per_step": ms_e2e, "h2d_ms_per_copy": ms_h2d,
+                "h2d_gbs": series_np.size * 4 / (ms_h2d * 1e-3) / 1e9,
+                "timing": "asynchronous public calls after untimed warm-up steps; each step's "
+                          "series copied from pinned host memory on a copy stream into one of two "
+                          "device buffers (overlapping the previous step's search) and its "
+                          "candidates read back"},
         "gpu_launches": (len(parts) * 9 + len(parts[0]["grids"]) * (len(parts) - 1)) * args.steps,
         "clocks": clocks,
     }

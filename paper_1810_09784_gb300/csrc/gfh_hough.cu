@@ -78,22 +78,28 @@ __global__ void k_set_offsets(int64_t* off, int64_t n) {
   if (threadIdx.x == 0) { off[0] = 0; off[1] = n; }
 }
 
-// Interval of peak p on the tile's first row: [A, B1 + 1) in 2^-32 columns, and its per-row shift
-// S.  Returns false (and flags the input) for an out-of-range FFT index or a bin outside the map
-// band, which only an unsorted peak list can put in a tile's range.
-__device__ __forceinline__ bool peak_interval(const MapDev& md, int row0, uint32_t f, int bin,
-                                              uint32_t nfft, unsigned jmax, unsigned int* flag,
-                                              int64_t& A, int64_t& B1, int64_t& S) {
+// Table rows of peak (f, bin): the FFT's base and shift per row, the bin's fixed-point edges.
+// Returns false (and flags the input) for an out-of-range FFT index or a bin outside the map band,
+// which only an unsorted peak list can put in a tile's range; the rows are then not read.
+__device__ __forceinline__ bool peak_rows(const MapDev& md, uint32_t f, int bin, uint32_t nfft,
+                                          unsigned jmax, unsigned int* flag, longlong2& bs,
+                                          longlong2& up) {
   const unsigned jl = (unsigned)(bin - md.bin_lo);
   if (f >= nfft) { atomicOr(flag, GFH_FLAG_FFT_RANGE); return false; }
   if (jl > jmax) { atomicOr(flag, GFH_FLAG_UNSORTED); return false; }
-  const longlong2 bs = __ldg(md.BS + f);
-  const longlong2 up = __ldg(md.UP + jl);
+  bs = __ldg(md.BS + f);
+  up = __ldg(md.UP + jl);
+  return true;
+}
+
+// Interval of a peak on the tile's first row from its table rows: [A, B1 + 1) in 2^-32 columns,
+// and its per-row shift S.
+__device__ __forceinline__ void peak_interval(int row0, const longlong2 bs, const longlong2 up,
+                                              int64_t& A, int64_t& B1, int64_t& S) {
   S = bs.y;
   const int64_t base = bs.x + (int64_t)row0 * S;
   A = up.x - base;        // interval start (upper-f edge)
   B1 = up.y - base - 1;   // interval end - 1 (lower-f edge)
-  return true;
 }
 
 
@@ -223,29 +229,33 @@ __device__ __forceinline__ void hough_tile(const MapDev* __restrict__ maps, cons
     int carry = 0;
     int carry_x[XD ? R : 1] = {};
     // Software pipeline over this thread's peaks p, p + NT, ...: the indices are loaded two
-    // peaks ahead and the table rows one peak ahead of the peak being drawn.
+    // peaks ahead and the table rows one peak ahead of the peak being drawn; the next peak's
+    // interval is formed from its rows after the current peak is drawn, so the loads have the
+    // whole drawing to arrive.
     int64_t p = pb + tid;
     uint32_t f_nx = 0xffffffffu;                 // indices of peak p + NT
     int j_nx = 0;
     int64_t a_cu = 0, b_cu = 0, s_cu = 0;        // interval of peak p
     bool ok_cu = false;
     if (p < pe) {
-      ok_cu = peak_interval(md, t.row0, __ldg(fft_idx + p), (int)__ldg(bins + p), nfft, jmax,
-                            flag, a_cu, b_cu, s_cu);
+      longlong2 bs, up;
+      ok_cu = peak_rows(md, __ldg(fft_idx + p), (int)__ldg(bins + p), nfft, jmax, flag, bs, up);
+      if (ok_cu) peak_interval(t.row0, bs, up, a_cu, b_cu, s_cu);
     }
     if (p + NT < pe) { f_nx = __ldg(fft_idx + p + NT); j_nx = (int)__ldg(bins + p + NT); }
     for (; p < pe; p += NT) {
       uint32_t f_nn = 0xffffffffu;               // indices of peak p + 2 NT
       int j_nn = 0;
       if (p + 2 * NT < pe) { f_nn = __ldg(fft_idx + p + 2 * NT); j_nn = (int)__ldg(bins + p + 2 * NT); }
-      int64_t a_nx = 0, b_nx = 0, s_nx = 0;
+      longlong2 bs_nx = make_longlong2(0, 0), up_nx = make_longlong2(0, 0);
       const bool ok_nx = f_nx != 0xffffffffu &&
-                         peak_interval(md, t.row0, f_nx, j_nx, nfft, jmax, flag, a_nx, b_nx, s_nx);
+                         peak_rows(md, f_nx, j_nx, nfft, jmax, flag, bs_nx, up_nx);
       if (ok_cu) {
         if constexpr (XD) draw_peak_x<R>(G0, lds, a_cu, b_cu, s_cu, c0, c1m1, ub, carry_x);
         else draw_peak<R>(G0, lds, a_cu, b_cu, s_cu, c0, c1m1, ub, carry);
       }
-      a_cu = a_nx; b_cu = b_nx; s_cu = s_nx; ok_cu = ok_nx;
+      peak_interval(t.row0, bs_nx, up_nx, a_cu, b_cu, s_cu);
+      ok_cu = ok_nx;
       f_nx = f_nn; j_nx = j_nn;
     }
     if constexpr (XD) {
