@@ -81,14 +81,15 @@ __global__ void k_set_offsets(int64_t* off, int64_t n) {
 // Table rows of peak (f, bin): the FFT's base and shift per row, the bin's fixed-point edges.
 // Returns false (and flags the input) for an out-of-range FFT index or a bin outside the map band,
 // which only an unsorted peak list can put in a tile's range; the rows are then not read.
-__device__ __forceinline__ bool peak_rows(const MapDev& md, uint32_t f, int bin, uint32_t nfft,
-                                          unsigned jmax, unsigned int* flag, longlong2& bs,
-                                          longlong2& up) {
-  const unsigned jl = (unsigned)(bin - md.bin_lo);
+__device__ __forceinline__ bool peak_rows(const longlong2* __restrict__ BS,
+                                          const longlong2* __restrict__ UP, int bin_lo, uint32_t f,
+                                          int bin, uint32_t nfft, unsigned jmax,
+                                          unsigned int* flag, longlong2& bs, longlong2& up) {
+  const unsigned jl = (unsigned)(bin - bin_lo);
   if (f >= nfft) { atomicOr(flag, GFH_FLAG_FFT_RANGE); return false; }
   if (jl > jmax) { atomicOr(flag, GFH_FLAG_UNSORTED); return false; }
-  bs = __ldg(md.BS + f);
-  up = __ldg(md.UP + jl);
+  bs = __ldg(BS + f);
+  up = __ldg(UP + jl);
   return true;
 }
 
@@ -225,6 +226,9 @@ __device__ __forceinline__ void hough_tile(const MapDev* __restrict__ maps, cons
     const int ub = min(c1m1, wm1);
     const uint32_t nfft = (uint32_t)md.n_fft;
     const unsigned jmax = (unsigned)(md.bin_hi - md.bin_lo);
+    const int bin_lo = md.bin_lo;                // map fields read once, kept in registers
+    const longlong2* const BS = md.BS;
+    const longlong2* const UP = md.UP;
     int* const G0 = G - c0;                      // rows indexed by absolute column
     int carry = 0;
     int carry_x[XD ? R : 1] = {};
@@ -239,7 +243,8 @@ __device__ __forceinline__ void hough_tile(const MapDev* __restrict__ maps, cons
     bool ok_cu = false;
     if (p < pe) {
       longlong2 bs, up;
-      ok_cu = peak_rows(md, __ldg(fft_idx + p), (int)__ldg(bins + p), nfft, jmax, flag, bs, up);
+      ok_cu = peak_rows(BS, UP, bin_lo, __ldg(fft_idx + p), (int)__ldg(bins + p), nfft, jmax, flag,
+                        bs, up);
       if (ok_cu) peak_interval(t.row0, bs, up, a_cu, b_cu, s_cu);
     }
     if (p + NT < pe) { f_nx = __ldg(fft_idx + p + NT); j_nx = (int)__ldg(bins + p + NT); }
@@ -249,7 +254,7 @@ __device__ __forceinline__ void hough_tile(const MapDev* __restrict__ maps, cons
       if (p + 2 * NT < pe) { f_nn = __ldg(fft_idx + p + 2 * NT); j_nn = (int)__ldg(bins + p + 2 * NT); }
       longlong2 bs_nx = make_longlong2(0, 0), up_nx = make_longlong2(0, 0);
       const bool ok_nx = f_nx != 0xffffffffu &&
-                         peak_rows(md, f_nx, j_nx, nfft, jmax, flag, bs_nx, up_nx);
+                         peak_rows(BS, UP, bin_lo, f_nx, j_nx, nfft, jmax, flag, bs_nx, up_nx);
       if (ok_cu) {
         if constexpr (XD) draw_peak_x<R>(G0, lds, a_cu, b_cu, s_cu, c0, c1m1, ub, carry_x);
         else draw_peak<R>(G0, lds, a_cu, b_cu, s_cu, c0, c1m1, ub, carry);
@@ -342,12 +347,13 @@ __device__ __forceinline__ void hough_tile(const MapDev* __restrict__ maps, cons
       for (int q = 0; q < 4; ++q)
         best[q] = cand_key(bc[q], (uint32_t)(t.row0 + br[q]) * W32 + (uint32_t)(t.col0 + col + q));
       // merge equal-band neighbours among the lane's 4 columns, then one shared atomic per run
+      // (at the run's last column; every index static, so the arrays stay in registers)
+      unsigned long long run = 0;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        if (band[q] < 0) continue;
-        unsigned long long k = best[q];
-        while (q + 1 < 4 && band[q + 1] == band[q]) { ++q; k = best[q] > k ? best[q] : k; }
-        atomicMax(&skey[band[q] - t.band_lo], k);
+        run = (q > 0 && band[q] == band[q - 1]) ? (best[q] > run ? best[q] : run) : best[q];
+        const bool last = q == 3 || band[q < 3 ? q + 1 : q] != band[q];
+        if (band[q] >= 0 && last) atomicMax(&skey[band[q] - t.band_lo], run);
       }
     }
   }
