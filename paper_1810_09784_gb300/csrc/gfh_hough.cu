@@ -123,8 +123,26 @@ __device__ __forceinline__ void draw_peak(int* G0, int lds, int64_t a, int64_t b
   // rows 1 .. R-1 (rows past the map's last k row are drawn too: they exist in shared memory
   // and are never stored).  Columns entered: [n1, min(n2, o1 - 1)]; columns left:
   // [max(o1, n2 + 1), o2].  A shift below one column per row enters and leaves at most one
-  // column per row: that common case is branch-free.
-  if (s < (int64_t(1) << GFH_FRAC_BITS)) {
+  // column per row: that common case has no inner loops, and a peak that stays clear of the
+  // tile's and the map's edges on all R rows needs no clamps either.
+  const bool interior = (int)((a - (int64_t)(R - 1) * s) >> GFH_FRAC_BITS) >= c0 &&
+                        (int)(b1 >> GFH_FRAC_BITS) <= ub && a <= b1;
+  if (s < (int64_t(1) << GFH_FRAC_BITS) && interior) {
+    // the interval stays inside the tile and the map on every row (its left edge is lowest on the
+    // last row, its right edge highest on row 0), so no clamp is active: a column is entered
+    // where the left edge moved and left where the right edge moved
+#pragma unroll
+    for (int rr = 1; rr < R; ++rr) {
+      a -= s;
+      b1 -= s;
+      const int n1 = (int)(a >> GFH_FRAC_BITS), n2 = (int)(b1 >> GFH_FRAC_BITS);
+      int* const Gr = G0 + rr * lds;
+      if (n1 < o1) atomicAdd(Gr + n1, 1);
+      if (n2 < o2) atomicAdd(Gr + o2, -1);
+      o1 = n1;
+      o2 = n2;
+    }
+  } else if (s < (int64_t(1) << GFH_FRAC_BITS)) {
 #pragma unroll
     for (int rr = 1; rr < R; ++rr) {
       a -= s;
@@ -296,6 +314,10 @@ __device__ __forceinline__ void hough_tile(const MapDev* __restrict__ maps, cons
   // ---- row 0: running sum along x0; rows r > 0: running sum along k; store; candidates
   long long s1 = 0, s2 = 0;
   const uint32_t W32 = (uint32_t)md.W;
+  // map fields of the store pass read once (a global store could otherwise force a reload)
+  int32_t* const out = md.out + t.col0;
+  const int64_t ld_out = md.ld;
+  const int32_t* const col_band = md.col_band + t.col0;
   for (int ch = warp; ch < nch; ch += NW) {
     const int col = ch * 128 + lane * 4;
     const bool in = col < C;
@@ -304,7 +326,7 @@ __device__ __forceinline__ void hough_tile(const MapDev* __restrict__ maps, cons
     // row reaching the best count wins: the lowest cell index)
     int bc[4] = {-1, -1, -1, -1}, br[4] = {0, 0, 0, 0};
     if (SELECT && in) {
-      const int4 bv = __ldg(reinterpret_cast<const int4*>(md.col_band + t.col0 + col));
+      const int4 bv = __ldg(reinterpret_cast<const int4*>(col_band + col));
       band[0] = bv.x; band[1] = bv.y; band[2] = bv.z; band[3] = bv.w;
     }
     const int cin = XD ? 0 : warp_sum((lane < ch) ? tot[lane] : 0);
@@ -327,7 +349,7 @@ __device__ __forceinline__ void hough_tile(const MapDev* __restrict__ maps, cons
       }
       if (in) {
         const int64_t row = t.row0 + rr;
-        __stcs(reinterpret_cast<int4*>(md.out + row * md.ld + t.col0 + col), v);
+        __stcs(reinterpret_cast<int4*>(out + row * ld_out + col), v);
         if (SELECT) {
           const int vals[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
