@@ -125,8 +125,7 @@ __device__ __forceinline__ void draw_peak(int* G0, int lds, int64_t a, int64_t b
   // [max(o1, n2 + 1), o2].  A shift below one column per row enters and leaves at most one
   // column per row: that common case has no inner loops, and a peak that stays clear of the
   // tile's and the map's edges on all R rows needs no clamps either.
-  const bool interior = (int)((a - (int64_t)(R - 1) * s) >> GFH_FRAC_BITS) >= c0 &&
-                        (int)(b1 >> GFH_FRAC_BITS) <= ub && a <= b1;
+  const bool interior = lo >= c0 + (R - 1) && (int)(b1 >> GFH_FRAC_BITS) <= ub && a <= b1;
   if (s < (int64_t(1) << GFH_FRAC_BITS) && interior) {
     // the interval stays inside the tile and the map on every row (its left edge is lowest on the
     // last row, its right edge highest on row 0), so no clamp is active: a column is entered
