@@ -111,25 +111,18 @@ __device__ __forceinline__ void peak_interval(int row0, const longlong2 bs, cons
 template <int R>
 __device__ __forceinline__ void draw_peak(int* G0, int lds, int64_t a, int64_t b1, int64_t s,
                                           int c0, int c1m1, int ub, int& carry) {
-  // row 0: first / last covered column, clamped to the map's last column and to the tile
+  constexpr int64_t kOne = int64_t(1) << GFH_FRAC_BITS;
   int lo = (int)(a >> GFH_FRAC_BITS);
-  int hi = min((int)(b1 >> GFH_FRAC_BITS), ub);
-  int o1 = max(lo, c0), o2 = hi;
-  if (o1 <= o2) {
-    if (lo < c0) carry += 1;
-    else atomicAdd(G0 + o1, 1);
-    if (hi < c1m1) atomicAdd(G0 + hi + 1, -1);
-  }
-  // rows 1 .. R-1 (rows past the map's last k row are drawn too: they exist in shared memory
-  // and are never stored).  Columns entered: [n1, min(n2, o1 - 1)]; columns left:
-  // [max(o1, n2 + 1), o2].  A shift below one column per row enters and leaves at most one
-  // column per row: that common case has no inner loops, and a peak that stays clear of the
-  // tile's and the map's edges on all R rows needs no clamps either.
-  const bool interior = lo >= c0 + (R - 1) && (int)(b1 >> GFH_FRAC_BITS) <= ub && a <= b1;
-  if (s < (int64_t(1) << GFH_FRAC_BITS) && interior) {
-    // the interval stays inside the tile and the map on every row (its left edge is lowest on the
-    // last row, its right edge highest on row 0), so no clamp is active: a column is entered
-    // where the left edge moved and left where the right edge moved
+  const int hr = (int)(b1 >> GFH_FRAC_BITS);    // row-0 last column before any clamp
+  // A peak that moves less than a column per row, starts at least R - 1 columns right of the
+  // tile's first column and ends before the tile's last column and inside the map stays clear of
+  // every edge on all R rows (its left edge is lowest on the last row, its right edge highest on
+  // row 0): no clamp, no carry, and on rows r > 0 a column is entered where the left edge moved
+  // and left where the right edge moved.
+  if ((s < kOne) & (lo >= c0 + (R - 1)) & (hr <= ub) & (hr < c1m1) & (a <= b1)) {
+    atomicAdd(G0 + lo, 1);
+    atomicAdd(G0 + hr + 1, -1);
+    int o1 = lo, o2 = hr;
 #pragma unroll
     for (int rr = 1; rr < R; ++rr) {
       a -= s;
@@ -141,7 +134,21 @@ __device__ __forceinline__ void draw_peak(int* G0, int lds, int64_t a, int64_t b
       o1 = n1;
       o2 = n2;
     }
-  } else if (s < (int64_t(1) << GFH_FRAC_BITS)) {
+    return;
+  }
+  // row 0: first / last covered column, clamped to the map's last column and to the tile
+  int hi = min(hr, ub);
+  int o1 = max(lo, c0), o2 = hi;
+  if (o1 <= o2) {
+    if (lo < c0) carry += 1;
+    else atomicAdd(G0 + o1, 1);
+    if (hi < c1m1) atomicAdd(G0 + hi + 1, -1);
+  }
+  // rows 1 .. R-1 (rows past the map's last k row are drawn too: they exist in shared memory
+  // and are never stored).  Columns entered: [n1, min(n2, o1 - 1)]; columns left:
+  // [max(o1, n2 + 1), o2].  A shift below one column per row enters and leaves at most one
+  // column per row: that case has no inner loops.
+  if (s < kOne) {
 #pragma unroll
     for (int rr = 1; rr < R; ++rr) {
       a -= s;
