@@ -4,7 +4,7 @@ The paper names machine learning as future work (Sec. VIII).  Here a small convo
 looks at a coarse image of a peakmap and ranks the coarse (x0, k) tiles of its Hough map (Sec. IV),
 so that the exact Hough runs on the best 32 of 64 x 64 tiles only.  Candidates always come from
 exact counts; a map whose proposal leaves more than `tau` probability outside the chosen tiles is
-searched in full instead (the exact Hough is the fallback and the judge of recall).
+searched in full instead (the exact Hough is the fallback and the reference for recall).
 
 Workload: maps shaped like the small plain search (1024 Hz sampling, 1800 s, T_FFT 2 s, 1799 FFTs,
 band 100-400 Hz, 500 k rows), one braking index per map from n = 2.0, 2.1, ..., 7.0 (sample s has
