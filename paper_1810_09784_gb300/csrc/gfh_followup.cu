@@ -108,7 +108,7 @@ __device__ __forceinline__ float2 het_sample(float h, const HetAnchor& A, int m)
 // residue), and thread k adds its output's share W_N^(k r) Y_r[k] (W_N^(k r0) by sincospif once per
 // group, the 32 steps of W_N^k by recurrence).  No FFT of the whole frame is formed.
 template <int J>
-__global__ void __launch_bounds__(J) k_band_dft(const float* __restrict__ h,
+__global__ void __launch_bounds__(J, J == 256 ? 3 : 1) k_band_dft(const float* __restrict__ h,
                                                 const HetAnchor* __restrict__ anchors,
                                                 int span_log2, int log2N, int hop, int n_frames,
                                                 int j0, float2* __restrict__ X) {
@@ -150,7 +150,25 @@ __global__ void __launch_bounds__(J) k_band_dft(const float* __restrict__ h,
 #pragma unroll
       for (int lg = 1; lg <= LOGJ; lg += 2) {
         const int L = 1 << (lg - 1);
-        if (lg + 1 <= LOGJ) {
+        if (lg == 1) {
+          // stages 1 and 2: every twiddle is 1 or -i, so the butterflies need no multiplies
+#pragma unroll
+          for (int it = 0; it < (J / 4) * RG / J; ++it) {
+            const int e = tid + it * J;
+            const int i0 = (e >> 5) << 2, rl = e & 31;
+            const float2 a0 = tile[i0 * LD + rl], a1 = tile[(i0 + 1) * LD + rl];
+            const float2 a2 = tile[(i0 + 2) * LD + rl], a3 = tile[(i0 + 3) * LD + rl];
+            const float2 s0 = make_float2(a0.x + a1.x, a0.y + a1.y);
+            const float2 d0 = make_float2(a0.x - a1.x, a0.y - a1.y);
+            const float2 s1 = make_float2(a2.x + a3.x, a2.y + a3.y);
+            const float2 d1 = make_float2(a2.x - a3.x, a2.y - a3.y);
+            const float2 v = make_float2(d1.y, -d1.x);           // d1 times -i
+            tile[i0 * LD + rl] = make_float2(s0.x + s1.x, s0.y + s1.y);
+            tile[(i0 + 2) * LD + rl] = make_float2(s0.x - s1.x, s0.y - s1.y);
+            tile[(i0 + 1) * LD + rl] = make_float2(d0.x + v.x, d0.y + v.y);
+            tile[(i0 + 3) * LD + rl] = make_float2(d0.x - v.x, d0.y - v.y);
+          }
+        } else if (lg + 1 <= LOGJ) {
 #pragma unroll
           for (int it = 0; it < (J / 4) * RG / J; ++it) {
             const int e = tid + it * J;
