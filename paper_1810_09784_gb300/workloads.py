@@ -176,19 +176,9 @@ def followup_fields(inj, t_obs: float, t_fft: float, half_band: float = 5.0, n_k
 P0_THETA_2_5 = 0.0755      # noise peak probability of a strict local maximum above 2.5 (exp(1) power)
 
 
-def uneven(seed: int = 4, n_maps: int = 256, hours=(1.0, 24.0), width_hz=(20.0, 1950.0),
-           n_k: int = 1000, p_track: float = 0.6):
-    """Independent peakmaps of uneven size (statistical peakmap model, no time series): duration
-    log-uniform in `hours`, T_FFT in {1, 2, 4, 8} s, a band of log-uniform width inside 50-2000 Hz,
-    0-3 power-law injections (n in [2, 7], |fdot0| log-uniform up to 1/T_FFT^2).  Each peakmap is
-    searched in 100 Hz analysis bands (peakmap band 50 Hz wider, capped at the band top) at the
-    braking index of its first injection (else uniform in [2, 7]) with `n_k` k rows.
-
-    Returns (lists, grids, truth): lists[l] = (fft_idx, bin); grids[m]['list'] = its peakmap.
-    """
-    import concurrent.futures
-    import os
-
+def uneven_specs(seed: int = 4, n_maps: int = 256, hours=(1.0, 24.0), width_hz=(20.0, 1950.0)):
+    """The peakmaps of `uneven` (no peaks yet): per peakmap its duration, T_FFT, band, injections
+    (f0, k, n) and the braking index it is searched at, each drawn from its own seeded stream."""
     specs = []
     for m in range(n_maps):
         rng = np.random.Generator(np.random.PCG64(seed * 100003 + m))
@@ -209,15 +199,12 @@ def uneven(seed: int = 4, n_maps: int = 256, hours=(1.0, 24.0), width_hz=(20.0, 
         n_hough = injs[0][2] if injs else rng.uniform(2.0, 7.0)
         specs.append(dict(t_obs=t_obs, t_fft=t_fft, df=df, n_fft=n_fft, bin_lo=bin_lo, bin_hi=bin_hi,
                           f_lo=bin_lo * df, f_hi=(bin_hi + 1) * df, injs=injs, n=n_hough, seed=seed * 100003 + m))
+    return specs
 
-    def make_list(s):
-        tracks = [synth.powerlaw_track(f0, k, n, s["df"], s["n_fft"], s["t_fft"] / 2, s["t_fft"] / 2)
-                  for f0, k, n in s["injs"]]
-        return synth.statistical_peaklist(s["n_fft"], s["bin_lo"], s["bin_hi"], P0_THETA_2_5,
-                                          s["seed"], tracks, p_track)
 
-    with concurrent.futures.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
-        lists = list(ex.map(make_list, specs))
+def uneven_grids(specs, n_k: int = 1000):
+    """Grid requests of the `uneven` peakmaps: 100 Hz analysis bands, each with its peakmap band
+    50 Hz wider (capped at the peakmap's top); grids[m]['list'] = its peakmap."""
     grids = []
     for l, s in enumerate(specs):
         a = s["f_lo"]
@@ -232,4 +219,30 @@ def uneven(seed: int = 4, n_maps: int = 256, hours=(1.0, 24.0), width_hz=(20.0, 
                                   n_k=n_k, k_min=0.0, dk=0.0, f_max=0.0, ana_lo=a, ana_hi=b,
                                   band_hz=1.0, list=l))
             a = b
-    return lists, grids, specs
+    return grids
+
+
+def uneven(seed: int = 4, n_maps: int = 256, hours=(1.0, 24.0), width_hz=(20.0, 1950.0),
+           n_k: int = 1000, p_track: float = 0.6):
+    """Independent peakmaps of uneven size (statistical peakmap model, no time series): duration
+    log-uniform in `hours`, T_FFT in {1, 2, 4, 8} s, a band of log-uniform width inside 50-2000 Hz,
+    0-3 power-law injections (n in [2, 7], |fdot0| log-uniform up to 1/T_FFT^2).  Each peakmap is
+    searched in 100 Hz analysis bands (peakmap band 50 Hz wider, capped at the band top) at the
+    braking index of its first injection (else uniform in [2, 7]) with `n_k` k rows.
+
+    Returns (lists, grids, truth): lists[l] = (fft_idx, bin); grids[m]['list'] = its peakmap.
+    """
+    import concurrent.futures
+    import os
+
+    specs = uneven_specs(seed, n_maps, hours, width_hz)
+
+    def make_list(s):
+        tracks = [synth.powerlaw_track(f0, k, n, s["df"], s["n_fft"], s["t_fft"] / 2, s["t_fft"] / 2)
+                  for f0, k, n in s["injs"]]
+        return synth.statistical_peaklist(s["n_fft"], s["bin_lo"], s["bin_hi"], P0_THETA_2_5,
+                                          s["seed"], tracks, p_track)
+
+    with concurrent.futures.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        lists = list(ex.map(make_list, specs))
+    return lists, uneven_grids(specs, n_k), specs
