@@ -3,7 +3,6 @@ handle and out-of-range sizes with GFH_ERR_ARG before touching the device; the h
 reject invalid grids."""
 import ctypes
 
-import numpy as np
 import pytest
 
 

@@ -1,5 +1,4 @@
 """GPU parity of the Hough map and candidates against the oracle, through the C ABI."""
-import dataclasses
 
 import numpy as np
 import pytest

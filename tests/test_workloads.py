@@ -2,7 +2,6 @@
 parameter ranges of the plain, batched-n, follow-up and uneven workloads.  The k step of the one
 injection placed on a chosen row is checked against the oracle's own grid."""
 import dataclasses
-import math
 
 import numpy as np
 import pytest
