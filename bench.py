@@ -604,7 +604,7 @@ def run_gpu_lists(args):
                 h.copy_(c, non_blocking=True)
         b_.record(stream)
         torch.cuda.synchronize()
-        ms_e2e = a.elapsed_time(b_) / args.steps
+        ms_e2e = ranks.combine(a.elapsed_time(b_) / args.steps, 0.0, device="cuda")[0]
         # one plan per peakmap, executed one after another
         per_list = {}
         for gf, g, m, c in zip(grid_fields, grids, maps, cands):
@@ -1012,7 +1012,7 @@ def run_followup(args):
                 s_[7].cpu()
         b.record(stream)
         barrier()
-        ms_e2e = a.elapsed_time(b) / args.steps
+        ms_e2e = ranks.combine(a.elapsed_time(b) / args.steps, 0.0, device="cuda")[0]
     if rank != 0:
         ctx.close()
         return
@@ -1268,7 +1268,7 @@ def run_splice(args):
         e2e_step(i, timed=True)
     b.record(stream)
     barrier()
-    ms_e2e = a.elapsed_time(b) / args.steps
+    ms_e2e = ranks.combine(a.elapsed_time(b) / args.steps, 0.0, device="cuda")[0]
     ms_h2d = sum(e0.elapsed_time(e1) for e0, e1 in h2d_ev) / args.steps
     # coincidences of the injections between the two portions (top candidate of each band)
     coinc = None
