@@ -14,10 +14,12 @@ What is written here is the plain definition of each step:
   conv3x3    out[b, y, x, o] = bias[o] + sum_{dy, dx, c} in[b, yS + dy - 1, xS + dx - 1, c] W[o, dy, dx, c]
              (zero outside the image), followed by ReLU; its input gradient and weight gradient are
              the adjoints of that linear map
-  pool       mean over the 64 rows of the last activation (time axis)
+  pool       mean over the 64 rows of the last activation (time axis); its adjoint spreads
+             d pooled / 64 over those rows
   head       logits[b, kt * F + f] = bh[kt] + sum_{d, c} WH[kt, d, c] pooled[b, f + d - 1, c], and
              one no-signal logit = bnull
   loss       mean softmax cross-entropy
+  head grads the adjoints of the head (a linear map) in its weights, biases and input
   AdamW      m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2; w -= lr (m/c1 / (sqrt(v/c2) + eps) + wd w)
   proposal   p = softmax(logits); class (d, xt) spreads p evenly over k tiles
              [floor(d gb), max(lo, ceil((d+1) ga) - 1)] (clamped to 63); tiles ranked by score, ties
@@ -165,6 +167,31 @@ def head(pooled: np.ndarray, WH: np.ndarray, bH: np.ndarray, bnull: float) -> np
     return np.concatenate([out.reshape(B, TILES * F), np.full((B, 1), float(bnull))], axis=1)
 
 
+def pool(a5: np.ndarray) -> np.ndarray:
+    """Mean over the time axis of the last activation [B, T, F, C] -> [B, F, C]."""
+    return a5.mean(axis=1)
+
+
+def pool_grad(dpooled: np.ndarray, T: int) -> np.ndarray:
+    """Adjoint of pool: every time row of [B, T, F, C] receives dpooled / T."""
+    return np.repeat((dpooled / T)[:, None, :, :], T, axis=1)
+
+
+def head_grads(dl: np.ndarray, pooled: np.ndarray, WH: np.ndarray):
+    """Adjoint of head in its parameters and its input, from d(loss)/d logits [B, TILES * F + 1]:
+    (dWH [TILES, 3, 64], dbH [TILES], dbnull [1], dpooled [B, F, 64])."""
+    B, F, _ = pooled.shape
+    dt = dl[:, :TILES * F].reshape(B, TILES, F)
+    pp = np.pad(pooled, ((0, 0), (1, 1), (0, 0)))
+    dWH = np.stack([np.einsum("bkf,bfc->kc", dt, pp[:, d:d + F, :]) for d in range(3)], axis=1)
+    dbH = dt.sum(axis=(0, 2))
+    dbnull = np.array([dl[:, TILES * F].sum()])
+    dpp = np.zeros((B, F + 2, 64))
+    for d in range(3):                       # tap d of logit f reads pooled row f + d - 1
+        dpp[:, d:d + F, :] += np.einsum("bkf,kc->bfc", dt, WH[:, d, :])
+    return dWH, dbH, dbnull, dpp[:, 1:F + 1, :]
+
+
 def softmax_ce(logits: np.ndarray, labels: np.ndarray):
     """Per-sample losses and d(mean loss)/d logits."""
     B = logits.shape[0]
@@ -190,7 +217,7 @@ def forward(params: np.ndarray, images: np.ndarray, mirror: bool = True) -> dict
             W = bf16(W)                                 # the layers run on bf16 weight copies
         pre = conv3x3(acts[-1], W, STRIDE[l]) + P[f"b{l + 1}"]
         acts.append(rnd(np.maximum(pre, 0.0)))
-    pooled = acts[5].mean(axis=1)
+    pooled = pool(acts[5])
     logits = head(pooled, P["WH"], P["bH"], P["bnull"][0])
     return {"P": P, "acts": acts, "pooled": pooled, "logits": logits, "mirror": mirror}
 
@@ -200,19 +227,9 @@ def backward(cache: dict, labels: np.ndarray):
     P, acts, pooled, mirror = cache["P"], cache["acts"], cache["pooled"], cache["mirror"]
     rnd = bf16 if mirror else (lambda v: v)
     loss, dl = softmax_ce(cache["logits"], labels)
-    B, F, _ = pooled.shape
     g = {}
-    dt = dl[:, :TILES * F].reshape(B, TILES, F)
-    pp = np.pad(pooled, ((0, 0), (1, 1), (0, 0)))
-    g["WH"] = np.stack([np.einsum("bkf,bfc->kc", dt, pp[:, d:d + F, :]) for d in range(3)], axis=1)
-    g["bH"] = dt.sum(axis=(0, 2))
-    g["bnull"] = np.array([dl[:, TILES * F].sum()])
-    dpool = np.zeros((B, F + 2, 64))
-    for d in range(3):                                  # adjoint of the head in pooled
-        dpool[:, d:d + F, :] += np.einsum("bkf,kc->bfc", dt, P["WH"][:, d, :])
-    dpool = dpool[:, 1:F + 1, :]
-    T = acts[5].shape[1]
-    da = rnd(np.repeat((dpool / T)[:, None, :, :], T, axis=1))
+    g["WH"], g["bH"], g["bnull"], dpool = head_grads(dl, pooled, P["WH"])
+    da = rnd(pool_grad(dpool, acts[5].shape[1]))
     for l in range(4, -1, -1):
         G = da * (acts[l + 1] > 0)
         g[f"W{l + 1}"] = conv3x3_weight_grad(G, acts[l], STRIDE[l])

@@ -212,3 +212,34 @@ def test_labels_follow_the_drift_and_gains_cover_the_true_row():
         assert drift >= lin * (1 - n * u / 2) - 1e-9, (b, lin, drift, u)
         checked += 1
     assert checked > 150
+
+
+def test_head_grads_and_pool_grad_are_adjoints():
+    """The head is bilinear in (weights, input) plus biases, and the pool is linear: their
+    gradients are fixed by <L x, y> = <x, L* y> for each argument on its own.  A transposed tap,
+    a dropped bias or a wrong 1/T would break one of these identities."""
+    rng = np.random.default_rng(21)
+    B, F = 3, 7
+    pooled = rng.standard_normal((B, F, 64))
+    WH = rng.standard_normal((64, 3, 64))
+    bH = rng.standard_normal(64)
+    dl = rng.standard_normal((B, 64 * F + 1))
+    dWH, dbH, dbnull, dpooled = C.head_grads(dl, pooled, WH)
+    z = np.zeros(64)
+    lin_in = C.head(pooled, WH, z, 0.0)                    # linear in pooled for fixed WH
+    assert math.isclose(float((lin_in * dl).sum()), float((pooled * dpooled).sum()), rel_tol=1e-11)
+    assert math.isclose(float((lin_in * dl).sum()), float((WH * dWH).sum()), rel_tol=1e-11)
+    only_b = C.head(np.zeros_like(pooled), WH, bH, 0.7)
+    assert math.isclose(float((only_b[:, :-1] * dl[:, :-1]).sum()), float(bH @ dbH), rel_tol=1e-11)
+    assert math.isclose(float(only_b[:, -1] @ dl[:, -1]), 0.7 * float(dbnull[0]), rel_tol=1e-11)
+    # edge taps: logit f = 0 reads no row -1, logit F - 1 no row F
+    one = np.zeros_like(dl)
+    one[0, 5 * F + 0] = 1.0
+    _, _, _, dp = C.head_grads(one, pooled, WH)
+    assert np.array_equal(dp[0, 0], WH[5, 1]) and np.array_equal(dp[0, 1], WH[5, 2])
+    assert np.all(dp[0, 2:] == 0) and np.all(dp[1:] == 0)
+    a = rng.standard_normal((B, 11, F, 64))
+    dp2 = rng.standard_normal((B, F, 64))
+    assert math.isclose(float((C.pool(a) * dp2).sum()), float((a * C.pool_grad(dp2, 11)).sum()),
+                        rel_tol=1e-11)
+    np.testing.assert_allclose(C.pool(a), a.sum(axis=1) / 11, rtol=1e-13)
