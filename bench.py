@@ -36,10 +36,29 @@ PEAKS = json.loads((ROOT / "MEASURED_PEAKS.json").read_text()) if (ROOT / "MEASU
 HBM_PEAK = PEAKS.get("hbm_gbs", 6800.0)
 HBM_PEAK_SRC = "measured" if "hbm_gbs" in PEAKS else "fallback"
 SM_MAX_MHZ = PEAKS.get("sm_max_mhz", 2070.0)
-# Shared-memory atomic peak (no MEASURED_PEAKS entry exists): 152 SMs x 16 conflict-free 32-bit
-# shared atomics per clock (one warp instruction every two clocks over 32 banks) x max SM clock.
-N_SM = 152
-SMEM_ATOMIC_PEAK = N_SM * 16 * SM_MAX_MHZ * 1e6 / 1e9      # G atomics / s
+# Shared-memory atomic peak: measured on this GPU by the library's probe kernel (conflict-free
+# 32-bit atomicAdd, every SM busy) before the timed steps; MEASURED_PEAKS has no such entry.
+_ATOMIC_PROBE = {}
+
+
+def atomic_peak(ctx, stream):
+    """(peak G atomics/s, probe record): the conflict-free rate measured once per process."""
+    if "rec" not in _ATOMIC_PROBE:
+        _ATOMIC_PROBE["rec"] = measure_smem_atomics(ctx, stream)
+    rec = _ATOMIC_PROBE["rec"]
+    return rec["conflict_free"]["gatomic_s"], rec
+
+
+def atomic_roofline(ctx, stream, achieved):
+    peak, rec = atomic_peak(ctx, stream)
+    return {"bound": "smem_atomic", "kernel": "k_hough", "achieved": achieved, "peak": peak,
+            "unit": "Gatomic/s", "frac": achieved / peak,
+            "peak_source": (f"measured: conflict-free shared atomicAdd over all {rec['sms']} SMs "
+                            f"(library probe, CUDA events), "
+                            f"{rec['conflict_free']['atomics_per_clk_per_sm']:.2f}/clk/SM at "
+                            f"{rec['clocks'].get('sm_mhz')} MHz"),
+            "probe": rec,
+            "algorithmic": "2 shared atomics per update (differential +1/-1)"}
 
 
 def parse():
@@ -140,6 +159,39 @@ class ClockSampler:
                 "sm_max_mhz": float(rows[0][2]) if rows[0][2].replace(".", "").isdigit() else None,
                 "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit()) if rows else None,
                 "samples": len(rows), "reasons": reasons}
+
+
+def measure_smem_atomics(ctx, stream, reps=3, iters=16384, threads=1024):
+    """Shared-memory atomicAdd throughput of this GPU (gfh_probe_smem_atomics), every mode timed
+    with CUDA events on the library's stream, best of `reps`; the SM count is read from the device
+    and the SM clocks sampled while the probe runs."""
+    import torch
+    sms = ctx.sms()
+    blocks = 2 * sms                                   # 2048 threads per SM
+    cycles = torch.zeros(blocks, dtype=torch.int64, device="cuda")
+    sink = torch.zeros(blocks, dtype=torch.int32, device="cuda")
+    out = {"sms": sms, "blocks": blocks, "threads": threads, "iters_per_thread": iters}
+    sampler = ClockSampler(torch.cuda.current_device())
+    with sampler, torch.cuda.stream(stream):
+        for mode, name in ((0, "conflict_free"), (1, "same_address"), (2, "random")):
+            best = None
+            for r in range(reps + 1):
+                sink.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                ctx.probe_smem_atomics(mode, blocks, threads, iters, cycles, sink)
+                b.record(stream)
+                b.synchronize()
+                if not bool((sink == threads * iters).all()):
+                    raise RuntimeError("shared-atomic probe lost updates")
+                ms = a.elapsed_time(b)
+                if r > 0 and (best is None or ms < best[0]):
+                    best = (ms, float(cycles.max().item()))
+            n = float(blocks) * threads * iters
+            out[name] = {"gatomic_s": n / (best[0] * 1e-3) / 1e9,
+                         "atomics_per_clk_per_sm": n / sms / best[1]}
+    out["clocks"] = sampler.summary()
+    return out
 
 
 def traffic_for(kernel):
@@ -498,10 +550,7 @@ def run_gpu(args):
                    "plan_build_s": round(t_plan, 3), "autotune_s": round(t_tune, 3)},
         "breakdown_ms": {"step_graph": ms_graph, "step_direct": ms_direct, "hough_select": ms_hough,
                          "peakmap_and_host": ms_direct - ms_hough},
-        "roofline": {"bound": "smem_atomic", "kernel": "k_hough", "achieved": achieved,
-                     "peak": SMEM_ATOMIC_PEAK, "unit": "Gatomic/s", "frac": achieved / SMEM_ATOMIC_PEAK,
-                     "peak_source": "derived: 152 SMs x 16 shared atomics/clk x max SM clock",
-                     "algorithmic": "2 shared atomics per update (differential +1/-1)",
+        "roofline": {**atomic_roofline(ctx, stream, achieved),
                      "traffic": traffic_for("k_hough") if args.workload == "plain_paper" and not args.maps else None,
                      "hbm": {"map_store_bytes": map_bytes, "achieved_gbs": map_bytes / (ms_hough * 1e-3) / 1e9,
                              "peak_gbs": HBM_PEAK, "frac": map_bytes / (ms_hough * 1e-3) / 1e9 / HBM_PEAK,
@@ -641,10 +690,7 @@ def run_gpu_lists(args):
                        "l2": "inputs larger than L2 (%d MB of peaks, %d MB of maps)" % (off_np[-1] * 8 // 1000000, map_bytes // 1000000),
                        "tile": list(tile) if tile else "default", "timing": "CUDA graph" if graph is not None else "direct",
                        "generate_s": round(t_gen, 2), "plan_build_s": round(t_plan, 2)},
-            "roofline": {"bound": "smem_atomic", "kernel": "k_hough", "achieved": achieved,
-                         "peak": SMEM_ATOMIC_PEAK, "unit": "Gatomic/s", "frac": achieved / SMEM_ATOMIC_PEAK,
-                         "peak_source": "derived: 152 SMs x 16 shared atomics/clk x max SM clock",
-                         "algorithmic": "2 shared atomics per update (differential +1/-1)", "traffic": None,
+            "roofline": {**atomic_roofline(ctx, stream, achieved), "traffic": None,
                          "hbm": {"map_store_bytes": map_bytes, "achieved_gbs": map_bytes / (ms * 1e-3) / 1e9,
                                  "peak_gbs": HBM_PEAK, "frac": map_bytes / (ms * 1e-3) / 1e9 / HBM_PEAK}},
             "e2e": {"value": total / (ms_e2e * 1e-3), "unit": "updates/s",
@@ -1026,7 +1072,7 @@ def run_followup(args):
     flops_frame = P * (J // 2) * int(math.log2(J)) * 10 + P * J * 8
     frames = (series_np.size - N) // (N // 2) + 1
     achieved = flops_frame * frames / (ms_band * 1e-3) / 1e12
-    fp32_peak = N_SM * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    fp32_peak = ctx.sms() * 128 * 2 * SM_MAX_MHZ * 1e6 / 1e12
     recovered = sum(1 for r in results if abs(r[2] - r[3].f0 + 0.3 * spec.df) < 1.0 and r[1] > 5.0)
     line = {
         "metric": "candidate follow-ups/s", "value": value, "unit": "candidates/s",
@@ -1051,7 +1097,7 @@ def run_followup(args):
                                                   "algorithmic": "12 bytes per sample"}},
         "roofline": {"bound": "alu", "kernel": "k_band_dft", "achieved": achieved, "peak": fp32_peak,
                      "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                     "peak_source": "derived: 152 SMs x 128 fp32 FMA/clk x 2 flops x max SM clock",
+                     "peak_source": "derived: device SM count x 128 fp32 FMA/clk x 2 flops x max SM clock",
                      "algorithmic": f"{flops_frame} flops per {N}-sample frame ({J} bins), {frames} frames; "
                                     "the timed call also holds the anchor pass and the band peak search",
                      "traffic": None},
@@ -1305,10 +1351,7 @@ def run_splice(args):
                          % (sum(g.n_k * g.ld_x0 * 4 for p in parts for g in p["grids"]) // 1000000),
                    "timing": "direct calls"},
         "breakdown_ms": {"step": ms, "hough_select": ms_hough, "rest": ms - ms_hough},
-        "roofline": {"bound": "smem_atomic", "kernel": "k_hough", "achieved": achieved,
-                     "peak": SMEM_ATOMIC_PEAK, "unit": "Gatomic/s", "frac": achieved / SMEM_ATOMIC_PEAK,
-                     "peak_source": "derived: 152 SMs x 16 shared atomics/clk x max SM clock",
-                     "algorithmic": "2 shared atomics per update (differential +1/-1)", "traffic": None},
+        "roofline": {**atomic_roofline(ctx, stream, achieved), "traffic": None},
         "coincidences": coinc,
         "e2e": {"value": total / (ms_e2e * 1e-3), "unit": "updates/s",
                 "h2d_bytes_per_step": series_np.size * 4,

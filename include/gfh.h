@@ -475,6 +475,39 @@ int gfh_cnn_train_step(gfh_cnn* net, const void* d_images, const int32_t* d_labe
                        float lr, float weight_decay, float* h_loss);
 
 /*
+ * Training state for checkpoint and resume: the fp32 parameters, the AdamW first and second
+ * moments (gfh_cnn_param_count entries each, host arrays) and the number of AdamW steps taken (the
+ * bias corrections depend on it).  get: any pointer may be NULL; synchronises.  set: all three
+ * arrays required; refreshes the bf16 weight copies; synchronises.  Resuming from a saved state
+ * and taking the same batches gives bit-identical parameters to never having stopped.
+ */
+int gfh_cnn_get_state(gfh_cnn* net, float* h_params, float* h_m, float* h_v, int64_t* h_step);
+int gfh_cnn_set_state(gfh_cnn* net, const float* h_params, const float* h_m, const float* h_v,
+                      int64_t step);
+
+/*
+ * Copy of one internal tensor of the last forward (and backward) pass to the host, for checking
+ * each stage on its own; synchronises.  which:
+ *   GFH_CNN_ACT + l (l = 1..5)    activation after layer l, bf16 NHWC [batch][h][h][c]
+ *                                 (h = 256, 128, 128, 64, 64; c = 32, 32, 64, 64, 64)
+ *   GFH_CNN_DACT + l (l = 1..5)   gradient of the mean loss in that activation, bf16, same shape
+ *   GFH_CNN_WBF16 + l (l = 0..4)  bf16 copy of the weights of layer l + 1, [cout][3][3][cin]
+ *   GFH_CNN_POOLED                fp32 [batch][64 f][64 c], mean of activation 5 over its 64 rows
+ *   GFH_CNN_LOGITS, GFH_CNN_DLOGITS   fp32 [batch][4097]: logits, d(mean loss)/d logits
+ *   GFH_CNN_LOSS                  fp32 [batch] per-image cross-entropy
+ * bytes = size of h_out; GFH_ERR_SIZE when it is too small, GFH_ERR_ARG for an unknown tensor or
+ * a batch outside [1, max_batch].  Values past the last pass's batch are stale.
+ */
+#define GFH_CNN_ACT 0
+#define GFH_CNN_DACT 10
+#define GFH_CNN_WBF16 20
+#define GFH_CNN_POOLED 30
+#define GFH_CNN_LOGITS 31
+#define GFH_CNN_DLOGITS 32
+#define GFH_CNN_LOSS 33
+int gfh_cnn_read_tensor(gfh_cnn* net, int32_t which, int32_t batch, void* h_out, int64_t bytes);
+
+/*
  * Coarse-tile proposals from logits [batch][4097]: p = softmax(logits); class (d, xt) spreads p
  * evenly over k tiles kt in [floor(d gb), max(lo, ceil((d + 1) ga) - 1)] (both clamped to 63),
  * with d_gain [batch][64][2] = (ga, gb) = ((f_max / f_a)^n, (f_max / f_b)^n) for x0 tile xt over
@@ -489,10 +522,26 @@ int gfh_propose_tiles(gfh_ctx* ctx, const float* d_logits, int32_t batch, const 
                       int32_t k, float tau, int32_t* d_top, float* d_resid, int32_t* d_full);
 
 /*
+ * Non-learned proposer (the baseline the network is judged against): straight-line sums over
+ * channel 0 of images d_images [batch][256][256][2] (as made by gfh_peaks_to_images for a band of
+ * n_bins >= 256 bins equal to the analysis band, maps of n_k k rows).  Class (d, xt) is a track
+ * starting in x0 tile xt (image columns 4 xt .. 4 xt + 3) that drifts (d + 1/2) n_k / 64 bins over
+ * the observation: in time bin tb it lies off = floor(((2d + 1)(2tb + 1) n_k + 128 n_bins) /
+ * (256 n_bins)) columns left of its start.  d_scores [batch][4096] (may be NULL) = the largest
+ * over the four start columns of the sum over tb of the pixels on that line (pixels left of column
+ * 0 add nothing); the sums are exact.  d_logits [batch][4097]: beta (score - mean) / std over the
+ * image's scores (0 when they are all equal), and null_logit for the no-signal class, ready for
+ * gfh_propose_tiles.  Asynchronous.
+ */
+int gfh_line_scores(gfh_ctx* ctx, const void* d_images, int32_t batch, int32_t n_k, int32_t n_bins,
+                    float beta, float null_logit, float* d_scores, float* d_logits);
+
+/*
  * One 3x3 layer alone (tests): mode 0 forward out = relu(conv(in) + bias) into d_res (bf16 NHWC);
  * mode 1 input gradient into d_res (bf16) from d_dout masked by d_out > 0; mode 2 weight gradient
  * added into d_res (fp32 [cout][3][3][cin]) and bias gradient added into d_db.  (cin, cout, stride)
- * is one of (32, 32, 2), (32, 64, 1), (64, 64, 2), (64, 64, 1); h = input height = width.
+ * is one of (2, 32, 1) (the first layer: modes 0 and 2 only), (32, 32, 2), (32, 64, 1),
+ * (64, 64, 2), (64, 64, 1); h = input height = width, a multiple of 16.
  */
 int gfh_conv3x3(gfh_ctx* ctx, int32_t mode, int32_t cin, int32_t cout, int32_t stride,
                 int32_t batch, int32_t h, const void* d_in, const void* d_w, const float* d_bias,
@@ -530,6 +579,20 @@ int gfh_plan_execute_tiles(gfh_plan* plan, const gfh_peaks* peaks, const int32_t
  * the context stays usable.  Asynchronous.  cycles <= 4e9.
  */
 int gfh_wait_check(gfh_ctx* ctx, int64_t cycles);
+
+/*
+ * Measurement of the accumulator's roofline denominator: shared-memory atomicAdd throughput.
+ * `blocks` blocks of `threads` threads each issue `iters` (a multiple of 4) 32-bit atomic adds of 1
+ * to shared memory, cycling over four words per thread: mode 0 one word per bank per warp
+ * (conflict-free), mode 1 one word per warp (all lanes the same address), mode 2 pseudo-random
+ * words of a 32 KB array.  d_cycles [blocks] receives each block's elapsed SM cycles (clock64)
+ * and d_sink [blocks] (zeroed by the caller) the sum of its array, blocks * threads * iters / blocks
+ * per block.  The caller times the launch (CUDA events on the context's stream) for atomics per
+ * second.  Asynchronous.  gfh_device_sms: the SM count of the context's device.
+ */
+int gfh_probe_smem_atomics(gfh_ctx* ctx, int32_t mode, int32_t blocks, int32_t threads,
+                           int32_t iters, long long* d_cycles, int32_t* d_sink);
+int gfh_device_sms(gfh_ctx* ctx, int32_t* h_sms);
 
 /* ---- allocation-free entry point -------------------------------------------------------------
  *

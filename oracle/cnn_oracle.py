@@ -21,6 +21,9 @@ What is written here is the plain definition of each step:
   loss       mean softmax cross-entropy
   head grads the adjoints of the head (a linear map) in its weights, biases and input
   AdamW      m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2; w -= lr (m/c1 / (sqrt(v/c2) + eps) + wd w)
+  lines      the non-learned proposer: per class the pixel sum along the straight line of its
+             mid drift from each of the x0 tile's start columns, the best start kept; logits =
+             beta times the standardised sums
   proposal   p = softmax(logits); class (d, xt) spreads p evenly over k tiles
              [floor(d gb), max(lo, ceil((d+1) ga) - 1)] (clamped to 63); tiles ranked by score, ties
              to the lower id; the first n leave resid_n = max(0, 1 - p_null - their sum); with
@@ -248,6 +251,38 @@ def adamw(w, g, m, v, step: int, lr: float, wd: float, b1=0.9, b2=0.999, eps=1e-
     c2 = 1 - b2 ** step
     w = w - lr * ((m / c1) / (np.sqrt(v / c2) + eps) + wd * w)
     return w, m, v
+
+
+# ---- the non-learned proposer -------------------------------------------------------------------
+
+def line_scores(ch0: np.ndarray, K: int, nb: int) -> np.ndarray:
+    """Straight-line sums of one image's channel 0 values [256 t][256 f] per class d * 64 + xt: a
+    track starting in image columns 4 xt .. 4 xt + 3 at t0 and drifting (d + 1/2) K / 64 bins over
+    the observation sits, in time bin tb (centre (tb + 1/2) / 256 of the observation),
+    (d + 1/2) (K / 64) (256 / nb) (tb + 1/2) / 256 columns left of its start, rounded to nearest
+    (halves up); the score is the best of the four start columns; columns left of 0 add nothing."""
+    img = np.asarray(ch0, np.float64)
+    out = np.zeros(TILES * TILES)
+    tb = np.arange(256)
+    for d in range(TILES):
+        off = ((2 * d + 1) * (2 * tb + 1) * K + 128 * nb) // (256 * nb)
+        for xt in range(TILES):
+            best = None
+            for c0 in range(4 * xt, 4 * xt + 4):
+                c = c0 - off
+                s = float(img[tb[c >= 0], c[c >= 0]].sum())
+                best = s if best is None else max(best, s)
+            out[d * TILES + xt] = best
+    return out
+
+
+def heuristic_logits(scores: np.ndarray, beta: float, null_logit: float) -> np.ndarray:
+    """beta (score - mean) / std over the 4096 scores (population std; 0 if constant), then the
+    no-signal logit."""
+    s = np.asarray(scores, np.float64)
+    sd = s.std()
+    z = (s - s.mean()) / sd if sd > 0 else np.zeros_like(s)
+    return np.concatenate([beta * z, [null_logit]])
 
 
 # ---- proposals ---------------------------------------------------------------------------------

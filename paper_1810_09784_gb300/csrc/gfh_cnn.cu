@@ -245,6 +245,83 @@ __global__ void __launch_bounds__(1024) k_propose(const float* __restrict__ logi
         q < n_keep ? (int32_t)(0xffffu - (uint32_t)(key[q] & 0xffffull)) : -1;
 }
 
+// Non-learned proposer: straight-line sums over channel 0 of an image.  Class (d, xt) is a track
+// that starts (t = t0) in x0 tile xt, i.e. image columns 4 xt .. 4 xt + 3 when the image band is
+// the analysis band, and drifts (d + 1/2) K / 64 bins over the observation; in time bin tb it
+// sits off(d, tb) = round((2d + 1)(2tb + 1) K / (256 nb)) image columns left of its start column.
+// score = the largest, over the four start columns c0, of sum_tb ch0[tb][c0 - off(d, tb)] (columns
+// left of the image add 0).  Sums of bf16 values (multiples of 2^-8 when >= 1/2, below 2^13 in
+// total) are exact in fp32.  logit = beta (score - mean) / std over the image's 4096 scores, the
+// no-signal logit = null_logit.  One block of 1024 threads per image, channel 0 (128 KB) and the
+// offset table (64 KB) staged in shared memory; thread t owns x0 tile t % 64 and drift classes
+// t / 64 + 16 j, j < 4, and sums its four start columns along each line together.
+__global__ void __launch_bounds__(1024) k_line_scores(const uint32_t* __restrict__ img, int K,
+                                                      int nb, float beta, float null_logit,
+                                                      float* __restrict__ scores,
+                                                      float* __restrict__ logits) {
+  extern __shared__ __align__(16) uint16_t ch0[];    // [256][256] bf16 bits, then off[64][256]
+  int* const offs = reinterpret_cast<int*>(ch0 + kImg * kImg);
+  __shared__ float red[2][32];
+  const uint32_t* im = img + (int64_t)blockIdx.x * kImg * kImg;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int p = tid; p < kImg * kImg; p += blockDim.x) ch0[p] = (uint16_t)(im[p] & 0xffffu);
+  const int64_t den = 256ll * nb;
+  for (int e = tid; e < kTiles * kImg; e += blockDim.x) {
+    const int d = e / kImg, tb = e % kImg;
+    offs[e] = (int)(((int64_t)(2 * d + 1) * (2 * tb + 1) * K + 128ll * nb) / den);
+  }
+  __syncthreads();
+  const int xt = tid % kTiles, dq = tid / kTiles;
+  float sc[4];
+  float s1 = 0.f, s2 = 0.f;
+#pragma unroll 1
+  for (int j = 0; j < 4; ++j) {
+    const int d = dq + 16 * j;
+    const int* const od = offs + d * kImg;
+    float sum[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int tb = 0; tb < kImg; ++tb) {
+      const int c = 4 * xt - od[tb];                // start column q = 0 on this row
+      const uint16_t* const row = ch0 + tb * kImg;
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (c + q >= 0) sum[q] += __uint_as_float((uint32_t)row[c + q] << 16);
+    }
+    const float best = fmaxf(fmaxf(sum[0], sum[1]), fmaxf(sum[2], sum[3]));
+    sc[j] = best;
+    s1 += best;
+    s2 += best * best;
+  }
+  // mean and deviation of the 4096 scores (fixed reduction order)
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+  }
+  if (lane == 0) { red[0][warp] = s1; red[1][warp] = s2; }
+  __syncthreads();
+  if (warp == 0) {
+    float a = red[0][lane], b2 = red[1][lane];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b2 += __shfl_xor_sync(0xffffffffu, b2, o);
+    }
+    if (lane == 0) { red[0][0] = a; red[1][0] = b2; }
+  }
+  __syncthreads();
+  const float mean = red[0][0] * (1.f / 4096.f);
+  const float var = fmaxf(red[1][0] * (1.f / 4096.f) - mean * mean, 0.f);
+  const float inv = var > 0.f ? 1.f / sqrtf(var) : 0.f;
+  float* const lo = logits + (int64_t)blockIdx.x * kClasses;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int c = (dq + 16 * j) * kTiles + xt;
+    if (scores) scores[(int64_t)blockIdx.x * (kClasses - 1) + c] = sc[j];
+    lo[c] = beta * ((sc[j] - mean) * inv);
+  }
+  if (tid == 0) lo[kClasses - 1] = null_logit;
+}
+
 // ---- tensor-core helpers --------------------------------------------------------------------------
 
 __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
@@ -449,12 +526,13 @@ __global__ void __launch_bounds__(256) k_conv_fwd_tc(const __nv_bfloat16* __rest
       const int b = t / (Ho / RT), y0 = (t - b * (Ho / RT)) * RT;
       const int rin = (RT - 1) * S + 3;
       const int jb_n = (NP + 15) / 16;               // blocks of 16 entries
-      const int tot = rin * S * (QC / 2) * jb_n * 32;
+      const int tot = rin * S * (QC > 1 ? QC / 2 : 1) * jb_n * 32;
       for (int e = tid; e < tot; e += blockDim.x) {
+        constexpr int QH = QC > 1 ? QC / 2 : 1;      // chunk pairs (the halo form has QC >= 2)
         const int qlo = e & 1, jj = (e >> 1) & 15;
         int blk = e >> 5;
         const int jb = blk % jb_n; blk /= jb_n;
-        const int qh = blk % (QC / 2); blk /= (QC / 2);
+        const int qh = blk % QH; blk /= QH;
         const int par = blk % S, ri = blk / S;
         const int j = jb * 16 + jj;
         if (j >= NP) continue;
@@ -652,14 +730,16 @@ __global__ void __launch_bounds__(256) k_conv_dgrad(const __nv_bfloat16* __restr
 }
 
 // ---- L2-L5 weight gradient: dW[co][kc] += sum_p G[p][co] patch[p][kc] ---------------------------
-// A block owns 64 patch columns kc in [n0, n0 + 64) and a range of output pixels; both operands are
+// A block owns 64 patch columns kc in [n0, n0 + 64) and pixel chunk blockIdx.x; both operands are
 // staged transposed (pixels contiguous) in shared memory, 64 pixels at a time, for mma.sync.  Pixel
-// coordinates of a chunk are decoded once into shared memory (32-bit: B (H/S)^2 < 2^31).
+// coordinates of a chunk are decoded once into shared memory (32-bit: B (H/S)^2 < 2^31).  The
+// block's sums go to part[chunk][co][kc] (every entry written by exactly one thread, no atomics);
+// k_sum_chunks adds the chunks in a fixed order, so the gradient is the same on every run.
 template <int CIN, int COUT, int S>
 __global__ void __launch_bounds__(256) k_conv_wgrad(const __nv_bfloat16* __restrict__ dout,
                                                     const __nv_bfloat16* __restrict__ out,
                                                     const __nv_bfloat16* __restrict__ in,
-                                                    float* __restrict__ dw, int B, int H,
+                                                    float* __restrict__ part, int B, int H,
                                                     int pix_per_block) {
   constexpr int PC = 64, LD = PC + 8;
   constexpr int MT = COUT / 16;            // m tiles of 16 output channels
@@ -727,41 +807,55 @@ __global__ void __launch_bounds__(256) k_conv_wgrad(const __nv_bfloat16* __restr
     }
   }
   if (active) {
+    float* const dw = part + (int64_t)blockIdx.x * COUT * 9 * CIN;
 #pragma unroll
     for (int n = 0; n < 4; ++n) {
       const int kc = n0 + nh * 32 + n * 8 + 2 * t;
       const int co = mt * 16 + g;
       if (kc < 9 * CIN) {
-        atomicAdd(&dw[co * 9 * CIN + kc], acc[n][0]);
-        atomicAdd(&dw[(co + 8) * 9 * CIN + kc], acc[n][2]);
+        dw[co * 9 * CIN + kc] = acc[n][0];
+        dw[(co + 8) * 9 * CIN + kc] = acc[n][2];
       }
       if (kc + 1 < 9 * CIN) {
-        atomicAdd(&dw[co * 9 * CIN + kc + 1], acc[n][1]);
-        atomicAdd(&dw[(co + 8) * 9 * CIN + kc + 1], acc[n][3]);
+        dw[co * 9 * CIN + kc + 1] = acc[n][1];
+        dw[(co + 8) * 9 * CIN + kc + 1] = acc[n][3];
       }
     }
   }
 }
 
-// Bias gradient of a ReLU layer: db[co] += sum_p G[p][co].
-__global__ void k_bias_grad(const __nv_bfloat16* __restrict__ dout,
-                            const __nv_bfloat16* __restrict__ out, float* __restrict__ db,
-                            int64_t M, int C) {
+// dst[e] += sum_{c < chunks} part[c * n + e], chunks in increasing order (deterministic).
+__global__ void k_sum_chunks(const float* __restrict__ part, int chunks, int n,
+                             float* __restrict__ dst) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  float s = 0.f;
+  for (int c = 0; c < chunks; ++c) s += part[(int64_t)c * n + e];
+  dst[e] += s;
+}
+
+// Bias gradient of a ReLU layer, db[co] = sum_p G[p][co], in kBiasBlocks x (256 / C) strided
+// partial sums part[(block * 256 / C + row)][co] (reduced by k_sum_chunks).
+constexpr int kBiasBlocks = 256;
+__global__ void __launch_bounds__(256) k_bias_grad(const __nv_bfloat16* __restrict__ dout,
+                                                   const __nv_bfloat16* __restrict__ out,
+                                                   float* __restrict__ part, int64_t M, int C) {
   const int co = threadIdx.x % C, rows = blockDim.x / C;
   float s = 0.f;
   for (int64_t p = (int64_t)blockIdx.x * rows + threadIdx.x / C; p < M; p += (int64_t)gridDim.x * rows)
     if (__bfloat162float(out[p * C + co]) > 0.f) s += __bfloat162float(dout[p * C + co]);
-  atomicAdd(&db[co], s);
+  part[((int64_t)blockIdx.x * rows + threadIdx.x / C) * C + co] = s;
 }
 
-// dW1[co][tap][ci] += sum_p G1[p][co] in[src(p, tap)][ci]; a block reduces a range of pixels for
-// all 576 weights (thread = (co, tap), both input channels).
+// dW1[co][tap][ci] = sum_p G1[p][co] in[src(p, tap)][ci] over images of H x H pixels; a block
+// reduces one chunk of pixels for all 576 weights (thread = (co, tap), both input channels) into
+// part[chunk][576] (reduced by k_sum_chunks).
 __global__ void k_conv1_wgrad(const __nv_bfloat16* __restrict__ dout,
                               const __nv_bfloat16* __restrict__ out,
-                              const __nv_bfloat16* __restrict__ in, float* __restrict__ dw, int B,
-                              int pix_per_block) {
+                              const __nv_bfloat16* __restrict__ in, float* __restrict__ part, int B,
+                              int H, int pix_per_block) {
   const int co = threadIdx.x / 9, tap = threadIdx.x % 9;   // 288 threads
-  const int64_t M = (int64_t)B * kImg * kImg;
+  const int64_t M = (int64_t)B * H * H;
   const int64_t p0 = (int64_t)blockIdx.x * pix_per_block;
   const int64_t p1 = p0 + pix_per_block < M ? p0 + pix_per_block : M;
   float s0 = 0.f, s1 = 0.f;
@@ -769,15 +863,16 @@ __global__ void k_conv1_wgrad(const __nv_bfloat16* __restrict__ dout,
     const float a = __bfloat162float(out[p * 32 + co]);
     if (!(a > 0.f)) continue;
     const float gv = __bfloat162float(dout[p * 32 + co]);
-    const int b = (int)(p / (kImg * kImg)), r = (int)(p % (kImg * kImg));
-    const int yi = r / kImg + tap / 3 - 1, xi = r % kImg + tap % 3 - 1;
-    if (yi < 0 || yi >= kImg || xi < 0 || xi >= kImg) continue;
-    const __nv_bfloat16* q = in + (((int64_t)b * kImg + yi) * kImg + xi) * 2;
+    const int b = (int)(p / ((int64_t)H * H)), r = (int)(p % ((int64_t)H * H));
+    const int yi = r / H + tap / 3 - 1, xi = r % H + tap % 3 - 1;
+    if (yi < 0 || yi >= H || xi < 0 || xi >= H) continue;
+    const __nv_bfloat16* q = in + (((int64_t)b * H + yi) * H + xi) * 2;
     s0 += gv * __bfloat162float(q[0]);
     s1 += gv * __bfloat162float(q[1]);
   }
-  atomicAdd(&dw[co * 18 + tap * 2], s0);
-  atomicAdd(&dw[co * 18 + tap * 2 + 1], s1);
+  float* const dw = part + (int64_t)blockIdx.x * 576;
+  dw[co * 18 + tap * 2] = s0;
+  dw[co * 18 + tap * 2 + 1] = s1;
 }
 
 // ---- mean over t, head, loss --------------------------------------------------------------------
@@ -973,18 +1068,70 @@ int conv_dgrad(const __nv_bfloat16* dout, const __nv_bfloat16* out, const __nv_b
   return GFH_OK;
 }
 
-template <int CIN, int COUT, int S>
-int conv_wgrad(const __nv_bfloat16* dout, const __nv_bfloat16* out, const __nv_bfloat16* in,
-               float* dw, float* db, int B, int H, int sms, cudaStream_t st) {
-  const int64_t M = (int64_t)B * (H / S) * (H / S);
-  if (M >= INT32_MAX) return GFH_ERR_SIZE;
-  const int ppb = 4096;
-  dim3 grid((unsigned)((M + ppb - 1) / ppb), (9 * CIN + 63) / 64);
-  k_conv_wgrad<CIN, COUT, S><<<grid, 256, 0, st>>>(dout, out, in, dw, B, H, ppb);
+// Pixel chunks of a weight gradient over M pixels: at most kMaxChunks chunks of a multiple of 64
+// pixels each (a function of M only, so the reduction order is the same on every run).
+constexpr int kMaxChunks = 256, kMaxChunks1 = 1024;
+inline int wgrad_chunk_pixels(int64_t M, int max_chunks, int min_pixels) {
+  int64_t ppb = std::max<int64_t>(min_pixels, (M + max_chunks - 1) / max_chunks);
+  return (int)((ppb + 63) / 64 * 64);
+}
+
+// Scratch floats of one layer's weight and bias gradients over M output pixels.
+size_t layer_partial_floats(int l, int64_t M) {
+  const bool first = l == 0;
+  const int64_t ppb = wgrad_chunk_pixels(M, first ? kMaxChunks1 : kMaxChunks, first ? 2048 : 4096);
+  return std::max((size_t)kBiasBlocks * 256, (size_t)((M + ppb - 1) / ppb) * kCout[l] * 9 * kCin[l]);
+}
+
+// Scratch floats the weight and bias gradients of every layer of the network need at batch B.
+size_t grad_partial_floats(int B) {
+  static const int hin[5] = {256, 256, 128, 128, 64};
+  size_t most = 0;
+  for (int l = 0; l < 5; ++l) {
+    const int64_t ho = hin[l] / kStride[l];
+    most = std::max(most, layer_partial_floats(l, (int64_t)B * ho * ho));
+  }
+  return most;
+}
+
+int bias_grad(const __nv_bfloat16* dout, const __nv_bfloat16* out, float* db, int64_t M, int C,
+              float* part, cudaStream_t st) {
+  k_bias_grad<<<kBiasBlocks, 256, 0, st>>>(dout, out, part, M, C);
   GFH_CUDA_TRY(cudaGetLastError());
-  k_bias_grad<<<sms * 2, 256, 0, st>>>(dout, out, db, M, COUT);
+  k_sum_chunks<<<1, 64, 0, st>>>(part, kBiasBlocks * 256 / C, C, db);
   GFH_CUDA_TRY(cudaGetLastError());
   return GFH_OK;
+}
+
+// Weight gradient added into dw [cout][3][3][cin] and bias gradient added into db; part holds at
+// least grad_partial_floats(B) floats.
+template <int CIN, int COUT, int S>
+int conv_wgrad(const __nv_bfloat16* dout, const __nv_bfloat16* out, const __nv_bfloat16* in,
+               float* dw, float* db, int B, int H, float* part, cudaStream_t st) {
+  const int64_t M = (int64_t)B * (H / S) * (H / S);
+  if (M >= INT32_MAX) return GFH_ERR_SIZE;
+  const int ppb = wgrad_chunk_pixels(M, kMaxChunks, 4096);
+  const int chunks = (int)((M + ppb - 1) / ppb);
+  dim3 grid((unsigned)chunks, (9 * CIN + 63) / 64);
+  k_conv_wgrad<CIN, COUT, S><<<grid, 256, 0, st>>>(dout, out, in, part, B, H, ppb);
+  GFH_CUDA_TRY(cudaGetLastError());
+  const int n = COUT * 9 * CIN;
+  k_sum_chunks<<<(n + 255) / 256, 256, 0, st>>>(part, chunks, n, dw);
+  GFH_CUDA_TRY(cudaGetLastError());
+  return bias_grad(dout, out, db, M, COUT, part, st);
+}
+
+// First layer (2 input channels) weight and bias gradients, added into dw and db.
+int conv1_wgrad(const __nv_bfloat16* dout, const __nv_bfloat16* out, const __nv_bfloat16* in,
+                float* dw, float* db, int B, int H, float* part, cudaStream_t st) {
+  const int64_t P1 = (int64_t)B * H * H;
+  const int ppb = wgrad_chunk_pixels(P1, kMaxChunks1, 2048);
+  const int chunks = (int)((P1 + ppb - 1) / ppb);
+  k_conv1_wgrad<<<(unsigned)chunks, 288, 0, st>>>(dout, out, in, part, B, H, ppb);
+  GFH_CUDA_TRY(cudaGetLastError());
+  k_sum_chunks<<<(576 + 255) / 256, 256, 0, st>>>(part, chunks, 576, dw);
+  GFH_CUDA_TRY(cudaGetLastError());
+  return bias_grad(dout, out, db, P1, 32, part, st);
 }
 
 }  // namespace
@@ -1002,6 +1149,7 @@ struct gfh_cnn {
   __nv_bfloat16* act[6] = {};                                      // a0 (input copy) .. a5
   __nv_bfloat16* dact[6] = {};                                     // d a1 .. d a5 (index 1..5)
   float *pooled = nullptr, *logits = nullptr, *dlogits = nullptr, *loss = nullptr;
+  float* part = nullptr;                                           // gradient partial sums
 };
 
 namespace {
@@ -1063,22 +1211,16 @@ int backward(gfh_cnn* n, const __nv_bfloat16* img, const int32_t* labels, int B)
                                                                n->gw + L.bh, n->gw + L.bnull, B);
   k_head_dgrad<<<(B * 4096 + 255) / 256, 256, 0, st>>>(n->dlogits, n->w + L.wh, n->dact[5], B);
   GFH_CUDA_TRY(cudaGetLastError());
-  int rc = conv_wgrad<64, 64, 1>(n->dact[5], n->act[5], n->act[4], n->gw + L.w[4], n->gw + L.b[4], B, 64, sms, st);
+  int rc = conv_wgrad<64, 64, 1>(n->dact[5], n->act[5], n->act[4], n->gw + L.w[4], n->gw + L.b[4], B, 64, n->part, st);
   if (!rc) rc = conv_dgrad<64, 64, 1>(n->dact[5], n->act[5], n->wb[4], n->dact[4], B, 64, sms, st);
-  if (!rc) rc = conv_wgrad<64, 64, 2>(n->dact[4], n->act[4], n->act[3], n->gw + L.w[3], n->gw + L.b[3], B, 128, sms, st);
+  if (!rc) rc = conv_wgrad<64, 64, 2>(n->dact[4], n->act[4], n->act[3], n->gw + L.w[3], n->gw + L.b[3], B, 128, n->part, st);
   if (!rc) rc = conv_dgrad<64, 64, 2>(n->dact[4], n->act[4], n->wb[3], n->dact[3], B, 128, sms, st);
-  if (!rc) rc = conv_wgrad<32, 64, 1>(n->dact[3], n->act[3], n->act[2], n->gw + L.w[2], n->gw + L.b[2], B, 128, sms, st);
+  if (!rc) rc = conv_wgrad<32, 64, 1>(n->dact[3], n->act[3], n->act[2], n->gw + L.w[2], n->gw + L.b[2], B, 128, n->part, st);
   if (!rc) rc = conv_dgrad<32, 64, 1>(n->dact[3], n->act[3], n->wb[2], n->dact[2], B, 128, sms, st);
-  if (!rc) rc = conv_wgrad<32, 32, 2>(n->dact[2], n->act[2], n->act[1], n->gw + L.w[1], n->gw + L.b[1], B, 256, sms, st);
+  if (!rc) rc = conv_wgrad<32, 32, 2>(n->dact[2], n->act[2], n->act[1], n->gw + L.w[1], n->gw + L.b[1], B, 256, n->part, st);
   if (!rc) rc = conv_dgrad<32, 32, 2>(n->dact[2], n->act[2], n->wb[1], n->dact[1], B, 256, sms, st);
   if (rc) return rc;
-  const int ppb = 2048;
-  const int64_t P1 = (int64_t)B * kImg * kImg;
-  k_conv1_wgrad<<<(unsigned)((P1 + ppb - 1) / ppb), 288, 0, st>>>(n->dact[1], n->act[1], img,
-                                                                  n->gw + L.w[0], B, ppb);
-  k_bias_grad<<<sms * 2, 256, 0, st>>>(n->dact[1], n->act[1], n->gw + L.b[0], P1, 32);
-  GFH_CUDA_TRY(cudaGetLastError());
-  return GFH_OK;
+  return conv1_wgrad(n->dact[1], n->act[1], img, n->gw + L.w[0], n->gw + L.b[0], B, kImg, n->part, st);
 }
 
 }  // namespace
@@ -1100,7 +1242,8 @@ extern "C" int gfh_cnn_create(gfh_ctx* ctx, int32_t max_batch, uint64_t seed, gf
   for (int l = 0; l < 5; ++l) o_wb[l] = take((size_t)kCout[l] * 9 * kCin[l] * 2);
   for (int l = 1; l < 6; ++l) { o_act[l] = take(act_elems(l, B) * 2); o_dact[l] = take(act_elems(l, B) * 2); }
   const size_t o_pool = take((size_t)B * 4096 * 4), o_log = take((size_t)B * kClasses * 4),
-               o_dlog = take((size_t)B * kClasses * 4), o_loss = take((size_t)B * 4);
+               o_dlog = take((size_t)B * kClasses * 4), o_loss = take((size_t)B * 4),
+               o_part = take(grad_partial_floats(B) * 4);
   if (cudaSetDevice(ctx->device) != cudaSuccess) { delete n; return GFH_ERR_CUDA; }
   if (cudaMalloc(&n->buf, off) != cudaSuccess) { delete n; return GFH_ERR_NOMEM; }
   char* base = (char*)n->buf;
@@ -1113,6 +1256,7 @@ extern "C" int gfh_cnn_create(gfh_ctx* ctx, int32_t max_batch, uint64_t seed, gf
   }
   n->pooled = (float*)(base + o_pool); n->logits = (float*)(base + o_log);
   n->dlogits = (float*)(base + o_dlog); n->loss = (float*)(base + o_loss);
+  n->part = (float*)(base + o_part);
   float* h = new (std::nothrow) float[n->L.total];
   if (!h) { cudaFree(n->buf); delete n; return GFH_ERR_NOMEM; }
   init_params(h, n->L, seed);
@@ -1156,6 +1300,68 @@ extern "C" int gfh_cnn_set_params(gfh_cnn* n, const float* h_params) {
   GFH_CUDA_TRY(cudaMemset(n->v, 0, n->L.total * 4));
   n->step = 0;
   return refresh_bf16(n);
+}
+
+extern "C" int gfh_cnn_get_state(gfh_cnn* n, float* h_params, float* h_m, float* h_v,
+                                 int64_t* h_step) {
+  if (!n) return GFH_ERR_ARG;
+  GFH_CUDA_TRY(cudaSetDevice(n->ctx->device));
+  GFH_CUDA_TRY(cudaStreamSynchronize(n->ctx->stream));
+  const size_t bytes = n->L.total * 4;
+  if (h_params) GFH_CUDA_TRY(cudaMemcpy(h_params, n->w, bytes, cudaMemcpyDeviceToHost));
+  if (h_m) GFH_CUDA_TRY(cudaMemcpy(h_m, n->m, bytes, cudaMemcpyDeviceToHost));
+  if (h_v) GFH_CUDA_TRY(cudaMemcpy(h_v, n->v, bytes, cudaMemcpyDeviceToHost));
+  if (h_step) *h_step = n->step;
+  return GFH_OK;
+}
+
+extern "C" int gfh_cnn_set_state(gfh_cnn* n, const float* h_params, const float* h_m,
+                                 const float* h_v, int64_t step) {
+  if (!n || !h_params || !h_m || !h_v || step < 0) return GFH_ERR_ARG;
+  GFH_CUDA_TRY(cudaSetDevice(n->ctx->device));
+  GFH_CUDA_TRY(cudaStreamSynchronize(n->ctx->stream));
+  const size_t bytes = n->L.total * 4;
+  GFH_CUDA_TRY(cudaMemcpy(n->w, h_params, bytes, cudaMemcpyHostToDevice));
+  GFH_CUDA_TRY(cudaMemcpy(n->m, h_m, bytes, cudaMemcpyHostToDevice));
+  GFH_CUDA_TRY(cudaMemcpy(n->v, h_v, bytes, cudaMemcpyHostToDevice));
+  n->step = step;
+  int rc = refresh_bf16(n);
+  if (!rc) GFH_CUDA_TRY(cudaStreamSynchronize(n->ctx->stream));
+  return rc;
+}
+
+extern "C" int gfh_cnn_read_tensor(gfh_cnn* n, int32_t which, int32_t batch, void* h_out,
+                                   int64_t bytes) {
+  if (!n || !h_out || batch < 1 || batch > n->max_batch) return GFH_ERR_ARG;
+  const void* src = nullptr;
+  size_t need = 0;
+  if (which >= GFH_CNN_ACT && which <= GFH_CNN_ACT + 5 && which != GFH_CNN_ACT) {
+    src = n->act[which - GFH_CNN_ACT];
+    need = act_elems(which - GFH_CNN_ACT, batch) * 2;
+  } else if (which > GFH_CNN_DACT && which <= GFH_CNN_DACT + 5) {
+    src = n->dact[which - GFH_CNN_DACT];
+    need = act_elems(which - GFH_CNN_DACT, batch) * 2;
+  } else if (which >= GFH_CNN_WBF16 && which < GFH_CNN_WBF16 + 5) {
+    const int l = which - GFH_CNN_WBF16;
+    src = n->wb[l];
+    need = (size_t)kCout[l] * 9 * kCin[l] * 2;
+  } else if (which == GFH_CNN_POOLED) {
+    src = n->pooled;
+    need = (size_t)batch * 4096 * 4;
+  } else if (which == GFH_CNN_LOGITS || which == GFH_CNN_DLOGITS) {
+    src = which == GFH_CNN_LOGITS ? n->logits : n->dlogits;
+    need = (size_t)batch * kClasses * 4;
+  } else if (which == GFH_CNN_LOSS) {
+    src = n->loss;
+    need = (size_t)batch * 4;
+  } else {
+    return GFH_ERR_ARG;
+  }
+  if (bytes < (int64_t)need) return GFH_ERR_SIZE;
+  GFH_CUDA_TRY(cudaSetDevice(n->ctx->device));
+  GFH_CUDA_TRY(cudaStreamSynchronize(n->ctx->stream));
+  GFH_CUDA_TRY(cudaMemcpy(h_out, src, need, cudaMemcpyDeviceToHost));
+  return GFH_OK;
 }
 
 extern "C" int gfh_cnn_forward(gfh_cnn* n, const void* d_images, int32_t batch, float* d_logits) {
@@ -1254,6 +1460,21 @@ extern "C" int gfh_propose_tiles(gfh_ctx* ctx, const float* d_logits, int32_t ba
   return GFH_OK;
 }
 
+extern "C" int gfh_line_scores(gfh_ctx* ctx, const void* d_images, int32_t batch, int32_t n_k,
+                               int32_t n_bins, float beta, float null_logit, float* d_scores,
+                               float* d_logits) {
+  if (!ctx || !d_images || !d_logits || batch < 1 || batch > 65535 || n_k < 1 || n_bins < kImg ||
+      !(beta == beta) || !(null_logit == null_logit))
+    return GFH_ERR_ARG;
+  GFH_CUDA_TRY(cudaSetDevice(ctx->device));
+  const int smem = kImg * kImg * 2 + kTiles * kImg * 4;
+  GFH_CUDA_TRY(cudaFuncSetAttribute(k_line_scores, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  k_line_scores<<<batch, 1024, smem, ctx->stream>>>((const uint32_t*)d_images, n_k, n_bins, beta,
+                                                    null_logit, d_scores, d_logits);
+  GFH_CUDA_TRY(cudaGetLastError());
+  return GFH_OK;
+}
+
 extern "C" int gfh_wait_check(gfh_ctx* ctx, int64_t cycles) {
   if (!ctx || cycles < 0 || cycles > 4000000000ll) return GFH_ERR_ARG;
   GFH_CUDA_TRY(cudaSetDevice(ctx->device));
@@ -1275,12 +1496,28 @@ extern "C" int gfh_conv3x3(gfh_ctx* ctx, int32_t mode, int32_t cin, int32_t cout
   const auto* w = (const __nv_bfloat16*)d_w;
   const auto* out = (const __nv_bfloat16*)d_out;
   const auto* dout = (const __nv_bfloat16*)d_dout;
+  float* part = nullptr;
+  if (mode == 2) {   // partial sums in the context scratch
+    int l = -1;
+    for (int q = 0; q < 5; ++q)
+      if (kCin[q] == cin && kCout[q] == cout && kStride[q] == stride) l = q;
+    if (l < 0) return GFH_ERR_ARG;
+    const int64_t ho = h / stride;
+    const int rc = ensure_scratch(ctx, layer_partial_floats(l, (int64_t)batch * ho * ho) * 4);
+    if (rc) return rc;
+    part = (float*)ctx->pm_buf;
+  }
 #define GFH_CONV_CASE(CI, CO, S)                                                                   \
   if (cin == CI && cout == CO && stride == S) {                                                    \
     if (mode == 0) return conv_fwd<CI, CO, S>(in, w, d_bias, (__nv_bfloat16*)d_res, batch, h, sms, st, ctx->d_flag); \
     if (mode == 1) return conv_dgrad<CI, CO, S>(dout, out, w, (__nv_bfloat16*)d_res, batch, h, sms, st); \
-    if (mode == 2) return conv_wgrad<CI, CO, S>(dout, out, in, (float*)d_res, d_db, batch, h, sms, st); \
+    if (mode == 2) return conv_wgrad<CI, CO, S>(dout, out, in, (float*)d_res, d_db, batch, h, part, st); \
     return GFH_ERR_ARG;                                                                            \
+  }
+  if (cin == 2 && cout == 32 && stride == 1) {                      // first layer: no input gradient
+    if (mode == 0) return conv_fwd<2, 32, 1>(in, w, d_bias, (__nv_bfloat16*)d_res, batch, h, sms, st, ctx->d_flag);
+    if (mode == 2) return conv1_wgrad(dout, out, in, (float*)d_res, d_db, batch, h, part, st);
+    return GFH_ERR_ARG;
   }
   GFH_CONV_CASE(32, 32, 2)
   GFH_CONV_CASE(32, 64, 1)

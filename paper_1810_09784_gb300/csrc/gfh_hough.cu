@@ -769,3 +769,62 @@ extern "C" int gfh_select(gfh_ctx* ctx, const int32_t* d_map, const gfh_grid* g,
   cudaFree(buf);
   return e == cudaSuccess ? GFH_OK : GFH_ERR_CUDA;
 }
+
+// ---- shared-memory atomic throughput (the denominator of the accumulator's roofline) ------------
+//
+// Every thread adds 1 with atomicAdd to 32-bit shared words, `iters` times, cycling over four words
+// of its own (so consecutive atomics of a thread do not wait on one word).  Mode 0: lane l of warp w
+// uses words w * 32 + l + 1024 q (one word per bank per warp: conflict-free); mode 1: all lanes of
+// a warp use the same word (same-address); mode 2: pseudo-random words of a 32 KB array.  The
+// block's elapsed SM cycles go to cycles[block]; the array's sum goes to sink[block] (kept live).
+namespace {
+
+template <int MODE>
+__global__ void __launch_bounds__(1024) k_smem_atomics(int iters, long long* __restrict__ cycles,
+                                                       int* __restrict__ sink) {
+  __shared__ int buf[8192];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int i = tid; i < 8192; i += blockDim.x) buf[i] = 0;
+  __syncthreads();
+  int a[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (MODE == 0) a[q] = ((warp * 32 + lane) & 1023) + 1024 * q;
+    else if (MODE == 1) a[q] = (warp & 255) * 32 + 1024 * q;
+    else a[q] = (int)(gfh_mix64((uint64_t)(blockIdx.x * 1024 + tid) * 4 + q) & 8191u);
+  }
+  const long long t0 = clock64();
+  for (int i = 0; i < iters; i += 4) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) atomicAdd(&buf[a[q]], 1);
+  }
+  __syncthreads();
+  const long long t1 = clock64();
+  int s = 0;
+  for (int i = tid; i < 8192; i += blockDim.x) s += buf[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) atomicAdd(&sink[blockIdx.x], s);
+  if (tid == 0) cycles[blockIdx.x] = t1 - t0;
+}
+
+}  // namespace
+
+extern "C" int gfh_probe_smem_atomics(gfh_ctx* ctx, int32_t mode, int32_t blocks, int32_t threads,
+                                      int32_t iters, long long* d_cycles, int32_t* d_sink) {
+  if (!ctx || mode < 0 || mode > 2 || blocks < 1 || threads < 32 || threads > 1024 ||
+      threads % 32 || iters < 4 || iters % 4 || !d_cycles || !d_sink)
+    return GFH_ERR_ARG;
+  GFH_CUDA_TRY(cudaSetDevice(ctx->device));
+  if (mode == 0) k_smem_atomics<0><<<blocks, threads, 0, ctx->stream>>>(iters, d_cycles, d_sink);
+  if (mode == 1) k_smem_atomics<1><<<blocks, threads, 0, ctx->stream>>>(iters, d_cycles, d_sink);
+  if (mode == 2) k_smem_atomics<2><<<blocks, threads, 0, ctx->stream>>>(iters, d_cycles, d_sink);
+  GFH_CUDA_TRY(cudaGetLastError());
+  return GFH_OK;
+}
+
+extern "C" int gfh_device_sms(gfh_ctx* ctx, int32_t* h_sms) {
+  if (!ctx || !h_sms) return GFH_ERR_ARG;
+  *h_sms = ctx->num_sms;
+  return GFH_OK;
+}

@@ -38,8 +38,13 @@ EXPORTED = [
     "gfh_propose_tiles", "gfh_conv3x3", "gfh_select_squares", "gfh_coincide",
     "gfh_n_grid", "gfh_k_segments", "gfh_wait_check",
     "gfh_heterodyne", "gfh_peakmap_complex", "gfh_project_peaks", "gfh_tfft_portions",
-    "gfh_heterodyne_band_peaks",
+    "gfh_heterodyne_band_peaks", "gfh_cnn_get_state", "gfh_cnn_set_state",
+    "gfh_cnn_read_tensor", "gfh_line_scores", "gfh_probe_smem_atomics", "gfh_device_sms",
 ]
+# gfh_cnn_read_tensor selectors
+CNN_ACT, CNN_DACT, CNN_WBF16 = 0, 10, 20
+CNN_POOLED, CNN_LOGITS, CNN_DLOGITS, CNN_LOSS = 30, 31, 32, 33
+_ACT_SHAPE = {1: (256, 32), 2: (128, 32), 3: (128, 64), 4: (64, 64), 5: (64, 64)}
 N_CLASSES = 4097        # 64 x 64 coarse tiles + no signal
 IMG = 256
 STATIC_SCRATCH_BYTES = 8 << 20
@@ -153,6 +158,12 @@ def lib() -> ctypes.CDLL:
             "gfh_tfft_portions": [dbl, dbl, dbl, dbl, dbl, i32, i32, vp, P(i32)],
             "gfh_heterodyne_band_peaks": [vp, vp, i64, dbl, dbl, dbl, dbl, dbl, dbl, i32, i32, dbl,
                                           vp, vp, i64, P(i64)],
+            "gfh_cnn_get_state": [vp, vp, vp, vp, P(i64)],
+            "gfh_cnn_set_state": [vp, vp, vp, vp, i64],
+            "gfh_cnn_read_tensor": [vp, i32, i32, vp, i64],
+            "gfh_line_scores": [vp, vp, i32, i32, i32, ctypes.c_float, ctypes.c_float, vp, vp],
+            "gfh_probe_smem_atomics": [vp, i32, i32, i32, i32, vp, vp],
+            "gfh_device_sms": [vp, P(i32)],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -399,6 +410,18 @@ class Context:
                              _ptr(out_map), _ptr(cands), _ptr(stats))
         _ok(rc, "gfh_hough")
 
+    def sms(self) -> int:
+        """The SM count of the context's device."""
+        n = ctypes.c_int32()
+        _ok(lib().gfh_device_sms(self.handle, ctypes.byref(n)), "gfh_device_sms")
+        return n.value
+
+    def probe_smem_atomics(self, mode: int, blocks: int, threads: int, iters: int, cycles,
+                           sink) -> None:
+        """gfh_probe_smem_atomics: shared-memory atomicAdd throughput kernel (caller times it)."""
+        _ok(lib().gfh_probe_smem_atomics(self.handle, mode, blocks, threads, iters, _ptr(cycles),
+                                         _ptr(sink)), "gfh_probe_smem_atomics")
+
     def wait_check(self, cycles: int) -> None:
         """gfh_wait_check: a bounded device wait that runs out (the next check() reports it)."""
         _ok(lib().gfh_wait_check(self._h, cycles), "gfh_wait_check")
@@ -540,6 +563,14 @@ def propose_tiles(ctx: Context, logits, gain, k: int, top, resid, tau: float = -
     _ok(rc, "gfh_propose_tiles")
 
 
+def line_scores(ctx: Context, images, n_k: int, n_bins: int, beta: float, null_logit: float,
+                logits, scores=None) -> None:
+    """gfh_line_scores: the non-learned proposer's straight-line sums and their logits."""
+    rc = lib().gfh_line_scores(ctx.handle, _ptr(images), images.shape[0], n_k, n_bins, beta,
+                               null_logit, _ptr(scores), _ptr(logits))
+    _ok(rc, "gfh_line_scores")
+
+
 def conv3x3(ctx: Context, mode: int, cin: int, cout: int, stride: int, batch: int, h: int,
             inp=None, w=None, bias=None, out=None, dout=None, res=None, db=None) -> None:
     """gfh_conv3x3: one 3x3 layer alone (0 forward, 1 input gradient, 2 weight gradient)."""
@@ -573,6 +604,38 @@ class Cnn:
         a = np.ascontiguousarray(params, dtype=np.float32)
         assert a.size == self.n_params
         _ok(lib().gfh_cnn_set_params(self._h, a.ctypes.data), "gfh_cnn_set_params")
+
+    def state(self) -> dict:
+        """Training state for a checkpoint: parameters, AdamW moments, step count."""
+        p, m, v = (np.empty(self.n_params, np.float32) for _ in range(3))
+        step = ctypes.c_int64()
+        _ok(lib().gfh_cnn_get_state(self._h, p.ctypes.data, m.ctypes.data, v.ctypes.data,
+                                    ctypes.byref(step)), "gfh_cnn_get_state")
+        return {"params": p, "m": m, "v": v, "step": int(step.value)}
+
+    def set_state(self, st: dict) -> None:
+        p, m, v = (np.ascontiguousarray(st[k], dtype=np.float32) for k in ("params", "m", "v"))
+        assert p.size == m.size == v.size == self.n_params
+        _ok(lib().gfh_cnn_set_state(self._h, p.ctypes.data, m.ctypes.data, v.ctypes.data,
+                                    int(st["step"])), "gfh_cnn_set_state")
+
+    def read_tensor(self, which: int, batch: int) -> np.ndarray:
+        """An internal tensor of the last pass (gfh_cnn_read_tensor): bf16 ones as uint16 bits."""
+        if CNN_ACT < which <= CNN_ACT + 5 or CNN_DACT < which <= CNN_DACT + 5:
+            h, c = _ACT_SHAPE[which % 10]
+            out = np.empty((batch, h, h, c), np.uint16)
+        elif CNN_WBF16 <= which < CNN_WBF16 + 5:
+            l = which - CNN_WBF16
+            out = np.empty(((32, 32, 64, 64, 64)[l], 3, 3, (2, 32, 32, 64, 64)[l]), np.uint16)
+        elif which == CNN_POOLED:
+            out = np.empty((batch, 64, 64), np.float32)
+        elif which in (CNN_LOGITS, CNN_DLOGITS):
+            out = np.empty((batch, N_CLASSES), np.float32)
+        else:
+            out = np.empty(batch, np.float32)
+        _ok(lib().gfh_cnn_read_tensor(self._h, which, batch, out.ctypes.data, out.nbytes),
+            "gfh_cnn_read_tensor")
+        return out
 
     def forward(self, images, logits=None) -> None:
         _ok(lib().gfh_cnn_forward(self._h, _ptr(images), images.shape[0], _ptr(logits)),

@@ -10,9 +10,12 @@ Workload: maps shaped like the small plain search (1024 Hz sampling, 1800 s, T_F
 band 100-400 Hz, 500 k rows), one braking index per map from n = 2.0, 2.1, ..., 7.0 (sample s has
 index s mod 51), half of them with one power-law injection (Sec. II Eq. powlaws) of spectral SNR
 uniform in [2, 8], f0 uniform over the band, k on a uniformly drawn row of the map's k grid.
-Peakmaps come from the statistical model of `synth` (noise peaks with the probability p0 of an
-equalised exponential spectrum above 2.5 that is a local maximum; the track's cell is a peak with
-the probability that a signal of that SNR exceeds 2.5), drawn on the GPU cell by cell.
+Peakmaps (spec.peakmaps = "series", the default) come from the method's own chain: a seeded
+white-noise strain series with the sample's injection (synth), then the library's peakmap
+(short FFTs, equaliser, threshold 2.5, local maximum; Sec. III).  The alternative "statistical"
+model draws each cell independently on the GPU (a noise peak with the probability p0 of an
+equalised exponential spectrum above 2.5 that is a local maximum; the track's cell with the
+probability that a signal of that SNR exceeds 2.5); it serves the kernel tests.
 
 Labels: class d * 64 + xt, xt = floor((f0 - ana_lo) / (ana_hi - ana_lo) * 64) and drift class
 d = floor(r (f0 / f_max)^n * 64 / K) (a track on k row r drifts r x0 columns over the observation,
@@ -48,6 +51,7 @@ class ProposerSpec:
     snr_hi: float = 8.0
     p_signal: float = 0.5
     seed: int = 20181023
+    peakmaps: str = "series"        # "series" (series -> gfh_peakmap) or "statistical"
 
     @property
     def n_fft(self) -> int:
@@ -101,6 +105,7 @@ class Samples:
     col: np.ndarray         # x0 column of the injection (-1 without)
     nplane: np.ndarray      # float32
     gain: np.ndarray        # [B][64][2] float32 (ga, gb)
+    phase0: np.ndarray      # initial phase of the injection [rad]
 
 
 def draw(spec: ProposerSpec, index) -> Samples:
@@ -140,7 +145,77 @@ def draw(spec: ProposerSpec, index) -> Samples:
         labels[b] = d * TILES + xt
         col[b] = int(math.floor((f0[b] ** (1.0 - n[b]) - g.x0_min) / g.dx0))
     return Samples(s, n, signal, f0, row, k, snr, p24, tracks, labels, col,
-                   ((n - 2.0) / 5.0).astype(np.float32), gain)
+                   ((n - 2.0) / 5.0).astype(np.float32), gain, 2.0 * math.pi * u[4])
+
+
+def injection_of(spec: ProposerSpec, smp: Samples, b: int):
+    """The power-law signal of sample b of a draw (None without one): amplitude for its spectral
+    SNR with spec.fs * spec.t_fft samples per FFT."""
+    if not smp.signal[b]:
+        return None
+    N = int(round(spec.fs * spec.t_fft))
+    return synth.Injection(f0=float(smp.f0[b]), k=float(smp.k[b]), n=float(smp.n[b]),
+                           amp=synth.amplitude_for_snr(float(smp.snr[b]), 1.0, N),
+                           phase0=float(smp.phase0[b]))
+
+
+def series_seed(spec: ProposerSpec, sample: int) -> int:
+    """Seed of the noise of sample `sample`'s strain series."""
+    return int(synth.sample_key(spec.seed, np.uint64(sample), 3))
+
+
+class PeakSource:
+    """Peak lists of up to max_maps samples on the device, sample i of a draw -> list i, compacted
+    so that list i is [offsets[i], offsets[i + 1]).  Series peakmaps: each sample's strain series is
+    drawn on the device and searched by gfh_peakmap_async into its own slot; statistical ones come
+    from gfh_synth_peaks.  One host synchronisation per load (the list lengths)."""
+
+    def __init__(self, ctx: gfh.Context, spec: ProposerSpec, max_maps: int):
+        import torch
+        self.torch, self.ctx, self.spec = torch, ctx, spec
+        nb = spec.bin_hi - spec.bin_lo + 1
+        self.cap = int(spec.n_fft * nb * 0.12) + 4096
+        self.fft = torch.empty(max_maps * self.cap, dtype=torch.int32, device="cuda")
+        self.bin = torch.empty(max_maps * self.cap, dtype=torch.int32, device="cuda")
+        self.cnt = torch.zeros(max_maps, dtype=torch.int64, device="cuda")
+        self.offsets = torch.zeros(max_maps + 1, dtype=torch.int64, device="cuda")
+        self.max_maps = max_maps
+        self.x = None
+        if spec.peakmaps == "series":
+            self.x = torch.empty(int(round(spec.fs * spec.t_obs)), dtype=torch.float32, device="cuda")
+
+    def load(self, smp: Samples) -> None:
+        torch, ctx, spec = self.torch, self.ctx, self.spec
+        B = smp.index.size
+        assert B <= self.max_maps
+        if spec.peakmaps == "series":
+            for i in range(B):
+                inj = injection_of(spec, smp, i)
+                synth.strain_series_device(self.x, spec.fs, series_seed(spec, int(smp.index[i])),
+                                           () if inj is None else (inj,))
+                o = i * self.cap
+                ctx.peakmap_async(self.x, spec.fs, spec.t_fft, spec.bin_lo, spec.bin_hi, THETA,
+                                  self.fft[o:o + self.cap], self.bin[o:o + self.cap],
+                                  self.cnt[i:i + 1])
+            counts = self.cnt[:B].cpu().numpy()
+            if ctx.check() != gfh.GFH_OK:
+                raise RuntimeError("peakmap capacity or input check failed")
+        else:
+            tracks = torch.from_numpy(smp.tracks).cuda()
+            counts = np.zeros(B, np.int64)
+            for i in range(B):
+                o = i * self.cap
+                counts[i] = gfh.synth_peaks(ctx, spec.seed, int(smp.index[i]), spec.n_fft,
+                                            spec.bin_lo, spec.bin_hi, spec.p_noise24,
+                                            int(smp.p_track24[i]), tracks[i],
+                                            self.fft[o:o + self.cap], self.bin[o:o + self.cap])
+        offs = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+        self.fft_c = torch.cat([self.fft[i * self.cap:i * self.cap + int(counts[i])] for i in range(B)])
+        self.bin_c = torch.cat([self.bin[i * self.cap:i * self.cap + int(counts[i])] for i in range(B)])
+        self.offsets[:B + 1].copy_(torch.from_numpy(offs))
+        self.counts = counts.astype(np.int64)
+        self.offs_host = [int(v) for v in offs]
+        self.n_lists = B
 
 
 class DeviceBatch:
@@ -158,7 +233,8 @@ class DeviceBatch:
         self.logits = torch.empty((batch, gfh.N_CLASSES), dtype=torch.float32, device=device)
 
     def load(self, ctx: gfh.Context, spec: ProposerSpec, smp: Samples) -> int:
-        """Uploads a draw and renders its images on the GPU; returns the batch size."""
+        """Uploads a draw and renders its images on the GPU (series peakmaps: through gfh_peakmap
+        and gfh_peaks_to_images; statistical ones: gfh_synth_images); returns the batch size."""
         torch = self.torch
         B = smp.index.size
         self.labels[:B].copy_(torch.from_numpy(smp.labels))
@@ -167,26 +243,83 @@ class DeviceBatch:
         self.nplane[:B].copy_(torch.from_numpy(smp.nplane))
         self.gain[:B].copy_(torch.from_numpy(smp.gain))
         assert np.all(np.diff(smp.index) == 1)
-        gfh.synth_images(ctx, spec.seed, int(smp.index[0]), spec.n_fft, spec.bin_lo, spec.bin_hi,
-                         spec.p_noise24, self.p24[:B], self.tracks[:B], self.nplane[:B],
-                         self.images[:B])
+        if spec.peakmaps == "series":
+            if getattr(self, "source", None) is None:
+                self.source = PeakSource(ctx, spec, self.images.shape[0])
+            src = self.source
+            src.load(smp)
+            gfh.peaks_to_images(ctx, src.fft_c, src.bin_c, src.offsets, B, spec.n_fft,
+                                spec.bin_lo, spec.bin_hi, self.nplane[:B], self.images[:B])
+        else:
+            gfh.synth_images(ctx, spec.seed, int(smp.index[0]), spec.n_fft, spec.bin_lo,
+                             spec.bin_hi, spec.p_noise24, self.p24[:B], self.tracks[:B],
+                             self.nplane[:B], self.images[:B])
         return B
 
 
+class ImageCache:
+    """Images and labels of samples [first, first + count) rendered once and kept on the device
+    (256 KB per image), so that several training passes draw each series and peakmap only once."""
+
+    def __init__(self, ctx: gfh.Context, spec: ProposerSpec, first: int, count: int,
+                 chunk: int = 256, log=None):
+        import torch
+        self.first, self.count = first, count
+        self.images = torch.empty((count, 256, 256, 2), dtype=torch.bfloat16, device="cuda")
+        self.labels = torch.empty(count, dtype=torch.int32, device="cuda")
+        buf = DeviceBatch(spec, chunk)
+        for c0 in range(0, count, chunk):
+            B = min(chunk, count - c0)
+            buf.load(ctx, spec, draw(spec, np.arange(first + c0, first + c0 + B)))
+            self.images[c0:c0 + B].copy_(buf.images[:B])
+            self.labels[c0:c0 + B].copy_(buf.labels[:B])
+            if log and (c0 // chunk) % 50 == 0:
+                log(f"images {c0 + B}/{count}")
+
+    def batch(self, s0: int, B: int):
+        o = s0 - self.first
+        assert 0 <= o and o + B <= self.count
+        return self.images[o:o + B], self.labels[o:o + B]
+
+
+def save_checkpoint(path, state: dict, meta: dict) -> None:
+    """Writes a training state (gfh.Cnn.state(): parameters, AdamW moments, step count) and a
+    JSON-serialisable description (schedule position, tau, data recipe) to one .npz file."""
+    import json
+    np.savez(path, params=np.asarray(state["params"], np.float32),
+             m=np.asarray(state["m"], np.float32), v=np.asarray(state["v"], np.float32),
+             step=np.int64(state["step"]), meta=np.frombuffer(json.dumps(meta).encode(), np.uint8))
+
+
+def load_checkpoint(path) -> tuple:
+    """(state, meta) written by save_checkpoint."""
+    import json
+    with np.load(path) as z:
+        state = {"params": z["params"].copy(), "m": z["m"].copy(), "v": z["v"].copy(),
+                 "step": int(z["step"])}
+        meta = json.loads(bytes(z["meta"]).decode())
+    return state, meta
+
+
 def train(ctx: gfh.Context, net: gfh.Cnn, spec: ProposerSpec, first: int, count: int,
-          batch: int = 256, lr: float = 2e-3, weight_decay: float = 1e-4, log=None) -> list:
-    """AdamW over samples [first, first + count) in order, cosine learning-rate decay; returns the
-    loss of every step."""
-    buf = DeviceBatch(spec, batch)
+          batch: int = 256, lr: float = 2e-3, weight_decay: float = 1e-4, log=None,
+          cache: ImageCache | None = None, start_step: int = 0) -> list:
+    """AdamW over samples [first, first + count) in order, cosine learning-rate decay, from step
+    `start_step` of the pass on (a resumed pass); images from `cache` when given, else rendered per
+    batch; returns the loss of every step taken."""
+    buf = None if cache is not None else DeviceBatch(spec, batch)
     steps = (count + batch - 1) // batch
     losses = []
-    for st in range(steps):
+    for st in range(start_step, steps):
         s0 = first + st * batch
         B = min(batch, first + count - s0)
-        smp = draw(spec, np.arange(s0, s0 + B))
-        buf.load(ctx, spec, smp)
+        if cache is not None:
+            images, labels = cache.batch(s0, B)
+        else:
+            buf.load(ctx, spec, draw(spec, np.arange(s0, s0 + B)))
+            images, labels = buf.images[:B], buf.labels[:B]
         lr_t = lr * 0.5 * (1.0 + math.cos(math.pi * st / steps))
-        loss = net.train_step(buf.images[:B], buf.labels[:B], lr_t, weight_decay)
+        loss = net.train_step(images, labels, lr_t, weight_decay)
         losses.append(loss)
         if log and (st % 50 == 0 or st == steps - 1):
             log(f"step {st}/{steps} loss {loss:.4f} lr {lr_t:.2e}")
@@ -210,37 +343,15 @@ class HoughBank:
         self.plan = gfh.Plan(ctx, self.grids, self.maps, self.cands, tile=tile)
         self.plan.set_coarse(TILES, TILES, max_sel)
         self.max_sel = max_sel
-        cap = int(spec.n_fft * (spec.bin_hi - spec.bin_lo + 1) * 0.1) + 4096
-        self.cap = cap
-        nl = len(N_GRID)
-        self.fft = torch.empty(nl * cap, dtype=torch.int32, device="cuda")
-        self.bin = torch.empty(nl * cap, dtype=torch.int32, device="cuda")
-        self.offsets = torch.zeros(nl + 1, dtype=torch.int64, device="cuda")
-        self.counts = np.zeros(nl, np.int64)
+        self.source = PeakSource(ctx, spec, len(N_GRID))
+        self.counts = np.zeros(len(N_GRID), np.int64)
 
     def load_peaks(self, smp: Samples) -> None:
-        """Peak lists of the 51 samples smp (sample i -> list i), drawn on the GPU."""
-        spec = self.spec
-        torch = self.torch
-        tracks = torch.from_numpy(smp.tracks).cuda()
-        offs = [0]
-        for i in range(smp.index.size):
-            o = i * self.cap
-            n = gfh.synth_peaks(self.ctx, spec.seed, int(smp.index[i]), spec.n_fft, spec.bin_lo,
-                                spec.bin_hi, spec.p_noise24, int(smp.p_track24[i]), tracks[i],
-                                self.fft[o:o + self.cap], self.bin[o:o + self.cap])
-            self.counts[i] = n
-        # lists were drawn at fixed strides; compact them so that list i starts at offsets[i]
-        parts_f, parts_b = [], []
-        for i in range(smp.index.size):
-            o = i * self.cap
-            parts_f.append(self.fft[o:o + self.counts[i]])
-            parts_b.append(self.bin[o:o + self.counts[i]])
-            offs.append(offs[-1] + int(self.counts[i]))
-        self.fft_c = torch.cat(parts_f)
-        self.bin_c = torch.cat(parts_b)
-        self.offsets.copy_(torch.tensor(offs, dtype=torch.int64))
-        self.offs_host = offs
+        """Peak lists of the 51 samples smp (sample i -> list i), made on the GPU."""
+        src = self.source
+        src.load(smp)
+        self.fft_c, self.bin_c, self.offsets = src.fft_c, src.bin_c, src.offsets
+        self.counts, self.offs_host = src.counts, src.offs_host
 
     def updates(self) -> int:
         """Hough updates of the full search of the loaded lists: peaks x k rows per map."""
@@ -378,10 +489,155 @@ def choose_tau(ctx: gfh.Context, net: gfh.Cnn, spec: ProposerSpec, first: int, c
 
 
 def train_default(ctx: gfh.Context, net: gfh.Cnn, spec: ProposerSpec, epochs: int = 3,
-                  n_train: int = 100000, batch: int = 256, lr: float = 2e-3, log=None) -> list:
+                  n_train: int = 100000, batch: int = 256, lr: float = 2e-3, log=None,
+                  checkpoint=None, resume=None, cache: ImageCache | None = None) -> list:
     """The training schedule of the proposer: `epochs` passes over samples [0, n_train), each a
-    cosine decay from lr / 2^epoch."""
+    cosine decay from lr / 2^epoch.  Series images are rendered once (ImageCache).  `checkpoint`:
+    a path written after every pass (state and schedule position); `resume`: a (state, meta) pair
+    from load_checkpoint to continue from."""
+    e0, st0 = 0, 0
+    if resume is not None:
+        state, meta = resume
+        net.set_state(state)
+        e0, st0 = int(meta["epoch"]), int(meta["step_in_epoch"])
+    if cache is None and spec.peakmaps == "series" and e0 < epochs:
+        cache = ImageCache(ctx, spec, 0, n_train, log=log)
     losses = []
-    for e in range(epochs):
-        losses += train(ctx, net, spec, 0, n_train, batch=batch, lr=lr * 0.5 ** e, log=log)
+    for e in range(e0, epochs):
+        losses += train(ctx, net, spec, 0, n_train, batch=batch, lr=lr * 0.5 ** e, log=log,
+                        cache=cache, start_step=st0 if e == e0 else 0)
+        if checkpoint is not None:
+            save_checkpoint(checkpoint, net.state(),
+                            {"epoch": e + 1, "step_in_epoch": 0, "epochs": epochs,
+                             "n_train": n_train, "batch": batch, "lr": lr,
+                             "peakmaps": spec.peakmaps})
     return losses
+
+
+# ---- the non-learned proposer ------------------------------------------------------------------
+
+class LineHeuristic:
+    """Stand-in for the network in PrunedSearch: gfh_line_scores ranks each class by the peak
+    counts along its straight mid-drift line in the image (no learning); beta and the no-signal
+    logit are its only two numbers, fitted by calibrate_heuristic."""
+
+    def __init__(self, ctx: gfh.Context, spec: ProposerSpec, beta: float = 1.0,
+                 null_logit: float = 0.0):
+        self.ctx, self.spec, self.beta, self.null_logit = ctx, spec, beta, null_logit
+
+    def forward(self, images, logits, scores=None) -> None:
+        spec = self.spec
+        gfh.line_scores(self.ctx, images, spec.n_k, spec.bin_hi - spec.bin_lo + 1, self.beta,
+                        self.null_logit, logits, scores)
+
+
+def calibrate_heuristic(ctx: gfh.Context, spec: ProposerSpec, first: int, count: int,
+                        betas=(0.5, 1.0, 1.5, 2.0, 3.0, 4.0, 6.0, 8.0),
+                        nulls=tuple(np.linspace(-5.0, 15.0, 41))) -> LineHeuristic:
+    """The (beta, null logit) pair of least mean cross-entropy of the line-sum logits against the
+    labels of samples [first, first + count) (a two-number fit, as a temperature would be)."""
+    import torch
+    h = LineHeuristic(ctx, spec)
+    buf = DeviceBatch(spec, 256)
+    zs, labels = [], []
+    scores = torch.empty((256, TILES * TILES), dtype=torch.float32, device="cuda")
+    logits = torch.empty((256, gfh.N_CLASSES), dtype=torch.float32, device="cuda")
+    for c0 in range(first, first + count, 256):
+        B = min(256, first + count - c0)
+        smp = draw(spec, np.arange(c0, c0 + B))
+        buf.load(ctx, spec, smp)
+        h.forward(buf.images[:B], logits[:B], scores[:B])
+        sc = scores[:B].double().cpu().numpy()
+        sd = sc.std(axis=1, keepdims=True)
+        zs.append((sc - sc.mean(axis=1, keepdims=True)) / np.where(sd > 0, sd, 1.0))
+        labels.append(smp.labels)
+    z = np.concatenate(zs)
+    y = np.concatenate(labels).astype(np.int64)
+    sig = y < NULL_CLASS
+    best = None
+    for beta in betas:
+        bz = beta * z
+        m = bz.max(axis=1)
+        lse_c = m + np.log(np.exp(bz - m[:, None]).sum(axis=1))     # log-sum-exp of the classes
+        zy = np.where(sig, bz[np.arange(y.size), np.minimum(y, NULL_CLASS - 1)], 0.0)
+        for c in nulls:
+            lse = np.logaddexp(lse_c, c)
+            ce = float(np.mean(lse - np.where(sig, zy, c)))
+            if best is None or ce < best[0]:
+                best = (ce, beta, float(c))
+    h.beta, h.null_logit = best[1], best[2]
+    h.cross_entropy = best[0]
+    return h
+
+
+# ---- command line: train a checkpoint, or evaluate one -------------------------------------------
+
+DEFAULT_CHECKPOINT = "weights/proposer_series.npz"
+VALIDATION_FIRST, HELD_OUT_FIRST = 200022, 100011
+
+
+def checkpoint_path(name: str = DEFAULT_CHECKPOINT):
+    import pathlib
+    return pathlib.Path(__file__).resolve().parent / name
+
+
+def _main(argv=None) -> None:
+    import argparse
+    import json
+    import time
+
+    import torch
+    ap = argparse.ArgumentParser(description="Train (or evaluate) the tile proposer on the GPU.")
+    ap.add_argument("cmd", choices=["train", "eval"])
+    ap.add_argument("--out", default=str(checkpoint_path()))
+    ap.add_argument("--epochs", type=int, default=3)
+    ap.add_argument("--n-train", type=int, default=100000)
+    ap.add_argument("--val-maps", type=int, default=51 * 40)
+    ap.add_argument("--eval-maps", type=int, default=51 * 196)
+    ap.add_argument("--resume", default=None)
+    args = ap.parse_args(argv)
+    log = lambda m: print(m, flush=True)
+    stream = torch.cuda.Stream()
+    ctx = gfh.Context(0, stream)
+    spec = ProposerSpec()
+    meta = {}
+    with torch.cuda.stream(stream):
+        net = gfh.Cnn(ctx, 256, seed=1)
+        if args.cmd == "train":
+            t0 = time.perf_counter()
+            resume = load_checkpoint(args.resume) if args.resume else None
+            losses = train_default(ctx, net, spec, epochs=args.epochs, n_train=args.n_train,
+                                   log=log, checkpoint=args.out + ".partial.npz", resume=resume)
+            torch.cuda.synchronize()
+            meta.update(train_s=round(time.perf_counter() - t0, 1),
+                        final_loss=float(np.mean(losses[-20:])) if losses else None)
+        else:
+            st, meta = load_checkpoint(args.out)
+            net.set_state(st)
+        bank = HoughBank(ctx, spec, max_sel=256)
+        bank.load_peaks(draw(spec, np.arange(VALIDATION_FIRST, VALIDATION_FIRST + 51)))
+        bank.autotune()
+        heur = calibrate_heuristic(ctx, spec, 0, 4096)
+        meta["heuristic"] = {"beta": heur.beta, "null_logit": heur.null_logit,
+                             "cross_entropy": heur.cross_entropy}
+        for cap in (32, 256):
+            for name, scorer in (("network", net), ("heuristic", heur)):
+                tau, val = choose_tau(ctx, scorer, spec, VALIDATION_FIRST, args.val_maps, bank, cap)
+                summ = summarize(evaluate(ctx, scorer, spec, HELD_OUT_FIRST, args.eval_maps, bank,
+                                          tau, cap))
+                meta.setdefault("tau", {}).setdefault(name, {})[str(cap)] = tau
+                meta.setdefault("validation", {}).setdefault(name, {})[str(cap)] = val
+                meta.setdefault("held_out", {}).setdefault(name, {})[str(cap)] = summ
+                log(f"{name} <= {cap} tiles: tau {tau} held-out {json.dumps(summ)}")
+        meta.update(epoch=args.epochs, step_in_epoch=0, epochs=args.epochs, n_train=args.n_train,
+                    peakmaps=spec.peakmaps, validation_first=VALIDATION_FIRST,
+                    held_out_first=HELD_OUT_FIRST, eval_maps=args.eval_maps)
+        save_checkpoint(args.out, net.state(), meta)
+        log(f"wrote {args.out}")
+    net.close()
+    bank.plan.close()
+    ctx.close()
+
+
+if __name__ == "__main__":
+    _main()

@@ -83,6 +83,39 @@ def strain_series(n_samples: int, fs: float, seed: int, injections=(), sigma: fl
     return out
 
 
+def strain_series_device(out, fs: float, seed: int, injections=(), sigma: float = 1.0):
+    """The recipe of strain_series drawn on a CUDA device into the float32 tensor `out`: white
+    Gaussian noise N(0, sigma^2) from torch's counter-based Philox generator seeded with `seed`,
+    plus the injections' h(t) = amp sin(phi(t) + phase0) with phi the closed form of
+    powerlaw_phase, summed in float64 before the one rounding to float32.  The noise draws differ
+    from strain_series' (another generator); their distribution is the same."""
+    import torch
+    gen = torch.Generator(device=out.device)
+    gen.manual_seed(int(seed) & 0x7FFFFFFFFFFFFFFF)
+    if not injections:
+        torch.randn(out.shape, generator=gen, out=out)
+        if sigma != 1.0:
+            out.mul_(sigma)
+        return out
+    x = torch.randn(out.shape, generator=gen, dtype=torch.float64, device=out.device)
+    if sigma != 1.0:
+        x.mul_(sigma)
+    t = torch.arange(out.numel(), dtype=torch.float64, device=out.device).div_(fs)
+    for inj in injections:
+        a = (inj.n - 1.0) * inj.k * inj.f0 ** (inj.n - 1.0)
+        if a == 0.0:
+            ph = t * (2.0 * math.pi * inj.f0)
+        elif abs(inj.n - 2.0) < 1e-12:
+            ph = torch.log1p(t * a).mul_(2.0 * math.pi * inj.f0 / a)
+        else:
+            e = (inj.n - 2.0) / (inj.n - 1.0)
+            ph = torch.expm1(torch.log1p(t * a).mul_(e)).mul_(
+                2.0 * math.pi * inj.f0 * (inj.n - 1.0) / (a * (inj.n - 2.0)))
+        x.add_(torch.sin(ph.add_(inj.phase0)).mul_(inj.amp))
+    out.copy_(x)
+    return out
+
+
 def statistical_peaklist(n_fft: int, bin_lo: int, bin_hi: int, p_noise: float, seed: int,
                          tracks=(), p_track: float = 0.6):
     """Peak list (fft_idx, bin) sorted by (bin, fft) from a statistical model of a peakmap.

@@ -190,3 +190,19 @@ def test_plain_paper_all_subbands(built_lib, gpu_ctx, paper_case):
             if b >= 0:
                 assert hm[r_, c_] <= c["count"][b]
     plan.close()
+
+
+def test_shared_atomic_probe_counts_every_update(built_lib, gpu_ctx):
+    """The roofline probe's three access patterns each land every one of their atomic adds (the
+    array of every block sums to threads x iterations) and report positive cycle counts."""
+    gfh = built_lib
+    blocks, threads, iters = 8, 256, 64
+    cycles = torch.zeros(blocks, dtype=torch.int64, device="cuda")
+    sink = torch.zeros(blocks, dtype=torch.int32, device="cuda")
+    assert gpu_ctx.sms() >= 1
+    for mode in (0, 1, 2):
+        sink.zero_()
+        gpu_ctx.probe_smem_atomics(mode, blocks, threads, iters, cycles, sink)
+        torch.cuda.synchronize()
+        assert bool((sink == threads * iters).all()), mode
+        assert bool((cycles > 0).all())

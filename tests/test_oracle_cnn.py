@@ -243,3 +243,36 @@ def test_head_grads_and_pool_grad_are_adjoints():
     assert math.isclose(float((C.pool(a) * dp2).sum()), float((a * C.pool_grad(dp2, 11)).sum()),
                         rel_tol=1e-11)
     np.testing.assert_allclose(C.pool(a), a.sum(axis=1) / 11, rtol=1e-13)
+
+
+def test_line_scores_against_loops_and_a_planted_track():
+    """The non-learned proposer's line sums: against a loop that places each time bin's pixel from
+    the drift in floating point (no exact halves occur for K = 500, nb = 600: (2d+1)(2tb+1) 10 is
+    never a multiple of 4 plus 1536 mod 3072), and a straight track drawn into an empty image
+    scores 256 x its value in its own class, more than in any other class."""
+    rng = np.random.default_rng(4)
+    K, nb = 500, 600
+    img = C.bf16(np.log1p(rng.poisson(1.2, (256, 256))))
+    sc = C.line_scores(img, K, nb)
+    for d, xt in ((0, 0), (5, 17), (63, 63), (30, 2), (12, 40)):
+        best = None
+        for c0 in range(4 * xt, 4 * xt + 4):
+            s = 0.0
+            for tb in range(256):
+                off = math.floor((d + 0.5) * K / 64 * 256 / nb * (tb + 0.5) / 256 + 0.5)
+                if c0 - off >= 0:
+                    s += img[tb, c0 - off]
+            best = s if best is None else max(best, s)
+        assert math.isclose(sc[d * 64 + xt], best, rel_tol=1e-12), (d, xt)
+    empty = np.zeros((256, 256))
+    d, xt, c0 = 10, 40, 161
+    for tb in range(256):
+        empty[tb, c0 - ((2 * d + 1) * (2 * tb + 1) * K + 128 * nb) // (256 * nb)] = 1.0
+    s2 = C.line_scores(empty, K, nb)
+    assert s2[d * 64 + xt] == 256.0 and np.argmax(s2) == d * 64 + xt
+    assert np.sort(s2)[-2] < 256.0
+    lg = C.heuristic_logits(s2, 2.0, -1.5)
+    assert lg[-1] == -1.5 and lg.size == 4097
+    z = (s2 - s2.mean()) / s2.std()
+    np.testing.assert_allclose(lg[:-1], 2.0 * z, rtol=1e-13)
+    assert np.all(C.heuristic_logits(np.ones(4096), 3.0, 0.0)[:-1] == 0.0)
