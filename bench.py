@@ -75,6 +75,8 @@ def parse():
     ap.add_argument("--tile", default=None, help="rows,cols,threads of the Hough tiles")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload only: leave out the batched_n, uneven and proposer sub-objects")
     ap.add_argument("--sequential", action="store_true",
                     help="also time one plan per map (always on for batched_n)")
     ap.add_argument("--epochs", type=int, default=3,
@@ -213,6 +215,160 @@ def traffic_for(kernel):
 # CPU oracle (baseline / reference arm)
 # ---------------------------------------------------------------------------------------------
 
+def host_cpu():
+    """(usable cores, CPU model) of this host."""
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count() or 1
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        import platform
+        model = platform.processor() or platform.machine()
+    return cores, model
+
+
+_OW = {}
+
+
+def _oracle_attach(names):
+    """Worker start-up: attach the shared arrays (series, peak list) by name; one numpy thread."""
+    from multiprocessing import shared_memory
+    os.environ["OMP_NUM_THREADS"] = "1"
+    for key, (name, dtype, n) in names.items():
+        shm = shared_memory.SharedMemory(name=name)
+        _OW[key + "_shm"] = shm
+        _OW[key] = np.ndarray((n,), dtype=np.dtype(dtype), buffer=shm.buf)
+
+
+def _oracle_peak_chunk(task):
+    """Peaks of frames [i0, i1) of the shared series: the oracle's peakmap of that slice (frames
+    are independent, so the union over slices is the peakmap of the whole series)."""
+    from oracle import gfh_oracle as O
+    i0, i1, fs, t_fft, lo, hi = task
+    N = int(round(fs * t_fft))
+    hop = N // 2
+    fi, bj = O.peakmap(_OW["x"][i0 * hop:(i1 - 1) * hop + N], fs, t_fft, lo, hi)
+    return fi.astype(np.int64) + i0, bj.astype(np.int64)
+
+
+def _oracle_rows(task):
+    """The oracle's k rows `rows` of one map on the shared peak list (each row on its own)."""
+    from oracle import gfh_oracle as O
+    fields, rows = task
+    og = O.make_grid(O.Grid(**{k: v for k, v in fields.items() if k != "list"}))
+    t0 = time.perf_counter()
+    out = [O.hough_row(og, _OW["fi"], _OW["bj"], int(r)) for r in rows]
+    return time.perf_counter() - t0, out
+
+
+class OraclePool:
+    """Spawned worker processes (spawn: safe after CUDA use) running the unmodified oracle on every
+    host core: the peakmap split by frames, Hough rows split by rows; inputs in shared memory."""
+
+    def __init__(self, cores=None):
+        import multiprocessing as mp
+        self.cores = cores or host_cpu()[0]
+        self.mp = mp.get_context("spawn")
+        self.pool = None
+        self.shms = []
+
+    def _share(self, arrays):
+        from multiprocessing import shared_memory
+        names = {}
+        for key, a in arrays.items():
+            a = np.ascontiguousarray(a)
+            shm = shared_memory.SharedMemory(create=True, size=max(1, a.nbytes))
+            np.ndarray(a.shape, a.dtype, buffer=shm.buf)[...] = a
+            self.shms.append(shm)
+            names[key] = (shm.name, a.dtype.str, a.size)
+        return names
+
+    def start(self, arrays):
+        self.close_pool()
+        self.pool = self.mp.Pool(self.cores, initializer=_oracle_attach, initargs=(self._share(arrays),))
+        return self
+
+    def peakmap(self, x, fs, t_fft, lo, hi):
+        """(fft_idx, bin) sorted by (bin, FFT), identical to O.peakmap(x, ...)."""
+        self.start({"x": np.asarray(x, np.float32)})
+        N = int(round(fs * t_fft))
+        n_frames = (x.size - N) // (N // 2) + 1
+        step = max(1, -(-n_frames // (4 * self.cores)))
+        tasks = [(i0, min(n_frames, i0 + step), fs, t_fft, lo, hi) for i0 in range(0, n_frames, step)]
+        parts = self.pool.map(_oracle_peak_chunk, tasks)
+        fi = np.concatenate([p[0] for p in parts])
+        bj = np.concatenate([p[1] for p in parts])
+        order = np.lexsort((fi, bj))
+        return fi[order].astype(np.uint32), bj[order].astype(np.uint32)
+
+    def rows(self, fi, bj, jobs):
+        """jobs: [(fields, rows)] -> [(seconds, [row arrays])] in job order."""
+        self.start({"fi": np.asarray(fi, np.uint32), "bj": np.asarray(bj, np.uint32)})
+        return self.pool.map(_oracle_rows, jobs)
+
+    def close_pool(self):
+        if self.pool is not None:
+            self.pool.close()
+            self.pool.join()
+            self.pool = None
+        for shm in self.shms:
+            shm.close()
+            shm.unlink()
+        self.shms = []
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close_pool()
+
+
+def oracle_sample_allcores(name, series, rank=0, rows_per_map=None, pool=None):
+    """The oracle on every host core on a bounded sample: the full peakmap (frames split over the
+    cores), then `rows_per_map` k rows of every map (rows split over the cores); the step time is
+    the measured wall time with the rows extrapolated to all rows of each map."""
+    from oracle import gfh_oracle as O
+    spec, pm, grids = workload(name, rank)
+    own = pool is None
+    pool = pool or OraclePool()
+    try:
+        rows_per_map = rows_per_map or 4 * pool.cores
+        t0 = time.perf_counter()
+        fi, bj = pool.peakmap(series, spec.fs, spec.t_fft, pm["bin_lo"], pm["bin_hi"])
+        t_pm = time.perf_counter() - t0
+        jobs, updates, n_rows = [], 0, []
+        for f in grids:
+            og = O.make_grid(O.Grid(**{k: v for k, v in f.items() if k != "list"}))
+            updates += int(((bj >= og.bin_lo) & (bj <= og.bin_hi)).sum()) * og.n_k
+            rows = np.linspace(0, og.n_k - 1, min(rows_per_map, og.n_k)).astype(int)
+            n_rows.append((og.n_k, rows.size))
+            for chunk in np.array_split(rows, max(1, min(rows.size, pool.cores))):
+                if chunk.size:
+                    jobs.append((f, chunk.tolist()))
+        t1 = time.perf_counter()
+        pool.rows(fi, bj, jobs)
+        t_rows_wall = time.perf_counter() - t1
+        # wall time of the sampled rows scaled by (all rows / sampled rows), over all maps
+        frac = sum(k for k, _ in n_rows) / sum(r for _, r in n_rows)
+        t_step = t_pm + t_rows_wall * frac
+    finally:
+        if own:
+            pool.close_pool()
+    sample = (f"oracle peakmap of the full series ({t_pm:.1f} s, frames split over {pool.cores} "
+              f"processes) + {rows_per_map} of the k rows of each of the {len(grids)} maps (rows "
+              f"split over the processes, {t_rows_wall:.1f} s), extrapolated to all rows; numpy, "
+              f"one thread per process")
+    return updates / t_step, t_step, sample, pool.cores
+
 def oracle_sample(name, series=None, rank=0, rows_per_map=20):
     """Times the oracle on a bounded sample: the full peakmap, then `rows_per_map` k rows of every
     map; the step time is extrapolated to all rows."""
@@ -282,25 +438,44 @@ def run_reference(args):
         return reference_followup(args)
     if args.workload == "splice":
         return reference_splice(args)
+    from oracle import gfh_oracle as O
     spec, pm, grids = workload(args.workload, 0)
     x = spec.series()
-    vals, times = [], []
-    for i in range(args.warmup + args.steps):
-        v, t, sample = oracle_sample(args.workload, x, 0,
-                                     rows_per_map=1 if args.workload == "paper_grids" else 10)
-        if i >= args.warmup:
-            vals.append(v)
-            times.append(t)
+    ogs = [O.make_grid(O.Grid(**{k: v for k, v in f.items() if k != "list"})) for f in grids]
+    vals, times, walls = [], [], []
+    cores, model = host_cpu()
+    with OraclePool(cores) as pool:
+        for i in range(args.warmup + args.steps):
+            w0 = time.perf_counter()
+            v, t, sample, used = oracle_sample_allcores(args.workload, x, 0, pool=pool,
+                                                        rows_per_map=4 if args.workload == "paper_grids" else None)
+            if i >= args.warmup:
+                vals.append(v)
+                times.append(t)
+                walls.append(time.perf_counter() - w0)
     value = float(np.mean(vals))
     line = {"impl": "reference", "metric": "Hough updates/s (peaks x k-bins)", "value": value,
             "unit": "updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32 counts, fp32 spectra, fp64 grid",
-            "data": "synthetic", "config": {"workload": describe(args.workload, spec, grids)},
-            "cpu_baseline": {"value": value, "unit": "updates/s", "cores": 1, "kind": "oracle",
-                             "sample": sample},
+            "data": "synthetic", "config": plain_config(args.workload, spec, grids, ogs),
+            "sampled_step_wall_s": float(np.mean(walls)),
+            "cpu_baseline": {"value": value, "unit": "updates/s", "cores": used, "kind": "oracle",
+                             "sample": sample, "cpu_model": model, "nproc": cores},
             "e2e": {"value": value, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def plain_config(name, spec, grid_fields, grids):
+    """The workload's `config` (the same on the GPU arm and the CPU reference arm): description,
+    maps, cells, k rows and the L2 statement.  `grids` have n_x0 and n_k."""
+    ld = [(g.n_x0 + 31) // 32 * 32 for g in grids]
+    map_bytes = sum(g.n_k * l * 4 for g, l in zip(grids, ld))
+    return {"workload": describe(name, spec, grid_fields), "maps": len(grids),
+            "cells": int(sum(g.n_k * g.n_x0 for g in grids)),
+            "k_rows": sorted({int(g.n_k) for g in grids}),
+            "l2": "inputs larger than L2 (series %d MB, maps %d MB per step)"
+                  % (spec.n_samples * 4 // 1000000, map_bytes // 1000000)}
 
 
 # ---------------------------------------------------------------------------------------------
@@ -540,14 +715,12 @@ def run_gpu(args):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int32 counts, fp32 spectra, fp64 grid", "data": "synthetic",
-        "config": {"workload": describe(args.workload, spec, grid_fields),
-                   "maps": len(grids), "peaks": n_peaks, "updates_per_step": updates,
-                   "cells": int(sum(g.n_k * g.n_x0 for g in grids)),
-                   "l2": "inputs larger than L2 (series %d MB, maps %d MB per step)" % (h2d // 1000000, map_bytes // 1000000),
-                   "tile": list(tile) if tile else (list(tuned) if tuned else "default"),
-                   "tile_source": "given" if tile else ("autotuned" if tuned else "default"),
-                   "timing": "CUDA graph of the step" if graph is not None else "direct calls",
-                   "plan_build_s": round(t_plan, 3), "autotune_s": round(t_tune, 3)},
+        "config": plain_config(args.workload, spec, grid_fields, grids),
+        "work": {"peaks": n_peaks, "updates_per_step": updates},
+        "run": {"tile": list(tile) if tile else (list(tuned) if tuned else "default"),
+                "tile_source": "given" if tile else ("autotuned" if tuned else "default"),
+                "timing": "CUDA graph of the step" if graph is not None else "direct calls",
+                "plan_build_s": round(t_plan, 3), "autotune_s": round(t_tune, 3)},
         "breakdown_ms": {"step_graph": ms_graph, "step_direct": ms_direct, "hough_select": ms_hough,
                          "peakmap_and_host": ms_direct - ms_hough},
         "roofline": {**atomic_roofline(ctx, stream, achieved),
@@ -568,13 +741,233 @@ def run_gpu(args):
     }
     if sequential:
         line["batched_vs_one_plan_per_map"] = sequential
+    if args.workload == "plain_paper" and world == 1 and not args.no_extras:
+        # configs 3-5 as compact sub-objects of the default line (their own timed regions)
+        ext_steps, ext_warm = max(3, min(args.steps, 10)), max(3, args.warmup)
+        t0 = time.perf_counter()
+        line["batched_n"] = measure_batched_n(ctx, stream, ext_steps, ext_warm)
+        line["uneven"] = measure_uneven(ctx, stream, ext_steps, ext_warm)
+        line["proposer"] = measure_proposer(ctx, stream, ext_steps, ext_warm, eval_maps=args.eval_maps)
+        line["extras_s"] = round(time.perf_counter() - t0, 1)
     if world == 1 and not args.no_cpu_baseline:
-        v, t, sample = oracle_sample(args.workload, series_np,
-                                     rows_per_map=2 if args.workload == "paper_grids" else 20)
-        line["cpu_baseline"] = {"value": v, "unit": "updates/s", "cores": 1, "kind": "oracle", "sample": sample}
+        cores, model = host_cpu()
+        v, t, sample, used = oracle_sample_allcores(args.workload, series_np,
+                                                    rows_per_map=4 if args.workload == "paper_grids" else None)
+        v1, t1, sample1 = oracle_sample(args.workload, series_np, rows_per_map=2 if args.workload == "paper_grids" else 5)
+        line["cpu_baseline"] = {"value": v, "unit": "updates/s", "cores": used, "kind": "oracle",
+                                "sample": sample, "cpu_model": model, "nproc": cores,
+                                "one_core": {"value": v1, "sample": sample1}}
     print(json.dumps(line), flush=True)
     plan.close()
     ctx.close()
+
+
+# ---------------------------------------------------------------------------------------------
+# Compact measurements of the batched and pruned forms (sub-objects of the default line)
+# ---------------------------------------------------------------------------------------------
+
+def _time_ms(stream, fn, steps):
+    """Mean device time of fn() over `steps` calls, CUDA events on `stream`."""
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(steps):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def _roofline_of(ctx, stream, updates, map_bytes, ms):
+    """The accumulator's bound: max(map store / HBM peak, 2 atomics per update / atomic peak)."""
+    peak, _ = atomic_peak(ctx, stream)
+    t_atomic = 2.0 * updates / (peak * 1e9) * 1e3
+    t_hbm = map_bytes / (HBM_PEAK * 1e9) * 1e3
+    bound = "smem_atomic" if t_atomic >= t_hbm else "hbm"
+    return {"bound": bound, "ms_at_bound": max(t_atomic, t_hbm), "frac": max(t_atomic, t_hbm) / ms,
+            "atomic_ms": t_atomic, "hbm_ms": t_hbm, "atomic_peak_gatomic_s": peak,
+            "hbm_peak_gbs": HBM_PEAK}
+
+
+def measure_batched_n(ctx, stream, steps, warmup, tile=(8, 3072, 512)):
+    """Config 3: the plain_small peakmap at 51 braking indices, one launch (CUDA graph), against
+    one plan per braking index run one after another."""
+    import torch
+    from paper_1810_09784_gb300 import gfh
+    spec, pm, grid_fields = workloads.batched_n(seed=ranks.rank_seed(1, 0))
+    x = torch.from_numpy(spec.series()).cuda()
+    cap = int(spec.n_fft * (pm["bin_hi"] - pm["bin_lo"] + 1) * 0.12) + 1024
+    fo = torch.empty(cap, dtype=torch.int32, device="cuda")
+    bo = torch.empty(cap, dtype=torch.int32, device="cuda")
+    with torch.cuda.stream(stream):
+        n = ctx.peakmap(x, spec.fs, spec.t_fft, pm["bin_lo"], pm["bin_hi"], 2.5, fo, bo)
+    off = torch.tensor([0, n], dtype=torch.int64, device="cuda")
+    grids = [gfh.grid_make(gfh.Grid(**f)) for f in grid_fields]
+    bins = bo[:n].cpu().numpy()
+    updates = sum(int(((bins >= g.bin_lo) & (bins <= g.bin_hi)).sum()) * g.n_k for g in grids)
+    maps = [torch.empty((g.n_k, g.ld_x0), dtype=torch.int32, device="cuda") for g in grids]
+    cands = [torch.empty(g.n_bands * gfh.CANDIDATE_BYTES, dtype=torch.uint8, device="cuda") for g in grids]
+    stats = torch.empty(len(grids) * gfh.STATS_BYTES, dtype=torch.uint8, device="cuda")
+    plan = gfh.Plan(ctx, grids, maps, cands, stats, tile=tile)
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            plan.execute(fo, bo, off, 1)
+        torch.cuda.synchronize()
+        if ctx.check() != gfh.GFH_OK:
+            raise RuntimeError("batched_n: input check failed")
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            plan.execute(fo, bo, off, 1)
+        graph.replay()
+        ms = _time_ms(stream, graph.replay, steps)
+        singles = [gfh.Plan(ctx, [g], [m], [c], None, tile=tile) for g, m, c in zip(grids, maps, cands)]
+        for sp in singles:
+            sp.execute(fo, bo, off, 1)
+        ms_seq = _time_ms(stream, lambda: [sp.execute(fo, bo, off, 1) for sp in singles], max(2, steps // 4))
+    for sp in singles:
+        sp.close()
+    map_bytes = sum(g.n_k * g.ld_x0 * 4 for g in grids)
+    out = {"workload": "batched_n: the plain_small peakmap at n = 2.0..7.0 (51 maps, 4000 -> 1000 "
+                       "k rows), one launch replayed as a CUDA graph",
+           "maps": len(grids), "peaks": int(n), "updates_per_step": updates,
+           "map_bytes": map_bytes, "tile": list(tile), "ms_per_step": ms,
+           "updates_per_s": updates / (ms * 1e-3), "ms_one_plan_per_map": ms_seq,
+           "speedup_vs_one_plan_per_map": ms_seq / ms,
+           "roofline": _roofline_of(ctx, stream, updates, map_bytes, ms)}
+    plan.close()
+    del maps, cands, stats, graph
+    torch.cuda.empty_cache()
+    return out
+
+
+def measure_uneven(ctx, stream, steps, warmup, tile=(8, 3072, 512)):
+    """Config 4: 256 uneven peakmaps (statistical model), every sub-band map in one launch, against
+    one plan per peakmap run one after another."""
+    import torch
+    from paper_1810_09784_gb300 import gfh
+    t0 = time.perf_counter()
+    lists, grid_fields, _ = workloads.uneven(seed=ranks.rank_seed(4, 0))
+    t_gen = time.perf_counter() - t0
+    off_np = np.cumsum([0] + [len(f) for f, _ in lists]).astype(np.int64)
+    fi = torch.from_numpy(np.concatenate([f for f, _ in lists]).view(np.int32)).cuda()
+    bj = torch.from_numpy(np.concatenate([b for _, b in lists]).view(np.int32)).cuda()
+    off = torch.from_numpy(off_np).cuda()
+    grids = [gfh.grid_make(gfh.Grid(**f)) for f in grid_fields]
+    updates = 0
+    for f, g in zip(grid_fields, grids):
+        b = lists[f["list"]][1]
+        updates += int(((b >= g.bin_lo) & (b <= g.bin_hi)).sum()) * g.n_k
+    del lists
+    maps = [torch.empty((g.n_k, g.ld_x0), dtype=torch.int32, device="cuda") for g in grids]
+    cands = [torch.empty(g.n_bands * gfh.CANDIDATE_BYTES, dtype=torch.uint8, device="cuda") for g in grids]
+    stats = torch.empty(len(grids) * gfh.STATS_BYTES, dtype=torch.uint8, device="cuda")
+    plan = gfh.Plan(ctx, grids, maps, cands, stats, tile=tile)
+    nl = len(off_np) - 1
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            plan.execute(fi, bj, off, nl)
+        torch.cuda.synchronize()
+        if ctx.check() != gfh.GFH_OK:
+            raise RuntimeError("uneven: input check failed")
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            plan.execute(fi, bj, off, nl)
+        graph.replay()
+        ms = _time_ms(stream, graph.replay, steps)
+        per_list = {}
+        for gf, g, m, c in zip(grid_fields, grids, maps, cands):
+            per_list.setdefault(gf["list"], []).append((g, m, c))
+        singles = [gfh.Plan(ctx, [x[0] for x in v], [x[1] for x in v], [x[2] for x in v], None,
+                            tile=tile) for v in per_list.values()]
+        for sp in singles:
+            sp.execute(fi, bj, off, nl)
+        ms_seq = _time_ms(stream, lambda: [sp.execute(fi, bj, off, nl) for sp in singles], 1)
+    for sp in singles:
+        sp.close()
+    map_bytes = sum(g.n_k * g.ld_x0 * 4 for g in grids)
+    npk = np.diff(off_np)
+    out = {"workload": "uneven: 256 statistical peakmaps (1-24 h, T_FFT 1-8 s, bands inside "
+                       "50-2000 Hz, 0-3 power-law tracks each), 100 Hz sub-bands, 1000 k rows, "
+                       "every map in one launch replayed as a CUDA graph",
+           "data": "statistical peakmap model (independent cells at p0, tracks at p = 0.6)",
+           "peakmaps": nl, "maps": len(grids), "peaks": int(off_np[-1]),
+           "peaks_per_peakmap": [int(npk.min()), int(npk.max())], "updates_per_step": updates,
+           "map_bytes": map_bytes, "tile": list(tile), "generate_s": round(t_gen, 1),
+           "ms_per_step": ms, "updates_per_s": updates / (ms * 1e-3),
+           "ms_one_plan_per_peakmap": ms_seq, "speedup_vs_one_plan_per_peakmap": ms_seq / ms,
+           "roofline": _roofline_of(ctx, stream, updates, map_bytes, ms)}
+    plan.close()
+    del maps, cands, stats, graph, fi, bj
+    torch.cuda.empty_cache()
+    return out
+
+
+def measure_proposer(ctx, stream, steps, warmup, eval_maps=51 * 196):
+    """Config 5 from the committed checkpoint (no training here): recall of the pruned search
+    against the full exact Hough on held-out maps built from seeded series through gfh_peakmap,
+    and the time of one batch of 51 maps (resident peak lists) searched in full and pruned, for
+    the network and for the non-learned line-sum ranker."""
+    import torch
+    from paper_1810_09784_gb300 import gfh
+    from paper_1810_09784_gb300 import proposer as PR
+    spec = PR.ProposerSpec()
+    nl = len(PR.N_GRID)
+    path = PR.checkpoint_path()
+    state, meta = PR.load_checkpoint(path)
+    out = {"workload": "proposer: 51 maps per step (n = 2.0..7.0), plain_small-shaped (1799 FFTs, "
+                       "100-400 Hz, 500 k rows), half with one power-law injection (SNR 2-8); "
+                       "at most 32 of 64 x 64 coarse tiles per map, full search of maps whose "
+                       "proposal leaves more than tau",
+           "data": "peakmaps built by gfh_peakmap from seeded white-noise series with power-law "
+                   "injections",
+           "checkpoint": f"{path.parent.name}/{path.name}: trained on {meta.get('n_train')} "
+                         f"series peakmaps, {meta.get('epochs')} passes, step {state['step']}"}
+    with torch.cuda.stream(stream):
+        net = gfh.Cnn(ctx, nl, seed=1)
+        net.set_state(state)
+        bank = PR.HoughBank(ctx, spec, max_sel=32)
+        bank.load_peaks(PR.draw(spec, np.arange(PR.VALIDATION_FIRST, PR.VALIDATION_FIRST + nl)))
+        tuned, _ = bank.autotune()
+        hm = meta.get("heuristic", {})
+        heur = PR.LineHeuristic(ctx, spec, hm.get("beta", 1.0), hm.get("det_a", 1.0), hm.get("det_b", 6.0))
+        scorers = {"network": (net, meta["tau"]["network"]["32"]),
+                   "line_heuristic": (heur, meta["tau"]["heuristic"]["32"])}
+        for name, (sc, tau) in scorers.items():
+            t0 = time.perf_counter()
+            summ = PR.summarize(PR.evaluate(ctx, sc, spec, PR.HELD_OUT_FIRST, eval_maps, bank, tau, 32))
+            search = PR.PrunedSearch(ctx, sc, bank, tau, 32)
+            t_full, t_pr = [], []
+            for st in range(warmup + steps):
+                s0 = PR.HELD_OUT_FIRST + nl * st
+                bank.load_peaks(PR.draw(spec, np.arange(s0, s0 + nl)))
+                torch.cuda.synchronize()
+                a = _time_ms(stream, bank.full, 1)
+                b = _time_ms(stream, search.run, 1)
+                if st >= warmup:
+                    t_full.append(a)
+                    t_pr.append(b)
+            ms_full, ms_pr = float(np.mean(t_full)), float(np.mean(t_pr))
+            out[name] = {"tau": tau, "recall": summ["recall"], "held_out_maps": summ["maps"],
+                         "detected_full": summ["det_full"], "detected_kept": summ["det_kept"],
+                         "fallback_frac": summ["fallback_frac"],
+                         "fallback_noise": summ["fallback_noise"],
+                         "mean_tiles_pruned": summ["mean_tiles_pruned"],
+                         "ms_full_exact_per_step": ms_full, "ms_pruned_per_step": ms_pr,
+                         "speedup_vs_full_exact": ms_full / ms_pr,
+                         "eval_s": round(time.perf_counter() - t0, 1)}
+        out["tile"] = list(tuned)
+        if "beta" in hm:
+            out["line_heuristic"]["parameters"] = {k: hm[k] for k in ("beta", "det_a", "det_b")}
+        f0_, f1_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        search = PR.PrunedSearch(ctx, net, bank, meta["tau"]["network"]["32"], 32)
+        search.propose()
+        torch.cuda.synchronize()
+        out["network_forward_ms_51_maps"] = _time_ms(stream, lambda: net.forward(search.images, search.logits), 5)
+    net.close()
+    bank.plan.close()
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_gpu_lists(args):

@@ -529,12 +529,14 @@ int gfh_propose_tiles(gfh_ctx* ctx, const float* d_logits, int32_t batch, const 
  * the observation: in time bin tb it lies off = floor(((2d + 1)(2tb + 1) n_k + 128 n_bins) /
  * (256 n_bins)) columns left of its start.  d_scores [batch][4096] (may be NULL) = the largest
  * over the four start columns of the sum over tb of the pixels on that line (pixels left of column
- * 0 add nothing); the sums are exact.  d_logits [batch][4097]: beta (score - mean) / std over the
- * image's scores (0 when they are all equal), and null_logit for the no-signal class, ready for
- * gfh_propose_tiles.  Asynchronous.
+ * 0 add nothing); the sums are exact.  d_logits [batch][4097], ready for gfh_propose_tiles: with
+ * z = (score - mean) / std over the image's scores (0 when they are all equal), class logit
+ * beta z (beta >= 0) and no-signal logit LSE + det_c - det_a zmax, LSE = log sum exp(beta z) over
+ * the classes and zmax the largest z, so that p(no signal) = 1 / (1 + exp(det_a zmax - det_c)).
+ * Asynchronous.
  */
 int gfh_line_scores(gfh_ctx* ctx, const void* d_images, int32_t batch, int32_t n_k, int32_t n_bins,
-                    float beta, float null_logit, float* d_scores, float* d_logits);
+                    float beta, float det_a, float det_c, float* d_scores, float* d_logits);
 
 /*
  * One 3x3 layer alone (tests): mode 0 forward out = relu(conv(in) + bias) into d_res (bf16 NHWC);
@@ -609,14 +611,16 @@ int gfh_device_sms(gfh_ctx* ctx, int32_t* h_sms);
  * per-bin counts: 256-aligned (bins * ceil(n_fft/32) * 4) + (bins + 1) * 8 bytes, with bins =
  * bin_hi - bin_lo + 1 (for example 7800 bins x 5040 FFTs fits).  Larger requests return
  * GFH_ERR_SIZE and launch nothing.
- *   stream      cudaStream_t (as void*) on the current device; all work is asynchronous on it
- *   d_n_peaks   device int64 that receives the total number of peaks; when it exceeds cap, the
- *               outputs hold the first cap peaks in (bin, FFT) order
+ *   stream      cudaStream_t (as void*) of the current device (GFH_ERR_ARG for a stream of
+ *               another device); all work is asynchronous on it
+ *   d_n_peaks   device int64 that receives the total number of peaks, which may exceed cap; the
+ *               outputs then hold the first cap peaks in (bin, FFT) order
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.  All calls share the one
- * array, so calls that overlap on the GPU (concurrent streams, or several host threads) race and
- * must be serialised by the caller; every call rewrites all the scratch it reads, so no state
- * carries over between calls.
+ * that device current and keeps it for later calls; make that first call before any stream
+ * capture.  A cudaDeviceReset of that device invalidates the kept address (the library must then
+ * be reloaded).  All calls share the one array, so calls that overlap on the GPU (concurrent
+ * streams, or several host threads) race and must be serialised by the caller; every call
+ * rewrites all the scratch it reads, so no state carries over between calls.
  */
 #define GFH_STATIC_SCRATCH_BYTES (8u << 20)
 int gfh_peaks_from_power_static(void* stream, const float* d_power, int64_t ld, int32_t n_fft,

@@ -22,8 +22,9 @@ What is written here is the plain definition of each step:
   head grads the adjoints of the head (a linear map) in its weights, biases and input
   AdamW      m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2; w -= lr (m/c1 / (sqrt(v/c2) + eps) + wd w)
   lines      the non-learned proposer: per class the pixel sum along the straight line of its
-             mid drift from each of the x0 tile's start columns, the best start kept; logits =
-             beta times the standardised sums
+             mid drift from each of the x0 tile's start columns, the best start kept; class logits
+             beta times the standardised sums z, and a no-signal probability that falls
+             logistically with the largest z
   proposal   p = softmax(logits); class (d, xt) spreads p evenly over k tiles
              [floor(d gb), max(lo, ceil((d+1) ga) - 1)] (clamped to 63); tiles ranked by score, ties
              to the lower id; the first n leave resid_n = max(0, 1 - p_null - their sum); with
@@ -276,13 +277,17 @@ def line_scores(ch0: np.ndarray, K: int, nb: int) -> np.ndarray:
     return out
 
 
-def heuristic_logits(scores: np.ndarray, beta: float, null_logit: float) -> np.ndarray:
-    """beta (score - mean) / std over the 4096 scores (population std; 0 if constant), then the
-    no-signal logit."""
+def heuristic_logits(scores: np.ndarray, beta: float, det_a: float, det_c: float) -> np.ndarray:
+    """z = (score - mean) / std over the 4096 scores (population std; 0 if constant); class logits
+    beta z; no-signal logit log(sum exp(beta z)) + det_c - det_a max(z), which makes
+    p(no signal) = 1 / (1 + exp(det_a max(z) - det_c))."""
     s = np.asarray(scores, np.float64)
     sd = s.std()
     z = (s - s.mean()) / sd if sd > 0 else np.zeros_like(s)
-    return np.concatenate([beta * z, [null_logit]])
+    lz = beta * z
+    m = lz.max()
+    lse = m + math.log(np.exp(lz - m).sum())
+    return np.concatenate([lz, [lse + det_c - det_a * z.max()]])
 
 
 # ---- proposals ---------------------------------------------------------------------------------

@@ -251,12 +251,14 @@ __global__ void __launch_bounds__(1024) k_propose(const float* __restrict__ logi
 // sits off(d, tb) = round((2d + 1)(2tb + 1) K / (256 nb)) image columns left of its start column.
 // score = the largest, over the four start columns c0, of sum_tb ch0[tb][c0 - off(d, tb)] (columns
 // left of the image add 0).  Sums of bf16 values (multiples of 2^-8 when >= 1/2, below 2^13 in
-// total) are exact in fp32.  logit = beta (score - mean) / std over the image's 4096 scores, the
-// no-signal logit = null_logit.  One block of 1024 threads per image, channel 0 (128 KB) and the
+// total) are exact in fp32.  z = (score - mean) / std over the image's 4096 scores; class logit =
+// beta z; no-signal logit = LSE + det_c - det_a zmax (LSE = log sum_c exp(beta z_c), zmax the
+// largest z), so that p(no signal) = 1 / (1 + exp(det_a zmax - det_c)): detection by the largest
+// line sum, localisation by the line sums.  One block of 1024 threads per image, channel 0 (128 KB) and the
 // offset table (64 KB) staged in shared memory; thread t owns x0 tile t % 64 and drift classes
 // t / 64 + 16 j, j < 4, and sums its four start columns along each line together.
 __global__ void __launch_bounds__(1024) k_line_scores(const uint32_t* __restrict__ img, int K,
-                                                      int nb, float beta, float null_logit,
+                                                      int nb, float beta, float det_a, float det_c,
                                                       float* __restrict__ scores,
                                                       float* __restrict__ logits) {
   extern __shared__ __align__(16) uint16_t ch0[];    // [256][256] bf16 bits, then off[64][256]
@@ -312,14 +314,44 @@ __global__ void __launch_bounds__(1024) k_line_scores(const uint32_t* __restrict
   const float mean = red[0][0] * (1.f / 4096.f);
   const float var = fmaxf(red[1][0] * (1.f / 4096.f) - mean * mean, 0.f);
   const float inv = var > 0.f ? 1.f / sqrtf(var) : 0.f;
+  __syncthreads();                                   // red is reused below
   float* const lo = logits + (int64_t)blockIdx.x * kClasses;
+  float zm = -INFINITY;
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const int c = (dq + 16 * j) * kTiles + xt;
     if (scores) scores[(int64_t)blockIdx.x * (kClasses - 1) + c] = sc[j];
-    lo[c] = beta * ((sc[j] - mean) * inv);
+    sc[j] = (sc[j] - mean) * inv;                    // z
+    lo[c] = beta * sc[j];
+    zm = fmaxf(zm, sc[j]);
   }
-  if (tid == 0) lo[kClasses - 1] = null_logit;
+  // zmax, then LSE of beta z (max first for the exponentials)
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) zm = fmaxf(zm, __shfl_xor_sync(0xffffffffu, zm, o));
+  if (lane == 0) red[0][warp] = zm;
+  __syncthreads();
+  if (warp == 0) {
+    float v = red[0][lane];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) red[1][0] = v;
+  }
+  __syncthreads();
+  zm = red[1][0];
+  const float lm = beta * zm;                        // the largest class logit (beta >= 0)
+  float e = 0.f;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) e += expf(beta * sc[j] - lm);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+  __syncthreads();
+  if (lane == 0) red[0][warp] = e;
+  __syncthreads();
+  if (tid == 0) {
+    float t = 0.f;
+    for (int w = 0; w < 32; ++w) t += red[0][w];
+    lo[kClasses - 1] = lm + logf(t) + det_c - det_a * zm;
+  }
 }
 
 // ---- tensor-core helpers --------------------------------------------------------------------------
@@ -1461,16 +1493,16 @@ extern "C" int gfh_propose_tiles(gfh_ctx* ctx, const float* d_logits, int32_t ba
 }
 
 extern "C" int gfh_line_scores(gfh_ctx* ctx, const void* d_images, int32_t batch, int32_t n_k,
-                               int32_t n_bins, float beta, float null_logit, float* d_scores,
-                               float* d_logits) {
+                               int32_t n_bins, float beta, float det_a, float det_c,
+                               float* d_scores, float* d_logits) {
   if (!ctx || !d_images || !d_logits || batch < 1 || batch > 65535 || n_k < 1 || n_bins < kImg ||
-      !(beta == beta) || !(null_logit == null_logit))
+      !(beta >= 0.f) || !(det_a == det_a) || !(det_c == det_c))
     return GFH_ERR_ARG;
   GFH_CUDA_TRY(cudaSetDevice(ctx->device));
   const int smem = kImg * kImg * 2 + kTiles * kImg * 4;
   GFH_CUDA_TRY(cudaFuncSetAttribute(k_line_scores, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   k_line_scores<<<batch, 1024, smem, ctx->stream>>>((const uint32_t*)d_images, n_k, n_bins, beta,
-                                                    null_logit, d_scores, d_logits);
+                                                    det_a, det_c, d_scores, d_logits);
   GFH_CUDA_TRY(cudaGetLastError());
   return GFH_OK;
 }

@@ -626,12 +626,20 @@ extern "C" int gfh_peaks_from_power_static(void* stream, const float* d_power, i
   const int n_words = (n_fft + 31) / 32;
   const size_t o_cnt = align256((size_t)n_bins * n_words * 4);
   if (o_cnt + ((size_t)n_bins + 1) * 8 > GFH_STATIC_SCRATCH_BYTES) return GFH_ERR_SIZE;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (st != nullptr && st != cudaStreamLegacy && st != cudaStreamPerThread) {
+    // the array's address is the current device's: a created stream must belong to that device
+    // (the default-stream handles always name the current device's)
+    int cur = -1, sdev = -1;
+    GFH_CUDA_TRY(cudaGetDevice(&cur));
+    GFH_CUDA_TRY(cudaStreamGetDevice(st, &sdev));
+    if (sdev != cur) return GFH_ERR_ARG;
+  }
   void* base = nullptr;
   const int rc = static_scratch_addr(&base);
   if (rc) return rc;
   uint32_t* bits = (uint32_t*)base;
   int64_t* cnt = (int64_t*)((char*)base + o_cnt);
-  cudaStream_t st = (cudaStream_t)stream;
   // Every word of the bit matrix and every count is rewritten below, so nothing left by an
   // earlier call is read.
   GFH_CUDA_TRY(launch_equalise(PowerIn{d_power, ld}, n_fft, bin_lo, bin_hi, (float)theta, bits,

@@ -161,7 +161,8 @@ def lib() -> ctypes.CDLL:
             "gfh_cnn_get_state": [vp, vp, vp, vp, P(i64)],
             "gfh_cnn_set_state": [vp, vp, vp, vp, i64],
             "gfh_cnn_read_tensor": [vp, i32, i32, vp, i64],
-            "gfh_line_scores": [vp, vp, i32, i32, i32, ctypes.c_float, ctypes.c_float, vp, vp],
+            "gfh_line_scores": [vp, vp, i32, i32, i32, ctypes.c_float, ctypes.c_float,
+                                ctypes.c_float, vp, vp],
             "gfh_probe_smem_atomics": [vp, i32, i32, i32, i32, vp, vp],
             "gfh_device_sms": [vp, P(i32)],
         }
@@ -515,8 +516,10 @@ def candidates_to_numpy(cands_tensor) -> np.ndarray:
 def peaks_from_power_static(stream, power, bin_lo: int, bin_hi: int, theta: float, fft_out,
                             bin_out, n_out) -> None:
     """gfh_peaks_from_power_static: peak selection without any device allocation, for callers
-    whose device memory belongs to another allocator.  Asynchronous on `stream`; the peak count
-    goes to the device int64 tensor `n_out`."""
+    whose device memory belongs to another allocator.  Asynchronous on `stream`, which must belong
+    to the current device; the total peak count goes to the device int64 tensor `n_out` and may
+    exceed fft_out.numel() (then only the first fft_out.numel() peaks, in (bin, FFT) order, are
+    written)."""
     rc = lib().gfh_peaks_from_power_static(_stream_handle(stream), _ptr(power), power.stride(0),
                                            power.shape[0], bin_lo, bin_hi, theta, _ptr(fft_out),
                                            _ptr(bin_out), fft_out.numel(), _ptr(n_out))
@@ -563,11 +566,11 @@ def propose_tiles(ctx: Context, logits, gain, k: int, top, resid, tau: float = -
     _ok(rc, "gfh_propose_tiles")
 
 
-def line_scores(ctx: Context, images, n_k: int, n_bins: int, beta: float, null_logit: float,
-                logits, scores=None) -> None:
+def line_scores(ctx: Context, images, n_k: int, n_bins: int, beta: float, det_a: float,
+                det_c: float, logits, scores=None) -> None:
     """gfh_line_scores: the non-learned proposer's straight-line sums and their logits."""
     rc = lib().gfh_line_scores(ctx.handle, _ptr(images), images.shape[0], n_k, n_bins, beta,
-                               null_logit, _ptr(scores), _ptr(logits))
+                               det_a, det_c, _ptr(scores), _ptr(logits))
     _ok(rc, "gfh_line_scores")
 
 

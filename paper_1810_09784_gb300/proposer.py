@@ -242,7 +242,6 @@ class DeviceBatch:
         self.p24[:B].copy_(torch.from_numpy(smp.p_track24.view(np.int32)))
         self.nplane[:B].copy_(torch.from_numpy(smp.nplane))
         self.gain[:B].copy_(torch.from_numpy(smp.gain))
-        assert np.all(np.diff(smp.index) == 1)
         if spec.peakmaps == "series":
             if getattr(self, "source", None) is None:
                 self.source = PeakSource(ctx, spec, self.images.shape[0])
@@ -251,6 +250,7 @@ class DeviceBatch:
             gfh.peaks_to_images(ctx, src.fft_c, src.bin_c, src.offsets, B, spec.n_fft,
                                 spec.bin_lo, spec.bin_hi, self.nplane[:B], self.images[:B])
         else:
+            assert np.all(np.diff(smp.index) == 1), "the statistical images take consecutive samples"
             gfh.synth_images(ctx, spec.seed, int(smp.index[0]), spec.n_fft, spec.bin_lo,
                              spec.bin_hi, spec.p_noise24, self.p24[:B], self.tracks[:B],
                              self.nplane[:B], self.images[:B])
@@ -518,24 +518,28 @@ def train_default(ctx: gfh.Context, net: gfh.Cnn, spec: ProposerSpec, epochs: in
 
 class LineHeuristic:
     """Stand-in for the network in PrunedSearch: gfh_line_scores ranks each class by the peak
-    counts along its straight mid-drift line in the image (no learning); beta and the no-signal
-    logit are its only two numbers, fitted by calibrate_heuristic."""
+    counts along its straight mid-drift line in the image (no learning): class logits beta z, and
+    p(no signal) = 1 / (1 + exp(det_a (zmax - det_b))) from the largest standardised line sum.
+    beta, det_a and det_b are its only numbers, fitted by calibrate_heuristic."""
 
     def __init__(self, ctx: gfh.Context, spec: ProposerSpec, beta: float = 1.0,
-                 null_logit: float = 0.0):
-        self.ctx, self.spec, self.beta, self.null_logit = ctx, spec, beta, null_logit
+                 det_a: float = 1.0, det_b: float = 6.0):
+        self.ctx, self.spec = ctx, spec
+        self.beta, self.det_a, self.det_b = beta, det_a, det_b
 
     def forward(self, images, logits, scores=None) -> None:
         spec = self.spec
         gfh.line_scores(self.ctx, images, spec.n_k, spec.bin_hi - spec.bin_lo + 1, self.beta,
-                        self.null_logit, logits, scores)
+                        self.det_a, self.det_a * self.det_b, logits, scores)
 
 
 def calibrate_heuristic(ctx: gfh.Context, spec: ProposerSpec, first: int, count: int,
-                        betas=(0.5, 1.0, 1.5, 2.0, 3.0, 4.0, 6.0, 8.0),
-                        nulls=tuple(np.linspace(-5.0, 15.0, 41))) -> LineHeuristic:
-    """The (beta, null logit) pair of least mean cross-entropy of the line-sum logits against the
-    labels of samples [first, first + count) (a two-number fit, as a temperature would be)."""
+                        betas=(0.5, 1.0, 2.0, 3.0, 4.0, 6.0, 8.0, 12.0),
+                        slopes=(0.25, 0.5, 1.0, 2.0, 4.0),
+                        thresholds=tuple(np.linspace(2.0, 14.0, 49))) -> LineHeuristic:
+    """The (beta, det_a, det_b) of least mean cross-entropy of the line-sum logits against the
+    labels of samples [first, first + count): a three-number fit, as a temperature and a detection
+    threshold would be."""
     import torch
     h = LineHeuristic(ctx, spec)
     buf = DeviceBatch(spec, 256)
@@ -554,18 +558,22 @@ def calibrate_heuristic(ctx: gfh.Context, spec: ProposerSpec, first: int, count:
     z = np.concatenate(zs)
     y = np.concatenate(labels).astype(np.int64)
     sig = y < NULL_CLASS
+    zmax = z.max(axis=1)
+    zy = z[np.arange(y.size), np.minimum(y, NULL_CLASS - 1)]
     best = None
     for beta in betas:
         bz = beta * z
         m = bz.max(axis=1)
-        lse_c = m + np.log(np.exp(bz - m[:, None]).sum(axis=1))     # log-sum-exp of the classes
-        zy = np.where(sig, bz[np.arange(y.size), np.minimum(y, NULL_CLASS - 1)], 0.0)
-        for c in nulls:
-            lse = np.logaddexp(lse_c, c)
-            ce = float(np.mean(lse - np.where(sig, zy, c)))
-            if best is None or ce < best[0]:
-                best = (ce, beta, float(c))
-    h.beta, h.null_logit = best[1], best[2]
+        lse = m + np.log(np.exp(bz - m[:, None]).sum(axis=1))
+        for a in slopes:
+            for b in thresholds:
+                u = a * (b - zmax)                       # no-signal logit minus LSE
+                sp = np.logaddexp(0.0, u)
+                nll = np.where(sig, lse + sp - beta * zy, np.logaddexp(0.0, -u))
+                ce = float(nll.mean())
+                if best is None or ce < best[0]:
+                    best = (ce, beta, a, float(b))
+    h.beta, h.det_a, h.det_b = best[1], best[2], best[3]
     h.cross_entropy = best[0]
     return h
 
@@ -618,8 +626,8 @@ def _main(argv=None) -> None:
         bank.load_peaks(draw(spec, np.arange(VALIDATION_FIRST, VALIDATION_FIRST + 51)))
         bank.autotune()
         heur = calibrate_heuristic(ctx, spec, 0, 4096)
-        meta["heuristic"] = {"beta": heur.beta, "null_logit": heur.null_logit,
-                             "cross_entropy": heur.cross_entropy}
+        meta["heuristic"] = {"beta": heur.beta, "det_a": heur.det_a, "det_b": heur.det_b,
+                             "cross_entropy": heur.cross_entropy, "calibration_maps": 4096}
         for cap in (32, 256):
             for name, scorer in (("network", net), ("heuristic", heur)):
                 tau, val = choose_tau(ctx, scorer, spec, VALIDATION_FIRST, args.val_maps, bank, cap)

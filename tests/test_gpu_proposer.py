@@ -180,7 +180,7 @@ def test_trained_network_gains_over_the_search_without_it(built_lib, gpu_ctx):
     s2 = PR.summarize(PR.evaluate(gpu_ctx, heur, SPEC, 100011, 51 * 8, bank, 0.1))
     print("untrained", s0)
     print("trained", s1, "work", _work(s1))
-    print("line heuristic", (heur.beta, heur.null_logit), s2, "work", _work(s2))
+    print("line heuristic", (heur.beta, heur.det_a, heur.det_b), s2, "work", _work(s2))
     assert s0["fallback_frac"] >= 0.95 and s0["recall"] == 1.0
     assert s1["fallback_frac"] <= 0.6 and s1["mean_tiles_pruned"] <= 32
     assert s1["recall"] >= 0.95
@@ -200,14 +200,14 @@ def test_line_scores_against_the_oracle(built_lib, gpu_ctx):
     scores = torch.empty((4, 4096), dtype=torch.float32, device="cuda")
     logits = torch.empty((4, gfh.N_CLASSES), dtype=torch.float32, device="cuda")
     nb = SPEC.bin_hi - SPEC.bin_lo + 1
-    gfh.line_scores(gpu_ctx, buf.images, SPEC.n_k, nb, 2.0, 1.5, logits, scores)
+    gfh.line_scores(gpu_ctx, buf.images, SPEC.n_k, nb, 2.0, 0.5, 3.0, logits, scores)
     torch.cuda.synchronize()
     img = C.bf16_value(buf.images.view(torch.int16).cpu().numpy().view(np.uint16))
     sc, lg = scores.cpu().numpy(), logits.cpu().numpy()
     for b in range(4):
         ref = C.line_scores(img[b, :, :, 0], SPEC.n_k, nb)
         assert np.array_equal(sc[b].astype(np.float64), ref), b
-        lref = C.heuristic_logits(ref, 2.0, 1.5)
+        lref = C.heuristic_logits(ref, 2.0, 0.5, 3.0)
         assert np.all(np.abs(lg[b] - lref) <= 1e-4 * (1.0 + np.abs(lref))), b
 
 

@@ -271,8 +271,13 @@ def test_line_scores_against_loops_and_a_planted_track():
     s2 = C.line_scores(empty, K, nb)
     assert s2[d * 64 + xt] == 256.0 and np.argmax(s2) == d * 64 + xt
     assert np.sort(s2)[-2] < 256.0
-    lg = C.heuristic_logits(s2, 2.0, -1.5)
-    assert lg[-1] == -1.5 and lg.size == 4097
+    lg = C.heuristic_logits(s2, 2.0, 0.7, -1.5)
+    assert lg.size == 4097
     z = (s2 - s2.mean()) / s2.std()
     np.testing.assert_allclose(lg[:-1], 2.0 * z, rtol=1e-13)
-    assert np.all(C.heuristic_logits(np.ones(4096), 3.0, 0.0)[:-1] == 0.0)
+    # the no-signal probability is the logistic function of 0.7 max(z) + 1.5
+    p = np.exp(lg - lg.max())
+    p /= p.sum()
+    assert math.isclose(p[-1], 1.0 / (1.0 + math.exp(0.7 * z.max() + 1.5)), rel_tol=1e-10)
+    flat = C.heuristic_logits(np.ones(4096), 3.0, 1.0, 0.0)
+    assert np.all(flat[:-1] == 0.0) and math.isclose(flat[-1], math.log(4096), rel_tol=1e-12)
