@@ -790,7 +790,7 @@ def _roofline_of(ctx, stream, updates, map_bytes, ms):
             "hbm_peak_gbs": HBM_PEAK}
 
 
-def measure_batched_n(ctx, stream, steps, warmup, tile=(8, 3072, 512)):
+def measure_batched_n(ctx, stream, steps, warmup, tile=(16, 3072, 1024)):
     """Config 3: the plain_small peakmap at 51 braking indices, one launch (CUDA graph), against
     one plan per braking index run one after another."""
     import torch
@@ -841,7 +841,7 @@ def measure_batched_n(ctx, stream, steps, warmup, tile=(8, 3072, 512)):
     return out
 
 
-def measure_uneven(ctx, stream, steps, warmup, tile=(8, 3072, 512)):
+def measure_uneven(ctx, stream, steps, warmup, tile=(16, 3072, 1024)):
     """Config 4: 256 uneven peakmaps (statistical model), every sub-band map in one launch, against
     one plan per peakmap run one after another."""
     import torch
@@ -926,17 +926,18 @@ def measure_proposer(ctx, stream, steps, warmup, eval_maps=51 * 196):
     with torch.cuda.stream(stream):
         net = gfh.Cnn(ctx, nl, seed=1)
         net.set_state(state)
-        bank = PR.HoughBank(ctx, spec, max_sel=32)
+        bank = PR.HoughBank(ctx, spec, max_sel=256)
         bank.load_peaks(PR.draw(spec, np.arange(PR.VALIDATION_FIRST, PR.VALIDATION_FIRST + nl)))
         tuned, _ = bank.autotune()
         hm = meta.get("heuristic", {})
         heur = PR.LineHeuristic(ctx, spec, hm.get("beta", 1.0), hm.get("det_a", 1.0), hm.get("det_b", 6.0))
-        scorers = {"network": (net, meta["tau"]["network"]["32"]),
-                   "line_heuristic": (heur, meta["tau"]["heuristic"]["32"])}
-        for name, (sc, tau) in scorers.items():
+        scorers = {f"{name}_{cap}": (sc, meta["tau"][key][str(cap)], cap)
+                   for cap in (32, 256)
+                   for name, key, sc in (("network", "network", net), ("line_heuristic", "heuristic", heur))}
+        for name, (sc, tau, cap) in scorers.items():
             t0 = time.perf_counter()
-            summ = PR.summarize(PR.evaluate(ctx, sc, spec, PR.HELD_OUT_FIRST, eval_maps, bank, tau, 32))
-            search = PR.PrunedSearch(ctx, sc, bank, tau, 32)
+            summ = PR.summarize(PR.evaluate(ctx, sc, spec, PR.HELD_OUT_FIRST, eval_maps, bank, tau, cap))
+            search = PR.PrunedSearch(ctx, sc, bank, tau, cap)
             t_full, t_pr = [], []
             for st in range(warmup + steps):
                 s0 = PR.HELD_OUT_FIRST + nl * st
@@ -948,7 +949,8 @@ def measure_proposer(ctx, stream, steps, warmup, eval_maps=51 * 196):
                     t_full.append(a)
                     t_pr.append(b)
             ms_full, ms_pr = float(np.mean(t_full)), float(np.mean(t_pr))
-            out[name] = {"tau": tau, "recall": summ["recall"], "held_out_maps": summ["maps"],
+            out[name] = {"tiles_at_most": cap, "tau": tau, "recall": summ["recall"],
+                         "held_out_maps": summ["maps"],
                          "detected_full": summ["det_full"], "detected_kept": summ["det_kept"],
                          "fallback_frac": summ["fallback_frac"],
                          "fallback_noise": summ["fallback_noise"],
@@ -958,7 +960,12 @@ def measure_proposer(ctx, stream, steps, warmup, eval_maps=51 * 196):
                          "eval_s": round(time.perf_counter() - t0, 1)}
         out["tile"] = list(tuned)
         if "beta" in hm:
-            out["line_heuristic"]["parameters"] = {k: hm[k] for k in ("beta", "det_a", "det_b")}
+            out["line_heuristic_parameters"] = {k: hm[k] for k in ("beta", "det_a", "det_b")}
+        ok = [k for k in out if k.startswith("network_") and out[k]["recall"] >= 0.99]
+        best = max(ok, key=lambda k: out[k]["speedup_vs_full_exact"]) if ok else None
+        out["speedup_vs_full_exact"] = out[best]["speedup_vs_full_exact"] if best else None
+        out["recall"] = out[best]["recall"] if best else None
+        out["operating_point"] = best
         f0_, f1_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         search = PR.PrunedSearch(ctx, net, bank, meta["tau"]["network"]["32"], 32)
         search.propose()
@@ -1605,7 +1612,7 @@ def run_splice(args):
         maps = [torch.empty((g.n_k, g.ld_x0), dtype=torch.int32, device="cuda") for g in grids]
         cands = [torch.empty(g.n_bands * gfh.CANDIDATE_BYTES, dtype=torch.uint8, device="cuda")
                  for g in grids]
-        hp = gfh.Plan(ctx, grids, maps, cands, None, tile=(8, 3072, 512))
+        hp = gfh.Plan(ctx, grids, maps, cands, None, tile=(16, 3072, 1024))
         lo = min(f["bin_lo"] for f in P.fields)
         hi = max(f["bin_hi"] for f in P.fields)
         n_fft = P.fields[0]["n_fft"]
@@ -1739,7 +1746,7 @@ def run_splice(args):
                    "portions": [[p["P"].t_fft, p["P"].s_begin / spec.fs, p["P"].s_end / spec.fs]
                                 for p in parts],
                    "maps": sum(len(p["grids"]) for p in parts), "updates_per_step": updates,
-                   "tile": [8, 3072, 512],
+                   "tile": [16, 3072, 1024],
                    "l2": "inputs larger than L2 (series 165 MB, maps %d MB per step)"
                          % (sum(g.n_k * g.ld_x0 * 4 for p in parts for g in p["grids"]) // 1000000),
                    "timing": "direct calls"},

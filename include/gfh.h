@@ -139,7 +139,7 @@ typedef struct gfh_peaks {
 typedef struct gfh_tile_config {
   int32_t rows;     /* k rows per tile: 4, 8, 16 or 32 */
   int32_t cols;     /* x0 columns per tile: multiple of 128, at most 4096 */
-  int32_t threads;  /* threads per block: 256 or 512 */
+  int32_t threads;  /* threads per block: 256 or 512, or 1024 with 16 or 32 rows */
   int32_t reserved;
 } gfh_tile_config;
 
@@ -286,15 +286,16 @@ int gfh_plan_destroy(gfh_plan* plan);
 /*
  * Runs the plan on peak lists: every map reads list grids[m].list.  Writes all maps, and the
  * candidates and statistics if bound.  Asynchronous; no host synchronisation and no allocation,
- * so it can be captured in a CUDA graph.  Input errors are reported through gfh_check.
+ * so it can be captured in a CUDA graph.  Input errors are reported through gfh_check (a tile
+ * whose bin range holds more than 2^31 - 2^20 peaks is not drawn: GFH_ERR_SIZE).
  */
 int gfh_plan_execute(gfh_plan* plan, const gfh_peaks* peaks);
 
 /*
  * Autotuner: times gfh_plan_execute on these peaks (reps runs each, CUDA events on the context's
  * stream) for the current tile shape and for every shape of rows {4, 8, 16} x cols {1024, 2048,
- * 3072, 4096} x threads {256, 512} that fits in shared memory, then rebuilds the plan with the
- * fastest.  The results are unchanged by the shape (the maps are exact).  Synchronises; writes
+ * 3072, 4096} x threads {256, 512} (and 1024 threads for 16 rows) that fits in shared memory,
+ * then rebuilds the plan with the fastest.  The results are unchanged by the shape (the maps are exact).  Synchronises; writes
  * the bound outputs.  h_best / h_best_ms (may be NULL) receive the chosen shape and its time.
  */
 int gfh_plan_autotune(gfh_plan* plan, const gfh_peaks* peaks, int32_t reps,

@@ -467,7 +467,8 @@ extern "C" int gfh_plan_create(gfh_ctx* ctx, int32_t n_maps, const gfh_grid* gri
     if (cfg->threads) tc.threads = cfg->threads;
   }
   if (!(tc.rows == 4 || tc.rows == 8 || tc.rows == 16 || tc.rows == 32) || tc.cols < 128 || tc.cols % 128 ||
-      tc.cols > 4096 || !(tc.threads == 256 || tc.threads == 512))
+      tc.cols > 4096 ||
+      !(tc.threads == 256 || tc.threads == 512 || (tc.threads == 1024 && tc.rows >= 16)))
     return GFH_ERR_ARG;
   const int nwarps = tc.threads / 32;
   if ((tc.cols / 128 + nwarps - 1) / nwarps > 4) return GFH_ERR_ARG;  // <= 4 chunks per warp
@@ -771,7 +772,7 @@ extern "C" int gfh_plan_autotune(gfh_plan* p, const gfh_peaks* peaks, int32_t re
   if (!p || !peaks || reps < 1) return GFH_ERR_ARG;
   static const int kRowsList[] = {4, 8, 16};
   static const int kColsList[] = {1024, 2048, 3072, 4096};
-  static const int kThreadsList[] = {256, 512};
+  static const int kThreadsList[] = {256, 512, 1024};
   gfh_tile_config best = p->cfg;
   float best_ms = 0.f;
   int rc = time_plan(p, peaks, reps, &best_ms);
@@ -782,6 +783,7 @@ extern "C" int gfh_plan_autotune(gfh_plan* p, const gfh_peaks* peaks, int32_t re
         gfh_tile_config cfg{r, c, t, 0};
         if (cfg.rows == p->cfg.rows && cfg.cols == p->cfg.cols && cfg.threads == p->cfg.threads)
           continue;
+        if (t == 1024 && r < 16) continue;     // 1024 threads only for 16-row tiles
         gfh_plan* q = nullptr;
         const int crc = gfh_plan_create(p->ctx, p->n_maps, p->grids.data(), p->h_maps.data(),
                                         p->h_cands.empty() ? nullptr : p->h_cands.data(),

@@ -260,22 +260,29 @@ __device__ __forceinline__ void hough_tile(const MapDev* __restrict__ maps, cons
     // peaks ahead and the table rows one peak ahead of the peak being drawn; the next peak's
     // interval is formed from its rows after the current peak is drawn, so the loads have the
     // whole drawing to arrive.
-    int64_t p = pb + tid;
+    // this tile's peaks with 32-bit offsets (a range beyond 2^31 - 2^20 peaks raises the capacity
+    // flag and is not drawn)
+    const bool fits = pe - pb <= (int64_t)0x7fffffff - (1 << 20);
+    if (!fits && tid == 0) atomicOr(flag, GFH_FLAG_CAPACITY);
+    const uint32_t* const fl = fft_idx + pb;
+    const uint32_t* const bl = bins + pb;
+    const int np = fits ? (int)(pe - pb) : 0;
+    int p = tid;
     uint32_t f_nx = 0xffffffffu;                 // indices of peak p + NT
     int j_nx = 0;
     int64_t a_cu = 0, b_cu = 0, s_cu = 0;        // interval of peak p
     bool ok_cu = false;
-    if (p < pe) {
+    if (p < np) {
       longlong2 bs, up;
-      ok_cu = peak_rows(BS, UP, bin_lo, __ldg(fft_idx + p), (int)__ldg(bins + p), nfft, jmax, flag,
+      ok_cu = peak_rows(BS, UP, bin_lo, __ldg(fl + p), (int)__ldg(bl + p), nfft, jmax, flag,
                         bs, up);
       if (ok_cu) peak_interval(t.row0, bs, up, a_cu, b_cu, s_cu);
     }
-    if (p + NT < pe) { f_nx = __ldg(fft_idx + p + NT); j_nx = (int)__ldg(bins + p + NT); }
-    for (; p < pe; p += NT) {
+    if (p + NT < np) { f_nx = __ldg(fl + p + NT); j_nx = (int)__ldg(bl + p + NT); }
+    for (; p < np; p += NT) {
       uint32_t f_nn = 0xffffffffu;               // indices of peak p + 2 NT
       int j_nn = 0;
-      if (p + 2 * NT < pe) { f_nn = __ldg(fft_idx + p + 2 * NT); j_nn = (int)__ldg(bins + p + 2 * NT); }
+      if (p + 2 * NT < np) { f_nn = __ldg(fl + p + 2 * NT); j_nn = (int)__ldg(bl + p + 2 * NT); }
       longlong2 bs_nx = make_longlong2(0, 0), up_nx = make_longlong2(0, 0);
       const bool ok_nx = f_nx != 0xffffffffu &&
                          peak_rows(BS, UP, bin_lo, f_nx, j_nx, nfft, jmax, flag, bs_nx, up_nx);
@@ -400,7 +407,7 @@ __device__ __forceinline__ void hough_tile(const MapDev* __restrict__ maps, cons
 
 // One block per tile of the plan.
 template <int R, int NT, bool SELECT, bool XD, int LDS = 0>
-__global__ void __launch_bounds__(NT, R <= 4 ? 3 : (R == 8 ? 2 : 1))
+__global__ void __launch_bounds__(NT, NT == 1024 ? 1 : (R <= 4 ? 3 : (R == 8 ? 2 : 1)))
 k_hough(const MapDev* __restrict__ maps, const TileDev* __restrict__ tiles,
         const uint32_t* __restrict__ fft_idx, const uint32_t* __restrict__ bins,
         unsigned int* __restrict__ flag, int c_max) {
@@ -413,7 +420,7 @@ k_hough(const MapDev* __restrict__ maps, const TileDev* __restrict__ tiles,
 // Persistent blocks over a tile list whose length is known on the device only (the coarse-tile
 // search): each block takes the next tile from a counter until the list is exhausted.
 template <int R, int NT, bool SELECT>
-__global__ void __launch_bounds__(NT, R <= 4 ? 3 : (R == 8 ? 2 : 1))
+__global__ void __launch_bounds__(NT, NT == 1024 ? 1 : (R <= 4 ? 3 : (R == 8 ? 2 : 1)))
 k_hough_list(const MapDev* __restrict__ maps, const TileDev* __restrict__ tiles,
              const int* __restrict__ count, int* __restrict__ next, int cap,
              const uint32_t* __restrict__ fft_idx, const uint32_t* __restrict__ bins,
@@ -514,12 +521,16 @@ __global__ void k_select_cols(const int32_t* __restrict__ map, const MapDev* __r
 template <int R, int NT, bool SEL>
 int launch_hough_t(gfh_plan* p, const gfh_peaks* peaks, const TileDev* tiles, int n_tiles,
                    size_t smem, bool prepare, bool xd) {
-  // 8-row tiles of 2048 or 3072 columns (the shapes the autotuner picks on the paper-shaped
-  // workloads) have the row stride fixed at compile time
+  // the shapes the autotuner picks on the paper-shaped workloads (8-row tiles of 2048 or 3072
+  // columns at 512 threads, 16-row tiles of 3072 columns at 1024 threads) have the row stride
+  // fixed at compile time
   auto fn = xd ? k_hough<R, NT, SEL, true> : k_hough<R, NT, SEL, false>;
   if constexpr (R == 8 && NT == 512) {
     if (!xd && p->cfg.cols == 3072) fn = k_hough<R, NT, SEL, false, 3074>;
     if (!xd && p->cfg.cols == 2048) fn = k_hough<R, NT, SEL, false, 2050>;
+  }
+  if constexpr (R == 16 && NT == 1024) {
+    if (!xd && p->cfg.cols == 3072) fn = k_hough<R, NT, SEL, false, 3074>;
   }
   auto fl = k_hough_list<R, NT, SEL>;
   if (prepare) {
@@ -565,6 +576,8 @@ int launch_hough_sel(gfh_plan* p, const gfh_peaks* peaks, const TileDev* tiles, 
 template <int R>
 int launch_hough_r(gfh_plan* p, const gfh_peaks* peaks, const TileDev* tiles, int n_tiles,
                    size_t smem, bool prepare, bool xd) {
+  if constexpr (R >= 16)   // 1024 threads: one block of 32 warps per SM holds a 16- or 32-row tile
+    if (p->cfg.threads == 1024) return launch_hough_sel<R, 1024>(p, peaks, tiles, n_tiles, smem, prepare, xd);
   return p->cfg.threads == 256
              ? launch_hough_sel<R, 256>(p, peaks, tiles, n_tiles, smem, prepare, xd)
              : launch_hough_sel<R, 512>(p, peaks, tiles, n_tiles, smem, prepare, xd);
