@@ -491,7 +491,9 @@ int gfh_cnn_set_state(gfh_cnn* net, const float* h_params, const float* h_m, con
  * each stage on its own; synchronises.  which:
  *   GFH_CNN_ACT + l (l = 1..5)    activation after layer l, bf16 NHWC [batch][h][h][c]
  *                                 (h = 256, 128, 128, 64, 64; c = 32, 32, 64, 64, 64)
- *   GFH_CNN_DACT + l (l = 1..5)   gradient of the mean loss in that activation, bf16, same shape
+ *   GFH_CNN_DACT + l (l = 1..5)   gradient of the mean loss in layer l's pre-activation (the
+ *                                 activation's gradient where the activation is > 0, else 0),
+ *                                 bf16, same shape
  *   GFH_CNN_WBF16 + l (l = 0..4)  bf16 copy of the weights of layer l + 1, [cout][3][3][cin]
  *   GFH_CNN_POOLED                fp32 [batch][64 f][64 c], mean of activation 5 over its 64 rows
  *   GFH_CNN_LOGITS, GFH_CNN_DLOGITS   fp32 [batch][4097]: logits, d(mean loss)/d logits

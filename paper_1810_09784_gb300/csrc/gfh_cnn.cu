@@ -5,17 +5,19 @@
 //
 // Architecture (bf16 activations and weights, fp32 accumulation, NHWC layout):
 //   input  [B][256 t][256 f][2]   log(1 + peak count) per (t, f) cell and a constant (n - 2) / 5
-//   L1 3x3  2 -> 32, stride 1, ReLU       (direct convolution, CUDA cores)
-//   L2 3x3 32 -> 32, stride 2, ReLU       (implicit GEMM on mma.sync bf16 tensor cores)
+//   L1 3x3  2 -> 32, stride 1, ReLU       (implicit GEMMs on tcgen05, accumulators in tensor memory)
+//   L2 3x3 32 -> 32, stride 2, ReLU
 //   L3 3x3 32 -> 64, stride 1, ReLU
 //   L4 3x3 64 -> 64, stride 2, ReLU
 //   L5 3x3 64 -> 64, stride 1, ReLU       -> [B][64 t][64 f][64]
 //   mean over t                           -> [B][64 f][64]
 //   head: 1-D conv over f, width 3, 64 -> 64 k tiles  -> logits[b][kt * 64 + f], plus one
 //   "no signal" logit: 4097 classes, softmax cross-entropy.
-// The gradient of every layer is computed by hand-written kernels (dgrad and wgrad of L2-L5 on
-// tensor cores, L1 and the head on CUDA cores); AdamW updates fp32 master weights and refreshes the
-// bf16 copies.
+// The gradient of every layer is computed by hand-written kernels: weight gradients of L2-L5 on
+// tcgen05, input gradients of L2-L5 on mma.sync, L1's weight gradient and the head on CUDA cores;
+// every reduction runs in a fixed order, so a training step is deterministic.  AdamW updates fp32
+// master weights and refreshes the bf16 copies.  Activation gradients are stored masked by their
+// ReLU (the gradients in the pre-activations), so the gradient kernels stage them as they are.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -696,11 +698,13 @@ __global__ void __launch_bounds__(256) k_conv_fwd_tc(const __nv_bfloat16* __rest
 // ---- L2-L5 input gradient: din[m][ci] = sum_{tap, co} G[src(m, tap)][co] W[co][tap][ci] ----------
 // m = input pixel (b, y, x); the output pixel that reads it through tap (dy, dx) is
 // ((y - dy + 1)/S, (x - dx + 1)/S) when that divides exactly and lies inside; G = dout masked by
-// the layer's ReLU.
+// the layer's ReLU.  With in_act (the layer's input activation) the result is stored masked by
+// in_act > 0, i.e. as the gradient in the previous layer's pre-activation.
 template <int CIN, int COUT, int S>
 __global__ void __launch_bounds__(256) k_conv_dgrad(const __nv_bfloat16* __restrict__ dout,
                                                     const __nv_bfloat16* __restrict__ out,
                                                     const __nv_bfloat16* __restrict__ w,
+                                                    const __nv_bfloat16* __restrict__ in_act,
                                                     __nv_bfloat16* __restrict__ din, int B, int H) {
   constexpr int K = 9 * COUT, KP = K + 8, NT8 = CIN / 8;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -755,105 +759,203 @@ __global__ void __launch_bounds__(256) k_conv_dgrad(const __nv_bfloat16* __restr
 #pragma unroll
     for (int n = 0; n < NT8; ++n) {
       const int col = n * 8 + 2 * t;
-      *reinterpret_cast<uint32_t*>(din + (m0 + g) * CIN + col) = pack_bf16(acc[n][0], acc[n][1]);
-      *reinterpret_cast<uint32_t*>(din + (m0 + g + 8) * CIN + col) = pack_bf16(acc[n][2], acc[n][3]);
+      uint32_t lo = pack_bf16(acc[n][0], acc[n][1]), hi = pack_bf16(acc[n][2], acc[n][3]);
+      if (in_act) {    // masked by the input activation's ReLU: the gradient in its pre-activation
+        lo = relu_mask(lo, ld_u32(in_act + (m0 + g) * CIN + col));
+        hi = relu_mask(hi, ld_u32(in_act + (m0 + g + 8) * CIN + col));
+      }
+      *reinterpret_cast<uint32_t*>(din + (m0 + g) * CIN + col) = lo;
+      *reinterpret_cast<uint32_t*>(din + (m0 + g + 8) * CIN + col) = hi;
     }
   }
 }
 
-// ---- L2-L5 weight gradient: dW[co][kc] += sum_p G[p][co] patch[p][kc] ---------------------------
-// A block owns 64 patch columns kc in [n0, n0 + 64) and pixel chunk blockIdx.x; both operands are
-// staged transposed (pixels contiguous) in shared memory, 64 pixels at a time, for mma.sync.  Pixel
-// coordinates of a chunk are decoded once into shared memory (32-bit: B (H/S)^2 < 2^31).  The
-// block's sums go to part[chunk][co][kc] (every entry written by exactly one thread, no atomics);
-// k_sum_chunks adds the chunks in a fixed order, so the gradient is the same on every run.
+// ---- L2-L5 weight gradient on tcgen05 -------------------------------------------------------------
+// dW[co][tap][ci] = sum_p G[p][co] X_tap[p][ci] with G the gradient in the layer's pre-activation
+// (stored masked, NHWC [p][co]) and X_tap[p] the input pixel that output pixel p reads through the
+// tap (zero outside the image).  Per tap a GEMM with M = 64 (co; rows >= COUT are padding), N = CIN
+// (ci) and K = output pixels, both operands MN-major in shared memory, so both are staged by 16-byte
+// cp.async straight from the NHWC tensors: A = G (16 bytes = 8 co of one pixel), B = X (16 bytes =
+// 8 ci of one input pixel).  Block (chunk, dy) keeps the accumulators of the taps (dy, 0..2) in
+// tensor memory over its chunk's tiles; a tile is WT_ROWS output rows x 64 columns of one image,
+// its K-steps 16 output pixels of one row.  Shared layout per buffer: G at [row][co chunk][64 px]
+// and X at [row][ci chunk][parity][NP entries], 16 bytes per pixel, so a tap's B operand is the
+// same array started dx entries later (S = 1) or in the other parity (S = 2): entry j of parity 0
+// is input column x0 S - 1 + j (S = 1), 2 (x0 + j) - 1 (S = 2), of parity 1 column 2 (x0 + j).
+// Core matrices: 8 pixels x 16 bytes, K-adjacent ones 128 bytes apart (the descriptor's leading
+// byte offset), M/N-adjacent ones one co / ci chunk apart (its stride byte offset).  Two buffers: tile i + 1 is staged while tile i's MMAs run.  The block's
+// sums go to part[chunk][co][tap][ci] (k_sum_chunks adds the chunks in order).
+constexpr int WT_ROWS = 2, WT_THREADS = 128, WT_CHUNKS = 96;
+
+// Row of an M = 64 accumulator held by tensor-memory lane `lane` (-1: no row): rows 16 q .. 16 q + 15
+// sit in lanes 32 q .. 32 q + 15, the first half of each warp's quarter of the lanes.
+__device__ __forceinline__ int wgrad_row_of_lane(int lane) {
+  return (lane & 31) < 16 ? (lane >> 5) * 16 + (lane & 31) : -1;
+}
+
+template <int CIN, int S>
+struct WgradTc {
+  static constexpr int NP = S == 1 ? 66 : 65;                         // entries per (row, chunk, parity)
+  static constexpr int XB = WT_ROWS * (CIN / 8) * S * NP * 16;         // X bytes per buffer
+};
+
 template <int CIN, int COUT, int S>
-__global__ void __launch_bounds__(256) k_conv_wgrad(const __nv_bfloat16* __restrict__ dout,
-                                                    const __nv_bfloat16* __restrict__ out,
-                                                    const __nv_bfloat16* __restrict__ in,
-                                                    float* __restrict__ part, int B, int H,
-                                                    int pix_per_block) {
-  constexpr int PC = 64, LD = PC + 8;
-  constexpr int MT = COUT / 16;            // m tiles of 16 output channels
-  __shared__ __align__(16) __nv_bfloat16 Gt[COUT][LD];
-  __shared__ __align__(16) __nv_bfloat16 Pt[64][LD];
-  __shared__ int pb[PC], py[PC], px[PC];   // image, first input row / column of the pixel's patch
+__global__ void __launch_bounds__(WT_THREADS) k_conv_wgrad_tc(const __nv_bfloat16* __restrict__ G,
+                                                            const __nv_bfloat16* __restrict__ in,
+                                                            float* __restrict__ part, int B, int H,
+                                                            unsigned int* flag) {
+  constexpr int NP = WgradTc<CIN, S>::NP;
+  constexpr int XB = WgradTc<CIN, S>::XB;
+  constexpr int GB = WT_ROWS * (COUT / 8) * 64 * 16;                   // G bytes per buffer
+  constexpr int GPAD = (64 - COUT) / 8 * 64 * 16;                      // padding rows' reach
+  constexpr int BUF = ((GB + GPAD + XB) + 1023) / 1024 * 1024;
+  constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+                             ((uint32_t)(CIN >> 3) << 17) | ((uint32_t)(64 >> 4) << 24);
+  constexpr uint32_t TCOLS = 3 * CIN <= 128 ? 128 : 256;
+  extern __shared__ __align__(1024) unsigned char smem_w[];
+  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ uint32_t tslot;
+  __shared__ int s_ok;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int chunk = blockIdx.x, dy = blockIdx.y;
   const int Ho = H / S;
-  const int M = B * Ho * Ho;
-  const int n0 = blockIdx.y * 64;
-  const int p_begin = blockIdx.x * pix_per_block;
-  const int p_end = min(p_begin + pix_per_block, M);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  // warp -> (m tile, n half); with COUT = 32 only warps 0..3 compute
-  const int mt = warp % 4, nh = warp / 4;
-  const bool active = mt < MT;
-  float acc[4][4];
-#pragma unroll
-  for (int n = 0; n < 4; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-  for (int p0 = p_begin; p0 < p_end; p0 += PC) {
-    __syncthreads();
-    if (threadIdx.x < PC) {
-      const int p = p0 + threadIdx.x;
-      const int b = p / (Ho * Ho), r = p - b * (Ho * Ho), yo = r / Ho, xo = r - yo * Ho;
-      pb[threadIdx.x] = p < p_end ? b : -1;
-      py[threadIdx.x] = yo * S - 1;
-      px[threadIdx.x] = xo * S - 1;
+  const int tiles_per_img = (Ho / WT_ROWS) * (Ho / 64);
+  const int n_tiles = B * tiles_per_img;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tslot)), "r"(TCOLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[0])), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[1])), "r"(1));
+  }
+  const uint32_t s32 = smem_u32(smem_w);
+  // zero the padding rows' reach once (read as A rows >= COUT, never stored)
+  if (GPAD > 0)
+    for (int i = tid; i < GPAD / 16; i += WT_THREADS)
+      for (int b2 = 0; b2 < 2; ++b2)
+        *reinterpret_cast<int4*>(smem_w + b2 * BUF + GB + i * 16) = make_int4(0, 0, 0, 0);
+
+  auto stage = [&](int q, int buf) {
+    const int b = q / tiles_per_img, rem = q - b * tiles_per_img;
+    const int rg = rem / (Ho / 64), cb = rem - rg * (Ho / 64);
+    const int y0 = rg * WT_ROWS, x0 = cb * 64;
+    unsigned char* base = smem_w + buf * BUF;
+    const uint32_t b32 = s32 + (uint32_t)(buf * BUF);
+    (void)base;
+    // G: [row][co chunk][64 px]
+    for (int e = tid; e < WT_ROWS * (COUT / 8) * 64; e += WT_THREADS) {
+      const int px = e & 63, rc = e >> 6, c = rc % (COUT / 8), r = rc / (COUT / 8);
+      const __nv_bfloat16* src = G + (((int64_t)b * Ho + y0 + r) * Ho + x0 + px) * COUT + c * 8;
+      cp_async16(b32 + (uint32_t)(((r * (COUT / 8) + c) * 64 + px) * 16), src, 16u);
     }
-    for (int e = threadIdx.x; e < PC * COUT; e += blockDim.x) {
-      const int pl = e / COUT, co = e % COUT;
-      const int p = p0 + pl;
-      __nv_bfloat16 v = __float2bfloat16_rn(0.f);
-      if (p < p_end) {
-        const __nv_bfloat16 gv = dout[(int64_t)p * COUT + co], av = out[(int64_t)p * COUT + co];
-        v = __bfloat162float(av) > 0.f ? gv : __float2bfloat16_rn(0.f);
-      }
-      Gt[co][pl] = v;
+    // X: [row][ci chunk][parity][NP], input row (y0 + r) S + dy - 1
+    for (int e = tid; e < WT_ROWS * (CIN / 8) * S * NP; e += WT_THREADS) {
+      const int j = e % NP;
+      int rest = e / NP;
+      const int par = rest % S;
+      rest /= S;
+      const int c = rest % (CIN / 8), r = rest / (CIN / 8);
+      const int yi = (y0 + r) * S + dy - 1;
+      const int xi = S == 1 ? x0 - 1 + j : (par == 0 ? 2 * (x0 + j) - 1 : 2 * (x0 + j));
+      const bool inside = yi >= 0 && yi < H && xi >= 0 && xi < H;
+      const __nv_bfloat16* src = inside ? in + (((int64_t)b * H + yi) * H + xi) * CIN + c * 8 : in;
+      cp_async16(b32 + (uint32_t)(GB + GPAD + (((r * (CIN / 8) + c) * S + par) * NP + j) * 16), src,
+                 inside ? 16u : 0u);
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < PC * 64; e += blockDim.x) {
-      const int pl = e >> 6, j = e & 63;
-      const int kc = n0 + j, tap = kc / CIN, ci = kc % CIN;
-      const int dy = tap / 3, dx = tap - 3 * dy;
-      const int b = pb[pl], yi = py[pl] + dy, xi = px[pl] + dx;
-      __nv_bfloat16 v = __float2bfloat16_rn(0.f);
-      if (b >= 0 && kc < 9 * CIN && yi >= 0 && yi < H && xi >= 0 && xi < H)
-        v = in[(((int64_t)b * H + yi) * H + xi) * CIN + ci];
-      Pt[j][pl] = v;
-    }
-    __syncthreads();
-    if (active) {
+  };
+
+  uint32_t ph[2] = {0u, 0u};
+  bool pending[2] = {false, false};
+  bool any = false;
+  int i = 0;
+  int q = chunk;
+  if (q < n_tiles) stage(q, 0);
+  cp_async_wait_all();
+  async_proxy_fence();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (tid == 0) s_ok = 1;
+  __syncthreads();
+  const uint32_t tmem = tslot;
+  for (; q < n_tiles; q += WT_CHUNKS, ++i) {
+    const int buf = i & 1;
+    if (tid == 0) {
+      const uint32_t b32 = s32 + (uint32_t)(buf * BUF);
+#pragma unroll 1
+      for (int r = 0; r < WT_ROWS; ++r)
+#pragma unroll 1
+        for (int ks = 0; ks < 4; ++ks) {
+          const uint32_t a_addr = b32 + (uint32_t)((r * (COUT / 8) * 64 + ks * 16) * 16);
+          // MN-major operands: leading byte offset = K-direction core-matrix stride (8 pixels,
+          // 128 bytes), stride byte offset = M/N-direction stride (one co / ci chunk)
+          const uint64_t ad = umma_desc(a_addr, 128u, 64u * 16u);
 #pragma unroll
-      for (int ks = 0; ks < PC / 16; ++ks) {
-        const int k = ks * 16 + 2 * t;
-        uint32_t a[4];
-        a[0] = ld_u32(&Gt[mt * 16 + g][k]);
-        a[1] = ld_u32(&Gt[mt * 16 + g + 8][k]);
-        a[2] = ld_u32(&Gt[mt * 16 + g][k + 8]);
-        a[3] = ld_u32(&Gt[mt * 16 + g + 8][k + 8]);
-#pragma unroll
-        for (int n = 0; n < 4; ++n) {
-          const __nv_bfloat16* pr = &Pt[nh * 32 + n * 8 + g][k];
-          mma_bf16(acc[n], a, ld_u32(pr), ld_u32(pr + 8));
+          for (int dx = 0; dx < 3; ++dx) {
+            const int par = S == 1 ? 0 : (dx == 1 ? 1 : 0);
+            const int jo = S == 1 ? dx : (dx == 2 ? 1 : 0);
+            const uint32_t b_addr = b32 + (uint32_t)(GB + GPAD + ((r * (CIN / 8) * S + par) * NP + ks * 16 + jo) * 16);
+            const uint64_t bd = umma_desc(b_addr, 128u, (uint32_t)(S * NP * 16));
+            umma_bf16(tmem + (uint32_t)(dx * CIN), ad, bd, IDESC, any ? 1u : 0u);
+          }
+          any = true;
         }
-      }
+      umma_commit(&mbar[buf]);
     }
+    pending[buf] = true;
+    // stage the next tile into the other buffer once the MMAs that read it (tile i - 1) are done
+    const int nq = q + WT_CHUNKS;
+    const int nb = buf ^ 1;
+    if (pending[nb]) {
+      if (warp == 0) {
+        const bool mine = mbar_wait(&mbar[nb], ph[nb]);
+        const bool all = __all_sync(0xffffffffu, mine) != 0;
+        if (lane == 0 && !all) { s_ok = 0; atomicOr(flag, GFH_FLAG_TIMEOUT); }
+      }
+      ph[nb] ^= 1u;
+      pending[nb] = false;
+      __syncthreads();
+      tc_fence_after();
+    }
+    if (!s_ok) break;
+    if (nq < n_tiles) stage(nq, nb);
+    cp_async_wait_all();
+    async_proxy_fence();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
   }
-  if (active) {
-    float* const dw = part + (int64_t)blockIdx.x * COUT * 9 * CIN;
+  // the last tiles' MMAs
+  for (int bfr = 0; bfr < 2; ++bfr)
+    if (pending[bfr] && s_ok) {
+      if (warp == 0) {
+        const bool mine = mbar_wait(&mbar[bfr], ph[bfr]);
+        const bool all = __all_sync(0xffffffffu, mine) != 0;
+        if (lane == 0 && !all) { s_ok = 0; atomicOr(flag, GFH_FLAG_TIMEOUT); }
+      }
+      ph[bfr] ^= 1u;
+      __syncthreads();
+    }
+  tc_fence_after();
+  // accumulators -> part[chunk][co][dy * 3 + dx][ci] (zeros for a block without tiles)
+  const bool have = chunk < n_tiles && s_ok;
+  float* const dst = part + (int64_t)chunk * COUT * 9 * CIN;
+  for (int dx = 0; dx < 3; ++dx)
+    for (int c0 = 0; c0 < CIN; c0 += 16) {
+      uint32_t v[16];
+      if (have) tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(dx * CIN + c0), v);
+      const int co = wgrad_row_of_lane(warp * 32 + lane);
+      if (co >= 0 && co < COUT) {
+        float* o = dst + ((int64_t)co * 9 + dy * 3 + dx) * CIN + c0;
 #pragma unroll
-    for (int n = 0; n < 4; ++n) {
-      const int kc = n0 + nh * 32 + n * 8 + 2 * t;
-      const int co = mt * 16 + g;
-      if (kc < 9 * CIN) {
-        dw[co * 9 * CIN + kc] = acc[n][0];
-        dw[(co + 8) * 9 * CIN + kc] = acc[n][2];
-      }
-      if (kc + 1 < 9 * CIN) {
-        dw[co * 9 * CIN + kc + 1] = acc[n][1];
-        dw[(co + 8) * 9 * CIN + kc + 1] = acc[n][3];
+        for (int j = 0; j < 16; ++j) o[j] = have ? __uint_as_float(v[j]) : 0.f;
       }
     }
-  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
 }
 
 // dst[e] += sum_{c < chunks} part[c * n + e], chunks in increasing order (deterministic).
@@ -866,8 +968,9 @@ __global__ void k_sum_chunks(const float* __restrict__ part, int chunks, int n,
   dst[e] += s;
 }
 
-// Bias gradient of a ReLU layer, db[co] = sum_p G[p][co], in kBiasBlocks x (256 / C) strided
-// partial sums part[(block * 256 / C + row)][co] (reduced by k_sum_chunks).
+// Bias gradient of a ReLU layer, db[co] = sum_p G[p][co] with G = dout where out > 0 (out NULL:
+// dout is G already), in kBiasBlocks x (256 / C) strided partial sums part[(block * 256 / C +
+// row)][co] (reduced by k_sum_chunks).
 constexpr int kBiasBlocks = 256;
 __global__ void __launch_bounds__(256) k_bias_grad(const __nv_bfloat16* __restrict__ dout,
                                                    const __nv_bfloat16* __restrict__ out,
@@ -875,8 +978,16 @@ __global__ void __launch_bounds__(256) k_bias_grad(const __nv_bfloat16* __restri
   const int co = threadIdx.x % C, rows = blockDim.x / C;
   float s = 0.f;
   for (int64_t p = (int64_t)blockIdx.x * rows + threadIdx.x / C; p < M; p += (int64_t)gridDim.x * rows)
-    if (__bfloat162float(out[p * C + co]) > 0.f) s += __bfloat162float(dout[p * C + co]);
+    if (!out || __bfloat162float(out[p * C + co]) > 0.f) s += __bfloat162float(dout[p * C + co]);
   part[((int64_t)blockIdx.x * rows + threadIdx.x / C) * C + co] = s;
+}
+
+// g[i] = dout[i] where out[i] > 0, else 0 (the gradient in a layer's pre-activation), n elements.
+__global__ void k_mask_grad(const __nv_bfloat16* __restrict__ dout,
+                            const __nv_bfloat16* __restrict__ out, __nv_bfloat16* __restrict__ g,
+                            int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) g[i] = __bfloat162float(out[i]) > 0.f ? dout[i] : __float2bfloat16_rn(0.f);
 }
 
 // dW1[co][tap][ci] = sum_p G1[p][co] in[src(p, tap)][ci] over images of H x H pixels; a block
@@ -1017,9 +1128,11 @@ __global__ void k_head_wgrad(const float* __restrict__ dlogits, const float* __r
   }
 }
 
-// d a5[b][t][f][c] = (1/64) sum_{kt, d} dlogits[b][kt * 64 + f - d + 1] wh[kt][d][c]  (same for all t)
+// d a5[b][t][f][c] = (1/64) sum_{kt, d} dlogits[b][kt * 64 + f - d + 1] wh[kt][d][c]  (same for all t),
+// stored masked by a5 > 0: the gradient in layer 5's pre-activation
 __global__ void k_head_dgrad(const float* __restrict__ dlogits, const float* __restrict__ wh,
-                             __nv_bfloat16* __restrict__ da5, int B) {
+                             const __nv_bfloat16* __restrict__ a5, __nv_bfloat16* __restrict__ da5,
+                             int B) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;   // (b, f, c)
   if (e >= B * 4096) return;
   const int b = e / 4096, f = (e / 64) % 64, c = e % 64;
@@ -1031,7 +1144,11 @@ __global__ void k_head_dgrad(const float* __restrict__ dlogits, const float* __r
       s += dlogits[(int64_t)b * kClasses + kt * 64 + fo] * wh[(kt * 3 + d) * 64 + c];
     }
   const __nv_bfloat16 v = __float2bfloat16_rn(s * (1.0f / 64.0f));
-  for (int tt = 0; tt < 64; ++tt) da5[((int64_t)b * 64 + tt) * 4096 + f * 64 + c] = v;
+  const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
+  for (int tt = 0; tt < 64; ++tt) {
+    const int64_t i = ((int64_t)b * 64 + tt) * 4096 + f * 64 + c;
+    da5[i] = __bfloat162float(a5[i]) > 0.f ? v : zero;
+  }
 }
 
 // AdamW on the fp32 master weights; refreshes the bf16 copies of L2-L5 (index map in bf16_of).
@@ -1089,20 +1206,22 @@ int conv_fwd(const __nv_bfloat16* in, const __nv_bfloat16* w, const float* bias,
 
 template <int CIN, int COUT, int S>
 int conv_dgrad(const __nv_bfloat16* dout, const __nv_bfloat16* out, const __nv_bfloat16* w,
-               __nv_bfloat16* din, int B, int H, int sms, cudaStream_t st) {
+               const __nv_bfloat16* in_act, __nv_bfloat16* din, int B, int H, int sms,
+               cudaStream_t st) {
   const size_t smem = (size_t)CIN * (9 * COUT + 8) * 2;
   auto fn = k_conv_dgrad<CIN, COUT, S>;
   GFH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int64_t tiles = (int64_t)B * H * H / 16;
   const int grid = (int)std::min<int64_t>((tiles + 7) / 8, (int64_t)sms * 8);
-  fn<<<grid, 256, smem, st>>>(dout, out, w, din, B, H);
+  fn<<<grid, 256, smem, st>>>(dout, out, w, in_act, din, B, H);
   GFH_CUDA_TRY(cudaGetLastError());
   return GFH_OK;
 }
 
-// Pixel chunks of a weight gradient over M pixels: at most kMaxChunks chunks of a multiple of 64
-// pixels each (a function of M only, so the reduction order is the same on every run).
-constexpr int kMaxChunks = 256, kMaxChunks1 = 1024;
+// Pixel chunks of the first layer's weight gradient over M pixels: at most max_chunks chunks of a
+// multiple of 64 pixels each (a function of M only, so the reduction order is the same on every
+// run).
+constexpr int kMaxChunks1 = 1024;
 inline int wgrad_chunk_pixels(int64_t M, int max_chunks, int min_pixels) {
   int64_t ppb = std::max<int64_t>(min_pixels, (M + max_chunks - 1) / max_chunks);
   return (int)((ppb + 63) / 64 * 64);
@@ -1110,9 +1229,12 @@ inline int wgrad_chunk_pixels(int64_t M, int max_chunks, int min_pixels) {
 
 // Scratch floats of one layer's weight and bias gradients over M output pixels.
 size_t layer_partial_floats(int l, int64_t M) {
-  const bool first = l == 0;
-  const int64_t ppb = wgrad_chunk_pixels(M, first ? kMaxChunks1 : kMaxChunks, first ? 2048 : 4096);
-  return std::max((size_t)kBiasBlocks * 256, (size_t)((M + ppb - 1) / ppb) * kCout[l] * 9 * kCin[l]);
+  size_t ch = WT_CHUNKS;                           // L2-L5: the tensor-core chunks
+  if (l == 0) {
+    const int64_t ppb = wgrad_chunk_pixels(M, kMaxChunks1, 2048);
+    ch = (size_t)((M + ppb - 1) / ppb);
+  }
+  return std::max((size_t)kBiasBlocks * 256, ch * kCout[l] * 9 * kCin[l]);
 }
 
 // Scratch floats the weight and bias gradients of every layer of the network need at batch B.
@@ -1135,22 +1257,26 @@ int bias_grad(const __nv_bfloat16* dout, const __nv_bfloat16* out, float* db, in
   return GFH_OK;
 }
 
-// Weight gradient added into dw [cout][3][3][cin] and bias gradient added into db; part holds at
-// least grad_partial_floats(B) floats.
+// Weight gradient on tcgen05 (k_conv_wgrad_tc) added into dw and bias gradient into db, from the
+// gradient in the pre-activation G (masked); output rows and columns a multiple of 64.
 template <int CIN, int COUT, int S>
-int conv_wgrad(const __nv_bfloat16* dout, const __nv_bfloat16* out, const __nv_bfloat16* in,
-               float* dw, float* db, int B, int H, float* part, cudaStream_t st) {
-  const int64_t M = (int64_t)B * (H / S) * (H / S);
-  if (M >= INT32_MAX) return GFH_ERR_SIZE;
-  const int ppb = wgrad_chunk_pixels(M, kMaxChunks, 4096);
-  const int chunks = (int)((M + ppb - 1) / ppb);
-  dim3 grid((unsigned)chunks, (9 * CIN + 63) / 64);
-  k_conv_wgrad<CIN, COUT, S><<<grid, 256, 0, st>>>(dout, out, in, part, B, H, ppb);
+int conv_wgrad_tc(const __nv_bfloat16* G, const __nv_bfloat16* in, float* dw, float* db, int B,
+                  int H, float* part, cudaStream_t st, unsigned int* flag) {
+  const int Ho = H / S;
+  if (Ho % 64 || H % S) return GFH_ERR_ARG;
+  constexpr int NP = WgradTc<CIN, S>::NP;
+  constexpr int GB = WT_ROWS * (COUT / 8) * 64 * 16;
+  constexpr int GPAD = (64 - COUT) / 8 * 64 * 16;
+  constexpr int BUF = ((GB + GPAD + WgradTc<CIN, S>::XB) + 1023) / 1024 * 1024;
+  (void)NP;
+  auto fn = k_conv_wgrad_tc<CIN, COUT, S>;
+  GFH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * BUF));
+  fn<<<dim3(WT_CHUNKS, 3), WT_THREADS, 2 * BUF, st>>>(G, in, part, B, H, flag);
   GFH_CUDA_TRY(cudaGetLastError());
   const int n = COUT * 9 * CIN;
-  k_sum_chunks<<<(n + 255) / 256, 256, 0, st>>>(part, chunks, n, dw);
+  k_sum_chunks<<<(n + 255) / 256, 256, 0, st>>>(part, WT_CHUNKS, n, dw);
   GFH_CUDA_TRY(cudaGetLastError());
-  return bias_grad(dout, out, db, M, COUT, part, st);
+  return bias_grad(G, nullptr, db, (int64_t)B * Ho * Ho, COUT, part, st);
 }
 
 // First layer (2 input channels) weight and bias gradients, added into dw and db.
@@ -1235,22 +1361,23 @@ int forward(gfh_cnn* n, const __nv_bfloat16* img, int B) {
 // Gradients of the mean loss into n->gw (zeroed first); per-sample losses in n->loss.
 int backward(gfh_cnn* n, const __nv_bfloat16* img, const int32_t* labels, int B) {
   cudaStream_t st = n->ctx->stream;
+  unsigned int* flag = n->ctx->d_flag;
   const int sms = n->ctx->num_sms;
   const Layout& L = n->L;
   GFH_CUDA_TRY(cudaMemsetAsync(n->gw, 0, L.total * sizeof(float), st));
   k_softmax_ce<<<B, 256, 0, st>>>(n->logits, labels, n->dlogits, n->loss, B);
   k_head_wgrad<<<(64 * 3 * 64 + 65 + 255) / 256, 256, 0, st>>>(n->dlogits, n->pooled, n->gw + L.wh,
                                                                n->gw + L.bh, n->gw + L.bnull, B);
-  k_head_dgrad<<<(B * 4096 + 255) / 256, 256, 0, st>>>(n->dlogits, n->w + L.wh, n->dact[5], B);
+  k_head_dgrad<<<(B * 4096 + 255) / 256, 256, 0, st>>>(n->dlogits, n->w + L.wh, n->act[5], n->dact[5], B);
   GFH_CUDA_TRY(cudaGetLastError());
-  int rc = conv_wgrad<64, 64, 1>(n->dact[5], n->act[5], n->act[4], n->gw + L.w[4], n->gw + L.b[4], B, 64, n->part, st);
-  if (!rc) rc = conv_dgrad<64, 64, 1>(n->dact[5], n->act[5], n->wb[4], n->dact[4], B, 64, sms, st);
-  if (!rc) rc = conv_wgrad<64, 64, 2>(n->dact[4], n->act[4], n->act[3], n->gw + L.w[3], n->gw + L.b[3], B, 128, n->part, st);
-  if (!rc) rc = conv_dgrad<64, 64, 2>(n->dact[4], n->act[4], n->wb[3], n->dact[3], B, 128, sms, st);
-  if (!rc) rc = conv_wgrad<32, 64, 1>(n->dact[3], n->act[3], n->act[2], n->gw + L.w[2], n->gw + L.b[2], B, 128, n->part, st);
-  if (!rc) rc = conv_dgrad<32, 64, 1>(n->dact[3], n->act[3], n->wb[2], n->dact[2], B, 128, sms, st);
-  if (!rc) rc = conv_wgrad<32, 32, 2>(n->dact[2], n->act[2], n->act[1], n->gw + L.w[1], n->gw + L.b[1], B, 256, n->part, st);
-  if (!rc) rc = conv_dgrad<32, 32, 2>(n->dact[2], n->act[2], n->wb[1], n->dact[1], B, 256, sms, st);
+  int rc = conv_wgrad_tc<64, 64, 1>(n->dact[5], n->act[4], n->gw + L.w[4], n->gw + L.b[4], B, 64, n->part, st, flag);
+  if (!rc) rc = conv_dgrad<64, 64, 1>(n->dact[5], n->act[5], n->wb[4], n->act[4], n->dact[4], B, 64, sms, st);
+  if (!rc) rc = conv_wgrad_tc<64, 64, 2>(n->dact[4], n->act[3], n->gw + L.w[3], n->gw + L.b[3], B, 128, n->part, st, flag);
+  if (!rc) rc = conv_dgrad<64, 64, 2>(n->dact[4], n->act[4], n->wb[3], n->act[3], n->dact[3], B, 128, sms, st);
+  if (!rc) rc = conv_wgrad_tc<32, 64, 1>(n->dact[3], n->act[2], n->gw + L.w[2], n->gw + L.b[2], B, 128, n->part, st, flag);
+  if (!rc) rc = conv_dgrad<32, 64, 1>(n->dact[3], n->act[3], n->wb[2], n->act[2], n->dact[2], B, 128, sms, st);
+  if (!rc) rc = conv_wgrad_tc<32, 32, 2>(n->dact[2], n->act[1], n->gw + L.w[1], n->gw + L.b[1], B, 256, n->part, st, flag);
+  if (!rc) rc = conv_dgrad<32, 32, 2>(n->dact[2], n->act[2], n->wb[1], n->act[1], n->dact[1], B, 256, sms, st);
   if (rc) return rc;
   return conv1_wgrad(n->dact[1], n->act[1], img, n->gw + L.w[0], n->gw + L.b[0], B, kImg, n->part, st);
 }
@@ -1529,21 +1656,29 @@ extern "C" int gfh_conv3x3(gfh_ctx* ctx, int32_t mode, int32_t cin, int32_t cout
   const auto* out = (const __nv_bfloat16*)d_out;
   const auto* dout = (const __nv_bfloat16*)d_dout;
   float* part = nullptr;
-  if (mode == 2) {   // partial sums in the context scratch
+  size_t part_bytes = 0;
+  if (mode == 2) {   // partial sums in the context scratch, then (L2-L5) the masked gradient
     int l = -1;
     for (int q = 0; q < 5; ++q)
       if (kCin[q] == cin && kCout[q] == cout && kStride[q] == stride) l = q;
     if (l < 0) return GFH_ERR_ARG;
     const int64_t ho = h / stride;
-    const int rc = ensure_scratch(ctx, layer_partial_floats(l, (int64_t)batch * ho * ho) * 4);
+    part_bytes = (layer_partial_floats(l, (int64_t)batch * ho * ho) * 4 + 255) / 256 * 256;
+    const int rc = ensure_scratch(ctx, part_bytes + (size_t)batch * ho * ho * cout * 2);
     if (rc) return rc;
     part = (float*)ctx->pm_buf;
   }
 #define GFH_CONV_CASE(CI, CO, S)                                                                   \
   if (cin == CI && cout == CO && stride == S) {                                                    \
     if (mode == 0) return conv_fwd<CI, CO, S>(in, w, d_bias, (__nv_bfloat16*)d_res, batch, h, sms, st, ctx->d_flag); \
-    if (mode == 1) return conv_dgrad<CI, CO, S>(dout, out, w, (__nv_bfloat16*)d_res, batch, h, sms, st); \
-    if (mode == 2) return conv_wgrad<CI, CO, S>(dout, out, in, (float*)d_res, d_db, batch, h, part, st); \
+    if (mode == 1) return conv_dgrad<CI, CO, S>(dout, out, w, nullptr, (__nv_bfloat16*)d_res, batch, h, sms, st); \
+    if (mode == 2) {                                                                               \
+      const int64_t n_el = (int64_t)batch * (h / S) * (h / S) * CO;                                \
+      __nv_bfloat16* g = (__nv_bfloat16*)((char*)ctx->pm_buf + part_bytes);                       \
+      k_mask_grad<<<(unsigned)((n_el + 255) / 256), 256, 0, st>>>(dout, out, g, n_el);              \
+      GFH_CUDA_TRY(cudaGetLastError());                                                            \
+      return conv_wgrad_tc<CI, CO, S>(g, in, (float*)d_res, d_db, batch, h, part, st, ctx->d_flag); \
+    }                                                                                              \
     return GFH_ERR_ARG;                                                                            \
   }
   if (cin == 2 && cout == 32 && stride == 1) {                      // first layer: no input gradient

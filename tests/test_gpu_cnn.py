@@ -141,12 +141,14 @@ def test_conv_input_gradient(built_lib, gpu_ctx, cin, cout, S):
 
 @pytest.mark.parametrize("cin,cout,S", ALL_LAYERS)
 def test_conv_weight_gradient(built_lib, gpu_ctx, cin, cout, S):
-    """fp32 sums over M = B (H/S)^2 pixels (per-chunk sums, then the chunks added in order): at
-    most M + 1024 rounded additions on any path, so within (M + 1024) u sum|terms| of the exact sum;
-    bias gradient likewise.  Run twice: the result is the same bit for bit (no atomics)."""
+    """fp32 sums over M = B (H/S)^2 pixels (per-chunk sums in tensor memory or registers, then the
+    chunks added in order): at most M + 1024 rounded additions on any path, so within
+    (M + 1024) u sum|terms| of the exact sum; bias gradient likewise.  Run twice: the result is
+    the same bit for bit (no atomics)."""
     gfh = built_lib
     rng = np.random.default_rng(200 + cin + cout + S)
-    B, H = 3, 48
+    B = 3
+    H = 48 if cin == 2 else 64 * S          # the tensor-core layers take output sides of 64k
     Ho = H // S
     xb = rand_bf16(rng, (B, H, H, cin), relu=True)
     gb = rand_bf16(rng, (B, Ho, Ho, cout), scale=0.01)
@@ -262,9 +264,11 @@ def test_network_stages_elementwise(built_lib, gpu_ctx):
     assert np.all(np.abs(GW["WH"] - gWH) <= K * U32 * aWH + 1e-30)
     assert np.all(np.abs(GW["bH"] - gbH) <= K * U32 * abH + 1e-30)
     assert np.all(np.abs(GW["bnull"] - gbn) <= K * U32 * abn + 1e-30)
-    # gradient in activation 5: 3 x 64 terms, / 64, one bf16 rounding, the same on every row
+    # gradient in layer 5's pre-activation: 3 x 64 terms, / 64, one bf16 rounding, the same on
+    # every row, stored masked by the ReLU (activation 5 > 0)
     da = C.bf16_value(net.read_tensor(gfh.CNN_DACT + 5, B))
-    assert_bf16_close(da, C.pool_grad(dpool, 64), 2 * 192 * U32 * C.pool_grad(adpool, 64))
+    m5 = acts[5] > 0
+    assert_bf16_close(da, C.pool_grad(dpool, 64) * m5, 2 * 192 * U32 * C.pool_grad(adpool, 64) * m5)
     # backward through the five layers on the GPU's stored gradients
     for l in range(4, -1, -1):
         S = C.STRIDE[l]
@@ -276,11 +280,12 @@ def test_network_stages_elementwise(built_lib, gpu_ctx):
         eb = G.sum(axis=(0, 1, 2))
         errb = (M + 8192) * U32 * np.abs(G).sum(axis=(0, 1, 2))
         assert np.all(np.abs(GW[f"b{l + 1}"] - eb) <= errb + 1e-30), l
-        if l > 0:
+        if l > 0:      # stored masked by the ReLU of activation l
             din = C.bf16_value(net.read_tensor(gfh.CNN_DACT + l, B))
             H = acts[l].shape[1]
-            exact = C.conv3x3_input_grad(G, Wb[l], S, H)
-            err = 9 * C.COUT[l] * U32 * C.conv3x3_input_grad(np.abs(G), np.abs(Wb[l]), S, H)
+            ml = acts[l] > 0
+            exact = C.conv3x3_input_grad(G, Wb[l], S, H) * ml
+            err = 9 * C.COUT[l] * U32 * C.conv3x3_input_grad(np.abs(G), np.abs(Wb[l]), S, H) * ml
             assert_bf16_close(din, exact, err)
     net.close()
 
