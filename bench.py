@@ -69,7 +69,7 @@ def parse():
     ap.add_argument("--impl", default="gfh", choices=["gfh", "reference"])
     ap.add_argument("--workload", default="plain_paper",
                     choices=["plain_paper", "plain_small", "batched_n", "paper_grids", "uneven",
-                             "proposer", "followup", "splice"])
+                             "proposer", "followup", "splice", "train"])
     ap.add_argument("--no-graph", action="store_true",
                     help="time direct calls only (default: the step is also replayed as a CUDA graph)")
     ap.add_argument("--tile", default=None, help="rows,cols,threads of the Hough tiles")
@@ -430,6 +430,37 @@ def reference_proposer(args):
                               "d2h_bytes_per_step": 0}}), flush=True)
 
 
+def reference_train(args):
+    """Reference arm of the training workload: the oracle's network forward and backward pass
+    (fp64 numpy, the kernels' bf16 storage points) on one image per step."""
+    from oracle import cnn_oracle as C
+    rng = np.random.default_rng(0)
+    params = rng.uniform(-0.05, 0.05, C.layout()[1])
+    img = C.bf16(np.log1p(rng.poisson(1.2, (1, 256, 256, 2)).astype(np.float64)))
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        C.backward(C.forward(params, img), np.array([7]))
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    t = float(np.mean(times))
+    value = 1.0 / t
+    cores, model = host_cpu()
+    print(json.dumps({"impl": "reference", "metric": "proposal-network training images/s",
+                      "value": value, "unit": "images/s", "n_gpus": args.gpus, "steps": args.steps,
+                      "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "fp64 (bf16 storage points)",
+                      "data": "synthetic",
+                      "config": {"workload": "one AdamW step of the proposal network on 256 images of 256 x 256 "
+                                             "x 2 (forward, weight and input gradients, optimiser)",
+                                 "batch": 256, "gflop_per_image": NET_TRAIN_FLOP / 1e9},
+                      "cpu_baseline": {"value": value, "unit": "images/s", "cores": 1, "kind": "oracle",
+                                       "sample": "oracle forward + backward of one image per step, numpy",
+                                       "cpu_model": model, "nproc": cores},
+                      "e2e": {"value": value, "unit": "images/s", "h2d_bytes_per_step": 0,
+                              "d2h_bytes_per_step": 0}}), flush=True)
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -440,6 +471,8 @@ def run_reference(args):
         return reference_followup(args)
     if args.workload == "splice":
         return reference_splice(args)
+    if args.workload == "train":
+        return reference_train(args)
     from oracle import gfh_oracle as O
     spec, pm, grids = workload(args.workload, 0)
     x = spec.series()
@@ -982,6 +1015,74 @@ def measure_proposer(ctx, stream, steps, warmup, eval_maps=51 * 196):
     bank.plan.close()
     torch.cuda.empty_cache()
     return out
+
+
+# multiply-adds per image of the proposal network: forward of the five 3x3 layers, their weight
+# gradients (the same count) and the input gradients of layers 2-5
+_NET_MACS = [256 * 256 * 32 * 18, 128 * 128 * 32 * 288, 128 * 128 * 64 * 288, 64 * 64 * 64 * 576,
+             64 * 64 * 64 * 576]
+NET_FWD_FLOP = 2.0 * sum(_NET_MACS)
+NET_TRAIN_FLOP = 2.0 * (2 * sum(_NET_MACS) + sum(_NET_MACS[1:]))
+
+
+def run_train(args):
+    """Training step of the proposal network: one AdamW step on a batch of 256 images (forward,
+    every gradient, optimiser), timed with CUDA events over `steps` steps on resident images."""
+    import torch
+    from paper_1810_09784_gb300 import build as _build
+    from paper_1810_09784_gb300 import gfh
+    from paper_1810_09784_gb300 import proposer as PR
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    _build.build()
+    stream = torch.cuda.Stream()
+    ctx = gfh.Context(local, stream)
+    spec = PR.ProposerSpec()
+    B = 256
+    with torch.cuda.stream(stream):
+        cache = PR.ImageCache(ctx, spec, 0, 2 * B)
+        net = gfh.Cnn(ctx, B, seed=1)
+        for i in range(args.warmup):
+            im, lb = cache.batch((i % 2) * B, B)
+            net.train_step(im, lb, 1e-3, 1e-4, want_loss=False)
+        torch.cuda.synchronize()
+        if ctx.check() != gfh.GFH_OK:
+            raise RuntimeError("training step flagged an error")
+        sampler = ClockSampler(local)
+        with sampler:
+            torch.cuda.nvtx.range_push("timed_steps")
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for i in range(args.steps):
+                im, lb = cache.batch((i % 2) * B, B)
+                net.train_step(im, lb, 1e-3, 1e-4, want_loss=False)
+            b.record(stream)
+            torch.cuda.synchronize()
+            torch.cuda.nvtx.range_pop()
+        ms = a.elapsed_time(b) / args.steps
+        fw = _time_ms(stream, lambda: net.forward(cache.images[:B]), max(3, args.steps))
+    net.close()
+    if rank != 0:
+        return
+    peak = PEAKS.get("bf16_tflops_sustained")
+    tflops = NET_TRAIN_FLOP * B / (ms * 1e-3) / 1e12
+    fw_tflops = NET_FWD_FLOP * B / (fw * 1e-3) / 1e12
+    print(json.dumps({
+        "metric": "proposal-network training images/s", "value": B / (ms * 1e-3), "unit": "images/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16 weights and activations, fp32 accumulate", "data": "synthetic (series peakmaps)",
+        "config": {"workload": "one AdamW step of the proposal network on 256 images of 256 x 256 "
+                               "x 2 (forward, weight and input gradients, optimiser)",
+                   "batch": B, "gflop_per_image": NET_TRAIN_FLOP / 1e9},
+        "roofline": {"bound": "tensor", "kernel": "whole training step", "achieved": tflops,
+                     "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak if peak else None,
+                     "peak_source": "measured cuBLAS bf16, sustained" if peak else "none",
+                     "algorithmic": f"{NET_TRAIN_FLOP / 1e9:.2f} GFLOP per image", "traffic": None},
+        "forward": {"ms_256_images": fw, "tflops": fw_tflops,
+                    "frac_of_burst_peak": fw_tflops / PEAKS["bf16_tflops"] if "bf16_tflops" in PEAKS else None},
+        "gpu_launches": None, "clocks": sampler.summary()}), flush=True)
+    ctx.close()
 
 
 def run_gpu_lists(args):
@@ -1790,6 +1891,8 @@ def main():
         run_followup(args)
     elif args.workload == "splice":
         run_splice(args)
+    elif args.workload == "train":
+        run_train(args)
     else:
         run_gpu(args)
 
