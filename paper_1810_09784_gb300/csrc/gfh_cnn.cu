@@ -13,8 +13,8 @@
 //   mean over t                           -> [B][64 f][64]
 //   head: 1-D conv over f, width 3, 64 -> 64 k tiles  -> logits[b][kt * 64 + f], plus one
 //   "no signal" logit: 4097 classes, softmax cross-entropy.
-// The gradient of every layer is computed by hand-written kernels: weight gradients of L2-L5 on
-// tcgen05, input gradients of L2-L5 on mma.sync, L1's weight gradient and the head on CUDA cores;
+// The gradient of every layer is computed by hand-written kernels: weight and input gradients of
+// L2-L5 on tcgen05, L1's weight gradient and the head on CUDA cores;
 // every reduction runs in a fixed order, so a training step is deterministic.  AdamW updates fp32
 // master weights and refreshes the bf16 copies.  Activation gradients are stored masked by their
 // ReLU (the gradients in the pre-activations), so the gradient kernels stage them as they are.
@@ -42,6 +42,7 @@ constexpr int kCin[5] = {2, 32, 32, 64, 64};
 constexpr int kCout[5] = {32, 32, 64, 64, 64};
 constexpr int kStride[5] = {1, 2, 1, 2, 1};
 
+// The head's weights, biases and no-signal bias are contiguous (one gradient reduction covers them).
 Layout make_layout() {
   Layout L{};
   size_t o = 0;
@@ -358,19 +359,6 @@ __global__ void __launch_bounds__(1024) k_line_scores(const uint32_t* __restrict
 
 // ---- tensor-core helpers --------------------------------------------------------------------------
 
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
-                                         uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-      "{%8,%9}, {%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-__device__ __forceinline__ uint32_t ld_u32(const __nv_bfloat16* p) {
-  return *reinterpret_cast<const uint32_t*>(p);
-}
-
 // Keeps each bf16 half of g where the matching half of the post-ReLU activation is positive.
 __device__ __forceinline__ uint32_t relu_mask(uint32_t g, uint32_t act) {
   const uint32_t lo = ((act & 0xffffu) != 0u && !(act & 0x8000u)) ? 0xffffu : 0u;
@@ -504,12 +492,25 @@ __device__ __forceinline__ void async_proxy_fence() {
 // MMA's A descriptor starts at that entry (any 16-byte row), 8-row groups 128 bytes apart, K
 // halves one chunk block apart; the over-read of the dropped rows stays inside a tail pad.
 // CIN = 2: a tile is 128 consecutive pixels staged im2col (k = 2 tap + ci, one 4-byte pair per tap).
-template <int CIN, int COUT, int S>
+// Output rows wider than 128 pixels are cut into column blocks of 128 (entries x0 - 1 .. x0 + 128).
+//
+// The same kernel computes input gradients (S = 1, no bias, no ReLU): with the gradient G in a
+// layer's pre-activation as `in` (CIN = the layer's output channels) and the layer's weights
+// W[CIN][3][3][COUT] as `w`, the input gradient din[y][x][c] = sum_{dy, dx, o} G[y + 1 - dy]
+// [x + 1 - dx][o] W[o][dy][dx][c] is this convolution with the taps flipped and W transposed
+// (B[c][(8 - tap) CIN + o] = W[o][tap][c], staged once per block).  MODE 1: a stride-1 layer (G of
+// H x H pixels).  MODE 2: a stride-2 layer, whose input gradient is the stride-1 convolution of G
+// with zeros inserted between its pixels (G of H/2 x H/2): the halo staging reads G at even rows
+// and columns and zero-fills the rest, so the zeros cost no memory.  The result is stored masked by
+// mask > 0 (the gradient in the previous layer's pre-activation) when mask is given.
+template <int CIN, int COUT, int S, int MODE = 0>
 __global__ void __launch_bounds__(256) k_conv_fwd_tc(const __nv_bfloat16* __restrict__ in,
                                                      const __nv_bfloat16* __restrict__ w,
                                                      const float* __restrict__ bias,
+                                                     const __nv_bfloat16* __restrict__ mask,
                                                      __nv_bfloat16* __restrict__ out, int B, int H,
                                                      int tcols, unsigned int* flag) {
+  static_assert(MODE == 0 || (S == 1 && CIN % 8 == 0), "input gradients: stride-1 halo form");
   constexpr bool HALO = CIN % 8 == 0;
   constexpr int KR = 9 * CIN;                        // real K
   constexpr int K = (KR + 15) / 16 * 16;             // padded K
@@ -528,20 +529,28 @@ __global__ void __launch_bounds__(256) k_conv_fwd_tc(const __nv_bfloat16* __rest
   const int Ho = H / S;
   const int M = B * Ho * Ho;
   const int RT = Ho <= 64 ? 2 : 1;                   // output rows per tile (halo form)
-  const int NP = Ho + 2;                             // halo entries per (row, chunk, parity)
+  const int CW = Ho > 128 ? 128 : Ho;                // output columns per tile
+  const int NCB = Ho / CW;                           // column blocks per row
+  const int NP = CW + 2;                             // halo entries per (row, chunk, parity)
   const int HBLK = S * NP * 16;                      // bytes per (row, chunk)
-  const int n_tiles = HALO ? B * (Ho / RT) : (M + 127) / 128;
+  const int n_tiles = HALO ? B * (Ho / RT) * NCB : (M + 127) / 128;
+  const int Hs = MODE == 2 ? H / 2 : H;              // rows / columns of `in`
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tslot)), "r"(tcols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   // weights, K-major rows of the output channel, zero-padded K
-  if (HALO) {
+  if (HALO && MODE == 0) {
     for (int e = tid; e < COUT * (KR / 8); e += blockDim.x) {
       const int co = e / (KR / 8), k = (e % (KR / 8)) * 8;
       *reinterpret_cast<int4*>(sb + cm_off(co, k, COUT)) =
           __ldg(reinterpret_cast<const int4*>(w + co * KR + k));
+    }
+  } else if (HALO) {                                 // transposed, taps flipped
+    for (int e = tid; e < COUT * KR; e += blockDim.x) {
+      const int n = e / KR, k = e - n * KR, tap = k / CIN, o = k - tap * CIN;
+      *reinterpret_cast<__nv_bfloat16*>(sb + cm_off(n, k, COUT)) = w[(o * 9 + 8 - tap) * COUT + n];
     }
   } else {
     for (int e = tid; e < COUT * K; e += blockDim.x) {
@@ -550,14 +559,16 @@ __global__ void __launch_bounds__(256) k_conv_fwd_tc(const __nv_bfloat16* __rest
           k < KR ? w[co * KR + k] : __float2bfloat16_rn(0.f);
     }
   }
-  for (int c = tid; c < COUT; c += blockDim.x) sbias[c] = bias[c];
+  for (int c = tid; c < COUT; c += blockDim.x) sbias[c] = MODE == 0 ? bias[c] : 0.f;
   if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
   const uint32_t sa32 = smem_u32(sa), sb32 = smem_u32(sb);
 
   auto stage = [&](int t) {
     if (HALO) {
-      // tile = rows y0 .. y0 + RT - 1 of image b; input rows y0 S - 1 + ri, ri < (RT - 1) S + 3
-      const int b = t / (Ho / RT), y0 = (t - b * (Ho / RT)) * RT;
+      // tile = rows y0 .. y0 + RT - 1, columns x0 .. x0 + CW - 1 of image b; input rows
+      // y0 S - 1 + ri, ri < (RT - 1) S + 3
+      const int b = t / ((Ho / RT) * NCB), rem = t - b * ((Ho / RT) * NCB);
+      const int y0 = (rem / NCB) * RT, x0 = (rem - (rem / NCB) * NCB) * CW;
       const int rin = (RT - 1) * S + 3;
       const int jb_n = (NP + 15) / 16;               // blocks of 16 entries
       const int tot = rin * S * (QC > 1 ? QC / 2 : 1) * jb_n * 32;
@@ -572,9 +583,11 @@ __global__ void __launch_bounds__(256) k_conv_fwd_tc(const __nv_bfloat16* __rest
         if (j >= NP) continue;
         const int q = 2 * qh + qlo;
         const int yi = y0 * S - 1 + ri;
-        const int xi = S == 1 ? j - 1 : (par == 0 ? 2 * j - 1 : 2 * j);
-        const bool inside = yi >= 0 && yi < H && xi >= 0 && xi < H;
-        const __nv_bfloat16* src = inside ? in + (((int64_t)b * H + yi) * H + xi) * CIN + q * 8 : in;
+        const int xi = S == 1 ? x0 + j - 1 : (par == 0 ? 2 * (x0 + j) - 1 : 2 * (x0 + j));
+        bool inside = yi >= 0 && yi < H && xi >= 0 && xi < H;
+        if (MODE == 2) inside = inside && !(yi & 1) && !(xi & 1);   // the inserted zeros
+        const int ys = MODE == 2 ? yi >> 1 : yi, xs = MODE == 2 ? xi >> 1 : xi;
+        const __nv_bfloat16* src = inside ? in + (((int64_t)b * Hs + ys) * Hs + xs) * CIN + q * 8 : in;
         cp_async16(sa32 + (uint32_t)(((ri * QC + q) * S + par) * NP * 16 + j * 16), src,
                    inside ? 16u : 0u);
       }
@@ -661,9 +674,10 @@ __global__ void __launch_bounds__(256) k_conv_fwd_tc(const __nv_bfloat16* __rest
       int64_t m;
       bool valid;
       if (HALO) {
-        const int b = tile / (Ho / RT), y = (tile - b * (Ho / RT)) * RT + r;
-        m = ((int64_t)b * Ho + y) * Ho + p;
-        valid = p < Ho;
+        const int b = tile / ((Ho / RT) * NCB), rem = tile - b * ((Ho / RT) * NCB);
+        const int y = (rem / NCB) * RT + r, x0 = (rem - (rem / NCB) * NCB) * CW;
+        m = ((int64_t)b * Ho + y) * Ho + x0 + p;
+        valid = p < CW;
       } else {
         m = (int64_t)tile * 128 + p;
         valid = m < M;
@@ -673,10 +687,24 @@ __global__ void __launch_bounds__(256) k_conv_fwd_tc(const __nv_bfloat16* __rest
           uint32_t v[16];
           tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(r * COUT + c0), v);
           uint32_t pk[8];
+          if (MODE == 0) {
 #pragma unroll
-          for (int j = 0; j < 8; ++j)
-            pk[j] = pack_bf16(fmaxf(__uint_as_float(v[2 * j]) + sbias[c0 + 2 * j], 0.f),
-                              fmaxf(__uint_as_float(v[2 * j + 1]) + sbias[c0 + 2 * j + 1], 0.f));
+            for (int j = 0; j < 8; ++j)
+              pk[j] = pack_bf16(fmaxf(__uint_as_float(v[2 * j]) + sbias[c0 + 2 * j], 0.f),
+                                fmaxf(__uint_as_float(v[2 * j + 1]) + sbias[c0 + 2 * j + 1], 0.f));
+          } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              pk[j] = pack_bf16(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
+            if (mask && valid) {
+              const int4* mk = reinterpret_cast<const int4*>(mask + m * COUT + c0);
+              const int4 m0 = __ldg(mk), m1 = __ldg(mk + 1);
+              const uint32_t mw[8] = {(uint32_t)m0.x, (uint32_t)m0.y, (uint32_t)m0.z, (uint32_t)m0.w,
+                                      (uint32_t)m1.x, (uint32_t)m1.y, (uint32_t)m1.z, (uint32_t)m1.w};
+#pragma unroll
+              for (int j = 0; j < 8; ++j) pk[j] = relu_mask(pk[j], mw[j]);
+            }
+          }
           if (valid) {
             int4* o = reinterpret_cast<int4*>(out + m * COUT + c0);
             o[0] = make_int4(pk[0], pk[1], pk[2], pk[3]);
@@ -693,81 +721,6 @@ __global__ void __launch_bounds__(256) k_conv_fwd_tc(const __nv_bfloat16* __rest
     if (!ok) break;
   }
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols));
-}
-
-// ---- L2-L5 input gradient: din[m][ci] = sum_{tap, co} G[src(m, tap)][co] W[co][tap][ci] ----------
-// m = input pixel (b, y, x); the output pixel that reads it through tap (dy, dx) is
-// ((y - dy + 1)/S, (x - dx + 1)/S) when that divides exactly and lies inside; G = dout masked by
-// the layer's ReLU.  With in_act (the layer's input activation) the result is stored masked by
-// in_act > 0, i.e. as the gradient in the previous layer's pre-activation.
-template <int CIN, int COUT, int S>
-__global__ void __launch_bounds__(256) k_conv_dgrad(const __nv_bfloat16* __restrict__ dout,
-                                                    const __nv_bfloat16* __restrict__ out,
-                                                    const __nv_bfloat16* __restrict__ w,
-                                                    const __nv_bfloat16* __restrict__ in_act,
-                                                    __nv_bfloat16* __restrict__ din, int B, int H) {
-  constexpr int K = 9 * COUT, KP = K + 8, NT8 = CIN / 8;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __nv_bfloat16* wt = reinterpret_cast<__nv_bfloat16*>(smem_raw);   // [ci][tap * COUT + co]
-  for (int e = threadIdx.x; e < COUT * 9 * CIN; e += blockDim.x) {
-    const int co = e / (9 * CIN), r = e % (9 * CIN), tap = r / CIN, ci = r % CIN;
-    wt[ci * KP + tap * COUT + co] = w[e];
-  }
-  __syncthreads();
-  const int Ho = H / S;
-  const int64_t M = (int64_t)B * H * H;
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  for (int64_t m0 = ((int64_t)blockIdx.x * 8 + (threadIdx.x >> 5)) * 16; m0 < M;
-       m0 += (int64_t)gridDim.x * 8 * 16) {
-    float acc[NT8][4];
-#pragma unroll
-    for (int n = 0; n < NT8; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
-    int yy[2], xx[2], bb[2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int64_t m = m0 + g + 8 * h;
-      bb[h] = (int)(m / (H * H));
-      const int r = (int)(m % (H * H));
-      yy[h] = r / H + 1;
-      xx[h] = r % H + 1;
-    }
-#pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-      int64_t o[2];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int ny = yy[h] - tap / 3, nx = xx[h] - tap % 3;   // = yo * S, xo * S
-        const bool ok = ny >= 0 && nx >= 0 && ny % S == 0 && nx % S == 0 && ny / S < Ho && nx / S < Ho;
-        o[h] = ok ? (((int64_t)bb[h] * Ho + ny / S) * Ho + nx / S) * COUT : -1;
-      }
-#pragma unroll
-      for (int cc = 0; cc < COUT / 16; ++cc) {
-        const int c = cc * 16 + 2 * t;
-        uint32_t a[4];
-        a[0] = o[0] >= 0 ? relu_mask(ld_u32(dout + o[0] + c), ld_u32(out + o[0] + c)) : 0u;
-        a[1] = o[1] >= 0 ? relu_mask(ld_u32(dout + o[1] + c), ld_u32(out + o[1] + c)) : 0u;
-        a[2] = o[0] >= 0 ? relu_mask(ld_u32(dout + o[0] + c + 8), ld_u32(out + o[0] + c + 8)) : 0u;
-        a[3] = o[1] >= 0 ? relu_mask(ld_u32(dout + o[1] + c + 8), ld_u32(out + o[1] + c + 8)) : 0u;
-        const int k0 = tap * COUT + cc * 16 + 2 * t;
-#pragma unroll
-        for (int n = 0; n < NT8; ++n) {
-          const __nv_bfloat16* wr = wt + (n * 8 + g) * KP + k0;
-          mma_bf16(acc[n], a, ld_u32(wr), ld_u32(wr + 8));
-        }
-      }
-    }
-#pragma unroll
-    for (int n = 0; n < NT8; ++n) {
-      const int col = n * 8 + 2 * t;
-      uint32_t lo = pack_bf16(acc[n][0], acc[n][1]), hi = pack_bf16(acc[n][2], acc[n][3]);
-      if (in_act) {    // masked by the input activation's ReLU: the gradient in its pre-activation
-        lo = relu_mask(lo, ld_u32(in_act + (m0 + g) * CIN + col));
-        hi = relu_mask(hi, ld_u32(in_act + (m0 + g + 8) * CIN + col));
-      }
-      *reinterpret_cast<uint32_t*>(din + (m0 + g) * CIN + col) = lo;
-      *reinterpret_cast<uint32_t*>(din + (m0 + g + 8) * CIN + col) = hi;
-    }
-  }
 }
 
 // ---- L2-L5 weight gradient on tcgen05 -------------------------------------------------------------
@@ -969,17 +922,42 @@ __global__ void k_sum_chunks(const float* __restrict__ part, int chunks, int n,
 }
 
 // Bias gradient of a ReLU layer, db[co] = sum_p G[p][co] with G = dout where out > 0 (out NULL:
-// dout is G already), in kBiasBlocks x (256 / C) strided partial sums part[(block * 256 / C +
-// row)][co] (reduced by k_sum_chunks).
-constexpr int kBiasBlocks = 256;
+// dout is G already): thread = (pixel row r of the block, 8 channels) reading 16 bytes per pixel
+// with a stride of kBiasBlocks x rows pixels; the block adds its rows in order into part[block][co]
+// (reduced by k_sum_chunks).
+constexpr int kBiasBlocks = 1024;
 __global__ void __launch_bounds__(256) k_bias_grad(const __nv_bfloat16* __restrict__ dout,
                                                    const __nv_bfloat16* __restrict__ out,
                                                    float* __restrict__ part, int64_t M, int C) {
-  const int co = threadIdx.x % C, rows = blockDim.x / C;
-  float s = 0.f;
-  for (int64_t p = (int64_t)blockIdx.x * rows + threadIdx.x / C; p < M; p += (int64_t)gridDim.x * rows)
-    if (!out || __bfloat162float(out[p * C + co]) > 0.f) s += __bfloat162float(dout[p * C + co]);
-  part[((int64_t)blockIdx.x * rows + threadIdx.x / C) * C + co] = s;
+  __shared__ float red[256 * 8];
+  const int q8 = C / 8;                              // 16-byte groups of 8 channels per pixel
+  const int g = threadIdx.x % q8, row = threadIdx.x / q8, rows = blockDim.x / q8;
+  float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (int64_t p = (int64_t)blockIdx.x * rows + row; p < M; p += (int64_t)gridDim.x * rows) {
+    const int4 v = __ldg(reinterpret_cast<const int4*>(dout + p * C) + g);
+    const uint32_t w[4] = {(uint32_t)v.x, (uint32_t)v.y, (uint32_t)v.z, (uint32_t)v.w};
+    uint32_t mk[4] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu};
+    if (out) {
+      const int4 a = __ldg(reinterpret_cast<const int4*>(out + p * C) + g);
+      const uint32_t aw[4] = {(uint32_t)a.x, (uint32_t)a.y, (uint32_t)a.z, (uint32_t)a.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) mk[j] = relu_mask(0xffffffffu, aw[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t m = w[j] & mk[j];
+      s[2 * j] += __uint_as_float(m << 16);
+      s[2 * j + 1] += __uint_as_float(m & 0xffff0000u);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 8; ++j) red[row * C + g * 8 + j] = s[j];
+  __syncthreads();
+  for (int c = threadIdx.x; c < C; c += blockDim.x) {
+    float t = 0.f;
+    for (int r = 0; r < rows; ++r) t += red[r * C + c];
+    part[(int64_t)blockIdx.x * C + c] = t;
+  }
 }
 
 // g[i] = dout[i] where out[i] > 0, else 0 (the gradient in a layer's pre-activation), n elements.
@@ -990,32 +968,47 @@ __global__ void k_mask_grad(const __nv_bfloat16* __restrict__ dout,
   if (i < n) g[i] = __bfloat162float(out[i]) > 0.f ? dout[i] : __float2bfloat16_rn(0.f);
 }
 
-// dW1[co][tap][ci] = sum_p G1[p][co] in[src(p, tap)][ci] over images of H x H pixels; a block
-// reduces one chunk of pixels for all 576 weights (thread = (co, tap), both input channels) into
-// part[chunk][576] (reduced by k_sum_chunks).
-__global__ void k_conv1_wgrad(const __nv_bfloat16* __restrict__ dout,
-                              const __nv_bfloat16* __restrict__ out,
-                              const __nv_bfloat16* __restrict__ in, float* __restrict__ part, int B,
-                              int H, int pix_per_block) {
-  const int co = threadIdx.x / 9, tap = threadIdx.x % 9;   // 288 threads
+// dW1[co][tap][ci] = sum_p G1[p][co] in[src(p, tap)][ci] over images of H x H pixels, G1 the
+// gradient in layer 1's pre-activation.  Block = one chunk of pixels; thread t owns output channel
+// t % 32 and every 8th pixel of the chunk (sub-stream t / 32), keeping its 18 (tap, ci) sums in
+// registers: per pixel one coalesced read of G1 and nine 4-byte input reads shared by the 32 lanes.
+// The block adds its 8 sub-streams in order into part[chunk][co][tap][ci] (k_sum_chunks follows).
+__global__ void __launch_bounds__(256) k_conv1_wgrad(const __nv_bfloat16* __restrict__ g1,
+                                                    const __nv_bfloat16* __restrict__ in,
+                                                    float* __restrict__ part, int B, int H,
+                                                    int pix_per_block) {
+  __shared__ float red[8][32 * 18];
+  const int co = threadIdx.x & 31, sub = threadIdx.x >> 5;
   const int64_t M = (int64_t)B * H * H;
   const int64_t p0 = (int64_t)blockIdx.x * pix_per_block;
   const int64_t p1 = p0 + pix_per_block < M ? p0 + pix_per_block : M;
-  float s0 = 0.f, s1 = 0.f;
-  for (int64_t p = p0; p < p1; ++p) {
-    const float a = __bfloat162float(out[p * 32 + co]);
-    if (!(a > 0.f)) continue;
-    const float gv = __bfloat162float(dout[p * 32 + co]);
+  float acc[18];
+#pragma unroll
+  for (int j = 0; j < 18; ++j) acc[j] = 0.f;
+  for (int64_t p = p0 + sub; p < p1; p += 8) {
+    const float gv = __bfloat162float(g1[p * 32 + co]);
     const int b = (int)(p / ((int64_t)H * H)), r = (int)(p % ((int64_t)H * H));
-    const int yi = r / H + tap / 3 - 1, xi = r % H + tap % 3 - 1;
-    if (yi < 0 || yi >= H || xi < 0 || xi >= H) continue;
-    const __nv_bfloat16* q = in + (((int64_t)b * H + yi) * H + xi) * 2;
-    s0 += gv * __bfloat162float(q[0]);
-    s1 += gv * __bfloat162float(q[1]);
+    const int y = r / H, x = r - y * H;
+    const __nv_bfloat16* const base = in + (int64_t)b * H * H * 2;
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+      const int yi = y + tap / 3 - 1, xi = x + tap % 3 - 1;
+      if (yi >= 0 && yi < H && xi >= 0 && xi < H) {
+        const __nv_bfloat162 q = *reinterpret_cast<const __nv_bfloat162*>(base + ((int64_t)yi * H + xi) * 2);
+        acc[2 * tap] = fmaf(gv, __low2float(q), acc[2 * tap]);
+        acc[2 * tap + 1] = fmaf(gv, __high2float(q), acc[2 * tap + 1]);
+      }
+    }
   }
-  float* const dw = part + (int64_t)blockIdx.x * 576;
-  dw[co * 18 + tap * 2] = s0;
-  dw[co * 18 + tap * 2 + 1] = s1;
+#pragma unroll
+  for (int j = 0; j < 18; ++j) red[sub][co * 18 + j] = acc[j];
+  __syncthreads();
+  for (int e = threadIdx.x; e < 32 * 18; e += blockDim.x) {
+    float s = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s += red[q][e];
+    part[(int64_t)blockIdx.x * 576 + e] = s;
+  }
 }
 
 // ---- mean over t, head, loss --------------------------------------------------------------------
@@ -1100,32 +1093,33 @@ __global__ void k_softmax_ce(const float* __restrict__ logits, const int32_t* __
       dlogits[(int64_t)b * kClasses + c] = (expf(l[c] - lse) - (c == y ? 1.f : 0.f)) / (float)B;
 }
 
-// Head weight/bias gradients: one thread per (kt, d, c) weight, plus bias and null bias.
+// Head weight/bias gradients: one thread per (kt, d, c) weight, plus bias and null bias, summing
+// the images of chunk blockIdx.y (kHeadImgs images) into part[chunk][weight] (k_sum_chunks adds the
+// chunks in order).
+constexpr int kHeadImgs = 16, kHeadParams = 64 * 3 * 64 + 65;
 __global__ void k_head_wgrad(const float* __restrict__ dlogits, const float* __restrict__ pooled,
-                             float* __restrict__ dwh, float* __restrict__ dbh,
-                             float* __restrict__ dbnull, int B) {
+                             float* __restrict__ part, int B) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int b0 = blockIdx.y * kHeadImgs, b1 = min(B, b0 + kHeadImgs);
+  float s = 0.f;
   if (e < 64 * 3 * 64) {
     const int kt = e / 192, d = (e / 64) % 3, c = e % 64;
-    float s = 0.f;
-    for (int b = 0; b < B; ++b)
+    for (int b = b0; b < b1; ++b)
       for (int f = 0; f < 64; ++f) {
         const int ff = f + d - 1;
         if (ff < 0 || ff >= 64) continue;
         s += dlogits[(int64_t)b * kClasses + kt * 64 + f] * pooled[((int64_t)b * 64 + ff) * 64 + c];
       }
-    dwh[e] += s;
   } else if (e < 64 * 3 * 64 + 64) {
     const int kt = e - 64 * 3 * 64;
-    float s = 0.f;
-    for (int b = 0; b < B; ++b)
+    for (int b = b0; b < b1; ++b)
       for (int f = 0; f < 64; ++f) s += dlogits[(int64_t)b * kClasses + kt * 64 + f];
-    dbh[kt] += s;
   } else if (e == 64 * 3 * 64 + 64) {
-    float s = 0.f;
-    for (int b = 0; b < B; ++b) s += dlogits[(int64_t)b * kClasses + kClasses - 1];
-    dbnull[0] += s;
+    for (int b = b0; b < b1; ++b) s += dlogits[(int64_t)b * kClasses + kClasses - 1];
+  } else {
+    return;
   }
+  part[(int64_t)blockIdx.y * kHeadParams + e] = s;
 }
 
 // d a5[b][t][f][c] = (1/64) sum_{kt, d} dlogits[b][kt * 64 + f - d + 1] wh[kt][d][c]  (same for all t),
@@ -1172,22 +1166,26 @@ __global__ void k_to_bf16(const float* __restrict__ a, __nv_bfloat16* __restrict
 
 // ---- launch helpers -------------------------------------------------------------------------------
 
-template <int CIN, int COUT, int S>
+template <int CIN, int COUT, int S, int MODE = 0>
 int conv_fwd(const __nv_bfloat16* in, const __nv_bfloat16* w, const float* bias,
-             __nv_bfloat16* out, int B, int H, int sms, cudaStream_t st, unsigned int* flag) {
+             const __nv_bfloat16* mask, __nv_bfloat16* out, int B, int H, int sms, cudaStream_t st,
+             unsigned int* flag) {
   constexpr bool HALO = CIN % 8 == 0;
   constexpr int K = (9 * CIN + 15) / 16 * 16;
   const int Ho = H / S;
-  if (HALO && (Ho > 128 || (Ho <= 64 && Ho % 2))) return GFH_ERR_ARG;   // tiles are output rows
+  // tiles are output rows (two when they are at most 64 wide), cut into blocks of 128 columns
+  if (HALO && ((Ho > 128 && Ho % 128) || (Ho <= 64 && Ho % 2))) return GFH_ERR_ARG;
+  if (MODE == 2 && H % 2) return GFH_ERR_ARG;
   const int RT = HALO && Ho <= 64 ? 2 : 1;
-  // halo: rows x chunks x parities x (W_out + 2) entries of 16 bytes, plus the dropped rows'
+  const int CW = Ho > 128 ? 128 : Ho;
+  // halo: rows x chunks x parities x (CW + 2) entries of 16 bytes, plus the dropped rows'
   // over-read (at most 128 entries past a block start); im2col: K/16 slices of 128 x 16
-  const size_t a_bytes = HALO ? (size_t)((RT - 1) * S + 3) * (CIN / 8) * S * (Ho + 2) * 16 + 128 * 16
+  const size_t a_bytes = HALO ? (size_t)((RT - 1) * S + 3) * (CIN / 8) * S * (CW + 2) * 16 + 128 * 16
                               : (size_t)(K / 16) * (128 / 8 * 256);
   const size_t smem = (size_t)(K / 16) * (COUT / 8 * 256) + a_bytes;
   if (smem > kMaxSmemBytes - 4096) return GFH_ERR_SIZE;
   const int tcols = RT * COUT < 32 ? 32 : RT * COUT;                   // power of two here
-  auto fn = k_conv_fwd_tc<CIN, COUT, S>;
+  auto fn = k_conv_fwd_tc<CIN, COUT, S, MODE>;
   GFH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   GFH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   // resident blocks per SM: shared memory (with the static part and the per-block reservation),
@@ -1197,23 +1195,9 @@ int conv_fwd(const __nv_bfloat16* in, const __nv_bfloat16* w, const float* bias,
   const int regs = std::max(1, (fa.numRegs + 7) / 8 * 8);
   const int per_sm = std::max(1, std::min({(int)(kSmemPerSm / (smem + fa.sharedSizeBytes + 1024)),
                                            65536 / (regs * 256), 8, 512 / tcols}));
-  const int64_t tiles = HALO ? (int64_t)B * (Ho / RT) : ((int64_t)B * Ho * Ho + 127) / 128;
+  const int64_t tiles = HALO ? (int64_t)B * (Ho / RT) * (Ho / CW) : ((int64_t)B * Ho * Ho + 127) / 128;
   const int grid = (int)std::min<int64_t>(tiles, (int64_t)sms * per_sm);
-  fn<<<grid, 256, smem, st>>>(in, w, bias, out, B, H, tcols, flag);
-  GFH_CUDA_TRY(cudaGetLastError());
-  return GFH_OK;
-}
-
-template <int CIN, int COUT, int S>
-int conv_dgrad(const __nv_bfloat16* dout, const __nv_bfloat16* out, const __nv_bfloat16* w,
-               const __nv_bfloat16* in_act, __nv_bfloat16* din, int B, int H, int sms,
-               cudaStream_t st) {
-  const size_t smem = (size_t)CIN * (9 * COUT + 8) * 2;
-  auto fn = k_conv_dgrad<CIN, COUT, S>;
-  GFH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const int64_t tiles = (int64_t)B * H * H / 16;
-  const int grid = (int)std::min<int64_t>((tiles + 7) / 8, (int64_t)sms * 8);
-  fn<<<grid, 256, smem, st>>>(dout, out, w, in_act, din, B, H);
+  fn<<<grid, 256, smem, st>>>(in, w, bias, mask, out, B, H, tcols, flag);
   GFH_CUDA_TRY(cudaGetLastError());
   return GFH_OK;
 }
@@ -1240,7 +1224,7 @@ size_t layer_partial_floats(int l, int64_t M) {
 // Scratch floats the weight and bias gradients of every layer of the network need at batch B.
 size_t grad_partial_floats(int B) {
   static const int hin[5] = {256, 256, 128, 128, 64};
-  size_t most = 0;
+  size_t most = (size_t)((B + kHeadImgs - 1) / kHeadImgs) * kHeadParams;
   for (int l = 0; l < 5; ++l) {
     const int64_t ho = hin[l] / kStride[l];
     most = std::max(most, layer_partial_floats(l, (int64_t)B * ho * ho));
@@ -1252,7 +1236,7 @@ int bias_grad(const __nv_bfloat16* dout, const __nv_bfloat16* out, float* db, in
               float* part, cudaStream_t st) {
   k_bias_grad<<<kBiasBlocks, 256, 0, st>>>(dout, out, part, M, C);
   GFH_CUDA_TRY(cudaGetLastError());
-  k_sum_chunks<<<1, 64, 0, st>>>(part, kBiasBlocks * 256 / C, C, db);
+  k_sum_chunks<<<1, 64, 0, st>>>(part, kBiasBlocks, C, db);
   GFH_CUDA_TRY(cudaGetLastError());
   return GFH_OK;
 }
@@ -1280,16 +1264,17 @@ int conv_wgrad_tc(const __nv_bfloat16* G, const __nv_bfloat16* in, float* dw, fl
 }
 
 // First layer (2 input channels) weight and bias gradients, added into dw and db.
-int conv1_wgrad(const __nv_bfloat16* dout, const __nv_bfloat16* out, const __nv_bfloat16* in,
-                float* dw, float* db, int B, int H, float* part, cudaStream_t st) {
+// G1 is the gradient in layer 1's pre-activation (stored masked).
+int conv1_wgrad(const __nv_bfloat16* g1, const __nv_bfloat16* in, float* dw, float* db, int B,
+                int H, float* part, cudaStream_t st) {
   const int64_t P1 = (int64_t)B * H * H;
-  const int ppb = wgrad_chunk_pixels(P1, kMaxChunks1, 2048);
+  const int ppb = wgrad_chunk_pixels(P1, kMaxChunks1, 256);
   const int chunks = (int)((P1 + ppb - 1) / ppb);
-  k_conv1_wgrad<<<(unsigned)chunks, 288, 0, st>>>(dout, out, in, part, B, H, ppb);
+  k_conv1_wgrad<<<(unsigned)chunks, 256, 0, st>>>(g1, in, part, B, H, ppb);
   GFH_CUDA_TRY(cudaGetLastError());
   k_sum_chunks<<<(576 + 255) / 256, 256, 0, st>>>(part, chunks, 576, dw);
   GFH_CUDA_TRY(cudaGetLastError());
-  return bias_grad(dout, out, db, P1, 32, part, st);
+  return bias_grad(g1, nullptr, db, P1, 32, part, st);
 }
 
 }  // namespace
@@ -1346,11 +1331,11 @@ int forward(gfh_cnn* n, const __nv_bfloat16* img, int B) {
   const int sms = n->ctx->num_sms;
   const Layout& L = n->L;
   unsigned int* flag = n->ctx->d_flag;
-  int rc = conv_fwd<2, 32, 1>(img, n->wb[0], n->w + L.b[0], n->act[1], B, 256, sms, st, flag);
-  if (!rc) rc = conv_fwd<32, 32, 2>(n->act[1], n->wb[1], n->w + L.b[1], n->act[2], B, 256, sms, st, flag);
-  if (!rc) rc = conv_fwd<32, 64, 1>(n->act[2], n->wb[2], n->w + L.b[2], n->act[3], B, 128, sms, st, flag);
-  if (!rc) rc = conv_fwd<64, 64, 2>(n->act[3], n->wb[3], n->w + L.b[3], n->act[4], B, 128, sms, st, flag);
-  if (!rc) rc = conv_fwd<64, 64, 1>(n->act[4], n->wb[4], n->w + L.b[4], n->act[5], B, 64, sms, st, flag);
+  int rc = conv_fwd<2, 32, 1>(img, n->wb[0], n->w + L.b[0], nullptr, n->act[1], B, 256, sms, st, flag);
+  if (!rc) rc = conv_fwd<32, 32, 2>(n->act[1], n->wb[1], n->w + L.b[1], nullptr, n->act[2], B, 256, sms, st, flag);
+  if (!rc) rc = conv_fwd<32, 64, 1>(n->act[2], n->wb[2], n->w + L.b[2], nullptr, n->act[3], B, 128, sms, st, flag);
+  if (!rc) rc = conv_fwd<64, 64, 2>(n->act[3], n->wb[3], n->w + L.b[3], nullptr, n->act[4], B, 128, sms, st, flag);
+  if (!rc) rc = conv_fwd<64, 64, 1>(n->act[4], n->wb[4], n->w + L.b[4], nullptr, n->act[5], B, 64, sms, st, flag);
   if (rc) return rc;
   k_pool<<<(B * 4096 + 255) / 256, 256, 0, st>>>(n->act[5], n->pooled, B);
   k_head_fwd<<<B, 256, 0, st>>>(n->pooled, n->w + L.wh, n->w + L.bh, n->w + L.bnull, n->logits);
@@ -1366,20 +1351,21 @@ int backward(gfh_cnn* n, const __nv_bfloat16* img, const int32_t* labels, int B)
   const Layout& L = n->L;
   GFH_CUDA_TRY(cudaMemsetAsync(n->gw, 0, L.total * sizeof(float), st));
   k_softmax_ce<<<B, 256, 0, st>>>(n->logits, labels, n->dlogits, n->loss, B);
-  k_head_wgrad<<<(64 * 3 * 64 + 65 + 255) / 256, 256, 0, st>>>(n->dlogits, n->pooled, n->gw + L.wh,
-                                                               n->gw + L.bh, n->gw + L.bnull, B);
+  const int hchunks = (B + kHeadImgs - 1) / kHeadImgs;
+  k_head_wgrad<<<dim3((kHeadParams + 255) / 256, hchunks), 256, 0, st>>>(n->dlogits, n->pooled, n->part, B);
+  k_sum_chunks<<<(kHeadParams + 255) / 256, 256, 0, st>>>(n->part, hchunks, kHeadParams, n->gw + L.wh);
   k_head_dgrad<<<(B * 4096 + 255) / 256, 256, 0, st>>>(n->dlogits, n->w + L.wh, n->act[5], n->dact[5], B);
   GFH_CUDA_TRY(cudaGetLastError());
   int rc = conv_wgrad_tc<64, 64, 1>(n->dact[5], n->act[4], n->gw + L.w[4], n->gw + L.b[4], B, 64, n->part, st, flag);
-  if (!rc) rc = conv_dgrad<64, 64, 1>(n->dact[5], n->act[5], n->wb[4], n->act[4], n->dact[4], B, 64, sms, st);
+  if (!rc) rc = conv_fwd<64, 64, 1, 1>(n->dact[5], n->wb[4], nullptr, n->act[4], n->dact[4], B, 64, sms, st, flag);
   if (!rc) rc = conv_wgrad_tc<64, 64, 2>(n->dact[4], n->act[3], n->gw + L.w[3], n->gw + L.b[3], B, 128, n->part, st, flag);
-  if (!rc) rc = conv_dgrad<64, 64, 2>(n->dact[4], n->act[4], n->wb[3], n->act[3], n->dact[3], B, 128, sms, st);
+  if (!rc) rc = conv_fwd<64, 64, 1, 2>(n->dact[4], n->wb[3], nullptr, n->act[3], n->dact[3], B, 128, sms, st, flag);
   if (!rc) rc = conv_wgrad_tc<32, 64, 1>(n->dact[3], n->act[2], n->gw + L.w[2], n->gw + L.b[2], B, 128, n->part, st, flag);
-  if (!rc) rc = conv_dgrad<32, 64, 1>(n->dact[3], n->act[3], n->wb[2], n->act[2], n->dact[2], B, 128, sms, st);
+  if (!rc) rc = conv_fwd<64, 32, 1, 1>(n->dact[3], n->wb[2], nullptr, n->act[2], n->dact[2], B, 128, sms, st, flag);
   if (!rc) rc = conv_wgrad_tc<32, 32, 2>(n->dact[2], n->act[1], n->gw + L.w[1], n->gw + L.b[1], B, 256, n->part, st, flag);
-  if (!rc) rc = conv_dgrad<32, 32, 2>(n->dact[2], n->act[2], n->wb[1], n->act[1], n->dact[1], B, 256, sms, st);
+  if (!rc) rc = conv_fwd<32, 32, 1, 2>(n->dact[2], n->wb[1], nullptr, n->act[1], n->dact[1], B, 256, sms, st, flag);
   if (rc) return rc;
-  return conv1_wgrad(n->dact[1], n->act[1], img, n->gw + L.w[0], n->gw + L.b[0], B, kImg, n->part, st);
+  return conv1_wgrad(n->dact[1], img, n->gw + L.w[0], n->gw + L.b[0], B, kImg, n->part, st);
 }
 
 }  // namespace
@@ -1657,6 +1643,10 @@ extern "C" int gfh_conv3x3(gfh_ctx* ctx, int32_t mode, int32_t cin, int32_t cout
   const auto* dout = (const __nv_bfloat16*)d_dout;
   float* part = nullptr;
   size_t part_bytes = 0;
+  if (mode == 1) {   // the masked gradient in the context scratch
+    const int rc = ensure_scratch(ctx, (size_t)batch * (h / stride) * (h / stride) * cout * 2);
+    if (rc) return rc;
+  }
   if (mode == 2) {   // partial sums in the context scratch, then (L2-L5) the masked gradient
     int l = -1;
     for (int q = 0; q < 5; ++q)
@@ -1670,8 +1660,15 @@ extern "C" int gfh_conv3x3(gfh_ctx* ctx, int32_t mode, int32_t cin, int32_t cout
   }
 #define GFH_CONV_CASE(CI, CO, S)                                                                   \
   if (cin == CI && cout == CO && stride == S) {                                                    \
-    if (mode == 0) return conv_fwd<CI, CO, S>(in, w, d_bias, (__nv_bfloat16*)d_res, batch, h, sms, st, ctx->d_flag); \
-    if (mode == 1) return conv_dgrad<CI, CO, S>(dout, out, w, nullptr, (__nv_bfloat16*)d_res, batch, h, sms, st); \
+    if (mode == 0) return conv_fwd<CI, CO, S>(in, w, d_bias, nullptr, (__nv_bfloat16*)d_res, batch, h, sms, st, ctx->d_flag); \
+    if (mode == 1) {                                                                               \
+      const int64_t n_el = (int64_t)batch * (h / S) * (h / S) * CO;                                \
+      __nv_bfloat16* g = (__nv_bfloat16*)ctx->pm_buf;                                              \
+      k_mask_grad<<<(unsigned)((n_el + 255) / 256), 256, 0, st>>>(dout, out, g, n_el);              \
+      GFH_CUDA_TRY(cudaGetLastError());                                                            \
+      return conv_fwd<CO, CI, 1, S == 1 ? 1 : 2>(g, w, nullptr, nullptr, (__nv_bfloat16*)d_res,     \
+                                                 batch, h, sms, st, ctx->d_flag);                  \
+    }                                                                                              \
     if (mode == 2) {                                                                               \
       const int64_t n_el = (int64_t)batch * (h / S) * (h / S) * CO;                                \
       __nv_bfloat16* g = (__nv_bfloat16*)((char*)ctx->pm_buf + part_bytes);                       \
@@ -1682,8 +1679,14 @@ extern "C" int gfh_conv3x3(gfh_ctx* ctx, int32_t mode, int32_t cin, int32_t cout
     return GFH_ERR_ARG;                                                                            \
   }
   if (cin == 2 && cout == 32 && stride == 1) {                      // first layer: no input gradient
-    if (mode == 0) return conv_fwd<2, 32, 1>(in, w, d_bias, (__nv_bfloat16*)d_res, batch, h, sms, st, ctx->d_flag);
-    if (mode == 2) return conv1_wgrad(dout, out, in, (float*)d_res, d_db, batch, h, part, st);
+    if (mode == 0) return conv_fwd<2, 32, 1>(in, w, d_bias, nullptr, (__nv_bfloat16*)d_res, batch, h, sms, st, ctx->d_flag);
+    if (mode == 2) {
+      const int64_t n_el = (int64_t)batch * h * h * 32;
+      __nv_bfloat16* g = (__nv_bfloat16*)((char*)ctx->pm_buf + part_bytes);
+      k_mask_grad<<<(unsigned)((n_el + 255) / 256), 256, 0, st>>>(dout, out, g, n_el);
+      GFH_CUDA_TRY(cudaGetLastError());
+      return conv1_wgrad(g, in, (float*)d_res, d_db, batch, h, part, st);
+    }
     return GFH_ERR_ARG;
   }
   GFH_CONV_CASE(32, 32, 2)
