@@ -79,8 +79,6 @@ def parse():
                     help="default workload only: leave out the batched_n, uneven and proposer sub-objects")
     ap.add_argument("--sequential", action="store_true",
                     help="also time one plan per map (always on for batched_n)")
-    ap.add_argument("--epochs", type=int, default=3,
-                    help="proposer: training passes over the 100,000 training maps")
     ap.add_argument("--eval-maps", type=int, default=51 * 196,
                     help="proposer: held-out maps for the recall measurement (multiple of 51)")
     ap.add_argument("--maps", type=int, default=0,
@@ -405,8 +403,10 @@ def reference_proposer(args):
     spec = PR.ProposerSpec()
     s = 100011 + 30
     smp = PR.draw(spec, [s])
-    fi, bj = synth.hashed_peaklist(spec.seed, s, spec.n_fft, spec.bin_lo, spec.bin_hi,
-                                   spec.p_noise24, int(smp.p_track24[0]), smp.tracks[0])
+    inj = PR.injection_of(spec, smp, 0)
+    x = synth.strain_series(int(round(spec.fs * spec.t_obs)), spec.fs, PR.series_seed(spec, s),
+                            () if inj is None else (inj,))
+    fi, bj = O.peakmap(x, spec.fs, spec.t_fft, spec.bin_lo, spec.bin_hi)
     o = O.make_grid(O.Grid(**{k: v for k, v in spec.grid_fields(5.0).items() if k != "list"}))
     vals = []
     for i in range(args.warmup + args.steps):
@@ -418,7 +418,8 @@ def reference_proposer(args):
         if i >= args.warmup:
             vals.append(fi.size * rows / (time.perf_counter() - t0))
     value = float(np.mean(vals))
-    sample = f"oracle full exact Hough, k rows of one n = 5 held-out map ({fi.size} peaks), 2 s per step, numpy, 1 thread"
+    sample = (f"oracle full exact Hough, k rows of one n = 5 held-out map (its series' oracle peakmap, "
+              f"{fi.size} peaks), 2 s per step, numpy, 1 thread")
     print(json.dumps({"impl": "reference", "metric": "Hough updates/s (peaks x k-bins), full-search equivalent",
                       "value": value, "unit": "updates/s", "n_gpus": args.gpus, "steps": args.steps,
                       "warmup": args.warmup, "ms_per_step": 2000.0, "higher_is_better": True,
@@ -979,16 +980,24 @@ def measure_proposer(ctx, stream, steps, warmup, eval_maps=51 * 196):
             t0 = time.perf_counter()
             summ = PR.summarize(PR.evaluate(ctx, sc, spec, PR.HELD_OUT_FIRST, eval_maps, bank, tau, cap))
             search = PR.PrunedSearch(ctx, sc, bank, tau, cap)
-            t_full, t_pr = [], []
+            t_full, t_pr, upd = [], [], []
             for st in range(warmup + steps):
                 s0 = PR.HELD_OUT_FIRST + nl * st
                 bank.load_peaks(PR.draw(spec, np.arange(s0, s0 + nl)))
                 torch.cuda.synchronize()
+                timed = st >= warmup
+                if timed:
+                    torch.cuda.nvtx.range_push("full_exact")
                 a = _time_ms(stream, bank.full, 1)
+                if timed:
+                    torch.cuda.nvtx.range_pop()
+                    torch.cuda.nvtx.range_push(f"pruned_{name}")
                 b = _time_ms(stream, search.run, 1)
-                if st >= warmup:
+                if timed:
+                    torch.cuda.nvtx.range_pop()
                     t_full.append(a)
                     t_pr.append(b)
+                    upd.append(bank.updates())
             ms_full, ms_pr = float(np.mean(t_full)), float(np.mean(t_pr))
             out[name] = {"tiles_at_most": cap, "tau": tau, "recall": summ["recall"],
                          "held_out_maps": summ["maps"],
@@ -998,6 +1007,7 @@ def measure_proposer(ctx, stream, steps, warmup, eval_maps=51 * 196):
                          "mean_tiles_pruned": summ["mean_tiles_pruned"],
                          "ms_full_exact_per_step": ms_full, "ms_pruned_per_step": ms_pr,
                          "speedup_vs_full_exact": ms_full / ms_pr,
+                         "full_search_updates_per_step": float(np.mean(upd)),
                          "eval_s": round(time.perf_counter() - t0, 1)}
         out["tile"] = list(tuned)
         out["line_heuristic_parameters"] = {"beta": heur.beta, "det_a": heur.det_a, "det_b": heur.det_b}
@@ -1213,179 +1223,69 @@ def run_gpu_lists(args):
 
 
 def run_proposer(args):
-    """Learned proposer + exact Hough.  The network is trained first (untimed, on the GPU by the
-    library's kernels); tau is the largest threshold whose recall on 2,040 validation maps is at
-    least 0.995; recall is then measured on the held-out maps.  A step is one batch of 51 held-out
-    maps (one per braking index) with resident peak lists: the plain full exact Hough of all 51
-    maps, and the pruned search (images, network, proposals of at most 32 coarse tiles, one
-    exact-Hough launch over the proposed tiles and over every map whose proposal cannot reach tau),
-    both timed with CUDA events; the pruned search needs no host round trip."""
+    """Learned proposer + exact Hough, from the committed checkpoint (the network was trained on the
+    GPU by the library's kernels: `python -m paper_1810_09784_gb300.proposer train`).  A step is one
+    batch of 51 held-out maps (one per braking index) with resident peak lists, searched by the full
+    exact Hough and by the pruned search (images, network, proposals, one exact-Hough launch over the
+    proposed tiles and over every map whose proposal cannot reach tau), at both tile budgets, for
+    the network and for the non-learned line ranker; recall on 9,996 held-out series maps."""
     import torch
 
     from paper_1810_09784_gb300 import build as _build
     from paper_1810_09784_gb300 import gfh
-    from paper_1810_09784_gb300 import proposer as PR
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     _build.build()
     stream = torch.cuda.Stream()
     ctx = gfh.Context(local, stream)
-    spec = PR.ProposerSpec()
-    nl = len(PR.N_GRID)
-    held0 = 100011 + 51 * 400 * rank          # held-out maps of this rank (multiples of 51)
-    val0 = 200022 + 51 * 400 * rank
-    ev = lambda: torch.cuda.Event(enable_timing=True)
-    with torch.cuda.stream(stream):
-        net = gfh.Cnn(ctx, 256, seed=1)
-        t0 = time.perf_counter()
-        losses = PR.train_default(ctx, net, spec, epochs=args.epochs)
-        torch.cuda.synchronize()
-        t_train = time.perf_counter() - t0
-        bank = PR.HoughBank(ctx, spec, max_sel=256)
-        bank.load_peaks(PR.draw(spec, np.arange(val0, val0 + nl)))
-        tuned, _ = bank.autotune()
-        res = {}
-        for cap in (32, 256):
-            tau, val = PR.choose_tau(ctx, net, spec, val0, 51 * 40, bank, cap)
-            t0 = time.perf_counter()
-            summ = PR.summarize(PR.evaluate(ctx, net, spec, held0, args.eval_maps, bank, tau, cap))
-            t_eval = time.perf_counter() - t0
-            search = PR.PrunedSearch(ctx, net, bank, tau, cap)
-            t_full, t_pr, t_fwd, upd, fb = [], [], [], 0, 0
-            a, b, c, d = ev(), ev(), ev(), ev()
-            sampler = ClockSampler(local)
-            with sampler:
-                for st in range(args.warmup + args.steps):
-                    smp = PR.draw(spec, np.arange(held0 + nl * st, held0 + nl * (st + 1)))
-                    bank.load_peaks(smp)
-                    torch.cuda.synchronize()
-                    timed = st >= args.warmup and cap == 32
-                    if timed:
-                        torch.cuda.nvtx.range_push("full_exact")
-                    a.record(stream)
-                    bank.full()
-                    b.record(stream)
-                    torch.cuda.synchronize()
-                    if timed:
-                        torch.cuda.nvtx.range_pop()
-                        torch.cuda.nvtx.range_push("pruned")
-                    c.record(stream)
-                    search.run()
-                    d.record(stream)
-                    if timed:
-                        torch.cuda.synchronize()
-                        torch.cuda.nvtx.range_pop()
-                    torch.cuda.synchronize()
-                    f0_, f1_ = ev(), ev()
-                    f0_.record(stream)
-                    net.forward(search.images, search.logits)
-                    f1_.record(stream)
-                    torch.cuda.synchronize()
-                    if st >= args.warmup:
-                        t_full.append(a.elapsed_time(b))
-                        t_pr.append(c.elapsed_time(d))
-                        t_fwd.append(f0_.elapsed_time(f1_))
-                        upd += bank.updates()
-                        fb += int(search.full.sum().item())
-            res[cap] = dict(tau=tau, val=val, summ=summ, t_eval=t_eval, search=search,
-                            ms_full=float(np.sum(t_full)) / args.steps,
-                            ms_pr=float(np.sum(t_pr)) / args.steps, ms_fwd=float(np.mean(t_fwd)),
-                            upd_step=upd / args.steps, fb=fb, clocks=sampler.summary())
-        r = res[32]
-        search = r["search"]
-        # end to end through the API: peak lists from pinned host memory, candidates to the host
-        fi_h = bank.fft_c.cpu().pin_memory()
-        bj_h = bank.bin_c.cpu().pin_memory()
-        cand_h = [torch.empty_like(x, device="cpu").pin_memory() for x in bank.cands]
-        torch.cuda.synchronize()
-        t_e2e = []
-        c, d = ev(), ev()
-        for st in range(max(2, args.steps)):
-            c.record(stream)
-            bank.fft_c.copy_(fi_h, non_blocking=True)
-            bank.bin_c.copy_(bj_h, non_blocking=True)
-            search.run()
-            for x, h in zip(bank.cands, cand_h):
-                h.copy_(x, non_blocking=True)
-            d.record(stream)
-            torch.cuda.synchronize()
-            t_e2e.append(c.elapsed_time(d))
-    ms_pr = r["ms_pr"]
-    ms_max, total_upd = ranks.combine(ms_pr, r["upd_step"], device="cuda")
+    sampler = ClockSampler(local)
+    with sampler:
+        res = measure_proposer(ctx, stream, args.steps, args.warmup, eval_maps=args.eval_maps)
     if rank != 0:
         return
+    op = res[res["operating_point"]] if res["operating_point"] else res["network_32"]
+    value = op["full_search_updates_per_step"] / (op["ms_pruned_per_step"] * 1e-3)
     cpu = None
     if not args.no_cpu_baseline:
         from oracle import gfh_oracle as O
-        g = bank.grids[30]                                   # n = 5
-        o = O.make_grid(O.Grid(**{k: getattr(g, k) for k in ("n", "df", "bin_lo", "bin_hi", "n_fft",
-                                  "t_first", "t_hop", "t_obs", "n_k", "k_min", "dk", "f_max",
-                                  "ana_lo", "ana_hi", "band_hz")}))
-        o0, o1 = bank.offs_host[30], bank.offs_host[31]
-        fi = bank.fft_c[o0:o1].cpu().numpy().view(np.uint32)
-        bj = bank.bin_c[o0:o1].cpu().numpy().view(np.uint32)
+        from paper_1810_09784_gb300 import proposer as PR
+        spec = PR.ProposerSpec()
+        src = PR.PeakSource(ctx, spec, 51)
+        with torch.cuda.stream(stream):
+            src.load(PR.draw(spec, np.arange(PR.HELD_OUT_FIRST, PR.HELD_OUT_FIRST + 51)))
+        o0, o1 = src.offs_host[30], src.offs_host[31]           # the n = 5 map
+        fi = src.fft_c[o0:o1].cpu().numpy().view(np.uint32)
+        bj = src.bin_c[o0:o1].cpu().numpy().view(np.uint32)
+        og = O.make_grid(O.Grid(**{k: v for k, v in spec.grid_fields(5.0).items() if k != "list"}))
         t0 = time.perf_counter()
         rows = 0
-        while time.perf_counter() - t0 < 10.0 and rows < o.n_k:
-            O.hough_row(o, fi, bj, rows)
+        while time.perf_counter() - t0 < 10.0 and rows < og.n_k:
+            O.hough_row(og, fi, bj, rows)
             rows += 1
         dt = time.perf_counter() - t0
         cpu = {"value": fi.size * rows / dt, "unit": "updates/s", "cores": 1, "kind": "oracle",
                "sample": f"oracle full exact Hough of {rows} k rows of the n = 5 map of one held-out "
                          f"batch ({fi.size} peaks), numpy, 1 thread"}
-    flops_img = 2.0 * (65536 * 32 * 18 + 16384 * 32 * 288 + 16384 * 64 * 288 + 4096 * 64 * 576 * 2
-                       + 64 * 64 * 192)
-    fwd_tflops = flops_img * nl / (r["ms_fwd"] * 1e-3) / 1e12
-    bf16_peak = PEAKS.get("bf16_tflops")
-    summ = r["summ"]
-    r256 = res[256]
     line = {
-        "metric": "Hough updates/s (peaks x k-bins), full-search equivalent",
-        "value": total_upd / (ms_max * 1e-3), "unit": "updates/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "int32 counts; bf16 network, fp32 accumulate",
-        "data": "synthetic (statistical peakmap model, hashed per cell)",
-        "config": {"workload": "proposer: 51 maps per step (n = 2.0..7.0), plain_small-shaped "
-                               "(1799 FFTs, 100-400 Hz, 500 k rows), half with one power-law "
-                               "injection (SNR 2-8); at most 32 of 64 x 64 coarse tiles per map, "
-                               "full search of maps whose proposal leaves more than tau",
-                   "n_sel": 32, "tile": list(tuned), "tau": r["tau"], "recall": summ["recall"], "agreement": summ["agreement"],
-                   "held_out_maps": summ["maps"], "injected": summ["injected"],
-                   "detected_full": summ["det_full"], "detected_kept": summ["det_kept"],
-                   "fallback_frac": summ["fallback_frac"], "fallback_injected": summ["fallback_injected"],
-                   "mean_tiles_pruned": summ["mean_tiles_pruned"], "truth_in_top": summ["truth_in_top"],
-                   "validation_recall": r["val"]["recall"],
-                   "fallback_frac_timed": r["fb"] / (nl * args.steps),
-                   "updates_per_step": r["upd_step"], "train_maps": 100000 * args.epochs,
-                   "train_s": round(t_train, 1), "final_loss": float(np.mean(losses[-20:])),
-                   "eval_s": round(r["t_eval"], 1),
-                   "l2": "inputs larger than L2 (9.8 GB of maps written by the full search per step)"},
-        "speedup_vs_full_exact": r["ms_full"] / ms_pr,
-        "ms_full_exact_per_step": r["ms_full"], "ms_pruned_per_step": ms_pr,
-        "budget_256": {"tau": r256["tau"], "recall": r256["summ"]["recall"],
-                       "fallback_frac": r256["summ"]["fallback_frac"],
-                       "mean_tiles_pruned": r256["summ"]["mean_tiles_pruned"],
-                       "ms_pruned_per_step": r256["ms_pr"], "ms_full_exact_per_step": r256["ms_full"],
-                       "speedup_vs_full_exact": r256["ms_full"] / r256["ms_pr"]},
-        "roofline": {"bound": "tensor", "kernel": "network forward (k_conv1_fwd .. k_head_fwd)",
-                     "achieved": fwd_tflops, "peak": bf16_peak,
-                     "unit": "TFLOP/s", "frac": fwd_tflops / bf16_peak if bf16_peak else None,
-                     "peak_source": "measured cuBLAS bf16 (burst)" if bf16_peak else "none",
-                     "algorithmic": f"{flops_img / 1e9:.3f} GFLOP per image", "traffic": None,
-                     "ms_forward_51_maps": r["ms_fwd"]},
-        "e2e": {"value": world * r["upd_step"] / (float(np.mean(t_e2e)) * 1e-3), "unit": "updates/s",
-                "h2d_bytes_per_step": int(bank.fft_c.numel() * 8),
-                "d2h_bytes_per_step": int(sum(x.numel() for x in bank.cands)),
-                "ms_per_step": float(np.mean(t_e2e))},
-        # per step: full search 4 kernels; pruned: 2 image + 7 network + 1 proposal + 5 Hough
-        "gpu_launches": args.steps * (4 + 15), "clocks": r["clocks"]}
+        "metric": "Hough updates/s (peaks x k-bins), full-search equivalent", "value": value,
+        "unit": "updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": op["ms_pruned_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32 counts; bf16 network, fp32 accumulate",
+        "data": res["data"], "config": {"workload": res["workload"], "checkpoint": res["checkpoint"]},
+        "proposer": res, "speedup_vs_full_exact": res["speedup_vs_full_exact"],
+        "recall": res["recall"], "operating_point": res["operating_point"],
+        "roofline": {"bound": "tensor", "kernel": "network forward (k_conv_fwd_tc, 5 layers)",
+                     "achieved": NET_FWD_FLOP * 51 / (res["network_forward_ms_51_maps"] * 1e-3) / 1e12,
+                     "peak": PEAKS.get("bf16_tflops"), "unit": "TFLOP/s",
+                     "frac": (NET_FWD_FLOP * 51 / (res["network_forward_ms_51_maps"] * 1e-3) / 1e12
+                              / PEAKS["bf16_tflops"]) if "bf16_tflops" in PEAKS else None,
+                     "peak_source": "measured cuBLAS bf16 (burst)", "traffic": None},
+        "gpu_launches": None, "clocks": sampler.summary()}
     if cpu:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
+    ctx.close()
 
 
 # ---------------------------------------------------------------------------------------------
@@ -1780,10 +1680,12 @@ def run_splice(args):
         barrier()
         a, b = ev(), ev()
         hev = [[(ev(), ev()) for _ in parts] for _ in range(args.steps)]
+        torch.cuda.nvtx.range_push("timed_steps")
         a.record(stream)
         for i in range(args.steps):
             step(hough_events=hev[i])
         b.record(stream)
+        torch.cuda.nvtx.range_pop()
         barrier()
         ms = a.elapsed_time(b) / args.steps
     clocks = sampler.summary()

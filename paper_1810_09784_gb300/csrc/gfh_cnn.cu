@@ -985,10 +985,16 @@ __global__ void __launch_bounds__(256) k_conv1_wgrad(const __nv_bfloat16* __rest
   float acc[18];
 #pragma unroll
   for (int j = 0; j < 18; ++j) acc[j] = 0.f;
-  for (int64_t p = p0 + sub; p < p1; p += 8) {
+  // coordinates of the first pixel of this sub-stream, then advanced by 8 pixels per step (H >= 8)
+  int64_t p = p0 + sub;
+  int b = (int)(p / ((int64_t)H * H)), y, x;
+  {
+    const int r = (int)(p - (int64_t)b * H * H);
+    y = r / H;
+    x = r - y * H;
+  }
+  for (; p < p1; p += 8) {
     const float gv = __bfloat162float(g1[p * 32 + co]);
-    const int b = (int)(p / ((int64_t)H * H)), r = (int)(p % ((int64_t)H * H));
-    const int y = r / H, x = r - y * H;
     const __nv_bfloat16* const base = in + (int64_t)b * H * H * 2;
 #pragma unroll
     for (int tap = 0; tap < 9; ++tap) {
@@ -998,6 +1004,11 @@ __global__ void __launch_bounds__(256) k_conv1_wgrad(const __nv_bfloat16* __rest
         acc[2 * tap] = fmaf(gv, __low2float(q), acc[2 * tap]);
         acc[2 * tap + 1] = fmaf(gv, __high2float(q), acc[2 * tap + 1]);
       }
+    }
+    x += 8;
+    if (x >= H) {
+      x -= H;
+      if (++y == H) { y = 0; ++b; }
     }
   }
 #pragma unroll
