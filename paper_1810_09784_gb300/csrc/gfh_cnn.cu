@@ -738,7 +738,10 @@ __global__ void __launch_bounds__(256) k_conv_fwd_tc(const __nv_bfloat16* __rest
 // Core matrices: 8 pixels x 16 bytes, K-adjacent ones 128 bytes apart (the descriptor's leading
 // byte offset), M/N-adjacent ones one co / ci chunk apart (its stride byte offset).  Two buffers: tile i + 1 is staged while tile i's MMAs run.  The block's
 // sums go to part[chunk][co][tap][ci] (k_sum_chunks adds the chunks in order).
-constexpr int WT_ROWS = 2, WT_THREADS = 128, WT_CHUNKS = 96;
+// Pixel chunks (blocks per tap row) of the weight gradients: a fixed count, so the chunk sums run in
+// the same order on every device; the first layer's narrow accumulators (24 tensor-memory columns)
+// leave room for four times the blocks per SM.
+constexpr int WT_ROWS = 2, WT_THREADS = 128, WT_CHUNKS = 96, WT_CHUNKS1 = 384;
 
 // Row of an M = 64 accumulator held by tensor-memory lane `lane` (-1: no row): rows 16 q .. 16 q + 15
 // sit in lanes 32 q .. 32 q + 15, the first half of each warp's quarter of the lanes.
@@ -756,7 +759,7 @@ template <int CIN, int COUT, int S>
 __global__ void __launch_bounds__(WT_THREADS) k_conv_wgrad_tc(const __nv_bfloat16* __restrict__ G,
                                                             const __nv_bfloat16* __restrict__ in,
                                                             float* __restrict__ part, int B, int H,
-                                                            unsigned int* flag) {
+                                                            int chunks, unsigned int* flag) {
   constexpr int NP = WgradTc<CIN, S>::NP;
   constexpr int XB = WgradTc<CIN, S>::XB;
   constexpr int GB = WT_ROWS * (COUT / 8) * 64 * 16;                   // G bytes per buffer
@@ -770,7 +773,7 @@ __global__ void __launch_bounds__(WT_THREADS) k_conv_wgrad_tc(const __nv_bfloat1
   __shared__ uint32_t tslot;
   __shared__ int s_ok;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int chunk = blockIdx.x, dy = blockIdx.y;
+  const int chunk = blockIdx.x, dy = blockIdx.y;   // gridDim.x == chunks
   const int Ho = H / S;
   const int tiles_per_img = (Ho / WT_ROWS) * (Ho / 64);
   const int n_tiles = B * tiles_per_img;
@@ -833,7 +836,7 @@ __global__ void __launch_bounds__(WT_THREADS) k_conv_wgrad_tc(const __nv_bfloat1
   if (tid == 0) s_ok = 1;
   __syncthreads();
   const uint32_t tmem = tslot;
-  for (; q < n_tiles; q += WT_CHUNKS, ++i) {
+  for (; q < n_tiles; q += chunks, ++i) {
     const int buf = i & 1;
     if (tid == 0) {
       const uint32_t b32 = s32 + (uint32_t)(buf * BUF);
@@ -859,7 +862,7 @@ __global__ void __launch_bounds__(WT_THREADS) k_conv_wgrad_tc(const __nv_bfloat1
     }
     pending[buf] = true;
     // stage the next tile into the other buffer once the MMAs that read it (tile i - 1) are done
-    const int nq = q + WT_CHUNKS;
+    const int nq = q + chunks;
     const int nb = buf ^ 1;
     if (pending[nb]) {
       if (warp == 0) {
@@ -895,6 +898,7 @@ __global__ void __launch_bounds__(WT_THREADS) k_conv_wgrad_tc(const __nv_bfloat1
   // accumulators -> part[chunk][co][dy * 3 + dx][ci] (zeros for a block without tiles)
   const bool have = chunk < n_tiles && s_ok;
   float* const dst = part + (int64_t)chunk * COUT * 9 * CIN;
+  constexpr int JN = CIN < 16 ? CIN : 16;          // columns of one tap read per load
   for (int dx = 0; dx < 3; ++dx)
     for (int c0 = 0; c0 < CIN; c0 += 16) {
       uint32_t v[16];
@@ -903,7 +907,7 @@ __global__ void __launch_bounds__(WT_THREADS) k_conv_wgrad_tc(const __nv_bfloat1
       if (co >= 0 && co < COUT) {
         float* o = dst + ((int64_t)co * 9 + dy * 3 + dx) * CIN + c0;
 #pragma unroll
-        for (int j = 0; j < 16; ++j) o[j] = have ? __uint_as_float(v[j]) : 0.f;
+        for (int j = 0; j < JN; ++j) o[j] = have ? __uint_as_float(v[j]) : 0.f;
       }
     }
   tc_fence_before();
@@ -968,58 +972,24 @@ __global__ void k_mask_grad(const __nv_bfloat16* __restrict__ dout,
   if (i < n) g[i] = __bfloat162float(out[i]) > 0.f ? dout[i] : __float2bfloat16_rn(0.f);
 }
 
-// dW1[co][tap][ci] = sum_p G1[p][co] in[src(p, tap)][ci] over images of H x H pixels, G1 the
-// gradient in layer 1's pre-activation.  Block = one chunk of pixels; thread t owns output channel
-// t % 32 and every 8th pixel of the chunk (sub-stream t / 32), keeping its 18 (tap, ci) sums in
-// registers: per pixel one coalesced read of G1 and nine 4-byte input reads shared by the 32 lanes.
-// The block adds its 8 sub-streams in order into part[chunk][co][tap][ci] (k_sum_chunks follows).
-__global__ void __launch_bounds__(256) k_conv1_wgrad(const __nv_bfloat16* __restrict__ g1,
-                                                    const __nv_bfloat16* __restrict__ in,
-                                                    float* __restrict__ part, int B, int H,
-                                                    int pix_per_block) {
-  __shared__ float red[8][32 * 18];
-  const int co = threadIdx.x & 31, sub = threadIdx.x >> 5;
-  const int64_t M = (int64_t)B * H * H;
-  const int64_t p0 = (int64_t)blockIdx.x * pix_per_block;
-  const int64_t p1 = p0 + pix_per_block < M ? p0 + pix_per_block : M;
-  float acc[18];
-#pragma unroll
-  for (int j = 0; j < 18; ++j) acc[j] = 0.f;
-  // coordinates of the first pixel of this sub-stream, then advanced by 8 pixels per step (H >= 8)
-  int64_t p = p0 + sub;
-  int b = (int)(p / ((int64_t)H * H)), y, x;
-  {
-    const int r = (int)(p - (int64_t)b * H * H);
-    y = r / H;
-    x = r - y * H;
-  }
-  for (; p < p1; p += 8) {
-    const float gv = __bfloat162float(g1[p * 32 + co]);
-    const __nv_bfloat16* const base = in + (int64_t)b * H * H * 2;
-#pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-      const int yi = y + tap / 3 - 1, xi = x + tap % 3 - 1;
-      if (yi >= 0 && yi < H && xi >= 0 && xi < H) {
-        const __nv_bfloat162 q = *reinterpret_cast<const __nv_bfloat162*>(base + ((int64_t)yi * H + xi) * 2);
-        acc[2 * tap] = fmaf(gv, __low2float(q), acc[2 * tap]);
-        acc[2 * tap + 1] = fmaf(gv, __high2float(q), acc[2 * tap + 1]);
-      }
-    }
-    x += 8;
-    if (x >= H) {
-      x -= H;
-      if (++y == H) { y = 0; ++b; }
-    }
-  }
-#pragma unroll
-  for (int j = 0; j < 18; ++j) red[sub][co * 18 + j] = acc[j];
-  __syncthreads();
-  for (int e = threadIdx.x; e < 32 * 18; e += blockDim.x) {
-    float s = 0.f;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) s += red[q][e];
-    part[(int64_t)blockIdx.x * 576 + e] = s;
-  }
+// The first layer's weight gradient runs on the tcgen05 weight-gradient kernel with the image's two
+// channels zero-padded to eight (one 16-byte core-matrix row per pixel): out8[p][0..1] = img[p],
+// out8[p][2..7] = 0.
+__global__ void k_pad_channels(const uint32_t* __restrict__ img, int4* __restrict__ out8,
+                               int64_t n_pix) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n_pix) out8[p] = make_int4((int)img[p], 0, 0, 0);
+}
+
+// dst[co][tap][ci] += sum_{c < chunks} part[c][co][tap][ci8] for ci < 2 (the padded layout has 8
+// input channels), chunks in increasing order.
+__global__ void k_sum_chunks_l1(const float* __restrict__ part, int chunks, float* __restrict__ dst) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;   // (co, tap, ci) of 32 x 9 x 2
+  if (e >= 576) return;
+  const int ci = e & 1, ct = e >> 1;
+  float s = 0.f;
+  for (int c = 0; c < chunks; ++c) s += part[(int64_t)c * 32 * 9 * 8 + ct * 8 + ci];
+  dst[e] += s;
 }
 
 // ---- mean over t, head, loss --------------------------------------------------------------------
@@ -1213,23 +1183,12 @@ int conv_fwd(const __nv_bfloat16* in, const __nv_bfloat16* w, const float* bias,
   return GFH_OK;
 }
 
-// Pixel chunks of the first layer's weight gradient over M pixels: at most max_chunks chunks of a
-// multiple of 64 pixels each (a function of M only, so the reduction order is the same on every
-// run).
-constexpr int kMaxChunks1 = 1024;
-inline int wgrad_chunk_pixels(int64_t M, int max_chunks, int min_pixels) {
-  int64_t ppb = std::max<int64_t>(min_pixels, (M + max_chunks - 1) / max_chunks);
-  return (int)((ppb + 63) / 64 * 64);
-}
-
 // Scratch floats of one layer's weight and bias gradients over M output pixels.
 size_t layer_partial_floats(int l, int64_t M) {
-  size_t ch = WT_CHUNKS;                           // L2-L5: the tensor-core chunks
-  if (l == 0) {
-    const int64_t ppb = wgrad_chunk_pixels(M, kMaxChunks1, 2048);
-    ch = (size_t)((M + ppb - 1) / ppb);
-  }
-  return std::max((size_t)kBiasBlocks * 256, ch * kCout[l] * 9 * kCin[l]);
+  (void)M;
+  const size_t cin = l == 0 ? 8 : kCin[l];         // the first layer runs on 8 padded channels
+  const size_t ch = l == 0 ? WT_CHUNKS1 : WT_CHUNKS;
+  return std::max((size_t)kBiasBlocks * 256, ch * kCout[l] * 9 * cin);
 }
 
 // Scratch floats the weight and bias gradients of every layer of the network need at batch B.
@@ -1266,7 +1225,7 @@ int conv_wgrad_tc(const __nv_bfloat16* G, const __nv_bfloat16* in, float* dw, fl
   (void)NP;
   auto fn = k_conv_wgrad_tc<CIN, COUT, S>;
   GFH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * BUF));
-  fn<<<dim3(WT_CHUNKS, 3), WT_THREADS, 2 * BUF, st>>>(G, in, part, B, H, flag);
+  fn<<<dim3(WT_CHUNKS, 3), WT_THREADS, 2 * BUF, st>>>(G, in, part, B, H, WT_CHUNKS, flag);
   GFH_CUDA_TRY(cudaGetLastError());
   const int n = COUT * 9 * CIN;
   k_sum_chunks<<<(n + 255) / 256, 256, 0, st>>>(part, WT_CHUNKS, n, dw);
@@ -1275,15 +1234,21 @@ int conv_wgrad_tc(const __nv_bfloat16* G, const __nv_bfloat16* in, float* dw, fl
 }
 
 // First layer (2 input channels) weight and bias gradients, added into dw and db.
-// G1 is the gradient in layer 1's pre-activation (stored masked).
-int conv1_wgrad(const __nv_bfloat16* g1, const __nv_bfloat16* in, float* dw, float* db, int B,
-                int H, float* part, cudaStream_t st) {
+// First layer (2 input channels) weight and bias gradients, added into dw and db, from G1 (the
+// gradient in layer 1's pre-activation, stored masked); img8 holds B H H x 8 bf16 (the padded image).
+int conv1_wgrad(const __nv_bfloat16* g1, const __nv_bfloat16* in, __nv_bfloat16* img8, float* dw,
+                float* db, int B, int H, float* part, cudaStream_t st, unsigned int* flag) {
   const int64_t P1 = (int64_t)B * H * H;
-  const int ppb = wgrad_chunk_pixels(P1, kMaxChunks1, 256);
-  const int chunks = (int)((P1 + ppb - 1) / ppb);
-  k_conv1_wgrad<<<(unsigned)chunks, 256, 0, st>>>(g1, in, part, B, H, ppb);
+  k_pad_channels<<<(unsigned)((P1 + 255) / 256), 256, 0, st>>>((const uint32_t*)in, (int4*)img8, P1);
   GFH_CUDA_TRY(cudaGetLastError());
-  k_sum_chunks<<<(576 + 255) / 256, 256, 0, st>>>(part, chunks, 576, dw);
+  constexpr int GB = WT_ROWS * (32 / 8) * 64 * 16, GPAD = (64 - 32) / 8 * 64 * 16;
+  constexpr int BUF = ((GB + GPAD + WgradTc<8, 1>::XB) + 1023) / 1024 * 1024;
+  if (H % 64) return GFH_ERR_ARG;
+  auto fn = k_conv_wgrad_tc<8, 32, 1>;
+  GFH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * BUF));
+  fn<<<dim3(WT_CHUNKS1, 3), WT_THREADS, 2 * BUF, st>>>(g1, img8, part, B, H, WT_CHUNKS1, flag);
+  GFH_CUDA_TRY(cudaGetLastError());
+  k_sum_chunks_l1<<<(576 + 255) / 256, 256, 0, st>>>(part, WT_CHUNKS1, dw);
   GFH_CUDA_TRY(cudaGetLastError());
   return bias_grad(g1, nullptr, db, P1, 32, part, st);
 }
@@ -1304,6 +1269,7 @@ struct gfh_cnn {
   __nv_bfloat16* dact[6] = {};                                     // d a1 .. d a5 (index 1..5)
   float *pooled = nullptr, *logits = nullptr, *dlogits = nullptr, *loss = nullptr;
   float* part = nullptr;                                           // gradient partial sums
+  __nv_bfloat16* img8 = nullptr;                                   // input padded to 8 channels
 };
 
 namespace {
@@ -1376,7 +1342,7 @@ int backward(gfh_cnn* n, const __nv_bfloat16* img, const int32_t* labels, int B)
   if (!rc) rc = conv_wgrad_tc<32, 32, 2>(n->dact[2], n->act[1], n->gw + L.w[1], n->gw + L.b[1], B, 256, n->part, st, flag);
   if (!rc) rc = conv_fwd<32, 32, 1, 2>(n->dact[2], n->wb[1], nullptr, n->act[1], n->dact[1], B, 256, sms, st, flag);
   if (rc) return rc;
-  return conv1_wgrad(n->dact[1], img, n->gw + L.w[0], n->gw + L.b[0], B, kImg, n->part, st);
+  return conv1_wgrad(n->dact[1], img, n->img8, n->gw + L.w[0], n->gw + L.b[0], B, kImg, n->part, st, flag);
 }
 
 }  // namespace
@@ -1399,7 +1365,8 @@ extern "C" int gfh_cnn_create(gfh_ctx* ctx, int32_t max_batch, uint64_t seed, gf
   for (int l = 1; l < 6; ++l) { o_act[l] = take(act_elems(l, B) * 2); o_dact[l] = take(act_elems(l, B) * 2); }
   const size_t o_pool = take((size_t)B * 4096 * 4), o_log = take((size_t)B * kClasses * 4),
                o_dlog = take((size_t)B * kClasses * 4), o_loss = take((size_t)B * 4),
-               o_part = take(grad_partial_floats(B) * 4);
+               o_part = take(grad_partial_floats(B) * 4),
+               o_img8 = take((size_t)B * kImg * kImg * 16);
   if (cudaSetDevice(ctx->device) != cudaSuccess) { delete n; return GFH_ERR_CUDA; }
   if (cudaMalloc(&n->buf, off) != cudaSuccess) { delete n; return GFH_ERR_NOMEM; }
   char* base = (char*)n->buf;
@@ -1413,6 +1380,7 @@ extern "C" int gfh_cnn_create(gfh_ctx* ctx, int32_t max_batch, uint64_t seed, gf
   n->pooled = (float*)(base + o_pool); n->logits = (float*)(base + o_log);
   n->dlogits = (float*)(base + o_dlog); n->loss = (float*)(base + o_loss);
   n->part = (float*)(base + o_part);
+  n->img8 = (__nv_bfloat16*)(base + o_img8);
   float* h = new (std::nothrow) float[n->L.total];
   if (!h) { cudaFree(n->buf); delete n; return GFH_ERR_NOMEM; }
   init_params(h, n->L, seed);
@@ -1665,7 +1633,9 @@ extern "C" int gfh_conv3x3(gfh_ctx* ctx, int32_t mode, int32_t cin, int32_t cout
     if (l < 0) return GFH_ERR_ARG;
     const int64_t ho = h / stride;
     part_bytes = (layer_partial_floats(l, (int64_t)batch * ho * ho) * 4 + 255) / 256 * 256;
-    const int rc = ensure_scratch(ctx, part_bytes + (size_t)batch * ho * ho * cout * 2);
+    // then the masked gradient, and for the first layer the input padded to 8 channels
+    const int rc = ensure_scratch(ctx, part_bytes + (size_t)batch * ho * ho * cout * 2 +
+                                           (l == 0 ? (size_t)batch * h * h * 16 : 0));
     if (rc) return rc;
     part = (float*)ctx->pm_buf;
   }
@@ -1694,9 +1664,10 @@ extern "C" int gfh_conv3x3(gfh_ctx* ctx, int32_t mode, int32_t cin, int32_t cout
     if (mode == 2) {
       const int64_t n_el = (int64_t)batch * h * h * 32;
       __nv_bfloat16* g = (__nv_bfloat16*)((char*)ctx->pm_buf + part_bytes);
+      __nv_bfloat16* img8 = g + n_el;
       k_mask_grad<<<(unsigned)((n_el + 255) / 256), 256, 0, st>>>(dout, out, g, n_el);
       GFH_CUDA_TRY(cudaGetLastError());
-      return conv1_wgrad(g, in, (float*)d_res, d_db, batch, h, part, st);
+      return conv1_wgrad(g, in, img8, (float*)d_res, d_db, batch, h, part, st, ctx->d_flag);
     }
     return GFH_ERR_ARG;
   }
