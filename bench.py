@@ -85,6 +85,8 @@ def parse():
                     help="profiling aid: keep only this many sub-band maps, spread over the band")
     ap.add_argument("--only-n", type=float, default=None,
                     help="profiling aid: keep only the maps of this braking index")
+    ap.add_argument("--batch", type=int, default=256,
+                    help="train: images per AdamW step (smaller batches are a profiling aid)")
     return ap.parse_args()
 
 
@@ -1033,6 +1035,11 @@ _NET_MACS = [256 * 256 * 32 * 18, 128 * 128 * 32 * 288, 128 * 128 * 64 * 288, 64
              64 * 64 * 64 * 576]
 NET_FWD_FLOP = 2.0 * sum(_NET_MACS)
 NET_TRAIN_FLOP = 2.0 * (2 * sum(_NET_MACS) + sum(_NET_MACS[1:]))
+# kernels one AdamW step launches: forward 5 convolutions + pool + head + softmax/CE; backward the
+# head (weights, chunk sum, input), 5 bias gradients with their chunk sums, 4 input and 4 weight
+# gradients with their chunk sums, the first layer's padding, weight gradient and chunk sum;
+# optimiser, then 5 bf16 weight copies
+TRAIN_LAUNCHES = 8 + 3 + 10 + 4 + 8 + 3 + 1 + 5
 
 
 def run_train(args):
@@ -1048,7 +1055,7 @@ def run_train(args):
     stream = torch.cuda.Stream()
     ctx = gfh.Context(local, stream)
     spec = PR.ProposerSpec()
-    B = 256
+    B = args.batch
     with torch.cuda.stream(stream):
         cache = PR.ImageCache(ctx, spec, 0, 2 * B)
         net = gfh.Cnn(ctx, B, seed=1)
@@ -1082,16 +1089,16 @@ def run_train(args):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16 weights and activations, fp32 accumulate", "data": "synthetic (series peakmaps)",
-        "config": {"workload": "one AdamW step of the proposal network on 256 images of 256 x 256 "
+        "config": {"workload": f"one AdamW step of the proposal network on {B} images of 256 x 256 "
                                "x 2 (forward, weight and input gradients, optimiser)",
                    "batch": B, "gflop_per_image": NET_TRAIN_FLOP / 1e9},
         "roofline": {"bound": "tensor", "kernel": "whole training step", "achieved": tflops,
                      "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak if peak else None,
                      "peak_source": "measured cuBLAS bf16, sustained" if peak else "none",
                      "algorithmic": f"{NET_TRAIN_FLOP / 1e9:.2f} GFLOP per image", "traffic": None},
-        "forward": {"ms_256_images": fw, "tflops": fw_tflops,
+        "forward": {"ms_batch": fw, "tflops": fw_tflops,
                     "frac_of_burst_peak": fw_tflops / PEAKS["bf16_tflops"] if "bf16_tflops" in PEAKS else None},
-        "gpu_launches": None, "clocks": sampler.summary()}), flush=True)
+        "gpu_launches": TRAIN_LAUNCHES * args.steps, "clocks": sampler.summary()}), flush=True)
     ctx.close()
 
 
