@@ -619,8 +619,7 @@ int gfh_device_sms(gfh_ctx* ctx, int32_t* h_sms);
  *   d_n_peaks   device int64 that receives the total number of peaks, which may exceed cap; the
  *               outputs then hold the first cap peaks in (bin, FFT) order
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current and keeps it for later calls; make that first call before any stream
- * capture.  A cudaDeviceReset of that device invalidates the kept address (the library must then
+ * that device current and keeps it for later calls.  A cudaDeviceReset of that device invalidates the kept address (the library must then
  * be reloaded).  All calls share the one array, so calls that overlap on the GPU (concurrent
  * streams, or several host threads) race and must be serialised by the caller; every call
  * rewrites all the scratch it reads, so no state carries over between calls.
