@@ -104,6 +104,17 @@ __device__ __forceinline__ void peak_interval(int row0, const longlong2 bs, cons
 }
 
 
+// Whether the interval of a peak ([a, b1 + 1) on the tile's first row, shifted left by s >= 0 per
+// row: t_first >= 0 and dk > 0 make every S_i non-negative) meets columns c0 .. ub on any of the
+// R rows: its right edge is highest on the first row and its left edge lowest on the last.  A
+// tile's bin range holds every bin that some FFT can bring into the tile at some row, so on a tall
+// map many of the peaks read lie outside it on all R rows; they draw nothing and are skipped whole.
+template <int R>
+__device__ __forceinline__ bool meets_tile(int64_t a, int64_t b1, int64_t s, int c0, int ub) {
+  return (b1 >> GFH_FRAC_BITS) >= (int64_t)c0 &&
+         ((a - (int64_t)(R - 1) * s) >> GFH_FRAC_BITS) <= (int64_t)ub;
+}
+
 // Events of one peak on the R rows of a tile (layout described at k_hough below).  The interval
 // on row 0 is [a, b1 + 1) in 2^-32 columns and moves left by s per row.  G0 + m is column m of row
 // 0 in absolute column numbering (the tile's first column is c0); ub = min(last column of the
@@ -145,20 +156,22 @@ __device__ __forceinline__ void draw_peak(int* G0, int lds, int64_t a, int64_t b
     if (hi < c1m1) atomicAdd(G0 + hi + 1, -1);
   }
   // rows 1 .. R-1 (rows past the map's last k row are drawn too: they exist in shared memory
-  // and are never stored).  Columns entered: [n1, min(n2, o1 - 1)]; columns left:
-  // [max(o1, n2 + 1), o2].  A shift below one column per row enters and leaves at most one
-  // column per row: that case has no inner loops.
+  // and are never stored).  A shift below one column per row moves each edge by at most one
+  // column per row: the left edge enters column n1 when it moves, the right edge leaves column
+  // o2 when it moves.  Edges are followed unclamped and an event is drawn only inside the tile's
+  // columns: an event right of the map's last column (inside the last tile of a map) lands in a
+  // cell that is never stored and changes no stored cell, because sums run rightwards and down.
   if (s < kOne) {
+    o1 = lo;
+    o2 = hr;
 #pragma unroll
     for (int rr = 1; rr < R; ++rr) {
       a -= s;
       b1 -= s;
-      lo = (int)(a >> GFH_FRAC_BITS);
-      const int n1 = max(lo, c0), n2 = min((int)(b1 >> GFH_FRAC_BITS), ub);
+      const int n1 = (int)(a >> GFH_FRAC_BITS), n2 = (int)(b1 >> GFH_FRAC_BITS);
       int* const Gr = G0 + rr * lds;
-      const int f1 = max(o1, n2 + 1);
-      if ((n1 < o1) & (n1 <= n2)) atomicAdd(Gr + n1, 1);
-      if (f1 <= o2) atomicAdd(Gr + f1, -1);
+      if ((n1 < o1) & ((unsigned)(n1 - c0) <= (unsigned)(c1m1 - c0))) atomicAdd(Gr + n1, 1);
+      if ((n2 < o2) & ((unsigned)(o2 - c0) <= (unsigned)(c1m1 - c0))) atomicAdd(Gr + o2, -1);
       o1 = n1;
       o2 = n2;
     }
@@ -286,7 +299,7 @@ __device__ __forceinline__ void hough_tile(const MapDev* __restrict__ maps, cons
       longlong2 bs_nx = make_longlong2(0, 0), up_nx = make_longlong2(0, 0);
       const bool ok_nx = f_nx != 0xffffffffu &&
                          peak_rows(BS, UP, bin_lo, f_nx, j_nx, nfft, jmax, flag, bs_nx, up_nx);
-      if (ok_cu) {
+      if (ok_cu && meets_tile<R>(a_cu, b_cu, s_cu, c0, ub)) {
         if constexpr (XD) draw_peak_x<R>(G0, lds, a_cu, b_cu, s_cu, c0, c1m1, ub, carry_x);
         else draw_peak<R>(G0, lds, a_cu, b_cu, s_cu, c0, c1m1, ub, carry);
       }
