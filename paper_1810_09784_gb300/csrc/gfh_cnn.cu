@@ -18,7 +18,9 @@
 // every reduction runs in a fixed order, so a training step is deterministic.  AdamW updates fp32
 // master weights and refreshes the bf16 copies.  Activation gradients are stored masked by their
 // ReLU (the gradients in the pre-activations), so the gradient kernels stage them as they are.
+#include <cuda.h>
 #include <cuda_bf16.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
@@ -723,6 +725,239 @@ __global__ void __launch_bounds__(256) k_conv_fwd_tc(const __nv_bfloat16* __rest
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols));
 }
 
+// ---- L2-L5 forward and stride-1 input gradients, TMA-fed and pipelined -------------------------------
+// The same convolution as k_conv_fwd_tc's halo form (CIN % 8 == 0, MODE 0 or 1), one output row of
+// CW <= 128 columns per tile, with the roles of a block split so that copies, tensor-core work and
+// the accumulator read-back of different tiles overlap:
+//   warp 0      issues the tile's input copies with the tensor memory accelerator (TMA) into one of
+//               NS stage buffers: one box per (8-channel chunk, parity) of 3 input rows x NP
+//               entries x 16 bytes, zero-filled outside the image by the copy itself;
+//   warp 1      holds the tensor memory (two accumulators of COUT columns) and issues the tile's
+//               MMAs (tap by tap, K = 16 per MMA) once its stage is full; their completion frees the
+//               stage and marks the accumulator full;
+//   warps 2-9   read an accumulator back (warp w: lanes 32 (w % 4) .., half (w - 2) / 4 of the
+//               columns), add the bias and apply the ReLU (MODE 0) or the mask (MODE 1), store bf16,
+//               and release the accumulator.
+// Stages and accumulators are handed over through mbarriers (copy bytes, MMA commits, arrivals); every
+// wait is bounded and a wait that runs out raises the timeout flag and ends the block's loop.
+// Input views for the copies (NHWC bf16, fully packed): S = 1: (CIN, W, H, B); S = 2: (CIN, 2, W/2,
+// H, B), whose parity coordinate picks the even or odd input columns, so entry j of parity 0 is
+// column 2 (x0 + j) - 1 and of parity 1 column 2 (x0 + j), as in k_conv_fwd_tc.
+constexpr int kTmaThreads = 320, kTmaEpiWarps = 8, kTmaMaxStages = 4;
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, uint64_t* bar,
+                                            int c0, int c1, int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)),
+      "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map, uint64_t* bar,
+                                            int c0, int c1, int c2, int c3, int c4) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)),
+      "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar)) : "memory");
+}
+
+// Bytes of one TMA box in shared memory (3 rows x np entries x 16 bytes, 128-byte aligned).
+__host__ __device__ constexpr int tma_box_bytes(int np) { return (3 * np * 16 + 127) / 128 * 128; }
+
+template <int CIN, int COUT, int S, int MODE>
+__global__ void __launch_bounds__(kTmaThreads, 1) k_conv_tma(const __grid_constant__ CUtensorMap tmap,
+                                                             const __nv_bfloat16* __restrict__ w,
+                                                             const float* __restrict__ bias,
+                                                             const __nv_bfloat16* __restrict__ mask,
+                                                             __nv_bfloat16* __restrict__ out, int B,
+                                                             int H, int ns, unsigned int* flag) {
+  static_assert(CIN % 16 == 0 && (MODE == 0 || (MODE == 1 && S == 1)), "halo form, stride-1 gradients");
+  constexpr int KR = 9 * CIN, SPT = CIN / 16, QC = CIN / 8;
+  constexpr int B_SL = COUT / 8 * 256;
+  constexpr uint32_t IDESC = umma_idesc_bf16(128, COUT);
+  constexpr int TCOLS = 2 * COUT;                    // two accumulators
+  extern __shared__ __align__(1024) unsigned char smem_tc[];
+  __shared__ __align__(8) uint64_t full[kTmaMaxStages], empty[kTmaMaxStages], accf[2], acce[2];
+  __shared__ uint32_t tslot;
+  __shared__ float sbias[COUT];
+  __shared__ volatile int s_fail;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int Ho = H / S, CW = Ho > 128 ? 128 : Ho, NCB = Ho / CW, NP = CW + 2;
+  const int BOXB = tma_box_bytes(NP), STAGE = QC * S * BOXB;
+  const int n_tiles = B * Ho * NCB;
+  const uint32_t sb32 = smem_u32(smem_tc), sa32 = sb32 + (uint32_t)(KR / 16 * B_SL);
+  auto fail = [&]() {
+    s_fail = 1;
+    atomicOr(flag, GFH_FLAG_TIMEOUT);
+  };
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tslot)), "r"(TCOLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  // weights, K-major rows of the output channel (MODE 1: transposed, taps flipped)
+  if (MODE == 0) {
+    for (int e = tid; e < COUT * (KR / 8); e += blockDim.x) {
+      const int co = e / (KR / 8), k = (e % (KR / 8)) * 8;
+      *reinterpret_cast<int4*>(smem_tc + cm_off(co, k, COUT)) =
+          __ldg(reinterpret_cast<const int4*>(w + co * KR + k));
+    }
+  } else {
+    for (int e = tid; e < COUT * KR; e += blockDim.x) {
+      const int n = e / KR, k = e - n * KR, tap = k / CIN, o = k - tap * CIN;
+      *reinterpret_cast<__nv_bfloat16*>(smem_tc + cm_off(n, k, COUT)) = w[(o * 9 + 8 - tap) * COUT + n];
+    }
+  }
+  for (int c = tid; c < COUT; c += blockDim.x) sbias[c] = MODE == 0 ? bias[c] : 0.f;
+  if (tid == 0) {
+    for (int s = 0; s < ns; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+    for (int a = 0; a < 2; ++a) { mbar_init(&accf[a], 1); mbar_init(&acce[a], kTmaEpiWarps); }
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  async_proxy_fence();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tslot;
+  int issued = 0;                                    // stages (warp 0) or tiles (warp 1) issued
+
+  if (warp == 0) {
+    if (lane == 0) {
+      asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap)) : "memory");
+      for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const int slot = issued % ns, use = issued / ns;
+        if (use > 0 && !mbar_wait(&empty[slot], (uint32_t)(use - 1) & 1u)) { fail(); break; }
+        if (s_fail) break;
+        const int b = t / (Ho * NCB), rem = t - b * (Ho * NCB), y = rem / NCB;
+        const int x0 = (rem - y * NCB) * CW;
+        mbar_expect_tx(&full[slot], (uint32_t)(QC * S * 48 * NP));
+        const uint32_t dst = sa32 + (uint32_t)(slot * STAGE);
+#pragma unroll
+        for (int q = 0; q < QC; ++q) {
+          if constexpr (S == 1) {
+            tma_load_4d(dst + (uint32_t)(q * BOXB), &tmap, &full[slot], 8 * q, x0 - 1, y - 1, b);
+          } else {   // parity 0: odd columns 2 (x0 + j) - 1; parity 1: even columns 2 (x0 + j)
+            tma_load_5d(dst + (uint32_t)(2 * q * BOXB), &tmap, &full[slot], 8 * q, 1, x0 - 1,
+                        2 * y - 1, b);
+            tma_load_5d(dst + (uint32_t)((2 * q + 1) * BOXB), &tmap, &full[slot], 8 * q, 0, x0,
+                        2 * y - 1, b);
+          }
+        }
+        ++issued;
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      const uint64_t bd0 = umma_desc(sb32);
+      for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const int slot = issued % ns, acc = issued & 1;
+        if (issued >= 2 && !mbar_wait(&acce[acc], (uint32_t)((issued >> 1) - 1) & 1u)) { fail(); break; }
+        if (!mbar_wait(&full[slot], (uint32_t)(issued / ns) & 1u)) { fail(); break; }
+        if (s_fail) break;
+        tc_fence_after();
+        const uint32_t a0 = sa32 + (uint32_t)(slot * STAGE);
+#pragma unroll 1
+        for (int tap = 0; tap < 9; ++tap) {
+          const int dy = tap / 3, dx = tap % 3;
+          const int par = S == 1 ? 0 : (dx == 1 ? 1 : 0);
+          const int jo = S == 1 ? dx : (dx == 2 ? 1 : 0);
+#pragma unroll
+          for (int sp = 0; sp < SPT; ++sp) {
+            const uint32_t a_addr =
+                a0 + (uint32_t)((2 * sp * S + par) * BOXB + dy * NP * 16 + jo * 16);
+            const int sl = tap * SPT + sp;
+            umma_bf16(tmem + (uint32_t)(acc * COUT), umma_desc(a_addr, (uint32_t)(S * BOXB), 128u),
+                      bd0 + (uint64_t)((sl * B_SL) >> 4), IDESC, sl > 0 ? 1u : 0u);
+          }
+        }
+        umma_commit(&empty[slot]);                   // the stage is free once these MMAs complete
+        umma_commit(&accf[acc]);
+        ++issued;
+      }
+    }
+  } else {
+    const int quarter = warp & 3, half = (warp - 2) >> 2;
+    const int p = quarter * 32 + lane;
+    const int cb = half * (COUT / 2);
+    int i = 0;
+    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++i) {
+      const int acc = i & 1;
+      const bool got = mbar_wait(&accf[acc], (uint32_t)(i >> 1) & 1u);
+      if (!__all_sync(0xffffffffu, got)) {
+        if (lane == 0) fail();
+        break;
+      }
+      if (__shfl_sync(0xffffffffu, s_fail, 0)) break;
+      tc_fence_after();
+      const int b = t / (Ho * NCB), rem = t - b * (Ho * NCB), y = rem / NCB;
+      const int x0 = (rem - y * NCB) * CW;
+      const int64_t m = ((int64_t)b * Ho + y) * Ho + x0 + p;
+      const bool valid = p < CW;
+      if (quarter * 32 < CW) {                       // warp-uniform: a row of the quarter is inside
+#pragma unroll
+        for (int c0 = cb; c0 < cb + COUT / 2; c0 += 16) {
+          uint32_t v[16];
+          tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * COUT + c0), v);
+          uint32_t pk[8];
+          if (MODE == 0) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              pk[j] = pack_bf16(fmaxf(__uint_as_float(v[2 * j]) + sbias[c0 + 2 * j], 0.f),
+                                fmaxf(__uint_as_float(v[2 * j + 1]) + sbias[c0 + 2 * j + 1], 0.f));
+          } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+              pk[j] = pack_bf16(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
+            if (mask && valid) {
+              const int4* mk = reinterpret_cast<const int4*>(mask + m * COUT + c0);
+              const int4 m0 = __ldg(mk), m1 = __ldg(mk + 1);
+              const uint32_t mw[8] = {(uint32_t)m0.x, (uint32_t)m0.y, (uint32_t)m0.z, (uint32_t)m0.w,
+                                      (uint32_t)m1.x, (uint32_t)m1.y, (uint32_t)m1.z, (uint32_t)m1.w};
+#pragma unroll
+              for (int j = 0; j < 8; ++j) pk[j] = relu_mask(pk[j], mw[j]);
+            }
+          }
+          if (valid) {
+            int4* o = reinterpret_cast<int4*>(out + m * COUT + c0);
+            o[0] = make_int4(pk[0], pk[1], pk[2], pk[3]);
+            o[1] = make_int4(pk[4], pk[5], pk[6], pk[7]);
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce[acc]);
+    }
+  }
+  __syncthreads();
+  if (s_fail) {
+    // a wait ran out: let the copies and MMAs already issued land (bounded) before the shared and
+    // tensor memory are given back
+    if (tid == 0) {
+      for (int s = 0; s < ns && s < issued; ++s) {
+        const int last = issued - 1 - ((issued - 1 - s) % ns);   // last stage issued into slot s
+        mbar_wait(&full[s], (uint32_t)(last / ns) & 1u);
+      }
+    }
+    if (tid == 32 && issued > 0) mbar_wait(&accf[(issued - 1) & 1], (uint32_t)((issued - 1) >> 1) & 1u);
+    __syncthreads();
+  }
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
+  }
+}
+
 // ---- L2-L5 weight gradient on tcgen05 -------------------------------------------------------------
 // dW[co][tap][ci] = sum_p G[p][co] X_tap[p][ci] with G the gradient in the layer's pre-activation
 // (stored masked, NHWC [p][co]) and X_tap[p] the input pixel that output pixel p reads through the
@@ -1147,40 +1382,115 @@ __global__ void k_to_bf16(const float* __restrict__ a, __nv_bfloat16* __restrict
 
 // ---- launch helpers -------------------------------------------------------------------------------
 
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess || q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  return fn;
+}
+
+// Launch of k_conv_tma (see there): the input view's tensor map, the stage count that fits in shared
+// memory next to the weights (4, 3 or 2), persistent blocks.
+template <int CIN, int COUT, int S, int MODE>
+int conv_tma(const __nv_bfloat16* in, const __nv_bfloat16* w, const float* bias,
+             const __nv_bfloat16* mask, __nv_bfloat16* out, int B, int H, int sms, cudaStream_t st,
+             unsigned int* flag) {
+  const int Ho = H / S, CW = Ho > 128 ? 128 : Ho, NP = CW + 2;
+  if (Ho < 1 || Ho * S != H || Ho % CW) return GFH_ERR_ARG;
+  const PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+  if (!encode) return GFH_ERR_CUDA;
+  alignas(64) CUtensorMap map;
+  const cuuint64_t e = 2;                            // bf16 bytes
+  CUresult r;
+  if (S == 1) {
+    const cuuint64_t dims[4] = {(cuuint64_t)CIN, (cuuint64_t)H, (cuuint64_t)H, (cuuint64_t)B};
+    const cuuint64_t strides[3] = {CIN * e, (cuuint64_t)H * CIN * e, (cuuint64_t)H * H * CIN * e};
+    const cuuint32_t box[4] = {8, (cuuint32_t)NP, 3, 1}, es[4] = {1, 1, 1, 1};
+    r = encode(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)in, dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  } else {
+    const cuuint64_t dims[5] = {(cuuint64_t)CIN, 2, (cuuint64_t)H / 2, (cuuint64_t)H, (cuuint64_t)B};
+    const cuuint64_t strides[4] = {CIN * e, 2 * CIN * e, (cuuint64_t)H * CIN * e,
+                                   (cuuint64_t)H * H * CIN * e};
+    const cuuint32_t box[5] = {8, 1, (cuuint32_t)NP, 3, 1}, es[5] = {1, 1, 1, 1, 1};
+    r = encode(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void*)in, dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  }
+  if (r != CUDA_SUCCESS) return GFH_ERR_CUDA;
+  auto fn = k_conv_tma<CIN, COUT, S, MODE>;
+  cudaFuncAttributes fa{};
+  GFH_CUDA_TRY(cudaFuncGetAttributes(&fa, fn));
+  // weights, stages, and the over-read of the dropped MMA rows past the last stage
+  const size_t w_bytes = (size_t)(9 * CIN / 16) * (COUT / 8 * 256);
+  const size_t stage = (size_t)(CIN / 8) * S * tma_box_bytes(NP);
+  const size_t room = kMaxSmemBytes - fa.sharedSizeBytes - 1024;
+  int ns = kTmaMaxStages;
+  while (ns >= 2 && w_bytes + ns * stage + 128 * 16 > room) --ns;
+  if (ns < 2) return GFH_ERR_SIZE;
+  const size_t smem = w_bytes + ns * stage + 128 * 16;
+  GFH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  GFH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+  const int regs = std::max(1, (fa.numRegs + 7) / 8 * 8);
+  const int per_sm = std::max(1, std::min({(int)(kSmemPerSm / (smem + fa.sharedSizeBytes + 1024)),
+                                           65536 / (regs * kTmaThreads), 2048 / kTmaThreads,
+                                           512 / (2 * COUT)}));
+  const int64_t tiles = (int64_t)B * Ho * (Ho / CW);
+  const int grid = (int)std::min<int64_t>(tiles, (int64_t)sms * per_sm);
+  fn<<<grid, kTmaThreads, smem, st>>>(map, w, bias, mask, out, B, H, ns, flag);
+  GFH_CUDA_TRY(cudaGetLastError());
+  return GFH_OK;
+}
+
 template <int CIN, int COUT, int S, int MODE = 0>
 int conv_fwd(const __nv_bfloat16* in, const __nv_bfloat16* w, const float* bias,
              const __nv_bfloat16* mask, __nv_bfloat16* out, int B, int H, int sms, cudaStream_t st,
              unsigned int* flag) {
-  constexpr bool HALO = CIN % 8 == 0;
-  constexpr int K = (9 * CIN + 15) / 16 * 16;
-  const int Ho = H / S;
-  // tiles are output rows (two when they are at most 64 wide), cut into blocks of 128 columns
-  if (HALO && ((Ho > 128 && Ho % 128) || (Ho <= 64 && Ho % 2))) return GFH_ERR_ARG;
-  if (MODE == 2 && H % 2) return GFH_ERR_ARG;
-  const int RT = HALO && Ho <= 64 ? 2 : 1;
-  const int CW = Ho > 128 ? 128 : Ho;
-  // halo: rows x chunks x parities x (CW + 2) entries of 16 bytes, plus the dropped rows'
-  // over-read (at most 128 entries past a block start); im2col: K/16 slices of 128 x 16
-  const size_t a_bytes = HALO ? (size_t)((RT - 1) * S + 3) * (CIN / 8) * S * (CW + 2) * 16 + 128 * 16
-                              : (size_t)(K / 16) * (128 / 8 * 256);
-  const size_t smem = (size_t)(K / 16) * (COUT / 8 * 256) + a_bytes;
-  if (smem > kMaxSmemBytes - 4096) return GFH_ERR_SIZE;
-  const int tcols = RT * COUT < 32 ? 32 : RT * COUT;                   // power of two here
-  auto fn = k_conv_fwd_tc<CIN, COUT, S, MODE>;
-  GFH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  GFH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-  // resident blocks per SM: shared memory (with the static part and the per-block reservation),
-  // registers, 8 warps of 2048 threads, tensor-memory columns
-  cudaFuncAttributes fa{};
-  GFH_CUDA_TRY(cudaFuncGetAttributes(&fa, fn));
-  const int regs = std::max(1, (fa.numRegs + 7) / 8 * 8);
-  const int per_sm = std::max(1, std::min({(int)(kSmemPerSm / (smem + fa.sharedSizeBytes + 1024)),
-                                           65536 / (regs * 256), 8, 512 / tcols}));
-  const int64_t tiles = HALO ? (int64_t)B * (Ho / RT) * (Ho / CW) : ((int64_t)B * Ho * Ho + 127) / 128;
-  const int grid = (int)std::min<int64_t>(tiles, (int64_t)sms * per_sm);
-  fn<<<grid, 256, smem, st>>>(in, w, bias, mask, out, B, H, tcols, flag);
-  GFH_CUDA_TRY(cudaGetLastError());
-  return GFH_OK;
+  // the halo form's forward layers and stride-1 input gradients run on the TMA-fed pipeline
+  if constexpr (CIN % 16 == 0 && MODE != 2)
+    return conv_tma<CIN, COUT, S, MODE>(in, w, bias, mask, out, B, H, sms, st, flag);
+  else {
+    constexpr bool HALO = CIN % 8 == 0;
+    constexpr int K = (9 * CIN + 15) / 16 * 16;
+    const int Ho = H / S;
+    // tiles are output rows (two when they are at most 64 wide), cut into blocks of 128 columns
+    if (HALO && ((Ho > 128 && Ho % 128) || (Ho <= 64 && Ho % 2))) return GFH_ERR_ARG;
+    if (MODE == 2 && H % 2) return GFH_ERR_ARG;
+    const int RT = HALO && Ho <= 64 ? 2 : 1;
+    const int CW = Ho > 128 ? 128 : Ho;
+    // halo: rows x chunks x parities x (CW + 2) entries of 16 bytes, plus the dropped rows'
+    // over-read (at most 128 entries past a block start); im2col: K/16 slices of 128 x 16
+    const size_t a_bytes =
+        HALO ? (size_t)((RT - 1) * S + 3) * (CIN / 8) * S * (CW + 2) * 16 + 128 * 16
+             : (size_t)(K / 16) * (128 / 8 * 256);
+    const size_t smem = (size_t)(K / 16) * (COUT / 8 * 256) + a_bytes;
+    if (smem > kMaxSmemBytes - 4096) return GFH_ERR_SIZE;
+    const int tcols = RT * COUT < 32 ? 32 : RT * COUT;                   // power of two here
+    auto fn = k_conv_fwd_tc<CIN, COUT, S, MODE>;
+    GFH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GFH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    // resident blocks per SM: shared memory (with the static part and the per-block reservation),
+    // registers, 8 warps of 2048 threads, tensor-memory columns
+    cudaFuncAttributes fa{};
+    GFH_CUDA_TRY(cudaFuncGetAttributes(&fa, fn));
+    const int regs = std::max(1, (fa.numRegs + 7) / 8 * 8);
+    const int per_sm =
+        std::max(1, std::min({(int)(kSmemPerSm / (smem + fa.sharedSizeBytes + 1024)),
+                              65536 / (regs * 256), 8, 512 / tcols}));
+    const int64_t tiles =
+        HALO ? (int64_t)B * (Ho / RT) * (Ho / CW) : ((int64_t)B * Ho * Ho + 127) / 128;
+    const int grid = (int)std::min<int64_t>(tiles, (int64_t)sms * per_sm);
+    fn<<<grid, 256, smem, st>>>(in, w, bias, mask, out, B, H, tcols, flag);
+    GFH_CUDA_TRY(cudaGetLastError());
+    return GFH_OK;
+  }
 }
 
 // Scratch floats of one layer's weight and bias gradients over M output pixels.
