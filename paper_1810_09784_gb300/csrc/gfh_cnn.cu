@@ -442,6 +442,20 @@ __global__ void k_wait_unsignalled(long long budget, unsigned int* flag) {
   if (threadIdx.x == 0 && !mbar_wait(&mbar, 0, budget)) atomicOr(flag, GFH_FLAG_TIMEOUT);
 }
 
+// 16 consecutive 32-bit accumulator columns of the warp's 32 lanes into v[0..15]; the values are
+// valid after tmem_ld_wait.
+__device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, uint32_t* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_wait() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
@@ -725,25 +739,34 @@ __global__ void __launch_bounds__(256) k_conv_fwd_tc(const __nv_bfloat16* __rest
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols));
 }
 
-// ---- L2-L5 forward and stride-1 input gradients, TMA-fed and pipelined -------------------------------
-// The same convolution as k_conv_fwd_tc's halo form (CIN % 8 == 0, MODE 0 or 1), one output row of
-// CW <= 128 columns per tile, with the roles of a block split so that copies, tensor-core work and
-// the accumulator read-back of different tiles overlap:
+// ---- L2-L5 forward and input gradients, TMA-fed and pipelined --------------------------------------
+// The same convolutions as k_conv_fwd_tc's halo form (CIN % 16 == 0), one output row of CW <= 128
+// columns per tile, with the roles of a block split so that copies, tensor-core work and the
+// accumulator read-back of different tiles overlap:
 //   warp 0      issues the tile's input copies with the tensor memory accelerator (TMA) into one of
 //               NS stage buffers: one box per (8-channel chunk, parity) of 3 input rows x NP
 //               entries x 16 bytes, zero-filled outside the image by the copy itself;
-//   warp 1      holds the tensor memory (two accumulators of COUT columns) and issues the tile's
-//               MMAs (tap by tap, K = 16 per MMA) once its stage is full; their completion frees the
-//               stage and marks the accumulator full;
-//   warps 2-9   read an accumulator back (warp w: lanes 32 (w % 4) .., half (w - 2) / 4 of the
-//               columns), add the bias and apply the ReLU (MODE 0) or the mask (MODE 1), store bf16,
-//               and release the accumulator.
+//   warp 1      holds the tensor memory (four accumulators of COUT columns) and issues the tile's
+//               MMAs (tap by tap, K = 16 per MMA) once its stage is full and its accumulator free;
+//               their completion frees the stage and marks the accumulator full;
+//   warps 2-9   two groups of four that take alternate tiles: read the tile's accumulator back
+//               (warp w: lanes 32 (w % 4) .., all COUT columns, one wait for all the loads), add the
+//               bias and apply the ReLU (MODE 0) or the mask (MODE 1), store bf16, and release the
+//               accumulator.
 // Stages and accumulators are handed over through mbarriers (copy bytes, MMA commits, arrivals); every
 // wait is bounded and a wait that runs out raises the timeout flag and ends the block's loop.
 // Input views for the copies (NHWC bf16, fully packed): S = 1: (CIN, W, H, B); S = 2: (CIN, 2, W/2,
 // H, B), whose parity coordinate picks the even or odd input columns, so entry j of parity 0 is
 // column 2 (x0 + j) - 1 and of parity 1 column 2 (x0 + j), as in k_conv_fwd_tc.
-constexpr int kTmaThreads = 320, kTmaEpiWarps = 8, kTmaMaxStages = 4;
+// MODE 2, the input gradient of a stride-2 layer, is split by output parity instead of running on
+// inserted zeros: din[y][x] = sum over taps (dy, dx) with y + dy - 1 and x + dx - 1 even of
+// G[(y + dy - 1) / 2][(x + dx - 1) / 2] Wf[dy][dx] (Wf the flipped, transposed weights of MODE 1).
+// An even output row takes dy = 1 only (G row y / 2), an odd one dy = 0 and 2 (G rows (y - 1) / 2
+// and (y + 1) / 2); likewise for columns.  A tile is one output row y and one column parity px:
+// output columns 2 (x0 + p) + px, p < CW, from the G rows Y = y / 2 and Y + 1 (a box of 2 rows) and
+// G columns x0 - 1 + j (entry j); its 1, 2, 2 or 4 taps are the parity class's only MMAs, a quarter
+// of the multiply-adds of the zero-inserted form.
+constexpr int kTmaThreads = 320, kTmaGroupWarps = 4, kTmaAcc = 4, kTmaMaxStages = 4;
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
@@ -770,8 +793,18 @@ __device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map
       "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar)) : "memory");
 }
 
-// Bytes of one TMA box in shared memory (3 rows x np entries x 16 bytes, 128-byte aligned).
-__host__ __device__ constexpr int tma_box_bytes(int np) { return (3 * np * 16 + 127) / 128 * 128; }
+// Bytes of one TMA box in shared memory (rows x np entries x 16 bytes, 128-byte aligned).
+__host__ __device__ constexpr int tma_box_bytes(int np, int rows) {
+  return (rows * np * 16 + 127) / 128 * 128;
+}
+
+// Taps of the stride-2 input gradient's parity class c = 2 py + px (see k_conv_tma): tap index
+// 3 dy + dx, box row (0: G row y / 2, 1: the next) and entry offset jo; class c has 1, 2, 2, 4 taps.
+__device__ __constant__ const int8_t kParityTaps[4][4][3] = {
+    {{4, 0, 1}, {0, 0, 0}, {0, 0, 0}, {0, 0, 0}},
+    {{3, 0, 1}, {5, 0, 2}, {0, 0, 0}, {0, 0, 0}},
+    {{1, 0, 1}, {7, 1, 1}, {0, 0, 0}, {0, 0, 0}},
+    {{0, 0, 1}, {2, 0, 2}, {6, 1, 1}, {8, 1, 2}}};
 
 template <int CIN, int COUT, int S, int MODE>
 __global__ void __launch_bounds__(kTmaThreads, 1) k_conv_tma(const __grid_constant__ CUtensorMap tmap,
@@ -780,20 +813,33 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_conv_tma(const __grid_consta
                                                              const __nv_bfloat16* __restrict__ mask,
                                                              __nv_bfloat16* __restrict__ out, int B,
                                                              int H, int ns, unsigned int* flag) {
-  static_assert(CIN % 16 == 0 && (MODE == 0 || (MODE == 1 && S == 1)), "halo form, stride-1 gradients");
+  static_assert(CIN % 16 == 0 && (MODE == 0 || S == 1), "halo form; gradients on the G grid");
   constexpr int KR = 9 * CIN, SPT = CIN / 16, QC = CIN / 8;
   constexpr int B_SL = COUT / 8 * 256;
   constexpr uint32_t IDESC = umma_idesc_bf16(128, COUT);
-  constexpr int TCOLS = 2 * COUT;                    // two accumulators
+  constexpr int TCOLS = kTmaAcc * COUT;
   extern __shared__ __align__(1024) unsigned char smem_tc[];
-  __shared__ __align__(8) uint64_t full[kTmaMaxStages], empty[kTmaMaxStages], accf[2], acce[2];
+  __shared__ __align__(8) uint64_t full[kTmaMaxStages], empty[kTmaMaxStages], accf[kTmaAcc],
+      acce[kTmaAcc];
   __shared__ uint32_t tslot;
   __shared__ float sbias[COUT];
   __shared__ volatile int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int Ho = H / S, CW = Ho > 128 ? 128 : Ho, NCB = Ho / CW, NP = CW + 2;
-  const int BOXB = tma_box_bytes(NP), STAGE = QC * S * BOXB;
-  const int n_tiles = B * Ho * NCB;
+  // MODE 2: Ho = H output rows, each with two column parities of Hg = H / 2 columns
+  constexpr int ROWS = MODE == 2 ? 2 : 3, NPAR = MODE == 2 ? 2 : 1;
+  const int Ho = H / S, Wt = MODE == 2 ? H / 2 : Ho;   // output rows, columns per tile row
+  const int CW = Wt > 128 ? 128 : Wt, NCB = Wt / CW, NP = CW + 2;
+  const int BOXB = tma_box_bytes(NP, ROWS), STAGE = QC * S * BOXB;
+  const int n_tiles = B * Ho * NPAR * NCB;
+  // tile t: image b, output row y, column parity px (MODE 2), first column x0 of the block
+  auto geo = [&](int t, int& b, int& y, int& px, int& x0) {
+    b = t / (Ho * NPAR * NCB);
+    int r = t - b * (Ho * NPAR * NCB);
+    y = r / (NPAR * NCB);
+    r -= y * (NPAR * NCB);
+    px = r / NCB;
+    x0 = (r - px * NCB) * CW;
+  };
   const uint32_t sb32 = smem_u32(smem_tc), sa32 = sb32 + (uint32_t)(KR / 16 * B_SL);
   auto fail = [&]() {
     s_fail = 1;
@@ -820,7 +866,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_conv_tma(const __grid_consta
   for (int c = tid; c < COUT; c += blockDim.x) sbias[c] = MODE == 0 ? bias[c] : 0.f;
   if (tid == 0) {
     for (int s = 0; s < ns; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-    for (int a = 0; a < 2; ++a) { mbar_init(&accf[a], 1); mbar_init(&acce[a], kTmaEpiWarps); }
+    for (int a = 0; a < kTmaAcc; ++a) { mbar_init(&accf[a], 1); mbar_init(&acce[a], kTmaGroupWarps); }
     s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -838,13 +884,15 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_conv_tma(const __grid_consta
         const int slot = issued % ns, use = issued / ns;
         if (use > 0 && !mbar_wait(&empty[slot], (uint32_t)(use - 1) & 1u)) { fail(); break; }
         if (s_fail) break;
-        const int b = t / (Ho * NCB), rem = t - b * (Ho * NCB), y = rem / NCB;
-        const int x0 = (rem - y * NCB) * CW;
-        mbar_expect_tx(&full[slot], (uint32_t)(QC * S * 48 * NP));
+        int b, y, px, x0;
+        geo(t, b, y, px, x0);
+        mbar_expect_tx(&full[slot], (uint32_t)(QC * S * ROWS * 16 * NP));
         const uint32_t dst = sa32 + (uint32_t)(slot * STAGE);
 #pragma unroll
         for (int q = 0; q < QC; ++q) {
-          if constexpr (S == 1) {
+          if constexpr (MODE == 2) {
+            tma_load_4d(dst + (uint32_t)(q * BOXB), &tmap, &full[slot], 8 * q, x0 - 1, y >> 1, b);
+          } else if constexpr (S == 1) {
             tma_load_4d(dst + (uint32_t)(q * BOXB), &tmap, &full[slot], 8 * q, x0 - 1, y - 1, b);
           } else {   // parity 0: odd columns 2 (x0 + j) - 1; parity 1: even columns 2 (x0 + j)
             tma_load_5d(dst + (uint32_t)(2 * q * BOXB), &tmap, &full[slot], 8 * q, 1, x0 - 1,
@@ -860,25 +908,45 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_conv_tma(const __grid_consta
     if (lane == 0) {
       const uint64_t bd0 = umma_desc(sb32);
       for (int t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-        const int slot = issued % ns, acc = issued & 1;
-        if (issued >= 2 && !mbar_wait(&acce[acc], (uint32_t)((issued >> 1) - 1) & 1u)) { fail(); break; }
+        const int slot = issued % ns, acc = issued % kTmaAcc;
+        if (issued >= kTmaAcc &&
+            !mbar_wait(&acce[acc], (uint32_t)(issued / kTmaAcc - 1) & 1u)) { fail(); break; }
         if (!mbar_wait(&full[slot], (uint32_t)(issued / ns) & 1u)) { fail(); break; }
         if (s_fail) break;
         tc_fence_after();
-        const uint32_t a0 = sa32 + (uint32_t)(slot * STAGE);
-#pragma unroll 1
+        // descriptors: the stage's first entry plus the (chunk, parity, row, entry) offset of each
+        // tap and K slice, in 16-byte units (all offsets stay inside the 14-bit address field)
+        const uint64_t ad0 = umma_desc(sa32 + (uint32_t)(slot * STAGE), (uint32_t)(S * BOXB), 128u);
+        const uint32_t d_tmem = tmem + (uint32_t)(acc * COUT);
+        if constexpr (MODE == 2) {
+          int b, y, px, x0;
+          geo(t, b, y, px, x0);
+          const int cls = 2 * (y & 1) + px, nt = cls == 0 ? 1 : (cls == 3 ? 4 : 2);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            if (k < nt) {
+              const int tap = kParityTaps[cls][k][0], row = kParityTaps[cls][k][1];
+              const int jo = kParityTaps[cls][k][2];
+#pragma unroll
+              for (int sp = 0; sp < SPT; ++sp)
+                umma_bf16(d_tmem, ad0 + (uint64_t)((2 * sp * BOXB + (row * NP + jo) * 16) >> 4),
+                          bd0 + (uint64_t)(((tap * SPT + sp) * B_SL) >> 4), IDESC,
+                          (k > 0 || sp > 0) ? 1u : 0u);
+            }
+          }
+        } else {
+#pragma unroll
         for (int tap = 0; tap < 9; ++tap) {
           const int dy = tap / 3, dx = tap % 3;
           const int par = S == 1 ? 0 : (dx == 1 ? 1 : 0);
           const int jo = S == 1 ? dx : (dx == 2 ? 1 : 0);
 #pragma unroll
           for (int sp = 0; sp < SPT; ++sp) {
-            const uint32_t a_addr =
-                a0 + (uint32_t)((2 * sp * S + par) * BOXB + dy * NP * 16 + jo * 16);
             const int sl = tap * SPT + sp;
-            umma_bf16(tmem + (uint32_t)(acc * COUT), umma_desc(a_addr, (uint32_t)(S * BOXB), 128u),
+            umma_bf16(d_tmem, ad0 + (uint64_t)(((2 * sp * S + par) * BOXB + (dy * NP + jo) * 16) >> 4),
                       bd0 + (uint64_t)((sl * B_SL) >> 4), IDESC, sl > 0 ? 1u : 0u);
           }
+        }
         }
         umma_commit(&empty[slot]);                   // the stage is free once these MMAs complete
         umma_commit(&accf[acc]);
@@ -886,38 +954,39 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_conv_tma(const __grid_consta
       }
     }
   } else {
-    const int quarter = warp & 3, half = (warp - 2) >> 2;
+    const int quarter = warp & 3, grp = (warp - 2) >> 2;
     const int p = quarter * 32 + lane;
-    const int cb = half * (COUT / 2);
-    int i = 0;
-    for (int t = blockIdx.x; t < n_tiles; t += gridDim.x, ++i) {
-      const int acc = i & 1;
-      const bool got = mbar_wait(&accf[acc], (uint32_t)(i >> 1) & 1u);
+    for (int i = grp, t = blockIdx.x + grp * gridDim.x; t < n_tiles; i += 2, t += 2 * gridDim.x) {
+      const int acc = i % kTmaAcc;
+      const bool got = mbar_wait(&accf[acc], (uint32_t)(i / kTmaAcc) & 1u);
       if (!__all_sync(0xffffffffu, got)) {
         if (lane == 0) fail();
         break;
       }
       if (__shfl_sync(0xffffffffu, s_fail, 0)) break;
       tc_fence_after();
-      const int b = t / (Ho * NCB), rem = t - b * (Ho * NCB), y = rem / NCB;
-      const int x0 = (rem - y * NCB) * CW;
-      const int64_t m = ((int64_t)b * Ho + y) * Ho + x0 + p;
+      int b, y, px, x0;
+      geo(t, b, y, px, x0);
+      const int64_t m = ((int64_t)b * Ho + y) * Ho + (MODE == 2 ? 2 * (x0 + p) + px : x0 + p);
       const bool valid = p < CW;
       if (quarter * 32 < CW) {                       // warp-uniform: a row of the quarter is inside
+        uint32_t v[COUT];
+        const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * COUT);
 #pragma unroll
-        for (int c0 = cb; c0 < cb + COUT / 2; c0 += 16) {
-          uint32_t v[16];
-          tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * COUT + c0), v);
+        for (int c0 = 0; c0 < COUT; c0 += 16) tmem_ld16_issue(ta + (uint32_t)c0, v + c0);
+        tmem_ld_wait();
+#pragma unroll
+        for (int c0 = 0; c0 < COUT; c0 += 16) {
           uint32_t pk[8];
           if (MODE == 0) {
 #pragma unroll
             for (int j = 0; j < 8; ++j)
-              pk[j] = pack_bf16(fmaxf(__uint_as_float(v[2 * j]) + sbias[c0 + 2 * j], 0.f),
-                                fmaxf(__uint_as_float(v[2 * j + 1]) + sbias[c0 + 2 * j + 1], 0.f));
+              pk[j] = pack_bf16(fmaxf(__uint_as_float(v[c0 + 2 * j]) + sbias[c0 + 2 * j], 0.f),
+                                fmaxf(__uint_as_float(v[c0 + 2 * j + 1]) + sbias[c0 + 2 * j + 1], 0.f));
           } else {
 #pragma unroll
             for (int j = 0; j < 8; ++j)
-              pk[j] = pack_bf16(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
+              pk[j] = pack_bf16(__uint_as_float(v[c0 + 2 * j]), __uint_as_float(v[c0 + 2 * j + 1]));
             if (mask && valid) {
               const int4* mk = reinterpret_cast<const int4*>(mask + m * COUT + c0);
               const int4 m0 = __ldg(mk), m1 = __ldg(mk + 1);
@@ -949,7 +1018,8 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_conv_tma(const __grid_consta
         mbar_wait(&full[s], (uint32_t)(last / ns) & 1u);
       }
     }
-    if (tid == 32 && issued > 0) mbar_wait(&accf[(issued - 1) & 1], (uint32_t)((issued - 1) >> 1) & 1u);
+    if (tid == 32 && issued > 0)
+      mbar_wait(&accf[(issued - 1) % kTmaAcc], (uint32_t)((issued - 1) / kTmaAcc) & 1u);
     __syncthreads();
   }
   if (warp == 1) {
@@ -1401,14 +1471,25 @@ template <int CIN, int COUT, int S, int MODE>
 int conv_tma(const __nv_bfloat16* in, const __nv_bfloat16* w, const float* bias,
              const __nv_bfloat16* mask, __nv_bfloat16* out, int B, int H, int sms, cudaStream_t st,
              unsigned int* flag) {
-  const int Ho = H / S, CW = Ho > 128 ? 128 : Ho, NP = CW + 2;
-  if (Ho < 1 || Ho * S != H || Ho % CW) return GFH_ERR_ARG;
+  // MODE 2: G is H/2 x H/2, a tile row holds one column parity (H/2 columns)
+  constexpr int ROWS = MODE == 2 ? 2 : 3;
+  const int Ho = H / S, Wt = MODE == 2 ? H / 2 : Ho;
+  const int CW = Wt > 128 ? 128 : Wt, NP = CW + 2;
+  if (Wt < 1 || Ho * S != H || (MODE == 2 && H % 2) || Wt % CW) return GFH_ERR_ARG;
   const PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
   if (!encode) return GFH_ERR_CUDA;
   alignas(64) CUtensorMap map;
   const cuuint64_t e = 2;                            // bf16 bytes
   CUresult r;
-  if (S == 1) {
+  if (MODE == 2) {
+    const cuuint64_t hg = (cuuint64_t)H / 2;
+    const cuuint64_t dims[4] = {(cuuint64_t)CIN, hg, hg, (cuuint64_t)B};
+    const cuuint64_t strides[3] = {CIN * e, hg * CIN * e, hg * hg * CIN * e};
+    const cuuint32_t box[4] = {8, (cuuint32_t)NP, 2, 1}, es[4] = {1, 1, 1, 1};
+    r = encode(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)in, dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  } else if (S == 1) {
     const cuuint64_t dims[4] = {(cuuint64_t)CIN, (cuuint64_t)H, (cuuint64_t)H, (cuuint64_t)B};
     const cuuint64_t strides[3] = {CIN * e, (cuuint64_t)H * CIN * e, (cuuint64_t)H * H * CIN * e};
     const cuuint32_t box[4] = {8, (cuuint32_t)NP, 3, 1}, es[4] = {1, 1, 1, 1};
@@ -1430,7 +1511,7 @@ int conv_tma(const __nv_bfloat16* in, const __nv_bfloat16* w, const float* bias,
   GFH_CUDA_TRY(cudaFuncGetAttributes(&fa, fn));
   // weights, stages, and the over-read of the dropped MMA rows past the last stage
   const size_t w_bytes = (size_t)(9 * CIN / 16) * (COUT / 8 * 256);
-  const size_t stage = (size_t)(CIN / 8) * S * tma_box_bytes(NP);
+  const size_t stage = (size_t)(CIN / 8) * S * tma_box_bytes(NP, ROWS);
   const size_t room = kMaxSmemBytes - fa.sharedSizeBytes - 1024;
   int ns = kTmaMaxStages;
   while (ns >= 2 && w_bytes + ns * stage + 128 * 16 > room) --ns;
@@ -1441,8 +1522,8 @@ int conv_tma(const __nv_bfloat16* in, const __nv_bfloat16* w, const float* bias,
   const int regs = std::max(1, (fa.numRegs + 7) / 8 * 8);
   const int per_sm = std::max(1, std::min({(int)(kSmemPerSm / (smem + fa.sharedSizeBytes + 1024)),
                                            65536 / (regs * kTmaThreads), 2048 / kTmaThreads,
-                                           512 / (2 * COUT)}));
-  const int64_t tiles = (int64_t)B * Ho * (Ho / CW);
+                                           512 / (kTmaAcc * COUT)}));
+  const int64_t tiles = (int64_t)B * Ho * (MODE == 2 ? 2 : 1) * (Wt / CW);
   const int grid = (int)std::min<int64_t>(tiles, (int64_t)sms * per_sm);
   fn<<<grid, kTmaThreads, smem, st>>>(map, w, bias, mask, out, B, H, ns, flag);
   GFH_CUDA_TRY(cudaGetLastError());
@@ -1453,8 +1534,8 @@ template <int CIN, int COUT, int S, int MODE = 0>
 int conv_fwd(const __nv_bfloat16* in, const __nv_bfloat16* w, const float* bias,
              const __nv_bfloat16* mask, __nv_bfloat16* out, int B, int H, int sms, cudaStream_t st,
              unsigned int* flag) {
-  // the halo form's forward layers and stride-1 input gradients run on the TMA-fed pipeline
-  if constexpr (CIN % 16 == 0 && MODE != 2)
+  // the halo form's forward layers and input gradients run on the TMA-fed pipeline
+  if constexpr (CIN % 16 == 0)
     return conv_tma<CIN, COUT, S, MODE>(in, w, bias, mask, out, B, H, sms, st, flag);
   else {
     constexpr bool HALO = CIN % 8 == 0;
