@@ -793,6 +793,41 @@ __device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map
       "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar)) : "memory");
 }
 
+// Tensor store of a shared-memory box to global memory (bulk group of the issuing thread).
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap* map, uint32_t src, int c0, int c1,
+                                             int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"(
+          reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(src)
+      : "memory");
+}
+__device__ __forceinline__ void tma_store_5d(const CUtensorMap* map, uint32_t src, int c0, int c1,
+                                             int c2, int c3, int c4) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4, %5}], [%6];" ::"l"(
+          reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(src)
+      : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void group_bar(int id) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kTmaGroupWarps * 32) : "memory");
+}
+// Barrier of an epilogue group that also returns whether c held on any of its threads.
+__device__ __forceinline__ bool group_any(int id, bool c) {
+  uint32_t r;
+  asm volatile(
+      "{\n.reg .pred p, q;\nsetp.ne.u32 q, %1, 0;\nbar.red.or.pred p, %2, %3, q;\n"
+      "selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)c), "r"(id), "r"(kTmaGroupWarps * 32)
+      : "memory");
+  return r != 0;
+}
+
 // Bytes of one TMA box in shared memory (rows x np entries x 16 bytes, 128-byte aligned).
 __host__ __device__ constexpr int tma_box_bytes(int np, int rows) {
   return (rows * np * 16 + 127) / 128 * 128;
@@ -808,6 +843,7 @@ __device__ __constant__ const int8_t kParityTaps[4][4][3] = {
 
 template <int CIN, int COUT, int S, int MODE>
 __global__ void __launch_bounds__(kTmaThreads, 1) k_conv_tma(const __grid_constant__ CUtensorMap tmap,
+                                                             const __grid_constant__ CUtensorMap omap,
                                                              const __nv_bfloat16* __restrict__ w,
                                                              const float* __restrict__ bias,
                                                              const __nv_bfloat16* __restrict__ mask,
@@ -841,6 +877,11 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_conv_tma(const __grid_consta
     x0 = (r - px * NCB) * CW;
   };
   const uint32_t sb32 = smem_u32(smem_tc), sa32 = sb32 + (uint32_t)(KR / 16 * B_SL);
+  // output staging of the two epilogue groups, after the stages and the MMA over-read pad, aligned
+  // to the 1024-byte swizzle atom: 128 rows (pixels) of COUT bf16, 16-byte chunks swizzled as the
+  // output tensor map's 128-byte (COUT = 64) or 64-byte (COUT = 32) mode expects
+  constexpr int RB = COUT * 2;
+  const uint32_t ob32 = (sa32 + (uint32_t)(ns * STAGE + 128 * 16) + 1023u) & ~1023u;
   auto fail = [&]() {
     s_fail = 1;
     atomicOr(flag, GFH_FLAG_TIMEOUT);
@@ -956,57 +997,70 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_conv_tma(const __grid_consta
   } else {
     const int quarter = warp & 3, grp = (warp - 2) >> 2;
     const int p = quarter * 32 + lane;
+    const bool leader = warp == 2 + 4 * grp && lane == 0;   // issues the group's output stores
+    const uint32_t obuf = ob32 + (uint32_t)(grp * 128 * RB);
+    const int swz = COUT == 64 ? (p & 7) : ((p >> 1) & 3);
     for (int i = grp, t = blockIdx.x + grp * gridDim.x; t < n_tiles; i += 2, t += 2 * gridDim.x) {
       const int acc = i % kTmaAcc;
       const bool got = mbar_wait(&accf[acc], (uint32_t)(i / kTmaAcc) & 1u);
-      if (!__all_sync(0xffffffffu, got)) {
-        if (lane == 0) fail();
-        break;
-      }
-      if (__shfl_sync(0xffffffffu, s_fail, 0)) break;
+      if (!got) fail();
+      // the whole group leaves together (it shares barriers), on its own timeout or another's
+      if (group_any(1 + grp, !got || s_fail != 0)) break;
       tc_fence_after();
       int b, y, px, x0;
       geo(t, b, y, px, x0);
       const int64_t m = ((int64_t)b * Ho + y) * Ho + (MODE == 2 ? 2 * (x0 + p) + px : x0 + p);
       const bool valid = p < CW;
-      if (quarter * 32 < CW) {                       // warp-uniform: a row of the quarter is inside
-        uint32_t v[COUT];
+      uint32_t v[COUT];
+      const bool live = quarter * 32 < CW;           // warp-uniform: a row of the quarter is inside
+      if (live) {
         const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * COUT);
 #pragma unroll
         for (int c0 = 0; c0 < COUT; c0 += 16) tmem_ld16_issue(ta + (uint32_t)c0, v + c0);
         tmem_ld_wait();
+      }
+      // the accumulator is in registers: hand it back before the output work
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce[acc]);
+      // the staging buffer is free once the group's previous store has read it
+      if (leader) bulk_wait_read0();
+      group_bar(1 + grp);
+      if (live && valid) {
 #pragma unroll
-        for (int c0 = 0; c0 < COUT; c0 += 16) {
-          uint32_t pk[8];
+        for (int c0 = 0; c0 < COUT; c0 += 8) {       // one 16-byte chunk: 8 channels
+          uint32_t pk[4];
           if (MODE == 0) {
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
+            for (int j = 0; j < 4; ++j)
               pk[j] = pack_bf16(fmaxf(__uint_as_float(v[c0 + 2 * j]) + sbias[c0 + 2 * j], 0.f),
                                 fmaxf(__uint_as_float(v[c0 + 2 * j + 1]) + sbias[c0 + 2 * j + 1], 0.f));
           } else {
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
+            for (int j = 0; j < 4; ++j)
               pk[j] = pack_bf16(__uint_as_float(v[c0 + 2 * j]), __uint_as_float(v[c0 + 2 * j + 1]));
-            if (mask && valid) {
-              const int4* mk = reinterpret_cast<const int4*>(mask + m * COUT + c0);
-              const int4 m0 = __ldg(mk), m1 = __ldg(mk + 1);
-              const uint32_t mw[8] = {(uint32_t)m0.x, (uint32_t)m0.y, (uint32_t)m0.z, (uint32_t)m0.w,
-                                      (uint32_t)m1.x, (uint32_t)m1.y, (uint32_t)m1.z, (uint32_t)m1.w};
-#pragma unroll
-              for (int j = 0; j < 8; ++j) pk[j] = relu_mask(pk[j], mw[j]);
+            if (mask) {
+              const int4 mw = __ldg(reinterpret_cast<const int4*>(mask + m * COUT + c0));
+              pk[0] = relu_mask(pk[0], (uint32_t)mw.x);
+              pk[1] = relu_mask(pk[1], (uint32_t)mw.y);
+              pk[2] = relu_mask(pk[2], (uint32_t)mw.z);
+              pk[3] = relu_mask(pk[3], (uint32_t)mw.w);
             }
           }
-          if (valid) {
-            int4* o = reinterpret_cast<int4*>(out + m * COUT + c0);
-            o[0] = make_int4(pk[0], pk[1], pk[2], pk[3]);
-            o[1] = make_int4(pk[4], pk[5], pk[6], pk[7]);
-          }
+          const uint32_t dst = obuf + (uint32_t)(p * RB + (((c0 >> 3) ^ swz) << 4));
+          asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(pk[0]), "r"(pk[1]),
+                       "r"(pk[2]), "r"(pk[3]) : "memory");
         }
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&acce[acc]);
+      async_proxy_fence();
+      group_bar(1 + grp);
+      if (leader) {
+        if constexpr (MODE == 2) tma_store_5d(&omap, obuf, 0, px, x0, y, b);
+        else tma_store_4d(&omap, obuf, 0, x0, y, b);
+        bulk_commit();
+      }
     }
+    if (leader) bulk_wait0();                        // the group's stores are complete
   }
   __syncthreads();
   if (s_fail) {
@@ -1506,17 +1560,41 @@ int conv_tma(const __nv_bfloat16* in, const __nv_bfloat16* w, const float* bias,
                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   }
   if (r != CUDA_SUCCESS) return GFH_ERR_CUDA;
+  // output view for the tensor stores: NHWC (COUT, Ho, Ho, B), boxes of CW pixels of one row; mode 2
+  // (COUT, 2, H/2, H, B), the parity coordinate picking even or odd output columns
+  alignas(64) CUtensorMap omap;
+  const CUtensorMapSwizzle oswz = COUT == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+  static_assert(COUT == 32 || COUT == 64, "output rows of 64 or 128 bytes");
+  if (MODE == 2) {
+    const cuuint64_t dims[5] = {(cuuint64_t)COUT, 2, (cuuint64_t)H / 2, (cuuint64_t)H, (cuuint64_t)B};
+    const cuuint64_t strides[4] = {COUT * e, 2 * COUT * e, (cuuint64_t)H * COUT * e,
+                                   (cuuint64_t)H * H * COUT * e};
+    const cuuint32_t box[5] = {(cuuint32_t)COUT, 1, (cuuint32_t)CW, 1, 1}, es[5] = {1, 1, 1, 1, 1};
+    r = encode(&omap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void*)out, dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, oswz, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  } else {
+    const cuuint64_t dims[4] = {(cuuint64_t)COUT, (cuuint64_t)Ho, (cuuint64_t)Ho, (cuuint64_t)B};
+    const cuuint64_t strides[3] = {COUT * e, (cuuint64_t)Ho * COUT * e, (cuuint64_t)Ho * Ho * COUT * e};
+    const cuuint32_t box[4] = {(cuuint32_t)COUT, (cuuint32_t)CW, 1, 1}, es[4] = {1, 1, 1, 1};
+    r = encode(&omap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)out, dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, oswz, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  }
+  if (r != CUDA_SUCCESS) return GFH_ERR_CUDA;
   auto fn = k_conv_tma<CIN, COUT, S, MODE>;
   cudaFuncAttributes fa{};
   GFH_CUDA_TRY(cudaFuncGetAttributes(&fa, fn));
-  // weights, stages, and the over-read of the dropped MMA rows past the last stage
+  // weights, stages, the over-read of the dropped MMA rows past the last stage, then (aligned to
+  // 1024 bytes) the two epilogue groups' output staging of 128 rows x COUT bf16
   const size_t w_bytes = (size_t)(9 * CIN / 16) * (COUT / 8 * 256);
   const size_t stage = (size_t)(CIN / 8) * S * tma_box_bytes(NP, ROWS);
+  const size_t o_bytes = 2 * 128 * COUT * 2 + 1024;
   const size_t room = kMaxSmemBytes - fa.sharedSizeBytes - 1024;
   int ns = kTmaMaxStages;
-  while (ns >= 2 && w_bytes + ns * stage + 128 * 16 > room) --ns;
+  while (ns >= 2 && w_bytes + ns * stage + 128 * 16 + o_bytes > room) --ns;
   if (ns < 2) return GFH_ERR_SIZE;
-  const size_t smem = w_bytes + ns * stage + 128 * 16;
+  const size_t smem = w_bytes + ns * stage + 128 * 16 + o_bytes;
   GFH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   GFH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
   const int regs = std::max(1, (fa.numRegs + 7) / 8 * 8);
@@ -1525,7 +1603,7 @@ int conv_tma(const __nv_bfloat16* in, const __nv_bfloat16* w, const float* bias,
                                            512 / (kTmaAcc * COUT)}));
   const int64_t tiles = (int64_t)B * Ho * (MODE == 2 ? 2 : 1) * (Wt / CW);
   const int grid = (int)std::min<int64_t>(tiles, (int64_t)sms * per_sm);
-  fn<<<grid, kTmaThreads, smem, st>>>(map, w, bias, mask, out, B, H, ns, flag);
+  fn<<<grid, kTmaThreads, smem, st>>>(map, omap, w, bias, mask, out, B, H, ns, flag);
   GFH_CUDA_TRY(cudaGetLastError());
   return GFH_OK;
 }
