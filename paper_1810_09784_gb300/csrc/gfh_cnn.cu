@@ -1124,8 +1124,11 @@ __global__ void __launch_bounds__(WT_THREADS) k_conv_wgrad_tc(const __nv_bfloat1
   constexpr int GB = WT_ROWS * (COUT / 8) * 64 * 16;                   // G bytes per buffer
   constexpr int GPAD = (64 - COUT) / 8 * 64 * 16;                      // padding rows' reach
   constexpr int BUF = ((GB + GPAD + XB) + 1023) / 1024 * 1024;
+  // CIN = 8 (one 16-byte chunk per pixel): the three dx taps are one MMA of N = 24, whose
+  // N-adjacent core matrices are the same input pixels shifted by one entry (16 bytes)
+  constexpr int NMMA = CIN == 8 ? 3 * CIN : CIN;
   constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
-                             ((uint32_t)(CIN >> 3) << 17) | ((uint32_t)(64 >> 4) << 24);
+                             ((uint32_t)(NMMA >> 3) << 17) | ((uint32_t)(64 >> 4) << 24);
   constexpr uint32_t TCOLS = 3 * CIN <= 128 ? 128 : 256;
   extern __shared__ __align__(1024) unsigned char smem_w[];
   __shared__ __align__(8) uint64_t mbar[2];
@@ -1207,13 +1210,19 @@ __global__ void __launch_bounds__(WT_THREADS) k_conv_wgrad_tc(const __nv_bfloat1
           // MN-major operands: leading byte offset = K-direction core-matrix stride (8 pixels,
           // 128 bytes), stride byte offset = M/N-direction stride (one co / ci chunk)
           const uint64_t ad = umma_desc(a_addr, 128u, 64u * 16u);
+          if constexpr (CIN == 8) {
+            const uint32_t b_addr = b32 + (uint32_t)(GB + GPAD + (r * NP + ks * 16) * 16);
+            umma_bf16(tmem, ad, umma_desc(b_addr, 128u, 16u), IDESC, any ? 1u : 0u);
+          } else {
 #pragma unroll
-          for (int dx = 0; dx < 3; ++dx) {
-            const int par = S == 1 ? 0 : (dx == 1 ? 1 : 0);
-            const int jo = S == 1 ? dx : (dx == 2 ? 1 : 0);
-            const uint32_t b_addr = b32 + (uint32_t)(GB + GPAD + ((r * (CIN / 8) * S + par) * NP + ks * 16 + jo) * 16);
-            const uint64_t bd = umma_desc(b_addr, 128u, (uint32_t)(S * NP * 16));
-            umma_bf16(tmem + (uint32_t)(dx * CIN), ad, bd, IDESC, any ? 1u : 0u);
+            for (int dx = 0; dx < 3; ++dx) {
+              const int par = S == 1 ? 0 : (dx == 1 ? 1 : 0);
+              const int jo = S == 1 ? dx : (dx == 2 ? 1 : 0);
+              const uint32_t b_addr =
+                  b32 + (uint32_t)(GB + GPAD + ((r * (CIN / 8) * S + par) * NP + ks * 16 + jo) * 16);
+              const uint64_t bd = umma_desc(b_addr, 128u, (uint32_t)(S * NP * 16));
+              umma_bf16(tmem + (uint32_t)(dx * CIN), ad, bd, IDESC, any ? 1u : 0u);
+            }
           }
           any = true;
         }
