@@ -1082,25 +1082,29 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_conv_tma(const __grid_consta
   }
 }
 
-// ---- L2-L5 weight gradient on tcgen05 -------------------------------------------------------------
+// ---- weight gradients on tcgen05, TMA-fed ----------------------------------------------------------
 // dW[co][tap][ci] = sum_p G[p][co] X_tap[p][ci] with G the gradient in the layer's pre-activation
 // (stored masked, NHWC [p][co]) and X_tap[p] the input pixel that output pixel p reads through the
-// tap (zero outside the image).  Per tap a GEMM with M = 64 (co; rows >= COUT are padding), N = CIN
-// (ci) and K = output pixels, both operands MN-major in shared memory, so both are staged by 16-byte
-// cp.async straight from the NHWC tensors: A = G (16 bytes = 8 co of one pixel), B = X (16 bytes =
-// 8 ci of one input pixel).  Block (chunk, dy) keeps the accumulators of the taps (dy, 0..2) in
-// tensor memory over its chunk's tiles; a tile is WT_ROWS output rows x 64 columns of one image,
-// its K-steps 16 output pixels of one row.  Shared layout per buffer: G at [row][co chunk][64 px]
-// and X at [row][ci chunk][parity][NP entries], 16 bytes per pixel, so a tap's B operand is the
-// same array started dx entries later (S = 1) or in the other parity (S = 2): entry j of parity 0
-// is input column x0 S - 1 + j (S = 1), 2 (x0 + j) - 1 (S = 2), of parity 1 column 2 (x0 + j).
+// tap (zero outside the image).  Per tap a GEMM with M = 64 (co; rows >= COUT are padding, their
+// accumulator rows never read), N = CIN (ci) and K = output pixels, both operands MN-major: a 16-byte
+// row of a core matrix is 8 co (A) or 8 ci (B) of one pixel, as the NHWC tensors hold them.
+// Block (chunk, dy) keeps the accumulators of the taps (dy, 0..2) in tensor memory over its chunk's
+// tiles; a tile is WT_ROWS output rows x 64 columns of one image, its K-steps 16 output pixels of one
+// row.  Warp 0 copies each tile with the tensor memory accelerator into one of WT_STAGES stages:
+//   G: one box per 8-co chunk c of WT_ROWS rows x 64 pixels  -> [c][row][64 px] x 16 bytes;
+//   X: one box per 8-ci chunk c (and column parity for S = 2) of the WT_ROWS input rows
+//      (y0 + r) S + dy - 1 x NP entries, zero-filled outside the image -> [c][par][row][NP] x 16
+//      bytes; entry j of parity 0 is input column x0 S - 1 + j (S = 1), 2 (x0 + j) - 1 (S = 2), of
+//      parity 1 column 2 (x0 + j).
+// Warp 1 issues the MMAs once a stage is full and frees it with their commit.  Tap dx's B operand is
+// the same array started dx entries later (S = 1) or in the other parity (S = 2); for CIN = 8 the
+// three taps are one MMA of N = 24 whose N-adjacent core matrices are one entry (16 bytes) apart.
 // Core matrices: 8 pixels x 16 bytes, K-adjacent ones 128 bytes apart (the descriptor's leading
-// byte offset), M/N-adjacent ones one co / ci chunk apart (its stride byte offset).  Two buffers: tile i + 1 is staged while tile i's MMAs run.  The block's
-// sums go to part[chunk][co][tap][ci] (k_sum_chunks adds the chunks in order).
-// Pixel chunks (blocks per tap row) of the weight gradients: a fixed count, so the chunk sums run in
-// the same order on every device; the first layer's narrow accumulators (24 tensor-memory columns)
-// leave room for four times the blocks per SM.
-constexpr int WT_ROWS = 2, WT_THREADS = 128, WT_CHUNKS = 96, WT_CHUNKS1 = 384;
+// byte offset), M/N-adjacent ones one chunk apart (its stride byte offset).  At the end the four
+// warps read the accumulators to part[chunk][co][tap][ci] (k_sum_chunks adds the chunks in order).
+// Pixel chunks (blocks per tap row) are a fixed count, so the chunk sums run in the same order on
+// every device; the first layer's narrow accumulators leave room for four times the blocks per SM.
+constexpr int WT_ROWS = 2, WT_THREADS = 128, WT_CHUNKS = 96, WT_CHUNKS1 = 384, WT_STAGES = 4;
 
 // Row of an M = 64 accumulator held by tensor-memory lane `lane` (-1: no row): rows 16 q .. 16 q + 15
 // sit in lanes 32 q .. 32 q + 15, the first half of each warp's quarter of the lanes.
@@ -1108,110 +1112,108 @@ __device__ __forceinline__ int wgrad_row_of_lane(int lane) {
   return (lane & 31) < 16 ? (lane >> 5) * 16 + (lane & 31) : -1;
 }
 
-template <int CIN, int S>
+template <int CIN, int COUT, int S>
 struct WgradTc {
-  static constexpr int NP = S == 1 ? 66 : 65;                         // entries per (row, chunk, parity)
-  static constexpr int XB = WT_ROWS * (CIN / 8) * S * NP * 16;         // X bytes per buffer
+  static constexpr int NP = S == 1 ? 66 : 65;                         // entries per (chunk, parity, row)
+  static constexpr int GBOX = WT_ROWS * 64 * 16;                      // one G box
+  static constexpr int XBOX = (WT_ROWS * NP * 16 + 127) / 128 * 128;  // one X box (128-aligned)
+  static constexpr int GB = (COUT / 8) * GBOX;
+  static constexpr int XB = (CIN / 8) * S * XBOX;
+  static constexpr int STAGE = (GB + XB + 127) / 128 * 128;
+  // A reads 8 co chunks (64 rows): the padding chunks past G reach into X or the next stage
+  static constexpr int PAD = (64 - COUT) / 8 * GBOX;
+  static constexpr int SMEM = WT_STAGES * STAGE + PAD;
 };
 
 template <int CIN, int COUT, int S>
-__global__ void __launch_bounds__(WT_THREADS) k_conv_wgrad_tc(const __nv_bfloat16* __restrict__ G,
-                                                            const __nv_bfloat16* __restrict__ in,
-                                                            float* __restrict__ part, int B, int H,
-                                                            int chunks, unsigned int* flag) {
-  constexpr int NP = WgradTc<CIN, S>::NP;
-  constexpr int XB = WgradTc<CIN, S>::XB;
-  constexpr int GB = WT_ROWS * (COUT / 8) * 64 * 16;                   // G bytes per buffer
-  constexpr int GPAD = (64 - COUT) / 8 * 64 * 16;                      // padding rows' reach
-  constexpr int BUF = ((GB + GPAD + XB) + 1023) / 1024 * 1024;
-  // CIN = 8 (one 16-byte chunk per pixel): the three dx taps are one MMA of N = 24, whose
-  // N-adjacent core matrices are the same input pixels shifted by one entry (16 bytes)
+__global__ void __launch_bounds__(WT_THREADS) k_wgrad_tma(const __grid_constant__ CUtensorMap gmap,
+                                                          const __grid_constant__ CUtensorMap xmap,
+                                                          float* __restrict__ part, int B, int H,
+                                                          int chunks, unsigned int* flag) {
+  using T = WgradTc<CIN, COUT, S>;
+  constexpr int NP = T::NP;
   constexpr int NMMA = CIN == 8 ? 3 * CIN : CIN;
   constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
                              ((uint32_t)(NMMA >> 3) << 17) | ((uint32_t)(64 >> 4) << 24);
   constexpr uint32_t TCOLS = 3 * CIN <= 128 ? 128 : 256;
   extern __shared__ __align__(1024) unsigned char smem_w[];
-  __shared__ __align__(8) uint64_t mbar[2];
+  __shared__ __align__(8) uint64_t full[WT_STAGES], empty[WT_STAGES], done;
   __shared__ uint32_t tslot;
-  __shared__ int s_ok;
+  __shared__ volatile int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int chunk = blockIdx.x, dy = blockIdx.y;   // gridDim.x == chunks
   const int Ho = H / S;
   const int tiles_per_img = (Ho / WT_ROWS) * (Ho / 64);
   const int n_tiles = B * tiles_per_img;
+  const uint32_t s32 = smem_u32(smem_w);
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&tslot)), "r"(TCOLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[0])), "r"(1));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[1])), "r"(1));
+    for (int s = 0; s < WT_STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+    mbar_init(&done, 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  const uint32_t s32 = smem_u32(smem_w);
-  // zero the padding rows' reach once (read as A rows >= COUT, never stored)
-  if (GPAD > 0)
-    for (int i = tid; i < GPAD / 16; i += WT_THREADS)
-      for (int b2 = 0; b2 < 2; ++b2)
-        *reinterpret_cast<int4*>(smem_w + b2 * BUF + GB + i * 16) = make_int4(0, 0, 0, 0);
-
-  auto stage = [&](int q, int buf) {
-    const int b = q / tiles_per_img, rem = q - b * tiles_per_img;
-    const int rg = rem / (Ho / 64), cb = rem - rg * (Ho / 64);
-    const int y0 = rg * WT_ROWS, x0 = cb * 64;
-    unsigned char* base = smem_w + buf * BUF;
-    const uint32_t b32 = s32 + (uint32_t)(buf * BUF);
-    (void)base;
-    // G: [row][co chunk][64 px]
-    for (int e = tid; e < WT_ROWS * (COUT / 8) * 64; e += WT_THREADS) {
-      const int px = e & 63, rc = e >> 6, c = rc % (COUT / 8), r = rc / (COUT / 8);
-      const __nv_bfloat16* src = G + (((int64_t)b * Ho + y0 + r) * Ho + x0 + px) * COUT + c * 8;
-      cp_async16(b32 + (uint32_t)(((r * (COUT / 8) + c) * 64 + px) * 16), src, 16u);
-    }
-    // X: [row][ci chunk][parity][NP], input row (y0 + r) S + dy - 1
-    for (int e = tid; e < WT_ROWS * (CIN / 8) * S * NP; e += WT_THREADS) {
-      const int j = e % NP;
-      int rest = e / NP;
-      const int par = rest % S;
-      rest /= S;
-      const int c = rest % (CIN / 8), r = rest / (CIN / 8);
-      const int yi = (y0 + r) * S + dy - 1;
-      const int xi = S == 1 ? x0 - 1 + j : (par == 0 ? 2 * (x0 + j) - 1 : 2 * (x0 + j));
-      const bool inside = yi >= 0 && yi < H && xi >= 0 && xi < H;
-      const __nv_bfloat16* src = inside ? in + (((int64_t)b * H + yi) * H + xi) * CIN + c * 8 : in;
-      cp_async16(b32 + (uint32_t)(GB + GPAD + (((r * (CIN / 8) + c) * S + par) * NP + j) * 16), src,
-                 inside ? 16u : 0u);
-    }
-  };
-
-  uint32_t ph[2] = {0u, 0u};
-  bool pending[2] = {false, false};
-  bool any = false;
-  int i = 0;
-  int q = chunk;
-  if (q < n_tiles) stage(q, 0);
-  cp_async_wait_all();
-  async_proxy_fence();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (tid == 0) s_ok = 1;
-  __syncthreads();
   const uint32_t tmem = tslot;
-  for (; q < n_tiles; q += chunks, ++i) {
-    const int buf = i & 1;
-    if (tid == 0) {
-      const uint32_t b32 = s32 + (uint32_t)(buf * BUF);
-#pragma unroll 1
+  int issued = 0;
+
+  if (warp == 0 && lane == 0) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&gmap)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&xmap)) : "memory");
+    for (int q = chunk; q < n_tiles; q += chunks) {
+      const int slot = issued % WT_STAGES, use = issued / WT_STAGES;
+      if (use > 0 && !mbar_wait(&empty[slot], (uint32_t)(use - 1) & 1u)) {
+        s_fail = 1;
+        atomicOr(flag, GFH_FLAG_TIMEOUT);
+        break;
+      }
+      const int b = q / tiles_per_img, rem = q - b * tiles_per_img;
+      const int rg = rem / (Ho / 64), cb = rem - rg * (Ho / 64);
+      const int y0 = rg * WT_ROWS, x0 = cb * 64;
+      const uint32_t st = s32 + (uint32_t)(slot * T::STAGE);
+      mbar_expect_tx(&full[slot], (uint32_t)(T::GB + (CIN / 8) * S * WT_ROWS * NP * 16));
+#pragma unroll
+      for (int c = 0; c < COUT / 8; ++c)
+        tma_load_4d(st + (uint32_t)(c * T::GBOX), &gmap, &full[slot], 8 * c, x0, y0, b);
+#pragma unroll
+      for (int c = 0; c < CIN / 8; ++c) {
+        const uint32_t xs = st + (uint32_t)(T::GB + c * S * T::XBOX);
+        if constexpr (S == 1) {
+          tma_load_4d(xs, &xmap, &full[slot], 8 * c, x0 - 1, y0 + dy - 1, b);
+        } else {   // rows 2 (y0 + r) + dy - 1 through the row traversal stride of 2
+          tma_load_5d(xs, &xmap, &full[slot], 8 * c, 1, x0 - 1, 2 * y0 + dy - 1, b);
+          tma_load_5d(xs + (uint32_t)T::XBOX, &xmap, &full[slot], 8 * c, 0, x0, 2 * y0 + dy - 1, b);
+        }
+      }
+      ++issued;
+    }
+  } else if (warp == 1 && lane == 0) {
+    bool any = false;
+    for (int q = chunk; q < n_tiles; q += chunks) {
+      const int slot = issued % WT_STAGES;
+      if (!mbar_wait(&full[slot], (uint32_t)(issued / WT_STAGES) & 1u)) {
+        s_fail = 1;
+        atomicOr(flag, GFH_FLAG_TIMEOUT);
+        break;
+      }
+      if (s_fail) break;
+      tc_fence_after();
+      const uint32_t st = s32 + (uint32_t)(slot * T::STAGE);
+#pragma unroll
       for (int r = 0; r < WT_ROWS; ++r)
-#pragma unroll 1
+#pragma unroll
         for (int ks = 0; ks < 4; ++ks) {
-          const uint32_t a_addr = b32 + (uint32_t)((r * (COUT / 8) * 64 + ks * 16) * 16);
-          // MN-major operands: leading byte offset = K-direction core-matrix stride (8 pixels,
-          // 128 bytes), stride byte offset = M/N-direction stride (one co / ci chunk)
-          const uint64_t ad = umma_desc(a_addr, 128u, 64u * 16u);
+          // A: [c][row][64 px]; B: [c][par][row][NP]
+          const uint64_t ad =
+              umma_desc(st + (uint32_t)((r * 64 + ks * 16) * 16), 128u, (uint32_t)T::GBOX);
           if constexpr (CIN == 8) {
-            const uint32_t b_addr = b32 + (uint32_t)(GB + GPAD + (r * NP + ks * 16) * 16);
+            const uint32_t b_addr = st + (uint32_t)(T::GB + (r * NP + ks * 16) * 16);
             umma_bf16(tmem, ad, umma_desc(b_addr, 128u, 16u), IDESC, any ? 1u : 0u);
           } else {
 #pragma unroll
@@ -1219,52 +1221,36 @@ __global__ void __launch_bounds__(WT_THREADS) k_conv_wgrad_tc(const __nv_bfloat1
               const int par = S == 1 ? 0 : (dx == 1 ? 1 : 0);
               const int jo = S == 1 ? dx : (dx == 2 ? 1 : 0);
               const uint32_t b_addr =
-                  b32 + (uint32_t)(GB + GPAD + ((r * (CIN / 8) * S + par) * NP + ks * 16 + jo) * 16);
-              const uint64_t bd = umma_desc(b_addr, 128u, (uint32_t)(S * NP * 16));
-              umma_bf16(tmem + (uint32_t)(dx * CIN), ad, bd, IDESC, any ? 1u : 0u);
+                  st + (uint32_t)(T::GB + par * T::XBOX + (r * NP + ks * 16 + jo) * 16);
+              umma_bf16(tmem + (uint32_t)(dx * CIN), ad,
+                        umma_desc(b_addr, 128u, (uint32_t)(S * T::XBOX)), IDESC, any ? 1u : 0u);
             }
           }
           any = true;
         }
-      umma_commit(&mbar[buf]);
+      umma_commit(&empty[slot]);
+      ++issued;
     }
-    pending[buf] = true;
-    // stage the next tile into the other buffer once the MMAs that read it (tile i - 1) are done
-    const int nq = q + chunks;
-    const int nb = buf ^ 1;
-    if (pending[nb]) {
-      if (warp == 0) {
-        const bool mine = mbar_wait(&mbar[nb], ph[nb]);
-        const bool all = __all_sync(0xffffffffu, mine) != 0;
-        if (lane == 0 && !all) { s_ok = 0; atomicOr(flag, GFH_FLAG_TIMEOUT); }
-      }
-      ph[nb] ^= 1u;
-      pending[nb] = false;
-      __syncthreads();
-      tc_fence_after();
-    }
-    if (!s_ok) break;
-    if (nq < n_tiles) stage(nq, nb);
-    cp_async_wait_all();
-    async_proxy_fence();
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
+    umma_commit(&done);                              // every MMA issued above has completed
   }
-  // the last tiles' MMAs
-  for (int bfr = 0; bfr < 2; ++bfr)
-    if (pending[bfr] && s_ok) {
-      if (warp == 0) {
-        const bool mine = mbar_wait(&mbar[bfr], ph[bfr]);
-        const bool all = __all_sync(0xffffffffu, mine) != 0;
-        if (lane == 0 && !all) { s_ok = 0; atomicOr(flag, GFH_FLAG_TIMEOUT); }
-      }
-      ph[bfr] ^= 1u;
-      __syncthreads();
-    }
-  tc_fence_after();
+  __syncthreads();
   // accumulators -> part[chunk][co][dy * 3 + dx][ci] (zeros for a block without tiles)
-  const bool have = chunk < n_tiles && s_ok;
+  bool ok = true;
+  if (warp == 0) {
+    const bool mine = mbar_wait(&done, 0u);
+    ok = __all_sync(0xffffffffu, mine) != 0;
+    if (lane == 0 && !ok) { s_fail = 1; atomicOr(flag, GFH_FLAG_TIMEOUT); }
+  }
+  __syncthreads();
+  if (s_fail && tid == 0) {
+    // let the copies already issued land (bounded) before the shared memory is given back
+    for (int s = 0; s < WT_STAGES && s < issued; ++s) {
+      const int last = issued - 1 - ((issued - 1 - s) % WT_STAGES);
+      mbar_wait(&full[s], (uint32_t)(last / WT_STAGES) & 1u);
+    }
+  }
+  tc_fence_after();
+  const bool have = chunk < n_tiles && !s_fail;
   float* const dst = part + (int64_t)chunk * COUT * 9 * CIN;
   constexpr int JN = CIN < 16 ? CIN : 16;          // columns of one tap read per load
   for (int dx = 0; dx < 3; ++dx)
@@ -1689,29 +1675,76 @@ int bias_grad(const __nv_bfloat16* dout, const __nv_bfloat16* out, float* db, in
   return GFH_OK;
 }
 
-// Weight gradient on tcgen05 (k_conv_wgrad_tc) added into dw and bias gradient into db, from the
+// Tensor maps of the weight-gradient kernel's operands: G (COUT, Ho, Ho, B) in boxes of 8 co x 64
+// pixels x WT_ROWS rows; X (CIN, H, H, B) in boxes of 8 ci x NP entries x WT_ROWS rows, or for S = 2
+// the column-parity view (CIN, 2, H/2, H, B) with rows traversed with a stride of 2.
+template <int CIN, int COUT, int S>
+int wgrad_maps(const __nv_bfloat16* G, const __nv_bfloat16* in, int B, int H, CUtensorMap* gmap,
+               CUtensorMap* xmap) {
+  const PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+  if (!encode) return GFH_ERR_CUDA;
+  const cuuint64_t e = 2, Ho = (cuuint64_t)(H / S);
+  constexpr int NP = WgradTc<CIN, COUT, S>::NP;
+  {
+    const cuuint64_t dims[4] = {(cuuint64_t)COUT, Ho, Ho, (cuuint64_t)B};
+    const cuuint64_t strides[3] = {COUT * e, Ho * COUT * e, Ho * Ho * COUT * e};
+    const cuuint32_t box[4] = {8, 64, WT_ROWS, 1}, es[4] = {1, 1, 1, 1};
+    if (encode(gmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)G, dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return GFH_ERR_CUDA;
+  }
+  const cuuint64_t h = (cuuint64_t)H;
+  CUresult r;
+  if (S == 1) {
+    const cuuint64_t dims[4] = {(cuuint64_t)CIN, h, h, (cuuint64_t)B};
+    const cuuint64_t strides[3] = {CIN * e, h * CIN * e, h * h * CIN * e};
+    const cuuint32_t box[4] = {8, (cuuint32_t)NP, WT_ROWS, 1}, es[4] = {1, 1, 1, 1};
+    r = encode(xmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)in, dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  } else {
+    const cuuint64_t dims[5] = {(cuuint64_t)CIN, 2, h / 2, h, (cuuint64_t)B};
+    const cuuint64_t strides[4] = {CIN * e, 2 * CIN * e, h * CIN * e, h * h * CIN * e};
+    const cuuint32_t box[5] = {8, 1, (cuuint32_t)NP, 2 * WT_ROWS, 1}, es[5] = {1, 1, 1, 2, 1};
+    r = encode(xmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void*)in, dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  }
+  return r == CUDA_SUCCESS ? GFH_OK : GFH_ERR_CUDA;
+}
+
+// Launch of k_wgrad_tma over `chunks` pixel chunks x 3 tap rows; partial sums to part.
+template <int CIN, int COUT, int S>
+int wgrad_launch(const __nv_bfloat16* G, const __nv_bfloat16* in, int B, int H, int chunks,
+                 float* part, cudaStream_t st, unsigned int* flag) {
+  if ((H / S) % 64 || H % S) return GFH_ERR_ARG;
+  alignas(64) CUtensorMap gmap, xmap;
+  const int rc = wgrad_maps<CIN, COUT, S>(G, in, B, H, &gmap, &xmap);
+  if (rc) return rc;
+  constexpr int smem = WgradTc<CIN, COUT, S>::SMEM;
+  static_assert(smem <= (int)kMaxSmemBytes - 1024, "weight-gradient stages fit in shared memory");
+  auto fn = k_wgrad_tma<CIN, COUT, S>;
+  GFH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  fn<<<dim3(chunks, 3), WT_THREADS, smem, st>>>(gmap, xmap, part, B, H, chunks, flag);
+  GFH_CUDA_TRY(cudaGetLastError());
+  return GFH_OK;
+}
+
+// Weight gradient on tcgen05 (k_wgrad_tma) added into dw and bias gradient into db, from the
 // gradient in the pre-activation G (masked); output rows and columns a multiple of 64.
 template <int CIN, int COUT, int S>
 int conv_wgrad_tc(const __nv_bfloat16* G, const __nv_bfloat16* in, float* dw, float* db, int B,
                   int H, float* part, cudaStream_t st, unsigned int* flag) {
-  const int Ho = H / S;
-  if (Ho % 64 || H % S) return GFH_ERR_ARG;
-  constexpr int NP = WgradTc<CIN, S>::NP;
-  constexpr int GB = WT_ROWS * (COUT / 8) * 64 * 16;
-  constexpr int GPAD = (64 - COUT) / 8 * 64 * 16;
-  constexpr int BUF = ((GB + GPAD + WgradTc<CIN, S>::XB) + 1023) / 1024 * 1024;
-  (void)NP;
-  auto fn = k_conv_wgrad_tc<CIN, COUT, S>;
-  GFH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * BUF));
-  fn<<<dim3(WT_CHUNKS, 3), WT_THREADS, 2 * BUF, st>>>(G, in, part, B, H, WT_CHUNKS, flag);
-  GFH_CUDA_TRY(cudaGetLastError());
+  const int rc = wgrad_launch<CIN, COUT, S>(G, in, B, H, WT_CHUNKS, part, st, flag);
+  if (rc) return rc;
   const int n = COUT * 9 * CIN;
   k_sum_chunks<<<(n + 255) / 256, 256, 0, st>>>(part, WT_CHUNKS, n, dw);
   GFH_CUDA_TRY(cudaGetLastError());
+  const int Ho = H / S;
   return bias_grad(G, nullptr, db, (int64_t)B * Ho * Ho, COUT, part, st);
 }
 
-// First layer (2 input channels) weight and bias gradients, added into dw and db.
 // First layer (2 input channels) weight and bias gradients, added into dw and db, from G1 (the
 // gradient in layer 1's pre-activation, stored masked); img8 holds B H H x 8 bf16 (the padded image).
 int conv1_wgrad(const __nv_bfloat16* g1, const __nv_bfloat16* in, __nv_bfloat16* img8, float* dw,
@@ -1719,13 +1752,8 @@ int conv1_wgrad(const __nv_bfloat16* g1, const __nv_bfloat16* in, __nv_bfloat16*
   const int64_t P1 = (int64_t)B * H * H;
   k_pad_channels<<<(unsigned)((P1 + 255) / 256), 256, 0, st>>>((const uint32_t*)in, (int4*)img8, P1);
   GFH_CUDA_TRY(cudaGetLastError());
-  constexpr int GB = WT_ROWS * (32 / 8) * 64 * 16, GPAD = (64 - 32) / 8 * 64 * 16;
-  constexpr int BUF = ((GB + GPAD + WgradTc<8, 1>::XB) + 1023) / 1024 * 1024;
-  if (H % 64) return GFH_ERR_ARG;
-  auto fn = k_conv_wgrad_tc<8, 32, 1>;
-  GFH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * BUF));
-  fn<<<dim3(WT_CHUNKS1, 3), WT_THREADS, 2 * BUF, st>>>(g1, img8, part, B, H, WT_CHUNKS1, flag);
-  GFH_CUDA_TRY(cudaGetLastError());
+  const int rc = wgrad_launch<8, 32, 1>(g1, img8, B, H, WT_CHUNKS1, part, st, flag);
+  if (rc) return rc;
   k_sum_chunks_l1<<<(576 + 255) / 256, 256, 0, st>>>(part, WT_CHUNKS1, dw);
   GFH_CUDA_TRY(cudaGetLastError());
   return bias_grad(g1, nullptr, db, P1, 32, part, st);
