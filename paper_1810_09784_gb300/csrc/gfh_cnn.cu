@@ -762,10 +762,11 @@ __global__ void __launch_bounds__(256) k_conv_fwd_tc(const __nv_bfloat16* __rest
 // inserted zeros: din[y][x] = sum over taps (dy, dx) with y + dy - 1 and x + dx - 1 even of
 // G[(y + dy - 1) / 2][(x + dx - 1) / 2] Wf[dy][dx] (Wf the flipped, transposed weights of MODE 1).
 // An even output row takes dy = 1 only (G row y / 2), an odd one dy = 0 and 2 (G rows (y - 1) / 2
-// and (y + 1) / 2); likewise for columns.  A tile is one output row y and one column parity px:
-// output columns 2 (x0 + p) + px, p < CW, from the G rows Y = y / 2 and Y + 1 (a box of 2 rows) and
-// G columns x0 - 1 + j (entry j); its 1, 2, 2 or 4 taps are the parity class's only MMAs, a quarter
-// of the multiply-adds of the zero-inserted form.
+// and (y + 1) / 2); likewise for columns.  A tile is one output row y and both column parities:
+// output columns 2 (x0 + p) + px, p < CW, px = 0, 1, from the G rows Y = y / 2 and Y + 1 (a box of 2
+// rows) and G columns x0 - 1 + j (entry j); each parity class's 1, 2, 2 or 4 taps are its only
+// MMAs (a quarter of the multiply-adds of the zero-inserted form), into one accumulator per column
+// parity, and the tile's 2 CW output pixels are one contiguous run of the row.
 constexpr int kTmaThreads = 320, kTmaGroupWarps = 4, kTmaAcc = 4, kTmaMaxStages = 4;
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
@@ -799,13 +800,6 @@ __device__ __forceinline__ void tma_store_4d(const CUtensorMap* map, uint32_t sr
   asm volatile(
       "cp.async.bulk.tensor.4d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4}], [%5];" ::"l"(
           reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(src)
-      : "memory");
-}
-__device__ __forceinline__ void tma_store_5d(const CUtensorMap* map, uint32_t src, int c0, int c1,
-                                             int c2, int c3, int c4) {
-  asm volatile(
-      "cp.async.bulk.tensor.5d.global.shared::cta.bulk_group [%0, {%1, %2, %3, %4, %5}], [%6];" ::"l"(
-          reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(src)
       : "memory");
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
@@ -853,7 +847,8 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_conv_tma(const __grid_consta
   constexpr int KR = 9 * CIN, SPT = CIN / 16, QC = CIN / 8;
   constexpr int B_SL = COUT / 8 * 256;
   constexpr uint32_t IDESC = umma_idesc_bf16(128, COUT);
-  constexpr int TCOLS = kTmaAcc * COUT;
+  constexpr int NPAR = MODE == 2 ? 2 : 1;          // column parities (accumulators) per tile
+  constexpr int TCOLS = kTmaAcc * NPAR * COUT;
   extern __shared__ __align__(1024) unsigned char smem_tc[];
   __shared__ __align__(8) uint64_t full[kTmaMaxStages], empty[kTmaMaxStages], accf[kTmaAcc],
       acce[kTmaAcc];
@@ -862,19 +857,17 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_conv_tma(const __grid_consta
   __shared__ volatile int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // MODE 2: Ho = H output rows, each with two column parities of Hg = H / 2 columns
-  constexpr int ROWS = MODE == 2 ? 2 : 3, NPAR = MODE == 2 ? 2 : 1;
+  constexpr int ROWS = MODE == 2 ? 2 : 3;
   const int Ho = H / S, Wt = MODE == 2 ? H / 2 : Ho;   // output rows, columns per tile row
   const int CW = Wt > 128 ? 128 : Wt, NCB = Wt / CW, NP = CW + 2;
   const int BOXB = tma_box_bytes(NP, ROWS), STAGE = QC * S * BOXB;
-  const int n_tiles = B * Ho * NPAR * NCB;
-  // tile t: image b, output row y, column parity px (MODE 2), first column x0 of the block
-  auto geo = [&](int t, int& b, int& y, int& px, int& x0) {
-    b = t / (Ho * NPAR * NCB);
-    int r = t - b * (Ho * NPAR * NCB);
-    y = r / (NPAR * NCB);
-    r -= y * (NPAR * NCB);
-    px = r / NCB;
-    x0 = (r - px * NCB) * CW;
+  const int n_tiles = B * Ho * NCB;
+  // tile t: image b, output row y, first column x0 of the block (of G columns in MODE 2)
+  auto geo = [&](int t, int& b, int& y, int& x0) {
+    b = t / (Ho * NCB);
+    const int r = t - b * (Ho * NCB);
+    y = r / NCB;
+    x0 = (r - y * NCB) * CW;
   };
   const uint32_t sb32 = smem_u32(smem_tc), sa32 = sb32 + (uint32_t)(KR / 16 * B_SL);
   // output staging of the two epilogue groups, after the stages and the MMA over-read pad, aligned
@@ -925,8 +918,8 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_conv_tma(const __grid_consta
         const int slot = issued % ns, use = issued / ns;
         if (use > 0 && !mbar_wait(&empty[slot], (uint32_t)(use - 1) & 1u)) { fail(); break; }
         if (s_fail) break;
-        int b, y, px, x0;
-        geo(t, b, y, px, x0);
+        int b, y, x0;
+        geo(t, b, y, x0);
         mbar_expect_tx(&full[slot], (uint32_t)(QC * S * ROWS * 16 * NP));
         const uint32_t dst = sa32 + (uint32_t)(slot * STAGE);
 #pragma unroll
@@ -958,21 +951,25 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_conv_tma(const __grid_consta
         // descriptors: the stage's first entry plus the (chunk, parity, row, entry) offset of each
         // tap and K slice, in 16-byte units (all offsets stay inside the 14-bit address field)
         const uint64_t ad0 = umma_desc(sa32 + (uint32_t)(slot * STAGE), (uint32_t)(S * BOXB), 128u);
-        const uint32_t d_tmem = tmem + (uint32_t)(acc * COUT);
+        const uint32_t d_tmem = tmem + (uint32_t)(acc * NPAR * COUT);
         if constexpr (MODE == 2) {
-          int b, y, px, x0;
-          geo(t, b, y, px, x0);
-          const int cls = 2 * (y & 1) + px, nt = cls == 0 ? 1 : (cls == 3 ? 4 : 2);
+          int b, y, x0;
+          geo(t, b, y, x0);
 #pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            if (k < nt) {
-              const int tap = kParityTaps[cls][k][0], row = kParityTaps[cls][k][1];
-              const int jo = kParityTaps[cls][k][2];
+          for (int px = 0; px < 2; ++px) {
+            const int cls = 2 * (y & 1) + px, nt = cls == 0 ? 1 : (cls == 3 ? 4 : 2);
 #pragma unroll
-              for (int sp = 0; sp < SPT; ++sp)
-                umma_bf16(d_tmem, ad0 + (uint64_t)((2 * sp * BOXB + (row * NP + jo) * 16) >> 4),
-                          bd0 + (uint64_t)(((tap * SPT + sp) * B_SL) >> 4), IDESC,
-                          (k > 0 || sp > 0) ? 1u : 0u);
+            for (int k = 0; k < 4; ++k) {
+              if (k < nt) {
+                const int tap = kParityTaps[cls][k][0], row = kParityTaps[cls][k][1];
+                const int jo = kParityTaps[cls][k][2];
+#pragma unroll
+                for (int sp = 0; sp < SPT; ++sp)
+                  umma_bf16(d_tmem + (uint32_t)(px * COUT),
+                            ad0 + (uint64_t)((2 * sp * BOXB + (row * NP + jo) * 16) >> 4),
+                            bd0 + (uint64_t)(((tap * SPT + sp) * B_SL) >> 4), IDESC,
+                            (k > 0 || sp > 0) ? 1u : 0u);
+              }
             }
           }
         } else {
@@ -998,8 +995,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_conv_tma(const __grid_consta
     const int quarter = warp & 3, grp = (warp - 2) >> 2;
     const int p = quarter * 32 + lane;
     const bool leader = warp == 2 + 4 * grp && lane == 0;   // issues the group's output stores
-    const uint32_t obuf = ob32 + (uint32_t)(grp * 128 * RB);
-    const int swz = COUT == 64 ? (p & 7) : ((p >> 1) & 3);
+    const uint32_t obuf = ob32 + (uint32_t)(grp * NPAR * 128 * RB);
     for (int i = grp, t = blockIdx.x + grp * gridDim.x; t < n_tiles; i += 2, t += 2 * gridDim.x) {
       const int acc = i % kTmaAcc;
       const bool got = mbar_wait(&accf[acc], (uint32_t)(i / kTmaAcc) & 1u);
@@ -1007,56 +1003,64 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_conv_tma(const __grid_consta
       // the whole group leaves together (it shares barriers), on its own timeout or another's
       if (group_any(1 + grp, !got || s_fail != 0)) break;
       tc_fence_after();
-      int b, y, px, x0;
-      geo(t, b, y, px, x0);
-      const int64_t m = ((int64_t)b * Ho + y) * Ho + (MODE == 2 ? 2 * (x0 + p) + px : x0 + p);
+      int b, y, x0;
+      geo(t, b, y, x0);
       const bool valid = p < CW;
-      uint32_t v[COUT];
       const bool live = quarter * 32 < CW;           // warp-uniform: a row of the quarter is inside
-      if (live) {
-        const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * COUT);
-#pragma unroll
-        for (int c0 = 0; c0 < COUT; c0 += 16) tmem_ld16_issue(ta + (uint32_t)c0, v + c0);
-        tmem_ld_wait();
-      }
-      // the accumulator is in registers: hand it back before the output work
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&acce[acc]);
       // the staging buffer is free once the group's previous store has read it
       if (leader) bulk_wait_read0();
       group_bar(1 + grp);
-      if (live && valid) {
 #pragma unroll
-        for (int c0 = 0; c0 < COUT; c0 += 8) {       // one 16-byte chunk: 8 channels
-          uint32_t pk[4];
-          if (MODE == 0) {
+      for (int px = 0; px < NPAR; ++px) {
+        // output pixel of this lane and parity: row q of the tile's staging (q = p, or 2 p + px)
+        const int q = NPAR * p + px;
+        const int64_t m = ((int64_t)b * Ho + y) * Ho + NPAR * x0 + q;
+        const int swz = COUT == 64 ? (q & 7) : ((q >> 1) & 3);
+        uint32_t v[COUT];
+        if (live) {
+          const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) +
+                              (uint32_t)((acc * NPAR + px) * COUT);
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-              pk[j] = pack_bf16(fmaxf(__uint_as_float(v[c0 + 2 * j]) + sbias[c0 + 2 * j], 0.f),
-                                fmaxf(__uint_as_float(v[c0 + 2 * j + 1]) + sbias[c0 + 2 * j + 1], 0.f));
-          } else {
+          for (int c0 = 0; c0 < COUT; c0 += 16) tmem_ld16_issue(ta + (uint32_t)c0, v + c0);
+          tmem_ld_wait();
+        }
+        if (px == NPAR - 1) {
+          // the accumulator is in registers: hand it back before the output work
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&acce[acc]);
+        }
+        if (live && valid) {
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-              pk[j] = pack_bf16(__uint_as_float(v[c0 + 2 * j]), __uint_as_float(v[c0 + 2 * j + 1]));
-            if (mask) {
-              const int4 mw = __ldg(reinterpret_cast<const int4*>(mask + m * COUT + c0));
-              pk[0] = relu_mask(pk[0], (uint32_t)mw.x);
-              pk[1] = relu_mask(pk[1], (uint32_t)mw.y);
-              pk[2] = relu_mask(pk[2], (uint32_t)mw.z);
-              pk[3] = relu_mask(pk[3], (uint32_t)mw.w);
+          for (int c0 = 0; c0 < COUT; c0 += 8) {     // one 16-byte chunk: 8 channels
+            uint32_t pk[4];
+            if (MODE == 0) {
+#pragma unroll
+              for (int j = 0; j < 4; ++j)
+                pk[j] = pack_bf16(fmaxf(__uint_as_float(v[c0 + 2 * j]) + sbias[c0 + 2 * j], 0.f),
+                                  fmaxf(__uint_as_float(v[c0 + 2 * j + 1]) + sbias[c0 + 2 * j + 1], 0.f));
+            } else {
+#pragma unroll
+              for (int j = 0; j < 4; ++j)
+                pk[j] = pack_bf16(__uint_as_float(v[c0 + 2 * j]), __uint_as_float(v[c0 + 2 * j + 1]));
+              if (mask) {
+                const int4 mw = __ldg(reinterpret_cast<const int4*>(mask + m * COUT + c0));
+                pk[0] = relu_mask(pk[0], (uint32_t)mw.x);
+                pk[1] = relu_mask(pk[1], (uint32_t)mw.y);
+                pk[2] = relu_mask(pk[2], (uint32_t)mw.z);
+                pk[3] = relu_mask(pk[3], (uint32_t)mw.w);
+              }
             }
+            const uint32_t dst = obuf + (uint32_t)(q * RB + (((c0 >> 3) ^ swz) << 4));
+            asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(pk[0]),
+                         "r"(pk[1]), "r"(pk[2]), "r"(pk[3]) : "memory");
           }
-          const uint32_t dst = obuf + (uint32_t)(p * RB + (((c0 >> 3) ^ swz) << 4));
-          asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(pk[0]), "r"(pk[1]),
-                       "r"(pk[2]), "r"(pk[3]) : "memory");
         }
       }
       async_proxy_fence();
       group_bar(1 + grp);
       if (leader) {
-        if constexpr (MODE == 2) tma_store_5d(&omap, obuf, 0, px, x0, y, b);
-        else tma_store_4d(&omap, obuf, 0, x0, y, b);
+        tma_store_4d(&omap, obuf, 0, NPAR * x0, y, b);
         bulk_commit();
       }
     }
@@ -1555,23 +1559,16 @@ int conv_tma(const __nv_bfloat16* in, const __nv_bfloat16* w, const float* bias,
                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   }
   if (r != CUDA_SUCCESS) return GFH_ERR_CUDA;
-  // output view for the tensor stores: NHWC (COUT, Ho, Ho, B), boxes of CW pixels of one row; mode 2
-  // (COUT, 2, H/2, H, B), the parity coordinate picking even or odd output columns
+  // output view for the tensor stores: NHWC (COUT, Ho, Ho, B), boxes of one row's CW pixels (mode
+  // 2: 2 CW, both column parities of the tile)
   alignas(64) CUtensorMap omap;
   const CUtensorMapSwizzle oswz = COUT == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
   static_assert(COUT == 32 || COUT == 64, "output rows of 64 or 128 bytes");
-  if (MODE == 2) {
-    const cuuint64_t dims[5] = {(cuuint64_t)COUT, 2, (cuuint64_t)H / 2, (cuuint64_t)H, (cuuint64_t)B};
-    const cuuint64_t strides[4] = {COUT * e, 2 * COUT * e, (cuuint64_t)H * COUT * e,
-                                   (cuuint64_t)H * H * COUT * e};
-    const cuuint32_t box[5] = {(cuuint32_t)COUT, 1, (cuuint32_t)CW, 1, 1}, es[5] = {1, 1, 1, 1, 1};
-    r = encode(&omap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void*)out, dims, strides, box, es,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, oswz, CU_TENSOR_MAP_L2_PROMOTION_NONE,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  } else {
+  constexpr int NPAR = MODE == 2 ? 2 : 1;
+  {
     const cuuint64_t dims[4] = {(cuuint64_t)COUT, (cuuint64_t)Ho, (cuuint64_t)Ho, (cuuint64_t)B};
     const cuuint64_t strides[3] = {COUT * e, (cuuint64_t)Ho * COUT * e, (cuuint64_t)Ho * Ho * COUT * e};
-    const cuuint32_t box[4] = {(cuuint32_t)COUT, (cuuint32_t)CW, 1, 1}, es[4] = {1, 1, 1, 1};
+    const cuuint32_t box[4] = {(cuuint32_t)COUT, (cuuint32_t)(NPAR * CW), 1, 1}, es[4] = {1, 1, 1, 1};
     r = encode(&omap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)out, dims, strides, box, es,
                CU_TENSOR_MAP_INTERLEAVE_NONE, oswz, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -1584,7 +1581,7 @@ int conv_tma(const __nv_bfloat16* in, const __nv_bfloat16* w, const float* bias,
   // 1024 bytes) the two epilogue groups' output staging of 128 rows x COUT bf16
   const size_t w_bytes = (size_t)(9 * CIN / 16) * (COUT / 8 * 256);
   const size_t stage = (size_t)(CIN / 8) * S * tma_box_bytes(NP, ROWS);
-  const size_t o_bytes = 2 * 128 * COUT * 2 + 1024;
+  const size_t o_bytes = 2 * NPAR * 128 * COUT * 2 + 1024;
   const size_t room = kMaxSmemBytes - fa.sharedSizeBytes - 1024;
   int ns = kTmaMaxStages;
   while (ns >= 2 && w_bytes + ns * stage + 128 * 16 + o_bytes > room) --ns;
@@ -1595,8 +1592,8 @@ int conv_tma(const __nv_bfloat16* in, const __nv_bfloat16* w, const float* bias,
   const int regs = std::max(1, (fa.numRegs + 7) / 8 * 8);
   const int per_sm = std::max(1, std::min({(int)(kSmemPerSm / (smem + fa.sharedSizeBytes + 1024)),
                                            65536 / (regs * kTmaThreads), 2048 / kTmaThreads,
-                                           512 / (kTmaAcc * COUT)}));
-  const int64_t tiles = (int64_t)B * Ho * (MODE == 2 ? 2 : 1) * (Wt / CW);
+                                           512 / (kTmaAcc * NPAR * COUT)}));
+  const int64_t tiles = (int64_t)B * Ho * (Wt / CW);
   const int grid = (int)std::min<int64_t>(tiles, (int64_t)sms * per_sm);
   fn<<<grid, kTmaThreads, smem, st>>>(map, omap, w, bias, mask, out, B, H, ns, flag);
   GFH_CUDA_TRY(cudaGetLastError());
