@@ -13,9 +13,9 @@
 //   mean over t                           -> [B][64 f][64]
 //   head: 1-D conv over f, width 3, 64 -> 64 k tiles  -> logits[b][kt * 64 + f], plus one
 //   "no signal" logit: 4097 classes, softmax cross-entropy.
-// The gradient of every layer is computed by hand-written kernels: weight and input gradients of
-// L2-L5 on tcgen05, L1's weight gradient and the head on CUDA cores;
-// every reduction runs in a fixed order, so a training step is deterministic.  AdamW updates fp32
+// The gradient of every layer is computed by hand-written kernels: weight gradients of L1-L5 and
+// input gradients of L2-L5 on tcgen05 (the bias gradients summed from the same staged tiles), the
+// head on CUDA cores; every reduction runs in a fixed order, so a training step is deterministic.  AdamW updates fp32
 // master weights and refreshes the bf16 copies.  Activation gradients are stored masked by their
 // ReLU (the gradients in the pre-activations), so the gradient kernels stage them as they are.
 #include <cuda.h>
@@ -1104,8 +1104,11 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_conv_tma(const __grid_consta
 // the same array started dx entries later (S = 1) or in the other parity (S = 2); for CIN = 8 the
 // three taps are one MMA of N = 24 whose N-adjacent core matrices are one entry (16 bytes) apart.
 // Core matrices: 8 pixels x 16 bytes, K-adjacent ones 128 bytes apart (the descriptor's leading
-// byte offset), M/N-adjacent ones one chunk apart (its stride byte offset).  At the end the four
-// warps read the accumulators to part[chunk][co][tap][ci] (k_sum_chunks adds the chunks in order).
+// byte offset), M/N-adjacent ones one chunk apart (its stride byte offset).  In the dy = 1 blocks,
+// whose tiles cover every output pixel once, warps 2-3 also sum each staged G tile over its pixels
+// (the bias gradient) before they release the stage with the MMA commit.  At the end the four
+// warps read the accumulators to part[chunk][co][tap][ci] and the bias sums to
+// bias_part[chunk][co] (k_sum_chunks adds the chunks in order).
 // Pixel chunks (blocks per tap row) are a fixed count, so the chunk sums run in the same order on
 // every device; the first layer's narrow accumulators leave room for four times the blocks per SM.
 constexpr int WT_ROWS = 2, WT_THREADS = 128, WT_CHUNKS = 96, WT_CHUNKS1 = 384, WT_STAGES = 4;
@@ -1132,7 +1135,8 @@ struct WgradTc {
 template <int CIN, int COUT, int S>
 __global__ void __launch_bounds__(WT_THREADS) k_wgrad_tma(const __grid_constant__ CUtensorMap gmap,
                                                           const __grid_constant__ CUtensorMap xmap,
-                                                          float* __restrict__ part, int B, int H,
+                                                          float* __restrict__ part,
+                                                          float* __restrict__ bias_part, int B, int H,
                                                           int chunks, unsigned int* flag) {
   using T = WgradTc<CIN, COUT, S>;
   constexpr int NP = T::NP;
@@ -1144,8 +1148,12 @@ __global__ void __launch_bounds__(WT_THREADS) k_wgrad_tma(const __grid_constant_
   __shared__ __align__(8) uint64_t full[WT_STAGES], empty[WT_STAGES], done;
   __shared__ uint32_t tslot;
   __shared__ volatile int s_fail;
+  // bias sums: 64 threads, TPC per 8-co chunk, 8 partial sums each
+  constexpr int TPC = 64 / (COUT / 8);
+  __shared__ float s_bias[64][8];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int chunk = blockIdx.x, dy = blockIdx.y;   // gridDim.x == chunks
+  const bool bias_blk = dy == 1;
   const int Ho = H / S;
   const int tiles_per_img = (Ho / WT_ROWS) * (Ho / 64);
   const int n_tiles = B * tiles_per_img;
@@ -1156,7 +1164,8 @@ __global__ void __launch_bounds__(WT_THREADS) k_wgrad_tma(const __grid_constant_
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    for (int s = 0; s < WT_STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+    // a stage is released by the MMA commit and, in the bias blocks, by warps 2 and 3
+    for (int s = 0; s < WT_STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], bias_blk ? 3 : 1); }
     mbar_init(&done, 1);
     s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1237,7 +1246,44 @@ __global__ void __launch_bounds__(WT_THREADS) k_wgrad_tma(const __grid_constant_
     }
     umma_commit(&done);                              // every MMA issued above has completed
   }
+  float bacc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (warp >= 2 && bias_blk) {
+    // thread u sums chunk c = u / TPC over the pixels j, j + TPC, ... of each tile (rows, then
+    // pixels, in order), j = u % TPC: consecutive threads read consecutive 16-byte rows
+    const int u = tid - 64, c = u / TPC, j = u % TPC;
+    int n = 0;
+    for (int q = chunk; q < n_tiles; q += chunks, ++n) {
+      const int slot = n % WT_STAGES;
+      const bool got = mbar_wait(&full[slot], (uint32_t)(n / WT_STAGES) & 1u);
+      if (!__all_sync(0xffffffffu, got)) {
+        if (lane == 0) { s_fail = 1; atomicOr(flag, GFH_FLAG_TIMEOUT); }
+        break;
+      }
+      if (__shfl_sync(0xffffffffu, s_fail, 0)) break;
+      const unsigned char* g = smem_w + slot * T::STAGE + c * T::GBOX;
+      for (int px = j; px < WT_ROWS * 64; px += TPC) {
+        const uint4 w4 = *reinterpret_cast<const uint4*>(g + px * 16);
+        const uint32_t wv[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          bacc[2 * e] += __uint_as_float(wv[e] << 16);
+          bacc[2 * e + 1] += __uint_as_float(wv[e] & 0xffff0000u);
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[slot]);
+    }
+#pragma unroll
+    for (int e = 0; e < 8; ++e) s_bias[u][e] = bacc[e];
+  }
   __syncthreads();
+  if (bias_blk && tid < COUT) {
+    // co = tid: its chunk's TPC partial sums in order
+    const int c = tid / 8, e = tid % 8;
+    float sum = 0.f;
+    for (int jj = 0; jj < TPC; ++jj) sum += s_bias[c * TPC + jj][e];
+    bias_part[(int64_t)chunk * COUT + tid] = (chunk < n_tiles && !s_fail) ? sum : 0.f;
+  }
   // accumulators -> part[chunk][co][dy * 3 + dx][ci] (zeros for a block without tiles)
   bool ok = true;
   if (warp == 0) {
@@ -1281,45 +1327,6 @@ __global__ void k_sum_chunks(const float* __restrict__ part, int chunks, int n,
   float s = 0.f;
   for (int c = 0; c < chunks; ++c) s += part[(int64_t)c * n + e];
   dst[e] += s;
-}
-
-// Bias gradient of a ReLU layer, db[co] = sum_p G[p][co] with G = dout where out > 0 (out NULL:
-// dout is G already): thread = (pixel row r of the block, 8 channels) reading 16 bytes per pixel
-// with a stride of kBiasBlocks x rows pixels; the block adds its rows in order into part[block][co]
-// (reduced by k_sum_chunks).
-constexpr int kBiasBlocks = 1024;
-__global__ void __launch_bounds__(256) k_bias_grad(const __nv_bfloat16* __restrict__ dout,
-                                                   const __nv_bfloat16* __restrict__ out,
-                                                   float* __restrict__ part, int64_t M, int C) {
-  __shared__ float red[256 * 8];
-  const int q8 = C / 8;                              // 16-byte groups of 8 channels per pixel
-  const int g = threadIdx.x % q8, row = threadIdx.x / q8, rows = blockDim.x / q8;
-  float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  for (int64_t p = (int64_t)blockIdx.x * rows + row; p < M; p += (int64_t)gridDim.x * rows) {
-    const int4 v = __ldg(reinterpret_cast<const int4*>(dout + p * C) + g);
-    const uint32_t w[4] = {(uint32_t)v.x, (uint32_t)v.y, (uint32_t)v.z, (uint32_t)v.w};
-    uint32_t mk[4] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu};
-    if (out) {
-      const int4 a = __ldg(reinterpret_cast<const int4*>(out + p * C) + g);
-      const uint32_t aw[4] = {(uint32_t)a.x, (uint32_t)a.y, (uint32_t)a.z, (uint32_t)a.w};
-#pragma unroll
-      for (int j = 0; j < 4; ++j) mk[j] = relu_mask(0xffffffffu, aw[j]);
-    }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const uint32_t m = w[j] & mk[j];
-      s[2 * j] += __uint_as_float(m << 16);
-      s[2 * j + 1] += __uint_as_float(m & 0xffff0000u);
-    }
-  }
-#pragma unroll
-  for (int j = 0; j < 8; ++j) red[row * C + g * 8 + j] = s[j];
-  __syncthreads();
-  for (int c = threadIdx.x; c < C; c += blockDim.x) {
-    float t = 0.f;
-    for (int r = 0; r < rows; ++r) t += red[r * C + c];
-    part[(int64_t)blockIdx.x * C + c] = t;
-  }
 }
 
 // g[i] = dout[i] where out[i] > 0, else 0 (the gradient in a layer's pre-activation), n elements.
@@ -1649,7 +1656,7 @@ size_t layer_partial_floats(int l, int64_t M) {
   (void)M;
   const size_t cin = l == 0 ? 8 : kCin[l];         // the first layer runs on 8 padded channels
   const size_t ch = l == 0 ? WT_CHUNKS1 : WT_CHUNKS;
-  return std::max((size_t)kBiasBlocks * 256, ch * kCout[l] * 9 * cin);
+  return ch * kCout[l] * (9 * cin + 1);                // weight, then bias partial sums
 }
 
 // Scratch floats the weight and bias gradients of every layer of the network need at batch B.
@@ -1661,15 +1668,6 @@ size_t grad_partial_floats(int B) {
     most = std::max(most, layer_partial_floats(l, (int64_t)B * ho * ho));
   }
   return most;
-}
-
-int bias_grad(const __nv_bfloat16* dout, const __nv_bfloat16* out, float* db, int64_t M, int C,
-              float* part, cudaStream_t st) {
-  k_bias_grad<<<kBiasBlocks, 256, 0, st>>>(dout, out, part, M, C);
-  GFH_CUDA_TRY(cudaGetLastError());
-  k_sum_chunks<<<1, 64, 0, st>>>(part, kBiasBlocks, C, db);
-  GFH_CUDA_TRY(cudaGetLastError());
-  return GFH_OK;
 }
 
 // Tensor maps of the weight-gradient kernel's operands: G (COUT, Ho, Ho, B) in boxes of 8 co x 64
@@ -1711,7 +1709,8 @@ int wgrad_maps(const __nv_bfloat16* G, const __nv_bfloat16* in, int B, int H, CU
   return r == CUDA_SUCCESS ? GFH_OK : GFH_ERR_CUDA;
 }
 
-// Launch of k_wgrad_tma over `chunks` pixel chunks x 3 tap rows; partial sums to part.
+// Launch of k_wgrad_tma over `chunks` pixel chunks x 3 tap rows: weight partial sums to part
+// [chunks][COUT][9][CIN], bias partial sums after them ([chunks][COUT]).
 template <int CIN, int COUT, int S>
 int wgrad_launch(const __nv_bfloat16* G, const __nv_bfloat16* in, int B, int H, int chunks,
                  float* part, cudaStream_t st, unsigned int* flag) {
@@ -1723,7 +1722,8 @@ int wgrad_launch(const __nv_bfloat16* G, const __nv_bfloat16* in, int B, int H, 
   static_assert(smem <= (int)kMaxSmemBytes - 1024, "weight-gradient stages fit in shared memory");
   auto fn = k_wgrad_tma<CIN, COUT, S>;
   GFH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  fn<<<dim3(chunks, 3), WT_THREADS, smem, st>>>(gmap, xmap, part, B, H, chunks, flag);
+  float* bias_part = part + (size_t)chunks * COUT * 9 * CIN;
+  fn<<<dim3(chunks, 3), WT_THREADS, smem, st>>>(gmap, xmap, part, bias_part, B, H, chunks, flag);
   GFH_CUDA_TRY(cudaGetLastError());
   return GFH_OK;
 }
@@ -1738,8 +1738,9 @@ int conv_wgrad_tc(const __nv_bfloat16* G, const __nv_bfloat16* in, float* dw, fl
   const int n = COUT * 9 * CIN;
   k_sum_chunks<<<(n + 255) / 256, 256, 0, st>>>(part, WT_CHUNKS, n, dw);
   GFH_CUDA_TRY(cudaGetLastError());
-  const int Ho = H / S;
-  return bias_grad(G, nullptr, db, (int64_t)B * Ho * Ho, COUT, part, st);
+  k_sum_chunks<<<1, 64, 0, st>>>(part + (size_t)WT_CHUNKS * n, WT_CHUNKS, COUT, db);
+  GFH_CUDA_TRY(cudaGetLastError());
+  return GFH_OK;
 }
 
 // First layer (2 input channels) weight and bias gradients, added into dw and db, from G1 (the
@@ -1753,7 +1754,9 @@ int conv1_wgrad(const __nv_bfloat16* g1, const __nv_bfloat16* in, __nv_bfloat16*
   if (rc) return rc;
   k_sum_chunks_l1<<<(576 + 255) / 256, 256, 0, st>>>(part, WT_CHUNKS1, dw);
   GFH_CUDA_TRY(cudaGetLastError());
-  return bias_grad(g1, nullptr, db, P1, 32, part, st);
+  k_sum_chunks<<<1, 64, 0, st>>>(part + (size_t)WT_CHUNKS1 * 32 * 9 * 8, WT_CHUNKS1, 32, db);
+  GFH_CUDA_TRY(cudaGetLastError());
+  return GFH_OK;
 }
 
 }  // namespace
