@@ -1092,26 +1092,38 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_conv_tma(const __grid_consta
 // tap (zero outside the image).  Per tap a GEMM with M = 64 (co; rows >= COUT are padding, their
 // accumulator rows never read), N = CIN (ci) and K = output pixels, both operands MN-major: a 16-byte
 // row of a core matrix is 8 co (A) or 8 ci (B) of one pixel, as the NHWC tensors hold them.
-// Block (chunk, dy) keeps the accumulators of the taps (dy, 0..2) in tensor memory over its chunk's
-// tiles; a tile is WT_ROWS output rows x 64 columns of one image, its K-steps 16 output pixels of one
-// row.  Warp 0 copies each tile with the tensor memory accelerator into one of WT_STAGES stages:
+// DYB = 3 (layers with CIN <= 32): block `chunk` keeps the accumulators of all nine taps in tensor
+// memory over its chunk's tiles, so G is read once.  DYB = 1 (CIN = 64, whose nine taps would not
+// fit): block (chunk, dy) keeps the taps (dy, 0..2) and G is read once per tap row.  A tile is
+// WT_ROWS output rows x 64 columns of one image, its K-steps 16 output pixels of one row.  Warp 0
+// copies each tile with the tensor memory accelerator into one of WT_STAGES stages:
 //   G: one box per 8-co chunk c of WT_ROWS rows x 64 pixels  -> [c][row][64 px] x 16 bytes;
-//   X: one box per 8-ci chunk c (and column parity for S = 2) of the WT_ROWS input rows
-//      (y0 + r) S + dy - 1 x NP entries, zero-filled outside the image -> [c][par][row][NP] x 16
-//      bytes; entry j of parity 0 is input column x0 S - 1 + j (S = 1), 2 (x0 + j) - 1 (S = 2), of
-//      parity 1 column 2 (x0 + j).
+//   X: one box per 8-ci chunk c (and column parity for S = 2) of the input rows the tile's taps
+//      read, x NP entries, zero-filled outside the image -> [c][par][row][NP] x 16 bytes: rows
+//      (y0 + r) S + dy - 1 for DYB = 1, or all rows y0 S - 1 .. (y0 + WT_ROWS - 1) S + 1 for
+//      DYB = 3 (tap row dy of output row r is row r S + dy of the box); entry j of parity 0 is
+//      input column x0 S - 1 + j (S = 1), 2 (x0 + j) - 1 (S = 2), of parity 1 column 2 (x0 + j).
 // Warp 1 issues the MMAs once a stage is full and frees it with their commit.  Tap dx's B operand is
 // the same array started dx entries later (S = 1) or in the other parity (S = 2); for CIN = 8 the
 // three taps are one MMA of N = 24 whose N-adjacent core matrices are one entry (16 bytes) apart.
 // Core matrices: 8 pixels x 16 bytes, K-adjacent ones 128 bytes apart (the descriptor's leading
-// byte offset), M/N-adjacent ones one chunk apart (its stride byte offset).  In the dy = 1 blocks,
-// whose tiles cover every output pixel once, warps 2-3 also sum each staged G tile over its pixels
+// byte offset), M/N-adjacent ones one chunk apart (its stride byte offset).  In the blocks whose
+// tiles cover every output pixel once (all blocks for DYB = 3, the dy = 1 ones for DYB = 1),
+// warps 2-3 also sum each staged G tile over its pixels
 // (the bias gradient) before they release the stage with the MMA commit.  At the end the four
 // warps read the accumulators to part[chunk][co][tap][ci] and the bias sums to
 // bias_part[chunk][co] (k_sum_chunks adds the chunks in order).
-// Pixel chunks (blocks per tap row) are a fixed count, so the chunk sums run in the same order on
-// every device; the first layer's narrow accumulators leave room for four times the blocks per SM.
-constexpr int WT_ROWS = 2, WT_THREADS = 128, WT_CHUNKS = 96, WT_CHUNKS1 = 384, WT_STAGES = 4;
+// Pixel chunks (blocks per tap row) are a fixed count per layer, so the chunk sums run in the same
+// order on every device: 384 for the first layer (narrow accumulators, several blocks per SM), 304
+// for the other DYB = 3 layers (one block per SM, two waves of 152), 96 per tap row for DYB = 1.
+constexpr int WT_ROWS = 2, WT_THREADS = 128, WT_STAGES = 4;
+constexpr int WT_CHUNKS = 96, WT_CHUNKS1 = 384, WT_CHUNKS3 = 304;
+
+// Tap rows per weight-gradient block and pixel chunks of a layer with CIN input channels.
+constexpr int wgrad_dyb(int cin) { return cin <= 32 ? 3 : 1; }
+constexpr int wgrad_chunks(int cin) {
+  return cin == 8 ? WT_CHUNKS1 : (wgrad_dyb(cin) == 3 ? WT_CHUNKS3 : WT_CHUNKS);
+}
 
 // Row of an M = 64 accumulator held by tensor-memory lane `lane` (-1: no row): rows 16 q .. 16 q + 15
 // sit in lanes 32 q .. 32 q + 15, the first half of each warp's quarter of the lanes.
@@ -1119,11 +1131,12 @@ __device__ __forceinline__ int wgrad_row_of_lane(int lane) {
   return (lane & 31) < 16 ? (lane >> 5) * 16 + (lane & 31) : -1;
 }
 
-template <int CIN, int COUT, int S>
+template <int CIN, int COUT, int S, int DYB>
 struct WgradTc {
   static constexpr int NP = S == 1 ? 66 : 65;                         // entries per (chunk, parity, row)
+  static constexpr int XROWS = DYB == 1 ? WT_ROWS : (WT_ROWS - 1) * S + 3;   // input rows per tile
   static constexpr int GBOX = WT_ROWS * 64 * 16;                      // one G box
-  static constexpr int XBOX = (WT_ROWS * NP * 16 + 127) / 128 * 128;  // one X box (128-aligned)
+  static constexpr int XBOX = (XROWS * NP * 16 + 127) / 128 * 128;    // one X box (128-aligned)
   static constexpr int GB = (COUT / 8) * GBOX;
   static constexpr int XB = (CIN / 8) * S * XBOX;
   static constexpr int STAGE = (GB + XB + 127) / 128 * 128;
@@ -1132,18 +1145,20 @@ struct WgradTc {
   static constexpr int SMEM = WT_STAGES * STAGE + PAD;
 };
 
-template <int CIN, int COUT, int S>
+template <int CIN, int COUT, int S, int DYB>
 __global__ void __launch_bounds__(WT_THREADS) k_wgrad_tma(const __grid_constant__ CUtensorMap gmap,
                                                           const __grid_constant__ CUtensorMap xmap,
                                                           float* __restrict__ part,
                                                           float* __restrict__ bias_part, int B, int H,
                                                           int chunks, unsigned int* flag) {
-  using T = WgradTc<CIN, COUT, S>;
+  using T = WgradTc<CIN, COUT, S, DYB>;
   constexpr int NP = T::NP;
   constexpr int NMMA = CIN == 8 ? 3 * CIN : CIN;
   constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
                              ((uint32_t)(NMMA >> 3) << 17) | ((uint32_t)(64 >> 4) << 24);
-  constexpr uint32_t TCOLS = 3 * CIN <= 128 ? 128 : 256;
+  constexpr int NACC = DYB * 3 * CIN;               // accumulator columns: (dy, dx, ci)
+  constexpr uint32_t TCOLS = NACC <= 128 ? 128 : (NACC <= 256 ? 256 : 512);
+  static_assert(NACC <= 512, "tensor memory holds the block's taps");
   extern __shared__ __align__(1024) unsigned char smem_w[];
   __shared__ __align__(8) uint64_t full[WT_STAGES], empty[WT_STAGES], done;
   __shared__ uint32_t tslot;
@@ -1152,8 +1167,8 @@ __global__ void __launch_bounds__(WT_THREADS) k_wgrad_tma(const __grid_constant_
   constexpr int TPC = 64 / (COUT / 8);
   __shared__ float s_bias[64][8];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int chunk = blockIdx.x, dy = blockIdx.y;   // gridDim.x == chunks
-  const bool bias_blk = dy == 1;
+  const int chunk = blockIdx.x, dy1 = blockIdx.y;  // gridDim.x == chunks; dy1: DYB = 1's tap row
+  const bool bias_blk = DYB == 3 || dy1 == 1;
   const int Ho = H / S;
   const int tiles_per_img = (Ho / WT_ROWS) * (Ho / 64);
   const int n_tiles = B * tiles_per_img;
@@ -1190,24 +1205,26 @@ __global__ void __launch_bounds__(WT_THREADS) k_wgrad_tma(const __grid_constant_
       const int rg = rem / (Ho / 64), cb = rem - rg * (Ho / 64);
       const int y0 = rg * WT_ROWS, x0 = cb * 64;
       const uint32_t st = s32 + (uint32_t)(slot * T::STAGE);
-      mbar_expect_tx(&full[slot], (uint32_t)(T::GB + (CIN / 8) * S * WT_ROWS * NP * 16));
+      mbar_expect_tx(&full[slot], (uint32_t)(T::GB + (CIN / 8) * S * T::XROWS * NP * 16));
 #pragma unroll
       for (int c = 0; c < COUT / 8; ++c)
         tma_load_4d(st + (uint32_t)(c * T::GBOX), &gmap, &full[slot], 8 * c, x0, y0, b);
 #pragma unroll
       for (int c = 0; c < CIN / 8; ++c) {
         const uint32_t xs = st + (uint32_t)(T::GB + c * S * T::XBOX);
+        // first input row: y0 S - 1 (all tap rows), or (y0 S) + dy - 1 for one tap row, whose
+        // S = 2 rows 2 (y0 + r) + dy - 1 come through the row traversal stride of 2
+        const int yr = y0 * S - 1 + (DYB == 1 ? dy1 : 0);
         if constexpr (S == 1) {
-          tma_load_4d(xs, &xmap, &full[slot], 8 * c, x0 - 1, y0 + dy - 1, b);
-        } else {   // rows 2 (y0 + r) + dy - 1 through the row traversal stride of 2
-          tma_load_5d(xs, &xmap, &full[slot], 8 * c, 1, x0 - 1, 2 * y0 + dy - 1, b);
-          tma_load_5d(xs + (uint32_t)T::XBOX, &xmap, &full[slot], 8 * c, 0, x0, 2 * y0 + dy - 1, b);
+          tma_load_4d(xs, &xmap, &full[slot], 8 * c, x0 - 1, yr, b);
+        } else {
+          tma_load_5d(xs, &xmap, &full[slot], 8 * c, 1, x0 - 1, yr, b);
+          tma_load_5d(xs + (uint32_t)T::XBOX, &xmap, &full[slot], 8 * c, 0, x0, yr, b);
         }
       }
       ++issued;
     }
   } else if (warp == 1 && lane == 0) {
-    bool any = false;
     for (int q = chunk; q < n_tiles; q += chunks) {
       const int slot = issued % WT_STAGES;
       if (!mbar_wait(&full[slot], (uint32_t)(issued / WT_STAGES) & 1u)) {
@@ -1225,21 +1242,28 @@ __global__ void __launch_bounds__(WT_THREADS) k_wgrad_tma(const __grid_constant_
           // A: [c][row][64 px]; B: [c][par][row][NP]
           const uint64_t ad =
               umma_desc(st + (uint32_t)((r * 64 + ks * 16) * 16), 128u, (uint32_t)T::GBOX);
-          if constexpr (CIN == 8) {
-            const uint32_t b_addr = st + (uint32_t)(T::GB + (r * NP + ks * 16) * 16);
-            umma_bf16(tmem, ad, umma_desc(b_addr, 128u, 16u), IDESC, any ? 1u : 0u);
-          } else {
+          // every accumulator column group starts with the block's first K-step
+          const uint32_t acc_on = (issued > 0 || r > 0 || ks > 0) ? 1u : 0u;
 #pragma unroll
-            for (int dx = 0; dx < 3; ++dx) {
-              const int par = S == 1 ? 0 : (dx == 1 ? 1 : 0);
-              const int jo = S == 1 ? dx : (dx == 2 ? 1 : 0);
-              const uint32_t b_addr =
-                  st + (uint32_t)(T::GB + par * T::XBOX + (r * NP + ks * 16 + jo) * 16);
-              umma_bf16(tmem + (uint32_t)(dx * CIN), ad,
-                        umma_desc(b_addr, 128u, (uint32_t)(S * T::XBOX)), IDESC, any ? 1u : 0u);
+          for (int d = 0; d < DYB; ++d) {
+            // box row of this output row's tap row, accumulator columns of the tap row
+            const int xr = DYB == 1 ? r : r * S + d;
+            const uint32_t tcol = tmem + (uint32_t)(d * 3 * CIN);
+            if constexpr (CIN == 8) {
+              const uint32_t b_addr = st + (uint32_t)(T::GB + (xr * NP + ks * 16) * 16);
+              umma_bf16(tcol, ad, umma_desc(b_addr, 128u, 16u), IDESC, acc_on);
+            } else {
+#pragma unroll
+              for (int dx = 0; dx < 3; ++dx) {
+                const int par = S == 1 ? 0 : (dx == 1 ? 1 : 0);
+                const int jo = S == 1 ? dx : (dx == 2 ? 1 : 0);
+                const uint32_t b_addr =
+                    st + (uint32_t)(T::GB + par * T::XBOX + (xr * NP + ks * 16 + jo) * 16);
+                umma_bf16(tcol + (uint32_t)(dx * CIN), ad,
+                          umma_desc(b_addr, 128u, (uint32_t)(S * T::XBOX)), IDESC, acc_on);
+              }
             }
           }
-          any = true;
         }
       umma_commit(&empty[slot]);
       ++issued;
@@ -1284,7 +1308,7 @@ __global__ void __launch_bounds__(WT_THREADS) k_wgrad_tma(const __grid_constant_
     for (int jj = 0; jj < TPC; ++jj) sum += s_bias[c * TPC + jj][e];
     bias_part[(int64_t)chunk * COUT + tid] = (chunk < n_tiles && !s_fail) ? sum : 0.f;
   }
-  // accumulators -> part[chunk][co][dy * 3 + dx][ci] (zeros for a block without tiles)
+  // accumulators -> part[chunk][co][tap][ci] (zeros for a block without tiles)
   bool ok = true;
   if (warp == 0) {
     const bool mine = mbar_wait(&done, 0u);
@@ -1303,17 +1327,20 @@ __global__ void __launch_bounds__(WT_THREADS) k_wgrad_tma(const __grid_constant_
   const bool have = chunk < n_tiles && !s_fail;
   float* const dst = part + (int64_t)chunk * COUT * 9 * CIN;
   constexpr int JN = CIN < 16 ? CIN : 16;          // columns of one tap read per load
-  for (int dx = 0; dx < 3; ++dx)
-    for (int c0 = 0; c0 < CIN; c0 += 16) {
-      uint32_t v[16];
-      if (have) tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(dx * CIN + c0), v);
-      const int co = wgrad_row_of_lane(warp * 32 + lane);
-      if (co >= 0 && co < COUT) {
-        float* o = dst + ((int64_t)co * 9 + dy * 3 + dx) * CIN + c0;
+  for (int d = 0; d < DYB; ++d)
+    for (int dx = 0; dx < 3; ++dx)
+      for (int c0 = 0; c0 < CIN; c0 += 16) {
+        const int tap = (DYB == 1 ? dy1 : d) * 3 + dx;
+        uint32_t v[16];
+        if (have)
+          tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((d * 3 + dx) * CIN + c0), v);
+        const int co = wgrad_row_of_lane(warp * 32 + lane);
+        if (co >= 0 && co < COUT) {
+          float* o = dst + ((int64_t)co * 9 + tap) * CIN + c0;
 #pragma unroll
-        for (int j = 0; j < JN; ++j) o[j] = have ? __uint_as_float(v[j]) : 0.f;
+          for (int j = 0; j < JN; ++j) o[j] = have ? __uint_as_float(v[j]) : 0.f;
+        }
       }
-    }
   tc_fence_before();
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
@@ -1655,7 +1682,7 @@ int conv_fwd(const __nv_bfloat16* in, const __nv_bfloat16* w, const float* bias,
 size_t layer_partial_floats(int l, int64_t M) {
   (void)M;
   const size_t cin = l == 0 ? 8 : kCin[l];         // the first layer runs on 8 padded channels
-  const size_t ch = l == 0 ? WT_CHUNKS1 : WT_CHUNKS;
+  const size_t ch = wgrad_chunks(l == 0 ? 8 : kCin[l]);
   return ch * kCout[l] * (9 * cin + 1);                // weight, then bias partial sums
 }
 
@@ -1671,15 +1698,15 @@ size_t grad_partial_floats(int B) {
 }
 
 // Tensor maps of the weight-gradient kernel's operands: G (COUT, Ho, Ho, B) in boxes of 8 co x 64
-// pixels x WT_ROWS rows; X (CIN, H, H, B) in boxes of 8 ci x NP entries x WT_ROWS rows, or for S = 2
-// the column-parity view (CIN, 2, H/2, H, B) with rows traversed with a stride of 2.
-template <int CIN, int COUT, int S>
+// pixels x WT_ROWS rows; X (CIN, H, H, B) in boxes of 8 ci x NP entries x XROWS rows, or for S = 2
+// the column-parity view (CIN, 2, H/2, H, B), its rows traversed with a stride of 2 for one tap row.
+template <int CIN, int COUT, int S, int DYB>
 int wgrad_maps(const __nv_bfloat16* G, const __nv_bfloat16* in, int B, int H, CUtensorMap* gmap,
                CUtensorMap* xmap) {
   const PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
   if (!encode) return GFH_ERR_CUDA;
   const cuuint64_t e = 2, Ho = (cuuint64_t)(H / S);
-  constexpr int NP = WgradTc<CIN, COUT, S>::NP;
+  constexpr int NP = WgradTc<CIN, COUT, S, DYB>::NP, XROWS = WgradTc<CIN, COUT, S, DYB>::XROWS;
   {
     const cuuint64_t dims[4] = {(cuuint64_t)COUT, Ho, Ho, (cuuint64_t)B};
     const cuuint64_t strides[3] = {COUT * e, Ho * COUT * e, Ho * Ho * COUT * e};
@@ -1694,14 +1721,17 @@ int wgrad_maps(const __nv_bfloat16* G, const __nv_bfloat16* in, int B, int H, CU
   if (S == 1) {
     const cuuint64_t dims[4] = {(cuuint64_t)CIN, h, h, (cuuint64_t)B};
     const cuuint64_t strides[3] = {CIN * e, h * CIN * e, h * h * CIN * e};
-    const cuuint32_t box[4] = {8, (cuuint32_t)NP, WT_ROWS, 1}, es[4] = {1, 1, 1, 1};
+    const cuuint32_t box[4] = {8, (cuuint32_t)NP, XROWS, 1}, es[4] = {1, 1, 1, 1};
     r = encode(xmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)in, dims, strides, box, es,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   } else {
     const cuuint64_t dims[5] = {(cuuint64_t)CIN, 2, h / 2, h, (cuuint64_t)B};
     const cuuint64_t strides[4] = {CIN * e, 2 * CIN * e, h * CIN * e, h * h * CIN * e};
-    const cuuint32_t box[5] = {8, 1, (cuuint32_t)NP, 2 * WT_ROWS, 1}, es[5] = {1, 1, 1, 2, 1};
+    // one tap row: rows 2 (y0 + r) + dy - 1 (stride 2); all tap rows: XROWS consecutive rows
+    const cuuint32_t rstride = DYB == 1 ? 2 : 1;
+    const cuuint32_t box[5] = {8, 1, (cuuint32_t)NP, (cuuint32_t)XROWS * rstride, 1},
+                     es[5] = {1, 1, 1, rstride, 1};
     r = encode(xmap, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, (void*)in, dims, strides, box, es,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -1709,21 +1739,23 @@ int wgrad_maps(const __nv_bfloat16* G, const __nv_bfloat16* in, int B, int H, CU
   return r == CUDA_SUCCESS ? GFH_OK : GFH_ERR_CUDA;
 }
 
-// Launch of k_wgrad_tma over `chunks` pixel chunks x 3 tap rows: weight partial sums to part
-// [chunks][COUT][9][CIN], bias partial sums after them ([chunks][COUT]).
+// Launch of k_wgrad_tma over the layer's pixel chunks (x 3 tap rows for DYB = 1): weight partial
+// sums to part [chunks][COUT][9][CIN], bias partial sums after them ([chunks][COUT]).
 template <int CIN, int COUT, int S>
-int wgrad_launch(const __nv_bfloat16* G, const __nv_bfloat16* in, int B, int H, int chunks,
-                 float* part, cudaStream_t st, unsigned int* flag) {
+int wgrad_launch(const __nv_bfloat16* G, const __nv_bfloat16* in, int B, int H, float* part,
+                 cudaStream_t st, unsigned int* flag) {
+  constexpr int DYB = wgrad_dyb(CIN), chunks = wgrad_chunks(CIN);
   if ((H / S) % 64 || H % S) return GFH_ERR_ARG;
   alignas(64) CUtensorMap gmap, xmap;
-  const int rc = wgrad_maps<CIN, COUT, S>(G, in, B, H, &gmap, &xmap);
+  const int rc = wgrad_maps<CIN, COUT, S, DYB>(G, in, B, H, &gmap, &xmap);
   if (rc) return rc;
-  constexpr int smem = WgradTc<CIN, COUT, S>::SMEM;
-  static_assert(smem <= (int)kMaxSmemBytes - 1024, "weight-gradient stages fit in shared memory");
-  auto fn = k_wgrad_tma<CIN, COUT, S>;
+  constexpr int smem = WgradTc<CIN, COUT, S, DYB>::SMEM;
+  static_assert(smem <= (int)kMaxSmemBytes - 4096, "weight-gradient stages fit in shared memory");
+  auto fn = k_wgrad_tma<CIN, COUT, S, DYB>;
   GFH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   float* bias_part = part + (size_t)chunks * COUT * 9 * CIN;
-  fn<<<dim3(chunks, 3), WT_THREADS, smem, st>>>(gmap, xmap, part, bias_part, B, H, chunks, flag);
+  fn<<<dim3(chunks, DYB == 3 ? 1 : 3), WT_THREADS, smem, st>>>(gmap, xmap, part, bias_part, B, H,
+                                                                chunks, flag);
   GFH_CUDA_TRY(cudaGetLastError());
   return GFH_OK;
 }
@@ -1733,12 +1765,12 @@ int wgrad_launch(const __nv_bfloat16* G, const __nv_bfloat16* in, int B, int H, 
 template <int CIN, int COUT, int S>
 int conv_wgrad_tc(const __nv_bfloat16* G, const __nv_bfloat16* in, float* dw, float* db, int B,
                   int H, float* part, cudaStream_t st, unsigned int* flag) {
-  const int rc = wgrad_launch<CIN, COUT, S>(G, in, B, H, WT_CHUNKS, part, st, flag);
+  const int rc = wgrad_launch<CIN, COUT, S>(G, in, B, H, part, st, flag);
   if (rc) return rc;
-  const int n = COUT * 9 * CIN;
-  k_sum_chunks<<<(n + 255) / 256, 256, 0, st>>>(part, WT_CHUNKS, n, dw);
+  const int n = COUT * 9 * CIN, chunks = wgrad_chunks(CIN);
+  k_sum_chunks<<<(n + 255) / 256, 256, 0, st>>>(part, chunks, n, dw);
   GFH_CUDA_TRY(cudaGetLastError());
-  k_sum_chunks<<<1, 64, 0, st>>>(part + (size_t)WT_CHUNKS * n, WT_CHUNKS, COUT, db);
+  k_sum_chunks<<<1, 64, 0, st>>>(part + (size_t)chunks * n, chunks, COUT, db);
   GFH_CUDA_TRY(cudaGetLastError());
   return GFH_OK;
 }
@@ -1750,7 +1782,7 @@ int conv1_wgrad(const __nv_bfloat16* g1, const __nv_bfloat16* in, __nv_bfloat16*
   const int64_t P1 = (int64_t)B * H * H;
   k_pad_channels<<<(unsigned)((P1 + 255) / 256), 256, 0, st>>>((const uint32_t*)in, (int4*)img8, P1);
   GFH_CUDA_TRY(cudaGetLastError());
-  const int rc = wgrad_launch<8, 32, 1>(g1, img8, B, H, WT_CHUNKS1, part, st, flag);
+  const int rc = wgrad_launch<8, 32, 1>(g1, img8, B, H, part, st, flag);
   if (rc) return rc;
   k_sum_chunks_l1<<<(576 + 255) / 256, 256, 0, st>>>(part, WT_CHUNKS1, dw);
   GFH_CUDA_TRY(cudaGetLastError());
