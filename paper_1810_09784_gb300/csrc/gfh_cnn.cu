@@ -361,11 +361,16 @@ __global__ void __launch_bounds__(1024) k_line_scores(const uint32_t* __restrict
 
 // ---- tensor-core helpers --------------------------------------------------------------------------
 
-// Keeps each bf16 half of g where the matching half of the post-ReLU activation is positive.
-__device__ __forceinline__ uint32_t relu_mask(uint32_t g, uint32_t act) {
-  const uint32_t lo = ((act & 0xffffu) != 0u && !(act & 0x8000u)) ? 0xffffu : 0u;
-  const uint32_t hi = ((act >> 16) != 0u && !(act & 0x80000000u)) ? 0xffff0000u : 0u;
-  return g & (lo | hi);
+// Bit 0 / bit 1: whether the low / high bf16 half of w is positive (where a ReLU passes gradient).
+__device__ __forceinline__ uint32_t pos_bits(uint32_t w) {
+  const uint32_t lo = w & 0xffffu, hi = w >> 16;
+  return (uint32_t)((lo & 0x7fffu) != 0u && !(lo & 0x8000u)) |
+         ((uint32_t)((hi & 0x7fffu) != 0u && !(hi & 0x8000u)) << 1);
+}
+
+// Keeps each bf16 half of g whose bit (0: low half, 1: high half) is set in b2.
+__device__ __forceinline__ uint32_t keep_by_bits(uint32_t g, uint32_t b2) {
+  return g & (((b2 & 1u) ? 0xffffu : 0u) | ((b2 & 2u) ? 0xffff0000u : 0u));
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
@@ -466,12 +471,8 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Asynchronous global -> shared copies (16 or 4 bytes); src_bytes = 0 fills the destination with
-// zeros (the source address is then not read).
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes)
-               : "memory");
-}
+// Asynchronous global -> shared copy of 4 bytes; src_bytes = 0 fills the destination with zeros
+// (the source address is then not read).
 __device__ __forceinline__ void cp_async4(uint32_t dst, const void* src, uint32_t src_bytes) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(src_bytes)
                : "memory");
@@ -490,138 +491,66 @@ __device__ __forceinline__ void async_proxy_fence() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// ---- L1-L5 forward on tcgen05: out[m][n] = relu(bias[n] + sum_k A[m][k] W[n][k]) ----------------
-// Implicit GEMM: m = output pixel (b, y, x), k = tap * CIN + ci (tap = 3 dy + dx, padded with zeros
-// to a multiple of 16), A[m][k] = in[b][y S + dy - 1][x S + dx - 1][ci] (zero outside the image).
-// Persistent blocks of 256 threads keep the weights in shared memory; one thread issues the MMAs
-// (M = 128, N = COUT, K = 16) into tensor memory and commits them to an mbarrier; after they
-// complete the next tile's asynchronous copies (zero-filled outside the image) start before the 8
+// ---- L1 forward on tcgen05: out[m][n] = relu(bias[n] + sum_k A[m][k] W[n][k]) -------------------
+// Implicit GEMM over the first layer's two input channels: m = output pixel (b, y, x), k = 2 tap + ci
+// (tap = 3 dy + dx; K = 18 padded with zeros to 32), A[m][k] = in[b][y + dy - 1][x + dx - 1][ci]
+// (zero outside the image).  A tile is 128 consecutive pixels staged im2col by cp.async (one 4-byte
+// pair per tap, zero-filled outside the image).  Persistent blocks of 256 threads keep the weights in
+// shared memory; one thread issues the tile's two MMAs (M = 128, N = 32, K = 16) into tensor memory
+// and commits them to an mbarrier; once they complete the next tile's copies start before the 8
 // warps read the accumulator back (warp w: rows 32 (w % 4) .., half w / 4 of the columns), add the
-// bias, apply the ReLU and store bf16.
-//
-// CIN % 8 == 0: a tile is RT output rows (RT = 2 when W_out <= 64, else 1; W_out <= 128), each row
-// one M = 128 MMA chain into its own accumulator (MMA rows past W_out are computed and dropped).
-// The (RT - 1) S + 3 input rows a tile reads are staged once, as 16-byte rows (8 channels) per
-// input pixel: [row][chunk][parity][entry], entry j = input column j - 1 (S = 1) or, for S = 2,
-// the odd columns 2j - 1 (parity 0) and the even columns 2j (parity 1), NP = W_out + 2 entries.
-// Tap (dy, dx) of output column x is entry x + dx (S = 1) or O[x], E[x], O[x + 1] (S = 2): the
-// MMA's A descriptor starts at that entry (any 16-byte row), 8-row groups 128 bytes apart, K
-// halves one chunk block apart; the over-read of the dropped rows stays inside a tail pad.
-// CIN = 2: a tile is 128 consecutive pixels staged im2col (k = 2 tap + ci, one 4-byte pair per tap).
-// Output rows wider than 128 pixels are cut into column blocks of 128 (entries x0 - 1 .. x0 + 128).
-//
-// The same kernel computes input gradients (S = 1, no bias, no ReLU): with the gradient G in a
-// layer's pre-activation as `in` (CIN = the layer's output channels) and the layer's weights
-// W[CIN][3][3][COUT] as `w`, the input gradient din[y][x][c] = sum_{dy, dx, o} G[y + 1 - dy]
-// [x + 1 - dx][o] W[o][dy][dx][c] is this convolution with the taps flipped and W transposed
-// (B[c][(8 - tap) CIN + o] = W[o][tap][c], staged once per block).  MODE 1: a stride-1 layer (G of
-// H x H pixels).  MODE 2: a stride-2 layer, whose input gradient is the stride-1 convolution of G
-// with zeros inserted between its pixels (G of H/2 x H/2): the halo staging reads G at even rows
-// and columns and zero-fills the rest, so the zeros cost no memory.  The result is stored masked by
-// mask > 0 (the gradient in the previous layer's pre-activation) when mask is given.
-template <int CIN, int COUT, int S, int MODE = 0>
-__global__ void __launch_bounds__(256) k_conv_fwd_tc(const __nv_bfloat16* __restrict__ in,
-                                                     const __nv_bfloat16* __restrict__ w,
-                                                     const float* __restrict__ bias,
-                                                     const __nv_bfloat16* __restrict__ mask,
-                                                     __nv_bfloat16* __restrict__ out, int B, int H,
-                                                     int tcols, unsigned int* flag) {
-  static_assert(MODE == 0 || (S == 1 && CIN % 8 == 0), "input gradients: stride-1 halo form");
-  constexpr bool HALO = CIN % 8 == 0;
-  constexpr int KR = 9 * CIN;                        // real K
-  constexpr int K = (KR + 15) / 16 * 16;             // padded K
-  constexpr int NSL = K / 16;
-  constexpr int QC = HALO ? CIN / 8 : 1;             // 16-byte chunks per pixel
+// bias, apply the ReLU and store bf16.  With `bits`, each warp half also stores which of its 16
+// stored values are positive, one bit per channel: bits16[2 m + w / 4], bit i = channel 16 (w / 4) + i
+// (the ReLU mask the stride-2 input gradient of layer 2 applies).
+__global__ void __launch_bounds__(256) k_conv1_fwd_tc(const __nv_bfloat16* __restrict__ in,
+                                                      const __nv_bfloat16* __restrict__ w,
+                                                      const float* __restrict__ bias,
+                                                      __nv_bfloat16* __restrict__ out,
+                                                      uint16_t* __restrict__ bits16, int B, int H,
+                                                      unsigned int* flag) {
+  constexpr int CIN = 2, COUT = 32;
+  constexpr int KR = 9 * CIN, K = 32, NSL = K / 16;
   constexpr int A_SL = 128 / 8 * 256, B_SL = COUT / 8 * 256;
   constexpr uint32_t IDESC = umma_idesc_bf16(128, COUT);
+  constexpr uint32_t TCOLS = 32;
   extern __shared__ __align__(1024) unsigned char smem_tc[];
   unsigned char* sb = smem_tc;                       // weights
-  unsigned char* sa = smem_tc + NSL * B_SL;          // A (halo or im2col)
+  unsigned char* sa = smem_tc + NSL * B_SL;          // A (im2col)
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tslot;
   __shared__ float sbias[COUT];
   __shared__ int s_ok;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int Ho = H / S;
-  const int M = B * Ho * Ho;
-  const int RT = Ho <= 64 ? 2 : 1;                   // output rows per tile (halo form)
-  const int CW = Ho > 128 ? 128 : Ho;                // output columns per tile
-  const int NCB = Ho / CW;                           // column blocks per row
-  const int NP = CW + 2;                             // halo entries per (row, chunk, parity)
-  const int HBLK = S * NP * 16;                      // bytes per (row, chunk)
-  const int n_tiles = HALO ? B * (Ho / RT) * NCB : (M + 127) / 128;
-  const int Hs = MODE == 2 ? H / 2 : H;              // rows / columns of `in`
+  const int M = B * H * H;
+  const int n_tiles = (M + 127) / 128;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(&tslot)), "r"(tcols));
+                     smem_u32(&tslot)), "r"(TCOLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   // weights, K-major rows of the output channel, zero-padded K
-  if (HALO && MODE == 0) {
-    for (int e = tid; e < COUT * (KR / 8); e += blockDim.x) {
-      const int co = e / (KR / 8), k = (e % (KR / 8)) * 8;
-      *reinterpret_cast<int4*>(sb + cm_off(co, k, COUT)) =
-          __ldg(reinterpret_cast<const int4*>(w + co * KR + k));
-    }
-  } else if (HALO) {                                 // transposed, taps flipped
-    for (int e = tid; e < COUT * KR; e += blockDim.x) {
-      const int n = e / KR, k = e - n * KR, tap = k / CIN, o = k - tap * CIN;
-      *reinterpret_cast<__nv_bfloat16*>(sb + cm_off(n, k, COUT)) = w[(o * 9 + 8 - tap) * COUT + n];
-    }
-  } else {
-    for (int e = tid; e < COUT * K; e += blockDim.x) {
-      const int co = e / K, k = e % K;
-      *reinterpret_cast<__nv_bfloat16*>(sb + cm_off(co, k, COUT)) =
-          k < KR ? w[co * KR + k] : __float2bfloat16_rn(0.f);
-    }
+  for (int e = tid; e < COUT * K; e += blockDim.x) {
+    const int co = e / K, k = e % K;
+    *reinterpret_cast<__nv_bfloat16*>(sb + cm_off(co, k, COUT)) =
+        k < KR ? w[co * KR + k] : __float2bfloat16_rn(0.f);
   }
-  for (int c = tid; c < COUT; c += blockDim.x) sbias[c] = MODE == 0 ? bias[c] : 0.f;
+  for (int c = tid; c < COUT; c += blockDim.x) sbias[c] = bias[c];
   if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
   const uint32_t sa32 = smem_u32(sa), sb32 = smem_u32(sb);
 
-  auto stage = [&](int t) {
-    if (HALO) {
-      // tile = rows y0 .. y0 + RT - 1, columns x0 .. x0 + CW - 1 of image b; input rows
-      // y0 S - 1 + ri, ri < (RT - 1) S + 3
-      const int b = t / ((Ho / RT) * NCB), rem = t - b * ((Ho / RT) * NCB);
-      const int y0 = (rem / NCB) * RT, x0 = (rem - (rem / NCB) * NCB) * CW;
-      const int rin = (RT - 1) * S + 3;
-      const int jb_n = (NP + 15) / 16;               // blocks of 16 entries
-      const int tot = rin * S * (QC > 1 ? QC / 2 : 1) * jb_n * 32;
-      for (int e = tid; e < tot; e += blockDim.x) {
-        constexpr int QH = QC > 1 ? QC / 2 : 1;      // chunk pairs (the halo form has QC >= 2)
-        const int qlo = e & 1, jj = (e >> 1) & 15;
-        int blk = e >> 5;
-        const int jb = blk % jb_n; blk /= jb_n;
-        const int qh = blk % QH; blk /= QH;
-        const int par = blk % S, ri = blk / S;
-        const int j = jb * 16 + jj;
-        if (j >= NP) continue;
-        const int q = 2 * qh + qlo;
-        const int yi = y0 * S - 1 + ri;
-        const int xi = S == 1 ? x0 + j - 1 : (par == 0 ? 2 * (x0 + j) - 1 : 2 * (x0 + j));
-        bool inside = yi >= 0 && yi < H && xi >= 0 && xi < H;
-        if (MODE == 2) inside = inside && !(yi & 1) && !(xi & 1);   // the inserted zeros
-        const int ys = MODE == 2 ? yi >> 1 : yi, xs = MODE == 2 ? xi >> 1 : xi;
-        const __nv_bfloat16* src = inside ? in + (((int64_t)b * Hs + ys) * Hs + xs) * CIN + q * 8 : in;
-        cp_async16(sa32 + (uint32_t)(((ri * QC + q) * S + par) * NP * 16 + j * 16), src,
-                   inside ? 16u : 0u);
-      }
-    } else {                                         // CIN = 2: k = 2 tap + ci, taps 0..15
-      const int p = tid & 127, par = tid >> 7;
-      const int m = t * 128 + p;
-      const int b = m / (Ho * Ho), r = m - b * (Ho * Ho), yo = r / Ho, xo = r - yo * Ho;
-      const int y0 = yo * S - 1, x0 = xo * S - 1;
+  auto stage = [&](int t) {                          // k = 2 tap + ci, taps 0..15 (>= 9: zeros)
+    const int p = tid & 127, par = tid >> 7;
+    const int m = t * 128 + p;
+    const int b = m / (H * H), r = m - b * (H * H), yo = r / H, xo = r - yo * H;
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int tap = par + 2 * i;
-        const int dy = tap / 3, dx = tap % 3;
-        const bool inside = tap < 9 && m < M && y0 + dy >= 0 && y0 + dy < H && x0 + dx >= 0 &&
-                            x0 + dx < H;
-        const __nv_bfloat16* src =
-            inside ? in + (((int64_t)b * H + y0 + dy) * H + x0 + dx) * CIN : in;
-        cp_async4(sa32 + cm_off(p, 2 * tap, 128), src, inside ? 4u : 0u);
-      }
+    for (int i = 0; i < 8; ++i) {
+      const int tap = par + 2 * i;
+      const int dy = tap / 3, dx = tap % 3;
+      const bool inside = tap < 9 && m < M && yo + dy - 1 >= 0 && yo + dy - 1 < H &&
+                          xo + dx - 1 >= 0 && xo + dx - 1 < H;
+      const __nv_bfloat16* src =
+          inside ? in + (((int64_t)b * H + yo + dy - 1) * H + xo + dx - 1) * CIN : in;
+      cp_async4(sa32 + cm_off(p, 2 * tap, 128), src, inside ? 4u : 0u);
     }
   };
 
@@ -634,35 +563,13 @@ __global__ void __launch_bounds__(256) k_conv_fwd_tc(const __nv_bfloat16* __rest
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tslot;
-  const uint64_t bd0 = umma_desc(sb32);
+  const uint64_t bd0 = umma_desc(sb32), ad0 = umma_desc(sa32);
   for (; tile < n_tiles; tile += gridDim.x) {
     if (tid == 0) {
-      if (HALO) {
-        constexpr int SPT = CIN / 16;                // K slices per tap
-        for (int r = 0; r < RT; ++r) {
-#pragma unroll 1
-          for (int tap = 0; tap < 9; ++tap) {
-            const int dy = tap / 3, dx = tap % 3;
-            const int par = S == 1 ? 0 : (dx == 1 ? 1 : 0);
-            const int jo = S == 1 ? dx : (dx == 2 ? 1 : 0);
-            const int ri = r * S + dy;
 #pragma unroll
-            for (int sp = 0; sp < SPT; ++sp) {
-              const uint32_t a_addr =
-                  sa32 + (uint32_t)(((ri * QC + 2 * sp) * S + par) * NP * 16 + jo * 16);
-              const int sl = tap * SPT + sp;
-              umma_bf16(tmem + (uint32_t)(r * COUT), umma_desc(a_addr, (uint32_t)HBLK, 128u),
-                        bd0 + (uint64_t)((sl * B_SL) >> 4), IDESC, sl > 0 ? 1u : 0u);
-            }
-          }
-        }
-      } else {
-        const uint64_t ad0 = umma_desc(sa32);
-#pragma unroll 1
-        for (int sl = 0; sl < NSL; ++sl)
-          umma_bf16(tmem, ad0 + (uint64_t)((sl * A_SL) >> 4), bd0 + (uint64_t)((sl * B_SL) >> 4),
-                    IDESC, sl > 0 ? 1u : 0u);
-      }
+      for (int sl = 0; sl < NSL; ++sl)
+        umma_bf16(tmem, ad0 + (uint64_t)((sl * A_SL) >> 4), bd0 + (uint64_t)((sl * B_SL) >> 4),
+                  IDESC, sl > 0 ? 1u : 0u);
       umma_commit(&mbar);
     }
     if (warp == 0) {
@@ -683,50 +590,22 @@ __global__ void __launch_bounds__(256) k_conv_fwd_tc(const __nv_bfloat16* __rest
     if (ok) {
       const int quarter = warp & 3, half = warp >> 2;
       const int p = quarter * 32 + lane;
-      // RT = 2: warp half h reads accumulator h (all columns); RT = 1: column half h
-      const int r = HALO && RT == 2 ? half : 0;
-      const int cb = HALO && RT == 2 ? 0 : half * (COUT / 2);
-      const int ce = HALO && RT == 2 ? COUT : cb + COUT / 2;
-      int64_t m;
-      bool valid;
-      if (HALO) {
-        const int b = tile / ((Ho / RT) * NCB), rem = tile - b * ((Ho / RT) * NCB);
-        const int y = (rem / NCB) * RT + r, x0 = (rem - (rem / NCB) * NCB) * CW;
-        m = ((int64_t)b * Ho + y) * Ho + x0 + p;
-        valid = p < CW;
-      } else {
-        m = (int64_t)tile * 128 + p;
-        valid = m < M;
+      const int c0 = half * (COUT / 2);
+      const int64_t m = (int64_t)tile * 128 + p;
+      uint32_t v[16];
+      tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
+      uint32_t pk[8], pos = 0;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        pk[j] = pack_bf16(fmaxf(__uint_as_float(v[2 * j]) + sbias[c0 + 2 * j], 0.f),
+                          fmaxf(__uint_as_float(v[2 * j + 1]) + sbias[c0 + 2 * j + 1], 0.f));
+        pos |= pos_bits(pk[j]) << (2 * j);
       }
-      if (!(HALO && RT == 2 && quarter * 32 >= Ho)) {   // whole warp past the row: nothing to read
-        for (int c0 = cb; c0 < ce; c0 += 16) {
-          uint32_t v[16];
-          tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(r * COUT + c0), v);
-          uint32_t pk[8];
-          if (MODE == 0) {
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-              pk[j] = pack_bf16(fmaxf(__uint_as_float(v[2 * j]) + sbias[c0 + 2 * j], 0.f),
-                                fmaxf(__uint_as_float(v[2 * j + 1]) + sbias[c0 + 2 * j + 1], 0.f));
-          } else {
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-              pk[j] = pack_bf16(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
-            if (mask && valid) {
-              const int4* mk = reinterpret_cast<const int4*>(mask + m * COUT + c0);
-              const int4 m0 = __ldg(mk), m1 = __ldg(mk + 1);
-              const uint32_t mw[8] = {(uint32_t)m0.x, (uint32_t)m0.y, (uint32_t)m0.z, (uint32_t)m0.w,
-                                      (uint32_t)m1.x, (uint32_t)m1.y, (uint32_t)m1.z, (uint32_t)m1.w};
-#pragma unroll
-              for (int j = 0; j < 8; ++j) pk[j] = relu_mask(pk[j], mw[j]);
-            }
-          }
-          if (valid) {
-            int4* o = reinterpret_cast<int4*>(out + m * COUT + c0);
-            o[0] = make_int4(pk[0], pk[1], pk[2], pk[3]);
-            o[1] = make_int4(pk[4], pk[5], pk[6], pk[7]);
-          }
-        }
+      if (m < M) {
+        int4* o = reinterpret_cast<int4*>(out + m * COUT + c0);
+        o[0] = make_int4(pk[0], pk[1], pk[2], pk[3]);
+        o[1] = make_int4(pk[4], pk[5], pk[6], pk[7]);
+        if (bits16) bits16[2 * m + half] = (uint16_t)pos;
       }
     }
     cp_async_wait_all();
@@ -736,11 +615,11 @@ __global__ void __launch_bounds__(256) k_conv_fwd_tc(const __nv_bfloat16* __rest
     tc_fence_after();
     if (!ok) break;
   }
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
 }
 
 // ---- L2-L5 forward and input gradients, TMA-fed and pipelined --------------------------------------
-// The same convolutions as k_conv_fwd_tc's halo form (CIN % 16 == 0), one output row of CW <= 128
+// Implicit GEMMs as in k_conv1_fwd_tc (CIN % 16 == 0 here), one output row of CW <= 128
 // columns per tile, with the roles of a block split so that copies, tensor-core work and the
 // accumulator read-back of different tiles overlap:
 //   warp 0      issues the tile's input copies with the tensor memory accelerator (TMA) into one of
@@ -750,9 +629,11 @@ __global__ void __launch_bounds__(256) k_conv_fwd_tc(const __nv_bfloat16* __rest
 //               MMAs (tap by tap, K = 16 per MMA) once its stage is full and its accumulator free;
 //               their completion frees the stage and marks the accumulator full;
 //   warps 2-9   two groups of four that take alternate tiles: read the tile's accumulator back
-//               (warp w: lanes 32 (w % 4) .., all COUT columns, one wait for all the loads), add the
-//               bias and apply the ReLU (MODE 0) or the mask (MODE 1), store bf16, and release the
-//               accumulator.
+//               (warp w: lanes 32 (w % 4) .., all COUT columns, one wait for all the loads) and
+//               release it, add the bias and apply the ReLU (MODE 0; with `bits`, also store one
+//               bit per channel where the stored value is positive) or multiply by the previous
+//               layer's ReLU mask given as such bits (MODE 1, 2), and write bf16 through shared
+//               memory and a tensor store.
 // Stages and accumulators are handed over through mbarriers (copy bytes, MMA commits, arrivals); every
 // wait is bounded and a wait that runs out raises the timeout flag and ends the block's loop.
 // Input views for the copies (NHWC bf16, fully packed): S = 1: (CIN, W, H, B); S = 2: (CIN, 2, W/2,
@@ -840,10 +721,12 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_conv_tma(const __grid_consta
                                                              const __grid_constant__ CUtensorMap omap,
                                                              const __nv_bfloat16* __restrict__ w,
                                                              const float* __restrict__ bias,
-                                                             const __nv_bfloat16* __restrict__ mask,
+                                                             const uint32_t* __restrict__ mbits,
+                                                             uint32_t* __restrict__ bits,
                                                              __nv_bfloat16* __restrict__ out, int B,
                                                              int H, int ns, unsigned int* flag) {
   static_assert(CIN % 16 == 0 && (MODE == 0 || S == 1), "halo form; gradients on the G grid");
+  constexpr int BW = COUT / 32;                      // mask words per pixel
   constexpr int KR = 9 * CIN, SPT = CIN / 16, QC = CIN / 8;
   constexpr int B_SL = COUT / 8 * 256;
   constexpr uint32_t IDESC = umma_idesc_bf16(128, COUT);
@@ -1031,29 +914,37 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_conv_tma(const __grid_consta
           if (lane == 0) mbar_arrive(&acce[acc]);
         }
         if (live && valid) {
+          uint32_t mw[BW > 0 ? BW : 1], pw[BW > 0 ? BW : 1];
+#pragma unroll
+          for (int k = 0; k < BW; ++k) {
+            pw[k] = 0u;
+            mw[k] = (MODE != 0 && mbits) ? __ldg(mbits + m * BW + k) : 0xffffffffu;
+          }
 #pragma unroll
           for (int c0 = 0; c0 < COUT; c0 += 8) {     // one 16-byte chunk: 8 channels
             uint32_t pk[4];
             if (MODE == 0) {
 #pragma unroll
-              for (int j = 0; j < 4; ++j)
+              for (int j = 0; j < 4; ++j) {
                 pk[j] = pack_bf16(fmaxf(__uint_as_float(v[c0 + 2 * j]) + sbias[c0 + 2 * j], 0.f),
                                   fmaxf(__uint_as_float(v[c0 + 2 * j + 1]) + sbias[c0 + 2 * j + 1], 0.f));
+                pw[c0 >> 5] |= pos_bits(pk[j]) << ((c0 & 31) + 2 * j);
+              }
             } else {
+              const uint32_t b8 = mw[c0 >> 5] >> (c0 & 31);
 #pragma unroll
               for (int j = 0; j < 4; ++j)
-                pk[j] = pack_bf16(__uint_as_float(v[c0 + 2 * j]), __uint_as_float(v[c0 + 2 * j + 1]));
-              if (mask) {
-                const int4 mw = __ldg(reinterpret_cast<const int4*>(mask + m * COUT + c0));
-                pk[0] = relu_mask(pk[0], (uint32_t)mw.x);
-                pk[1] = relu_mask(pk[1], (uint32_t)mw.y);
-                pk[2] = relu_mask(pk[2], (uint32_t)mw.z);
-                pk[3] = relu_mask(pk[3], (uint32_t)mw.w);
-              }
+                pk[j] = keep_by_bits(
+                    pack_bf16(__uint_as_float(v[c0 + 2 * j]), __uint_as_float(v[c0 + 2 * j + 1])),
+                    b8 >> (2 * j));
             }
             const uint32_t dst = obuf + (uint32_t)(q * RB + (((c0 >> 3) ^ swz) << 4));
             asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(pk[0]),
                          "r"(pk[1]), "r"(pk[2]), "r"(pk[3]) : "memory");
+          }
+          if (MODE == 0 && bits) {
+#pragma unroll
+            for (int k = 0; k < BW; ++k) bits[m * BW + k] = pw[k];
           }
         }
       }
@@ -1556,9 +1447,9 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // memory next to the weights (4, 3 or 2), persistent blocks.
 template <int CIN, int COUT, int S, int MODE>
 int conv_tma(const __nv_bfloat16* in, const __nv_bfloat16* w, const float* bias,
-             const __nv_bfloat16* mask, __nv_bfloat16* out, int B, int H, int sms, cudaStream_t st,
-             unsigned int* flag) {
-  // MODE 2: G is H/2 x H/2, a tile row holds one column parity (H/2 columns)
+             const uint32_t* mbits, uint32_t* bits, __nv_bfloat16* out, int B, int H, int sms,
+             cudaStream_t st, unsigned int* flag) {
+  // MODE 2: G is H/2 x H/2; a tile covers CW of its columns, both output column parities
   constexpr int ROWS = MODE == 2 ? 2 : 3;
   const int Ho = H / S, Wt = MODE == 2 ? H / 2 : Ho;
   const int CW = Wt > 128 ? 128 : Wt, NP = CW + 2;
@@ -1629,50 +1520,40 @@ int conv_tma(const __nv_bfloat16* in, const __nv_bfloat16* w, const float* bias,
                                            512 / (kTmaAcc * NPAR * COUT)}));
   const int64_t tiles = (int64_t)B * Ho * (Wt / CW);
   const int grid = (int)std::min<int64_t>(tiles, (int64_t)sms * per_sm);
-  fn<<<grid, kTmaThreads, smem, st>>>(map, omap, w, bias, mask, out, B, H, ns, flag);
+  fn<<<grid, kTmaThreads, smem, st>>>(map, omap, w, bias, mbits, bits, out, B, H, ns, flag);
   GFH_CUDA_TRY(cudaGetLastError());
   return GFH_OK;
 }
 
+// One 3x3 layer: forward (MODE 0) or input gradient (MODE 1: stride-1 layer, MODE 2: stride-2
+// layer; `in` the gradient in the layer's pre-activation, `w` the layer's weights).  bits (MODE 0,
+// nullable): one bit per output channel, set where the stored value is positive, COUT / 32 words
+// per pixel.  mbits (MODE 1, 2, nullable): such bits of the previous layer's output, the ReLU mask
+// the stored gradient is multiplied by.
 template <int CIN, int COUT, int S, int MODE = 0>
 int conv_fwd(const __nv_bfloat16* in, const __nv_bfloat16* w, const float* bias,
-             const __nv_bfloat16* mask, __nv_bfloat16* out, int B, int H, int sms, cudaStream_t st,
-             unsigned int* flag) {
-  // the halo form's forward layers and input gradients run on the TMA-fed pipeline
-  if constexpr (CIN % 16 == 0)
-    return conv_tma<CIN, COUT, S, MODE>(in, w, bias, mask, out, B, H, sms, st, flag);
-  else {
-    constexpr bool HALO = CIN % 8 == 0;
-    constexpr int K = (9 * CIN + 15) / 16 * 16;
-    const int Ho = H / S;
-    // tiles are output rows (two when they are at most 64 wide), cut into blocks of 128 columns
-    if (HALO && ((Ho > 128 && Ho % 128) || (Ho <= 64 && Ho % 2))) return GFH_ERR_ARG;
-    if (MODE == 2 && H % 2) return GFH_ERR_ARG;
-    const int RT = HALO && Ho <= 64 ? 2 : 1;
-    const int CW = Ho > 128 ? 128 : Ho;
-    // halo: rows x chunks x parities x (CW + 2) entries of 16 bytes, plus the dropped rows'
-    // over-read (at most 128 entries past a block start); im2col: K/16 slices of 128 x 16
-    const size_t a_bytes =
-        HALO ? (size_t)((RT - 1) * S + 3) * (CIN / 8) * S * (CW + 2) * 16 + 128 * 16
-             : (size_t)(K / 16) * (128 / 8 * 256);
-    const size_t smem = (size_t)(K / 16) * (COUT / 8 * 256) + a_bytes;
-    if (smem > kMaxSmemBytes - 4096) return GFH_ERR_SIZE;
-    const int tcols = RT * COUT < 32 ? 32 : RT * COUT;                   // power of two here
-    auto fn = k_conv_fwd_tc<CIN, COUT, S, MODE>;
+             const uint32_t* mbits, uint32_t* bits, __nv_bfloat16* out, int B, int H, int sms,
+             cudaStream_t st, unsigned int* flag) {
+  if constexpr (CIN % 16 == 0) {
+    return conv_tma<CIN, COUT, S, MODE>(in, w, bias, mbits, bits, out, B, H, sms, st, flag);
+  } else {
+    static_assert(CIN == 2 && COUT == 32 && S == 1 && MODE == 0, "the first layer's forward");
+    (void)mbits;
+    // weights: 2 K slices of 32 rows; A: 2 K slices of 128 rows
+    constexpr size_t smem = 2 * (32 / 8 * 256) + 2 * (128 / 8 * 256);
+    auto fn = k_conv1_fwd_tc;
     GFH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    GFH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     // resident blocks per SM: shared memory (with the static part and the per-block reservation),
-    // registers, 8 warps of 2048 threads, tensor-memory columns
+    // registers, 8 warps of 2048 threads, 32 tensor-memory columns each
     cudaFuncAttributes fa{};
     GFH_CUDA_TRY(cudaFuncGetAttributes(&fa, fn));
     const int regs = std::max(1, (fa.numRegs + 7) / 8 * 8);
     const int per_sm =
         std::max(1, std::min({(int)(kSmemPerSm / (smem + fa.sharedSizeBytes + 1024)),
-                              65536 / (regs * 256), 8, 512 / tcols}));
-    const int64_t tiles =
-        HALO ? (int64_t)B * (Ho / RT) * (Ho / CW) : ((int64_t)B * Ho * Ho + 127) / 128;
+                              65536 / (regs * 256), 8, 512 / 32}));
+    const int64_t tiles = ((int64_t)B * H * H + 127) / 128;
     const int grid = (int)std::min<int64_t>(tiles, (int64_t)sms * per_sm);
-    fn<<<grid, 256, smem, st>>>(in, w, bias, mask, out, B, H, tcols, flag);
+    fn<<<grid, 256, smem, st>>>(in, w, bias, out, reinterpret_cast<uint16_t*>(bits), B, H, flag);
     GFH_CUDA_TRY(cudaGetLastError());
     return GFH_OK;
   }
@@ -1808,6 +1689,7 @@ struct gfh_cnn {
   float *pooled = nullptr, *logits = nullptr, *dlogits = nullptr, *loss = nullptr;
   float* part = nullptr;                                           // gradient partial sums
   __nv_bfloat16* img8 = nullptr;                                   // input padded to 8 channels
+  uint32_t* mbits[5] = {};                                         // ReLU masks of a1 .. a4 (1..4)
 };
 
 namespace {
@@ -1841,16 +1723,23 @@ int refresh_bf16(gfh_cnn* n) {
   return GFH_OK;
 }
 
-int forward(gfh_cnn* n, const __nv_bfloat16* img, int B) {
+// Forward pass; `masks`: also store the ReLU masks of a1 .. a4 (bits per channel) for the backward.
+int forward(gfh_cnn* n, const __nv_bfloat16* img, int B, bool masks) {
   cudaStream_t st = n->ctx->stream;
   const int sms = n->ctx->num_sms;
   const Layout& L = n->L;
   unsigned int* flag = n->ctx->d_flag;
-  int rc = conv_fwd<2, 32, 1>(img, n->wb[0], n->w + L.b[0], nullptr, n->act[1], B, 256, sms, st, flag);
-  if (!rc) rc = conv_fwd<32, 32, 2>(n->act[1], n->wb[1], n->w + L.b[1], nullptr, n->act[2], B, 256, sms, st, flag);
-  if (!rc) rc = conv_fwd<32, 64, 1>(n->act[2], n->wb[2], n->w + L.b[2], nullptr, n->act[3], B, 128, sms, st, flag);
-  if (!rc) rc = conv_fwd<64, 64, 2>(n->act[3], n->wb[3], n->w + L.b[3], nullptr, n->act[4], B, 128, sms, st, flag);
-  if (!rc) rc = conv_fwd<64, 64, 1>(n->act[4], n->wb[4], n->w + L.b[4], nullptr, n->act[5], B, 64, sms, st, flag);
+  uint32_t* const* mb = n->mbits;
+  int rc = conv_fwd<2, 32, 1>(img, n->wb[0], n->w + L.b[0], nullptr, masks ? mb[1] : nullptr,
+                              n->act[1], B, 256, sms, st, flag);
+  if (!rc) rc = conv_fwd<32, 32, 2>(n->act[1], n->wb[1], n->w + L.b[1], nullptr, masks ? mb[2] : nullptr,
+                                    n->act[2], B, 256, sms, st, flag);
+  if (!rc) rc = conv_fwd<32, 64, 1>(n->act[2], n->wb[2], n->w + L.b[2], nullptr, masks ? mb[3] : nullptr,
+                                    n->act[3], B, 128, sms, st, flag);
+  if (!rc) rc = conv_fwd<64, 64, 2>(n->act[3], n->wb[3], n->w + L.b[3], nullptr, masks ? mb[4] : nullptr,
+                                    n->act[4], B, 128, sms, st, flag);
+  if (!rc) rc = conv_fwd<64, 64, 1>(n->act[4], n->wb[4], n->w + L.b[4], nullptr, nullptr, n->act[5],
+                                    B, 64, sms, st, flag);
   if (rc) return rc;
   k_pool<<<(B * 4096 + 255) / 256, 256, 0, st>>>(n->act[5], n->pooled, B);
   k_head_fwd<<<B, 256, 0, st>>>(n->pooled, n->w + L.wh, n->w + L.bh, n->w + L.bnull, n->logits);
@@ -1872,13 +1761,13 @@ int backward(gfh_cnn* n, const __nv_bfloat16* img, const int32_t* labels, int B)
   k_head_dgrad<<<(B * 4096 + 255) / 256, 256, 0, st>>>(n->dlogits, n->w + L.wh, n->act[5], n->dact[5], B);
   GFH_CUDA_TRY(cudaGetLastError());
   int rc = conv_wgrad_tc<64, 64, 1>(n->dact[5], n->act[4], n->gw + L.w[4], n->gw + L.b[4], B, 64, n->part, st, flag);
-  if (!rc) rc = conv_fwd<64, 64, 1, 1>(n->dact[5], n->wb[4], nullptr, n->act[4], n->dact[4], B, 64, sms, st, flag);
+  if (!rc) rc = conv_fwd<64, 64, 1, 1>(n->dact[5], n->wb[4], nullptr, n->mbits[4], nullptr, n->dact[4], B, 64, sms, st, flag);
   if (!rc) rc = conv_wgrad_tc<64, 64, 2>(n->dact[4], n->act[3], n->gw + L.w[3], n->gw + L.b[3], B, 128, n->part, st, flag);
-  if (!rc) rc = conv_fwd<64, 64, 1, 2>(n->dact[4], n->wb[3], nullptr, n->act[3], n->dact[3], B, 128, sms, st, flag);
+  if (!rc) rc = conv_fwd<64, 64, 1, 2>(n->dact[4], n->wb[3], nullptr, n->mbits[3], nullptr, n->dact[3], B, 128, sms, st, flag);
   if (!rc) rc = conv_wgrad_tc<32, 64, 1>(n->dact[3], n->act[2], n->gw + L.w[2], n->gw + L.b[2], B, 128, n->part, st, flag);
-  if (!rc) rc = conv_fwd<64, 32, 1, 1>(n->dact[3], n->wb[2], nullptr, n->act[2], n->dact[2], B, 128, sms, st, flag);
+  if (!rc) rc = conv_fwd<64, 32, 1, 1>(n->dact[3], n->wb[2], nullptr, n->mbits[2], nullptr, n->dact[2], B, 128, sms, st, flag);
   if (!rc) rc = conv_wgrad_tc<32, 32, 2>(n->dact[2], n->act[1], n->gw + L.w[1], n->gw + L.b[1], B, 256, n->part, st, flag);
-  if (!rc) rc = conv_fwd<32, 32, 1, 2>(n->dact[2], n->wb[1], nullptr, n->act[1], n->dact[1], B, 256, sms, st, flag);
+  if (!rc) rc = conv_fwd<32, 32, 1, 2>(n->dact[2], n->wb[1], nullptr, n->mbits[1], nullptr, n->dact[1], B, 256, sms, st, flag);
   if (rc) return rc;
   return conv1_wgrad(n->dact[1], img, n->img8, n->gw + L.w[0], n->gw + L.b[0], B, kImg, n->part, st, flag);
 }
@@ -1905,6 +1794,8 @@ extern "C" int gfh_cnn_create(gfh_ctx* ctx, int32_t max_batch, uint64_t seed, gf
                o_dlog = take((size_t)B * kClasses * 4), o_loss = take((size_t)B * 4),
                o_part = take(grad_partial_floats(B) * 4),
                o_img8 = take((size_t)B * kImg * kImg * 16);
+  size_t o_mb[5] = {};
+  for (int l = 1; l < 5; ++l) o_mb[l] = take(act_elems(l, B) / 8);   // one bit per element
   if (cudaSetDevice(ctx->device) != cudaSuccess) { delete n; return GFH_ERR_CUDA; }
   if (cudaMalloc(&n->buf, off) != cudaSuccess) { delete n; return GFH_ERR_NOMEM; }
   char* base = (char*)n->buf;
@@ -1919,6 +1810,7 @@ extern "C" int gfh_cnn_create(gfh_ctx* ctx, int32_t max_batch, uint64_t seed, gf
   n->dlogits = (float*)(base + o_dlog); n->loss = (float*)(base + o_loss);
   n->part = (float*)(base + o_part);
   n->img8 = (__nv_bfloat16*)(base + o_img8);
+  for (int l = 1; l < 5; ++l) n->mbits[l] = (uint32_t*)(base + o_mb[l]);
   float* h = new (std::nothrow) float[n->L.total];
   if (!h) { cudaFree(n->buf); delete n; return GFH_ERR_NOMEM; }
   init_params(h, n->L, seed);
@@ -2029,7 +1921,7 @@ extern "C" int gfh_cnn_read_tensor(gfh_cnn* n, int32_t which, int32_t batch, voi
 extern "C" int gfh_cnn_forward(gfh_cnn* n, const void* d_images, int32_t batch, float* d_logits) {
   if (!n || !d_images || batch < 1 || batch > n->max_batch) return GFH_ERR_ARG;
   GFH_CUDA_TRY(cudaSetDevice(n->ctx->device));
-  int rc = forward(n, (const __nv_bfloat16*)d_images, batch);
+  int rc = forward(n, (const __nv_bfloat16*)d_images, batch, false);
   if (rc) return rc;
   if (d_logits)
     GFH_CUDA_TRY(cudaMemcpyAsync(d_logits, n->logits, (size_t)batch * kClasses * 4,
@@ -2041,7 +1933,7 @@ extern "C" int gfh_cnn_gradients(gfh_cnn* n, const void* d_images, const int32_t
                                  int32_t batch, float* h_loss) {
   if (!n || !d_images || !d_labels || batch < 1 || batch > n->max_batch) return GFH_ERR_ARG;
   GFH_CUDA_TRY(cudaSetDevice(n->ctx->device));
-  int rc = forward(n, (const __nv_bfloat16*)d_images, batch);
+  int rc = forward(n, (const __nv_bfloat16*)d_images, batch, true);
   if (!rc) rc = backward(n, (const __nv_bfloat16*)d_images, d_labels, batch);
   if (rc) return rc;
   if (h_loss) {
@@ -2179,13 +2071,13 @@ extern "C" int gfh_conv3x3(gfh_ctx* ctx, int32_t mode, int32_t cin, int32_t cout
   }
 #define GFH_CONV_CASE(CI, CO, S)                                                                   \
   if (cin == CI && cout == CO && stride == S) {                                                    \
-    if (mode == 0) return conv_fwd<CI, CO, S>(in, w, d_bias, nullptr, (__nv_bfloat16*)d_res, batch, h, sms, st, ctx->d_flag); \
+    if (mode == 0) return conv_fwd<CI, CO, S>(in, w, d_bias, nullptr, nullptr, (__nv_bfloat16*)d_res, batch, h, sms, st, ctx->d_flag); \
     if (mode == 1) {                                                                               \
       const int64_t n_el = (int64_t)batch * (h / S) * (h / S) * CO;                                \
       __nv_bfloat16* g = (__nv_bfloat16*)ctx->pm_buf;                                              \
       k_mask_grad<<<(unsigned)((n_el + 255) / 256), 256, 0, st>>>(dout, out, g, n_el);              \
       GFH_CUDA_TRY(cudaGetLastError());                                                            \
-      return conv_fwd<CO, CI, 1, S == 1 ? 1 : 2>(g, w, nullptr, nullptr, (__nv_bfloat16*)d_res,     \
+      return conv_fwd<CO, CI, 1, S == 1 ? 1 : 2>(g, w, nullptr, nullptr, nullptr, (__nv_bfloat16*)d_res, \
                                                  batch, h, sms, st, ctx->d_flag);                  \
     }                                                                                              \
     if (mode == 2) {                                                                               \
@@ -2198,7 +2090,7 @@ extern "C" int gfh_conv3x3(gfh_ctx* ctx, int32_t mode, int32_t cin, int32_t cout
     return GFH_ERR_ARG;                                                                            \
   }
   if (cin == 2 && cout == 32 && stride == 1) {                      // first layer: no input gradient
-    if (mode == 0) return conv_fwd<2, 32, 1>(in, w, d_bias, nullptr, (__nv_bfloat16*)d_res, batch, h, sms, st, ctx->d_flag);
+    if (mode == 0) return conv_fwd<2, 32, 1>(in, w, d_bias, nullptr, nullptr, (__nv_bfloat16*)d_res, batch, h, sms, st, ctx->d_flag);
     if (mode == 2) {
       const int64_t n_el = (int64_t)batch * h * h * 32;
       __nv_bfloat16* g = (__nv_bfloat16*)((char*)ctx->pm_buf + part_bytes);
