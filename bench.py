@@ -1035,11 +1035,11 @@ _NET_MACS = [256 * 256 * 32 * 18, 128 * 128 * 32 * 288, 128 * 128 * 64 * 288, 64
              64 * 64 * 64 * 576]
 NET_FWD_FLOP = 2.0 * sum(_NET_MACS)
 NET_TRAIN_FLOP = 2.0 * (2 * sum(_NET_MACS) + sum(_NET_MACS[1:]))
-# kernels one AdamW step launches: forward 5 convolutions + pool + head + softmax/CE; backward the
-# head (weights, chunk sum, input), 4 input gradients, 4 weight gradients (bias sums inside) with
-# their weight and bias chunk sums, the first layer's padding, weight gradient and two chunk sums;
-# optimiser, then 5 bf16 weight copies
-TRAIN_LAUNCHES = 8 + 3 + 4 + 4 * 3 + 4 + 1 + 5
+# kernels one AdamW step launches: forward the image padded to 8 channels, 5 convolutions, pool,
+# head, softmax/CE; backward the head (weights, chunk sum, input), 4 input gradients, 5 weight
+# gradients (bias sums inside) with their weight and bias chunk sums; optimiser, then 5 bf16
+# weight copies
+TRAIN_LAUNCHES = 9 + 3 + 4 + 5 * 3 + 1 + 5
 
 
 def run_train(args):

@@ -471,16 +471,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Asynchronous global -> shared copy of 4 bytes; src_bytes = 0 fills the destination with zeros
-// (the source address is then not read).
-__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src, uint32_t src_bytes) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(src_bytes)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
-}
-
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -491,137 +481,15 @@ __device__ __forceinline__ void async_proxy_fence() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// ---- L1 forward on tcgen05: out[m][n] = relu(bias[n] + sum_k A[m][k] W[n][k]) -------------------
-// Implicit GEMM over the first layer's two input channels: m = output pixel (b, y, x), k = 2 tap + ci
-// (tap = 3 dy + dx; K = 18 padded with zeros to 32), A[m][k] = in[b][y + dy - 1][x + dx - 1][ci]
-// (zero outside the image).  A tile is 128 consecutive pixels staged im2col by cp.async (one 4-byte
-// pair per tap, zero-filled outside the image).  Persistent blocks of 256 threads keep the weights in
-// shared memory; one thread issues the tile's two MMAs (M = 128, N = 32, K = 16) into tensor memory
-// and commits them to an mbarrier; once they complete the next tile's copies start before the 8
-// warps read the accumulator back (warp w: rows 32 (w % 4) .., half w / 4 of the columns), add the
-// bias, apply the ReLU and store bf16.  With `bits`, each warp half also stores which of its 16
-// stored values are positive, one bit per channel: bits16[2 m + w / 4], bit i = channel 16 (w / 4) + i
-// (the ReLU mask the stride-2 input gradient of layer 2 applies).
-__global__ void __launch_bounds__(256) k_conv1_fwd_tc(const __nv_bfloat16* __restrict__ in,
-                                                      const __nv_bfloat16* __restrict__ w,
-                                                      const float* __restrict__ bias,
-                                                      __nv_bfloat16* __restrict__ out,
-                                                      uint16_t* __restrict__ bits16, int B, int H,
-                                                      unsigned int* flag) {
-  constexpr int CIN = 2, COUT = 32;
-  constexpr int KR = 9 * CIN, K = 32, NSL = K / 16;
-  constexpr int A_SL = 128 / 8 * 256, B_SL = COUT / 8 * 256;
-  constexpr uint32_t IDESC = umma_idesc_bf16(128, COUT);
-  constexpr uint32_t TCOLS = 32;
-  extern __shared__ __align__(1024) unsigned char smem_tc[];
-  unsigned char* sb = smem_tc;                       // weights
-  unsigned char* sa = smem_tc + NSL * B_SL;          // A (im2col)
-  __shared__ __align__(8) uint64_t mbar;
-  __shared__ uint32_t tslot;
-  __shared__ float sbias[COUT];
-  __shared__ int s_ok;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int M = B * H * H;
-  const int n_tiles = (M + 127) / 128;
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(&tslot)), "r"(TCOLS));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  // weights, K-major rows of the output channel, zero-padded K
-  for (int e = tid; e < COUT * K; e += blockDim.x) {
-    const int co = e / K, k = e % K;
-    *reinterpret_cast<__nv_bfloat16*>(sb + cm_off(co, k, COUT)) =
-        k < KR ? w[co * KR + k] : __float2bfloat16_rn(0.f);
-  }
-  for (int c = tid; c < COUT; c += blockDim.x) sbias[c] = bias[c];
-  if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
-  const uint32_t sa32 = smem_u32(sa), sb32 = smem_u32(sb);
-
-  auto stage = [&](int t) {                          // k = 2 tap + ci, taps 0..15 (>= 9: zeros)
-    const int p = tid & 127, par = tid >> 7;
-    const int m = t * 128 + p;
-    const int b = m / (H * H), r = m - b * (H * H), yo = r / H, xo = r - yo * H;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int tap = par + 2 * i;
-      const int dy = tap / 3, dx = tap % 3;
-      const bool inside = tap < 9 && m < M && yo + dy - 1 >= 0 && yo + dy - 1 < H &&
-                          xo + dx - 1 >= 0 && xo + dx - 1 < H;
-      const __nv_bfloat16* src =
-          inside ? in + (((int64_t)b * H + yo + dy - 1) * H + xo + dx - 1) * CIN : in;
-      cp_async4(sa32 + cm_off(p, 2 * tap, 128), src, inside ? 4u : 0u);
-    }
-  };
-
-  uint32_t parity = 0;
-  int tile = blockIdx.x;
-  if (tile < n_tiles) stage(tile);
-  cp_async_wait_all();
-  async_proxy_fence();
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = tslot;
-  const uint64_t bd0 = umma_desc(sb32), ad0 = umma_desc(sa32);
-  for (; tile < n_tiles; tile += gridDim.x) {
-    if (tid == 0) {
-#pragma unroll
-      for (int sl = 0; sl < NSL; ++sl)
-        umma_bf16(tmem, ad0 + (uint64_t)((sl * A_SL) >> 4), bd0 + (uint64_t)((sl * B_SL) >> 4),
-                  IDESC, sl > 0 ? 1u : 0u);
-      umma_commit(&mbar);
-    }
-    if (warp == 0) {
-      const bool mine = mbar_wait(&mbar, parity);
-      const bool all = __all_sync(0xffffffffu, mine) != 0;
-      if (lane == 0) {
-        s_ok = all ? 1 : 0;
-        if (!all) atomicOr(flag, GFH_FLAG_TIMEOUT);
-      }
-    }
-    parity ^= 1u;
-    __syncthreads();
-    const bool ok = s_ok != 0;
-    tc_fence_after();
-    // A is free: the next tile's copies fly while this tile's accumulator is read back
-    const int next = tile + gridDim.x;
-    if (ok && next < n_tiles) stage(next);
-    if (ok) {
-      const int quarter = warp & 3, half = warp >> 2;
-      const int p = quarter * 32 + lane;
-      const int c0 = half * (COUT / 2);
-      const int64_t m = (int64_t)tile * 128 + p;
-      uint32_t v[16];
-      tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
-      uint32_t pk[8], pos = 0;
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        pk[j] = pack_bf16(fmaxf(__uint_as_float(v[2 * j]) + sbias[c0 + 2 * j], 0.f),
-                          fmaxf(__uint_as_float(v[2 * j + 1]) + sbias[c0 + 2 * j + 1], 0.f));
-        pos |= pos_bits(pk[j]) << (2 * j);
-      }
-      if (m < M) {
-        int4* o = reinterpret_cast<int4*>(out + m * COUT + c0);
-        o[0] = make_int4(pk[0], pk[1], pk[2], pk[3]);
-        o[1] = make_int4(pk[4], pk[5], pk[6], pk[7]);
-        if (bits16) bits16[2 * m + half] = (uint16_t)pos;
-      }
-    }
-    cp_async_wait_all();
-    async_proxy_fence();
-    tc_fence_before();
-    __syncthreads();                                 // accumulator read, next A in place
-    tc_fence_after();
-    if (!ok) break;
-  }
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
-}
-
-// ---- L2-L5 forward and input gradients, TMA-fed and pipelined --------------------------------------
-// Implicit GEMMs as in k_conv1_fwd_tc (CIN % 16 == 0 here), one output row of CW <= 128
-// columns per tile, with the roles of a block split so that copies, tensor-core work and the
-// accumulator read-back of different tiles overlap:
+// ---- forward layers and input gradients on tcgen05, TMA-fed and pipelined ---------------------------
+// Implicit GEMM out[m][n] = relu(bias[n] + sum_k A[m][k] W[n][k]): m = output pixel (b, y, x),
+// k = tap * CIN + ci (tap = 3 dy + dx), A[m][k] = in[b][y S + dy - 1][x S + dx - 1][ci] (zero outside
+// the image); tcgen05.mma M = 128 output pixels x N = COUT x K = 16 (8-channel chunks as 16-byte
+// rows of K-major core matrices, taps addressed through descriptor offsets into the staged input
+// rows).  The first layer runs on its image padded to 8 channels (CIN = 8): a K slice is then two
+// taps of one row, one input entry apart.  One output row of CW <= 128 columns per tile, with the
+// roles of a block split so that copies, tensor-core work and the accumulator read-back of
+// different tiles overlap:
 //   warp 0      issues the tile's input copies with the tensor memory accelerator (TMA) into one of
 //               NS stage buffers: one box per (8-channel chunk, parity) of 3 input rows x NP
 //               entries x 16 bytes, zero-filled outside the image by the copy itself;
@@ -725,9 +593,15 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_conv_tma(const __grid_consta
                                                              uint32_t* __restrict__ bits,
                                                              __nv_bfloat16* __restrict__ out, int B,
                                                              int H, int ns, unsigned int* flag) {
-  static_assert(CIN % 16 == 0 && (MODE == 0 || S == 1), "halo form; gradients on the G grid");
+  static_assert((CIN % 16 == 0 || (CIN == 8 && S == 1 && MODE == 0)) && (MODE == 0 || S == 1),
+                "halo form; gradients on the G grid");
   constexpr int BW = COUT / 32;                      // mask words per pixel
-  constexpr int KR = 9 * CIN, SPT = CIN / 16, QC = CIN / 8;
+  // CIN = 8: the first layer on its image padded to 8 channels (2 real); a K slice of 16 is two
+  // taps (dx = 2 s, 2 s + 1) of one tap row, one entry apart, so a row takes 2 slices (the tap
+  // dx = 3 has zero weights): 6 slices
+  constexpr bool L1 = CIN == 8;
+  constexpr int KR = 9 * CIN, SPT = CIN / 16, QC = L1 ? 1 : CIN / 8;
+  constexpr int NSLW = L1 ? 6 : KR / 16;             // weight K slices
   constexpr int B_SL = COUT / 8 * 256;
   constexpr uint32_t IDESC = umma_idesc_bf16(128, COUT);
   constexpr int NPAR = MODE == 2 ? 2 : 1;          // column parities (accumulators) per tile
@@ -752,7 +626,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_conv_tma(const __grid_consta
     y = r / NCB;
     x0 = (r - y * NCB) * CW;
   };
-  const uint32_t sb32 = smem_u32(smem_tc), sa32 = sb32 + (uint32_t)(KR / 16 * B_SL);
+  const uint32_t sb32 = smem_u32(smem_tc), sa32 = sb32 + (uint32_t)(NSLW * B_SL);
   // output staging of the two epilogue groups, after the stages and the MMA over-read pad, aligned
   // to the 1024-byte swizzle atom: 128 rows (pixels) of COUT bf16, 16-byte chunks swizzled as the
   // output tensor map's 128-byte (COUT = 64) or 64-byte (COUT = 32) mode expects
@@ -767,8 +641,17 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_conv_tma(const __grid_consta
                      smem_u32(&tslot)), "r"(TCOLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  // weights, K-major rows of the output channel (MODE 1: transposed, taps flipped)
-  if (MODE == 0) {
+  // weights, K-major rows of the output channel (MODE 1: transposed, taps flipped; L1: w holds the
+  // layer's [co][tap][2] weights, placed at slice 2 dy + s, K element 8 h + ci for dx = 2 s + h)
+  if (L1) {
+    for (int e = tid; e < COUT * NSLW * 16; e += blockDim.x) {
+      const int co = e / (NSLW * 16), k = e % (NSLW * 16);
+      const int sl = k >> 4, hh = (k >> 3) & 1, ci = k & 7;
+      const int dy = sl >> 1, dx = 2 * (sl & 1) + hh;
+      *reinterpret_cast<__nv_bfloat16*>(smem_tc + cm_off(co, k, COUT)) =
+          (dx < 3 && ci < 2) ? w[co * 18 + (3 * dy + dx) * 2 + ci] : __float2bfloat16_rn(0.f);
+    }
+  } else if (MODE == 0) {
     for (int e = tid; e < COUT * (KR / 8); e += blockDim.x) {
       const int co = e / (KR / 8), k = (e % (KR / 8)) * 8;
       *reinterpret_cast<int4*>(smem_tc + cm_off(co, k, COUT)) =
@@ -781,6 +664,12 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_conv_tma(const __grid_consta
     }
   }
   for (int c = tid; c < COUT; c += blockDim.x) sbias[c] = MODE == 0 ? bias[c] : 0.f;
+  if (L1) {
+    // the zero-weight tap dx = 3 of the last row reads one entry past its box: zeros, not stale
+    // bits (0 x NaN would poison the pixel), in the slack no copy writes
+    for (int i = tid; i < (ns * STAGE + 128 * 16) / 16; i += blockDim.x)
+      *reinterpret_cast<int4*>(smem_tc + NSLW * B_SL + i * 16) = make_int4(0, 0, 0, 0);
+  }
   if (tid == 0) {
     for (int s = 0; s < ns; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
     for (int a = 0; a < kTmaAcc; ++a) { mbar_init(&accf[a], 1); mbar_init(&acce[a], kTmaGroupWarps); }
@@ -835,7 +724,14 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_conv_tma(const __grid_consta
         // tap and K slice, in 16-byte units (all offsets stay inside the 14-bit address field)
         const uint64_t ad0 = umma_desc(sa32 + (uint32_t)(slot * STAGE), (uint32_t)(S * BOXB), 128u);
         const uint32_t d_tmem = tmem + (uint32_t)(acc * NPAR * COUT);
-        if constexpr (MODE == 2) {
+        if constexpr (L1) {
+          // K halves one entry apart: the descriptor's leading byte offset is 16 bytes
+          const uint64_t a1 = umma_desc(sa32 + (uint32_t)(slot * STAGE), 16u, 128u);
+#pragma unroll
+          for (int sl = 0; sl < 6; ++sl)
+            umma_bf16(d_tmem, a1 + (uint64_t)((((sl >> 1) * NP + 2 * (sl & 1)) * 16) >> 4),
+                      bd0 + (uint64_t)((sl * B_SL) >> 4), IDESC, sl > 0 ? 1u : 0u);
+        } else if constexpr (MODE == 2) {
           int b, y, x0;
           geo(t, b, y, x0);
 #pragma unroll
@@ -1504,7 +1400,7 @@ int conv_tma(const __nv_bfloat16* in, const __nv_bfloat16* w, const float* bias,
   GFH_CUDA_TRY(cudaFuncGetAttributes(&fa, fn));
   // weights, stages, the over-read of the dropped MMA rows past the last stage, then (aligned to
   // 1024 bytes) the two epilogue groups' output staging of 128 rows x COUT bf16
-  const size_t w_bytes = (size_t)(9 * CIN / 16) * (COUT / 8 * 256);
+  const size_t w_bytes = (size_t)(CIN == 8 ? 6 : 9 * CIN / 16) * (COUT / 8 * 256);
   const size_t stage = (size_t)(CIN / 8) * S * tma_box_bytes(NP, ROWS);
   const size_t o_bytes = 2 * NPAR * 128 * COUT * 2 + 1024;
   const size_t room = kMaxSmemBytes - fa.sharedSizeBytes - 1024;
@@ -1534,29 +1430,19 @@ template <int CIN, int COUT, int S, int MODE = 0>
 int conv_fwd(const __nv_bfloat16* in, const __nv_bfloat16* w, const float* bias,
              const uint32_t* mbits, uint32_t* bits, __nv_bfloat16* out, int B, int H, int sms,
              cudaStream_t st, unsigned int* flag) {
-  if constexpr (CIN % 16 == 0) {
-    return conv_tma<CIN, COUT, S, MODE>(in, w, bias, mbits, bits, out, B, H, sms, st, flag);
-  } else {
-    static_assert(CIN == 2 && COUT == 32 && S == 1 && MODE == 0, "the first layer's forward");
-    (void)mbits;
-    // weights: 2 K slices of 32 rows; A: 2 K slices of 128 rows
-    constexpr size_t smem = 2 * (32 / 8 * 256) + 2 * (128 / 8 * 256);
-    auto fn = k_conv1_fwd_tc;
-    GFH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    // resident blocks per SM: shared memory (with the static part and the per-block reservation),
-    // registers, 8 warps of 2048 threads, 32 tensor-memory columns each
-    cudaFuncAttributes fa{};
-    GFH_CUDA_TRY(cudaFuncGetAttributes(&fa, fn));
-    const int regs = std::max(1, (fa.numRegs + 7) / 8 * 8);
-    const int per_sm =
-        std::max(1, std::min({(int)(kSmemPerSm / (smem + fa.sharedSizeBytes + 1024)),
-                              65536 / (regs * 256), 8, 512 / 32}));
-    const int64_t tiles = ((int64_t)B * H * H + 127) / 128;
-    const int grid = (int)std::min<int64_t>(tiles, (int64_t)sms * per_sm);
-    fn<<<grid, 256, smem, st>>>(in, w, bias, out, reinterpret_cast<uint16_t*>(bits), B, H, flag);
-    GFH_CUDA_TRY(cudaGetLastError());
-    return GFH_OK;
-  }
+  static_assert(CIN % 16 == 0 || CIN == 8, "16-byte channel chunks (the first layer padded to 8)");
+  return conv_tma<CIN, COUT, S, MODE>(in, w, bias, mbits, bits, out, B, H, sms, st, flag);
+}
+
+// The first layer's forward: the image [B][H][H][2] padded to 8 channels into img8, then the
+// TMA-fed convolution on it (w: the layer's [32][3][3][2] weights).
+int conv1_fwd(const __nv_bfloat16* img, __nv_bfloat16* img8, const __nv_bfloat16* w,
+              const float* bias, uint32_t* bits, __nv_bfloat16* out, int B, int H, int sms,
+              cudaStream_t st, unsigned int* flag) {
+  const int64_t P1 = (int64_t)B * H * H;
+  k_pad_channels<<<(unsigned)((P1 + 255) / 256), 256, 0, st>>>((const uint32_t*)img, (int4*)img8, P1);
+  GFH_CUDA_TRY(cudaGetLastError());
+  return conv_fwd<8, 32, 1>(img8, w, bias, nullptr, bits, out, B, H, sms, st, flag);
 }
 
 // Scratch floats of one layer's weight and bias gradients over M output pixels.
@@ -1657,12 +1543,16 @@ int conv_wgrad_tc(const __nv_bfloat16* G, const __nv_bfloat16* in, float* dw, fl
 }
 
 // First layer (2 input channels) weight and bias gradients, added into dw and db, from G1 (the
-// gradient in layer 1's pre-activation, stored masked); img8 holds B H H x 8 bf16 (the padded image).
+// gradient in layer 1's pre-activation, stored masked); img8 receives (padded = false) or already
+// holds (padded = true, as the forward left it) the image padded to 8 channels, B H H x 8 bf16.
 int conv1_wgrad(const __nv_bfloat16* g1, const __nv_bfloat16* in, __nv_bfloat16* img8, float* dw,
-                float* db, int B, int H, float* part, cudaStream_t st, unsigned int* flag) {
+                float* db, int B, int H, float* part, cudaStream_t st, unsigned int* flag,
+                bool padded) {
   const int64_t P1 = (int64_t)B * H * H;
-  k_pad_channels<<<(unsigned)((P1 + 255) / 256), 256, 0, st>>>((const uint32_t*)in, (int4*)img8, P1);
-  GFH_CUDA_TRY(cudaGetLastError());
+  if (!padded) {
+    k_pad_channels<<<(unsigned)((P1 + 255) / 256), 256, 0, st>>>((const uint32_t*)in, (int4*)img8, P1);
+    GFH_CUDA_TRY(cudaGetLastError());
+  }
   const int rc = wgrad_launch<8, 32, 1>(g1, img8, B, H, part, st, flag);
   if (rc) return rc;
   k_sum_chunks_l1<<<(576 + 255) / 256, 256, 0, st>>>(part, WT_CHUNKS1, dw);
@@ -1730,8 +1620,8 @@ int forward(gfh_cnn* n, const __nv_bfloat16* img, int B, bool masks) {
   const Layout& L = n->L;
   unsigned int* flag = n->ctx->d_flag;
   uint32_t* const* mb = n->mbits;
-  int rc = conv_fwd<2, 32, 1>(img, n->wb[0], n->w + L.b[0], nullptr, masks ? mb[1] : nullptr,
-                              n->act[1], B, 256, sms, st, flag);
+  int rc = conv1_fwd(img, n->img8, n->wb[0], n->w + L.b[0], masks ? mb[1] : nullptr, n->act[1],
+                     B, 256, sms, st, flag);
   if (!rc) rc = conv_fwd<32, 32, 2>(n->act[1], n->wb[1], n->w + L.b[1], nullptr, masks ? mb[2] : nullptr,
                                     n->act[2], B, 256, sms, st, flag);
   if (!rc) rc = conv_fwd<32, 64, 1>(n->act[2], n->wb[2], n->w + L.b[2], nullptr, masks ? mb[3] : nullptr,
@@ -1769,7 +1659,8 @@ int backward(gfh_cnn* n, const __nv_bfloat16* img, const int32_t* labels, int B)
   if (!rc) rc = conv_wgrad_tc<32, 32, 2>(n->dact[2], n->act[1], n->gw + L.w[1], n->gw + L.b[1], B, 256, n->part, st, flag);
   if (!rc) rc = conv_fwd<32, 32, 1, 2>(n->dact[2], n->wb[1], nullptr, n->mbits[1], nullptr, n->dact[1], B, 256, sms, st, flag);
   if (rc) return rc;
-  return conv1_wgrad(n->dact[1], img, n->img8, n->gw + L.w[0], n->gw + L.b[0], B, kImg, n->part, st, flag);
+  return conv1_wgrad(n->dact[1], img, n->img8, n->gw + L.w[0], n->gw + L.b[0], B, kImg, n->part, st,
+                     flag, true);
 }
 
 }  // namespace
@@ -2052,6 +1943,10 @@ extern "C" int gfh_conv3x3(gfh_ctx* ctx, int32_t mode, int32_t cin, int32_t cout
   const auto* dout = (const __nv_bfloat16*)d_dout;
   float* part = nullptr;
   size_t part_bytes = 0;
+  if (mode == 0 && cin == 2) {   // the image padded to 8 channels in the context scratch
+    const int rc = ensure_scratch(ctx, (size_t)batch * h * h * 16);
+    if (rc) return rc;
+  }
   if (mode == 1) {   // the masked gradient in the context scratch
     const int rc = ensure_scratch(ctx, (size_t)batch * (h / stride) * (h / stride) * cout * 2);
     if (rc) return rc;
@@ -2090,14 +1985,16 @@ extern "C" int gfh_conv3x3(gfh_ctx* ctx, int32_t mode, int32_t cin, int32_t cout
     return GFH_ERR_ARG;                                                                            \
   }
   if (cin == 2 && cout == 32 && stride == 1) {                      // first layer: no input gradient
-    if (mode == 0) return conv_fwd<2, 32, 1>(in, w, d_bias, nullptr, nullptr, (__nv_bfloat16*)d_res, batch, h, sms, st, ctx->d_flag);
+    if (mode == 0)
+      return conv1_fwd(in, (__nv_bfloat16*)ctx->pm_buf, w, d_bias, nullptr, (__nv_bfloat16*)d_res,
+                       batch, h, sms, st, ctx->d_flag);
     if (mode == 2) {
       const int64_t n_el = (int64_t)batch * h * h * 32;
       __nv_bfloat16* g = (__nv_bfloat16*)((char*)ctx->pm_buf + part_bytes);
       __nv_bfloat16* img8 = g + n_el;
       k_mask_grad<<<(unsigned)((n_el + 255) / 256), 256, 0, st>>>(dout, out, g, n_el);
       GFH_CUDA_TRY(cudaGetLastError());
-      return conv1_wgrad(g, in, img8, (float*)d_res, d_db, batch, h, part, st, ctx->d_flag);
+      return conv1_wgrad(g, in, img8, (float*)d_res, d_db, batch, h, part, st, ctx->d_flag, false);
     }
     return GFH_ERR_ARG;
   }
