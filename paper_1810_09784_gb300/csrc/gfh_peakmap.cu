@@ -72,8 +72,9 @@ __device__ __forceinline__ void eq_copy(Raw* dst, const Raw* src, bool ok) {
 //               of chunk c+1 and turn them into powers for the recurrence.
 // Rings: kEqDepth + 1 raw tiles, three power tiles, two mean tiles, two equalised tiles; one block
 // barrier per chunk.  The copies run kEqDepth chunks ahead so that memory latency stays off the
-// recurrence.
-constexpr int kEqWarps = 8;
+// recurrence, and a full chunk past the warm-up is one straight-line run of 32 updates, its loads
+// issued ahead of the chain.
+constexpr int kEqWarps = 16;
 constexpr int kEqHelpers = kEqWarps - 1;
 constexpr int kEqDepth = 4;
 constexpr int kEqRing = kEqDepth + 1;
@@ -142,18 +143,32 @@ __global__ void __launch_bounds__(32 * kEqWarps) k_equalise(In in, int n_fft, in
         const int nq = min(32, j_end - cb + 1);
         const float* row = Pt[c % 3][lane];
         float* srow = Sm[c & 1][lane];
+        if (nq == 32 && cb >= bin_lo - 1) {
+          // a full chunk past the warm-up (all but a few): straight-line code, so the chunk's
+          // loads and the P-only products run ahead of the chain of dependent updates
+          float P[32];
 #pragma unroll
-        for (int q = 0; q < 32; ++q) {
-          if (q < nq) {
-            const int j = cb + q;
-            const float P = row[q];
+          for (int q = 0; q < 32; ++q) P[q] = row[q];
+#pragma unroll
+          for (int q = 0; q < 32; ++q) {
             srow[q] = S;
-            if (j < bin_lo - 1) {
-              S = __fadd_rn(S, P);
-              if (j == bin_lo - 2) S = __fmul_rn(S, 1.0f / kWarm);
-            } else {
-              const float u = fminf(__fmul_rn(P, kGain), __fmul_rn(S, kClipGain));
-              S = __fadd_rn(S, __fmul_rn(kArWeight, __fsub_rn(u, S)));
+            const float u = fminf(__fmul_rn(P[q], kGain), __fmul_rn(S, kClipGain));
+            S = __fadd_rn(S, __fmul_rn(kArWeight, __fsub_rn(u, S)));
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < 32; ++q) {
+            if (q < nq) {
+              const int j = cb + q;
+              const float P = row[q];
+              srow[q] = S;
+              if (j < bin_lo - 1) {
+                S = __fadd_rn(S, P);
+                if (j == bin_lo - 2) S = __fmul_rn(S, 1.0f / kWarm);
+              } else {
+                const float u = fminf(__fmul_rn(P, kGain), __fmul_rn(S, kClipGain));
+                S = __fadd_rn(S, __fmul_rn(kArWeight, __fsub_rn(u, S)));
+              }
             }
           }
         }
