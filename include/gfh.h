@@ -441,7 +441,7 @@ int gfh_synth_images(gfh_ctx* ctx, uint64_t seed, int64_t sample0, int32_t batch
 /* The same images from peak lists: list l of `peaks` (each sorted by bin) into image l of d_images
  * [n_lists][256][256][2]; all maps share the band bin_lo..bin_hi and n_fft FFTs; d_nplane [n_lists].
  * Peaks outside the band are skipped; an FFT index >= n_fft sets the input flag (gfh_check).
- * Asynchronous. */
+ * GFH_ERR_ARG also for n_fft or nb of 2^24 or more.  Asynchronous. */
 int gfh_peaks_to_images(gfh_ctx* ctx, const gfh_peaks* peaks, int32_t n_fft, int32_t bin_lo,
                         int32_t bin_hi, const float* d_nplane, void* d_images);
 

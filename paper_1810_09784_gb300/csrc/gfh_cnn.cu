@@ -95,23 +95,34 @@ __global__ void k_synth_images(uint64_t seed, int64_t sample0, int n_fft, int bi
 }
 
 // Counts peaks per pixel: list l of the peak lists into image l (one 32-bit word per pixel,
-// zeroed before).
+// zeroed before).  A warp takes 32 consecutive peaks; sorted lists put runs of them in one pixel,
+// so lanes with the same pixel add their count in one atomic.
 __global__ void k_image_count(const uint32_t* __restrict__ fft_idx, const uint32_t* __restrict__ bin,
                               const int64_t* __restrict__ offsets, int n_fft, int bin_lo, int nb,
                               uint32_t* __restrict__ img, unsigned int* flag) {
-  const int l = blockIdx.y;
+  const int l = blockIdx.y, lane = threadIdx.x & 31;
   uint32_t* im = img + (int64_t)l * kImg * kImg;
   const int64_t p1 = offsets[l + 1];
-  for (int64_t p = offsets[l] + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < p1;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t i = fft_idx[p];
-    const int64_t jl = (int64_t)bin[p] - bin_lo;
-    if (i >= (uint32_t)n_fft) { atomicOr(flag, GFH_FLAG_FFT_RANGE); continue; }
-    if (jl < 0 || jl >= nb) continue;
-    // pixel whose range [tb N / 256, (tb + 1) N / 256) holds i: tb = (256 (i + 1) - 1) / N
-    const int tb = (int)(((int64_t)kImg * (i + 1) - 1) / n_fft);
-    const int fb = (int)(((int64_t)kImg * (jl + 1) - 1) / nb);
-    atomicAdd(im + tb * kImg + fb, 1u);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // the loop runs alike on all lanes of a warp (its bound is the warp's first peak)
+  for (int64_t q = offsets[l] + (int64_t)blockIdx.x * blockDim.x + (threadIdx.x - lane); q < p1;
+       q += stride) {
+    const int64_t p = q + lane;
+    int pix = -1;
+    if (p < p1) {
+      const uint32_t i = fft_idx[p];
+      const int64_t jl = (int64_t)bin[p] - bin_lo;
+      if (i >= (uint32_t)n_fft) atomicOr(flag, GFH_FLAG_FFT_RANGE);
+      else if (jl >= 0 && jl < nb) {
+        // pixel whose range [tb N / 256, (tb + 1) N / 256) holds i: tb = (256 (i + 1) - 1) / N
+        // (32-bit: the host keeps 256 n_fft and 256 nb below 2^32)
+        const int tb = (int)(((uint32_t)kImg * (i + 1u) - 1u) / (uint32_t)n_fft);
+        const int fb = (int)(((uint32_t)kImg * (uint32_t)(jl + 1) - 1u) / (uint32_t)nb);
+        pix = tb * kImg + fb;
+      }
+    }
+    const unsigned same = __match_any_sync(0xffffffffu, pix);
+    if (pix >= 0 && lane == __ffs(same) - 1) atomicAdd(im + pix, (uint32_t)__popc(same));
   }
 }
 
@@ -132,7 +143,9 @@ __global__ void k_image_finish(uint32_t* __restrict__ img, const float* __restri
 // over the complemented id; the first n tiles leave resid_n = max(0, 1 - p(null) - their score
 // sum).  With tau >= 0 the list stops at the smallest n <= k with resid_n <= tau (the rest of top is
 // -1), and a map whose resid_k exceeds tau is flagged for a full search; with tau < 0 all k tiles
-// are kept.  1024 threads per map: the class ranges and shares are computed once per class.
+// are kept.  1024 threads per map: the class ranges and shares are computed once per class.  For
+// k <= 512 only the k largest keys are found (radix selection) and sorted.
+constexpr int kProposeSelectMax = 512;   // k up to this: selection, then a sort of k keys
 __global__ void __launch_bounds__(1024) k_propose(const float* __restrict__ logits,
                                                   const float* __restrict__ gain, int k, float tau,
                                                   int32_t* __restrict__ top,
@@ -211,23 +224,95 @@ __global__ void __launch_bounds__(1024) k_propose(const float* __restrict__ logi
     kreg[r] = ((unsigned long long)bits << 32) | (unsigned long long)(0xffffu - (uint32_t)c);
   }
   __syncthreads();
+  if (k <= kProposeSelectMax) {
+    // The k largest keys (all keys differ: each holds its tile id) without sorting all 4096: the
+    // k-th largest key by an 8-bit-digit radix selection over its 48 significant bits (score bits
+    // 63..32 and complemented id 15..0; bits 31..16 are 0), then the keys at or above it gathered
+    // and sorted.
+    unsigned int* hist = reinterpret_cast<unsigned int*>(sbuf + kProposeSelectMax * 8);
+    __shared__ unsigned long long s_prefix;
+    __shared__ int s_rank, s_count;
+    unsigned long long prefix = 0ull, known = 0ull;    // digits fixed so far, and their bit mask
+    int rank = k;                                      // rank still wanted among the matching keys
+    for (int pass = 0; pass < 6; ++pass) {
+      const int shift = pass < 4 ? 56 - 8 * pass : 8 - 8 * (pass - 4);   // 56 48 40 32 8 0
+      for (int i = tid; i < 256; i += NT) hist[i] = 0u;
+      __syncthreads();
 #pragma unroll
-  for (int r = 0; r < PER; ++r) key[tid + r * NT] = kreg[r];
-  __syncthreads();
-  // bitonic sort, descending keys
-  for (int kk = 2; kk <= NCT; kk <<= 1) {
-    for (int j = kk >> 1; j > 0; j >>= 1) {
-      for (int i = tid; i < NCT; i += NT) {
-        const int o = i ^ j;
-        if (o > i) {
-          const unsigned long long ki = key[i], ko = key[o];
-          if (((i & kk) == 0) ? (ko > ki) : (ko < ki)) {
-            key[i] = ko;
-            key[o] = ki;
+      for (int r = 0; r < PER; ++r)
+        if ((kreg[r] & known) == prefix) atomicAdd(&hist[(kreg[r] >> shift) & 255u], 1u);
+      __syncthreads();
+      if (warp == 0) {
+        // lane l holds digits 255 - 8 l - 7 .. 255 - 8 l: counts of larger digits come first
+        unsigned int c[8], tot = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) { c[q] = hist[255 - 8 * lane - q]; tot += c[q]; }
+        unsigned int incl = tot;                       // inclusive scan over the lanes
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const unsigned int u = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += u;
+        }
+        unsigned int above = incl - tot;               // keys with a larger digit than this lane's
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          if (above < (unsigned int)rank && above + c[q] >= (unsigned int)rank) {
+            s_prefix = prefix | ((unsigned long long)(255 - 8 * lane - q) << shift);
+            s_rank = rank - (int)above;
           }
+          above += c[q];
         }
       }
       __syncthreads();
+      prefix = s_prefix;
+      rank = s_rank;
+      known |= 255ull << shift;
+    }
+    // prefix is now the k-th largest key: gather the k keys >= it, pad to a power of two with 0
+    // (every key is above 0) and sort them descending
+    int P = 1;
+    while (P < k) P <<= 1;
+    if (tid == 0) s_count = 0;
+    for (int i = tid; i < P; i += NT) key[i] = 0ull;
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < PER; ++r)
+      if (kreg[r] >= prefix) key[atomicAdd(&s_count, 1)] = kreg[r];
+    __syncthreads();
+    for (int kk = 2; kk <= P; kk <<= 1) {
+      for (int j = kk >> 1; j > 0; j >>= 1) {
+        for (int i = tid; i < P; i += NT) {
+          const int o = i ^ j;
+          if (o > i) {
+            const unsigned long long ki = key[i], ko = key[o];
+            if (((i & kk) == 0) ? (ko > ki) : (ko < ki)) {
+              key[i] = ko;
+              key[o] = ki;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < PER; ++r) key[tid + r * NT] = kreg[r];
+    __syncthreads();
+    // bitonic sort of all keys, descending
+    for (int kk = 2; kk <= NCT; kk <<= 1) {
+      for (int j = kk >> 1; j > 0; j >>= 1) {
+        for (int i = tid; i < NCT; i += NT) {
+          const int o = i ^ j;
+          if (o > i) {
+            const unsigned long long ki = key[i], ko = key[o];
+            if (((i & kk) == 0) ? (ko > ki) : (ko < ki)) {
+              key[i] = ko;
+              key[o] = ki;
+            }
+          }
+        }
+        __syncthreads();
+      }
     }
   }
   __shared__ int n_keep;
@@ -1183,9 +1268,11 @@ __global__ void k_pool(const __nv_bfloat16* __restrict__ a5, float* __restrict__
 }
 
 // logits[b][kt * 64 + f] = bh[kt] + sum_{d, c} wh[kt][d][c] pooled[b][f + d - 1][c]; logits[b][4096]
-// = bnull.  One block per image: pooled (zero-padded rows -1 and 64) in shared memory; a thread owns
-// one kt and 16 consecutive f, so each weight is loaded once for 16 products and each pooled value
-// once per (c, row) for up to 3 taps.
+// = bnull.  Block (q, b): image b, k tiles kt = 16 q .. 16 q + 15, their weights and the image's
+// pooled rows (zero-padded rows -1 and 64) in shared memory; a thread owns one kt and 4
+// consecutive f, so each weight is read once for 4 products and each pooled value once per (c, row)
+// for up to 3 taps.  Every logit sums its terms in the same order (c ascending, taps d = 0, 1, 2).
+constexpr int kHeadKtPerBlock = 16;
 __global__ void __launch_bounds__(256) k_head_fwd(const float* __restrict__ pooled,
                                                   const float* __restrict__ wh,
                                                   const float* __restrict__ bh,
@@ -1193,31 +1280,34 @@ __global__ void __launch_bounds__(256) k_head_fwd(const float* __restrict__ pool
                                                   float* __restrict__ logits) {
   constexpr int LDP = 65;                  // padded row: rows differing in f fall in other banks
   __shared__ float pp[66 * LDP];
-  const int b = blockIdx.x;
+  __shared__ float ws[kHeadKtPerBlock * 192];
+  const int b = blockIdx.y, kt0 = blockIdx.x * kHeadKtPerBlock;
   for (int e = threadIdx.x; e < 66 * 64; e += blockDim.x) {
     const int row = e / 64, c = e % 64;
     const int f = row - 1;
     pp[row * LDP + c] = (f >= 0 && f < 64) ? pooled[((int64_t)b * 64 + f) * 64 + c] : 0.f;
   }
+  for (int e = threadIdx.x; e < kHeadKtPerBlock * 192; e += blockDim.x) ws[e] = wh[kt0 * 192 + e];
   __syncthreads();
-  const int kt = threadIdx.x >> 2, f0 = (threadIdx.x & 3) * 16;
-  float acc[16];
+  const int kl = threadIdx.x >> 4, f0 = (threadIdx.x & 15) * 4, kt = kt0 + kl;
+  float acc[4];
   const float bias = bh[kt];
 #pragma unroll
-  for (int j = 0; j < 16; ++j) acc[j] = bias;
-  const float* w = wh + kt * 192;
+  for (int j = 0; j < 4; ++j) acc[j] = bias;
+  const float* w = ws + kl * 192;
+#pragma unroll 4
   for (int c = 0; c < 64; ++c) {
     const float w0 = w[c], w1 = w[64 + c], w2 = w[128 + c];
-    float v[18];
+    float v[6];
 #pragma unroll
-    for (int j = 0; j < 18; ++j) v[j] = pp[(f0 + j) * LDP + c];   // rows f0 .. f0 + 17 = f - 1 ..
+    for (int j = 0; j < 6; ++j) v[j] = pp[(f0 + j) * LDP + c];   // rows f0 .. f0 + 5 = f - 1 ..
 #pragma unroll
-    for (int j = 0; j < 16; ++j) acc[j] += w0 * v[j] + w1 * v[j + 1] + w2 * v[j + 2];
+    for (int j = 0; j < 4; ++j) acc[j] += w0 * v[j] + w1 * v[j + 1] + w2 * v[j + 2];
   }
   float* o = logits + (int64_t)b * kClasses + kt * 64 + f0;
 #pragma unroll
-  for (int j = 0; j < 16; ++j) o[j] = acc[j];
-  if (threadIdx.x == 0) logits[(int64_t)b * kClasses + kClasses - 1] = bnull[0];
+  for (int j = 0; j < 4; ++j) o[j] = acc[j];
+  if (blockIdx.x == 0 && threadIdx.x == 0) logits[(int64_t)b * kClasses + kClasses - 1] = bnull[0];
 }
 
 // Softmax cross-entropy per sample (one block of 256 threads per sample): loss[b], and dlogits =
@@ -1632,7 +1722,8 @@ int forward(gfh_cnn* n, const __nv_bfloat16* img, int B, bool masks) {
                                     B, 64, sms, st, flag);
   if (rc) return rc;
   k_pool<<<(B * 4096 + 255) / 256, 256, 0, st>>>(n->act[5], n->pooled, B);
-  k_head_fwd<<<B, 256, 0, st>>>(n->pooled, n->w + L.wh, n->w + L.bh, n->w + L.bnull, n->logits);
+  k_head_fwd<<<dim3(kTiles / kHeadKtPerBlock, B), 256, 0, st>>>(n->pooled, n->w + L.wh, n->w + L.bh,
+                                                                n->w + L.bnull, n->logits);
   GFH_CUDA_TRY(cudaGetLastError());
   return GFH_OK;
 }
@@ -1876,8 +1967,9 @@ extern "C" int gfh_peaks_to_images(gfh_ctx* ctx, const gfh_peaks* peaks, int32_t
                                    int32_t bin_lo, int32_t bin_hi, const float* d_nplane,
                                    void* d_images) {
   if (!ctx || !peaks || !peaks->offsets || peaks->n_lists < 1 || peaks->n_lists > 65535 ||
-      !peaks->fft_idx || !peaks->bin || n_fft < kImg || bin_lo < 0 || bin_hi < bin_lo ||
-      bin_hi - bin_lo + 1 < kImg || !d_nplane || !d_images)
+      !peaks->fft_idx || !peaks->bin || n_fft < kImg || n_fft >= (1 << 24) || bin_lo < 0 ||
+      bin_hi < bin_lo || bin_hi - bin_lo + 1 < kImg || bin_hi - bin_lo + 1 >= (1 << 24) ||
+      !d_nplane || !d_images)
     return GFH_ERR_ARG;
   GFH_CUDA_TRY(cudaSetDevice(ctx->device));
   const int L = peaks->n_lists;

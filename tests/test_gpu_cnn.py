@@ -397,6 +397,34 @@ def test_proposals(built_lib, gpu_ctx):
             assert rs[3] < 1e-3 and np.all(fl == 0)
 
 
+def test_proposal_selection_equals_full_ranking(built_lib, gpu_ctx):
+    """For k <= 512 the tiles are found by a radix selection of the k best keys and a sort of those
+    alone; k = 4096 sorts every tile.  The selected tiles are the full ranking's first k, in the
+    same order, ties included (equal scores go to the lower tile id)."""
+    gfh = built_lib
+    spec = PR.ProposerSpec()
+    smp = PR.draw(spec, np.arange(200, 208))
+    rng = np.random.default_rng(11)
+    logits = (rng.standard_normal((8, gfh.N_CLASSES)) * 3).astype(np.float32)
+    logits[2] = 0.0                                    # equal logits: many equal scores
+    logits[4, : 2048] = -np.inf                        # half the classes without probability
+    logits[6, 64 * 7 + 3] = 30.0                       # one confident class
+    lt = torch.from_numpy(logits).cuda()
+    gain = torch.from_numpy(smp.gain).cuda()
+
+    def ranked(k):
+        top = torch.empty((8, k), dtype=torch.int32, device="cuda")
+        resid = torch.empty(8, dtype=torch.float32, device="cuda")
+        gfh.propose_tiles(gpu_ctx, lt, gain, k, top, resid, -1.0, None)
+        torch.cuda.synchronize()
+        return top.cpu().numpy()
+
+    full = ranked(4096)
+    assert np.all(np.sort(full, axis=1) == np.arange(4096))
+    for k in (1, 32, 256, 300, 512):
+        assert np.array_equal(ranked(k), full[:, :k]), k
+
+
 def test_bounded_wait_reports_timeout_and_context_survives(built_lib, gpu_ctx):
     """A device wait that nothing ends gives up after its limit and raises the timeout status;
     the context then works normally (the same network forward as before, no fault)."""
