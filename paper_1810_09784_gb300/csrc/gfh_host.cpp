@@ -503,7 +503,7 @@ extern "C" int gfh_plan_create(gfh_ctx* ctx, int32_t n_maps, const gfh_grid* gri
   const bool select = h_cands != nullptr || d_stats != nullptr;
   const size_t smem = (size_t)tc.rows * (tc.cols + 2) * 4 + 32 * 4 * (tiles_x.empty() ? 1 : tc.rows) +
                       (select ? (size_t)max_tile_bands * 8 : 0);
-  if (smem > 227 * 1024) return GFH_ERR_SIZE;
+  if (smem > kHoughSmemLimit) return GFH_ERR_SIZE;
   // Longest work first: bins x rows; the x-direction tiles form a second list after the others.
   auto by_work = [](const TileDev& a, const TileDev& b) {
     const int64_t wa = (int64_t)std::max(0, a.bin_b - a.bin_a + 1) * a.nrows;
@@ -536,6 +536,7 @@ extern "C" int gfh_plan_create(gfh_ctx* ctx, int32_t n_maps, const gfh_grid* gri
     o_csr[m] = take(sizeof(int64_t) * (size_t)(grids[m].bin_hi - grids[m].bin_lo + 2));
   }
   const size_t o_single = take(sizeof(int64_t) * 2);
+  const size_t o_next = take(sizeof(int) * 2);
   const size_t total = off;
 
   gfh_plan* p = new (std::nothrow) gfh_plan();
@@ -612,6 +613,7 @@ extern "C" int gfh_plan_create(gfh_ctx* ctx, int32_t n_maps, const gfh_grid* gri
   p->d_csr_map = (int32_t*)(base + o_csrmap);
   p->select = h_cands != nullptr || d_stats != nullptr;
   p->d_offsets_single = (int64_t*)(base + o_single);
+  p->d_next = (int*)(base + o_next);
   p->h_maps.assign(h_maps, h_maps + n_maps);
   if (h_cands) p->h_cands.assign(h_cands, h_cands + n_maps);
   p->d_stats = d_stats;
@@ -697,7 +699,7 @@ extern "C" int gfh_plan_set_coarse(gfh_plan* p, int32_t coarse_k, int32_t coarse
   if (fine.size() > (size_t)INT32_MAX || worst > (size_t)INT32_MAX) return GFH_ERR_SIZE;
   const size_t smem = (size_t)p->cfg.rows * (p->cfg.cols + 2) * 4 + 32 * 4 +
                       (p->select ? (size_t)max_bands * 8 : 0);
-  if (smem > 227 * 1024) return GFH_ERR_SIZE;
+  if (smem > kHoughSmemLimit) return GFH_ERR_SIZE;
 
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };

@@ -15,7 +15,6 @@
 namespace {
 
 constexpr int kLane = 32;
-constexpr size_t kListStaticSmem = 64;   // bound on k_hough_list's static shared memory
 
 __device__ __forceinline__ int warp_sum(int v) {
 #pragma unroll
@@ -418,16 +417,31 @@ __device__ __forceinline__ void hough_tile(const MapDev* __restrict__ maps, cons
   }
 }
 
-// One block per tile of the plan.
+// Persistent blocks over the plan's n_tiles tiles (every map of the plan in one launch): each block
+// takes the next tile from the counter `next` (zeroed before the launch) until none is left.  The
+// plan lists the tiles longest first, so the blocks finish together.  The index of a block's next
+// tile is claimed when it starts a tile and read when it has finished it, so the atomic's round
+// trip is hidden behind the tile.
 template <int R, int NT, bool SELECT, bool XD, int LDS = 0>
 __global__ void __launch_bounds__(NT, NT == 1024 ? 1 : (R <= 4 ? 3 : (R == 8 ? 2 : 1)))
-k_hough(const MapDev* __restrict__ maps, const TileDev* __restrict__ tiles,
-        const uint32_t* __restrict__ fft_idx, const uint32_t* __restrict__ bins,
-        unsigned int* __restrict__ flag, int c_max) {
+k_hough(const MapDev* __restrict__ maps, const TileDev* __restrict__ tiles, int n_tiles,
+        int* __restrict__ next, const uint32_t* __restrict__ fft_idx,
+        const uint32_t* __restrict__ bins, unsigned int* __restrict__ flag, int c_max) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const TileDev t = tiles[blockIdx.x];
-  if (t.nrows <= 0) return;
-  hough_tile<R, NT, SELECT, XD, LDS>(maps, t, fft_idx, bins, flag, c_max, smem);
+  __shared__ int s_next;
+  if (threadIdx.x == 0) s_next = atomicAdd(next, 1);
+  __syncthreads();
+  int ti = s_next;
+  while (ti < n_tiles) {
+    __syncthreads();                                  // every thread has read s_next
+    int claimed = 0;
+    if (threadIdx.x == 0) claimed = atomicAdd(next, 1);
+    const TileDev t = tiles[ti];
+    if (t.nrows > 0) hough_tile<R, NT, SELECT, XD, LDS>(maps, t, fft_idx, bins, flag, c_max, smem);
+    if (threadIdx.x == 0) s_next = claimed;
+    __syncthreads();
+    ti = s_next;
+  }
 }
 
 // Persistent blocks over a tile list whose length is known on the device only (the coarse-tile
@@ -439,16 +453,20 @@ k_hough_list(const MapDev* __restrict__ maps, const TileDev* __restrict__ tiles,
              const uint32_t* __restrict__ fft_idx, const uint32_t* __restrict__ bins,
              unsigned int* __restrict__ flag, int c_max) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int cur;
+  __shared__ int s_next;
   const int n = min(*count, cap);
-  for (;;) {
-    if (threadIdx.x == 0) cur = atomicAdd(next, 1);
+  if (threadIdx.x == 0) s_next = atomicAdd(next, 1);
+  __syncthreads();
+  int ti = s_next;
+  while (ti < n) {                                    // next tile claimed during this one
     __syncthreads();
-    const int ti = cur;
-    __syncthreads();
-    if (ti >= n) break;
+    int claimed = 0;
+    if (threadIdx.x == 0) claimed = atomicAdd(next, 1);
     const TileDev t = tiles[ti];
     if (t.nrows > 0) hough_tile<R, NT, SELECT>(maps, t, fft_idx, bins, flag, c_max, smem);
+    if (threadIdx.x == 0) s_next = claimed;
+    __syncthreads();
+    ti = s_next;
   }
 }
 
@@ -547,26 +565,30 @@ int launch_hough_t(gfh_plan* p, const gfh_peaks* peaks, const TileDev* tiles, in
   }
   auto fl = k_hough_list<R, NT, SEL>;
   if (prepare) {
-    // the list kernel also holds a few bytes of static shared memory
-    cudaFuncAttributes fa{};
-    GFH_CUDA_TRY(cudaFuncGetAttributes(&fa, fl));
-    GFH_CUDA_TRY(cudaFuncSetAttribute(k_hough<R, NT, SEL, false>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)kMaxSmemBytes));
-    GFH_CUDA_TRY(cudaFuncSetAttribute(k_hough<R, NT, SEL, true>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)kMaxSmemBytes));
-    if (fn != k_hough<R, NT, SEL, false> && fn != k_hough<R, NT, SEL, true>)
-      GFH_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)kMaxSmemBytes));
-    GFH_CUDA_TRY(cudaFuncSetAttribute(fl, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)(kMaxSmemBytes - fa.sharedSizeBytes)));
-    return GFH_OK;
+    // both kernels also hold a few bytes of static shared memory (the tile counter)
+    auto set_max = [](const void* f) -> int {
+      cudaFuncAttributes fa{};
+      GFH_CUDA_TRY(cudaFuncGetAttributes(&fa, f));
+      GFH_CUDA_TRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)(kMaxSmemBytes - fa.sharedSizeBytes)));
+      return GFH_OK;
+    };
+    int rc = set_max((const void*)k_hough<R, NT, SEL, false>);
+    if (!rc) rc = set_max((const void*)k_hough<R, NT, SEL, true>);
+    if (!rc && fn != k_hough<R, NT, SEL, false> && fn != k_hough<R, NT, SEL, true>)
+      rc = set_max((const void*)fn);
+    if (!rc) rc = set_max((const void*)fl);
+    return rc;
   }
-  if (n_tiles < 0 && smem + kListStaticSmem > kMaxSmemBytes) return GFH_ERR_SIZE;
+  if (smem > kHoughSmemLimit) return GFH_ERR_SIZE;
   if (n_tiles >= 0) {
-    fn<<<n_tiles, NT, smem, p->ctx->stream>>>(p->d_maps, tiles, peaks->fft_idx, peaks->bin,
-                                              p->ctx->d_flag, p->cfg.cols);
+    if (n_tiles == 0) return GFH_OK;
+    int per_sm = 0;
+    GFH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, NT, smem));
+    const int grid = std::min(n_tiles, p->ctx->num_sms * (per_sm > 0 ? per_sm : 1));
+    fn<<<grid, NT, smem, p->ctx->stream>>>(p->d_maps, tiles, n_tiles, p->d_next + (xd ? 1 : 0),
+                                           peaks->fft_idx, peaks->bin, p->ctx->d_flag,
+                                           p->cfg.cols);
   } else {
     int per_sm = 0;
     GFH_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fl, NT, smem));
@@ -641,7 +663,7 @@ size_t gfh_hough_smem_bytes(const gfh_plan* p, bool xd) {
 
 int gfh_prepare_plan(gfh_plan* p) {
   const size_t smem = gfh_hough_smem_bytes(p, p->n_tiles_x > 0);
-  if (smem > 227 * 1024) return GFH_ERR_SIZE;
+  if (smem > kHoughSmemLimit) return GFH_ERR_SIZE;
   return launch_hough(p, nullptr, nullptr, 0, smem, true);
 }
 
@@ -678,9 +700,10 @@ int gfh_launch_plan(gfh_plan* p, const gfh_peaks* peaks) {
   GFH_CUDA_TRY(cudaSetDevice(p->ctx->device));
   const size_t smem = gfh_hough_smem_bytes(p, false);
   const size_t smem_x = gfh_hough_smem_bytes(p, true);
-  if (smem > 227 * 1024 || (p->n_tiles_x > 0 && smem_x > 227 * 1024)) return GFH_ERR_SIZE;
+  if (smem > kHoughSmemLimit || (p->n_tiles_x > 0 && smem_x > kHoughSmemLimit)) return GFH_ERR_SIZE;
   int rc = launch_prologue(p, peaks);
   if (rc) return rc;
+  GFH_CUDA_TRY(cudaMemsetAsync(p->d_next, 0, 2 * sizeof(int), p->ctx->stream));
   if (p->n_tiles > 0) {
     rc = launch_hough(p, peaks, p->d_tiles, p->n_tiles, smem, false);
     if (rc) return rc;
@@ -696,7 +719,7 @@ int gfh_launch_plan_tiles(gfh_plan* p, const gfh_peaks* peaks, const int32_t* d_
                           const int32_t* d_full) {
   GFH_CUDA_TRY(cudaSetDevice(p->ctx->device));
   const size_t smem = gfh_hough_smem_bytes(p, false);
-  if (smem > 227 * 1024) return GFH_ERR_SIZE;
+  if (smem > kHoughSmemLimit) return GFH_ERR_SIZE;
   int rc = launch_prologue(p, peaks);
   if (rc) return rc;
   const int nct = p->coarse_k * p->coarse_x;

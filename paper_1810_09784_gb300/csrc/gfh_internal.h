@@ -13,6 +13,8 @@
 
 // Largest dynamic shared memory a block may use on sm_103a (227 KB).
 constexpr size_t kMaxSmemBytes = 227 * 1024;
+// dynamic shared memory a Hough tile may take: the kernels keep a few static bytes (tile counter)
+constexpr size_t kHoughSmemLimit = kMaxSmemBytes - 64;
 
 // Counter-based generator of the statistical peakmap model: the splitmix64 finaliser (Steele, Lea
 // and Flood, "Fast splittable pseudorandom number generators", OOPSLA 2014) applied to a key built
@@ -136,6 +138,7 @@ struct gfh_plan {
   int32_t* d_csr_map = nullptr;           // per CSR entry: map index
   bool select = false;
   int64_t* d_offsets_single = nullptr;    // scratch offsets for gfh_hough
+  int* d_next = nullptr;                  // tile counters of the full search's two launches
   // the bound outputs, kept so that the autotuner can rebuild the plan with another tile shape
   std::vector<int32_t*> h_maps;
   std::vector<gfh_candidate*> h_cands;
