@@ -295,11 +295,21 @@ int gfh_plan_execute(gfh_plan* plan, const gfh_peaks* peaks);
  * Autotuner: times gfh_plan_execute on these peaks (reps runs each, CUDA events on the context's
  * stream) for the current tile shape and for every shape of rows {4, 8, 16} x cols {1024, 2048,
  * 3072, 4096} x threads {256, 512} (and 1024 threads for 16 rows) that fits in shared memory,
- * then rebuilds the plan with the fastest.  The results are unchanged by the shape (the maps are exact).  Synchronises; writes
- * the bound outputs.  h_best / h_best_ms (may be NULL) receive the chosen shape and its time.
+ * then rebuilds the plan with the fastest.  The results are unchanged by the shape (the maps are
+ * exact).  Synchronises; writes the bound outputs.  h_best / h_best_ms (may be NULL) receive the
+ * chosen shape and its time.
+ * The choice is cached for the life of the process, keyed by the plan's signature: the device
+ * (compute capability, SM count), whether candidates are selected, and per map its k rows, x0
+ * columns, bins, FFTs, line form and peak-density class (log2 of its list's peaks per (FFT, bin)
+ * of its band, in quarter steps).  A plan whose signature is in the cache is rebuilt with the
+ * cached shape and only that shape is timed.  Thread-safe.
  */
 int gfh_plan_autotune(gfh_plan* plan, const gfh_peaks* peaks, int32_t reps,
                       gfh_tile_config* h_best, float* h_best_ms);
+
+/* Number of plan signatures in the autotuner's cache, and emptying it (host only). */
+int gfh_autotune_cache_size(void);
+void gfh_autotune_cache_clear(void);
 
 /* Convenience: one grid, one peak list of n_peaks entries; plan, execute, destroy. */
 int gfh_hough(gfh_ctx* ctx, const uint32_t* d_fft_idx, const uint32_t* d_bin, int64_t n_peaks,

@@ -6,8 +6,11 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <numeric>
+#include <string>
 
 #include "gfh_internal.h"
 
@@ -747,6 +750,37 @@ extern "C" int gfh_plan_execute_tiles(gfh_plan* p, const gfh_peaks* peaks, const
 
 namespace {
 
+// Shapes the autotuner chose, by plan signature (plan_signature), for this process.
+std::mutex g_tune_mu;
+std::map<std::string, gfh_tile_config> g_tune_cache;
+
+// Signature of a plan and its peak lists for the autotuner's cache: the device (compute capability,
+// SMs), whether candidates are selected, and per map its k rows, x0 columns, bins, FFTs, line form
+// (along k or along x0) and peak-density class: log2 of its list's peaks per (FFT, bin) of its
+// band, in quarter steps (the list offsets are read back; the autotuner synchronises anyway).
+int plan_signature(const gfh_plan* p, const gfh_peaks* peaks, std::string* key) {
+  std::vector<int64_t> off((size_t)peaks->n_lists + 1);
+  if (p->ctx->stream) GFH_CUDA_TRY(cudaStreamSynchronize(p->ctx->stream));
+  GFH_CUDA_TRY(cudaMemcpy(off.data(), peaks->offsets, off.size() * sizeof(int64_t),
+                          cudaMemcpyDeviceToHost));
+  cudaDeviceProp prop{};
+  GFH_CUDA_TRY(cudaGetDeviceProperties(&prop, p->ctx->device));
+  std::string k = "cc" + std::to_string(prop.major) + "." + std::to_string(prop.minor) + " sm" +
+                  std::to_string(prop.multiProcessorCount) + (p->select ? " sel" : " nosel");
+  for (int m = 0; m < p->n_maps; ++m) {
+    const gfh_grid& g = p->grids[m];
+    if (g.list < 0 || g.list >= peaks->n_lists) return GFH_ERR_ARG;
+    const double cells = (double)g.n_fft * (double)(g.bin_hi - g.bin_lo + 1);
+    const double n = (double)(off[g.list + 1] - off[g.list]);
+    const int cls = n > 0.0 ? (int)std::floor(4.0 * std::log2(n / cells)) : -1000;
+    k += " " + std::to_string(g.n_k) + "x" + std::to_string(g.n_x0) + "b" +
+         std::to_string(g.bin_hi - g.bin_lo + 1) + "f" + std::to_string(g.n_fft) +
+         (p->map_xd[m] ? "x" : "k") + "d" + std::to_string(cls);
+  }
+  *key = k;
+  return GFH_OK;
+}
+
 // Mean time of `reps` executions of plan q on its stream (after one untimed run), in ms.
 int time_plan(gfh_plan* q, const gfh_peaks* peaks, int reps, float* ms) {
   cudaStream_t st = q->ctx->stream;
@@ -767,17 +801,51 @@ int time_plan(gfh_plan* q, const gfh_peaks* peaks, int reps, float* ms) {
   return rc;
 }
 
+// Rebuilds plan p with tile shape `shape` (same grids and outputs; coarse tiles follow the shape).
+int reshape_plan(gfh_plan* p, const gfh_tile_config& shape) {
+  if (shape.rows == p->cfg.rows && shape.cols == p->cfg.cols && shape.threads == p->cfg.threads)
+    return GFH_OK;
+  gfh_plan* q = nullptr;
+  gfh_tile_config cfg = shape;
+  int rc = gfh_plan_create(p->ctx, p->n_maps, p->grids.data(), p->h_maps.data(),
+                           p->h_cands.empty() ? nullptr : p->h_cands.data(), p->d_stats, &cfg, &q);
+  if (rc) return rc;
+  if (p->ctx->stream) cudaStreamSynchronize(p->ctx->stream);
+  const int ck = p->coarse_k, cx = p->coarse_x, ms = p->max_sel;
+  std::swap(*p, *q);      // p takes the new tables; q holds the old ones and is freed
+  gfh_plan_destroy(q);
+  if (ck > 0) return gfh_plan_set_coarse(p, ck, cx, ms);
+  return GFH_OK;
+}
+
 }  // namespace
 
 extern "C" int gfh_plan_autotune(gfh_plan* p, const gfh_peaks* peaks, int32_t reps,
                                  gfh_tile_config* h_best, float* h_best_ms) {
-  if (!p || !peaks || reps < 1) return GFH_ERR_ARG;
+  if (!p || !peaks || !peaks->offsets || peaks->n_lists < 1 || reps < 1) return GFH_ERR_ARG;
   static const int kRowsList[] = {4, 8, 16};
   static const int kColsList[] = {1024, 2048, 3072, 4096};
   static const int kThreadsList[] = {256, 512, 1024};
+  std::string key;
+  int rc = plan_signature(p, peaks, &key);
+  if (rc) return rc;
+  bool cached = false;
   gfh_tile_config best = p->cfg;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) { best = it->second; cached = true; }
+  }
   float best_ms = 0.f;
-  int rc = time_plan(p, peaks, reps, &best_ms);
+  if (cached) {                 // tuned before: take that shape and time it alone
+    rc = reshape_plan(p, best);
+    if (!rc) rc = time_plan(p, peaks, reps, &best_ms);
+    if (rc) return rc;
+    if (h_best) *h_best = best;
+    if (h_best_ms) *h_best_ms = best_ms;
+    return GFH_OK;
+  }
+  rc = time_plan(p, peaks, reps, &best_ms);
   if (rc) return rc;
   for (int r : kRowsList)
     for (int c : kColsList)
@@ -798,21 +866,23 @@ extern "C" int gfh_plan_autotune(gfh_plan* p, const gfh_peaks* peaks, int32_t re
         if (rc) return rc;
         if (ms < best_ms) { best_ms = ms; best = cfg; }
       }
-  if (best.rows != p->cfg.rows || best.cols != p->cfg.cols || best.threads != p->cfg.threads) {
-    gfh_plan* q = nullptr;
-    rc = gfh_plan_create(p->ctx, p->n_maps, p->grids.data(), p->h_maps.data(),
-                         p->h_cands.empty() ? nullptr : p->h_cands.data(), p->d_stats, &best, &q);
-    if (rc) return rc;
-    if (p->ctx->stream) cudaStreamSynchronize(p->ctx->stream);
-    const int ck = p->coarse_k, cx = p->coarse_x, ms = p->max_sel;
-    std::swap(*p, *q);      // p takes the tuned tables; q holds the old ones and is freed
-    gfh_plan_destroy(q);
-    if (ck > 0) {           // coarse tiles follow the tile shape
-      rc = gfh_plan_set_coarse(p, ck, cx, ms);
-      if (rc) return rc;
-    }
+  rc = reshape_plan(p, best);
+  if (rc) return rc;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = best;
   }
   if (h_best) *h_best = best;
   if (h_best_ms) *h_best_ms = best_ms;
   return GFH_OK;
+}
+
+extern "C" int gfh_autotune_cache_size(void) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  return (int)g_tune_cache.size();
+}
+
+extern "C" void gfh_autotune_cache_clear(void) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache.clear();
 }

@@ -30,7 +30,7 @@ EXPORTED = [
     "gfh_grid_make", "gfh_grid_tables", "gfh_grid_columns",
     "gfh_peaks_from_power", "gfh_peakmap", "gfh_peakmap_async",
     "gfh_plan_create", "gfh_plan_destroy", "gfh_plan_execute", "gfh_plan_autotune",
-    "gfh_hough", "gfh_select", "gfh_peaks_from_power_static",
+    "gfh_autotune_cache_size", "gfh_autotune_cache_clear", "gfh_hough", "gfh_select", "gfh_peaks_from_power_static",
     "gfh_plan_set_coarse", "gfh_plan_execute_tiles",
     "gfh_synth_peaks", "gfh_synth_images", "gfh_peaks_to_images",
     "gfh_cnn_create", "gfh_cnn_destroy", "gfh_cnn_param_count", "gfh_cnn_get_params",
@@ -129,6 +129,8 @@ def lib() -> ctypes.CDLL:
             "gfh_plan_destroy": [vp],
             "gfh_plan_execute": [vp, P(PeaksC)],
             "gfh_plan_autotune": [vp, P(PeaksC), i32, P(TileConfigC), P(ctypes.c_float)],
+            "gfh_autotune_cache_size": [],
+            "gfh_autotune_cache_clear": [],
             "gfh_hough": [vp, vp, vp, i64, P(GridC), vp, vp, vp],
             "gfh_select": [vp, vp, P(GridC), vp, vp],
             "gfh_peaks_from_power_static": [vp, vp, i64, i32, i32, i32, dbl, vp, vp, i64, vp],
@@ -174,12 +176,23 @@ def lib() -> ctypes.CDLL:
         L.gfh_cnn_param_count.restype = i64
         L.gfh_strerror.argtypes = [ctypes.c_int]
         L.gfh_strerror.restype = ctypes.c_char_p
+        L.gfh_autotune_cache_clear.restype = None
         _lib = L
     return _lib
 
 
 def strerror(code: int) -> str:
     return lib().gfh_strerror(code).decode()
+
+
+def autotune_cache_size() -> int:
+    """gfh_autotune_cache_size: plan signatures whose tuned tile shape this process keeps."""
+    return int(lib().gfh_autotune_cache_size())
+
+
+def autotune_cache_clear() -> None:
+    """gfh_autotune_cache_clear: forget every tuned shape (the next autotune times them all)."""
+    lib().gfh_autotune_cache_clear()
 
 
 def _ok(code: int, where: str) -> None:

@@ -15,7 +15,7 @@ HEADER = pathlib.Path(__file__).resolve().parent.parent / "include" / "gfh.h"
 
 def declared_functions():
     text = HEADER.read_text()
-    return sorted(set(re.findall(r"^\s*(?:int|int64_t|const char\*)\s+(gfh_\w+)\s*\(", text, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:int|int64_t|void|const char\*)\s+(gfh_\w+)\s*\(", text, re.M)))
 
 
 def test_every_declared_symbol_is_exported(built_lib):
@@ -25,6 +25,12 @@ def test_every_declared_symbol_is_exported(built_lib):
     for name in names:
         assert hasattr(L, name), name
     assert sorted(built_lib.EXPORTED) == names
+
+
+def test_autotune_cache_host_calls(built_lib):
+    """The autotuner's cache is host state: its size and clearing need no GPU."""
+    built_lib.autotune_cache_clear()
+    assert built_lib.autotune_cache_size() == 0
 
 
 def test_strerror(built_lib):

@@ -93,6 +93,44 @@ def test_autotuned_plan_gives_the_same_map(built_lib, gpu_ctx):
                          read_stats(built_lib, stats), fields, fi, bj)
 
 
+def test_autotune_cache(built_lib, gpu_ctx):
+    """A plan whose signature was tuned before takes the cached shape: the cache keeps one entry
+    per signature, a second plan of the same grid and lists reuses it, another peak density is a
+    new entry, and the maps stay bit-exact."""
+    gfh = built_lib
+    gfh.autotune_cache_clear()
+    assert gfh.autotune_cache_size() == 0
+    fields, fi, bj = medium_case(6, n_k=45, nb=400)
+    g = gfh.grid_make(gfh.Grid(**fields))
+    dfi, dbj = to_dev(torch, fi), to_dev(torch, bj)
+    off = to_dev(torch, np.array([0, len(fi)], np.int64))
+    shapes = []
+    for _ in range(2):
+        hmap, cands, stats = alloc_outputs(torch, g)
+        plan = gfh.Plan(gpu_ctx, [g], [hmap], [cands], stats, tile=(4, 1024, 256))
+        best, ms = plan.autotune(dfi, dbj, off, 1, reps=1)
+        shapes.append(best)
+        assert gfh.autotune_cache_size() == 1 and ms > 0
+        hmap.fill_(-7)
+        plan.execute(dfi, dbj, off, 1)
+        torch.cuda.synchronize()
+        plan.close()
+        check_against_oracle(g, hmap.cpu().numpy(), read_cands(gfh, cands), read_stats(gfh, stats),
+                             fields, fi, bj)
+    assert shapes[0] == shapes[1]
+    # a sparser list of the same grid: another density class, another entry
+    keep = np.arange(len(fi)) % 4 == 0
+    fi4, bj4 = fi[keep], bj[keep]
+    hmap, cands, stats = alloc_outputs(torch, g)
+    plan = gfh.Plan(gpu_ctx, [g], [hmap], [cands], stats)
+    plan.autotune(to_dev(torch, fi4), to_dev(torch, bj4),
+                  to_dev(torch, np.array([0, len(fi4)], np.int64)), 1, reps=1)
+    plan.close()
+    assert gfh.autotune_cache_size() == 2
+    gfh.autotune_cache_clear()
+    assert gfh.autotune_cache_size() == 0
+
+
 def test_edge_cases(built_lib, gpu_ctx):
     fields, fi, bj = medium_case(9)
     # empty list: all-zero map, candidates at the first cell of each band
