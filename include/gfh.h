@@ -135,12 +135,17 @@ typedef struct gfh_peaks {
 } gfh_peaks;
 
 /* Tile shape of the Hough kernel; zero fields pick the library default (16 x 3072, 512).  The
- * tile (rows x (cols + 2) int32 plus the candidate keys) must fit in 227 KB of shared memory. */
+ * tile (rows x (cols + 2) int32 plus the candidate keys) must fit in 227 KB of shared memory.
+ * form chooses how a warp draws its 32 peaks: 0 = each peak in its own form (interior peaks, clear
+ * of the tile's edges on every row, in a shorter form than peaks near an edge; a warp holding both
+ * runs both), 1 = one form per warp (the edge-following form for all 32 as soon as one needs it).
+ * The maps are identical; 1 pays where many warps mix the two kinds of peak (narrow tiles, tall
+ * maps).  The coarse-tile search always draws one form per warp. */
 typedef struct gfh_tile_config {
   int32_t rows;     /* k rows per tile: 4, 8, 16 or 32 */
   int32_t cols;     /* x0 columns per tile: multiple of 128, at most 4096 */
   int32_t threads;  /* threads per block: 256 or 512, or 1024 with 16 or 32 rows */
-  int32_t reserved;
+  int32_t form;     /* drawing form: 0 or 1 */
 } gfh_tile_config;
 
 /* Context: binds a device and a stream (cudaStream_t passed as void*; NULL = legacy default). */
@@ -295,7 +300,7 @@ int gfh_plan_execute(gfh_plan* plan, const gfh_peaks* peaks);
  * Autotuner: times gfh_plan_execute on these peaks (reps runs each, CUDA events on the context's
  * stream) for the current tile shape and for every shape of rows {4, 8, 16} x cols {1024, 2048,
  * 3072, 4096} x threads {256, 512} (and 1024 threads for 16 rows) that fits in shared memory,
- * then rebuilds the plan with the fastest.  The results are unchanged by the shape (the maps are
+ * then the fastest shape with the other drawing form, and rebuilds the plan with the fastest.  The results are unchanged by the shape (the maps are
  * exact).  Synchronises; writes the bound outputs.  h_best / h_best_ms (may be NULL) receive the
  * chosen shape and its time.
  * The choice is cached for the life of the process, keyed by the plan's signature: the device

@@ -468,9 +468,10 @@ extern "C" int gfh_plan_create(gfh_ctx* ctx, int32_t n_maps, const gfh_grid* gri
     if (cfg->rows) tc.rows = cfg->rows;
     if (cfg->cols) tc.cols = cfg->cols;
     if (cfg->threads) tc.threads = cfg->threads;
+    tc.form = cfg->form;
   }
   if (!(tc.rows == 4 || tc.rows == 8 || tc.rows == 16 || tc.rows == 32) || tc.cols < 128 || tc.cols % 128 ||
-      tc.cols > 4096 ||
+      tc.cols > 4096 || !(tc.form == 0 || tc.form == 1) ||
       !(tc.threads == 256 || tc.threads == 512 || (tc.threads == 1024 && tc.rows >= 16)))
     return GFH_ERR_ARG;
   const int nwarps = tc.threads / 32;
@@ -802,9 +803,12 @@ int time_plan(gfh_plan* q, const gfh_peaks* peaks, int reps, float* ms) {
 }
 
 // Rebuilds plan p with tile shape `shape` (same grids and outputs; coarse tiles follow the shape).
+bool same_shape(const gfh_tile_config& a, const gfh_tile_config& b) {
+  return a.rows == b.rows && a.cols == b.cols && a.threads == b.threads && a.form == b.form;
+}
+
 int reshape_plan(gfh_plan* p, const gfh_tile_config& shape) {
-  if (shape.rows == p->cfg.rows && shape.cols == p->cfg.cols && shape.threads == p->cfg.threads)
-    return GFH_OK;
+  if (same_shape(shape, p->cfg)) return GFH_OK;
   gfh_plan* q = nullptr;
   gfh_tile_config cfg = shape;
   int rc = gfh_plan_create(p->ctx, p->n_maps, p->grids.data(), p->h_maps.data(),
@@ -847,25 +851,34 @@ extern "C" int gfh_plan_autotune(gfh_plan* p, const gfh_peaks* peaks, int32_t re
   }
   rc = time_plan(p, peaks, reps, &best_ms);
   if (rc) return rc;
+  auto try_shape = [&](const gfh_tile_config& cfg) -> int {
+    if (same_shape(cfg, p->cfg)) return GFH_OK;
+    gfh_plan* q = nullptr;
+    gfh_tile_config c = cfg;
+    const int crc = gfh_plan_create(p->ctx, p->n_maps, p->grids.data(), p->h_maps.data(),
+                                    p->h_cands.empty() ? nullptr : p->h_cands.data(), p->d_stats,
+                                    &c, &q);
+    if (crc == GFH_ERR_SIZE || crc == GFH_ERR_ARG) return GFH_OK;   // shape does not fit
+    if (crc) return crc;
+    float ms = 0.f;
+    const int trc = time_plan(q, peaks, reps, &ms);
+    gfh_plan_destroy(q);
+    if (trc) return trc;
+    if (ms < best_ms) { best_ms = ms; best = cfg; }
+    return GFH_OK;
+  };
   for (int r : kRowsList)
     for (int c : kColsList)
       for (int t : kThreadsList) {
-        gfh_tile_config cfg{r, c, t, 0};
-        if (cfg.rows == p->cfg.rows && cfg.cols == p->cfg.cols && cfg.threads == p->cfg.threads)
-          continue;
         if (t == 1024 && r < 16) continue;     // 1024 threads only for 16-row tiles
-        gfh_plan* q = nullptr;
-        const int crc = gfh_plan_create(p->ctx, p->n_maps, p->grids.data(), p->h_maps.data(),
-                                        p->h_cands.empty() ? nullptr : p->h_cands.data(),
-                                        p->d_stats, &cfg, &q);
-        if (crc == GFH_ERR_SIZE || crc == GFH_ERR_ARG) continue;   // shape does not fit
-        if (crc) return crc;
-        float ms = 0.f;
-        rc = time_plan(q, peaks, reps, &ms);
-        gfh_plan_destroy(q);
+        rc = try_shape(gfh_tile_config{r, c, t, 0});
         if (rc) return rc;
-        if (ms < best_ms) { best_ms = ms; best = cfg; }
       }
+  // the fastest shape with the other drawing form
+  gfh_tile_config other = best;
+  other.form = 1 - best.form;
+  rc = try_shape(other);
+  if (rc) return rc;
   rc = reshape_plan(p, best);
   if (rc) return rc;
   {

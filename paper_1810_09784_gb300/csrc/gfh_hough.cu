@@ -118,18 +118,28 @@ __device__ __forceinline__ bool meets_tile(int64_t a, int64_t b1, int64_t s, int
 // on row 0 is [a, b1 + 1) in 2^-32 columns and moves left by s per row.  G0 + m is column m of row
 // 0 in absolute column numbering (the tile's first column is c0); ub = min(last column of the
 // tile, last column of the map).
+// A peak that moves less than a column per row, starts at least R - 1 columns right of the tile's
+// first column and ends before the tile's last column and inside the map stays clear of every
+// edge on all R rows (its left edge is lowest on the last row, its right edge highest on row 0):
+// no clamp, no carry, and on rows r > 0 a column is entered where the left edge moved and left
+// where the right edge moved.
+template <int R>
+__device__ __forceinline__ bool peak_interior(int64_t a, int64_t b1, int64_t s, int c0, int c1m1,
+                                              int ub) {
+  constexpr int64_t kOne = int64_t(1) << GFH_FRAC_BITS;
+  const int lo = (int)(a >> GFH_FRAC_BITS), hr = (int)(b1 >> GFH_FRAC_BITS);
+  return (s < kOne) & (lo >= c0 + (R - 1)) & (hr <= ub) & (hr < c1m1) & (a <= b1);
+}
+
+// interior: draw in the interior form (the caller has checked peak_interior for this peak); the
+// edge-following form below draws every peak, interior ones with the same events.
 template <int R>
 __device__ __forceinline__ void draw_peak(int* G0, int lds, int64_t a, int64_t b1, int64_t s,
-                                          int c0, int c1m1, int ub, int& carry) {
+                                          int c0, int c1m1, int ub, int& carry, bool interior) {
   constexpr int64_t kOne = int64_t(1) << GFH_FRAC_BITS;
   int lo = (int)(a >> GFH_FRAC_BITS);
   const int hr = (int)(b1 >> GFH_FRAC_BITS);    // row-0 last column before any clamp
-  // A peak that moves less than a column per row, starts at least R - 1 columns right of the
-  // tile's first column and ends before the tile's last column and inside the map stays clear of
-  // every edge on all R rows (its left edge is lowest on the last row, its right edge highest on
-  // row 0): no clamp, no carry, and on rows r > 0 a column is entered where the left edge moved
-  // and left where the right edge moved.
-  if ((s < kOne) & (lo >= c0 + (R - 1)) & (hr <= ub) & (hr < c1m1) & (a <= b1)) {
+  if (interior) {
     atomicAdd(G0 + lo, 1);
     atomicAdd(G0 + hr + 1, -1);
     int o1 = lo, o2 = hr;
@@ -229,7 +239,7 @@ __device__ __forceinline__ void draw_peak_x(int* G0, int lds, int64_t a, int64_t
 // Shared memory: G[R][C+2] | tot[32] row-0 chunk sums | skey[bands] candidate keys.
 // XD (maps whose line moves more than two x0 columns per k row): every row differenced along x0
 // and scanned on its own; chunk sums tot[R][32].
-template <int R, int NT, bool SELECT, bool XD = false, int LDS = 0>
+template <int R, int NT, bool SELECT, bool XD = false, int LDS = 0, bool UNIF = false>
 __device__ __forceinline__ void hough_tile(const MapDev* __restrict__ maps, const TileDev t,
                                            const uint32_t* __restrict__ fft_idx,
                                            const uint32_t* __restrict__ bins,
@@ -298,9 +308,19 @@ __device__ __forceinline__ void hough_tile(const MapDev* __restrict__ maps, cons
       longlong2 bs_nx = make_longlong2(0, 0), up_nx = make_longlong2(0, 0);
       const bool ok_nx = f_nx != 0xffffffffu &&
                          peak_rows(BS, UP, bin_lo, f_nx, j_nx, nfft, jmax, flag, bs_nx, up_nx);
-      if (ok_cu && meets_tile<R>(a_cu, b_cu, s_cu, c0, ub)) {
-        if constexpr (XD) draw_peak_x<R>(G0, lds, a_cu, b_cu, s_cu, c0, c1m1, ub, carry_x);
-        else draw_peak<R>(G0, lds, a_cu, b_cu, s_cu, c0, c1m1, ub, carry);
+      const bool draw = ok_cu && meets_tile<R>(a_cu, b_cu, s_cu, c0, ub);
+      if constexpr (XD) {
+        if (draw) draw_peak_x<R>(G0, lds, a_cu, b_cu, s_cu, c0, c1m1, ub, carry_x);
+      } else if constexpr (UNIF) {
+        // one drawing form per warp: the interior form when every drawing lane's peak is
+        // interior, else the edge-following form for all, so that a warp never runs both
+        const bool interior = __all_sync(__activemask(),
+                                         !draw || peak_interior<R>(a_cu, b_cu, s_cu, c0, c1m1, ub));
+        if (draw) draw_peak<R>(G0, lds, a_cu, b_cu, s_cu, c0, c1m1, ub, carry, interior);
+      } else {
+        if (draw)
+          draw_peak<R>(G0, lds, a_cu, b_cu, s_cu, c0, c1m1, ub, carry,
+                       peak_interior<R>(a_cu, b_cu, s_cu, c0, c1m1, ub));
       }
       peak_interval(t.row0, bs_nx, up_nx, a_cu, b_cu, s_cu);
       ok_cu = ok_nx;
@@ -422,7 +442,7 @@ __device__ __forceinline__ void hough_tile(const MapDev* __restrict__ maps, cons
 // plan lists the tiles longest first, so the blocks finish together.  The index of a block's next
 // tile is claimed when it starts a tile and read when it has finished it, so the atomic's round
 // trip is hidden behind the tile.
-template <int R, int NT, bool SELECT, bool XD, int LDS = 0>
+template <int R, int NT, bool SELECT, bool XD, int LDS = 0, bool UNIF = false>
 __global__ void __launch_bounds__(NT, NT == 1024 ? 1 : (R <= 4 ? 3 : (R == 8 ? 2 : 1)))
 k_hough(const MapDev* __restrict__ maps, const TileDev* __restrict__ tiles, int n_tiles,
         int* __restrict__ next, const uint32_t* __restrict__ fft_idx,
@@ -437,7 +457,8 @@ k_hough(const MapDev* __restrict__ maps, const TileDev* __restrict__ tiles, int 
     int claimed = 0;
     if (threadIdx.x == 0) claimed = atomicAdd(next, 1);
     const TileDev t = tiles[ti];
-    if (t.nrows > 0) hough_tile<R, NT, SELECT, XD, LDS>(maps, t, fft_idx, bins, flag, c_max, smem);
+    if (t.nrows > 0)
+      hough_tile<R, NT, SELECT, XD, LDS, UNIF>(maps, t, fft_idx, bins, flag, c_max, smem);
     if (threadIdx.x == 0) s_next = claimed;
     __syncthreads();
     ti = s_next;
@@ -445,7 +466,9 @@ k_hough(const MapDev* __restrict__ maps, const TileDev* __restrict__ tiles, int 
 }
 
 // Persistent blocks over a tile list whose length is known on the device only (the coarse-tile
-// search): each block takes the next tile from a counter until the list is exhausted.
+// search): each block takes the next tile from a counter until the list is exhausted.  Its tiles
+// are mostly narrow (a coarse tile's columns), where many warps mix interior peaks with peaks near
+// an edge, so it always draws one form per warp.
 template <int R, int NT, bool SELECT>
 __global__ void __launch_bounds__(NT, NT == 1024 ? 1 : (R <= 4 ? 3 : (R == 8 ? 2 : 1)))
 k_hough_list(const MapDev* __restrict__ maps, const TileDev* __restrict__ tiles,
@@ -463,7 +486,7 @@ k_hough_list(const MapDev* __restrict__ maps, const TileDev* __restrict__ tiles,
     int claimed = 0;
     if (threadIdx.x == 0) claimed = atomicAdd(next, 1);
     const TileDev t = tiles[ti];
-    if (t.nrows > 0) hough_tile<R, NT, SELECT>(maps, t, fft_idx, bins, flag, c_max, smem);
+    if (t.nrows > 0) hough_tile<R, NT, SELECT, false, 0, true>(maps, t, fft_idx, bins, flag, c_max, smem);
     if (threadIdx.x == 0) s_next = claimed;
     __syncthreads();
     ti = s_next;
@@ -555,17 +578,21 @@ int launch_hough_t(gfh_plan* p, const gfh_peaks* peaks, const TileDev* tiles, in
   // the shapes the autotuner picks on the paper-shaped workloads (8-row tiles of 2048 or 3072
   // columns at 512 threads, 16-row tiles of 3072 columns at 1024 threads) have the row stride
   // fixed at compile time
-  auto fn = xd ? k_hough<R, NT, SEL, true> : k_hough<R, NT, SEL, false>;
+  // drawing form 1: one form per warp
+  const bool unif = p->cfg.form == 1;
+  auto fk = unif ? k_hough<R, NT, SEL, false, 0, true> : k_hough<R, NT, SEL, false>;
   if constexpr (R == 8 && NT == 512) {
-    if (!xd && p->cfg.cols == 3072) fn = k_hough<R, NT, SEL, false, 3074>;
-    if (!xd && p->cfg.cols == 2048) fn = k_hough<R, NT, SEL, false, 2050>;
+    if (p->cfg.cols == 3072) fk = unif ? k_hough<R, NT, SEL, false, 3074, true> : k_hough<R, NT, SEL, false, 3074>;
+    if (p->cfg.cols == 2048) fk = unif ? k_hough<R, NT, SEL, false, 2050, true> : k_hough<R, NT, SEL, false, 2050>;
   }
   if constexpr (R == 16 && NT == 1024) {
-    if (!xd && p->cfg.cols == 3072) fn = k_hough<R, NT, SEL, false, 3074>;
+    if (p->cfg.cols == 3072) fk = unif ? k_hough<R, NT, SEL, false, 3074, true> : k_hough<R, NT, SEL, false, 3074>;
   }
+  auto fn = xd ? k_hough<R, NT, SEL, true> : fk;
   auto fl = k_hough_list<R, NT, SEL>;
   if (prepare) {
-    // both kernels also hold a few bytes of static shared memory (the tile counter)
+    // the kernels this plan launches; each also holds a few bytes of static shared memory (the
+    // tile counter)
     auto set_max = [](const void* f) -> int {
       cudaFuncAttributes fa{};
       GFH_CUDA_TRY(cudaFuncGetAttributes(&fa, f));
@@ -573,10 +600,8 @@ int launch_hough_t(gfh_plan* p, const gfh_peaks* peaks, const TileDev* tiles, in
                                         (int)(kMaxSmemBytes - fa.sharedSizeBytes)));
       return GFH_OK;
     };
-    int rc = set_max((const void*)k_hough<R, NT, SEL, false>);
+    int rc = set_max((const void*)fk);
     if (!rc) rc = set_max((const void*)k_hough<R, NT, SEL, true>);
-    if (!rc && fn != k_hough<R, NT, SEL, false> && fn != k_hough<R, NT, SEL, true>)
-      rc = set_max((const void*)fn);
     if (!rc) rc = set_max((const void*)fl);
     return rc;
   }

@@ -7,6 +7,7 @@ module fails loudly when the library has not been built.
 """
 from __future__ import annotations
 
+import atexit
 import ctypes
 import dataclasses
 import pathlib
@@ -90,7 +91,7 @@ class PeaksC(ctypes.Structure):
 
 class TileConfigC(ctypes.Structure):
     _fields_ = [("rows", ctypes.c_int32), ("cols", ctypes.c_int32),
-                ("threads", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("threads", ctypes.c_int32), ("form", ctypes.c_int32)]
 
 
 CANDIDATE_BYTES = ctypes.sizeof(CandidateC)   # 64
@@ -313,14 +314,32 @@ def grid_columns(g: Grid):
 
 # ---- GPU entry points -------------------------------------------------------------------------
 
+_LIVE_CONTEXTS = weakref.WeakSet()
+
+
+@atexit.register
+def _close_live_contexts() -> None:
+    """Contexts (and their plans and networks) still open at exit are destroyed while the CUDA
+    runtime and the caller's streams are still alive, not in whatever order the interpreter's
+    teardown collects them."""
+    for c in list(_LIVE_CONTEXTS):
+        try:
+            c.close()
+        except Exception:
+            pass
+
+
 class Context:
-    """gfh_create / gfh_destroy; `stream` is a torch.cuda.Stream, a raw handle or None."""
+    """gfh_create / gfh_destroy; `stream` is a torch.cuda.Stream, a raw handle or None.  The
+    context keeps a reference to the stream object, so the stream outlives it."""
 
     def __init__(self, device: int = 0, stream=None):
         self._h = ctypes.c_void_p()
         _ok(lib().gfh_create(ctypes.byref(self._h), device, _stream_handle(stream)), "gfh_create")
         self.device = device
+        self._stream = stream
         self._children = weakref.WeakSet()     # plans and networks: destroyed before the context
+        _LIVE_CONTEXTS.add(self)
 
     def _adopt(self, child) -> None:
         self._children.add(child)
@@ -331,6 +350,7 @@ class Context:
 
     def set_stream(self, stream) -> None:
         _ok(lib().gfh_set_stream(self._h, _stream_handle(stream)), "gfh_set_stream")
+        self._stream = stream
 
     def check(self) -> int:
         """gfh_check: GFH_OK or GFH_ERR_INPUT (does not raise)."""
@@ -490,13 +510,14 @@ class Plan:
         _ok(lib().gfh_plan_execute(self._h, ctypes.byref(pk)), "gfh_plan_execute")
 
     def autotune(self, fft_idx, bins, offsets, n_lists: int, reps: int = 3):
-        """gfh_plan_autotune: returns ((rows, cols, threads), ms per execute) of the chosen shape."""
+        """gfh_plan_autotune: returns ((rows, cols, threads, form), ms per execute) of the chosen
+        shape."""
         pk = PeaksC(_ptr(fft_idx), _ptr(bins), _ptr(offsets), n_lists)
         best = TileConfigC()
         ms = ctypes.c_float()
         _ok(lib().gfh_plan_autotune(self._h, ctypes.byref(pk), reps, ctypes.byref(best),
                                     ctypes.byref(ms)), "gfh_plan_autotune")
-        return (best.rows, best.cols, best.threads), ms.value
+        return (best.rows, best.cols, best.threads, best.form), ms.value
 
     def set_coarse(self, coarse_k: int, coarse_x: int, max_sel: int) -> None:
         _ok(lib().gfh_plan_set_coarse(self._h, coarse_k, coarse_x, max_sel), "gfh_plan_set_coarse")

@@ -49,9 +49,11 @@ def medium_case(seed, n=5.0, n_k=37, n_fft=60, nb=300, bin_lo=200, density=0.08,
     return fields, fi, bj
 
 
+# (rows, cols, threads[, drawing form]); form 1 draws one form per warp
 TILES = [(8, 128, 256), (16, 1024, 512), (16, 3072, 512), (32, 640, 256), (8, 4096, 512),
          (32, 1536, 256), (16, 384, 512), (8, 3072, 512), (8, 2048, 512), (16, 3072, 1024),
-         (32, 1024, 1024), (16, 640, 1024)]
+         (32, 1024, 1024), (16, 640, 1024), (8, 128, 256, 1), (16, 3072, 1024, 1),
+         (8, 3072, 512, 1), (4, 1024, 256, 1)]
 
 
 @pytest.mark.parametrize("tile", TILES, ids=str)
