@@ -198,8 +198,8 @@ def measure_smem_atomics(ctx, stream, reps=3, iters=16384, threads=1024):
     return out
 
 
-def traffic_for(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None when the kernel's
+def profile_record(kernel):
+    """The committed ncu record of `kernel` (profiles/traffic.json), or None when the kernel's
     source changed since the counters were taken."""
     p = ROOT / "profiles" / "traffic.json"
     if not p.exists():
@@ -208,7 +208,28 @@ def traffic_for(kernel):
     if not rec:
         return None
     src = (ROOT / rec["source"]).read_bytes()
-    return rec["bytes_per_launch"] if hashlib.sha256(src).hexdigest() == rec["sha256"] else None
+    return rec if hashlib.sha256(src).hexdigest() == rec["sha256"] else None
+
+
+def traffic_for(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None when the kernel's
+    source changed since the counters were taken."""
+    rec = profile_record(kernel)
+    return rec["bytes_per_launch"] if rec else None
+
+
+def issue_roofline(updates_per_s, sms, sm_mhz):
+    """k_hough against the SMs' instruction issue: warp instructions per update from the committed
+    ncu record (all of the kernel's instructions) times the measured update rate, against 4 warp
+    instructions per clock per SM at the SM clock sampled under load; None without a record."""
+    rec = profile_record("k_hough")
+    if not rec or "warp_inst_per_update" not in rec:
+        return None
+    achieved = updates_per_s * rec["warp_inst_per_update"] / 1e9
+    peak = sms * 4 * sm_mhz * 1e6 / 1e9
+    return {"achieved": achieved, "peak": peak, "unit": "Gwarp-inst/s", "frac": achieved / peak,
+            "warp_inst_per_update": rec["warp_inst_per_update"],
+            "peak_source": f"{sms} SMs x 4 schedulers x {sm_mhz:.0f} MHz (sampled under load)"}
 
 
 
@@ -769,6 +790,9 @@ def run_gpu(args):
                          "peakmap_and_host": ms_direct - ms_hough},
         "roofline": {**atomic_roofline(ctx, stream, achieved),
                      "traffic": traffic_for("k_hough") if args.workload == "plain_paper" and not args.maps else None,
+                     "issue": issue_roofline(updates / (ms_hough * 1e-3), atomic_peak(ctx, stream)[1]["sms"],
+                                             (clocks or {}).get("sm_mhz") or 2070.0)
+                     if args.workload == "plain_paper" and not args.maps else None,
                      "hbm": {"map_store_bytes": map_bytes, "achieved_gbs": map_bytes / (ms_hough * 1e-3) / 1e9,
                              "peak_gbs": HBM_PEAK, "frac": map_bytes / (ms_hough * 1e-3) / 1e9 / HBM_PEAK,
                              "peak_source": HBM_PEAK_SRC}},
