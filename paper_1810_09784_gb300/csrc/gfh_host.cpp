@@ -402,6 +402,59 @@ void tile_bins(const gfh_grid& g, const HostMap& hm, int64_t s_min, int64_t s_ma
   *jb = g.bin_lo + b;
 }
 
+// Bins per tile of the coarse-tile search's FFT sub-ranges (8 bytes each in shared memory) that
+// fit beside a tile of `base` bytes without lowering the blocks per SM (228 KB per SM, 1 KB of it
+// reserved per block, at most the Hough kernels' limit per block), at most 1024.
+int sub_capacity(size_t base, int threads) {
+  constexpr size_t kSmemSM = 228 * 1024, kReserve = 1024, kOwn = kMaxSmemBytes - kHoughSmemLimit;
+  const int blocks = (int)std::min<size_t>(kSmemSM / (base + kOwn + kReserve), (size_t)(2048 / threads));
+  if (blocks < 1) return 0;
+  const size_t room = std::min(kSmemSM / blocks - kReserve - kOwn, kHoughSmemLimit);
+  if (room <= base + 16) return 0;
+  const size_t cap = std::min<size_t>((room - base - 16) / 8, 1024);
+  return cap >= 32 ? (int)cap : 0;
+}
+
+// Number of FFTs whose interval of bin jl (local) meets columns c0 .. ub on some of the R rows
+// from row0 (B_i + r S_i does not fall as i grows when k_min >= 0: two bisections).
+int64_t window_ffts(const gfh_grid& g, const HostMap& hm, int jl, int row0, int R, int64_t c0,
+                    int64_t ub) {
+  const int64_t x_hi = hm.U[jl] - 1 - (c0 << GFH_FRAC_BITS);
+  const int64_t y_lo = hm.U[jl + 1] - ((ub + 1) << GFH_FRAC_BITS);
+  const int64_t r_last = (int64_t)row0 + R - 1;
+  int lo = 0, hi = g.n_fft;
+  while (lo < hi) {
+    const int mid = (lo + hi) / 2;
+    if (hm.B[mid] + (int64_t)row0 * hm.S[mid] <= x_hi) lo = mid + 1; else hi = mid;
+  }
+  const int last = lo - 1;
+  lo = 0;
+  hi = last + 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) / 2;
+    if (hm.B[mid] + r_last * hm.S[mid] > y_lo) hi = mid; else lo = mid + 1;
+  }
+  return last - lo + 1;
+}
+
+// Whether a tile of the coarse-tile search walks only its bins' FFT sub-ranges: they fit
+// (sub_cap), the shifts grow with the FFT (k_min >= 0) and, over up to 8 bins sampled across the
+// tile's bin range, at most half the (FFT, bin) pairs read meet the tile.
+bool tile_walks_sub_ranges(const gfh_grid& g, const HostMap& hm, const TileDev& t, int R,
+                           int sub_cap) {
+  const int nb = t.bin_b - t.bin_a + 1;
+  if (sub_cap <= 0 || nb <= 0 || nb > sub_cap || g.k_min < 0.0 || g.n_fft < 1) return false;
+  const int64_t c0 = t.col0;
+  const int64_t ub = std::min<int64_t>(c0 + t.ncols - 1, g.n_x0 - 1);
+  const int samples = std::min(nb, 8);
+  int64_t meet = 0;
+  for (int q = 0; q < samples; ++q) {
+    const int jl = t.bin_a - g.bin_lo + (int)((int64_t)q * (nb - 1) / std::max(1, samples - 1));
+    meet += std::max<int64_t>(0, window_ffts(g, hm, jl, t.row0, R, c0, ub));
+  }
+  return (double)meet <= 0.5 * (double)samples * (double)g.n_fft;
+}
+
 // Tiles of map m covering rows [r0, r1) x columns [c_lo, c_hi) (c_lo, c_hi multiples of 4) with
 // the plan's tile shape; appended to `tiles`.
 void map_tiles(const gfh_grid& g, const HostMap& hm, int m, const gfh_tile_config& tc, int r0,
@@ -649,6 +702,15 @@ extern "C" int gfh_plan_set_coarse(gfh_plan* p, int32_t coarse_k, int32_t coarse
   const int nct = coarse_k * coarse_x;
   std::vector<TileDev> fine;
   std::vector<int32_t> first;
+  // the search's tile, chunk sums and band keys; the FFT sub-ranges fit in what the list kernel's
+  // occupancy leaves
+  const int sub_cap = sub_capacity((size_t)p->cfg.rows * (p->cfg.cols + 2) * 4 + 32 * 4 +
+                                       (p->select ? (size_t)p->max_tile_bands * 8 + 64 : 0),
+                                   p->cfg.threads);
+  std::vector<CoarseMapDev> cms(p->n_maps);
+  std::vector<size_t> fblk_off(p->n_maps);
+  size_t fblk_total = 0;
+  int n_lists = 0, fblk_entries = 0;
   first.reserve((size_t)p->n_maps * (nct + 1) + 1);
   int max_fine = 0, max_bands = p->max_tile_bands;
   size_t worst = 0;                        // longest gathered list: every map at its largest
@@ -659,6 +721,22 @@ extern "C" int gfh_plan_set_coarse(gfh_plan* p, int32_t coarse_k, int32_t coarse
     if (rc) return rc;
     rc = gfh_host_columns(&g, hm.band, hm.f0, hm.f0n);
     if (rc) return rc;
+    const size_t map_begin = fine.size();
+    {
+      CoarseMapDev& cm = cms[m];
+      const int J = g.bin_hi - g.bin_lo + 1;
+      cm.nb1 = (g.n_fft + kFftBlock - 1) / kFftBlock + 1;
+      cm.list = g.list;
+      cm.b0 = hm.B[0];
+      cm.s0 = hm.S[0];
+      cm.db = g.n_fft > 1 ? (double)(hm.B[g.n_fft - 1] - hm.B[0]) / (g.n_fft - 1) : 0.0;
+      cm.ds = g.n_fft > 1 ? (double)(hm.S[g.n_fft - 1] - hm.S[0]) / (g.n_fft - 1) : 0.0;
+      if ((int64_t)J * cm.nb1 > INT32_MAX) return GFH_ERR_SIZE;
+      fblk_off[m] = fblk_total;
+      fblk_total += (size_t)J * cm.nb1;
+      fblk_entries = std::max(fblk_entries, J * cm.nb1);
+      n_lists = std::max(n_lists, g.list + 1);
+    }
     // columns of each f0 tile: analysis columns only; f0 falls with the column, so each range is
     // contiguous
     std::vector<int64_t> cmin(coarse_x, INT64_MAX), cmax(coarse_x, -1);
@@ -694,6 +772,8 @@ extern "C" int gfh_plan_set_coarse(gfh_plan* p, int32_t coarse_k, int32_t coarse
     const size_t before = fine.size();
     map_tiles(g, hm, m, p->cfg, 0, g.n_k, 0, g.ld_x0, fine, max_bands);
     const size_t whole = fine.size() - before;
+    for (size_t q = map_begin; q < fine.size(); ++q)
+      fine[q].sub = tile_walks_sub_ranges(g, hm, fine[q], p->cfg.rows, sub_cap) ? 1 : 0;
     std::sort(sizes.begin(), sizes.end(), std::greater<int>());
     size_t top = 0;
     for (int i = 0; i < max_sel && i < (int)sizes.size(); ++i) top += sizes[i];
@@ -701,8 +781,11 @@ extern "C" int gfh_plan_set_coarse(gfh_plan* p, int32_t coarse_k, int32_t coarse
   }
   first.push_back((int32_t)fine.size());
   if (fine.size() > (size_t)INT32_MAX || worst > (size_t)INT32_MAX) return GFH_ERR_SIZE;
+  if (max_bands > p->max_tile_bands + 8) {   // the sub-range room assumed the plan's band keys
+    for (TileDev& t : fine) t.sub = 0;
+  }
   const size_t smem = (size_t)p->cfg.rows * (p->cfg.cols + 2) * 4 + 32 * 4 +
-                      (p->select ? (size_t)max_bands * 8 : 0);
+                      (p->select ? (size_t)max_bands * 8 : 0) + (size_t)sub_cap * 8 + 16;
   if (smem > kHoughSmemLimit) return GFH_ERR_SIZE;
 
   size_t off = 0;
@@ -711,16 +794,22 @@ extern "C" int gfh_plan_set_coarse(gfh_plan* p, int32_t coarse_k, int32_t coarse
   const size_t o_first = take(sizeof(int32_t) * first.size());
   const size_t o_sel = take(sizeof(TileDev) * std::max<size_t>(worst, 1));
   const size_t o_cnt = take(2 * sizeof(int));
+  const size_t o_cms = take(sizeof(CoarseMapDev) * p->n_maps);
+  const size_t o_uns = take(sizeof(int) * std::max(n_lists, 1));
+  const size_t o_fblk = take(sizeof(int32_t) * std::max<size_t>(fblk_total, 1));
   GFH_CUDA_TRY(cudaSetDevice(p->ctx->device));
   if (p->ctx->stream) GFH_CUDA_TRY(cudaStreamSynchronize(p->ctx->stream));
   void* buf = nullptr;
   if (cudaMalloc(&buf, off) != cudaSuccess) return GFH_ERR_NOMEM;
   char* base = (char*)buf;
+  for (int m = 0; m < p->n_maps; ++m) cms[m].fblk = (int32_t*)(base + o_fblk) + fblk_off[m];
   cudaError_t e = cudaSuccess;
   if (!fine.empty())
     e = cudaMemcpy(base + o_fine, fine.data(), sizeof(TileDev) * fine.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(base + o_first, first.data(), sizeof(int32_t) * first.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(base + o_cms, cms.data(), sizeof(CoarseMapDev) * cms.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) { cudaFree(buf); return GFH_ERR_CUDA; }
   if (p->d_coarse_buf) cudaFree(p->d_coarse_buf);
   p->d_coarse_buf = buf;
@@ -734,6 +823,13 @@ extern "C" int gfh_plan_set_coarse(gfh_plan* p, int32_t coarse_k, int32_t coarse
   p->max_sel = max_sel;
   p->max_fine = max_fine;
   p->max_tile_bands = max_bands;
+  p->d_cmaps = (CoarseMapDev*)(base + o_cms);
+  p->d_fft_unsorted = (int*)(base + o_uns);
+  p->n_list_flags = std::max(n_lists, 1);
+  p->sub_cap = sub_cap;
+  p->fblk_entries = fblk_entries;
+  p->n_sub_tiles = 0;
+  for (const TileDev& t : fine) p->n_sub_tiles += t.sub;
   return GFH_OK;
 }
 

@@ -45,15 +45,42 @@ __device__ __forceinline__ unsigned long long cand_key(int count, uint32_t lin) 
 
 // ---- per-execute preparation --------------------------------------------------------------------
 
-// Flags peak lists whose bins are not sorted ascending.
-__global__ void k_check_sorted(const uint32_t* __restrict__ bins, const int64_t* __restrict__ off,
-                               unsigned int* flag) {
+// Flags peak lists whose bins are not sorted ascending.  fft_unsorted (may be null; n_flags
+// entries, zeroed before): 1 for a list in which some bin's peaks are not in FFT order (the
+// coarse-tile search then walks that list's peaks in full).
+__global__ void k_check_sorted(const uint32_t* __restrict__ bins, const uint32_t* __restrict__ fft,
+                               const int64_t* __restrict__ off, unsigned int* flag,
+                               int* __restrict__ fft_unsorted, int n_flags) {
   const int l = blockIdx.y;
   const int64_t b = off[l], e = off[l + 1];
+  const bool check_fft = fft_unsorted && l < n_flags;
   for (int64_t p = b + 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < e;
        p += (int64_t)gridDim.x * blockDim.x) {
-    if (bins[p] < bins[p - 1]) atomicOr(flag, GFH_FLAG_UNSORTED);
+    const uint32_t j1 = bins[p], j0 = bins[p - 1];
+    if (j1 < j0) atomicOr(flag, GFH_FLAG_UNSORTED);
+    else if (check_fft && j1 == j0 && fft[p] < fft[p - 1]) fft_unsorted[l] = 1;
   }
+}
+
+// Per map (blockIdx.y), bin jl and FFT block b: the offset in the bin's peaks of its first peak
+// with FFT index >= kFftBlock b (the bin's count when none), by bisection over the bin's FFT
+// indices.  Meaningful for lists whose bins hold their peaks in FFT order.
+__global__ void k_fft_blocks(const MapDev* __restrict__ maps, const CoarseMapDev* __restrict__ cmaps,
+                             const uint32_t* __restrict__ fft) {
+  const MapDev& md = maps[blockIdx.y];
+  const CoarseMapDev& cm = cmaps[blockIdx.y];
+  const int J = md.bin_hi - md.bin_lo + 1;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= J * cm.nb1) return;
+  const int jl = e / cm.nb1, b = e - jl * cm.nb1;
+  const int64_t s = md.csr[jl], t = md.csr[jl + 1];
+  const uint32_t key = (uint32_t)b * (uint32_t)kFftBlock;
+  int64_t lo = s, hi = t;
+  while (lo < hi) {
+    const int64_t mid = lo + ((hi - lo) >> 1);
+    if (__ldg(fft + mid) < key) lo = mid + 1; else hi = mid;
+  }
+  cm.fblk[e] = (int32_t)(lo - s);
 }
 
 // csr[e] = index of the first peak of the map's list whose bin is >= bin_lo + e.
@@ -112,6 +139,33 @@ template <int R>
 __device__ __forceinline__ bool meets_tile(int64_t a, int64_t b1, int64_t s, int c0, int ub) {
   return (b1 >> GFH_FRAC_BITS) >= (int64_t)c0 &&
          ((a - (int64_t)(R - 1) * s) >> GFH_FRAC_BITS) <= (int64_t)ub;
+}
+
+// Largest i in [-1, n) with shift B_i + r S_i <= x on row r; with k_min >= 0 the shift does not
+// fall as i grows (t_i grows, dk > 0).  The guess comes from the straight line through the
+// table's first and last rows (B_i and S_i are floors of linear functions of t_i, so it is off by
+// far less than one FFT); the table confirms it with two loads issued together, and a bisection
+// over the table settles a guess it does not confirm.
+__device__ __forceinline__ int last_shift_at_most(const longlong2* __restrict__ BS, int n,
+                                                  int64_t r, int64_t x, int64_t base0,
+                                                  double inv_slope) {
+  int i;
+  if (inv_slope > 0.0) {
+    const double e = floor((double)(x - base0) * inv_slope);
+    i = e < -1.0 ? -1 : (e > (double)(n - 1) ? n - 1 : (int)e);
+  } else {
+    i = x >= base0 ? n - 1 : -1;        // every row of the table holds the same shift
+  }
+  const longlong2 a = __ldg(BS + max(i, 0));
+  const longlong2 b = __ldg(BS + min(i + 1, n - 1));
+  if ((i < 0 || a.x + r * a.y <= x) && (i + 1 >= n || b.x + r * b.y > x)) return i;
+  int lo = 0, hi = n;                   // count of the FFTs with shift <= x
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    const longlong2 bs = __ldg(BS + mid);
+    if (bs.x + r * bs.y <= x) lo = mid + 1; else hi = mid;
+  }
+  return lo - 1;
 }
 
 // Events of one peak on the R rows of a tile (layout described at k_hough below).  The interval
@@ -239,12 +293,24 @@ __device__ __forceinline__ void draw_peak_x(int* G0, int lds, int64_t a, int64_t
 // Shared memory: G[R][C+2] | tot[32] row-0 chunk sums | skey[bands] candidate keys.
 // XD (maps whose line moves more than two x0 columns per k row): every row differenced along x0
 // and scanned on its own; chunk sums tot[R][32].
-template <int R, int NT, bool SELECT, bool XD = false, int LDS = 0, bool UNIF = false>
+//
+// SUB (the coarse-tile search): a tile flagged `sub` whose list holds each bin's peaks in FFT
+// order walks only, per read bin, the peaks of the FFTs whose interval can meet it.  On a narrow
+// tile over k rows where the FFTs' shifts spread far wider than the tile, most peaks of its bins
+// miss it.  Each bin's window of FFTs comes from the shift table (last_shift_at_most), its peaks
+// from the FFT-block index (whole 64-FFT blocks, so a few peaks outside the window are read and
+// dropped by the meets test).  The bins' start offsets and a prefix sum of their counts take the
+// last 8 sub_cap + 16 bytes of the dynamic shared memory.
+template <int R, int NT, bool SELECT, bool XD = false, int LDS = 0, bool UNIF = false,
+          bool SUB = false>
 __device__ __forceinline__ void hough_tile(const MapDev* __restrict__ maps, const TileDev t,
                                            const uint32_t* __restrict__ fft_idx,
                                            const uint32_t* __restrict__ bins,
                                            unsigned int* __restrict__ flag, int c_max,
-                                           unsigned char* smem) {
+                                           unsigned char* smem,
+                                           const CoarseMapDev* __restrict__ cmaps = nullptr,
+                                           const int* __restrict__ fft_unsorted = nullptr,
+                                           int sub_cap = 0) {
   constexpr int NW = NT / kLane;
   const MapDev& md = maps[t.map];
   const int C = t.ncols;
@@ -256,20 +322,80 @@ __device__ __forceinline__ void hough_tile(const MapDev* __restrict__ maps, cons
   unsigned long long* skey = reinterpret_cast<unsigned long long*>(tot + (XD ? R : 1) * kLane);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nb_tile = t.band_hi >= t.band_lo ? t.band_hi - t.band_lo + 1 : 0;
+  const int c0 = (int)t.col0;
+  const int c1m1 = c0 + C - 1;                   // last column of the tile
+  const int ub = min(c1m1, (int)md.W - 1);       // ... and of the map
+  const int nbw = t.bin_b - t.bin_a + 1;         // bins read
+  bool use_sub = false;
+  int* sub_pre = nullptr;                        // per read bin: first walk index (then the total)
+  int* sub_st = nullptr;                         // per read bin: its first peak, from the tile's
+  if constexpr (SUB) {
+    use_sub = t.sub != 0 && nbw > 0 && nbw <= sub_cap && fft_unsorted[cmaps[t.map].list] == 0;
+    uint32_t dyn_bytes;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn_bytes));
+    sub_pre = reinterpret_cast<int*>(smem + dyn_bytes - (8u * (uint32_t)sub_cap + 16u));
+    sub_st = sub_pre + sub_cap + 2;
+  }
 
   for (int i = tid; i < R * lds / 2; i += NT) reinterpret_cast<int2*>(G)[i] = make_int2(0, 0);
   if (SELECT)
     for (int i = tid; i < nb_tile; i += NT) skey[i] = 0ull;
+  if constexpr (SUB) {
+    if (use_sub) {
+      // per read bin: its window of FFTs, then its peaks in those FFTs' blocks
+      const CoarseMapDev& cm = cmaps[t.map];
+      const int64_t pb0 = md.csr[t.bin_a - md.bin_lo];
+      const int64_t r0 = t.row0, r1 = (int64_t)t.row0 + (R - 1);
+      const double sl0 = cm.db + (double)r0 * cm.ds, sl1 = cm.db + (double)r1 * cm.ds;
+      const double inv0 = sl0 > 0.0 ? 1.0 / sl0 : 0.0, inv1 = sl1 > 0.0 ? 1.0 / sl1 : 0.0;
+      for (int q = tid; q < nbw; q += NT) {
+        const int jl = t.bin_a - md.bin_lo + q;
+        const longlong2 up = __ldg(md.UP + jl);
+        // right edge on the first row reaches c0; left edge on the last row stays left of ub + 1
+        const int last = last_shift_at_most(md.BS, md.n_fft, r0,
+                                            up.y - 1 - ((int64_t)c0 << GFH_FRAC_BITS),
+                                            cm.b0 + r0 * cm.s0, inv0);
+        const int first = last_shift_at_most(md.BS, md.n_fft, r1,
+                                             up.x - ((int64_t)(ub + 1) << GFH_FRAC_BITS),
+                                             cm.b0 + r1 * cm.s0, inv1) + 1;
+        int st = 0, cnt = 0;
+        if (first <= last) {
+          const int32_t* fb = cm.fblk + (int64_t)jl * cm.nb1;
+          const int o0 = fb[first / kFftBlock], o1 = fb[last / kFftBlock + 1];
+          st = (int)(md.csr[jl] - pb0) + o0;
+          cnt = o1 - o0;
+        }
+        sub_st[q] = st;
+        sub_pre[q] = cnt;
+      }
+    }
+  }
   __syncthreads();
+  if constexpr (SUB) {
+    if (use_sub) {
+      // exclusive prefix of the counts (warp 0, 32 consecutive runs), the total after them
+      if (warp == 0) {
+        const int per = (nbw + kLane - 1) / kLane;
+        const int q0 = min(lane * per, nbw), q1 = min(q0 + per, nbw);
+        int sum = 0;
+        for (int q = q0; q < q1; ++q) sum += sub_pre[q];
+        const int incl = warp_incl_scan(sum, lane);
+        int run = incl - sum;
+        for (int q = q0; q < q1; ++q) {
+          const int c = sub_pre[q];
+          sub_pre[q] = run;
+          run += c;
+        }
+        if (lane == kLane - 1) sub_pre[nbw] = incl;
+      }
+      __syncthreads();
+    }
+  }
 
   // ---- accumulate
   if (t.bin_a <= t.bin_b) {
     const int64_t pb = md.csr[t.bin_a - md.bin_lo];
     const int64_t pe = md.csr[t.bin_b - md.bin_lo + 1];
-    const int wm1 = (int)md.W - 1;
-    const int c0 = (int)t.col0;
-    const int c1m1 = c0 + C - 1;                 // last column of the tile
-    const int ub = min(c1m1, wm1);
     const uint32_t nfft = (uint32_t)md.n_fft;
     const unsigned jmax = (unsigned)(md.bin_hi - md.bin_lo);
     const int bin_lo = md.bin_lo;                // map fields read once, kept in registers
@@ -289,42 +415,66 @@ __device__ __forceinline__ void hough_tile(const MapDev* __restrict__ maps, cons
     const uint32_t* const fl = fft_idx + pb;
     const uint32_t* const bl = bins + pb;
     const int np = fits ? (int)(pe - pb) : 0;
-    int p = tid;
-    uint32_t f_nx = 0xffffffffu;                 // indices of peak p + NT
-    int j_nx = 0;
-    int64_t a_cu = 0, b_cu = 0, s_cu = 0;        // interval of peak p
-    bool ok_cu = false;
-    if (p < np) {
-      longlong2 bs, up;
-      ok_cu = peak_rows(BS, UP, bin_lo, __ldg(fl + p), (int)__ldg(bl + p), nfft, jmax, flag,
-                        bs, up);
-      if (ok_cu) peak_interval(t.row0, bs, up, a_cu, b_cu, s_cu);
-    }
-    if (p + NT < np) { f_nx = __ldg(fl + p + NT); j_nx = (int)__ldg(bl + p + NT); }
-    for (; p < np; p += NT) {
-      uint32_t f_nn = 0xffffffffu;               // indices of peak p + 2 NT
-      int j_nn = 0;
-      if (p + 2 * NT < np) { f_nn = __ldg(fl + p + 2 * NT); j_nn = (int)__ldg(bl + p + 2 * NT); }
-      longlong2 bs_nx = make_longlong2(0, 0), up_nx = make_longlong2(0, 0);
-      const bool ok_nx = f_nx != 0xffffffffu &&
-                         peak_rows(BS, UP, bin_lo, f_nx, j_nx, nfft, jmax, flag, bs_nx, up_nx);
-      const bool draw = ok_cu && meets_tile<R>(a_cu, b_cu, s_cu, c0, ub);
-      if constexpr (XD) {
-        if (draw) draw_peak_x<R>(G0, lds, a_cu, b_cu, s_cu, c0, c1m1, ub, carry_x);
-      } else if constexpr (UNIF) {
-        // one drawing form per warp: the interior form when every drawing lane's peak is
-        // interior, else the edge-following form for all, so that a warp never runs both
-        const bool interior = __all_sync(__activemask(),
-                                         !draw || peak_interior<R>(a_cu, b_cu, s_cu, c0, c1m1, ub));
-        if (draw) draw_peak<R>(G0, lds, a_cu, b_cu, s_cu, c0, c1m1, ub, carry, interior);
-      } else {
-        if (draw)
-          draw_peak<R>(G0, lds, a_cu, b_cu, s_cu, c0, c1m1, ub, carry,
-                       peak_interior<R>(a_cu, b_cu, s_cu, c0, c1m1, ub));
+    // walk n peaks; fetch(i, f, j) gives the FFT and bin of the i-th (i < n)
+    auto walk = [&](int n, auto fetch) {
+      int p = tid;
+      uint32_t f_nx = 0xffffffffu;               // indices of peak p + NT
+      int j_nx = 0;
+      int64_t a_cu = 0, b_cu = 0, s_cu = 0;      // interval of peak p
+      bool ok_cu = false;
+      if (p < n) {
+        uint32_t f;
+        int j;
+        fetch(p, f, j);
+        longlong2 bs, up;
+        ok_cu = peak_rows(BS, UP, bin_lo, f, j, nfft, jmax, flag, bs, up);
+        if (ok_cu) peak_interval(t.row0, bs, up, a_cu, b_cu, s_cu);
       }
-      peak_interval(t.row0, bs_nx, up_nx, a_cu, b_cu, s_cu);
-      ok_cu = ok_nx;
-      f_nx = f_nn; j_nx = j_nn;
+      if (p + NT < n) fetch(p + NT, f_nx, j_nx);
+      for (; p < n; p += NT) {
+        uint32_t f_nn = 0xffffffffu;             // indices of peak p + 2 NT
+        int j_nn = 0;
+        if (p + 2 * NT < n) fetch(p + 2 * NT, f_nn, j_nn);
+        longlong2 bs_nx = make_longlong2(0, 0), up_nx = make_longlong2(0, 0);
+        const bool ok_nx = f_nx != 0xffffffffu &&
+                           peak_rows(BS, UP, bin_lo, f_nx, j_nx, nfft, jmax, flag, bs_nx, up_nx);
+        const bool draw = ok_cu && meets_tile<R>(a_cu, b_cu, s_cu, c0, ub);
+        if constexpr (XD) {
+          if (draw) draw_peak_x<R>(G0, lds, a_cu, b_cu, s_cu, c0, c1m1, ub, carry_x);
+        } else if constexpr (UNIF) {
+          // one drawing form per warp: the interior form when every drawing lane's peak is
+          // interior, else the edge-following form for all, so that a warp never runs both
+          const bool interior = __all_sync(__activemask(),
+                                           !draw || peak_interior<R>(a_cu, b_cu, s_cu, c0, c1m1, ub));
+          if (draw) draw_peak<R>(G0, lds, a_cu, b_cu, s_cu, c0, c1m1, ub, carry, interior);
+        } else {
+          if (draw)
+            draw_peak<R>(G0, lds, a_cu, b_cu, s_cu, c0, c1m1, ub, carry,
+                         peak_interior<R>(a_cu, b_cu, s_cu, c0, c1m1, ub));
+        }
+        peak_interval(t.row0, bs_nx, up_nx, a_cu, b_cu, s_cu);
+        ok_cu = ok_nx;
+        f_nx = f_nn; j_nx = j_nn;
+      }
+    };
+    if (SUB && use_sub) {
+      // walk index v: its bin q is the last with sub_pre[q] <= v (empty bins share the prefix of
+      // the next), its peak the bin's first peak + v - sub_pre[q]
+      const int n_sub = fits ? sub_pre[nbw] : 0;
+      walk(n_sub, [&](int v, uint32_t& f, int& j) {
+        int lo = 0, hi = nbw - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (sub_pre[mid] <= v) lo = mid; else hi = mid - 1;
+        }
+        f = __ldg(fl + sub_st[lo] + (v - sub_pre[lo]));
+        j = t.bin_a + lo;
+      });
+    } else {
+      walk(np, [&](int p, uint32_t& f, int& j) {
+        f = __ldg(fl + p);
+        j = (int)__ldg(bl + p);
+      });
     }
     if constexpr (XD) {
 #pragma unroll
@@ -468,13 +618,15 @@ k_hough(const MapDev* __restrict__ maps, const TileDev* __restrict__ tiles, int 
 // Persistent blocks over a tile list whose length is known on the device only (the coarse-tile
 // search): each block takes the next tile from a counter until the list is exhausted.  Its tiles
 // are mostly narrow (a coarse tile's columns), where many warps mix interior peaks with peaks near
-// an edge, so it always draws one form per warp.
+// an edge, so it always draws one form per warp, and tiles flagged `sub` walk only their bins'
+// FFT sub-ranges (hough_tile).
 template <int R, int NT, bool SELECT>
 __global__ void __launch_bounds__(NT, NT == 1024 ? 1 : (R <= 4 ? 3 : (R == 8 ? 2 : 1)))
 k_hough_list(const MapDev* __restrict__ maps, const TileDev* __restrict__ tiles,
              const int* __restrict__ count, int* __restrict__ next, int cap,
              const uint32_t* __restrict__ fft_idx, const uint32_t* __restrict__ bins,
-             unsigned int* __restrict__ flag, int c_max) {
+             unsigned int* __restrict__ flag, int c_max, const CoarseMapDev* __restrict__ cmaps,
+             const int* __restrict__ fft_unsorted, int sub_cap) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_next;
   const int n = min(*count, cap);
@@ -486,7 +638,9 @@ k_hough_list(const MapDev* __restrict__ maps, const TileDev* __restrict__ tiles,
     int claimed = 0;
     if (threadIdx.x == 0) claimed = atomicAdd(next, 1);
     const TileDev t = tiles[ti];
-    if (t.nrows > 0) hough_tile<R, NT, SELECT, false, 0, true>(maps, t, fft_idx, bins, flag, c_max, smem);
+    if (t.nrows > 0)
+      hough_tile<R, NT, SELECT, false, 0, true, true>(maps, t, fft_idx, bins, flag, c_max, smem,
+                                                      cmaps, fft_unsorted, sub_cap);
     if (threadIdx.x == 0) s_next = claimed;
     __syncthreads();
     ti = s_next;
@@ -620,7 +774,7 @@ int launch_hough_t(gfh_plan* p, const gfh_peaks* peaks, const TileDev* tiles, in
     const int grid = p->ctx->num_sms * (per_sm > 0 ? per_sm : 1);
     fl<<<grid, NT, smem, p->ctx->stream>>>(p->d_maps, tiles, p->d_sel_count, p->d_sel_count + 1,
                                            p->sel_cap, peaks->fft_idx, peaks->bin, p->ctx->d_flag,
-                                           p->cfg.cols);
+                                           p->cfg.cols, p->d_cmaps, p->d_fft_unsorted, p->sub_cap);
   }
   GFH_CUDA_TRY(cudaGetLastError());
   return GFH_OK;
@@ -694,17 +848,26 @@ int gfh_prepare_plan(gfh_plan* p) {
 
 // Per-execute preparation shared by the full and the coarse-tile forms: input check, per-map CSR
 // over bins, zeroed candidate keys.
-static int launch_prologue(gfh_plan* p, const gfh_peaks* peaks) {
+static int launch_prologue(gfh_plan* p, const gfh_peaks* peaks, bool coarse = false) {
   gfh_ctx* ctx = p->ctx;
   cudaStream_t st = ctx->stream;
+  coarse = coarse && p->d_fft_unsorted;
+  if (coarse)
+    GFH_CUDA_TRY(cudaMemsetAsync(p->d_fft_unsorted, 0, sizeof(int) * p->n_list_flags, st));
   {
     dim3 grid(64, peaks->n_lists);
-    k_check_sorted<<<grid, 256, 0, st>>>(peaks->bin, peaks->offsets, ctx->d_flag);
+    k_check_sorted<<<grid, 256, 0, st>>>(peaks->bin, peaks->fft_idx, peaks->offsets, ctx->d_flag,
+                                         coarse ? p->d_fft_unsorted : nullptr, p->n_list_flags);
     GFH_CUDA_TRY(cudaGetLastError());
   }
   k_csr<<<(p->csr_entries + 255) / 256, 256, 0, st>>>(p->d_maps, p->d_csr_map, p->csr_entries,
                                                       peaks->bin, peaks->offsets);
   GFH_CUDA_TRY(cudaGetLastError());
+  if (coarse && p->fblk_entries > 0) {
+    k_fft_blocks<<<dim3((p->fblk_entries + 255) / 256, p->n_maps), 256, 0, st>>>(
+        p->d_maps, p->d_cmaps, peaks->fft_idx);
+    GFH_CUDA_TRY(cudaGetLastError());
+  }
   if (p->select)
     GFH_CUDA_TRY(cudaMemsetAsync(p->d_keys, 0, p->key_words * sizeof(unsigned long long), st));
   return GFH_OK;
@@ -743,9 +906,10 @@ int gfh_launch_plan(gfh_plan* p, const gfh_peaks* peaks) {
 int gfh_launch_plan_tiles(gfh_plan* p, const gfh_peaks* peaks, const int32_t* d_coarse, int n_sel,
                           const int32_t* d_full) {
   GFH_CUDA_TRY(cudaSetDevice(p->ctx->device));
-  const size_t smem = gfh_hough_smem_bytes(p, false);
+  // the list kernel's tile, plus the FFT sub-ranges of up to sub_cap bins
+  const size_t smem = gfh_hough_smem_bytes(p, false) + (size_t)p->sub_cap * 8 + 16;
   if (smem > kHoughSmemLimit) return GFH_ERR_SIZE;
-  int rc = launch_prologue(p, peaks);
+  int rc = launch_prologue(p, peaks, true);
   if (rc) return rc;
   const int nct = p->coarse_k * p->coarse_x;
   cudaStream_t st = p->ctx->stream;

@@ -106,6 +106,19 @@ struct MapDev {
   int32_t csr_base;         // index of this map's first CSR entry in the plan-wide numbering
 };
 
+// Per map, for the coarse-tile search's FFT sub-ranges: an index of each bin's peaks by blocks of
+// kFftBlock FFTs (built per execute, valid when the map's list holds each bin's peaks in FFT
+// order) and the shift B_i + r S_i against i as a line through the table's first and last rows
+// (the starting guess of a bin's FFT window, which the table then confirms).
+constexpr int kFftBlock = 64;
+struct CoarseMapDev {
+  int32_t* fblk;            // [J][nb1]: offset in the bin's peaks of its first peak with FFT >= 64 b
+  int32_t nb1;              // ceil(n_fft / 64) + 1 entries per bin
+  int32_t list;             // the map's peak list
+  int64_t b0, s0;           // B_0, S_0
+  double db, ds;            // (B_last - B_0) / (n_fft - 1), (S_last - S_0) / (n_fft - 1)
+};
+
 // One tile of the accumulation kernel: k rows [row0, row0+nrows) x columns [col0, col0+ncols).
 struct TileDev {
   int32_t map;
@@ -117,6 +130,8 @@ struct TileDev {
   int32_t bin_b;
   int32_t band_lo;    // candidate bands present in the tile's columns (band_hi < 0: none)
   int32_t band_hi;
+  int32_t sub;        // coarse-tile search: walk only each bin's FFT sub-range (see hough_tile)
+  int32_t reserved;
 };
 
 struct gfh_plan {
@@ -152,6 +167,12 @@ struct gfh_plan {
   TileDev* d_sel_tiles = nullptr;      // the gathered tile list (worst case: every map in full)
   int* d_sel_count = nullptr;          // [0] list length, [1] next tile (persistent blocks)
   int sel_cap = 0;                     // capacity of d_sel_tiles
+  CoarseMapDev* d_cmaps = nullptr;     // per map: FFT block index and shift line
+  int* d_fft_unsorted = nullptr;       // per peak list: 1 if some bin's peaks are not in FFT order
+  int n_list_flags = 0;                // entries of d_fft_unsorted (largest list index + 1)
+  int sub_cap = 0;                     // bins per tile the sub-range walk holds in shared memory
+  int fblk_entries = 0;                // largest J * nb1 over the maps (index build grid)
+  int n_sub_tiles = 0;                 // coarse-group fine tiles flagged for the sub-range walk
 };
 
 // Host-side planning (gfh_host.cpp).

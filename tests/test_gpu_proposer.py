@@ -130,6 +130,51 @@ def test_selected_tiles_exact_and_nothing_else(built_lib, gpu_ctx):
             assert (int(rec["count"]), int(rec["row"]), int(rec["col"])) == want, (f["n"], int(rec["band"]))
 
 
+@pytest.mark.parametrize("fft_order", [True, False], ids=["fft-sorted", "fft-shuffled"])
+def test_selected_tiles_high_rows_and_frequencies(built_lib, gpu_ctx, fft_order):
+    """Coarse tiles at the high-f0 end and in the upper k rows, where a tile is a few columns wide
+    and its bins' FFT shifts spread far wider: with each bin's peaks in FFT order the search walks
+    only their FFT sub-ranges; with the FFTs shuffled inside each bin it walks every peak read.
+    Every computed cell equals the oracle's full map, nothing else is written."""
+    gfh = built_lib
+    ns = [2.0, 4.0, 5.5]
+    fields = [SPEC.grid_fields(n, i) for i, n in enumerate(ns)]
+    gs = [gfh.grid_make(gfh.Grid(**f)) for f in fields]
+    maps = [torch.full((g.n_k, g.ld_x0), -7, dtype=torch.int32, device="cuda") for g in gs]
+    cands = [torch.zeros(g.n_bands * 64, dtype=torch.uint8, device="cuda") for g in gs]
+    plan = gfh.Plan(gpu_ctx, gs, maps, cands, tile=(8, 3072, 512))
+    plan.set_coarse(64, 64, 24)
+    lists = [_peaks(s, n)[1] for s, n in zip((21, 22, 23), ns)]
+    rng = np.random.default_rng(6)
+    if not fft_order:
+        shuffled = []
+        for f, b in lists:
+            key = rng.permutation(f.size)
+            o = np.lexsort((key, b))            # bins ascending, FFTs in random order inside a bin
+            shuffled.append((f[o], b[o]))
+        lists = shuffled
+    fi = np.concatenate([l[0] for l in lists])
+    bj = np.concatenate([l[1] for l in lists])
+    offs = np.cumsum([0] + [l[0].size for l in lists]).astype(np.int64)
+    # 24 tiles per map: x0 tiles 40-63, k tiles 32-63 (and two at the top corner)
+    sel = np.stack([rng.choice([kt * 64 + xt for kt in range(32, 64) for xt in range(40, 64)], 24,
+                               replace=False) for _ in ns]).astype(np.int32)
+    sel[:, 0] = 63 * 64 + 63
+    sel[:, 1] = 62 * 64 + 63
+    plan.execute_tiles(to_dev(torch, fi), to_dev(torch, bj), to_dev(torch, offs), 3,
+                       to_dev(torch, sel), 24)
+    torch.cuda.synchronize()
+    assert gpu_ctx.check() == gfh.GFH_OK
+    for m, (f, g) in enumerate(zip(fields, gs)):
+        ref = O.hough_map(oracle_grid(f), lists[m][0], lists[m][1])
+        mask, _ = coarse_mask(f, g, sel[m])
+        got = maps[m].cpu().numpy()
+        W = g.n_x0
+        assert np.array_equal(got[:, :W][mask[:, :W]], ref[mask[:, :W]]), f["n"]
+        assert np.all(got[:, :W][~mask[:, :W]] == -7)
+    plan.close()
+
+
 def test_autotune_keeps_coarse_tiles(built_lib, gpu_ctx):
     gfh = built_lib
     fields = SPEC.grid_fields(3.0)
