@@ -585,8 +585,10 @@ int gfh_conv3x3(gfh_ctx* ctx, int32_t mode, int32_t cin, int32_t cout, int32_t s
  * in one launch of persistent blocks.  Candidates are the best computed cell of each band (count
  * -1 where no cell of the band was computed).  cr and the statistics come from sums over the
  * computed cells only (a cell computed twice counts twice) with the map's full cell count: they
- * are comparable with those of gfh_plan_execute only for maps searched in full.  Asynchronous,
- * allocation-free, capturable.
+ * are comparable with those of gfh_plan_execute only for maps searched in full.  A peak list whose
+ * bins hold their peaks in FFT order (as gfh_peakmap emits them) lets narrow fine tiles read only
+ * the peaks of the FFTs that can meet them; any other bin-sorted list is read in full, with the
+ * same results.  Asynchronous, allocation-free, capturable.
  */
 int gfh_plan_set_coarse(gfh_plan* plan, int32_t coarse_k, int32_t coarse_x, int32_t max_sel);
 int gfh_plan_execute_tiles(gfh_plan* plan, const gfh_peaks* peaks, const int32_t* d_coarse,
