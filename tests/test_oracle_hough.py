@@ -101,6 +101,49 @@ def test_differential_equals_brute_force(seed):
     assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("n,k_min", [(2.0, 0.0), (4.0, 0.0), (5.0, 3e-9), (7.0, 0.0)])
+def test_fft_window_is_exactly_the_meeting_peaks(n, k_min):
+    """With k_min >= 0 the shift B_i + r S_i does not fall as i grows (Sec. IV: x0 = x - (n-1) k
+    t_i with t_i growing), so the FFTs of one bin whose interval meets a block of rows and columns
+    are one contiguous window: those whose right edge on the block's first row is at or right of
+    its first column (a prefix of the FFTs) and whose left edge on its last row is left of its
+    last column + 1 (a suffix).  Checked against a direct test of every row of the block, the
+    window the coarse-tile search walks instead of the bin's whole peak list."""
+    g = small_grid(n=n, bin_lo=200, bin_hi=279, n_fft=90, n_k=60, k_min=k_min)
+    U = np.array(O.edge_positions(g), dtype=np.int64)
+    B, S = (np.array(v, dtype=np.int64) for v in O.fft_shifts(g))
+    assert np.all(np.diff(B) >= 0) and np.all(np.diff(S) >= 0)
+    rng = np.random.default_rng(int(n * 10))
+    for _ in range(40):
+        R = int(rng.choice([4, 8, 16]))
+        row0 = int(rng.integers(0, g.n_k - R + 1))
+        c0 = int(rng.integers(0, g.n_x0))
+        ub = min(g.n_x0 - 1, c0 + int(rng.integers(0, 40)))
+        for jl in range(g.bin_hi - g.bin_lo + 1):
+            # the window: last FFT whose shift on row0 is <= U[jl] - 1 - c0 2^32, first FFT whose
+            # shift on the last row exceeds U[jl+1] - (ub + 1) 2^32
+            last = int(np.searchsorted(B + row0 * S, U[jl] - 1 - (c0 << 32), side="right")) - 1
+            first = int(np.searchsorted(B + (row0 + R - 1) * S, U[jl + 1] - ((ub + 1) << 32),
+                                        side="right"))
+            window = set(range(first, last + 1))
+            # direct: the interval [U[jl+1] - shift, U[jl] - shift) covers a column c0..ub on a row
+            direct = set()
+            for i in range(g.n_fft):
+                for r in range(row0, row0 + R):
+                    sh = B[i] + r * S[i]
+                    lo, hi = (U[jl + 1] - sh) >> 32, (U[jl] - sh - 1) >> 32
+                    if lo <= ub and hi >= c0 and lo <= hi:
+                        direct.add(i)
+                        break
+            assert direct <= window, (jl, row0, R, c0, ub)
+            # and the window is exactly the per-peak test of the extreme edges (right edge on
+            # the first row, left edge on the last) that every drawn peak passes
+            edge_test = {i for i in range(g.n_fft)
+                         if ((U[jl] - B[i] - row0 * S[i] - 1) >> 32) >= c0
+                         and ((U[jl + 1] - B[i] - (row0 + R - 1) * S[i]) >> 32) <= ub}
+            assert edge_test == window, (jl, row0, R, c0, ub)
+
+
 @pytest.mark.parametrize("seed", range(4))
 def test_row_sums_equal_covered_columns(seed):
     """Each row of the map sums to the total number of columns the peaks' intervals overlap,
